@@ -1,0 +1,325 @@
+"""FP64 CPU oracle of the forward-folding likelihood fit - TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference leg
+may import this package. The CUDA library never calls it, and the two share no code: this
+wrapper only marshals the seeded inputs of ``paper_2502_15253_gb300.synth`` into the C
+structures of ``oracle.c`` (its own definitions) and calls the plain FP64 implementation.
+
+Parity status per function (what pins it is in tests/test_oracle_pins.py):
+  survival (Eq. 1 / 3-flavour vacuum) - pinned (zero mixing, 2-flavour limit, brute-force
+      PMNS amplitude, corrected Eq. 10, Eq. 1 vs exact bound)
+  remap (energy correction)           - pinned (identity, shift by whole bins, conservation,
+      brute-force fine-grid integration)
+  deviance / nll / gradient           - pinned (closed forms, Asimov zero, central FD,
+      hand-summed toy model)
+  fit (BFGS)                          - pinned (Asimov recovery, pure-scale closed form,
+      prior-only closed form, brute-force grid scan on a 2-parameter model)
+  sigma (FD Hessian)                  - pinned (prior-only model: 2 H^-1 = V exactly)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+STATUS = {0: "converged", 1: "maxiter", 2: "linesearch_fail", 3: "nonfinite"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (gcc, OpenMP when available)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    base = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+class _OrcModel(C.Structure):
+    _fields_ = [
+        ("n_params", C.c_int),
+        ("theta0", C.POINTER(C.c_double)), ("prior_sigma", C.POINTER(C.c_double)),
+        ("scale", C.POINTER(C.c_double)),
+        ("n_cov", C.c_int), ("cov_size", C.POINTER(C.c_int)), ("cov_idx", C.POINTER(C.c_int)),
+        ("cov", C.POINTER(C.c_double)),
+        ("osc_mode", C.c_int), ("osc_idx", C.c_int * 4), ("osc_val", C.c_double * 4),
+        ("n_cores", C.c_int), ("core_power_idx", C.POINTER(C.c_int)),
+        ("n_true", C.c_int), ("e_lo", C.c_double), ("e_hi", C.c_double),
+        ("n_det", C.c_int), ("det_n_reco", C.POINTER(C.c_int)),
+        ("det_response", C.POINTER(C.c_double)),
+        ("n_ds", C.c_int), ("ds_det", C.POINTER(C.c_int)), ("ds_t", C.POINTER(C.c_double)),
+        ("ds_baseline", C.POINTER(C.c_double)), ("ds_weight", C.POINTER(C.c_double)),
+        ("ds_norm_idx", C.POINTER(C.c_int)), ("ds_eff_idx", C.POINTER(C.c_int)),
+        ("ds_escale_idx", C.POINTER(C.c_int)), ("ds_shape_idx", C.POINTER(C.c_int)),
+        ("n_bkg", C.c_int), ("bkg_ds", C.POINTER(C.c_int)),
+        ("bkg_template", C.POINTER(C.c_double)), ("bkg_rate_idx", C.POINTER(C.c_int)),
+        ("bkg_shape_idx", C.POINTER(C.c_int)),
+    ]
+
+
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int)
+
+
+def _declare(L):
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.POINTER(_OrcModel)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_n_data.restype = C.c_int
+    L.orc_n_data.argtypes = [C.c_void_p]
+    L.orc_survival.restype = C.c_double
+    L.orc_survival.argtypes = [C.c_int, _DP, C.c_double, C.c_double, _DP]
+    L.orc_remap.restype = C.c_int
+    L.orc_remap.argtypes = [C.POINTER(_OrcModel), _DP, _DP, _DP]
+    L.orc_expected.restype = C.c_int
+    L.orc_expected.argtypes = [C.c_void_p, _DP, _DP]
+    L.orc_deviance.restype = C.c_double
+    L.orc_deviance.argtypes = [C.c_double, C.c_double]
+    L.orc_nll.restype = C.c_double
+    L.orc_nll.argtypes = [C.c_void_p, _DP, _DP, C.c_uint32, _DP]
+    L.orc_theta_of_z.argtypes = [C.c_void_p, _DP, _DP]
+    L.orc_z_of_theta.argtypes = [C.c_void_p, _DP, _DP]
+    L.orc_fit.restype = C.c_int
+    L.orc_fit.argtypes = [C.c_void_p, _DP, C.c_uint32, _DP, C.c_double, C.c_int, _DP, _DP, _IP,
+                          _IP, _DP]
+    L.orc_fit_many.argtypes = [C.POINTER(C.c_void_p), C.c_int, _IP, C.POINTER(_DP),
+                               C.POINTER(C.c_uint32), C.POINTER(_DP), C.c_double, C.c_int,
+                               C.POINTER(_DP), _DP, _IP, _IP, _IP, C.c_int]
+    L.orc_openmp_enabled.restype = C.c_int
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_DP)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_IP)
+
+
+def survival(mode: int, p, L: float, E: float, with_grad: bool = False):
+    """Survival probability P(L, E) (Eq. 1 for mode 0, exact 3-flavour vacuum for mode 1)."""
+    pa, pp = _d(p)
+    dp = np.zeros(4)
+    val = lib().orc_survival(int(mode), pp, float(L), float(E), _d(dp)[1] if with_grad else None)
+    if with_grad:
+        # _d returned a view of dp (already float64 contiguous), so dp was written in place
+        return val, dp
+    return val
+
+
+def deviance(n: float, mu: float) -> float:
+    return lib().orc_deviance(float(n), float(mu))
+
+
+class OracleModel:
+    """A ModelSpec marshalled into the oracle's C structure."""
+
+    def __init__(self, spec):
+        self.spec = spec
+        keep = []
+
+        def d(a):
+            arr, ptr = _d(a)
+            keep.append(arr)
+            return ptr
+
+        def i(a):
+            arr, ptr = _i(a)
+            keep.append(arr)
+            return ptr
+
+        s = spec
+        m = _OrcModel()
+        m.n_params = s.n_params
+        m.theta0, m.prior_sigma, m.scale = d(s.theta0), d(s.prior_sigma), d(s.scale)
+        m.n_cov = len(s.cov_blocks)
+        m.cov_size = i([len(ix) for ix, _ in s.cov_blocks] or [0])
+        m.cov_idx = i(np.concatenate([ix for ix, _ in s.cov_blocks]) if s.cov_blocks else [0])
+        m.cov = d(np.concatenate([c.ravel() for _, c in s.cov_blocks]) if s.cov_blocks else [0.0])
+        m.osc_mode = s.osc_mode
+        for k in range(4):
+            m.osc_idx[k] = int(s.osc_idx[k])
+            m.osc_val[k] = float(s.osc_val[k])
+        m.n_cores = s.n_cores
+        m.core_power_idx = i(s.core_power_idx)
+        m.n_true, m.e_lo, m.e_hi = s.n_true, s.e_lo, s.e_hi
+        m.n_det = len(s.detectors)
+        m.det_n_reco = i([dt.n_reco for dt in s.detectors])
+        m.det_response = d(np.concatenate([dt.response.ravel() for dt in s.detectors]))
+        m.n_ds = len(s.datasets)
+        ds = s.datasets
+        m.ds_det = i([x.det for x in ds])
+        m.ds_t = d(np.concatenate([x.t for x in ds]))
+        m.ds_baseline = d(np.concatenate([x.baseline for x in ds]))
+        m.ds_weight = d(np.concatenate([x.weight for x in ds]))
+        m.ds_norm_idx = i([x.norm_idx for x in ds])
+        m.ds_eff_idx = i([x.eff_idx for x in ds])
+        m.ds_escale_idx = i(np.concatenate([x.escale_idx for x in ds]))
+        m.ds_shape_idx = i(np.concatenate([x.shape_idx for x in ds]))
+        bk = [(di, b) for di, x in enumerate(ds) for b in x.backgrounds]
+        m.n_bkg = len(bk)
+        m.bkg_ds = i([di for di, _ in bk] or [0])
+        m.bkg_template = d(np.concatenate([b.template for _, b in bk]) if bk else [0.0])
+        m.bkg_rate_idx = i([b.rate_idx for _, b in bk] or [0])
+        m.bkg_shape_idx = i(np.concatenate([b.shape_idx for _, b in bk]) if bk else [0])
+        self._keep = keep
+        self._m = m
+        self.h = lib().orc_create(C.byref(m))
+        if not self.h:
+            raise ValueError("oracle: a prior covariance block is not symmetric positive definite")
+        self.n_params = s.n_params
+        self.n_data = lib().orc_n_data(self.h)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h and _lib is not None:
+            _lib.orc_destroy(h)
+            self.h = None
+
+    # -- forward model ------------------------------------------------------------------
+    def expected(self, theta) -> np.ndarray:
+        th, tp = _d(theta)
+        mu = np.zeros(self.n_data)
+        st = lib().orc_expected(self.h, tp, mu.ctypes.data_as(_DP))
+        if st:
+            raise ValueError("oracle: energy map not increasing on the grid")
+        return mu
+
+    def nll(self, theta, data, mask=None, grad=False):
+        th, tp = _d(theta)
+        da, dp = _d(data)
+        mask = self.spec.all_mask() if mask is None else mask
+        if grad:
+            g = np.zeros(self.n_params)
+            v = lib().orc_nll(self.h, tp, dp, C.c_uint32(mask), g.ctypes.data_as(_DP))
+            return v, g
+        return lib().orc_nll(self.h, tp, dp, C.c_uint32(mask), None)
+
+    def remap(self, a, u) -> np.ndarray:
+        aa, ap = _d(a)
+        ua, up = _d(u)
+        v = np.zeros(self.spec.n_true)
+        st = lib().orc_remap(C.byref(self._m), ap, up, v.ctypes.data_as(_DP))
+        if st:
+            raise ValueError("oracle: energy map not increasing on the grid")
+        return v
+
+    # -- transformation layer -----------------------------------------------------------
+    def theta_of_z(self, z):
+        za, zp = _d(z)
+        th = np.zeros(self.n_params)
+        lib().orc_theta_of_z(self.h, zp, th.ctypes.data_as(_DP))
+        return th
+
+    def z_of_theta(self, theta):
+        ta, tp = _d(theta)
+        z = np.zeros(self.n_params)
+        lib().orc_z_of_theta(self.h, tp, z.ctypes.data_as(_DP))
+        return z
+
+    # -- minimiser ----------------------------------------------------------------------
+    def fit(self, data, mask=None, start=None, edm_tol=1e-10, max_iter=5000):
+        """Dense BFGS fit. Returns dict(theta, nll, iters, nevals, edm, status)."""
+        mask = self.spec.all_mask() if mask is None else mask
+        start = self.spec.theta0 if start is None else start
+        da, dp = _d(data)
+        sa, sp = _d(start)
+        th = np.zeros(self.n_params)
+        nll, edm = C.c_double(), C.c_double()
+        it, ne = C.c_int(), C.c_int()
+        st = lib().orc_fit(self.h, dp, C.c_uint32(mask), sp, edm_tol, max_iter,
+                           th.ctypes.data_as(_DP), C.byref(nll), C.byref(it), C.byref(ne),
+                           C.byref(edm))
+        return dict(theta=th, nll=nll.value, iters=it.value, nevals=ne.value, edm=edm.value,
+                    status=st)
+
+    def hessian(self, theta, data, mask=None, rel_step=1e-3):
+        """Hessian of -2lnL in theta, by central differences of the analytic gradient.
+
+        Steps are rel_step times each parameter's minimiser scale; the result is symmetrised.
+        """
+        n = self.n_params
+        h = np.where(self.spec.prior_sigma > 0, self.spec.prior_sigma, self.spec.scale) * rel_step
+        H = np.zeros((n, n))
+        for i in range(n):
+            tp = np.array(theta, np.float64)
+            tm = tp.copy()
+            tp[i] += h[i]
+            tm[i] -= h[i]
+            gp = self.nll(tp, data, mask, grad=True)[1]
+            gm = self.nll(tm, data, mask, grad=True)[1]
+            H[:, i] = (gp - gm) / (2.0 * h[i])
+        return 0.5 * (H + H.T)
+
+    def sigma(self, theta, data, mask=None, rel_step=1e-3):
+        """Parameter errors sqrt(2 (H^-1)_ii) at theta (H = Hessian of -2lnL).
+
+        Parameters with no curvature (no data and no prior) get +inf.
+        """
+        H = self.hessian(theta, data, mask, rel_step)
+        live = np.abs(np.diag(H)) > 1e-300
+        sig = np.full(self.n_params, np.inf)
+        if live.any():
+            Hl = H[np.ix_(live, live)]
+            sig[live] = np.sqrt(np.maximum(2.0 * np.diag(np.linalg.inv(Hl)), 0.0))
+        return sig
+
+
+def fit_many(models, model_of, data, masks, starts, edm_tol=1e-10, max_iter=5000, n_threads=None):
+    """Fits many instances on host threads (OpenMP). models: list of OracleModel."""
+    n = len(model_of)
+    n_threads = n_threads or os.cpu_count() or 1
+    hs = (C.c_void_p * len(models))(*[m.h for m in models])
+    mo, mop = _i(model_of)
+    keep = []
+    dptr = (_DP * n)()
+    sptr = (_DP * n)()
+    optr = (_DP * n)()
+    outs = []
+    for i in range(n):
+        a, p = _d(data[i])
+        b, q = _d(starts[i])
+        o = np.zeros(models[model_of[i]].n_params)
+        keep += [a, b]
+        outs.append(o)
+        dptr[i], sptr[i], optr[i] = p, q, o.ctypes.data_as(_DP)
+    mk = np.ascontiguousarray(masks, dtype=np.uint32)
+    nll = np.zeros(n)
+    iters = np.zeros(n, np.int32)
+    nev = np.zeros(n, np.int32)
+    st = np.zeros(n, np.int32)
+    lib().orc_fit_many(hs, n, mop, dptr, mk.ctypes.data_as(C.POINTER(C.c_uint32)), sptr,
+                       edm_tol, max_iter, optr, nll.ctypes.data_as(_DP),
+                       iters.ctypes.data_as(_IP), nev.ctypes.data_as(_IP),
+                       st.ctypes.data_as(_IP), int(n_threads))
+    return dict(theta=outs, nll=nll, iters=iters, nevals=nev, status=st)
+
+
+def openmp_enabled() -> bool:
+    return bool(lib().orc_openmp_enabled())

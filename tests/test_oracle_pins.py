@@ -1,0 +1,418 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test checks one oracle function against an independent source: a brute-force PMNS
+amplitude sum, the paper's closed forms (Eq. 1, the corrected Eq. 10, Eq. 2), library
+probability routines (scipy Poisson PMF, multivariate normal), a fine-grid integration of the
+energy map, closed-form minima, and a brute-force grid scan. A plausible slip in the oracle
+(a dropped term, a wrong sign, a transposed response, a wrong prior matrix) fails at least one.
+"""
+import copy
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_2502_15253_gb300 import synth
+
+K = 1.266932679815373  # dm2[eV^2] L[m] / (4 E[MeV])
+
+
+# ---------------------------------------------------------------------------------------
+# independent survival probabilities
+# ---------------------------------------------------------------------------------------
+def p_amplitude(s12, s13, dm21, dm31, L, E, delta=0.0):
+    """|sum_i |U_ei|^2 exp(-i m_i^2 L / 2E)|^2 from the PMNS first row (m_1 = 0)."""
+    ue = np.array([np.sqrt((1 - s12) * (1 - s13)), np.sqrt(s12 * (1 - s13)),
+                   np.sqrt(s13) * np.exp(-1j * delta)])
+    m2 = np.array([0.0, dm21, dm31])
+    amp = (np.abs(ue) ** 2 * np.exp(-1j * 2.0 * K * m2 * L / E)).sum()
+    return abs(amp) ** 2
+
+
+def p_two_flavour_amplitude(theta, dm2, L, E):
+    """2x2 rotation amplitude: |cos^2 th + sin^2 th exp(-i dm2 L / 2E)|^2."""
+    amp = np.cos(theta) ** 2 + np.sin(theta) ** 2 * np.exp(-1j * 2.0 * K * dm2 * L / E)
+    return abs(amp) ** 2
+
+
+def p_eq10_corrected(s12, s13, dm21, dm31, L, E):
+    """Eq. 10 in its corrected reading (normal ordering, +phi)."""
+    t12, t13 = np.arcsin(np.sqrt(s12)), np.arcsin(np.sqrt(s13))
+    S12, S13 = np.sin(2 * t12) ** 2, np.sin(2 * t13) ** 2
+    dmee = np.cos(t12) ** 2 * abs(dm31) + np.sin(t12) ** 2 * abs(dm31 - dm21)   # Eq. 2
+    d21, dee = K * dm21 * L / E, K * dmee * L / E
+    phi = np.arctan2(np.cos(2 * t12) * np.sin(d21), np.cos(d21)) - d21 * np.cos(2 * t12)
+    return (1 - 0.5 * S13 * (1 - np.sqrt(1 - S12 * np.sin(d21) ** 2) * np.cos(2 * dee + phi))
+            - S12 * np.cos(t13) ** 4 * np.sin(d21) ** 2)
+
+
+GRID = [(L, E) for L in (400.0, 1050.0, 52500.0) for E in np.linspace(1.8, 10.0, 37)]
+
+
+def test_survival_zero_mixing_is_one():
+    for L, E in GRID:
+        assert oracle.survival(0, [0.0, 2.5e-3, 0.0, 7.5e-5], L, E) == 1.0
+        assert oracle.survival(1, [0.0, 0.0, 7.5e-5, 2.5e-3], L, E) == 1.0
+
+
+def test_vacuum3_matches_pmns_amplitude():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        s12, s13 = rng.uniform(0.05, 0.6), rng.uniform(0.0, 0.2)
+        dm21, dm31 = rng.uniform(1e-5, 2e-4), rng.uniform(1e-3, 4e-3)
+        L, E = rng.uniform(100, 6e4), rng.uniform(1.8, 10)
+        delta = rng.uniform(0, 2 * np.pi)          # P_ee does not depend on the CP phase
+        got = oracle.survival(1, [s12, s13, dm21, dm31], L, E)
+        assert got == pytest.approx(p_amplitude(s12, s13, dm21, dm31, L, E, delta), abs=1e-13)
+
+
+def test_vacuum3_matches_corrected_eq10():
+    for L, E in GRID:
+        p = [0.307, 0.022, 7.5e-5, 2.5e-3]
+        assert oracle.survival(1, p, L, E) == pytest.approx(p_eq10_corrected(*p, L, E), abs=1e-13)
+
+
+def test_eq1_two_flavour_limit_matches_rotation_amplitude():
+    for L, E in GRID:
+        th = 0.5 * np.arcsin(np.sqrt(0.09))
+        got = oracle.survival(0, [0.09, 2.5e-3, 0.0, 7.53e-5], L, E)
+        assert got == pytest.approx(p_two_flavour_amplitude(th, 2.5e-3, L, E), abs=1e-14)
+
+
+def test_eq1_with_eq2_close_to_exact_at_short_baseline_only():
+    """Eq. 1 + Eq. 2 approximates the exact probability to < 5e-5 at ~1 km, not at 52 km."""
+    s12, s13, dm21, dm31 = 0.307, 0.022, 7.5e-5, 2.5e-3
+    t12, t13 = np.arcsin(np.sqrt(s12)), np.arcsin(np.sqrt(s13))
+    S12, S13 = np.sin(2 * t12) ** 2, np.sin(2 * t13) ** 2
+    dmee = np.cos(t12) ** 2 * dm31 + np.sin(t12) ** 2 * (dm31 - dm21)
+    short, far = 0.0, 0.0
+    for E in np.linspace(1.8, 10.0, 400):
+        for L, acc in ((1050.0, "s"), (52500.0, "f")):
+            d = abs(oracle.survival(0, [S13, dmee, S12, dm21], L, E)
+                    - p_amplitude(s12, s13, dm21, dm31, L, E))
+            if acc == "s":
+                short = max(short, d)
+            else:
+                far = max(far, d)
+    assert short < 5e-5
+    assert far > 1e-2
+
+
+@pytest.mark.parametrize("mode,p", [(0, [0.09, 2.5e-3, 0.851, 7.53e-5]),
+                                    (1, [0.307, 0.022, 7.5e-5, 2.5e-3])])
+def test_survival_partials_match_central_differences(mode, p):
+    for L, E in GRID[::5]:
+        _, dp = oracle.survival(mode, p, L, E, with_grad=True)
+        for i in range(4):
+            h = 1e-6 * abs(p[i])
+            pp, pm = list(p), list(p)
+            pp[i] += h
+            pm[i] -= h
+            fd = (oracle.survival(mode, pp, L, E) - oracle.survival(mode, pm, L, E)) / (2 * h)
+            assert dp[i] == pytest.approx(fd, rel=1e-6, abs=1e-9 / abs(p[i]))
+
+
+# ---------------------------------------------------------------------------------------
+# energy correction (remap)
+# ---------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c0():
+    spec = synth.make_model("c0")
+    return spec, oracle.OracleModel(spec)
+
+
+def test_remap_identity_bit_exact(c0):
+    spec, om = c0
+    u = np.random.default_rng(1).uniform(0, 10, spec.n_true)
+    assert np.array_equal(om.remap([0.0, 1.0, 0.0], u), u)
+
+
+def test_remap_whole_bin_shift(c0):
+    spec, om = c0
+    de = (spec.e_hi - spec.e_lo) / spec.n_true
+    u = np.random.default_rng(2).uniform(0, 10, spec.n_true)
+    for m in (1, 3, -2):
+        v = om.remap([m * de, 1.0, 0.0], u)
+        ref = np.zeros_like(u)
+        if m > 0:
+            ref[m:] = u[:-m]
+        else:
+            ref[:m] = u[-m:]
+        np.testing.assert_allclose(v, ref, rtol=1e-9, atol=1e-9)
+
+
+def test_remap_conserves_content_inside_grid(c0):
+    spec, om = c0
+    u = np.zeros(spec.n_true)
+    u[30:170] = np.random.default_rng(3).uniform(1, 5, 140)
+    for a in ([0.02, 1.003, -0.0005], [-0.03, 0.99, 0.001], [0.0, 1.0, 0.0008]):
+        assert om.remap(a, u).sum() == pytest.approx(u.sum(), rel=1e-12)
+
+
+def test_remap_matches_fine_grid_integration(c0):
+    """Brute force: split every source bin into 4000 equal pieces, map each piece's centre."""
+    spec, om = c0
+    edges = spec.true_edges
+    u = np.random.default_rng(4).uniform(1, 5, spec.n_true)
+    a = np.array([0.013, 1.004, 0.0007])
+    n_sub = 4000
+    frac = (np.arange(n_sub) + 0.5) / n_sub
+    ref = np.zeros(spec.n_true)
+    for k in range(spec.n_true):
+        x = edges[k] + frac * (edges[k + 1] - edges[k])
+        y = a[0] + a[1] * x + a[2] * x * x
+        t = np.floor((y - spec.e_lo) / (edges[1] - edges[0])).astype(int)
+        ok = (t >= 0) & (t < spec.n_true)
+        np.add.at(ref, t[ok], u[k] / n_sub)
+    np.testing.assert_allclose(om.remap(a, u), ref, rtol=0, atol=2e-3 * u.max())
+
+
+# ---------------------------------------------------------------------------------------
+# deviance, priors, expectation
+# ---------------------------------------------------------------------------------------
+def test_deviance_is_saturated_poisson_ratio():
+    for n in (0, 1, 3, 17, 250, 4000):
+        for mu in (0.3, 2.5, 17.2, 260.0, 3900.0):
+            ref = -2.0 * (stats.poisson.logpmf(n, mu) - stats.poisson.logpmf(n, n)) if n else 2 * mu
+            assert oracle.deviance(n, mu) == pytest.approx(ref, rel=1e-10, abs=1e-10)
+    assert oracle.deviance(42.0, 42.0) == 0.0
+    assert oracle.deviance(5.0, 0.0) == np.inf
+
+
+def test_prior_only_nll_is_gaussian_logpdf():
+    """No dataset enabled: -2lnL is the prior of Eq. 6, i.e. -2 ln N(theta) up to a constant."""
+    spec = synth.make_model("c1")
+    om = oracle.OracleModel(spec)
+    rng = np.random.default_rng(5)
+    theta = om.theta_of_z(rng.standard_normal(spec.n_params))
+    ref = 0.0
+    for i in range(spec.n_params):
+        if spec.prior_sigma[i] > 0:
+            ref += -2 * (stats.norm.logpdf(theta[i], spec.theta0[i], spec.prior_sigma[i])
+                         - stats.norm.logpdf(spec.theta0[i], spec.theta0[i], spec.prior_sigma[i]))
+    for idx, cov in spec.cov_blocks:
+        mvn = stats.multivariate_normal(spec.theta0[idx], cov)
+        ref += -2 * (mvn.logpdf(theta[idx]) - mvn.logpdf(spec.theta0[idx]))
+    assert om.nll(theta, np.zeros(spec.n_bins), mask=0) == pytest.approx(ref, rel=1e-9)
+
+
+def test_transformation_layer_whitens_the_prior():
+    spec = synth.make_model("c1")
+    om = oracle.OracleModel(spec)
+    z = np.random.default_rng(6).standard_normal(spec.n_params)
+    theta = om.theta_of_z(z)
+    np.testing.assert_allclose(om.z_of_theta(theta), z, atol=1e-10)
+    prior_only = om.nll(theta, np.zeros(spec.n_bins), mask=0)
+    constrained = (spec.prior_sigma > 0) | np.isin(np.arange(spec.n_params),
+                                                   np.concatenate([i for i, _ in spec.cov_blocks]))
+    assert prior_only == pytest.approx((z[constrained] ** 2).sum(), rel=1e-9)
+
+
+def test_response_column_sums_equal_efficiency_times_coverage():
+    for name in ("c0", "c1", "c2"):
+        spec = synth.make_model(name)
+        ec = 0.5 * (spec.true_edges[:-1] + spec.true_edges[1:])
+        for det, res in zip(spec.detectors, {"c0": [0.08], "c1": [0.08, 0.08],
+                                             "c2": [0.03, 0.03]}[name]):
+            evis = ec - synth.PROMPT_SHIFT_MEV
+            sig = res * np.sqrt(evis)
+            cover = (stats.norm.cdf((det.reco_edges[-1] - evis) / sig)
+                     - stats.norm.cdf((det.reco_edges[0] - evis) / sig))
+            np.testing.assert_allclose(det.response.sum(0), synth.RESPONSE_EPS0 * cover,
+                                       atol=1e-10)
+
+
+def test_expected_matches_matrix_form_with_amplitude_probability():
+    """mu = eps R (t n s sum_c p_c w_c P_c) + backgrounds at nominal energy scale, with P from
+    the PMNS amplitude and the fold as a library matrix product."""
+    spec = synth.make_model("c2")
+    om = oracle.OracleModel(spec)
+    theta = spec.theta0.copy()
+    rng = np.random.default_rng(7)
+    for i in range(spec.n_params):
+        if not spec.param_names[i].startswith("a"):
+            theta[i] += 0.5 * rng.standard_normal() * (spec.prior_sigma[i] or spec.scale[i])
+    mu = om.expected(theta)
+    s12, s13, dm21, dm31 = theta[spec.osc_idx]
+    ec = 0.5 * (spec.true_edges[:-1] + spec.true_edges[1:])
+    off = spec.data_offsets()
+    for d, ds in enumerate(spec.datasets):
+        ptot = np.zeros(spec.n_true)
+        for c in range(spec.n_cores):
+            pw = theta[spec.core_power_idx[c]]
+            ptot += pw * ds.weight[c] * np.array(
+                [p_amplitude(s12, s13, dm21, dm31, ds.baseline[c], e) for e in ec])
+        u = ds.t * theta[ds.norm_idx] * theta[ds.shape_idx] * ptot
+        ref = spec.detectors[ds.det].response @ u
+        np.testing.assert_allclose(mu[off[d]:off[d + 1]], ref, rtol=1e-11)
+
+
+def test_expected_backgrounds_and_efficiency_c1():
+    spec = synth.make_model("c1")
+    om = oracle.OracleModel(spec)
+    theta = spec.theta0.copy()
+    s13 = spec.index("sin2_2th13")
+    theta[s13] = 0.0
+    theta[spec.index("sin2_2th12")] = 0.0           # no oscillation: P = 1
+    rng = np.random.default_rng(8)
+    bkg = [i for i, n in enumerate(spec.param_names) if "rate" in n or "li9_shape" in n
+           or "acc_shape" in n or n.startswith("eff")]
+    theta[bkg] += 0.05 * rng.standard_normal(len(bkg))
+    mu = om.expected(theta)
+    off = spec.data_offsets()
+    for d, ds in enumerate(spec.datasets):
+        u = ds.t * theta[ds.shape_idx] * (theta[spec.core_power_idx] * ds.weight).sum()
+        ref = theta[ds.eff_idx] * (spec.detectors[ds.det].response @ u)
+        for b in ds.backgrounds:
+            sh = np.where(b.shape_idx >= 0, theta[np.maximum(b.shape_idx, 0)], 0.0)
+            ref = ref + theta[b.rate_idx] * b.template * (1 + sh)
+        np.testing.assert_allclose(mu[off[d]:off[d + 1]], ref, rtol=1e-11)
+
+
+# ---------------------------------------------------------------------------------------
+# -2lnL and gradient
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["c0", "c1", "c2"])
+def test_asimov_nll_is_zero(name):
+    spec = synth.make_model(name)
+    om = oracle.OracleModel(spec)
+    v, g = om.nll(spec.theta0, om.expected(spec.theta0), grad=True)
+    assert abs(v) < 1e-9
+    assert np.abs(g).max() < 1e-6
+
+
+def test_poisson_part_equals_library_pmf_sum():
+    spec = synth.make_model("c1")
+    om = oracle.OracleModel(spec)
+    theta = spec.theta0.copy()
+    mu = om.expected(theta)
+    data = synth.poisson_data(mu, 11)
+    ref = -2.0 * (stats.poisson.logpmf(data, mu) - stats.poisson.logpmf(data, data)).sum()
+    assert om.nll(theta, data) == pytest.approx(ref, rel=1e-10)
+    # masking datasets drops exactly their bins
+    off = spec.data_offsets()
+    m = 0b101
+    keep = np.concatenate([np.arange(off[d], off[d + 1]) for d in (0, 2)])
+    ref_m = -2.0 * (stats.poisson.logpmf(data[keep], mu[keep])
+                    - stats.poisson.logpmf(data[keep], data[keep])).sum()
+    assert om.nll(theta, data, mask=m) == pytest.approx(ref_m, rel=1e-10)
+
+
+@pytest.mark.parametrize("name", ["c0", "c1", "c2"])
+def test_gradient_matches_central_differences(name):
+    spec = synth.make_model(name)
+    om = oracle.OracleModel(spec)
+    rng = np.random.default_rng(9)
+    data = synth.poisson_data(om.expected(spec.theta0), 12)
+    theta = om.theta_of_z(0.4 * rng.standard_normal(spec.n_params))
+    _, g = om.nll(theta, data, grad=True)
+    scale = np.where(spec.prior_sigma > 0, spec.prior_sigma, spec.scale)
+    idx = np.arange(spec.n_params) if spec.n_params < 60 else np.unique(
+        np.concatenate([np.arange(20), rng.choice(spec.n_params, 40, replace=False)]))
+    for i in idx:
+        h = 1e-6 * scale[i]
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (om.nll(tp, data) - om.nll(tm, data)) / (2 * h)
+        # compare in units of the parameter's scale (z units)
+        assert abs(fd - g[i]) * scale[i] < 1e-5 * (1 + abs(g[i]) * scale[i]), spec.param_names[i]
+
+
+# ---------------------------------------------------------------------------------------
+# minimiser
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["c0", "c1"])
+def test_asimov_fit_recovers_injected_parameters(name):
+    spec = synth.make_model(name)
+    om = oracle.OracleModel(spec)
+    # shift only parameters without a prior, so the injected point has -2lnL = 0 exactly
+    truth = spec.theta0.copy()
+    free = [i for i in range(spec.n_params) if spec.prior_sigma[i] == 0
+            and not any(i in idx for idx, _ in spec.cov_blocks)]
+    truth[free] += 1.5 * spec.scale[free]
+    data = om.expected(truth)
+    assert om.nll(truth, data) == pytest.approx(0.0, abs=1e-9)
+    r = om.fit(data)
+    assert r["status"] == 0
+    assert abs(r["nll"]) < 1e-7
+    sig = om.sigma(r["theta"], data)
+    assert np.all(np.abs(r["theta"] - truth) < 1e-3 * sig + 1e-12)
+
+
+def _norm_only(spec):
+    """C0 geometry with one free parameter: the signal normalisation; no backgrounds."""
+    s = copy.deepcopy(spec)
+    inorm = s.index("norm")
+    ds = s.datasets[0]
+    ds.backgrounds = []
+    ds.escale_idx = np.array([-1, -1, -1], np.int32)
+    ds.shape_idx = np.full(s.n_true, -1, np.int32)
+    s.osc_idx = np.array([-1, -1, -1, -1], np.int32)
+    s.cov_blocks = []
+    s.param_names = ["norm"]
+    s.theta0 = np.array([1.0])
+    s.prior_sigma = np.array([0.0])
+    s.scale = np.array([0.01])
+    ds.norm_idx = 0
+    del inorm
+    return s
+
+
+def test_pure_scale_fit_closed_form():
+    """mu = s mu0 gives the Poisson MLE s_hat = sum n / sum mu0 (Eq. 3-5)."""
+    spec = _norm_only(synth.make_model("c0"))
+    om = oracle.OracleModel(spec)
+    mu0 = om.expected(np.array([1.0]))
+    data = synth.poisson_data(1.07 * mu0, 13)
+    r = om.fit(data, edm_tol=1e-14)
+    assert r["theta"][0] == pytest.approx(data.sum() / mu0.sum(), rel=1e-9)
+
+
+def test_prior_only_fit_returns_prior_means_and_covariance():
+    spec = synth.make_model("c0")
+    om = oracle.OracleModel(spec)
+    start = om.theta_of_z(np.random.default_rng(14).standard_normal(spec.n_params))
+    zero = np.zeros(spec.n_bins)
+    r = om.fit(zero, mask=0, start=start)
+    constrained = spec.prior_sigma > 0
+    for idx, _ in spec.cov_blocks:
+        constrained[idx] = True
+    np.testing.assert_allclose(r["theta"][constrained], spec.theta0[constrained], atol=1e-7)
+    H = om.hessian(spec.theta0, zero, mask=0)
+    sub = np.flatnonzero(constrained)
+    V = 2.0 * np.linalg.inv(H[np.ix_(sub, sub)])
+    ref = np.zeros((spec.n_params, spec.n_params))
+    for i in sub:
+        ref[i, i] = spec.prior_sigma[i] ** 2
+    for idx, cov in spec.cov_blocks:
+        ref[np.ix_(idx, idx)] = cov
+    np.testing.assert_allclose(V, ref[np.ix_(sub, sub)], rtol=1e-6, atol=1e-12)
+
+
+def test_grid_scan_matches_fit_minimum():
+    """Two free parameters (sin^2 2th13, dm2_ee): a 401 x 401 scan plus local refinement."""
+    spec = synth.make_model("c0_tiny")
+    om = oracle.OracleModel(spec)
+    truth = np.array([0.085, 2.45e-3])
+    data = synth.poisson_data(om.expected(truth), 15)
+    r = om.fit(data)
+    assert r["status"] == 0
+    s13 = np.linspace(0.0, 0.2, 401)
+    dm = np.linspace(1.5e-3, 3.5e-3, 401)
+    vals = np.array([[om.nll([a, b], data) for b in dm] for a in s13])
+    i, j = np.unravel_index(np.argmin(vals), vals.shape)
+    best = vals[i, j]
+    ca, cb = s13[i], dm[j]
+    wa, wb = s13[1] - s13[0], dm[1] - dm[0]
+    wa, wb = 3 * wa, 3 * wb
+    for _ in range(14):                     # zoomed 21 x 21 rescans around the best point
+        aa = np.linspace(ca - wa, ca + wa, 21)
+        bb = np.linspace(cb - wb, cb + wb, 21)
+        v2 = np.array([[om.nll([a, b], data) for b in bb] for a in aa])
+        i, j = np.unravel_index(np.argmin(v2), v2.shape)
+        ca, cb, best = aa[i], bb[j], min(best, v2[i, j])
+        wa, wb = wa / 3, wb / 3
+    assert r["nll"] == pytest.approx(best, abs=1e-6)
+    assert r["nll"] <= best + 1e-9
