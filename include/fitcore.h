@@ -1,0 +1,207 @@
+/*
+ * fitcore.h - C ABI of the GB300 forward-folding likelihood-fit library.
+ *
+ * The library evaluates the binned expectation of a reactor-neutrino oscillation model, the
+ * Poisson -2lnL with Gaussian and covariance priors, its gradient, and runs many quasi-Newton
+ * fits at once, all on one GPU (sm_103a). It follows PhyLiNO (arXiv 2502.15253):
+ *
+ *   expectation per dataset d, true bin k, reco bin j (Sec. 5-6, Eq. 9):
+ *     u_dk  = t_dk n_d s_g(k) sum_c p_c w_dc P(L_dc, E_k; eta)        survival: Eq. 1 with
+ *             Delta m^2_ee of Eq. 2, or the exact 3-flavour vacuum probability (Eq. 10)
+ *     v_d   = M(a_d) u_d  energy correction E' = a0 + a1 E + a2 E^2, each true bin's content
+ *             spread over the original binning by overlap length (Sec. 6, third signal step)
+ *     mu_dj = eps_d sum_k R_d[j,k] v_dk + sum_b r_b B_bj (1 + delta_bj)
+ *   -2lnL = sum_d sum_j 2[mu - n + n ln(n/mu)]            Eq. 3-5 normalised as in Eq. 8
+ *         + sum_i ((theta_i - theta0_i)/sigma_i)^2          Eq. 6
+ *         + sum_B (theta_B - theta0_B)^T V_B^-1 (theta_B - theta0_B)   Eq. 6, Eq. 9
+ *
+ * Conventions
+ *  - Every function returns FIT_OK (0) or a negative FIT_ERR_* code; fit_last_error() then
+ *    gives a message (thread-local). No function traps the GPU; device-side failures become
+ *    per-instance statuses.
+ *  - Pointers marked "host or device" may point to either; the library asks the CUDA runtime
+ *    which (cudaPointerGetAttributes) and stages host buffers through device memory itself.
+ *    Pointers marked "host" must be host memory. The caller owns all buffers it passes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls that
+ *    read or write only device buffers are asynchronous on that stream; calls with a host
+ *    output synchronise the stream before returning.
+ *  - Parameter vectors are double at the boundary. The kernels compute in FP32; the -2lnL
+ *    bin sum, the prior quadratic form and the minimiser's curvature scalars are accumulated
+ *    in double precision.
+ *  - A model is immutable after creation and may be used from several streams at once.
+ *    fit_batch() uses a library-owned device workspace guarded by a lock.
+ */
+#ifndef FITCORE_H
+#define FITCORE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------------------- */
+#define FIT_OK 0
+#define FIT_ERR_INVALID_ARG (-1)    /* null pointer, size out of range, bad index          */
+#define FIT_ERR_INVALID_CONFIG (-2) /* inconsistent model description                      */
+#define FIT_ERR_NON_SPD_COV (-3)    /* a prior covariance block is not symmetric pos. def. */
+#define FIT_ERR_CUDA (-4)           /* a CUDA runtime call failed (message has the name)   */
+#define FIT_ERR_TIMEOUT (-5)        /* a device wait exceeded its bound                    */
+#define FIT_ERR_OOM (-6)            /* device allocation failed                            */
+
+/* ---- per-evaluation / per-instance statuses ------------------------------------------ */
+#define FIT_STATUS_CONVERGED 0          /* EDM below tolerance                                */
+#define FIT_STATUS_MAXITER 1            /* iteration limit reached                            */
+#define FIT_STATUS_LINESEARCH_FAIL 2    /* no acceptable step along a descent direction       */
+#define FIT_STATUS_NONFINITE 3          /* -2lnL or its gradient not finite at the start      */
+#define FIT_STATUS_MU_NONPOSITIVE 4     /* an expected count <= 0 on a used bin (nll = +inf)  */
+#define FIT_STATUS_ESCALE_NONMONOTONE 5 /* dE'/dE outside (0.25, 4) on the grid (nll = +inf)  */
+#define FIT_STATUS_TIMEOUT 6            /* the fit exceeded its clock budget                  */
+
+/* Survival-probability forms */
+#define FIT_OSC_EQ1 0     /* eta = (sin^2 2th13, dm2_ee, sin^2 2th12, dm2_21)       Eq. 1, 2 */
+#define FIT_OSC_VACUUM3 1 /* eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31), normal ordering */
+
+/* Size limits of one model */
+#define FIT_MAX_DATASETS 8
+#define FIT_MAX_DETECTORS 4
+#define FIT_MAX_BACKGROUNDS 24
+#define FIT_MAX_CORES 16
+#define FIT_MAX_PARAMS 1024
+#define FIT_MAX_TRUE_BINS 4096
+#define FIT_MAX_RECO_BINS 1024
+
+/*
+ * Model description (all pointers host memory, read during fit_model_create only).
+ * A parameter index of -1 means "fixed at its nominal value": 1 for multiplicative factors
+ * (norm, efficiency, shape reweight, rate, core power), (0, 1, 0) for (a0, a1, a2), 0 for a
+ * background shape delta. Arrays marked "concatenated" list the items back to back.
+ */
+typedef struct fit_model_desc {
+    int n_params;
+    const double *theta0;      /* [P] nominal values = prior means                             */
+    const double *prior_sigma; /* [P] Gaussian prior width; 0 = no individual prior            */
+    const double *scale;       /* [P] minimiser step scale (> 0) for parameters without prior  */
+    int n_cov;                 /* covariance-prior blocks (Eq. 6); their parameters need sigma 0 */
+    const int *cov_size;       /* [n_cov] block sizes m_b                                      */
+    const int *cov_idx;        /* concatenated parameter indices, sum m_b                      */
+    const double *cov;         /* concatenated row-major m_b x m_b covariance matrices         */
+    int osc_mode;              /* FIT_OSC_EQ1 or FIT_OSC_VACUUM3                               */
+    int osc_idx[4];            /* parameter index of each survival parameter, or -1            */
+    double osc_val[4];         /* value used where osc_idx is -1                               */
+    int n_cores;               /* reactor cores, <= FIT_MAX_CORES                              */
+    const int *core_power_idx; /* [C] parameter index of each core's power factor              */
+    int n_true;                /* true-energy grid: n_true uniform bins over [e_lo, e_hi] MeV  */
+    double e_lo, e_hi;
+    int n_det;
+    const int *det_n_reco;       /* [n_det] reco bins per detector                            */
+    const double *det_response;  /* concatenated row-major [N_r x n_true] per detector        */
+    int n_ds;
+    const int *ds_det;           /* [n_ds] detector of each dataset                           */
+    const double *ds_t;          /* [n_ds x n_true] un-oscillated expected signal counts      */
+    const double *ds_baseline;   /* [n_ds x C] baseline of each core, metres                  */
+    const double *ds_weight;     /* [n_ds x C] flux share per core (0 = core not seen)        */
+    const int *ds_norm_idx;      /* [n_ds] signal normalisation parameter                     */
+    const int *ds_eff_idx;       /* [n_ds] efficiency parameter                               */
+    const int *ds_escale_idx;    /* [n_ds x 3] (a0, a1, a2) parameters                        */
+    const int *ds_shape_idx;     /* [n_ds x n_true] shape-reweight parameter per true bin     */
+    int n_bkg;
+    const int *bkg_ds;           /* [n_bkg] dataset of each background                        */
+    const double *bkg_template;  /* concatenated [N_r of its dataset] expected counts         */
+    const int *bkg_rate_idx;     /* [n_bkg] rate parameter                                    */
+    const int *bkg_shape_idx;    /* concatenated [N_r] shape-delta parameter per reco bin     */
+} fit_model_desc;
+
+typedef struct fit_model fit_model; /* opaque, device-resident constants */
+
+typedef struct fit_model_info_t {
+    int n_params;
+    int n_data;       /* total reco bins over all datasets = length of one data vector */
+    int n_datasets;
+    int n_true;
+    size_t device_bytes; /* device memory held by the model */
+} fit_model_info_t;
+
+/* Builds a model from its description: validates it, computes the banded response layout,
+ * the Cholesky factors of the prior blocks (the transformation layer of Sec. 6) and uploads
+ * everything to the current device. *out receives the model (free with fit_model_destroy).
+ * Errors: INVALID_ARG / INVALID_CONFIG (message names the field), NON_SPD_COV, OOM, CUDA. */
+int fit_model_create(const fit_model_desc *desc, fit_model **out);
+void fit_model_destroy(fit_model *model);
+int fit_model_info(const fit_model *model, fit_model_info_t *info);
+
+/* Expected counts mu (Sec. 5-6) for B parameter vectors.
+ * theta: host or device, [B x P] double. mu_out: host or device, [B x n_data] float.
+ * status_out: host or device [B] int (FIT_STATUS_*) or NULL. */
+int fit_model_expected(fit_model *model, int B, const double *theta, float *mu_out,
+                       int *status_out, void *stream);
+
+/* -2lnL and its gradient for B parameter vectors at once (Eq. 3-9).
+ * theta: host or device [B x P] double; data: host or device [B x n_data] float counts
+ * (NULL = every row uses the model's Asimov data at theta0); masks: host [B] uint32 bit d
+ * set = dataset d enters the Poisson term (NULL = all datasets).
+ * nll_out: host or device [B] double (+inf where mu <= 0 or the energy map is invalid).
+ * grad_out: host or device [B x P] float d(-2lnL)/dtheta, or NULL to skip.
+ * status_out: host or device [B] int or NULL. */
+int fit_model_eval(fit_model *model, int B, const double *theta, const float *data,
+                   const uint32_t *masks, double *nll_out, float *grad_out, int *status_out,
+                   void *stream);
+
+/* One fit instance of fit_batch. */
+typedef struct fit_instance {
+    int model;         /* index into the models array                                  */
+    uint32_t mask;     /* datasets entering the Poisson term                            */
+    int64_t data_off;  /* offset (floats) of its data vector in `data`                  */
+    int64_t param_off; /* offset (doubles) of its start / result vector in start / best */
+} fit_instance;
+
+typedef struct fit_batch_opts {
+    double edm_tol;       /* stop when EDM = 1/2 g^T H g < edm_tol (default 1e-8)             */
+    int max_iter;         /* iteration limit (default 2000)                                  */
+    int history;          /* L-BFGS pairs kept, 1..16 (default 10)                           */
+    double f_noise_rel;   /* relative noise allowance of -2lnL in the line search (1e-6)     */
+    int threads;          /* threads per block, multiple of 32 in [64, 256]; 0 = default 256 */
+    int blocks_per_sm;    /* resident blocks per SM; 0 = autotuned / occupancy maximum      */
+    int use_graph;        /* 1 = launch through a cached CUDA graph                          */
+    double time_budget_s; /* per-launch clock budget (0 = 60 s); exceeded -> FIT_STATUS_TIMEOUT */
+} fit_batch_opts;
+
+/* Result of one instance. */
+typedef struct fit_result {
+    double nll_min; /* -2lnL at the returned point           */
+    double edm;     /* EDM at the returned point             */
+    int iters;      /* quasi-Newton iterations                */
+    int n_evals;    /* expectation + gradient evaluations     */
+    int status;     /* FIT_STATUS_*                           */
+    int pad;
+} fit_result;
+
+/* Sets *opts to the defaults. */
+void fit_batch_default_opts(fit_batch_opts *opts);
+
+/* Fits n_inst pseudo-experiments of possibly different models in one persistent launch:
+ * one block per instance at a time, per-instance L-BFGS state on the device, the whole
+ * expectation / -2lnL / adjoint evaluated inside the block (Sec. 6: minimiser loop around the
+ * likelihood; many fits in parallel as in the paper's ensemble studies).
+ * models: host [n_models]; inst: host [n_inst];
+ * data: host or device floats, instance i reads data + inst[i].data_off (n_data of its model);
+ * start: host or device doubles, instance i starts at start + inst[i].param_off (NULL = the
+ *        model's theta0);
+ * best: host or device doubles, receives the best fit at best + inst[i].param_off;
+ * results: host or device [n_inst];
+ * opts: host, NULL = defaults. Synchronises `stream` if any output is host memory. */
+int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst,
+              const float *data, const double *start, double *best, fit_result *results,
+              const fit_batch_opts *opts, void *stream);
+
+/* Message of the last error on this thread ("" if none). */
+const char *fit_last_error(void);
+
+/* Number of kernels the library launched on this thread since the last call (and resets). */
+int64_t fit_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FITCORE_H */

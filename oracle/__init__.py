@@ -286,8 +286,13 @@ class OracleModel:
         live = np.abs(np.diag(H)) > 1e-300
         sig = np.full(self.n_params, np.inf)
         if live.any():
+            # At a kink of the energy correction the difference Hessian can have a slightly
+            # negative eigenvalue; inverting its projection onto the positive semidefinite
+            # cone (eigenvalues floored at 1e-9 of the largest) keeps every sigma > 0.
             Hl = H[np.ix_(live, live)]
-            sig[live] = np.sqrt(np.maximum(2.0 * np.diag(np.linalg.inv(Hl)), 0.0))
+            w, V = np.linalg.eigh(Hl)
+            w = np.maximum(w, 1e-9 * max(w.max(), 1e-300))
+            sig[live] = np.sqrt(2.0 * np.einsum("ij,j,ij->i", V, 1.0 / w, V))
         return sig
 
 

@@ -1,0 +1,796 @@
+// Host side of the C ABI (include/fitcore.h): model construction, argument staging, launches.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+using fitcore::DevModel;
+
+namespace {
+
+thread_local std::string g_err;
+thread_local int64_t g_launches = 0;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define FIT_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? FIT_ERR_OOM : FIT_ERR_CUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+        }                                                                                  \
+    } while (0)
+
+constexpr double kOscK = 1.266932679815373;  // dm2[eV^2] L[m] / (4 E[MeV]) in radians, from hbar c
+
+bool on_device(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Host staging of arrays into one device allocation.
+struct Arena {
+    std::vector<unsigned char> buf;
+    std::vector<std::pair<const void **, size_t>> fix;
+    size_t put(const void *p, size_t n) {
+        size_t off = (buf.size() + 255) & ~size_t(255);
+        buf.resize(off + std::max<size_t>(n, 16));
+        if (n) std::memcpy(buf.data() + off, p, n);
+        return off;
+    }
+    template <class T>
+    void put(const T **field, const std::vector<T> &v) {
+        fix.emplace_back(reinterpret_cast<const void **>(field), put(v.data(), v.size() * sizeof(T)));
+    }
+    void bind(void *base) {
+        for (auto &f : fix) *f.first = static_cast<unsigned char *>(base) + f.second;
+    }
+};
+
+// Cholesky V = L L^T (lower, row-major); returns false if V is not positive definite.
+bool cholesky_lower(int n, const double *v, std::vector<double> &L) {
+    L.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double d = v[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(d > 0.0) || !std::isfinite(d)) return false;
+        const double ljj = std::sqrt(d);
+        L[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double s = v[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = s / ljj;
+        }
+    }
+    return true;
+}
+
+// W = L^-1 for lower-triangular L (forward substitution on the identity's columns)
+void lower_inverse(int n, const std::vector<double> &L, std::vector<double> &W) {
+    W.assign((size_t)n * n, 0.0);
+    for (int c = 0; c < n; ++c) {
+        for (int i = c; i < n; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) s -= L[(size_t)i * n + k] * W[(size_t)k * n + c];
+            W[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+        }
+    }
+}
+
+struct LaunchCfg {
+    int sms = 0;
+    size_t smem_optin = 0;
+};
+
+int device_cfg(LaunchCfg &c) {
+    int dev;
+    FIT_CUDA(cudaGetDevice(&dev));
+    FIT_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
+    int v;
+    FIT_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    c.smem_optin = (size_t)v;
+    return FIT_OK;
+}
+
+// A device buffer that is either the caller's device pointer or a stream-ordered staging copy.
+struct Staged {
+    void *dev = nullptr;
+    bool owned = false;
+};
+
+int stage_in(const void *src, size_t bytes, cudaStream_t s, Staged &out) {
+    if (!src || bytes == 0) {
+        out.dev = const_cast<void *>(src);
+        return FIT_OK;
+    }
+    if (on_device(src)) {
+        out.dev = const_cast<void *>(src);
+        return FIT_OK;
+    }
+    FIT_CUDA(cudaMallocAsync(&out.dev, bytes, s));
+    out.owned = true;
+    FIT_CUDA(cudaMemcpyAsync(out.dev, src, bytes, cudaMemcpyHostToDevice, s));
+    return FIT_OK;
+}
+
+int stage_out(void *dst, size_t bytes, cudaStream_t s, Staged &out, bool &host) {
+    host = false;
+    if (!dst || bytes == 0) {
+        out.dev = dst;
+        return FIT_OK;
+    }
+    if (on_device(dst)) {
+        out.dev = dst;
+        return FIT_OK;
+    }
+    host = true;
+    FIT_CUDA(cudaMallocAsync(&out.dev, bytes, s));
+    out.owned = true;
+    return FIT_OK;
+}
+
+void release(Staged &b, cudaStream_t s) {
+    if (b.owned && b.dev) cudaFreeAsync(b.dev, s);
+    b.dev = nullptr;
+    b.owned = false;
+}
+
+std::mutex g_ws_mutex;
+
+}  // namespace
+
+struct fit_model {
+    DevModel host;         // field values with device pointers
+    DevModel *dev = nullptr;
+    void *arena = nullptr;
+    size_t bytes = 0;
+    int n_params = 0, n_data = 0, n_ds = 0, n_true = 0;
+};
+
+extern "C" {
+
+const char *fit_last_error(void) { return g_err.c_str(); }
+
+int64_t fit_kernel_launches(void) {
+    int64_t n = g_launches;
+    g_launches = 0;
+    return n;
+}
+
+void fit_model_destroy(fit_model *model) {
+    if (!model) return;
+    if (model->arena) cudaFree(model->arena);
+    delete model;
+}
+
+int fit_model_info(const fit_model *model, fit_model_info_t *info) {
+    if (!model || !info) return fail(FIT_ERR_INVALID_ARG, "fit_model_info: null argument");
+    info->n_params = model->n_params;
+    info->n_data = model->n_data;
+    info->n_datasets = model->n_ds;
+    info->n_true = model->n_true;
+    info->device_bytes = model->bytes;
+    return FIT_OK;
+}
+
+static int launch_eval(fit_model *model, int B, const double *theta_d, const float *data_d,
+                       const uint32_t *masks_d, double *nll_d, float *grad_d, float *mu_d,
+                       int *st_d, cudaStream_t s);
+
+int fit_model_create(const fit_model_desc *d, fit_model **out) {
+    using std::vector;
+    if (!d || !out) return fail(FIT_ERR_INVALID_ARG, "fit_model_create: null argument");
+    *out = nullptr;
+    const int P = d->n_params, Nt = d->n_true, C = d->n_cores;
+    auto bad = [](const std::string &m) { return fail(FIT_ERR_INVALID_CONFIG, "fit_model_create: " + m); };
+    if (P < 1 || P > FIT_MAX_PARAMS) return bad("n_params out of range");
+    if (Nt < 2 || Nt > FIT_MAX_TRUE_BINS) return bad("n_true out of range");
+    if (C < 1 || C > FIT_MAX_CORES) return bad("n_cores out of range");
+    if (d->n_det < 1 || d->n_det > FIT_MAX_DETECTORS) return bad("n_det out of range");
+    if (d->n_ds < 1 || d->n_ds > FIT_MAX_DATASETS) return bad("n_ds out of range");
+    if (d->n_bkg < 0 || d->n_bkg > FIT_MAX_BACKGROUNDS) return bad("n_bkg out of range");
+    if (d->osc_mode != FIT_OSC_EQ1 && d->osc_mode != FIT_OSC_VACUUM3) return bad("osc_mode");
+    if (!(d->e_lo > 0.0 && d->e_hi > d->e_lo)) return bad("energy grid");
+    if (!d->theta0 || !d->prior_sigma || !d->scale || !d->core_power_idx || !d->det_n_reco ||
+        !d->det_response || !d->ds_det || !d->ds_t || !d->ds_baseline || !d->ds_weight ||
+        !d->ds_norm_idx || !d->ds_eff_idx || !d->ds_escale_idx || !d->ds_shape_idx)
+        return bad("missing array");
+    if (d->n_cov > 0 && (!d->cov_size || !d->cov_idx || !d->cov)) return bad("missing covariance arrays");
+    if (d->n_bkg > 0 && (!d->bkg_ds || !d->bkg_template || !d->bkg_rate_idx || !d->bkg_shape_idx))
+        return bad("missing background arrays");
+    auto pidx_ok = [P](int i) { return i >= -1 && i < P; };
+    for (int i = 0; i < 4; ++i)
+        if (!pidx_ok(d->osc_idx[i])) return bad("osc_idx");
+    for (int c = 0; c < C; ++c)
+        if (!pidx_ok(d->core_power_idx[c])) return bad("core_power_idx");
+    for (int i = 0; i < d->n_det; ++i)
+        if (d->det_n_reco[i] < 1 || d->det_n_reco[i] > FIT_MAX_RECO_BINS) return bad("det_n_reco");
+
+    fit_model *M = new fit_model();
+    DevModel &h = M->host;
+    std::memset(&h, 0, sizeof(DevModel));
+    Arena A;
+    h.P = P;
+    h.N_t = Nt;
+    h.C = C;
+    h.n_ds = d->n_ds;
+    h.osc_mode = d->osc_mode;
+    const double de = (d->e_hi - d->e_lo) / Nt;
+    h.e_lo = (float)d->e_lo;
+    h.de = (float)de;
+    h.inv_de = (float)(1.0 / de);
+    for (int i = 0; i < 4; ++i) {
+        h.osc_idx[i] = d->osc_idx[i];
+        h.osc_val[i] = (float)d->osc_val[i];
+        h.osc_val_lo[i] = (float)(d->osc_val[i] - (double)h.osc_val[i]);
+        h.osc_val_d[i] = d->osc_val[i];
+    }
+    for (int c = 0; c < C; ++c) h.core_power_idx[c] = d->core_power_idx[c];
+    {
+        vector<float> edge(Nt + 1), ih(Nt), il(Nt);
+        for (int k = 0; k <= Nt; ++k) edge[k] = (float)(d->e_lo + k * de);
+        for (int k = 0; k < Nt; ++k) {
+            const double inv = 1.0 / (d->e_lo + (k + 0.5) * de);
+            ih[k] = (float)inv;
+            il[k] = (float)(inv - (double)ih[k]);
+        }
+        A.put(&h.e_edge, edge);
+        A.put(&h.inv_e_hi, ih);
+        A.put(&h.inv_e_lo, il);
+    }
+    // ---- detectors: banded response -------------------------------------------------------
+    vector<int> det_off(d->n_det + 1, 0);
+    for (int i = 0; i < d->n_det; ++i) det_off[i + 1] = det_off[i] + d->det_n_reco[i] * Nt;
+    int max_reco = 0;
+    for (int i = 0; i < d->n_det; ++i) {
+        const int nr = d->det_n_reco[i];
+        max_reco = std::max(max_reco, nr);
+        const double *R = d->det_response + det_off[i];
+        vector<int> rlo(nr), rlen(nr), roff(nr);
+        vector<float> rrow;
+        for (int j = 0; j < nr; ++j) {
+            int a = Nt, b = -1;
+            for (int k = 0; k < Nt; ++k) {
+                const double x = R[(size_t)j * Nt + k];
+                if (!std::isfinite(x) || x < 0.0) {
+                    delete M;
+                    return bad("response entries must be finite and >= 0");
+                }
+                if (x != 0.0) {
+                    a = std::min(a, k);
+                    b = std::max(b, k);
+                }
+            }
+            if (b < a) a = b = 0;   // empty row: one zero entry
+            rlo[j] = a;
+            rlen[j] = b - a + 1;
+            roff[j] = (int)rrow.size();
+            for (int k = a; k <= b; ++k) rrow.push_back((float)R[(size_t)j * Nt + k]);
+            while (rrow.size() % 4) rrow.push_back(0.f);
+        }
+        vector<int> clo(Nt);
+        int cw = 1;
+        for (int k = 0; k < Nt; ++k) {
+            int a = nr, b = -1;
+            for (int j = 0; j < nr; ++j)
+                if (R[(size_t)j * Nt + k] != 0.0) {
+                    a = std::min(a, j);
+                    b = std::max(b, j);
+                }
+            if (b < a) a = b = 0;
+            clo[k] = a;
+            cw = std::max(cw, b - a + 1);
+        }
+        vector<float> rcol((size_t)cw * Nt, 0.f);
+        for (int k = 0; k < Nt; ++k)
+            for (int b = 0; b < cw && clo[k] + b < nr; ++b)
+                rcol[(size_t)b * Nt + k] = (float)R[(size_t)(clo[k] + b) * Nt + k];
+        fitcore::DevDetector &dt = h.det[i];
+        dt.n_reco = nr;
+        dt.col_w = cw;
+        A.put(&dt.row_lo, rlo);
+        A.put(&dt.row_len, rlen);
+        A.put(&dt.row_off, roff);
+        A.put(&dt.rrow, rrow);
+        A.put(&dt.col_lo, clo);
+        A.put(&dt.rcol, rcol);
+    }
+    h.max_reco = max_reco;
+    // ---- datasets -------------------------------------------------------------------------
+    int data_off = 0;
+    vector<int> bkg_order;
+    for (int ds = 0; ds < d->n_ds; ++ds) {
+        fitcore::DevDataset &D = h.ds[ds];
+        const int det = d->ds_det[ds];
+        if (det < 0 || det >= d->n_det) {
+            delete M;
+            return bad("ds_det");
+        }
+        D.det = det;
+        D.n_reco = d->det_n_reco[det];
+        D.data_off = data_off;
+        data_off += D.n_reco;
+        D.norm_idx = d->ds_norm_idx[ds];
+        D.eff_idx = d->ds_eff_idx[ds];
+        if (!pidx_ok(D.norm_idx) || !pidx_ok(D.eff_idx)) {
+            delete M;
+            return bad("ds_norm_idx / ds_eff_idx");
+        }
+        for (int i = 0; i < 3; ++i) {
+            D.esc_idx[i] = d->ds_escale_idx[3 * ds + i];
+            if (!pidx_ok(D.esc_idx[i])) {
+                delete M;
+                return bad("ds_escale_idx");
+            }
+        }
+        D.a1_off = D.esc_idx[1] >= 0 ? (float)(d->theta0[D.esc_idx[1]] - 1.0) : 0.f;
+        for (int c = 0; c < C; ++c) {
+            const double w = d->ds_weight[ds * C + c], L = d->ds_baseline[ds * C + c];
+            if (!(w >= 0.0) || (w > 0.0 && !(L > 0.0))) {
+                delete M;
+                return bad("ds_weight / ds_baseline");
+            }
+            D.w[c] = (float)w;
+            const double kl = kOscK * L / M_PI;   // phase per (dm2 / E) in half-turns
+            D.kl_hi[c] = (float)kl;
+            D.kl_lo[c] = (float)(kl - (double)D.kl_hi[c]);
+        }
+        vector<float> t(Nt);
+        vector<int> sidx(Nt);
+        for (int k = 0; k < Nt; ++k) {
+            t[k] = (float)d->ds_t[(size_t)ds * Nt + k];
+            sidx[k] = d->ds_shape_idx[(size_t)ds * Nt + k];
+            if (!pidx_ok(sidx[k]) || !(t[k] >= 0.f)) {
+                delete M;
+                return bad("ds_t / ds_shape_idx");
+            }
+        }
+        // CSR of true bins per distinct shape parameter
+        vector<int> params;
+        for (int k = 0; k < Nt; ++k)
+            if (sidx[k] >= 0) params.push_back(sidx[k]);
+        std::sort(params.begin(), params.end());
+        params.erase(std::unique(params.begin(), params.end()), params.end());
+        vector<int> ptr(params.size() + 1, 0), ks;
+        for (size_t q = 0; q < params.size(); ++q) {
+            for (int k = 0; k < Nt; ++k)
+                if (sidx[k] == params[q]) ks.push_back(k);
+            ptr[q + 1] = (int)ks.size();
+        }
+        D.n_sp = (int)params.size();
+        A.put(&D.t, t);
+        A.put(&D.shape_idx, sidx);
+        A.put(&D.sp_param, params);
+        A.put(&D.sp_ptr, ptr);
+        A.put(&D.sp_k, ks);
+        // backgrounds of this dataset, in description order
+        D.bkg_begin = (int)bkg_order.size();
+        for (int b = 0; b < d->n_bkg; ++b)
+            if (d->bkg_ds[b] == ds) bkg_order.push_back(b);
+        D.bkg_end = (int)bkg_order.size();
+        if (D.bkg_end - D.bkg_begin > fitcore::kMaxBkgDs) {
+            delete M;
+            return bad("more than 6 backgrounds in one dataset");
+        }
+    }
+    h.n_data = data_off;
+    {
+        vector<int> boff(d->n_bkg + 1, 0);
+        for (int b = 0; b < d->n_bkg; ++b) {
+            if (d->bkg_ds[b] < 0 || d->bkg_ds[b] >= d->n_ds) {
+                delete M;
+                return bad("bkg_ds");
+            }
+            boff[b + 1] = boff[b] + d->det_n_reco[d->ds_det[d->bkg_ds[b]]];
+        }
+        h.n_bkg = d->n_bkg;
+        for (size_t q = 0; q < bkg_order.size(); ++q) {
+            const int b = bkg_order[q];
+            const int nr = boff[b + 1] - boff[b];
+            vector<float> tm(nr);
+            vector<int> si(nr);
+            for (int j = 0; j < nr; ++j) {
+                tm[j] = (float)d->bkg_template[boff[b] + j];
+                si[j] = d->bkg_shape_idx[boff[b] + j];
+                if (!pidx_ok(si[j])) {
+                    delete M;
+                    return bad("bkg_shape_idx");
+                }
+            }
+            if (!pidx_ok(d->bkg_rate_idx[b])) {
+                delete M;
+                return bad("bkg_rate_idx");
+            }
+            h.bkg[q].rate_idx = d->bkg_rate_idx[b];
+            A.put(&h.bkg[q].tmpl, tm);
+            A.put(&h.bkg[q].shape_idx, si);
+        }
+    }
+    // ---- parameters, priors, transformation layer ----------------------------------------
+    {
+        vector<double> th0(d->theta0, d->theta0 + P);
+        vector<float> th0f(P), th0lo(P), zscale(P, 0.f), pinv(P, 0.f);
+        vector<int> in_block(P, 0);
+        vector<int> bsz, boff, bidx;
+        vector<int64_t> moff;
+        vector<float> Lf, Wf;
+        vector<double> L64;
+        int64_t mo = 0;
+        for (int b = 0, ioff = 0; b < d->n_cov; ++b) {
+            const int n = d->cov_size[b];
+            if (n < 1 || ioff + n > P * 4) {
+                delete M;
+                return bad("cov_size");
+            }
+            const int *idx = d->cov_idx + ioff;
+            for (int i = 0; i < n; ++i) {
+                if (idx[i] < 0 || idx[i] >= P || in_block[idx[i]] || d->prior_sigma[idx[i]] != 0.0) {
+                    delete M;
+                    return bad("cov_idx: a parameter is out of range, in two blocks, or also has prior_sigma");
+                }
+                in_block[idx[i]] = 1;
+            }
+            const double *V = d->cov + mo / 2;   // blocks are packed m*m back to back
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < i; ++j)
+                    if (std::fabs(V[(size_t)i * n + j] - V[(size_t)j * n + i]) >
+                        1e-12 * (std::fabs(V[(size_t)i * n + i]) + std::fabs(V[(size_t)j * n + j]))) {
+                        delete M;
+                        return fail(FIT_ERR_NON_SPD_COV, "fit_model_create: covariance block not symmetric");
+                    }
+            vector<double> L, W;
+            if (!cholesky_lower(n, V, L)) {
+                delete M;
+                return fail(FIT_ERR_NON_SPD_COV, "fit_model_create: covariance block not positive definite");
+            }
+            lower_inverse(n, L, W);
+            bsz.push_back(n);
+            boff.push_back(ioff);
+            for (int i = 0; i < n; ++i) bidx.push_back(idx[i]);
+            moff.push_back(mo);
+            // [L | L^T] and [W | W^T], dense row-major
+            const size_t base = Lf.size();
+            Lf.resize(base + 2 * (size_t)n * n);
+            Wf.resize(base + 2 * (size_t)n * n);
+            L64.resize(base + 2 * (size_t)n * n);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    Lf[base + (size_t)i * n + j] = (float)L[(size_t)i * n + j];
+                    Lf[base + (size_t)n * n + (size_t)j * n + i] = (float)L[(size_t)i * n + j];
+                    Wf[base + (size_t)i * n + j] = (float)W[(size_t)i * n + j];
+                    Wf[base + (size_t)n * n + (size_t)j * n + i] = (float)W[(size_t)i * n + j];
+                    L64[base + (size_t)i * n + j] = L[(size_t)i * n + j];
+                }
+            mo += 2 * (int64_t)n * n;
+            ioff += n;
+        }
+        for (int i = 0; i < P; ++i) {
+            th0f[i] = (float)th0[i];
+            th0lo[i] = (float)(th0[i] - (double)th0f[i]);
+            if (in_block[i]) continue;
+            const double ps = d->prior_sigma[i], sc = d->scale[i];
+            if (ps < 0.0 || !std::isfinite(ps)) {
+                delete M;
+                return bad("prior_sigma");
+            }
+            if (ps > 0.0) {
+                zscale[i] = (float)ps;
+                pinv[i] = (float)(1.0 / ps);
+            } else {
+                if (!(sc > 0.0) || !std::isfinite(sc)) {
+                    delete M;
+                    return bad("scale must be > 0 for a parameter without prior");
+                }
+                zscale[i] = (float)sc;
+            }
+        }
+        h.n_blocks = d->n_cov;
+        A.put(&h.theta0, th0);
+        A.put(&h.theta0_f, th0f);
+        A.put(&h.theta0_lo, th0lo);
+        A.put(&h.zscale, zscale);
+        A.put(&h.prior_inv, pinv);
+        if (bsz.empty()) {
+            bsz.push_back(0);
+            boff.push_back(0);
+            bidx.push_back(0);
+            moff.push_back(0);
+            Lf.push_back(0.f);
+            Wf.push_back(0.f);
+            L64.push_back(0.0);
+        }
+        A.put(&h.blk_size, bsz);
+        A.put(&h.blk_idx_off, boff);
+        A.put(&h.blk_idx, bidx);
+        A.put(&h.blk_mat_off, moff);
+        A.put(&h.blk_L, Lf);
+        A.put(&h.blk_W, Wf);
+        A.put(&h.blk_L64, L64);
+    }
+    {
+        vector<float> asimov(h.n_data, 0.f);
+        A.put(&h.asimov, asimov);
+    }
+    h.ws_eval_floats = fitcore::eval_ws_floats(Nt, C, max_reco);
+
+    // ---- upload ---------------------------------------------------------------------------
+    cudaError_t e = cudaMalloc(&M->arena, A.buf.size());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete M;
+        return fail(FIT_ERR_OOM, std::string("fit_model_create: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    A.bind(M->arena);
+    e = cudaMemcpy(M->arena, A.buf.data(), A.buf.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&M->dev, sizeof(DevModel));
+    if (e == cudaSuccess) e = cudaMemcpy(M->dev, &h, sizeof(DevModel), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (M->dev) cudaFree(M->dev);
+        fit_model_destroy(M);
+        return fail(FIT_ERR_CUDA, std::string("fit_model_create: upload: ") + cudaGetErrorString(e));
+    }
+    M->bytes = A.buf.size() + sizeof(DevModel);
+    M->n_params = P;
+    M->n_data = h.n_data;
+    M->n_ds = h.n_ds;
+    M->n_true = Nt;
+    // Asimov data = expectation at theta0
+    {
+        double *th = nullptr;
+        int rc = FIT_OK;
+        if (cudaMalloc(&th, sizeof(double) * P) != cudaSuccess ||
+            cudaMemcpy(th, d->theta0, sizeof(double) * P, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = fail(FIT_ERR_CUDA, "fit_model_create: asimov staging");
+        if (rc == FIT_OK)
+            rc = launch_eval(M, 1, th, nullptr, nullptr, nullptr, nullptr,
+                             const_cast<float *>(h.asimov), nullptr, 0);
+        if (rc == FIT_OK && cudaDeviceSynchronize() != cudaSuccess)
+            rc = fail(FIT_ERR_CUDA, "fit_model_create: asimov evaluation");
+        if (th) cudaFree(th);
+        if (rc != FIT_OK) {
+            cudaGetLastError();
+            cudaFree(M->dev);
+            M->dev = nullptr;
+            fit_model_destroy(M);
+            return rc;
+        }
+    }
+    *out = M;
+    return FIT_OK;
+}
+
+// one block per parameter vector (grid-strided), workspace in shared memory when small
+static int launch_eval(fit_model *model, int B, const double *theta_d, const float *data_d,
+                       const uint32_t *masks_d, double *nll_d, float *grad_d, float *mu_d,
+                       int *st_d, cudaStream_t s) {
+    LaunchCfg cfg;
+    int rc = device_cfg(cfg);
+    if (rc) return rc;
+    const DevModel &h = model->host;
+    const int threads = 256;
+    bool in_smem = fitcore::eval_smem_bytes(h, true) <= 96 * 1024;
+    size_t smem = fitcore::eval_smem_bytes(h, in_smem);
+    FIT_CUDA(cudaFuncSetAttribute(fitcore::eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)std::min(smem, cfg.smem_optin)));
+    int per_sm = 0;
+    FIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fitcore::eval_kernel, threads, smem));
+    if (per_sm < 1) return fail(FIT_ERR_INVALID_CONFIG, "fit_model_eval: model too large for one block");
+    const int grid = std::max(1, std::min(B, per_sm * cfg.sms));
+    float *ws = nullptr;
+    if (!in_smem) FIT_CUDA(cudaMallocAsync(&ws, sizeof(float) * (size_t)grid * h.ws_eval_floats, s));
+    fitcore::eval_kernel<<<grid, threads, smem, s>>>(model->dev, B, theta_d, data_d, masks_d, nll_d,
+                                                     grad_d, mu_d, st_d, ws, in_smem ? 1 : 0);
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (ws) cudaFreeAsync(ws, s);
+    if (e != cudaSuccess) return fail(FIT_ERR_CUDA, std::string("eval_kernel launch: ") + cudaGetErrorString(e));
+    return FIT_OK;
+}
+
+int fit_model_expected(fit_model *model, int B, const double *theta, float *mu_out, int *status_out,
+                       void *stream) {
+    if (!model || !theta || !mu_out || B < 0) return fail(FIT_ERR_INVALID_ARG, "fit_model_expected: bad argument");
+    if (B == 0) return FIT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t P = model->n_params, D = model->n_data;
+    Staged th, mu, st;
+    bool hmu = false, hst = false;
+    int rc = stage_in(theta, sizeof(double) * P * B, s, th);
+    if (!rc) rc = stage_out(mu_out, sizeof(float) * D * B, s, mu, hmu);
+    if (!rc) rc = stage_out(status_out, sizeof(int) * B, s, st, hst);
+    if (!rc) rc = launch_eval(model, B, (const double *)th.dev, nullptr, nullptr, nullptr, nullptr,
+                              (float *)mu.dev, (int *)st.dev, s);
+    if (!rc && hmu) rc = cudaMemcpyAsync(mu_out, mu.dev, sizeof(float) * D * B, cudaMemcpyDeviceToHost, s)
+                             ? fail(FIT_ERR_CUDA, "fit_model_expected: copy back") : FIT_OK;
+    if (!rc && hst) rc = cudaMemcpyAsync(status_out, st.dev, sizeof(int) * B, cudaMemcpyDeviceToHost, s)
+                             ? fail(FIT_ERR_CUDA, "fit_model_expected: copy back") : FIT_OK;
+    release(th, s);
+    release(mu, s);
+    release(st, s);
+    if (!rc && (hmu || hst) && cudaStreamSynchronize(s) != cudaSuccess)
+        rc = fail(FIT_ERR_CUDA, "fit_model_expected: synchronise");
+    return rc;
+}
+
+int fit_model_eval(fit_model *model, int B, const double *theta, const float *data, const uint32_t *masks,
+                   double *nll_out, float *grad_out, int *status_out, void *stream) {
+    if (!model || !theta || !nll_out || B < 0) return fail(FIT_ERR_INVALID_ARG, "fit_model_eval: bad argument");
+    if (B == 0) return FIT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t P = model->n_params, D = model->n_data;
+    Staged th, da, mk, nl, gr, st;
+    bool hnl = false, hgr = false, hst = false;
+    int rc = stage_in(theta, sizeof(double) * P * B, s, th);
+    if (!rc) rc = stage_in(data, sizeof(float) * D * B, s, da);
+    if (!rc) rc = stage_in(masks, sizeof(uint32_t) * B, s, mk);
+    if (!rc) rc = stage_out(nll_out, sizeof(double) * B, s, nl, hnl);
+    if (!rc) rc = stage_out(grad_out, sizeof(float) * P * B, s, gr, hgr);
+    if (!rc) rc = stage_out(status_out, sizeof(int) * B, s, st, hst);
+    if (!rc) rc = launch_eval(model, B, (const double *)th.dev, (const float *)da.dev, (const uint32_t *)mk.dev,
+                              (double *)nl.dev, (float *)gr.dev, nullptr, (int *)st.dev, s);
+    if (!rc && hnl && cudaMemcpyAsync(nll_out, nl.dev, sizeof(double) * B, cudaMemcpyDeviceToHost, s))
+        rc = fail(FIT_ERR_CUDA, "fit_model_eval: copy back");
+    if (!rc && hgr && cudaMemcpyAsync(grad_out, gr.dev, sizeof(float) * P * B, cudaMemcpyDeviceToHost, s))
+        rc = fail(FIT_ERR_CUDA, "fit_model_eval: copy back");
+    if (!rc && hst && cudaMemcpyAsync(status_out, st.dev, sizeof(int) * B, cudaMemcpyDeviceToHost, s))
+        rc = fail(FIT_ERR_CUDA, "fit_model_eval: copy back");
+    release(th, s);
+    release(da, s);
+    release(mk, s);
+    release(nl, s);
+    release(gr, s);
+    release(st, s);
+    if (!rc && (hnl || hgr || hst) && cudaStreamSynchronize(s) != cudaSuccess)
+        rc = fail(FIT_ERR_CUDA, "fit_model_eval: synchronise");
+    return rc;
+}
+
+void fit_batch_default_opts(fit_batch_opts *o) {
+    if (!o) return;
+    o->edm_tol = 1e-8;
+    o->max_iter = 2000;
+    o->history = 10;
+    o->f_noise_rel = 1e-6;
+    o->threads = 0;
+    o->blocks_per_sm = 0;
+    o->use_graph = 0;
+    o->time_budget_s = 60.0;
+}
+
+int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst, const float *data,
+              const double *start, double *best, fit_result *results, const fit_batch_opts *opts_in,
+              void *stream) {
+    if (!models || n_models < 1 || !inst || n_inst < 0 || !data || !best || !results)
+        return fail(FIT_ERR_INVALID_ARG, "fit_batch: bad argument");
+    if (n_inst == 0) return FIT_OK;
+    fit_batch_opts o;
+    fit_batch_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if (o.history < 1 || o.history > 16) return fail(FIT_ERR_INVALID_ARG, "fit_batch: history must be 1..16");
+    if (o.threads == 0) o.threads = 256;
+    if (o.threads < 64 || o.threads > 256 || o.threads % 32)
+        return fail(FIT_ERR_INVALID_ARG, "fit_batch: threads must be a multiple of 32 in [64, 256]");
+    if (!(o.edm_tol > 0.0) || o.max_iter < 0) return fail(FIT_ERR_INVALID_ARG, "fit_batch: edm_tol / max_iter");
+    if (o.time_budget_s <= 0.0) o.time_budget_s = 60.0;
+    cudaStream_t s = (cudaStream_t)stream;
+    // extents of the flat data / parameter arrays
+    int64_t data_len = 0, par_len = 0;
+    int max_need = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const fit_instance &q = inst[i];
+        if (q.model < 0 || q.model >= n_models || !models[q.model] || q.data_off < 0 || q.param_off < 0)
+            return fail(FIT_ERR_INVALID_ARG, "fit_batch: instance " + std::to_string(i) + " out of range");
+        data_len = std::max<int64_t>(data_len, q.data_off + models[q.model]->n_data);
+        par_len = std::max<int64_t>(par_len, q.param_off + models[q.model]->n_params);
+    }
+    for (int mi = 0; mi < n_models; ++mi) {
+        const DevModel &h = models[mi]->host;
+        max_need = std::max(max_need, fitcore::fit_vec_floats(h.P, o.history) + h.ws_eval_floats);
+    }
+    LaunchCfg cfg;
+    int rc = device_cfg(cfg);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    // workspace placement: shared memory if the largest model fits in ~1/2 of an SM's share
+    const size_t need_bytes = fitcore::fit_smem_bytes(max_need);
+    const bool in_smem = need_bytes <= 112 * 1024;
+    const size_t smem = in_smem ? need_bytes : fitcore::fit_smem_bytes(0);
+    FIT_CUDA(cudaFuncSetAttribute(fitcore::fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)std::min(smem, cfg.smem_optin)));
+    int per_sm = 0;
+    FIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fitcore::fit_kernel, o.threads, smem));
+    if (per_sm < 1) return fail(FIT_ERR_INVALID_CONFIG, "fit_batch: launch configuration does not fit an SM");
+    if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, o.blocks_per_sm);
+    const int grid = std::max(1, std::min(n_inst, per_sm * cfg.sms));
+
+    Staged dm, di, dd, dst, dbe, dre, dws, dq;
+    bool hbe = false, hre = false;
+    std::vector<DevModel> hm(n_models);
+    for (int i = 0; i < n_models; ++i) hm[i] = models[i]->host;
+    rc = stage_in(hm.data(), sizeof(DevModel) * n_models, s, dm);
+    if (!rc) rc = stage_in(inst, sizeof(fit_instance) * n_inst, s, di);
+    if (!rc) rc = stage_in(data, sizeof(float) * data_len, s, dd);
+    if (!rc && start) rc = stage_in(start, sizeof(double) * par_len, s, dst);
+    if (!rc) rc = stage_out(best, sizeof(double) * par_len, s, dbe, hbe);
+    if (!rc) rc = stage_out(results, sizeof(fit_result) * n_inst, s, dre, hre);
+    if (!rc && !in_smem) {
+        if (cudaMallocAsync(&dws.dev, sizeof(float) * (size_t)grid * max_need, s))
+            rc = fail(FIT_ERR_OOM, "fit_batch: workspace");
+        dws.owned = true;
+    }
+    if (!rc) {
+        if (cudaMallocAsync(&dq.dev, sizeof(int), s) || cudaMemsetAsync(dq.dev, 0, sizeof(int), s))
+            rc = fail(FIT_ERR_CUDA, "fit_batch: queue");
+        dq.owned = true;
+    }
+    if (!rc) {
+        fitcore::FitArgs a;
+        a.models = (const DevModel *)dm.dev;
+        a.inst = (const fit_instance *)di.dev;
+        a.n_inst = n_inst;
+        a.hist = o.history;
+        a.max_iter = o.max_iter;
+        a.max_ls = 30;
+        a.edm_tol = o.edm_tol;
+        a.f_noise_rel = o.f_noise_rel;
+        a.data = (const float *)dd.dev;
+        a.start = start ? (const double *)dst.dev : nullptr;
+        a.best = (double *)dbe.dev;
+        a.results = (fit_result *)dre.dev;
+        a.queue = (int *)dq.dev;
+        a.ws_global = (float *)dws.dev;
+        a.ws_stride = max_need;
+        a.smem_floats = in_smem ? max_need : 0;
+        a.budget_ns = (uint64_t)(o.time_budget_s * 1e9);
+        fitcore::fit_kernel<<<grid, o.threads, smem, s>>>(a);
+        g_launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = fail(FIT_ERR_CUDA, std::string("fit_kernel launch: ") + cudaGetErrorString(e));
+    }
+    if (!rc && hbe) {
+        // copy back only the parameter ranges the instances own (merged intervals), so that
+        // other entries of a host `best` array keep their values
+        std::vector<std::pair<int64_t, int64_t>> iv;
+        iv.reserve(n_inst);
+        for (int i = 0; i < n_inst; ++i)
+            iv.emplace_back(inst[i].param_off, inst[i].param_off + models[inst[i].model]->n_params);
+        std::sort(iv.begin(), iv.end());
+        int64_t a = iv[0].first, b = iv[0].second;
+        for (size_t q = 1; q <= iv.size() && !rc; ++q) {
+            if (q < iv.size() && iv[q].first <= b) {
+                b = std::max(b, iv[q].second);
+                continue;
+            }
+            if (cudaMemcpyAsync(best + a, (double *)dbe.dev + a, sizeof(double) * (b - a),
+                                cudaMemcpyDeviceToHost, s))
+                rc = fail(FIT_ERR_CUDA, "fit_batch: copy back");
+            if (q < iv.size()) {
+                a = iv[q].first;
+                b = iv[q].second;
+            }
+        }
+    }
+    if (!rc && hre && cudaMemcpyAsync(results, dre.dev, sizeof(fit_result) * n_inst, cudaMemcpyDeviceToHost, s))
+        rc = fail(FIT_ERR_CUDA, "fit_batch: copy back");
+    for (Staged *b : {&dm, &di, &dd, &dst, &dbe, &dre, &dws, &dq}) release(*b, s);
+    // the staged model table and instance table are host vectors: finish before they go away
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_batch: synchronise");
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,576 @@
+// Device-side model layout and block-level building blocks of the forward-folding fit.
+//
+// One thread block evaluates one parameter vector of one model: the expectation of every
+// dataset (survival x reweights on the fine true grid, energy correction by overlap length,
+// banded response fold, backgrounds), the Poisson -2lnL and its adjoint gradient. The same
+// device functions serve the batched evaluation kernels and the persistent fit kernel.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fitcore.h"
+
+namespace fitcore {
+
+constexpr int kMaxWarps = 16;      // blocks of at most 512 threads
+constexpr int kMaxBkgDs = 6;       // backgrounds per dataset
+
+struct DevDetector {
+    int n_reco;
+    int col_w;               // padded width of the column bands
+    const int *row_lo;       // [N_r] first true bin of row j's band
+    const int *row_len;      // [N_r] band length
+    const int *row_off;      // [N_r] offset of the row's band in rrow
+    const float *rrow;       // packed row bands
+    const int *col_lo;       // [N_t] first reco row of column k's band
+    const float *rcol;       // [col_w x N_t]: rcol[b * N_t + k] = R[col_lo[k] + b][k] (0 past the band)
+};
+
+struct DevBkg {
+    const float *tmpl;       // [N_r] expected counts at nominal
+    const int *shape_idx;    // [N_r] parameter of delta_j or -1
+    int rate_idx;
+    int pad;
+};
+
+struct DevDataset {
+    int det, n_reco, data_off;
+    int norm_idx, eff_idx;
+    int esc_idx[3];
+    float a1_off;            // theta0(a1) - 1, so that a1 - 1 = a1_off + (theta - theta0)
+    int bkg_begin, bkg_end;  // backgrounds of this dataset in DevModel::bkg
+    int n_sp;                // distinct shape parameters used by this dataset
+    const float *t;          // [N_t] un-oscillated signal
+    const int *shape_idx;    // [N_t]
+    const int *sp_param;     // [n_sp] parameter index
+    const int *sp_ptr;       // [n_sp + 1] CSR offsets into sp_k
+    const int *sp_k;         // true bins of each shape parameter
+    float w[FIT_MAX_CORES];  // core flux shares
+    float kl_hi[FIT_MAX_CORES], kl_lo[FIT_MAX_CORES];  // K L_dc / pi as a float pair (half-turns)
+};
+
+struct DevModel {
+    int P, N_t, C, n_ds, n_data, osc_mode, n_blocks, n_bkg;
+    float e_lo, de, inv_de;
+    int osc_idx[4];
+    float osc_val[4];
+    float osc_val_lo[4];     // low parts of the constant survival parameters
+    double osc_val_d[4];     // the constant survival parameters in double
+    int core_power_idx[FIT_MAX_CORES];
+    const float *e_edge;     // [N_t + 1]
+    const float *inv_e_hi;   // [N_t] 1 / E_k (true-bin centre) as a float pair
+    const float *inv_e_lo;
+    DevDataset ds[FIT_MAX_DATASETS];
+    DevDetector det[FIT_MAX_DETECTORS];
+    DevBkg bkg[FIT_MAX_BACKGROUNDS];
+    // parameters, priors and the transformation layer
+    const double *theta0;    // [P]
+    const float *theta0_f;   // [P] theta0 rounded to float
+    const float *theta0_lo;  // [P] theta0 - theta0_f (the low part of a float pair)
+    const float *zscale;     // [P] sigma (individual prior) or scale (free); 0 in a block
+    const float *prior_inv;  // [P] 1/sigma for individually constrained parameters, else 0
+    const int *blk_size;     // [n_blocks]
+    const int *blk_idx_off;  // [n_blocks]
+    const int *blk_idx;      // concatenated parameter indices
+    const int64_t *blk_mat_off;  // [n_blocks] offset of the block's m x m matrices
+    const float *blk_L;      // lower Cholesky factor of V (row-major, dense)
+    const float *blk_W;      // L^-1 (row-major, dense lower triangle)
+    const double *blk_L64;   // L in double (final theta of a fit)
+    const float *asimov;     // [n_data] expectation at theta0
+    int ws_eval_floats;      // per-block workspace of one evaluation
+    int max_reco;
+};
+
+// ------------------------------------------------------------------------------------
+// Reductions: FP32 within a warp, FP64 across warps.
+// ------------------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void warp_sum(float (&v)[N]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+}
+
+// Sums N per-thread values over the block. red: shared scratch of kMaxWarps * N doubles
+// (+ N result slots). Every thread returns the N totals. Contains two __syncthreads.
+template <int N>
+__device__ __forceinline__ void block_sum(float (&v)[N], double *red, double (&out)[N]) {
+    warp_sum<N>(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) red[warp * N + i] = (double)v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[w * N + threadIdx.x];
+        red[kMaxWarps * N + threadIdx.x] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = red[kMaxWarps * N + i];
+    __syncthreads();
+}
+
+// Same with double per-thread inputs (used where a thread already sums many terms).
+template <int N>
+__device__ __forceinline__ void block_sum_d(double (&v)[N], double *red, double (&out)[N]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) red[warp * N + i] = v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[w * N + threadIdx.x];
+        red[kMaxWarps * N + threadIdx.x] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = red[kMaxWarps * N + i];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------
+// Survival probability with phase arithmetic in float pairs.
+// ------------------------------------------------------------------------------------
+// Phase in half-turns: y = x / pi = (dm_hi + dm_lo) * (c_hi + c_lo), c = K L / (pi E), carried
+// as a float pair. The probability depends on sin^2 x and sin 2x only, so y is reduced by
+// its nearest integer, which is exact (y_hi - rint(y_hi) is representable), and sin, cos of
+// pi r, |r| <= 1/2, come from sincospif. The pair keeps r accurate to ~1e-8 even at 50 km
+// (y ~ 30), and no pi constant or multi-word reduction enters the arithmetic.
+__device__ __forceinline__ void phase_sc(float dm, float dm_lo, float c_hi, float c_lo, float &s,
+                                         float &c) {
+    const float yh = dm * c_hi;
+    const float yl = fmaf(dm, c_hi, -yh) + fmaf(dm, c_lo, dm_lo * c_hi);
+    const float r = (yh - rintf(yh)) + yl;
+    sincospif(r, &s, &c);
+}
+
+// Coefficients of the sin^2 terms of P, formed once per evaluation in double from the exact
+// parameter values and applied as float pairs (a single FP32 rounding of a coefficient would
+// bias every bin coherently).
+//   FIT_OSC_EQ1:     P = 1 - C0 sin^2 x_ee - C1 sin^2 x_21,  C0 = sin^2 2th13,
+//                    C1 = cos^4 th13 sin^2 2th12
+//   FIT_OSC_VACUUM3: P = 1 - C0 sin^2 x_21 - C1 sin^2 x_31 - C2 sin^2 x_32,
+//                    C0 = cos^4 th13 sin^2 2th12, C1 = sin^2 2th13 cos^2 th12,
+//                    C2 = sin^2 2th13 sin^2 th12
+struct OscCoef {
+    float hi[3], lo[3];
+};
+
+__device__ __forceinline__ float cterm(const OscCoef &k, int i, float q) {
+    return fmaf(q, k.lo[i], k.hi[i] * q);
+}
+
+// P(L_dc, E_k) and dP/d(eta_i) for the four survival parameters.
+//  mode FIT_OSC_EQ1:     eta = (sin^2 2th13, dm2_ee, sin^2 2th12, dm2_21), Eq. 1
+//  mode FIT_OSC_VACUUM3: eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31), exact vacuum P
+// eta_lo carries the low parts of the two mass splittings; dx = pi c (dx/d dm2).
+__device__ __forceinline__ float survival(const DevModel &m, const float (&eta)[4],
+                                          const float (&eta_lo)[4], const OscCoef &k,
+                                          float c_hi, float c_lo, float (&dP)[4]) {
+    const float dx = 3.14159265358979f * c_hi;
+    if (m.osc_mode == FIT_OSC_EQ1) {
+        const float S13 = eta[0], S12 = eta[2];
+        const float root = sqrtf(fmaxf(1.f - S13, 1e-12f));
+        const float c2 = 0.5f * (1.f + root);
+        const float c4 = c2 * c2;
+        float se, ce, s2, cc2;
+        phase_sc(eta[1], eta_lo[1], c_hi, c_lo, se, ce);
+        phase_sc(eta[3], eta_lo[3], c_hi, c_lo, s2, cc2);
+        const float qe = se * se, q21 = s2 * s2;
+        const float P = (1.f - cterm(k, 0, qe)) - cterm(k, 1, q21);
+        const float dc4 = -c2 * 0.5f / root;
+        dP[0] = -qe - dc4 * S12 * q21;
+        dP[1] = -S13 * 2.f * se * ce * dx;
+        dP[2] = -c4 * q21;
+        dP[3] = -c4 * S12 * 2.f * s2 * cc2 * dx;
+        return P;
+    } else {
+        const float s12 = eta[0], s13 = eta[1];
+        const float c12 = 1.f - s12, c13 = 1.f - s13;
+        const float S12 = 4.f * s12 * c12, S13 = 4.f * s13 * c13;
+        float a21, b21, a31, b31;
+        phase_sc(eta[2], eta_lo[2], c_hi, c_lo, a21, b21);
+        phase_sc(eta[3], eta_lo[3], c_hi, c_lo, a31, b31);
+        const float a32 = a31 * b21 - b31 * a21;   // sin(x31 - x21)
+        const float b32 = b31 * b21 + a31 * a21;   // cos(x31 - x21)
+        const float q21 = a21 * a21, q31 = a31 * a31, q32 = a32 * a32;
+        const float d21 = 2.f * a21 * b21 * dx, d31 = 2.f * a31 * b31 * dx,
+                    d32 = 2.f * a32 * b32 * dx;
+        const float P = ((1.f - cterm(k, 0, q21)) - cterm(k, 1, q31)) - cterm(k, 2, q32);
+        dP[0] = -c13 * c13 * 4.f * (1.f - 2.f * s12) * q21 - S13 * (q32 - q31);
+        dP[1] = 2.f * c13 * S12 * q21 - 4.f * (1.f - 2.f * s13) * (c12 * q31 + s12 * q32);
+        dP[2] = -c13 * c13 * S12 * d21 + S13 * s12 * d32;
+        dP[3] = -S13 * (c12 * d31 + s12 * d32);
+        return P;
+    }
+}
+
+// Poisson deviance 2[mu - n + n ln(n/mu)] = 2 mu h(r), r = (n - mu)/mu,
+// h(r) = (1+r) ln(1+r) - r, by its alternating series for |r| < 1/4.
+__device__ __forceinline__ float deviance(float n, float mu) {
+    if (n == 0.f) return 2.f * mu;
+    const float r = (n - mu) / mu;
+    float h;
+    if (fabsf(r) < 0.25f) {
+        // h = sum_{j>=2} (-1)^j r^j / (j (j-1))
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 14; j >= 2; --j) {
+            const float cj = ((j & 1) ? -1.f : 1.f) / (float)(j * (j - 1));
+            acc = fmaf(acc, r, cj);
+        }
+        h = acc * r * r;
+    } else {
+        h = (1.f + r) * log1pf(r) - r;
+    }
+    return 2.f * mu * h;
+}
+
+// ------------------------------------------------------------------------------------
+// Per-dataset workspace (floats), all of length N_t unless noted:
+//   u, v(->gv), ts = t s, ptot, dp0..dp3 (dp0 is reused for the shape gradient),
+//   pcw[C] = w_c P_c per core, f0[max_reco], gmu[max_reco]
+// ------------------------------------------------------------------------------------
+struct EvalWs {
+    float *u, *v, *ts, *ptot, *dp, *pcw, *f0, *gmu;
+};
+
+__host__ __device__ inline int eval_ws_floats(int N_t, int C, int max_reco) {
+    return (8 + C) * N_t + 2 * max_reco;
+}
+
+__device__ __forceinline__ EvalWs carve_eval_ws(float *base, int N_t, int C, int max_reco) {
+    EvalWs w;
+    w.u = base;
+    w.v = w.u + N_t;
+    w.ts = w.v + N_t;
+    w.ptot = w.ts + N_t;
+    w.dp = w.ptot + N_t;          // 4 * N_t
+    w.pcw = w.dp + 4 * N_t;       // C * N_t
+    w.f0 = w.pcw + C * N_t;       // max_reco
+    w.gmu = w.f0 + max_reco;      // max_reco
+    return w;
+}
+
+// Parameter access: pv = value, pd = value - theta0 (kept separately for precision).
+__device__ __forceinline__ float pval(const float *pv, int idx, float dflt) {
+    return idx >= 0 ? pv[idx] : dflt;
+}
+
+// A parameter as the float pair h + l: h = its float value, l = the exact rounding residual
+// (theta0_f - h) + delta + theta0_lo. Products x * theta are then formed as fma(x, l, x h),
+// so the kernels evaluate at the caller's double-precision point, not at its float rounding
+// (high-statistics normalisations have enough curvature for that rounding to show).
+struct PP {
+    float h, l;
+};
+
+__device__ __forceinline__ PP ppair(const DevModel &m, const float *pv, const float *pd, int p,
+                                    float dflt) {
+    if (p < 0) return PP{dflt, 0.f};
+    const float h = pv[p];
+    return PP{h, ((m.theta0_f[p] - h) + pd[p]) + m.theta0_lo[p]};
+}
+
+__device__ __forceinline__ float pmul(PP a, float x) { return fmaf(x, a.l, x * a.h); }
+
+// Status bits raised during an evaluation
+constexpr int kStMuNonpos = 1;
+constexpr int kStEscale = 2;
+
+// Energy map of dataset d in grid units: displacement D(e) = (a0 + (a1-1) e + a2 e^2) / de.
+struct EMap {
+    float a0, a1m1, a2, inv_de, e_lo, de;
+    __device__ __forceinline__ float disp(float e) const {
+        return fmaf(fmaf(a2, e, a1m1), e, a0) * inv_de;
+    }
+    __device__ __forceinline__ float slope(float e) const { return 1.f + a1m1 + 2.f * a2 * e; }
+};
+
+__device__ __forceinline__ EMap make_emap(const DevModel &m, const DevDataset &ds, const float *pv,
+                                          const float *pd) {
+    EMap em;
+    em.a0 = ds.esc_idx[0] >= 0 ? pv[ds.esc_idx[0]] : 0.f;
+    em.a1m1 = ds.esc_idx[1] >= 0 ? ds.a1_off + pd[ds.esc_idx[1]] : 0.f;
+    em.a2 = ds.esc_idx[2] >= 0 ? pv[ds.esc_idx[2]] : 0.f;
+    em.inv_de = m.inv_de;
+    em.e_lo = m.e_lo;
+    em.de = m.de;
+    return em;
+}
+
+// ------------------------------------------------------------------------------------
+// Block-level evaluation of one dataset: adds its Poisson -2lnL and (if grad != nullptr)
+// its gradient contributions (in theta space, shared-memory array of P floats).
+// Returns the dataset's -2lnL (all threads); *status |= kSt* bits on failure.
+// ------------------------------------------------------------------------------------
+static __device__ double eval_dataset(const DevModel &m, int d, const float *pv, const float *pd,
+                               const float *data, EvalWs ws, float *grad, double *red,
+                               int *status, float *mu_out) {
+    const DevDataset &ds = m.ds[d];
+    const DevDetector &dt = m.det[ds.det];
+    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+
+    // survival parameters; mass splittings as float pairs theta0_f + (theta0_lo + delta)
+    // Survival parameters: mass splittings as theta0_f + (theta0_lo + delta) inside the
+    // phase; the sin^2 coefficients from the exact values, in double, by one thread.
+    __shared__ OscCoef kco;
+    float eta[4], eta_lo[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int p = m.osc_idx[i];
+        const bool is_dm = (m.osc_mode == FIT_OSC_EQ1) ? (i == 1 || i == 3) : (i >= 2);
+        if (is_dm) {
+            eta[i] = p >= 0 ? m.theta0_f[p] : m.osc_val[i];
+            eta_lo[i] = p >= 0 ? m.theta0_lo[p] + pd[p] : m.osc_val_lo[i];
+        } else {
+            eta[i] = p >= 0 ? pv[p] : m.osc_val[i];
+            eta_lo[i] = 0.f;
+        }
+    }
+    if (tid == 0) {
+        double e[4];
+        for (int i = 0; i < 4; ++i) {
+            const int p = m.osc_idx[i];
+            e[i] = p >= 0 ? m.theta0[p] + (double)pd[p] : m.osc_val_d[i];
+        }
+        double c[3];
+        if (m.osc_mode == FIT_OSC_EQ1) {
+            const double c2 = 0.5 * (1.0 + sqrt(fmax(1.0 - e[0], 0.0)));
+            c[0] = e[0];
+            c[1] = c2 * c2 * e[2];
+            c[2] = 0.0;
+        } else {
+            const double S12 = 4.0 * e[0] * (1.0 - e[0]), S13 = 4.0 * e[1] * (1.0 - e[1]);
+            c[0] = (1.0 - e[1]) * (1.0 - e[1]) * S12;
+            c[1] = S13 * (1.0 - e[0]);
+            c[2] = S13 * e[0];
+        }
+        for (int i = 0; i < 3; ++i) {
+            kco.hi[i] = (float)c[i];
+            kco.lo[i] = (float)(c[i] - (double)kco.hi[i]);
+        }
+    }
+    __syncthreads();
+    const OscCoef kc = kco;
+    const PP nrm = ppair(m, pv, pd, ds.norm_idx, 1.f);
+    const PP eff = ppair(m, pv, pd, ds.eff_idx, 1.f);
+    const EMap em = make_emap(m, ds, pv, pd);
+
+    // the map must be increasing with slope in (1/4, 4) everywhere on the grid
+    {
+        const float s0 = em.slope(m.e_edge[0]), s1 = em.slope(m.e_edge[N_t]);
+        if (!(s0 > 0.25f && s0 < 4.f && s1 > 0.25f && s1 < 4.f)) {
+            if (tid == 0) atomicOr(status, kStEscale);
+            return 0.0;
+        }
+    }
+
+    // ---- stage A: signal on the true grid (Eq. 1/2 x shares x reweights) -----------------
+    for (int k = tid; k < N_t; k += nth) {
+        const float ih = m.inv_e_hi[k], il = m.inv_e_lo[k];
+        float pt = 0.f, dpt[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int c = 0; c < C; ++c) {
+            const float w = ds.w[c];
+            if (w == 0.f) {
+                ws.pcw[c * N_t + k] = 0.f;
+                continue;
+            }
+            const float ch = ds.kl_hi[c] * ih;
+            const float cl = fmaf(ds.kl_hi[c], ih, -ch) + ds.kl_hi[c] * il + ds.kl_lo[c] * ih;
+            float dP[4];
+            const float P = survival(m, eta, eta_lo, kc, ch, cl, dP);
+            const PP pw = ppair(m, pv, pd, m.core_power_idx[c], 1.f);
+            const float wP = w * P;
+            ws.pcw[c * N_t + k] = wP;
+            pt += pmul(pw, wP);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dpt[i] = fmaf(pw.h * w, dP[i], dpt[i]);
+        }
+        const float ts = pmul(ppair(m, pv, pd, ds.shape_idx[k], 1.f), ds.t[k]);
+        ws.ts[k] = ts;
+        ws.ptot[k] = pt;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ws.dp[i * N_t + k] = dpt[i];
+        ws.u[k] = pmul(nrm, ts * pt);
+    }
+    __syncthreads();
+
+    // ---- stage B: energy correction, gather per target bin ------------------------------
+    // Source bin k covers [Y_k, Y_k+1] in grid units, Y_k = k + D(e_k). Target m gathers the
+    // sources whose mapped interval overlaps [m, m+1]; overlaps are computed relative to the
+    // target (k - m is an exact small integer), which keeps them accurate in FP32.
+    for (int t = tid; t < N_t; t += nth) {
+        // first source whose mapped upper edge lies above t: start from the fixed point
+        // k ~ t - D(k) and step until the bracket is right
+        int k = t - (int)floorf(em.disp(m.e_edge[t]));
+        k = min(max(k, 0), N_t - 1);
+        k = t - (int)floorf(em.disp(m.e_edge[k]));
+        k = min(max(k - 1, 0), N_t - 1);
+        while (k > 0 && (float)(k - t) + em.disp(m.e_edge[k]) > 0.f) --k;
+        float acc = 0.f;
+        float dlo = em.disp(m.e_edge[k]);
+        for (int it = 0; it < 64 && k < N_t; ++it, ++k) {
+            const float dhi = em.disp(m.e_edge[k + 1]);
+            const float ylo = (float)(k - t) + dlo;      // mapped edges relative to target t
+            const float yhi = (float)(k + 1 - t) + dhi;
+            if (ylo >= 1.f) break;
+            const float ov = fminf(yhi, 1.f) - fmaxf(ylo, 0.f);
+            if (ov > 0.f) acc = fmaf(ws.u[k], ov / (1.f + (dhi - dlo)), acc);
+            dlo = dhi;
+        }
+        ws.v[t] = acc;
+    }
+    __syncthreads();
+
+    // ---- stage C: fold into reco bins (banded rows, warp per row) ------------------------
+    for (int j = warp; j < nr; j += nw) {
+        const int lo = dt.row_lo[j], len = dt.row_len[j];
+        const float *rr = dt.rrow + dt.row_off[j];
+        float s = 0.f;
+        for (int b = lane; b < len; b += 32) s = fmaf(rr[b], ws.v[lo + b], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) ws.f0[j] = s;
+    }
+    __syncthreads();
+
+    // ---- stage C2: backgrounds, deviance, dD/dmu ----------------------------------------
+    const int nb = ds.bkg_end - ds.bkg_begin;
+    float part[2 + kMaxBkgDs];
+    // part[0] = deviance, part[1] = d/d eff, part[2+b] = d/d rate_b
+#pragma unroll
+    for (int i = 0; i < 2 + kMaxBkgDs; ++i) part[i] = 0.f;
+    for (int j = tid; j < nr; j += nth) {
+        float mu = pmul(eff, ws.f0[j]);
+#pragma unroll
+        for (int b = 0; b < kMaxBkgDs; ++b) {
+            if (b >= nb) break;
+            const DevBkg &bk = m.bkg[ds.bkg_begin + b];
+            const float tm = bk.tmpl[j];
+            const float shaped = bk.shape_idx[j] >= 0 ? fmaf(tm, pv[bk.shape_idx[j]], tm) : tm;
+            mu += pmul(ppair(m, pv, pd, bk.rate_idx, 1.f), shaped);
+        }
+        if (mu_out) mu_out[j] = mu;
+        if (data == nullptr) continue;
+        const float n = data[ds.data_off + j];
+        if (!(mu > 0.f)) {
+            atomicOr(status, kStMuNonpos);
+            continue;
+        }
+        part[0] += deviance(n, mu);
+        const float g = 2.f * (mu - n) / mu;
+        ws.gmu[j] = g;
+        if (grad) {
+            part[1] = fmaf(g, ws.f0[j], part[1]);
+#pragma unroll
+            for (int b = 0; b < kMaxBkgDs; ++b) {
+                if (b >= nb) break;
+                const DevBkg &bk = m.bkg[ds.bkg_begin + b];
+                const int si = bk.shape_idx[j];
+                const float sh = 1.f + (si >= 0 ? pv[si] : 0.f);
+                part[2 + b] = fmaf(g * bk.tmpl[j], sh, part[2 + b]);
+                if (si >= 0) atomicAdd(&grad[si], g * pval(pv, bk.rate_idx, 1.f) * bk.tmpl[j]);
+            }
+        }
+    }
+    double tot[2 + kMaxBkgDs];
+    block_sum<2 + kMaxBkgDs>(part, red, tot);
+    const double nll_d = tot[0];
+    if (data == nullptr || grad == nullptr || (*(volatile int *)status) != 0) return nll_d;
+    if (tid == 0) {
+        if (ds.eff_idx >= 0) grad[ds.eff_idx] += (float)tot[1];
+#pragma unroll
+        for (int b = 0; b < kMaxBkgDs; ++b) {
+            if (b >= nb) break;
+            const int ri = m.bkg[ds.bkg_begin + b].rate_idx;
+            if (ri >= 0) grad[ri] += (float)tot[2 + b];
+        }
+    }
+
+    // ---- stage D: adjoint of the fold, gv = eff R^T gmu (column bands) --------------------
+    float *gv = ws.v;   // v is dead after the fold
+    for (int k = tid; k < N_t; k += nth) {
+        const int lo = dt.col_lo[k];
+        float s = 0.f;
+        for (int b = 0; b < dt.col_w; ++b) {
+            const int j = lo + b;
+            if (j >= nr) break;
+            s = fmaf(dt.rcol[b * N_t + k], ws.gmu[j], s);
+        }
+        gv[k] = pmul(eff, s);
+    }
+    __syncthreads();
+
+    // ---- stage E: adjoint of the energy map and of the signal ---------------------------
+    // per source k: gu = sum_t F_kt gv_t; A0 = (gu - gv(floor Y_k)) / w, A1 = (gv(floor Y_k+1) - gu) / w
+    float ep[8 + FIT_MAX_CORES];
+    // ep[0..2] d/da, ep[3..6] d/d eta, ep[7] d/d norm, ep[8+c] d/d power_c
+#pragma unroll
+    for (int i = 0; i < 8 + FIT_MAX_CORES; ++i) ep[i] = 0.f;
+    for (int k = tid; k < N_t; k += nth) {
+        const float e0 = m.e_edge[k], e1 = m.e_edge[k + 1];
+        const float d0 = em.disp(e0), d1 = em.disp(e1);
+        const float w = 1.f + (d1 - d0);
+        const int f0i = (int)floorf(d0), f1i = (int)floorf(d1);
+        const int t0 = k + f0i, t1 = k + 1 + f1i;
+        float gu = 0.f;
+        for (int t = max(t0, 0); t <= min(t1, N_t - 1); ++t) {
+            const float ylo = (float)(k - t) + d0, yhi = (float)(k + 1 - t) + d1;
+            const float ov = fminf(yhi, 1.f) - fmaxf(ylo, 0.f);
+            if (ov > 0.f) gu = fmaf(ov / w, gv[t], gu);
+        }
+        const float g0 = (t0 >= 0 && t0 < N_t) ? gv[t0] : 0.f;
+        const float g1 = (t1 >= 0 && t1 < N_t) ? gv[t1] : 0.f;
+        const float uk = ws.u[k];
+        const float A0 = uk * (gu - g0) / w, A1 = uk * (g1 - gu) / w;
+        ep[0] += (A0 + A1) * em.inv_de;
+        ep[1] += (A0 * e0 + A1 * e1) * em.inv_de;
+        ep[2] += (A0 * e0 * e0 + A1 * e1 * e1) * em.inv_de;
+        const float ts = ws.ts[k], pt = ws.ptot[k];
+        const float gb = pmul(nrm, gu * ts);    // d nll / d(ptot)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ep[3 + i] = fmaf(gb, ws.dp[i * N_t + k], ep[3 + i]);
+        ep[7] = fmaf(gu * ts, pt, ep[7]);
+#pragma unroll
+        for (int c = 0; c < FIT_MAX_CORES; ++c)
+            if (c < C) ep[8 + c] = fmaf(gb, ws.pcw[c * N_t + k], ep[8 + c]);
+        ws.dp[k] = pmul(nrm, gu * ds.t[k] * pt);    // d nll / d s for this bin (dp0 reused)
+    }
+    double etot[8 + FIT_MAX_CORES];
+    block_sum<8 + FIT_MAX_CORES>(ep, red, etot);
+    if (tid == 0) {
+        for (int i = 0; i < 3; ++i)
+            if (ds.esc_idx[i] >= 0) grad[ds.esc_idx[i]] += (float)etot[i];
+        for (int i = 0; i < 4; ++i)
+            if (m.osc_idx[i] >= 0) grad[m.osc_idx[i]] += (float)etot[3 + i];
+        if (ds.norm_idx >= 0) grad[ds.norm_idx] += (float)etot[7];
+#pragma unroll
+        for (int c = 0; c < FIT_MAX_CORES; ++c)
+            if (c < C && m.core_power_idx[c] >= 0) grad[m.core_power_idx[c]] += (float)etot[8 + c];
+    }
+    // ---- stage F: shape reweights (one thread per distinct parameter, CSR over bins) -----
+    for (int i = tid; i < ds.n_sp; i += nth) {
+        float s = 0.f;
+        for (int q = ds.sp_ptr[i]; q < ds.sp_ptr[i + 1]; ++q) s += ws.dp[ds.sp_k[q]];
+        grad[ds.sp_param[i]] += s;
+    }
+    __syncthreads();
+    return nll_d;
+}
+
+}  // namespace fitcore

@@ -1,0 +1,36 @@
+// Kernel entry points and launch arguments shared by kernels.cu and capi.cu.
+#pragma once
+#include "dev_model.cuh"
+
+namespace fitcore {
+
+struct FitArgs {
+    const DevModel *models;      // device array, one per model
+    const fit_instance *inst;    // device [n_inst]
+    int n_inst;
+    int hist;                    // L-BFGS pairs
+    int max_iter;
+    int max_ls;                  // trial steps per line search
+    double edm_tol;
+    double f_noise_rel;
+    const float *data;           // device
+    const double *start;         // device or nullptr
+    double *best;                // device
+    fit_result *results;         // device [n_inst]
+    int *queue;                  // device counter, zero at launch
+    float *ws_global;            // per-block global workspace slices (or nullptr)
+    int64_t ws_stride;           // floats per block slice
+    int smem_floats;             // dynamic shared floats available for the workspace
+    uint64_t budget_ns;
+};
+
+__global__ void eval_kernel(const DevModel *gm, int B, const double *theta, const float *data,
+                            const uint32_t *masks, double *nll_out, float *grad_out,
+                            float *mu_out, int *status_out, float *ws_global, int ws_in_smem);
+__global__ void fit_kernel(FitArgs A);
+
+size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem);
+size_t fit_smem_bytes(int floats);
+__host__ __device__ inline int fit_vec_floats(int P, int hist) { return (12 + 2 * hist) * P; }
+
+}  // namespace fitcore

@@ -1,0 +1,295 @@
+"""Thin ctypes binding of the C ABI in include/fitcore.h (argument marshalling only).
+
+Every computation runs in libfitcore.so. Arguments may be torch tensors (CPU or CUDA) or
+numpy arrays; their data pointers are handed to the library, which stages host buffers
+through device memory itself. If the library cannot be loaded this module raises: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class FitError(RuntimeError):
+    pass
+
+
+# ---- C structures (mirror include/fitcore.h) ----------------------------------------------
+class fit_model_desc(C.Structure):
+    _fields_ = [
+        ("n_params", C.c_int),
+        ("theta0", C.POINTER(C.c_double)), ("prior_sigma", C.POINTER(C.c_double)),
+        ("scale", C.POINTER(C.c_double)),
+        ("n_cov", C.c_int), ("cov_size", C.POINTER(C.c_int)), ("cov_idx", C.POINTER(C.c_int)),
+        ("cov", C.POINTER(C.c_double)),
+        ("osc_mode", C.c_int), ("osc_idx", C.c_int * 4), ("osc_val", C.c_double * 4),
+        ("n_cores", C.c_int), ("core_power_idx", C.POINTER(C.c_int)),
+        ("n_true", C.c_int), ("e_lo", C.c_double), ("e_hi", C.c_double),
+        ("n_det", C.c_int), ("det_n_reco", C.POINTER(C.c_int)),
+        ("det_response", C.POINTER(C.c_double)),
+        ("n_ds", C.c_int), ("ds_det", C.POINTER(C.c_int)), ("ds_t", C.POINTER(C.c_double)),
+        ("ds_baseline", C.POINTER(C.c_double)), ("ds_weight", C.POINTER(C.c_double)),
+        ("ds_norm_idx", C.POINTER(C.c_int)), ("ds_eff_idx", C.POINTER(C.c_int)),
+        ("ds_escale_idx", C.POINTER(C.c_int)), ("ds_shape_idx", C.POINTER(C.c_int)),
+        ("n_bkg", C.c_int), ("bkg_ds", C.POINTER(C.c_int)),
+        ("bkg_template", C.POINTER(C.c_double)), ("bkg_rate_idx", C.POINTER(C.c_int)),
+        ("bkg_shape_idx", C.POINTER(C.c_int)),
+    ]
+
+
+class fit_model_info_t(C.Structure):
+    _fields_ = [("n_params", C.c_int), ("n_data", C.c_int), ("n_datasets", C.c_int),
+                ("n_true", C.c_int), ("device_bytes", C.c_size_t)]
+
+
+class fit_instance(C.Structure):
+    _fields_ = [("model", C.c_int), ("mask", C.c_uint32), ("data_off", C.c_int64),
+                ("param_off", C.c_int64)]
+
+
+class fit_batch_opts(C.Structure):
+    _fields_ = [("edm_tol", C.c_double), ("max_iter", C.c_int), ("history", C.c_int),
+                ("f_noise_rel", C.c_double), ("threads", C.c_int), ("blocks_per_sm", C.c_int),
+                ("use_graph", C.c_int), ("time_budget_s", C.c_double)]
+
+
+class fit_result(C.Structure):
+    _fields_ = [("nll_min", C.c_double), ("edm", C.c_double), ("iters", C.c_int),
+                ("n_evals", C.c_int), ("status", C.c_int), ("pad", C.c_int)]
+
+
+RESULT_DTYPE = np.dtype([("nll_min", "<f8"), ("edm", "<f8"), ("iters", "<i4"),
+                         ("n_evals", "<i4"), ("status", "<i4"), ("pad", "<i4")])
+INSTANCE_DTYPE = np.dtype([("model", "<i4"), ("mask", "<u4"), ("data_off", "<i8"),
+                           ("param_off", "<i8")])
+assert RESULT_DTYPE.itemsize == C.sizeof(fit_result)
+assert INSTANCE_DTYPE.itemsize == C.sizeof(fit_instance)
+
+STATUS = {0: "converged", 1: "maxiter", 2: "linesearch_fail", 3: "nonfinite",
+          4: "mu_nonpositive", 5: "escale_nonmonotone", 6: "timeout"}
+
+EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model_expected",
+           "fit_model_eval", "fit_batch_default_opts", "fit_batch", "fit_last_error",
+           "fit_kernel_launches")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libfitcore.so (building it first if asked). Raises FitError if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise FitError(f"libfitcore.so is not built ({_build.LIB}); run __graft_entry__.build()")
+    L = C.CDLL(_build.LIB)
+    vp = C.c_void_p
+    L.fit_model_create.argtypes = [C.POINTER(fit_model_desc), C.POINTER(vp)]
+    L.fit_model_destroy.argtypes = [vp]
+    L.fit_model_info.argtypes = [vp, C.POINTER(fit_model_info_t)]
+    L.fit_model_expected.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    L.fit_model_eval.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
+    L.fit_batch_default_opts.argtypes = [C.POINTER(fit_batch_opts)]
+    L.fit_batch.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_int, vp, vp, vp, vp,
+                            C.POINTER(fit_batch_opts), vp]
+    L.fit_last_error.restype = C.c_char_p
+    L.fit_kernel_launches.restype = C.c_int64
+    for f in ("fit_model_create", "fit_model_info", "fit_model_expected", "fit_model_eval",
+              "fit_batch"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = load().fit_last_error().decode(errors="replace")
+        raise FitError(f"{what} failed ({rc}): {msg}")
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor / numpy array (must be contiguous), or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Model:
+    """A model resident on the current CUDA device (wraps fit_model*)."""
+
+    def __init__(self, spec):
+        L = load()
+        self.spec = spec
+        keep = []
+
+        def d(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data_as(C.POINTER(C.c_double))
+
+        def i(a):
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            keep.append(a)
+            return a.ctypes.data_as(C.POINTER(C.c_int))
+
+        s = spec
+        m = fit_model_desc()
+        m.n_params = s.n_params
+        m.theta0, m.prior_sigma, m.scale = d(s.theta0), d(s.prior_sigma), d(s.scale)
+        m.n_cov = len(s.cov_blocks)
+        m.cov_size = i([len(ix) for ix, _ in s.cov_blocks] or [0])
+        m.cov_idx = i(np.concatenate([ix for ix, _ in s.cov_blocks]) if s.cov_blocks else [0])
+        m.cov = d(np.concatenate([c.ravel() for _, c in s.cov_blocks]) if s.cov_blocks else [0.0])
+        m.osc_mode = s.osc_mode
+        for k in range(4):
+            m.osc_idx[k] = int(s.osc_idx[k])
+            m.osc_val[k] = float(s.osc_val[k])
+        m.n_cores = s.n_cores
+        m.core_power_idx = i(s.core_power_idx)
+        m.n_true, m.e_lo, m.e_hi = s.n_true, s.e_lo, s.e_hi
+        m.n_det = len(s.detectors)
+        m.det_n_reco = i([dt.n_reco for dt in s.detectors])
+        m.det_response = d(np.concatenate([dt.response.ravel() for dt in s.detectors]))
+        ds = s.datasets
+        m.n_ds = len(ds)
+        m.ds_det = i([x.det for x in ds])
+        m.ds_t = d(np.concatenate([x.t for x in ds]))
+        m.ds_baseline = d(np.concatenate([x.baseline for x in ds]))
+        m.ds_weight = d(np.concatenate([x.weight for x in ds]))
+        m.ds_norm_idx = i([x.norm_idx for x in ds])
+        m.ds_eff_idx = i([x.eff_idx for x in ds])
+        m.ds_escale_idx = i(np.concatenate([x.escale_idx for x in ds]))
+        m.ds_shape_idx = i(np.concatenate([x.shape_idx for x in ds]))
+        bk = [(di, b) for di, x in enumerate(ds) for b in x.backgrounds]
+        m.n_bkg = len(bk)
+        m.bkg_ds = i([di for di, _ in bk] or [0])
+        m.bkg_template = d(np.concatenate([b.template for _, b in bk]) if bk else [0.0])
+        m.bkg_rate_idx = i([b.rate_idx for _, b in bk] or [0])
+        m.bkg_shape_idx = i(np.concatenate([b.shape_idx for _, b in bk]) if bk else [0])
+        h = C.c_void_p()
+        _check(L.fit_model_create(C.byref(m), C.byref(h)), "fit_model_create")
+        self.handle = h
+        info = fit_model_info_t()
+        _check(L.fit_model_info(h, C.byref(info)), "fit_model_info")
+        self.n_params, self.n_data = info.n_params, info.n_data
+        self.n_datasets, self.device_bytes = info.n_datasets, info.device_bytes
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fit_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def fit_model_create(spec) -> Model:
+    return Model(spec)
+
+
+def fit_model_destroy(model: Model):
+    model.close()
+
+
+def fit_model_expected(model: Model, B: int, theta, mu_out, status_out=None, stream=None):
+    _check(load().fit_model_expected(model.handle, int(B), _ptr(theta), _ptr(mu_out),
+                                     _ptr(status_out), _stream_ptr(stream)),
+           "fit_model_expected")
+
+
+def fit_model_eval(model: Model, B: int, theta, data, masks, nll_out, grad_out=None,
+                   status_out=None, stream=None):
+    if masks is not None:
+        masks = np.ascontiguousarray(masks, dtype=np.uint32)
+    _check(load().fit_model_eval(model.handle, int(B), _ptr(theta), _ptr(data), _ptr(masks),
+                                 _ptr(nll_out), _ptr(grad_out), _ptr(status_out),
+                                 _stream_ptr(stream)),
+           "fit_model_eval")
+
+
+def fit_batch_default_opts() -> fit_batch_opts:
+    o = fit_batch_opts()
+    load().fit_batch_default_opts(C.byref(o))
+    return o
+
+
+def fit_batch(models, inst, data, start, best, results, opts=None, stream=None):
+    """inst: numpy structured array of INSTANCE_DTYPE; results: RESULT_DTYPE array or a
+    uint8 device tensor of n_inst * 32 bytes."""
+    L = load()
+    hs = (C.c_void_p * len(models))(*[m.handle.value for m in models])
+    inst = np.ascontiguousarray(inst, dtype=INSTANCE_DTYPE)
+    o = opts if opts is not None else fit_batch_default_opts()
+    _check(L.fit_batch(hs, len(models), inst.ctypes.data, len(inst), _ptr(data), _ptr(start),
+                       _ptr(best), _ptr(results), C.byref(o), _stream_ptr(stream)),
+           "fit_batch")
+
+
+def fit_kernel_launches() -> int:
+    return int(load().fit_kernel_launches())
+
+
+# ---- convenience wrappers used by tests and the benchmark ---------------------------------
+def eval_numpy(model: Model, theta, data=None, masks=None, grad=True):
+    """-2lnL (and gradient) for a [B, P] float64 array, host buffers in and out."""
+    theta = np.ascontiguousarray(np.atleast_2d(theta), dtype=np.float64)
+    B = theta.shape[0]
+    if data is not None:
+        data = np.ascontiguousarray(np.atleast_2d(data), dtype=np.float32)
+    nll = np.zeros(B)
+    g = np.zeros((B, model.n_params), np.float32) if grad else None
+    st = np.zeros(B, np.int32)
+    fit_model_eval(model, B, theta, data, masks, nll, g, st)
+    return nll, g, st
+
+
+def expected_numpy(model: Model, theta):
+    theta = np.ascontiguousarray(np.atleast_2d(theta), dtype=np.float64)
+    mu = np.zeros((theta.shape[0], model.n_data), np.float32)
+    st = np.zeros(theta.shape[0], np.int32)
+    fit_model_expected(model, theta.shape[0], theta, mu, st)
+    return mu, st
+
+
+def fit_numpy(models, inst, data, start=None, opts=None):
+    """Runs fit_batch on host arrays; returns (best [flat float64], results RESULT_DTYPE)."""
+    inst = np.ascontiguousarray(inst, dtype=INSTANCE_DTYPE)
+    npar = max(int(r["param_off"]) + models[int(r["model"])].n_params for r in inst)
+    best = np.zeros(npar)
+    res = np.zeros(len(inst), RESULT_DTYPE)
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    if start is not None:
+        start = np.ascontiguousarray(start, dtype=np.float64)
+    fit_batch(models, inst, data, start, best, res, opts)
+    return best, res

@@ -1,0 +1,54 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/*.h declares.
+
+No compute call is made here (CPU only)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+
+from paper_2502_15253_gb300 import fitcore
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(fit_\w+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("fit_model_create", "fit_model_eval", "fit_model_expected", "fit_batch"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = fitcore.load(build_if_missing=True)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_header_sizes():
+    # sizes of the ABI structs as laid out by the binding (natural alignment, x86-64 / aarch64)
+    assert ctypes.sizeof(fitcore.fit_instance) == 24
+    assert ctypes.sizeof(fitcore.fit_result) == 32
+    assert ctypes.sizeof(fitcore.fit_batch_opts) == 48
+    assert fitcore.RESULT_DTYPE.itemsize == 32
+
+
+def test_default_opts_and_error_message_without_gpu():
+    L = fitcore.load(build_if_missing=True)
+    o = fitcore.fit_batch_default_opts()
+    assert o.history == 10 and o.max_iter > 0 and o.edm_tol > 0
+    # invalid arguments are rejected on the host before any device work
+    rc = L.fit_model_create(None, None)
+    assert rc == -1
+    assert b"null" in L.fit_last_error()
+    assert np.isfinite(o.f_noise_rel)
