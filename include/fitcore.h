@@ -139,8 +139,8 @@ int fit_model_expected(fit_model *model, int B, const double *theta, float *mu_o
 
 /* -2lnL and its gradient for B parameter vectors at once (Eq. 3-9).
  * theta: host or device [B x P] double; data: host or device [B x n_data] float counts
- * (NULL = every row uses the model's Asimov data at theta0); masks: host [B] uint32 bit d
- * set = dataset d enters the Poisson term (NULL = all datasets).
+ * (NULL = every row uses the model's Asimov data at theta0); masks: host or device [B]
+ * uint32, bit d set = dataset d enters the Poisson term (NULL = all datasets).
  * nll_out: host or device [B] double (+inf where mu <= 0 or the energy map is invalid).
  * grad_out: host or device [B x P] float d(-2lnL)/dtheta, or NULL to skip.
  * status_out: host or device [B] int or NULL. */
@@ -159,12 +159,16 @@ typedef struct fit_instance {
 typedef struct fit_batch_opts {
     double edm_tol;       /* stop when EDM = 1/2 g^T H g < edm_tol (default 1e-8)             */
     int max_iter;         /* iteration limit (default 2000)                                  */
-    int history;          /* L-BFGS pairs kept, 1..16 (default 10)                           */
+    int history;          /* L-BFGS pairs kept, 1..16 (default 16)                           */
     double f_noise_rel;   /* relative noise allowance of -2lnL in the line search (1e-6)     */
     int threads;          /* threads per block, multiple of 32 in [64, 256]; 0 = default 256 */
     int blocks_per_sm;    /* resident blocks per SM; 0 = autotuned / occupancy maximum      */
     int use_graph;        /* 1 = launch through a cached CUDA graph                          */
     double time_budget_s; /* per-launch clock budget (0 = 60 s); exceeded -> FIT_STATUS_TIMEOUT */
+    int restarts;         /* history restarts after the first EDM convergence, 0..8 (default 0):
+                             each rebuilds the L-BFGS pairs for at least `history` iterations,
+                             which firms up the EDM estimate in flat directions             */
+    int pad;
 } fit_batch_opts;
 
 /* Result of one instance. */

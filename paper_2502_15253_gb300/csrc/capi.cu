@@ -664,12 +664,13 @@ void fit_batch_default_opts(fit_batch_opts *o) {
     if (!o) return;
     o->edm_tol = 1e-8;
     o->max_iter = 2000;
-    o->history = 10;
+    o->history = 16;
     o->f_noise_rel = 1e-6;
     o->threads = 0;
     o->blocks_per_sm = 0;
     o->use_graph = 0;
     o->time_budget_s = 60.0;
+    o->restarts = 0;
 }
 
 int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst, const float *data,
@@ -682,6 +683,7 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
     fit_batch_default_opts(&o);
     if (opts_in) o = *opts_in;
     if (o.history < 1 || o.history > 16) return fail(FIT_ERR_INVALID_ARG, "fit_batch: history must be 1..16");
+    if (o.restarts < 0 || o.restarts > 8) return fail(FIT_ERR_INVALID_ARG, "fit_batch: restarts must be 0..8");
     if (o.threads == 0) o.threads = 256;
     if (o.threads < 64 || o.threads > 256 || o.threads % 32)
         return fail(FIT_ERR_INVALID_ARG, "fit_batch: threads must be a multiple of 32 in [64, 256]");
@@ -746,6 +748,7 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
         a.hist = o.history;
         a.max_iter = o.max_iter;
         a.max_ls = 30;
+        a.restarts = o.restarts;
         a.edm_tol = o.edm_tol;
         a.f_noise_rel = o.f_noise_rel;
         a.data = (const float *)dd.dev;

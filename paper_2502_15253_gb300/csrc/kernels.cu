@@ -358,6 +358,11 @@ __global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
             if (!isfinite(f)) status = FIT_STATUS_NONFINITE;
             int hn = 0, head = 0;   // history size and next slot
             double gamma = 1.0;
+            // After the first EDM convergence the history is dropped and rebuilt (at least
+            // hist_max iterations) up to A.restarts times: the fresh pairs come from the
+            // directions still moving, which are the flat ones a short history had not seen,
+            // and where its EDM estimate was too small.
+            int restarts_left = A.restarts, since_restart = hist_max;
             while (status == FIT_STATUS_MAXITER) {
                 // ---- direction d = -H g, two-loop recursion ------------------------------
                 vcopy(V.d, V.g, P);
@@ -397,9 +402,16 @@ __global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
                 }
                 const double edm = -0.5 * gd;
                 res.edm = edm;
-                if (edm < A.edm_tol) {
-                    status = FIT_STATUS_CONVERGED;
-                    break;
+                if (edm < A.edm_tol && since_restart >= hist_max) {
+                    if (restarts_left == 0) {
+                        status = FIT_STATUS_CONVERGED;
+                        break;
+                    }
+                    --restarts_left;
+                    since_restart = 0;
+                    hn = 0;
+                    head = 0;
+                    continue;
                 }
                 if (res.iters >= A.max_iter) break;
                 if (global_ns() > deadline) {
@@ -505,6 +517,7 @@ __global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
                 __syncthreads();
                 f = fa;
                 res.iters++;
+                since_restart++;
             }
             res.nll_min = f;
         }

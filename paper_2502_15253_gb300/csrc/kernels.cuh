@@ -11,6 +11,7 @@ struct FitArgs {
     int hist;                    // L-BFGS pairs
     int max_iter;
     int max_ls;                  // trial steps per line search
+    int restarts;                // history restarts after the first EDM convergence
     double edm_tol;
     double f_noise_rel;
     const float *data;           // device

@@ -57,7 +57,8 @@ class fit_instance(C.Structure):
 class fit_batch_opts(C.Structure):
     _fields_ = [("edm_tol", C.c_double), ("max_iter", C.c_int), ("history", C.c_int),
                 ("f_noise_rel", C.c_double), ("threads", C.c_int), ("blocks_per_sm", C.c_int),
-                ("use_graph", C.c_int), ("time_budget_s", C.c_double)]
+                ("use_graph", C.c_int), ("time_budget_s", C.c_double), ("restarts", C.c_int),
+                ("pad", C.c_int)]
 
 
 class fit_result(C.Structure):
@@ -230,7 +231,7 @@ def fit_model_expected(model: Model, B: int, theta, mu_out, status_out=None, str
 
 def fit_model_eval(model: Model, B: int, theta, data, masks, nll_out, grad_out=None,
                    status_out=None, stream=None):
-    if masks is not None:
+    if masks is not None and not hasattr(masks, "data_ptr"):
         masks = np.ascontiguousarray(masks, dtype=np.uint32)
     _check(load().fit_model_eval(model.handle, int(B), _ptr(theta), _ptr(data), _ptr(masks),
                                  _ptr(nll_out), _ptr(grad_out), _ptr(status_out),

@@ -39,14 +39,14 @@ def test_struct_layouts_match_header_sizes():
     # sizes of the ABI structs as laid out by the binding (natural alignment, x86-64 / aarch64)
     assert ctypes.sizeof(fitcore.fit_instance) == 24
     assert ctypes.sizeof(fitcore.fit_result) == 32
-    assert ctypes.sizeof(fitcore.fit_batch_opts) == 48
+    assert ctypes.sizeof(fitcore.fit_batch_opts) == 56
     assert fitcore.RESULT_DTYPE.itemsize == 32
 
 
 def test_default_opts_and_error_message_without_gpu():
     L = fitcore.load(build_if_missing=True)
     o = fitcore.fit_batch_default_opts()
-    assert o.history == 10 and o.max_iter > 0 and o.edm_tol > 0
+    assert o.history == 16 and o.max_iter > 0 and o.edm_tol > 0
     # invalid arguments are rejected on the host before any device work
     rc = L.fit_model_create(None, None)
     assert rc == -1
