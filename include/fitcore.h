@@ -5,15 +5,18 @@
  * Poisson -2lnL with Gaussian and covariance priors, its gradient, and runs many quasi-Newton
  * fits at once, all on one GPU (sm_103a). It follows PhyLiNO (arXiv 2502.15253):
  *
- *   expectation per dataset d, true bin k, reco bin j (Sec. 5-6, Eq. 9):
+ *   expectation per dataset d, true bin k, reco bin j (Eq. 9; [L], [S]):
  *     u_dk  = t_dk n_d s_g(k) sum_c p_c w_dc P(L_dc, E_k; eta)        survival: Eq. 1 with
  *             Delta m^2_ee of Eq. 2, or the exact 3-flavour vacuum probability (Eq. 10)
  *     v_d   = M(a_d) u_d  energy correction E' = a0 + a1 E + a2 E^2, each true bin's content
- *             spread over the original binning by overlap length (Sec. 6, third signal step)
+ *             spread over the original binning by overlap length ([S], third signal step)
  *     mu_dj = eps_d sum_k R_d[j,k] v_dk + sum_b r_b B_bj (1 + delta_bj)
  *   -2lnL = sum_d sum_j 2[mu - n + n ln(n/mu)]            Eq. 3-5 normalised as in Eq. 8
  *         + sum_i ((theta_i - theta0_i)/sigma_i)^2          Eq. 6
  *         + sum_B (theta_B - theta0_B)^T V_B^-1 (theta_B - theta0_B)   Eq. 6, Eq. 9
+ *
+ * [S] = the paper's section "Structure of the framework"; [L] = its section "Likelihood
+ * implementation for Double Chooz within the framework".
  *
  * Conventions
  *  - Every function returns FIT_OK (0) or a negative FIT_ERR_* code; fit_last_error() then
@@ -124,14 +127,14 @@ typedef struct fit_model_info_t {
 } fit_model_info_t;
 
 /* Builds a model from its description: validates it, computes the banded response layout,
- * the Cholesky factors of the prior blocks (the transformation layer of Sec. 6) and uploads
+ * the Cholesky factors of the prior blocks (the transformation layer of [S]) and uploads
  * everything to the current device. *out receives the model (free with fit_model_destroy).
  * Errors: INVALID_ARG / INVALID_CONFIG (message names the field), NON_SPD_COV, OOM, CUDA. */
 int fit_model_create(const fit_model_desc *desc, fit_model **out);
 void fit_model_destroy(fit_model *model);
 int fit_model_info(const fit_model *model, fit_model_info_t *info);
 
-/* Expected counts mu (Sec. 5-6) for B parameter vectors.
+/* Expected counts mu ([L], [S]) for B parameter vectors.
  * theta: host or device, [B x P] double. mu_out: host or device, [B x n_data] float.
  * status_out: host or device [B] int (FIT_STATUS_*) or NULL. */
 int fit_model_expected(fit_model *model, int B, const double *theta, float *mu_out,
@@ -186,7 +189,7 @@ void fit_batch_default_opts(fit_batch_opts *opts);
 
 /* Fits n_inst pseudo-experiments of possibly different models in one persistent launch:
  * one block per instance at a time, per-instance L-BFGS state on the device, the whole
- * expectation / -2lnL / adjoint evaluated inside the block (Sec. 6: minimiser loop around the
+ * expectation / -2lnL / adjoint evaluated inside the block ([S]: minimiser loop around the
  * likelihood; many fits in parallel as in the paper's ensemble studies).
  * models: host [n_models]; inst: host [n_inst];
  * data: host or device floats, instance i reads data + inst[i].data_off (n_data of its model);

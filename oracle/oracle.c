@@ -5,17 +5,20 @@
  * checked against. Only the test-suite, the smoke check and the benchmark's CPU-baseline leg
  * may load it; the library never calls it and shares no code with it.
  *
+ * Citations: [S] = section "Structure of the framework" of the paper, [L] = section
+ * "Likelihood implementation for Double Chooz within the framework".
+ *
  * What it computes (all in double precision, written loop by loop):
  *
  *   per dataset d, true bin k (centre E_k), core c with baseline L_dc:
  *     Ptot_dk = sum_c p_c w_dc P(L_dc, E_k; eta)                 survival, Eq. 1 / Eq. 2
  *                                                                 (or exact 3-flavour vacuum,
  *                                                                  the quantity Eq. 10 expands)
- *     u_dk    = t_dk * n_d * s_(g(k)) * Ptot_dk                   flux x xsec x reweights (Sec. 6)
+ *     u_dk    = t_dk * n_d * s_(g(k)) * Ptot_dk                   flux x xsec x reweights [S]
  *     v_d     = M(a_d) u_d   energy correction E' = a0 + a1 E + a2 E^2, each true bin's content
- *                            spread over the original binning by overlap length (Sec. 6)
- *     f_dj    = eps_d sum_k R_d[j,k] v_dk                         fold into reco bins (Sec. 6)
- *     mu_dj   = f_dj + sum_b r_b B_bj (1 + delta_bj)              backgrounds (Sec. 5, Eq. 9)
+ *                            spread over the original binning by overlap length [S]
+ *     f_dj    = eps_d sum_k R_d[j,k] v_dk                         fold into reco bins [S]
+ *     mu_dj   = f_dj + sum_b r_b B_bj (1 + delta_bj)              backgrounds [L], Eq. 9
  *   -2lnL     = sum_d sum_j 2 [mu - n + n ln(n/mu)]               Poisson, Eq. 3-5, normalised
  *                                                                 to the saturated model, Eq. 8
  *             + sum_i ((theta_i - theta0_i)/sigma_i)^2            Gaussian priors, Eq. 6
@@ -23,8 +26,8 @@
  *
  * plus the analytic gradient of -2lnL with respect to every parameter, and a dense BFGS
  * minimiser with a strong-Wolfe line search that stops when the estimated distance to the
- * minimum, EDM = 1/2 g^T H g, falls below a threshold (Sec. 6, the variable-metric method
- * with EDM stop). As in Sec. 6 ("transformation layer") the minimiser works in coordinates
+ * minimum, EDM = 1/2 g^T H g, falls below a threshold ([S], the variable-metric method
+ * with EDM stop). As in [S] ("transformation layer") the minimiser works in coordinates
  * z in which the prior is uncorrelated: theta_B = theta0_B + L_B z_B with V_B = L_B L_B^T,
  * theta_i = theta0_i + sigma_i z_i otherwise (sigma_i = the parameter's step scale).
  */
@@ -233,7 +236,7 @@ double orc_survival(int mode, const double *p, double L, double E, double *dP)
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Energy correction: quadratic map re-integrated over the original binning (Sec. 6)      */
+/* Energy correction: quadratic map re-integrated over the original binning [S]           */
 /* ------------------------------------------------------------------------------------ */
 /* Source bin k = [E_k, E_k+1] is mapped to [y0, y1] = [E'(E_k), E'(E_k+1)] and its content is
  * shared among target bins m = [T_m, T_m+1] in proportion to the overlap length
@@ -521,7 +524,7 @@ double orc_nll(const orc_handle *h, const double *theta, const double *data, uin
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Transformation layer: theta(z) and the chain rule (Sec. 6)                             */
+/* Transformation layer: theta(z) and the chain rule [S]                                  */
 /* ------------------------------------------------------------------------------------ */
 static void theta_of_z(const orc_handle *h, const double *z, double *theta)
 {

@@ -10,11 +10,13 @@ of the method.
 
 The three geometries follow the paper's two case studies:
 
-* ``c0`` - one detector, one reactor at 1050 m (the Double Chooz far detector, Sec. 2).
+* ``c0`` - one detector, one reactor at 1050 m (the Double Chooz far detector, section "Experimental context").
 * ``c1`` - the Double Chooz three-dataset layout FD-I, FD-II, ND with two cores, 38 reco bins
-  per dataset (Sec. 4, Eq. 9) and the nuisance families listed in Sec. 5 (flux/shape bins,
+  per dataset (Eq. 9) and the nuisance families listed in section "Likelihood
+  implementation for Double Chooz within the framework" (flux/shape bins,
   Li-9, accidental and fast-neutron backgrounds, quadratic energy response, efficiencies).
-* ``c2`` - the medium-baseline (JUNO-like) study of Sec. 7.3: a far detector 52-53.5 km from
+* ``c2`` - the medium-baseline (JUNO-like) study of section "Application to medium
+  baseline reactor measurements": a far detector 52-53.5 km from
   ten cores, a near detector at the Double Chooz near baseline, 3 %/sqrt(E) resolution.
 
 Every number the paper does not fix (bin counts, templates, prior widths, event counts) is a
