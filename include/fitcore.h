@@ -202,6 +202,29 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
               const float *data, const double *start, double *best, fit_result *results,
               const fit_batch_opts *opts, void *stream);
 
+/* Batched -2lnL and gradient, as fit_model_eval, for callers that cannot allocate device
+ * memory: a host application that owns a fixed device-memory budget and hands out every
+ * buffer itself, a plugin running under another framework's allocator that forbids direct
+ * cudaMalloc / cudaFree, or a latency-critical loop that must not call into the allocator.
+ * The paper has no counterpart; this is a deployment variant of the same evaluation.
+ *  - Allocates nothing: it calls no cudaMalloc / cudaFree / allocating library routine. Its
+ *    per-block workspace is a 16 MiB array in this library's device memory, which every GPU
+ *    that loads the library holds until the process exits.
+ *  - theta, data, masks, nll_out, grad_out, status_out must all be device memory (host
+ *    buffers are rejected with FIT_ERR_INVALID_ARG, since staging them would allocate).
+ *    data and masks may be NULL with the meaning they have in fit_model_eval, whose outputs
+ *    and semantics this call shares.
+ *  - A model whose per-block workspace exceeds the 16 MiB is rejected (FIT_ERR_INVALID_ARG);
+ *    larger batches are processed by fewer resident blocks, never by a larger workspace.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *    with that device current); make that first call before any stream capture.
+ *  - Every call shares the one array and leaves its last contents in it: calls whose
+ *    executions overlap on the GPU (on different streams, or from different threads) race
+ *    on it and must be serialised by the caller. Asynchronous on `stream`. */
+int fit_model_eval_noalloc(fit_model *model, int B, const double *theta, const float *data,
+                           const uint32_t *masks, double *nll_out, float *grad_out,
+                           int *status_out, void *stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char *fit_last_error(void);
 

@@ -161,6 +161,15 @@ struct fit_model {
     int n_params = 0, n_data = 0, n_ds = 0, n_true = 0;
 };
 
+// hooks for noalloc.cu (same library)
+int fitcore_noalloc_fail(int code, const std::string &msg) { return fail(code, msg); }
+int fitcore_model_device(fit_model *model, const DevModel **dev, const DevModel **host) {
+    *dev = model->dev;
+    *host = &model->host;
+    return FIT_OK;
+}
+void fitcore_count_launch() { g_launches++; }
+
 extern "C" {
 
 const char *fit_last_error(void) { return g_err.c_str(); }

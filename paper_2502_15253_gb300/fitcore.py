@@ -77,8 +77,8 @@ STATUS = {0: "converged", 1: "maxiter", 2: "linesearch_fail", 3: "nonfinite",
           4: "mu_nonpositive", 5: "escale_nonmonotone", 6: "timeout"}
 
 EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model_expected",
-           "fit_model_eval", "fit_batch_default_opts", "fit_batch", "fit_last_error",
-           "fit_kernel_launches")
+           "fit_model_eval", "fit_model_eval_noalloc", "fit_batch_default_opts", "fit_batch",
+           "fit_last_error", "fit_kernel_launches")
 
 
 def lib_path() -> str:
@@ -101,13 +101,14 @@ def load(build_if_missing: bool = False):
     L.fit_model_info.argtypes = [vp, C.POINTER(fit_model_info_t)]
     L.fit_model_expected.argtypes = [vp, C.c_int, vp, vp, vp, vp]
     L.fit_model_eval.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
+    L.fit_model_eval_noalloc.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
     L.fit_batch_default_opts.argtypes = [C.POINTER(fit_batch_opts)]
     L.fit_batch.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_int, vp, vp, vp, vp,
                             C.POINTER(fit_batch_opts), vp]
     L.fit_last_error.restype = C.c_char_p
     L.fit_kernel_launches.restype = C.c_int64
     for f in ("fit_model_create", "fit_model_info", "fit_model_expected", "fit_model_eval",
-              "fit_batch"):
+              "fit_model_eval_noalloc", "fit_batch"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -237,6 +238,15 @@ def fit_model_eval(model: Model, B: int, theta, data, masks, nll_out, grad_out=N
                                  _ptr(nll_out), _ptr(grad_out), _ptr(status_out),
                                  _stream_ptr(stream)),
            "fit_model_eval")
+
+
+def fit_model_eval_noalloc(model: Model, B: int, theta, data, masks, nll_out, grad_out=None,
+                           status_out=None, stream=None):
+    """fit_model_eval without any device allocation (all buffers must be device memory)."""
+    _check(load().fit_model_eval_noalloc(model.handle, int(B), _ptr(theta), _ptr(data),
+                                         _ptr(masks), _ptr(nll_out), _ptr(grad_out),
+                                         _ptr(status_out), _stream_ptr(stream)),
+           "fit_model_eval_noalloc")
 
 
 def fit_batch_default_opts() -> fit_batch_opts:
