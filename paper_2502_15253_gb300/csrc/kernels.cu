@@ -148,10 +148,21 @@ size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem) {
 // ------------------------------------------------------------------------------------
 // persistent batched L-BFGS
 // ------------------------------------------------------------------------------------
+constexpr int kMaxHist = 16;
+constexpr int kNDots = 4 * kMaxHist + 1;
+
 struct FitSmem {
     DevModel m;
     double red[kMaxWarps * 24 + 24];
-    double rho[16], alf[16];
+    // L-BFGS history in scalars: SY[i][j] = s_i.y_j (needed for i older than j and i = j),
+    // YY[i][j] = y_i.y_j (symmetric), rho_i = 1 / s_i.y_i, by history slot
+    double SY[kMaxHist][kMaxHist], YY[kMaxHist][kMaxHist];
+    double rho[kMaxHist], alf[kMaxHist], bet[kMaxHist];
+    double dots[kNDots];       // fused pass: S.y_new | Y.y_new | S.g | Y.g | g.g
+    float cs[kMaxHist], cy[kMaxHist];   // d = -(cg g + sum cs_j s_j + sum cy_j y_j)
+    float cg;
+    double gHg, gamma;
+    int hn, head, occ;
     int status;
     int inst;
 };
@@ -188,10 +199,128 @@ __device__ __forceinline__ double bdot(const float *a, const float *b, int n, do
     return out[0];
 }
 
-// theta from z (transformation layer): pd = J z, pv = theta0 + pd
+// One pass of block-wide dot products, a warp per product (lanes stride the P entries, a
+// shuffle tree adds them). Products q < 4 kMaxHist: type q / kMaxHist (0: s_j.y_new,
+// 1: y_j.y_new, 2: s_j.g, 3: y_j.g) for the history slots set in `occ`; q = 4 kMaxHist: g.g.
+// The results land in S.dots; ends with a barrier.
+__device__ void fused_dots(const float *Sv, const float *Yv, const float *ynew, const float *g, int P,
+                           unsigned occ, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = warp; q < kNDots; q += nw) {
+        const float *a, *b;
+        if (q == kNDots - 1) {
+            a = g;
+            b = g;
+        } else {
+            const int type = q / kMaxHist, slot = q % kMaxHist;
+            if (!((occ >> slot) & 1u) || (type < 2 && ynew == nullptr)) continue;
+            a = ((type & 1) ? Yv : Sv) + (int64_t)slot * P;
+            b = (type < 2) ? ynew : g;
+        }
+        float acc = 0.f;
+        for (int i = lane; i < P; i += 32) acc = fmaf(a[i], b[i], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[q] = (double)acc;
+    }
+    __syncthreads();
+}
+
+// Warp 0: folds the pending curvature pair (slot S.head, if `pending`) into the scalar
+// history and runs the L-BFGS two-loop recursion on scalars. Every inner product the
+// recursion needs is one of s_i.g, y_i.g, s_i.y_j (i older than j) or y_i.y_j, so the
+// direction is d = -(cg g + sum_j cs_j s_j + sum_j cy_j y_j) with coefficients from the
+// recurrence, and g^T H g follows from the same scalars. Lane k holds chronological history
+// position k; both triangular recurrences run column by column (one shuffle per step).
+__device__ void lbfgs_scalars(FitSmem &S, int hist_max, bool pending) {
+    const int lane = threadIdx.x & 31;
+    const double *dt = S.dots;
+    if (pending && lane == 0) {
+        const int c = S.head;
+        const double sy = dt[c], yy = dt[kMaxHist + c];
+        if (sy > 1e-10 * yy && yy > 0.0) {
+            for (int j = 0; j < hist_max; ++j)
+                if (((S.occ >> j) & 1) && j != c) {
+                    S.SY[j][c] = dt[j];
+                    S.YY[j][c] = S.YY[c][j] = dt[kMaxHist + j];
+                }
+            S.SY[c][c] = sy;
+            S.YY[c][c] = yy;
+            S.rho[c] = 1.0 / sy;
+            S.occ |= 1u << c;
+            S.head = (c + 1) % hist_max;
+            S.hn = min(S.hn + 1, hist_max);
+            S.gamma = sy / yy;
+        } else if ((S.occ >> c) & 1) {
+            // rejected pair written over the oldest one: that pair is gone as well
+            S.occ &= ~(1u << c);
+            S.hn -= 1;
+        }
+    }
+    __syncwarp();
+    const int hn = S.hn, oldest = (S.head - hn + hist_max) % hist_max;
+    const double gam = S.gamma, gg = dt[kNDots - 1];
+    const bool live = lane < hn;
+    const int sl = live ? (oldest + lane) % hist_max : 0;    // this lane's history slot
+    const double sg = live ? dt[2 * kMaxHist + sl] : 0.0, yg = live ? dt[3 * kMaxHist + sl] : 0.0;
+    const double rho = live ? S.rho[sl] : 0.0;
+    // alpha_k = rho_k (s_k.g - sum_{l > k} alpha_l s_k.y_l), newest first
+    double acc = sg, alpha = 0.0;
+    for (int l = hn - 1; l >= 0; --l) {
+        const double al = __shfl_sync(0xffffffffu, rho * acc, l);
+        if (lane == l) alpha = al;
+        const int sll = (oldest + l) % hist_max;
+        if (lane < l) acc -= al * S.SY[sl][sll];
+    }
+    // u_k = sum_l alpha_l y_k.y_l
+    double u = 0.0;
+    for (int l = 0; l < hn; ++l) {
+        const double al = __shfl_sync(0xffffffffu, alpha, l);
+        if (live) u += al * S.YY[sl][(oldest + l) % hist_max];
+    }
+    // beta_k = rho_k (gam (y_k.g - u_k) + sum_{l < k} (alpha_l - beta_l) s_l.y_k), oldest first
+    double acc2 = gam * (yg - u), beta = 0.0;
+    for (int l = 0; l < hn; ++l) {
+        const double bl = __shfl_sync(0xffffffffu, rho * acc2, l);
+        const double cl = __shfl_sync(0xffffffffu, alpha, l) - bl;
+        if (lane == l) beta = bl;
+        if (live && lane > l) acc2 += cl * S.SY[(oldest + l) % hist_max][sl];
+    }
+    const double cs = alpha - beta, cy = -gam * alpha;
+    double part = live ? cs * sg + cy * yg : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    double ghg = gam * gg + part;
+    if (lane < kMaxHist) {
+        S.cs[lane] = 0.f;
+        S.cy[lane] = 0.f;
+    }
+    __syncwarp();
+    if (live) {
+        S.cs[sl] = (float)cs;
+        S.cy[sl] = (float)cy;
+    }
+    if (lane == 0) S.cg = (float)gam;
+    __syncwarp();
+    if (!(ghg > 0.0)) {   // not a descent direction: drop the history, steepest descent
+        if (lane < kMaxHist) S.cs[lane] = S.cy[lane] = 0.f;
+        if (lane == 0) {
+            S.hn = 0;
+            S.occ = 0;
+            S.head = 0;
+            S.gamma = 1.0;
+            S.cg = 1.f;
+        }
+        ghg = gg;
+    }
+    if (lane == 0) S.gHg = ghg;
+}
+
+// theta from z (transformation layer): pd = J z, pv = theta0 + pd. In a prior block the
+// rows of L z are formed a thread per row over the stored L^T, so each step is a coalesced
+// load plus a shared-memory broadcast of z, and the loop keeps many loads in flight.
 __device__ void theta_of_z(const DevModel &m, const float *z, float *pv, float *pd) {
-    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5,
-              nw = nth >> 5;
+    const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < m.P; i += nth) {
         const float s = m.zscale[i];
         if (s > 0.f) pd[i] = s * z[i];
@@ -199,13 +328,16 @@ __device__ void theta_of_z(const DevModel &m, const float *z, float *pv, float *
     for (int b = 0; b < m.n_blocks; ++b) {
         const int n = m.blk_size[b];
         const int *idx = m.blk_idx + m.blk_idx_off[b];
-        const float *L = m.blk_L + m.blk_mat_off[b];
-        for (int i = warp; i < n; i += nw) {
-            float s = 0.f;
-            for (int j = lane; j <= i; j += 32) s = fmaf(L[(int64_t)i * n + j], z[idx[j]], s);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) pd[idx[i]] = s;
+        const float *Lt = m.blk_L + m.blk_mat_off[b] + (int64_t)n * n;   // L^T, row-major
+        for (int i = tid; i < n; i += nth) {
+            float s0 = 0.f, s1 = 0.f;
+            int j = 0;
+            for (; j + 1 <= i; j += 2) {
+                s0 = fmaf(Lt[(int64_t)j * n + i], z[idx[j]], s0);
+                s1 = fmaf(Lt[(int64_t)(j + 1) * n + i], z[idx[j + 1]], s1);
+            }
+            if (j <= i) s0 = fmaf(Lt[(int64_t)j * n + i], z[idx[j]], s0);
+            pd[idx[i]] = s0 + s1;
         }
     }
     __syncthreads();
@@ -228,8 +360,7 @@ __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &
         if (S.status) return INFINITY;
     }
     // prior = |z|^2 over constrained coordinates; gz = J^T gth + 2 z
-    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5,
-              nw = nth >> 5;
+    const int tid = threadIdx.x, nth = blockDim.x;
     float acc[1] = {0.f};
     for (int i = tid; i < m.P; i += nth) {
         const float s = m.zscale[i];
@@ -242,17 +373,18 @@ __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &
     for (int b = 0; b < m.n_blocks; ++b) {
         const int n = m.blk_size[b];
         const int *idx = m.blk_idx + m.blk_idx_off[b];
-        const float *Lt = m.blk_L + m.blk_mat_off[b] + (int64_t)n * n;   // L^T, row-major
-        for (int j = warp; j < n; j += nw) {
-            float s = 0.f;
-            for (int i = j + lane; i < n; i += 32) s = fmaf(Lt[(int64_t)j * n + i], V.gth[idx[i]], s);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) {
-                const float zj = z[idx[j]];
-                gz[idx[j]] = s + 2.f * zj;
-                acc[0] = fmaf(zj, zj, acc[0]);
+        const float *L = m.blk_L + m.blk_mat_off[b];   // L, row-major: (L^T g)_j = sum_i L_ij g_i
+        for (int j = tid; j < n; j += nth) {
+            float s0 = 0.f, s1 = 0.f;
+            int i = j;
+            for (; i + 1 < n; i += 2) {
+                s0 = fmaf(L[(int64_t)i * n + j], V.gth[idx[i]], s0);
+                s1 = fmaf(L[(int64_t)(i + 1) * n + j], V.gth[idx[i + 1]], s1);
             }
+            if (i < n) s0 = fmaf(L[(int64_t)i * n + j], V.gth[idx[i]], s0);
+            const float zj = z[idx[j]];
+            gz[idx[j]] = (s0 + s1) + 2.f * zj;
+            acc[0] = fmaf(zj, zj, acc[0]);
         }
     }
     double tot[1];
@@ -356,50 +488,41 @@ __global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
             double f = eval_z(m, V.z, V.g, V, ws, data, in.mask, S);
             res.n_evals = 1;
             if (!isfinite(f)) status = FIT_STATUS_NONFINITE;
-            int hn = 0, head = 0;   // history size and next slot
-            double gamma = 1.0;
-            // After the first EDM convergence the history is dropped and rebuilt (at least
-            // hist_max iterations) up to A.restarts times: the fresh pairs come from the
-            // directions still moving, which are the flat ones a short history had not seen,
-            // and where its EDM estimate was too small.
+            if (tid == 0) {
+                S.hn = 0;
+                S.head = 0;
+                S.occ = 0;
+                S.gamma = 1.0;
+            }
+            // After the first EDM convergence the history can be dropped and rebuilt (at
+            // least hist_max iterations) up to A.restarts times: the fresh pairs come from the
+            // directions still moving, the flat ones a short history may not have seen.
             int restarts_left = A.restarts, since_restart = hist_max;
+            bool pending = false;
             while (status == FIT_STATUS_MAXITER) {
-                // ---- direction d = -H g, two-loop recursion ------------------------------
-                vcopy(V.d, V.g, P);
+                // ---- direction d = -H g: fused dot products, scalar two-loop, one combination
                 __syncthreads();
-                for (int q = 0; q < hn; ++q) {
-                    const int slot = (head - 1 - q + hist_max) % hist_max;
-                    const float *s = V.S + (int64_t)slot * P, *y = V.Y + (int64_t)slot * P;
-                    const double a = S.rho[slot] * bdot(s, V.d, P, S.red);
-                    if (tid == 0) S.alf[slot] = a;
-                    const float af = (float)a;
-                    for (int i = tid; i < P; i += blockDim.x) V.d[i] = fmaf(-af, y[i], V.d[i]);
-                    __syncthreads();
-                }
+                fused_dots(V.S, V.Y, pending ? V.Y + (int64_t)S.head * P : nullptr, V.g, P,
+                           (unsigned)S.occ | (pending ? 1u << S.head : 0u), S.dots);
+                if (tid < 32) lbfgs_scalars(S, hist_max, pending);
+                pending = false;
+                __syncthreads();
                 {
-                    const float gf = (float)gamma;
-                    for (int i = tid; i < P; i += blockDim.x) V.d[i] *= gf;
-                    __syncthreads();
+                    const float cg = S.cg;
+                    const unsigned occ = (unsigned)S.occ;
+                    for (int i = tid; i < P; i += blockDim.x) {
+                        float h = cg * V.g[i];
+                        for (int j = 0; j < hist_max; ++j)
+                            if ((occ >> j) & 1u) {
+                                h = fmaf(S.cs[j], V.S[(int64_t)j * P + i], h);
+                                h = fmaf(S.cy[j], V.Y[(int64_t)j * P + i], h);
+                            }
+                        V.d[i] = -h;
+                    }
                 }
-                for (int q = hn - 1; q >= 0; --q) {
-                    const int slot = (head - 1 - q + hist_max) % hist_max;
-                    const float *s = V.S + (int64_t)slot * P, *y = V.Y + (int64_t)slot * P;
-                    const double bta = S.rho[slot] * bdot(y, V.d, P, S.red);
-                    const float cf = (float)(S.alf[slot] - bta);
-                    for (int i = tid; i < P; i += blockDim.x) V.d[i] = fmaf(cf, s[i], V.d[i]);
-                    __syncthreads();
-                }
-                for (int i = tid; i < P; i += blockDim.x) V.d[i] = -V.d[i];
                 __syncthreads();
-                double gd = bdot(V.g, V.d, P, S.red);
-                if (!(gd < 0.0)) {   // not a descent direction: drop the history
-                    hn = 0;
-                    head = 0;
-                    gamma = 1.0;
-                    for (int i = tid; i < P; i += blockDim.x) V.d[i] = -V.g[i];
-                    __syncthreads();
-                    gd = -bdot(V.g, V.g, P, S.red);
-                }
+                const double gd = -S.gHg;
+                const int hn = S.hn;
                 const double edm = -0.5 * gd;
                 res.edm = edm;
                 if (edm < A.edm_tol && since_restart >= hist_max) {
@@ -409,8 +532,12 @@ __global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
                     }
                     --restarts_left;
                     since_restart = 0;
-                    hn = 0;
-                    head = 0;
+                    __syncthreads();
+                    if (tid == 0) {
+                        S.hn = 0;
+                        S.head = 0;
+                        S.occ = 0;
+                    }
                     continue;
                 }
                 if (res.iters >= A.max_iter) break;
@@ -423,8 +550,8 @@ __global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
                 const double dphi0 = gd;
                 const double eps_f = A.f_noise_rel * (1.0 + fabs(f));
                 double alpha;
-                if (hn == 0) {
-                    const double dn = sqrt(bdot(V.d, V.d, P, S.red));
+                if (hn == 0) {   // |d| = cg |g| with the history empty
+                    const double dn = (double)S.cg * sqrt(S.dots[kNDots - 1]);
                     alpha = fmin(1.0, 1.0 / fmax(dn, 1e-30));
                 } else {
                     alpha = 1.0;
@@ -489,32 +616,30 @@ __global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
                 }
                 if (!accepted) {
                     if (hn > 0) {   // retry from steepest descent
-                        hn = 0;
-                        head = 0;
-                        gamma = 1.0;
+                        __syncthreads();
+                        if (tid == 0) {
+                            S.hn = 0;
+                            S.head = 0;
+                            S.occ = 0;
+                            S.gamma = 1.0;
+                        }
                         continue;
                     }
                     status = FIT_STATUS_LINESEARCH_FAIL;
                     break;
                 }
-                // ---- curvature pair -------------------------------------------------------
-                float *s_new = V.S + (int64_t)head * P, *y_new = V.Y + (int64_t)head * P;
-                for (int i = tid; i < P; i += blockDim.x) {
-                    s_new[i] = V.zt[i] - V.z[i];
-                    y_new[i] = V.gt[i] - V.g[i];
+                // ---- curvature pair into the next slot; folded in by the next fused pass ---
+                {
+                    const int c = S.head;
+                    float *s_new = V.S + (int64_t)c * P, *y_new = V.Y + (int64_t)c * P;
+                    for (int i = tid; i < P; i += blockDim.x) {
+                        s_new[i] = V.zt[i] - V.z[i];
+                        y_new[i] = V.gt[i] - V.g[i];
+                        V.z[i] = V.zt[i];
+                        V.g[i] = V.gt[i];
+                    }
+                    pending = true;
                 }
-                __syncthreads();
-                const double sy = bdot(s_new, y_new, P, S.red);
-                const double yy = bdot(y_new, y_new, P, S.red);
-                if (sy > 1e-10 * yy && yy > 0.0) {
-                    if (tid == 0) S.rho[head] = 1.0 / sy;
-                    head = (head + 1) % hist_max;
-                    hn = min(hn + 1, hist_max);
-                    gamma = sy / yy;
-                }
-                vcopy(V.z, V.zt, P);
-                vcopy(V.g, V.gt, P);
-                __syncthreads();
                 f = fa;
                 res.iters++;
                 since_restart++;
