@@ -225,6 +225,20 @@ int fit_model_eval_noalloc(fit_model *model, int B, const double *theta, const f
                            const uint32_t *masks, double *nll_out, float *grad_out,
                            int *status_out, void *stream);
 
+/* Tensor-core GEMM of the library (tcgen05 on sm_103a), used by the warm-start MLP and the
+ * batched response fold, exposed for callers and tests. D = A B^T with A [M x K] and
+ * B [N x K] row-major; tf32 = 0: bf16 operands (kind::f16), tf32 = 1: float operands read as
+ * TF32 (kind::tf32); FP32 accumulation. All pointers device memory; rows 16-byte aligned
+ * (lda, ldb multiples of 8 for bf16, of 4 for float). Epilogue `epi`:
+ *   0: C = D;  1: C = D + bias[n];  2: C = D + bias[n] and Y = gelu(C) (bf16, exact erf GELU);
+ *   3: Y = D * gelu'(aux[m][n]) (bf16);  4: C += D.
+ * Asynchronous on `stream`. fit_tc_gemm_status() synchronises and returns (and clears) a
+ * nonzero flag if a pipeline wait inside the kernel gave up (bounded waits, no hang). */
+int fit_tc_gemm(int tf32, int M, int N, int K, const void *A, int lda, const void *B, int ldb, int epi,
+                float *C, int ldc, void *Y, int ldy, const float *bias, const float *aux, int ldaux,
+                void *stream);
+int fit_tc_gemm_status(void);
+
 /* Message of the last error on this thread ("" if none). */
 const char *fit_last_error(void);
 

@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "gemm_tc.cuh"
 #include "kernels.cuh"
 
 using fitcore::DevModel;
@@ -160,6 +161,9 @@ struct fit_model {
     size_t bytes = 0;
     int n_params = 0, n_data = 0, n_ds = 0, n_true = 0;
 };
+
+// error / launch-count hooks for the other translation units of the library
+int fitcore_fail(int code, const std::string &msg) { return fail(code, msg); }
 
 // hooks for noalloc.cu (same library)
 int fitcore_noalloc_fail(int code, const std::string &msg) { return fail(code, msg); }
@@ -668,6 +672,27 @@ int fit_model_eval(fit_model *model, int B, const double *theta, const float *da
         rc = fail(FIT_ERR_CUDA, "fit_model_eval: synchronise");
     return rc;
 }
+
+int fit_tc_gemm(int tf32, int M, int N, int K, const void *A, int lda, const void *B, int ldb, int epi, float *C,
+                int ldc, void *Y, int ldy, const float *bias, const float *aux, int ldaux, void *stream) {
+    fitcore::GemmOut o;
+    o.epi = epi;
+    o.C = C;
+    o.ldc = ldc;
+    o.Y = static_cast<__nv_bfloat16 *>(Y);
+    o.ldy = ldy;
+    o.bias = bias;
+    o.aux = aux;
+    o.ldaux = ldaux;
+    if (epi < fitcore::EPI_F32 || epi > fitcore::EPI_F32_ADD) return fail(FIT_ERR_INVALID_ARG, "fit_tc_gemm: epilogue");
+    const bool needC = epi != fitcore::EPI_DGELU, needY = epi == fitcore::EPI_BIAS_GELU || epi == fitcore::EPI_DGELU;
+    if ((needC && !C) || (needY && !Y) || ((epi == fitcore::EPI_BIAS_F32 || epi == fitcore::EPI_BIAS_GELU) && !bias) ||
+        (epi == fitcore::EPI_DGELU && !aux))
+        return fail(FIT_ERR_INVALID_ARG, "fit_tc_gemm: missing output for the epilogue");
+    return fitcore::tc_gemm(tf32 != 0, M, N, K, A, lda, B, ldb, o, (cudaStream_t)stream, nullptr);
+}
+
+int fit_tc_gemm_status(void) { return fitcore::tc_gemm_take_error(); }
 
 void fit_batch_default_opts(fit_batch_opts *o) {
     if (!o) return;

@@ -78,7 +78,7 @@ STATUS = {0: "converged", 1: "maxiter", 2: "linesearch_fail", 3: "nonfinite",
 
 EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model_expected",
            "fit_model_eval", "fit_model_eval_noalloc", "fit_batch_default_opts", "fit_batch",
-           "fit_last_error", "fit_kernel_launches")
+           "fit_tc_gemm", "fit_tc_gemm_status", "fit_last_error", "fit_kernel_launches")
 
 
 def lib_path() -> str:
@@ -103,6 +103,10 @@ def load(build_if_missing: bool = False):
     L.fit_model_eval.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
     L.fit_model_eval_noalloc.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, vp]
     L.fit_batch_default_opts.argtypes = [C.POINTER(fit_batch_opts)]
+    L.fit_tc_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, C.c_int,
+                              vp, C.c_int, vp, C.c_int, vp, vp, C.c_int, vp]
+    L.fit_tc_gemm.restype = C.c_int
+    L.fit_tc_gemm_status.restype = C.c_int
     L.fit_batch.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_int, vp, vp, vp, vp,
                             C.POINTER(fit_batch_opts), vp]
     L.fit_last_error.restype = C.c_char_p
@@ -265,6 +269,18 @@ def fit_batch(models, inst, data, start, best, results, opts=None, stream=None):
     _check(L.fit_batch(hs, len(models), inst.ctypes.data, len(inst), _ptr(data), _ptr(start),
                        _ptr(best), _ptr(results), C.byref(o), _stream_ptr(stream)),
            "fit_batch")
+
+
+def fit_tc_gemm(tf32, M, N, K, A, lda, B, ldb, epi, C=None, ldc=0, Y=None, ldy=0, bias=None,
+                aux=None, ldaux=0, stream=None):
+    """Tensor-core GEMM D = A B^T with a fused epilogue (device buffers)."""
+    _check(load().fit_tc_gemm(int(tf32), int(M), int(N), int(K), _ptr(A), int(lda), _ptr(B), int(ldb),
+                              int(epi), _ptr(C), int(ldc), _ptr(Y), int(ldy), _ptr(bias), _ptr(aux),
+                              int(ldaux), _stream_ptr(stream)), "fit_tc_gemm")
+
+
+def fit_tc_gemm_status() -> int:
+    return int(load().fit_tc_gemm_status())
 
 
 def fit_kernel_launches() -> int:

@@ -1,0 +1,63 @@
+"""The tcgen05 tensor-core GEMM against a float64 matrix product of the same operands.
+
+bf16 operands are exact in float64, so the only error is the FP32 accumulation (relative
+~K * 2^-24 of the sum of |terms|). TF32 reads the top 19 bits of each float (the hardware
+ignores the rest), so the reference rounds the operands the same way; the remaining error is
+again the FP32 accumulation. Shapes cover one tile, ragged M/N/K tails and multi-tile grids.
+"""
+import numpy as np
+import pytest
+
+from paper_2502_15253_gb300 import fitcore
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def tf32_trunc(x):
+    return (x.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def run(tf32, M, N, K, epi=0, seed=0):
+    rng = np.random.default_rng(seed)
+    lda = ((K + 7) // 8) * 8
+    A = rng.standard_normal((M, lda)).astype(np.float32)
+    B = rng.standard_normal((N, lda)).astype(np.float32)
+    dev = torch.device("cuda")
+    if tf32:
+        Ad, Bd = torch.tensor(A, device=dev), torch.tensor(B, device=dev)
+        Aref, Bref = tf32_trunc(A[:, :K]), tf32_trunc(B[:, :K])
+    else:
+        Ad = torch.tensor(A, device=dev).to(torch.bfloat16)
+        Bd = torch.tensor(B, device=dev).to(torch.bfloat16)
+        Aref = Ad.float().cpu().numpy()[:, :K]
+        Bref = Bd.float().cpu().numpy()[:, :K]
+    ref = Aref.astype(np.float64) @ Bref.astype(np.float64).T
+    absref = np.abs(Aref.astype(np.float64)) @ np.abs(Bref.astype(np.float64)).T
+    C = torch.full((M, N), np.nan, dtype=torch.float32, device=dev)
+    bias = torch.tensor(rng.standard_normal(N).astype(np.float32), device=dev)
+    if epi == 0:
+        fitcore.fit_tc_gemm(tf32, M, N, K, Ad, lda, Bd, lda, 0, C=C, ldc=N)
+    else:
+        fitcore.fit_tc_gemm(tf32, M, N, K, Ad, lda, Bd, lda, 1, C=C, ldc=N, bias=bias)
+        ref = ref + bias.cpu().numpy()[None, :]
+    torch.cuda.synchronize()
+    assert fitcore.fit_tc_gemm_status() == 0
+    got = C.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref) / (absref + 1e-30)
+    return err.max()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (128, 256, 128), (300, 208, 438), (37, 12, 512),
+                                   (1024, 512, 448), (129, 400, 200)])
+def test_bf16_gemm(M, N, K):
+    assert run(False, M, N, K) <= 4e-6 * np.sqrt(K / 64)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 48, 400), (256, 400, 2000), (77, 38, 400), (512, 16, 32)])
+def test_tf32_gemm(M, N, K):
+    assert run(True, M, N, K) <= 4e-6 * np.sqrt(K / 32)
+
+
+def test_bias_epilogue():
+    assert run(False, 200, 120, 96, epi=1) <= 1e-5
