@@ -239,6 +239,54 @@ int fit_tc_gemm(int tf32, int M, int N, int K, const void *A, int lda, const voi
                 void *stream);
 int fit_tc_gemm_status(void);
 
+/* Expected counts for B parameter vectors with the response fold on tensor cores (Eq. 9
+ * expectation as fit_model_expected): the energy-corrected true spectra of all instances form
+ * V_d [B x N_t] per dataset and F_d = V_d R_d^T is one tcgen05 GEMM (the dense contraction of
+ * the path: one response matrix times many spectra). precision 0: TF32 operands (about 3e-4
+ * relative per product; used to generate training spectra); precision 1: split 3xTF32,
+ * x = x_hi + x_lo with x_hi exact in TF32, F = Vh Rh^T + Vh Rl^T + Vl Rh^T (FP32-level).
+ * theta: host or device [B x P] double; mu_out: host or device [B x n_data] float (NaN rows
+ * where the energy map is invalid); status_out: host or device [B] int or NULL. */
+int fit_model_expected_tc(fit_model *model, int B, const double *theta, float *mu_out,
+                          int *status_out, int precision, void *stream);
+
+/* Poisson pseudo-data: out[i] ~ Poisson(mu[i]) as floats, i < n. Philox4x32-10 counters
+ * (i + offset, draw, 0, 0) under key = seed, so results do not depend on the launch shape;
+ * Knuth's multiplication method below mu = 10, Hormann's PTRS above. Domain 0 <= mu < 2^22;
+ * mu = 0 gives 0, negative, non-finite or larger mu give NaN. mu, out: host or device. */
+int fit_poisson_sample(int64_t n, const float *mu, uint64_t seed, uint64_t offset, float *out,
+                       void *stream);
+
+/* Warm-start network (not in the paper): an MLP n_in -> n_hidden (GELU) x n_hidden_layers ->
+ * n_out with bf16 weights / activations, FP32 master weights and accumulation, every product
+ * on the tensor-core GEMM, trained with AdamW on an MSE loss. */
+typedef struct fit_mlp fit_mlp;
+int fit_mlp_create(int n_in, int n_hidden, int n_hidden_layers, int n_out, uint64_t seed,
+                   fit_mlp **out);
+void fit_mlp_destroy(fit_mlp *mlp);
+/* y = mlp(x): x device [B x n_in] float, y host or device [B x n_out] float. */
+int fit_mlp_forward(fit_mlp *mlp, int B, const float *x, float *y, void *stream);
+/* One AdamW step on the mean squared error against target (device [B x n_out]); x device
+ * [B x n_in]; loss_out (host or device double, or NULL) receives the batch loss before the step. */
+int fit_mlp_train_step(fit_mlp *mlp, int B, const float *x, const float *target, float lr,
+                       float weight_decay, double *loss_out, void *stream);
+/* Layer `layer` (0-based) master weights [out x in], bias [out] and the last step's gradients
+ * (host or device buffers, any may be NULL); set_layer replaces weights and bias. Synchronous. */
+int fit_mlp_get_layer(const fit_mlp *mlp, int layer, float *w, float *b, float *gw, float *gb);
+int fit_mlp_set_layer(fit_mlp *mlp, int layer, const float *w, const float *b);
+
+/* Network inputs of pseudo-experiments: x[b][slot0 + q] = log(1 + n_q) / log(1 + nbar_q) - 1
+ * with nbar the model's expectation at theta0, other slots 0 and x[b][onehot_slot] = 1 (if
+ * >= 0). data device [B x n_data], x device [B x n_in]. */
+int fit_warmstart_features(const fit_model *model, int B, const float *data, int n_in, int slot0,
+                           int onehot_slot, float *x, void *stream);
+/* Start points for fit_batch from the network: theta = theta0, then
+ * theta[target_idx[t]] = theta0 + y_t * target_scale[t] for the first n_targets outputs.
+ * data device [B x n_data]; target arrays host; theta_out device [B x P]. Synchronous. */
+int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const float *data, int slot0,
+                          int onehot_slot, int n_targets, const int *target_idx,
+                          const double *target_scale, double *theta_out, void *stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char *fit_last_error(void);
 

@@ -15,6 +15,9 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
   fit (BFGS)                          - pinned (Asimov recovery, pure-scale closed form,
       prior-only closed form, brute-force grid scan on a 2-parameter model)
   sigma (FD Hessian)                  - pinned (prior-only model: 2 H^-1 = V exactly)
+  philox4x32_10 (rng.c)               - pinned (published known-answer vectors)
+  poisson_sample (rng.c)              - pinned (chi-square against the exact Poisson PMF,
+      mean and variance, counter/offset invariance)
 """
 from __future__ import annotations
 
@@ -26,6 +29,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "rng.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
@@ -36,10 +40,11 @@ def build(force: bool = False) -> str:
     """Compile oracle.c into a shared library (gcc, OpenMP when available)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    base = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    base = ["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *_SRCS, "-o",
+            tmp, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -110,6 +115,14 @@ def _declare(L):
                                C.POINTER(C.c_uint32), C.POINTER(_DP), C.c_double, C.c_int,
                                C.POINTER(_DP), _DP, _IP, _IP, _IP, C.c_int]
     L.orc_openmp_enabled.restype = C.c_int
+    L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+    L.orc_philox4x32_10.restype = None
+    L.orc_poisson_sample.argtypes = [C.c_int64, C.POINTER(C.c_float), C.c_uint64, C.c_uint64,
+                                     C.POINTER(C.c_float)]
+    L.orc_poisson_sample.restype = None
+    L.orc_ptrs_step_many.argtypes = [C.c_float, C.c_int64, C.POINTER(C.c_float),
+                                     C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    L.orc_ptrs_step_many.restype = None
 
 
 def _d(a):
@@ -328,3 +341,32 @@ def fit_many(models, model_of, data, masks, starts, edm_tol=1e-10, max_iter=5000
 
 def openmp_enabled() -> bool:
     return bool(lib().orc_openmp_enabled())
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block: four 32-bit output words for a 4-word counter and 2-word key."""
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    lib().orc_philox4x32_10(c, k)
+    return [int(x) for x in c]
+
+
+def poisson_sample(mu, seed: int, offset: int = 0):
+    """Poisson draws (float32) for the float32 means mu; element i uses counter i + offset."""
+    mu = np.ascontiguousarray(mu, dtype=np.float32).ravel()
+    out = np.zeros_like(mu)
+    lib().orc_poisson_sample(len(mu), mu.ctypes.data_as(C.POINTER(C.c_float)),
+                             C.c_uint64(int(seed) & (2**64 - 1)), C.c_uint64(int(offset)),
+                             out.ctypes.data_as(C.POINTER(C.c_float)))
+    return out
+
+
+def ptrs_step(mu: float, U, V):
+    """One PTRS trial per (U, V) pair for mean mu >= 10: accepted count, or -1 if rejected."""
+    U = np.ascontiguousarray(U, dtype=np.float32).ravel()
+    V = np.ascontiguousarray(V, dtype=np.float32).ravel()
+    k = np.zeros_like(U)
+    F = C.POINTER(C.c_float)
+    lib().orc_ptrs_step_many(float(mu), len(U), U.ctypes.data_as(F), V.ctypes.data_as(F),
+                             k.ctypes.data_as(F))
+    return k

@@ -9,6 +9,11 @@
 #include "gemm_tc.cuh"
 #include "kernels.cuh"
 
+namespace fitcore {
+float *mlp_input_buffer(fit_mlp *m, int B);
+int mlp_dims(const fit_mlp *m, int *n_in, int *n_out);
+}
+
 using fitcore::DevModel;
 
 namespace {
@@ -321,6 +326,22 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         A.put(&dt.rrow, rrow);
         A.put(&dt.col_lo, clo);
         A.put(&dt.rcol, rcol);
+        // dense copy for the tensor-core fold, split into a TF32-exact high part and the rest
+        const int ldt = (Nt + 3) / 4 * 4;
+        vector<float> rhi((size_t)nr * ldt, 0.f), rlow((size_t)nr * ldt, 0.f);
+        for (int j = 0; j < nr; ++j)
+            for (int k = 0; k < Nt; ++k) {
+                const float x = (float)R[(size_t)j * Nt + k];
+                uint32_t bits;
+                std::memcpy(&bits, &x, 4);
+                bits = (bits + 0x1000u) & 0xFFFFE000u;   // nearest value with 10 mantissa bits
+                float hi;
+                std::memcpy(&hi, &bits, 4);
+                rhi[(size_t)j * ldt + k] = hi;
+                rlow[(size_t)j * ldt + k] = x - hi;
+            }
+        A.put(&dt.rdense_hi, rhi);
+        A.put(&dt.rdense_lo, rlow);
     }
     h.max_reco = max_reco;
     // ---- datasets -------------------------------------------------------------------------
@@ -539,6 +560,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         A.put(&h.asimov, asimov);
     }
     h.ws_eval_floats = fitcore::eval_ws_floats(Nt, C, max_reco);
+    h.ldt = (Nt + 3) / 4 * 4;
 
     // ---- upload ---------------------------------------------------------------------------
     cudaError_t e = cudaMalloc(&M->arena, A.buf.size());
@@ -693,6 +715,99 @@ int fit_tc_gemm(int tf32, int M, int N, int K, const void *A, int lda, const voi
 }
 
 int fit_tc_gemm_status(void) { return fitcore::tc_gemm_take_error(); }
+
+int fit_model_expected_tc(fit_model *model, int B, const double *theta, float *mu_out, int *status_out, int precision,
+                          void *stream) {
+    if (!model || !theta || !mu_out || B < 0 || (precision != 0 && precision != 1))
+        return fail(FIT_ERR_INVALID_ARG, "fit_model_expected_tc: bad argument");
+    if (B == 0) return FIT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t P = model->n_params, D = model->n_data;
+    Staged th, mu, st;
+    bool hmu = false, hst = false;
+    int rc = stage_in(theta, sizeof(double) * P * B, s, th);
+    if (!rc) rc = stage_out(mu_out, sizeof(float) * D * B, s, mu, hmu);
+    if (!rc) {
+        if (status_out) {
+            rc = stage_out(status_out, sizeof(int) * B, s, st, hst);
+        } else {
+            if (cudaMallocAsync(&st.dev, sizeof(int) * B, s)) rc = fail(FIT_ERR_OOM, "fit_model_expected_tc: status");
+            st.owned = true;
+        }
+    }
+    if (!rc) rc = fitcore::expected_tc(model->host, model->dev, B, (const double *)th.dev, (float *)mu.dev,
+                                       (int *)st.dev, precision, s);
+    if (!rc && hmu && cudaMemcpyAsync(mu_out, mu.dev, sizeof(float) * D * B, cudaMemcpyDeviceToHost, s))
+        rc = fail(FIT_ERR_CUDA, "fit_model_expected_tc: copy back");
+    if (!rc && hst && cudaMemcpyAsync(status_out, st.dev, sizeof(int) * B, cudaMemcpyDeviceToHost, s))
+        rc = fail(FIT_ERR_CUDA, "fit_model_expected_tc: copy back");
+    release(th, s);
+    release(mu, s);
+    release(st, s);
+    if (!rc && (hmu || hst) && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_model_expected_tc: sync");
+    return rc;
+}
+
+int fit_poisson_sample(int64_t n, const float *mu, uint64_t seed, uint64_t offset, float *out, void *stream) {
+    if (n < 0 || (n > 0 && (!mu || !out))) return fail(FIT_ERR_INVALID_ARG, "fit_poisson_sample: bad argument");
+    if (n == 0) return FIT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Staged a, b;
+    bool hb = false;
+    int rc = stage_in(mu, sizeof(float) * n, s, a);
+    if (!rc) rc = stage_out(out, sizeof(float) * n, s, b, hb);
+    if (!rc) rc = fitcore::poisson_sample(n, (const float *)a.dev, seed, offset, (float *)b.dev, s);
+    if (!rc && hb && cudaMemcpyAsync(out, b.dev, sizeof(float) * n, cudaMemcpyDeviceToHost, s))
+        rc = fail(FIT_ERR_CUDA, "fit_poisson_sample: copy back");
+    release(a, s);
+    release(b, s);
+    if (!rc && hb && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_poisson_sample: sync");
+    return rc;
+}
+
+int fit_warmstart_features(const fit_model *model, int B, const float *data, int n_in, int slot0, int onehot_slot,
+                           float *x, void *stream) {
+    if (!model || !data || !x || B < 0 || n_in < 1 || slot0 < 0 || slot0 + model->n_data > n_in)
+        return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_features: bad argument");
+    if (B == 0) return FIT_OK;
+    if (!on_device(data) || !on_device(x)) return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_features: device buffers");
+    return fitcore::features(B, model->n_data, data, model->host.asimov, n_in, slot0, onehot_slot, x,
+                             (cudaStream_t)stream);
+}
+
+int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const float *data, int slot0, int onehot_slot,
+                          int n_targets, const int *target_idx, const double *target_scale, double *theta_out,
+                          void *stream) {
+    int n_in = 0, n_out = 0;
+    if (!mlp || !model || !data || !theta_out || !target_idx || !target_scale || B < 0)
+        return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: bad argument");
+    fitcore::mlp_dims(mlp, &n_in, &n_out);
+    if (n_targets < 1 || n_targets > n_out) return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: n_targets");
+    for (int t = 0; t < n_targets; ++t)
+        if (target_idx[t] < 0 || target_idx[t] >= model->n_params)
+            return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: target index");
+    if (B == 0) return FIT_OK;
+    if (!on_device(data) || !on_device(theta_out)) return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: device buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    float *x = fitcore::mlp_input_buffer(mlp, B);
+    if (!x) return fail(FIT_ERR_OOM, "fit_warmstart_predict: input buffer");
+    int rc = fit_warmstart_features(model, B, data, n_in, slot0, onehot_slot, x, stream);
+    float *out = nullptr;
+    int *idx = nullptr;
+    double *scl = nullptr;
+    if (!rc && (cudaMallocAsync(&out, sizeof(float) * (size_t)B * n_out, s) || cudaMallocAsync(&idx, sizeof(int) * n_targets, s) ||
+                cudaMallocAsync(&scl, sizeof(double) * n_targets, s)))
+        rc = fail(FIT_ERR_OOM, "fit_warmstart_predict: workspace");
+    if (!rc && (cudaMemcpyAsync(idx, target_idx, sizeof(int) * n_targets, cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(scl, target_scale, sizeof(double) * n_targets, cudaMemcpyHostToDevice, s)))
+        rc = fail(FIT_ERR_CUDA, "fit_warmstart_predict: upload");
+    if (!rc) rc = fit_mlp_forward(mlp, B, x, out, stream);
+    if (!rc) rc = fitcore::starts(B, model->n_params, model->host.theta0, n_targets, idx, scl, out, n_out, theta_out, s);
+    for (void *p : {(void *)out, (void *)idx, (void *)scl})
+        if (p) cudaFreeAsync(p, s);
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_warmstart_predict: sync");
+    return rc;
+}
 
 void fit_batch_default_opts(fit_batch_opts *o) {
     if (!o) return;

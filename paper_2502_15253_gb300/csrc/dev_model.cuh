@@ -24,6 +24,8 @@ struct DevDetector {
     const float *rrow;       // packed row bands
     const int *col_lo;       // [N_t] first reco row of column k's band
     const float *rcol;       // [col_w x N_t]: rcol[b * N_t + k] = R[col_lo[k] + b][k] (0 past the band)
+    const float *rdense_hi;  // [N_r x ldt] dense response, TF32-exact high part (tensor-core fold)
+    const float *rdense_lo;  // [N_r x ldt] R - rdense_hi
 };
 
 struct DevBkg {
@@ -79,6 +81,7 @@ struct DevModel {
     const float *asimov;     // [n_data] expectation at theta0
     int ws_eval_floats;      // per-block workspace of one evaluation
     int max_reco;
+    int ldt;                 // row stride of the dense response (N_t rounded up to 4)
 };
 
 // ------------------------------------------------------------------------------------

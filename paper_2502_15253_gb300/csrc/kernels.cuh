@@ -31,6 +31,15 @@ __global__ void eval_kernel(const DevModel *gm, int B, const double *theta, cons
 __global__ void fit_kernel(FitArgs A);
 
 size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem);
+
+// batched.cu / poisson.cu / mlp.cu
+int expected_tc(const DevModel &h, const DevModel *dev, int B, const double *theta, float *mu, int *status,
+                int precision, cudaStream_t s);
+int poisson_sample(int64_t n, const float *mu, uint64_t seed, uint64_t offset, float *out, cudaStream_t s);
+int features(int B, int n_data, const float *data, const float *nbar, int n_in, int slot0, int onehot, float *x,
+             cudaStream_t s);
+int starts(int B, int P, const double *theta0, int n_t, const int *idx, const double *scale, const float *out,
+           int n_out, double *theta, cudaStream_t s);
 size_t fit_smem_bytes(int floats);
 __host__ __device__ inline int fit_vec_floats(int P, int hist) { return (12 + 2 * hist) * P; }
 

@@ -1,0 +1,472 @@
+// Warm-start network: a multilayer perceptron n_in -> [n_hidden, GELU] x n_hid_layers -> n_out
+// that maps a pseudo-experiment's log-normalised reco spectra to a start point of the fit.
+// Weights and activations are bf16 with FP32 master weights; every product runs on the
+// tensor-core GEMM (tcgen05, FP32 accumulation) with the bias/GELU (forward) and
+// GELU-derivative (backward) epilogues fused; AdamW updates the master weights and rewrites
+// the bf16 copies (W and W^T, the operand layouts of the forward and backward products).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fitcore.h"
+#include "gemm_tc.cuh"
+#include "kernels.cuh"
+
+int fitcore_fail(int code, const std::string &msg);
+void fitcore_count_launch();
+
+namespace {
+
+constexpr int kMaxLayers = 8;
+
+inline int pad8(int x) { return (x + 7) / 8 * 8; }
+
+__global__ void prep_input_kernel(int B, int n_in, int ld, const float *__restrict__ x, __nv_bfloat16 *__restrict__ a0) {
+    const int64_t total = (int64_t)B * ld;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / ld), i = (int)(e % ld);
+        a0[e] = __float2bfloat16(i < n_in ? x[(int64_t)b * n_in + i] : 0.f);
+    }
+}
+
+// d loss / d out for the mean squared error over B x n_out; loss (double) accumulated
+__global__ void mse_kernel(int B, int n_out, int ld, const float *__restrict__ out, const float *__restrict__ tgt,
+                           __nv_bfloat16 *__restrict__ dout, double *__restrict__ loss) {
+    const int64_t total = (int64_t)B * ld;
+    const float scale = 2.f / (float)((int64_t)B * n_out);
+    double acc = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / ld), o = (int)(e % ld);
+        float g = 0.f;
+        if (o < n_out) {
+            const float r = out[(int64_t)b * n_out + o] - tgt[(int64_t)b * n_out + o];
+            acc += (double)r * r;
+            g = scale * r;
+        }
+        dout[e] = __float2bfloat16(g);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)((int64_t)B * n_out));
+}
+
+// dst[c][r] = src[r][c] for r < R, c < Cn; dst rows have ldd elements (padding rows/cols zero)
+__global__ void transpose_bf16_kernel(int R, int Cn, int lds, const __nv_bfloat16 *__restrict__ src, int ldd,
+                                      __nv_bfloat16 *__restrict__ dst) {
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < R && c < Cn) ? src[(int64_t)r * lds + c] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < Cn && r < ldd) dst[(int64_t)c * ldd + r] = tile[threadIdx.x][i];
+    }
+}
+
+// db[o] = sum_b d[b][o]
+__global__ void colsum_kernel(int B, int n, int ld, const __nv_bfloat16 *__restrict__ d, float *__restrict__ db) {
+    const int o = blockIdx.x * blockDim.y + threadIdx.y;
+    if (o >= n) return;
+    float acc = 0.f;
+    for (int b = threadIdx.x; b < B; b += 32) acc += __bfloat162float(d[(int64_t)b * ld + o]);
+    for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+    if (threadIdx.x == 0) db[o] = acc;
+}
+
+struct AdamW {
+    float lr, b1, b2, eps, wd, c1, c2;   // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
+};
+
+// AdamW on the [out x in] weights (+ bias); rewrites W (bf16, [out x ldw]) and W^T ([in x ldwt])
+__global__ void adamw_kernel(int out, int in, AdamW h, float *__restrict__ w, const float *__restrict__ g,
+                             float *__restrict__ mw, float *__restrict__ vw, float *__restrict__ bias,
+                             const float *__restrict__ gb, float *__restrict__ mb, float *__restrict__ vb,
+                             __nv_bfloat16 *__restrict__ wbf, int ldw, __nv_bfloat16 *__restrict__ wt, int ldwt) {
+    const int64_t total = (int64_t)out * in + out;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const bool is_b = e >= (int64_t)out * in;
+        float *p = is_b ? bias + (e - (int64_t)out * in) : w + e;
+        const float gr = is_b ? gb[e - (int64_t)out * in] : g[e];
+        float *m = is_b ? mb + (e - (int64_t)out * in) : mw + e;
+        float *v = is_b ? vb + (e - (int64_t)out * in) : vw + e;
+        *m = h.b1 * *m + (1.f - h.b1) * gr;
+        *v = h.b2 * *v + (1.f - h.b2) * gr * gr;
+        const float upd = (*m * h.c1) / (sqrtf(*v * h.c2) + h.eps) + (is_b ? 0.f : h.wd * *p);
+        *p -= h.lr * upd;
+        if (!is_b) {
+            const int o = (int)(e / in), i = (int)(e % in);
+            const __nv_bfloat16 q = __float2bfloat16(*p);
+            wbf[(int64_t)o * ldw + i] = q;
+            wt[(int64_t)i * ldwt + o] = q;
+        }
+    }
+}
+
+__global__ void cast_weights_kernel(int out, int in, const float *__restrict__ w, __nv_bfloat16 *__restrict__ wbf,
+                                    int ldw, __nv_bfloat16 *__restrict__ wt, int ldwt) {
+    const int64_t total = (int64_t)out * in;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(e / in), i = (int)(e % in);
+        const __nv_bfloat16 q = __float2bfloat16(w[e]);
+        wbf[(int64_t)o * ldw + i] = q;
+        wt[(int64_t)i * ldwt + o] = q;
+    }
+}
+
+// Log-normalised spectra: x[b][slot0 + q] = log(1 + n_q) / log(1 + nbar_q) - 1, other slots 0,
+// the geometry's one-hot slot 1.
+__global__ void features_kernel(int B, int n_data, const float *__restrict__ data, const float *__restrict__ nbar,
+                                int n_in, int slot0, int onehot, float *__restrict__ x) {
+    const int64_t total = (int64_t)B * n_in;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / n_in), s = (int)(e % n_in);
+        const int q = s - slot0;
+        float v = 0.f;
+        if (q >= 0 && q < n_data) {
+            const float nb = nbar[q];
+            v = nb > 0.f ? log1pf(data[(int64_t)b * n_data + q]) / log1pf(nb) - 1.f : 0.f;
+        } else if (s == onehot) {
+            v = 1.f;
+        }
+        x[e] = v;
+    }
+}
+
+// theta[b] = theta0, then theta[b][idx_t] = theta0 + out[b][t] * scale_t
+__global__ void starts_kernel(int B, int P, const double *__restrict__ theta0, int n_t, const int *__restrict__ idx,
+                              const double *__restrict__ scale, const float *__restrict__ out, int n_out,
+                              double *__restrict__ theta) {
+    const int64_t total = (int64_t)B * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / P), i = (int)(e % P);
+        double v = theta0[i];
+        for (int t = 0; t < n_t; ++t)
+            if (idx[t] == i) v += (double)out[(int64_t)b * n_out + t] * scale[t];
+        theta[e] = v;
+    }
+}
+
+inline int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
+}  // namespace
+
+struct fit_mlp {
+    int n_layers = 0;               // linear layers
+    int dims[kMaxLayers + 1] = {0};
+    int ld[kMaxLayers + 1] = {0};   // padded row lengths (multiples of 8)
+    uint64_t seed = 0;
+    int step = 0;
+    // parameters (device)
+    float *w[kMaxLayers] = {nullptr}, *b[kMaxLayers] = {nullptr};
+    float *mw[kMaxLayers] = {nullptr}, *vw[kMaxLayers] = {nullptr}, *mb[kMaxLayers] = {nullptr}, *vb[kMaxLayers] = {nullptr};
+    float *gw[kMaxLayers] = {nullptr}, *gb[kMaxLayers] = {nullptr};
+    __nv_bfloat16 *wbf[kMaxLayers] = {nullptr}, *wt[kMaxLayers] = {nullptr};
+    // batch buffers
+    int cap = 0;
+    __nv_bfloat16 *act[kMaxLayers] = {nullptr};      // act[0] = input, act[l] = GELU(pre[l-1])
+    float *pre[kMaxLayers] = {nullptr};              // pre-activation of layer l (hidden layers)
+    __nv_bfloat16 *dpre[kMaxLayers] = {nullptr};     // d loss / d pre of layer l (bf16)
+    float *out = nullptr, *x32 = nullptr;
+    __nv_bfloat16 *tA = nullptr, *tB = nullptr;      // transposes for the weight gradients
+    double *loss = nullptr;
+    std::vector<void *> owned;
+};
+
+namespace {
+
+int dev_alloc(fit_mlp *m, void **p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fitcore_fail(FIT_ERR_OOM, "fit_mlp: device allocation");
+    }
+    cudaMemset(*p, 0, bytes);
+    m->owned.push_back(*p);
+    return FIT_OK;
+}
+
+bool is_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ensure_batch(fit_mlp *m, int B) {
+    if (B <= m->cap) return FIT_OK;
+    for (int l = 0; l < m->n_layers; ++l) {
+        if (m->act[l]) cudaFree(m->act[l]);
+        if (m->pre[l]) cudaFree(m->pre[l]);
+        if (m->dpre[l]) cudaFree(m->dpre[l]);
+        m->act[l] = nullptr;
+        m->pre[l] = nullptr;
+        m->dpre[l] = nullptr;
+    }
+    for (void *p : {(void *)m->out, (void *)m->x32, (void *)m->tA, (void *)m->tB})
+        if (p) cudaFree(p);
+    int rc = FIT_OK;
+    const int L = m->n_layers, Bp = pad8(B);
+    auto al = [&](void **p, size_t bytes) {
+        if (rc) return;
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fitcore_fail(FIT_ERR_OOM, "fit_mlp: batch buffers");
+            return;
+        }
+        cudaMemset(*p, 0, bytes);
+    };
+    int maxld = 0;
+    for (int l = 0; l <= L; ++l) maxld = std::max(maxld, m->ld[l]);
+    for (int l = 0; l < L; ++l) al((void **)&m->act[l], sizeof(__nv_bfloat16) * (size_t)B * m->ld[l]);
+    for (int l = 0; l < L; ++l) al((void **)&m->pre[l], sizeof(float) * (size_t)B * m->dims[l + 1]);
+    for (int l = 0; l < L; ++l) al((void **)&m->dpre[l], sizeof(__nv_bfloat16) * (size_t)B * m->ld[l + 1]);
+    al((void **)&m->out, sizeof(float) * (size_t)B * m->dims[L]);
+    al((void **)&m->x32, sizeof(float) * (size_t)B * m->dims[0]);
+    al((void **)&m->tA, sizeof(__nv_bfloat16) * (size_t)maxld * Bp);
+    al((void **)&m->tB, sizeof(__nv_bfloat16) * (size_t)maxld * Bp);
+    if (rc == FIT_OK) m->cap = B;
+    return rc;
+}
+
+// forward through all layers from m->act[0]; result (fp32) in m->out
+int forward(fit_mlp *m, int B, cudaStream_t s) {
+    const int L = m->n_layers;
+    for (int l = 0; l < L; ++l) {
+        fitcore::GemmOut o;
+        if (l + 1 < L) {
+            o.epi = fitcore::EPI_BIAS_GELU;
+            o.C = m->pre[l];
+            o.ldc = m->dims[l + 1];
+            o.Y = m->act[l + 1];
+            o.ldy = m->ld[l + 1];
+        } else {
+            o.epi = fitcore::EPI_BIAS_F32;
+            o.C = m->out;
+            o.ldc = m->dims[L];
+        }
+        o.bias = m->b[l];
+        int rc = fitcore::tc_gemm(false, B, m->dims[l + 1], m->dims[l], m->act[l], m->ld[l], m->wbf[l], m->ld[l], o, s,
+                                  nullptr);
+        if (rc) return rc;
+    }
+    return FIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fit_mlp_create(int n_in, int n_hidden, int n_hidden_layers, int n_out, uint64_t seed, fit_mlp **out) {
+    if (!out || n_in < 1 || n_hidden < 1 || n_out < 1 || n_hidden_layers < 0 || n_hidden_layers + 1 > kMaxLayers ||
+        n_in > 65536 || n_hidden > 65536 || n_out > 256)
+        return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_mlp_create: bad dimensions");
+    fit_mlp *m = new fit_mlp();
+    m->n_layers = n_hidden_layers + 1;
+    m->dims[0] = n_in;
+    for (int l = 1; l <= n_hidden_layers; ++l) m->dims[l] = n_hidden;
+    m->dims[m->n_layers] = n_out;
+    for (int l = 0; l <= m->n_layers; ++l) m->ld[l] = pad8(m->dims[l]);
+    m->seed = seed;
+    // He-normal initial weights from a SplitMix64 stream (Box-Muller), biases 0
+    uint64_t st = seed;
+    auto next = [&]() {
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    int rc = FIT_OK;
+    for (int l = 0; l < m->n_layers && rc == FIT_OK; ++l) {
+        const int o = m->dims[l + 1], in = m->dims[l];
+        std::vector<float> w((size_t)o * in);
+        const double sd = std::sqrt(2.0 / in);
+        for (size_t e = 0; e < w.size(); ++e) {
+            const double u1 = next(), u2 = next();
+            w[e] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+        }
+        const size_t nw = (size_t)o * in;
+        rc = dev_alloc(m, (void **)&m->w[l], sizeof(float) * nw);
+        if (!rc) rc = dev_alloc(m, (void **)&m->b[l], sizeof(float) * o);
+        if (!rc) rc = dev_alloc(m, (void **)&m->mw[l], sizeof(float) * nw);
+        if (!rc) rc = dev_alloc(m, (void **)&m->vw[l], sizeof(float) * nw);
+        if (!rc) rc = dev_alloc(m, (void **)&m->mb[l], sizeof(float) * o);
+        if (!rc) rc = dev_alloc(m, (void **)&m->vb[l], sizeof(float) * o);
+        if (!rc) rc = dev_alloc(m, (void **)&m->gw[l], sizeof(float) * nw);
+        if (!rc) rc = dev_alloc(m, (void **)&m->gb[l], sizeof(float) * o);
+        if (!rc) rc = dev_alloc(m, (void **)&m->wbf[l], sizeof(__nv_bfloat16) * (size_t)o * m->ld[l]);
+        if (!rc) rc = dev_alloc(m, (void **)&m->wt[l], sizeof(__nv_bfloat16) * (size_t)in * m->ld[l + 1]);
+        if (!rc && cudaMemcpy(m->w[l], w.data(), sizeof(float) * nw, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = fitcore_fail(FIT_ERR_CUDA, "fit_mlp_create: upload");
+        if (!rc) {
+            cast_weights_kernel<<<grid_for((int64_t)nw), 256>>>(o, in, m->w[l], m->wbf[l], m->ld[l], m->wt[l], m->ld[l + 1]);
+            fitcore_count_launch();
+        }
+    }
+    if (!rc) rc = dev_alloc(m, (void **)&m->loss, sizeof(double));
+    if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = fitcore_fail(FIT_ERR_CUDA, "fit_mlp_create: init");
+    if (rc) {
+        fit_mlp_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return FIT_OK;
+}
+
+void fit_mlp_destroy(fit_mlp *m) {
+    if (!m) return;
+    for (void *p : m->owned) cudaFree(p);
+    for (int l = 0; l < m->n_layers; ++l) {
+        if (m->act[l]) cudaFree(m->act[l]);
+        if (m->pre[l]) cudaFree(m->pre[l]);
+        if (m->dpre[l]) cudaFree(m->dpre[l]);
+    }
+    for (void *p : {(void *)m->out, (void *)m->x32, (void *)m->tA, (void *)m->tB})
+        if (p) cudaFree(p);
+    delete m;
+}
+
+int fit_mlp_forward(fit_mlp *m, int B, const float *x, float *y, void *stream) {
+    if (!m || !x || !y || B < 1) return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_mlp_forward: bad argument");
+    if (!is_device(x)) return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_mlp_forward: x must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_batch(m, B);
+    if (rc) return rc;
+    prep_input_kernel<<<grid_for((int64_t)B * m->ld[0]), 256, 0, s>>>(B, m->dims[0], m->ld[0], x, m->act[0]);
+    fitcore_count_launch();
+    rc = forward(m, B, s);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(y, m->out, sizeof(float) * (size_t)B * m->dims[m->n_layers], cudaMemcpyDefault, s) != cudaSuccess)
+        return fitcore_fail(FIT_ERR_CUDA, "fit_mlp_forward: copy out");
+    return FIT_OK;
+}
+
+int fit_mlp_train_step(fit_mlp *m, int B, const float *x, const float *target, float lr, float weight_decay,
+                       double *loss_out, void *stream) {
+    if (!m || !x || !target || B < 1 || !(lr >= 0.f))
+        return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_mlp_train_step: bad argument");
+    if (!is_device(x) || !is_device(target))
+        return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_mlp_train_step: x and target must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_batch(m, B);
+    if (rc) return rc;
+    const int L = m->n_layers, Bp = pad8(B);
+    prep_input_kernel<<<grid_for((int64_t)B * m->ld[0]), 256, 0, s>>>(B, m->dims[0], m->ld[0], x, m->act[0]);
+    cudaMemsetAsync(m->loss, 0, sizeof(double), s);
+    fitcore_count_launch();
+    if ((rc = forward(m, B, s))) return rc;
+    mse_kernel<<<grid_for((int64_t)B * m->ld[L]), 256, 0, s>>>(B, m->dims[L], m->ld[L], m->out, target, m->dpre[L - 1],
+                                                                m->loss);
+    fitcore_count_launch();
+    for (int l = L - 1; l >= 0; --l) {
+        const int o = m->dims[l + 1], in = m->dims[l];
+        colsum_kernel<<<(o + 7) / 8, dim3(32, 8), 0, s>>>(B, o, m->ld[l + 1], m->dpre[l], m->gb[l]);
+        // dW = dpre^T act: operands as K-major rows over the batch
+        transpose_bf16_kernel<<<dim3((o + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s>>>(B, o, m->ld[l + 1], m->dpre[l],
+                                                                                        Bp, m->tA);
+        transpose_bf16_kernel<<<dim3((in + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s>>>(B, in, m->ld[l], m->act[l], Bp,
+                                                                                         m->tB);
+        fitcore_count_launch();
+        fitcore_count_launch();
+        fitcore_count_launch();
+        fitcore::GemmOut gw;
+        gw.epi = fitcore::EPI_F32;
+        gw.C = m->gw[l];
+        gw.ldc = in;
+        if ((rc = fitcore::tc_gemm(false, o, in, B, m->tA, Bp, m->tB, Bp, gw, s, nullptr))) return rc;
+        if (l > 0) {
+            // d pre_{l-1} = (d pre_l W_l) * gelu'(pre_{l-1})
+            fitcore::GemmOut gx;
+            gx.epi = fitcore::EPI_DGELU;
+            gx.Y = m->dpre[l - 1];
+            gx.ldy = m->ld[l];
+            gx.aux = m->pre[l - 1];
+            gx.ldaux = in;
+            if ((rc = fitcore::tc_gemm(false, B, in, o, m->dpre[l], m->ld[l + 1], m->wt[l], m->ld[l + 1], gx, s, nullptr)))
+                return rc;
+        }
+    }
+    m->step++;
+    AdamW h;
+    h.lr = lr;
+    h.b1 = 0.9f;
+    h.b2 = 0.999f;
+    h.eps = 1e-8f;
+    h.wd = weight_decay;
+    h.c1 = (float)(1.0 / (1.0 - std::pow(0.9, m->step)));
+    h.c2 = (float)(1.0 / (1.0 - std::pow(0.999, m->step)));
+    for (int l = 0; l < L; ++l) {
+        const int o = m->dims[l + 1], in = m->dims[l];
+        adamw_kernel<<<grid_for((int64_t)o * in + o), 256, 0, s>>>(o, in, h, m->w[l], m->gw[l], m->mw[l], m->vw[l], m->b[l],
+                                                                  m->gb[l], m->mb[l], m->vb[l], m->wbf[l], m->ld[l],
+                                                                  m->wt[l], m->ld[l + 1]);
+        fitcore_count_launch();
+    }
+    if (loss_out && cudaMemcpyAsync(loss_out, m->loss, sizeof(double), cudaMemcpyDefault, s) != cudaSuccess)
+        return fitcore_fail(FIT_ERR_CUDA, "fit_mlp_train_step: loss");
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("fit_mlp_train_step: ") + cudaGetErrorString(e));
+    return FIT_OK;
+}
+
+int fit_mlp_get_layer(const fit_mlp *m, int layer, float *w, float *b, float *gw, float *gb) {
+    if (!m || layer < 0 || layer >= m->n_layers) return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_mlp_get_layer: layer");
+    const size_t nw = (size_t)m->dims[layer + 1] * m->dims[layer], nb = m->dims[layer + 1];
+    cudaDeviceSynchronize();
+    if ((w && cudaMemcpy(w, m->w[layer], sizeof(float) * nw, cudaMemcpyDefault)) ||
+        (b && cudaMemcpy(b, m->b[layer], sizeof(float) * nb, cudaMemcpyDefault)) ||
+        (gw && cudaMemcpy(gw, m->gw[layer], sizeof(float) * nw, cudaMemcpyDefault)) ||
+        (gb && cudaMemcpy(gb, m->gb[layer], sizeof(float) * nb, cudaMemcpyDefault)))
+        return fitcore_fail(FIT_ERR_CUDA, "fit_mlp_get_layer: copy");
+    return FIT_OK;
+}
+
+int fit_mlp_set_layer(fit_mlp *m, int layer, const float *w, const float *b) {
+    if (!m || layer < 0 || layer >= m->n_layers || !w || !b)
+        return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_mlp_set_layer: bad argument");
+    const int o = m->dims[layer + 1], in = m->dims[layer];
+    const size_t nw = (size_t)o * in;
+    if (cudaMemcpy(m->w[layer], w, sizeof(float) * nw, cudaMemcpyDefault) ||
+        cudaMemcpy(m->b[layer], b, sizeof(float) * o, cudaMemcpyDefault))
+        return fitcore_fail(FIT_ERR_CUDA, "fit_mlp_set_layer: copy");
+    cast_weights_kernel<<<grid_for((int64_t)nw), 256>>>(o, in, m->w[layer], m->wbf[layer], m->ld[layer], m->wt[layer],
+                                                        m->ld[layer + 1]);
+    fitcore_count_launch();
+    if (cudaDeviceSynchronize() != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, "fit_mlp_set_layer: cast");
+    return FIT_OK;
+}
+
+}  // extern "C"
+
+namespace fitcore {
+
+int features(int B, int n_data, const float *data, const float *nbar, int n_in, int slot0, int onehot, float *x,
+             cudaStream_t s) {
+    features_kernel<<<grid_for((int64_t)B * n_in), 256, 0, s>>>(B, n_data, data, nbar, n_in, slot0, onehot, x);
+    fitcore_count_launch();
+    return cudaGetLastError() == cudaSuccess ? FIT_OK : fitcore_fail(FIT_ERR_CUDA, "warm start: features");
+}
+
+int starts(int B, int P, const double *theta0, int n_t, const int *idx, const double *scale, const float *out,
+           int n_out, double *theta, cudaStream_t s) {
+    starts_kernel<<<grid_for((int64_t)B * P), 256, 0, s>>>(B, P, theta0, n_t, idx, scale, out, n_out, theta);
+    fitcore_count_launch();
+    return cudaGetLastError() == cudaSuccess ? FIT_OK : fitcore_fail(FIT_ERR_CUDA, "warm start: starts");
+}
+
+float *mlp_input_buffer(fit_mlp *m, int B) { return ensure_batch(m, B) == FIT_OK ? m->x32 : nullptr; }
+int mlp_dims(const fit_mlp *m, int *n_in, int *n_out) {
+    *n_in = m->dims[0];
+    *n_out = m->dims[m->n_layers];
+    return FIT_OK;
+}
+
+}  // namespace fitcore

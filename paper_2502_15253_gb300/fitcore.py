@@ -78,7 +78,10 @@ STATUS = {0: "converged", 1: "maxiter", 2: "linesearch_fail", 3: "nonfinite",
 
 EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model_expected",
            "fit_model_eval", "fit_model_eval_noalloc", "fit_batch_default_opts", "fit_batch",
-           "fit_tc_gemm", "fit_tc_gemm_status", "fit_last_error", "fit_kernel_launches")
+           "fit_tc_gemm", "fit_tc_gemm_status", "fit_last_error", "fit_kernel_launches",
+           "fit_model_expected_tc", "fit_poisson_sample", "fit_mlp_create", "fit_mlp_destroy",
+           "fit_mlp_forward", "fit_mlp_train_step", "fit_mlp_get_layer", "fit_mlp_set_layer",
+           "fit_warmstart_features", "fit_warmstart_predict")
 
 
 def lib_path() -> str:
@@ -109,6 +112,22 @@ def load(build_if_missing: bool = False):
     L.fit_tc_gemm_status.restype = C.c_int
     L.fit_batch.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_int, vp, vp, vp, vp,
                             C.POINTER(fit_batch_opts), vp]
+    L.fit_model_expected_tc.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, vp]
+    L.fit_poisson_sample.argtypes = [C.c_int64, vp, C.c_uint64, C.c_uint64, vp, vp]
+    L.fit_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(vp)]
+    L.fit_mlp_destroy.argtypes = [vp]
+    L.fit_mlp_destroy.restype = None
+    L.fit_mlp_forward.argtypes = [vp, C.c_int, vp, vp, vp]
+    L.fit_mlp_train_step.argtypes = [vp, C.c_int, vp, vp, C.c_float, C.c_float, vp, vp]
+    L.fit_mlp_get_layer.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    L.fit_mlp_set_layer.argtypes = [vp, C.c_int, vp, vp]
+    L.fit_warmstart_features.argtypes = [vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp]
+    L.fit_warmstart_predict.argtypes = [vp, vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp,
+                                        vp, vp]
+    for f in ("fit_model_expected_tc", "fit_poisson_sample", "fit_mlp_create", "fit_mlp_forward",
+              "fit_mlp_train_step", "fit_mlp_get_layer", "fit_mlp_set_layer",
+              "fit_warmstart_features", "fit_warmstart_predict"):
+        getattr(L, f).restype = C.c_int
     L.fit_last_error.restype = C.c_char_p
     L.fit_kernel_launches.restype = C.c_int64
     for f in ("fit_model_create", "fit_model_info", "fit_model_expected", "fit_model_eval",
@@ -285,6 +304,86 @@ def fit_tc_gemm_status() -> int:
 
 def fit_kernel_launches() -> int:
     return int(load().fit_kernel_launches())
+
+
+def fit_model_expected_tc(model: Model, B: int, theta, mu_out, status_out=None, precision=1,
+                          stream=None):
+    """Expected counts with the response fold on tensor cores (precision 0: TF32, 1: 3xTF32)."""
+    _check(load().fit_model_expected_tc(model.handle, int(B), _ptr(theta), _ptr(mu_out),
+                                        _ptr(status_out), int(precision), _stream_ptr(stream)),
+           "fit_model_expected_tc")
+
+
+def fit_poisson_sample(n, mu, seed, offset, out, stream=None):
+    """out[i] ~ Poisson(mu[i]) (float32), Philox4x32-10 counters (i + offset, draw)."""
+    _check(load().fit_poisson_sample(int(n), _ptr(mu), C.c_uint64(int(seed) & (2**64 - 1)),
+                                     C.c_uint64(int(offset)), _ptr(out), _stream_ptr(stream)),
+           "fit_poisson_sample")
+
+
+class Mlp:
+    """Warm-start network resident on the current CUDA device (wraps fit_mlp*)."""
+
+    def __init__(self, n_in, n_hidden, n_hidden_layers, n_out, seed=0):
+        h = C.c_void_p()
+        _check(load().fit_mlp_create(int(n_in), int(n_hidden), int(n_hidden_layers), int(n_out),
+                                     C.c_uint64(int(seed)), C.byref(h)), "fit_mlp_create")
+        self.handle = h
+        self.n_in, self.n_hidden, self.n_out = int(n_in), int(n_hidden), int(n_out)
+        self.n_layers = int(n_hidden_layers) + 1
+
+    def layer_shape(self, layer):
+        fan_in = self.n_in if layer == 0 else self.n_hidden
+        fan_out = self.n_out if layer == self.n_layers - 1 else self.n_hidden
+        return fan_out, fan_in
+
+    def forward(self, B, x, y, stream=None):
+        _check(load().fit_mlp_forward(self.handle, int(B), _ptr(x), _ptr(y), _stream_ptr(stream)),
+               "fit_mlp_forward")
+
+    def train_step(self, B, x, target, lr, weight_decay=0.0, loss_out=None, stream=None):
+        _check(load().fit_mlp_train_step(self.handle, int(B), _ptr(x), _ptr(target), float(lr),
+                                         float(weight_decay), _ptr(loss_out), _stream_ptr(stream)),
+               "fit_mlp_train_step")
+
+    def get_layer(self, layer):
+        o, i = self.layer_shape(layer)
+        w, b = np.zeros((o, i), np.float32), np.zeros(o, np.float32)
+        gw, gb = np.zeros((o, i), np.float32), np.zeros(o, np.float32)
+        _check(load().fit_mlp_get_layer(self.handle, int(layer), _ptr(w), _ptr(b), _ptr(gw),
+                                        _ptr(gb)), "fit_mlp_get_layer")
+        return w, b, gw, gb
+
+    def set_layer(self, layer, w, b):
+        o, i = self.layer_shape(layer)
+        w = np.ascontiguousarray(w, dtype=np.float32).reshape(o, i)
+        b = np.ascontiguousarray(b, dtype=np.float32).reshape(o)
+        _check(load().fit_mlp_set_layer(self.handle, int(layer), _ptr(w), _ptr(b)),
+               "fit_mlp_set_layer")
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fit_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def fit_warmstart_features(model: Model, B, data, n_in, slot0, onehot_slot, x, stream=None):
+    _check(load().fit_warmstart_features(model.handle, int(B), _ptr(data), int(n_in), int(slot0),
+                                         int(onehot_slot), _ptr(x), _stream_ptr(stream)),
+           "fit_warmstart_features")
+
+
+def fit_warmstart_predict(mlp: Mlp, model: Model, B, data, slot0, onehot_slot, target_idx,
+                          target_scale, theta_out, stream=None):
+    idx = np.ascontiguousarray(target_idx, dtype=np.int32)
+    scl = np.ascontiguousarray(target_scale, dtype=np.float64)
+    _check(load().fit_warmstart_predict(mlp.handle, model.handle, int(B), _ptr(data), int(slot0),
+                                        int(onehot_slot), len(idx), _ptr(idx), _ptr(scl),
+                                        _ptr(theta_out), _stream_ptr(stream)),
+           "fit_warmstart_predict")
 
 
 # ---- convenience wrappers used by tests and the benchmark ---------------------------------
