@@ -276,16 +276,56 @@ int fit_mlp_get_layer(const fit_mlp *mlp, int layer, float *w, float *b, float *
 int fit_mlp_set_layer(fit_mlp *mlp, int layer, const float *w, const float *b);
 
 /* Network inputs of pseudo-experiments: x[b][slot0 + q] = log(1 + n_q) / log(1 + nbar_q) - 1
- * with nbar the model's expectation at theta0, other slots 0 and x[b][onehot_slot] = 1 (if
+ * with nbar the model's expectation at theta0; bins of datasets whose bit is clear in masks[b]
+ * (device [B], or NULL = all datasets) are 0; other slots 0 and x[b][onehot_slot] = 1 (if
  * >= 0). data device [B x n_data], x device [B x n_in]. */
-int fit_warmstart_features(const fit_model *model, int B, const float *data, int n_in, int slot0,
-                           int onehot_slot, float *x, void *stream);
+int fit_warmstart_features(const fit_model *model, int B, const float *data, const uint32_t *masks,
+                           int n_in, int slot0, int onehot_slot, float *x, void *stream);
 /* Start points for fit_batch from the network: theta = theta0, then
  * theta[target_idx[t]] = theta0 + y_t * target_scale[t] for the first n_targets outputs.
- * data device [B x n_data]; target arrays host; theta_out device [B x P]. Synchronous. */
-int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const float *data, int slot0,
-                          int onehot_slot, int n_targets, const int *target_idx,
-                          const double *target_scale, double *theta_out, void *stream);
+ * data device [B x n_data]; masks as above; target arrays host; theta_out device [B x P].
+ * Synchronous. */
+int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const float *data,
+                          const uint32_t *masks, int slot0, int onehot_slot, int n_targets,
+                          const int *target_idx, const double *target_scale, double *theta_out,
+                          void *stream);
+
+#define FIT_WS_MAX_TARGETS 16
+#define FIT_WS_MAX_MASKS 8
+
+/* How one model (geometry) enters the warm-start network: where its bins sit among the inputs,
+ * which parameters the outputs predict (standardised: y = (theta - theta0) / scale), which
+ * parameters training draws uniformly in theta0 +- half instead of from their priors, and the
+ * dataset masks a training sample draws from (uniformly; none = all datasets). */
+typedef struct fit_warmstart_geom {
+    int slot0;
+    int onehot_slot;                          /* -1 = none                                  */
+    int n_targets;
+    int target_idx[FIT_WS_MAX_TARGETS];
+    double target_scale[FIT_WS_MAX_TARGETS];
+    int n_uniform;
+    int uniform_idx[FIT_WS_MAX_TARGETS];
+    double uniform_half[FIT_WS_MAX_TARGETS];
+    int n_masks;
+    uint32_t masks[FIT_WS_MAX_MASKS];
+} fit_warmstart_geom;
+
+/* Training parameter vectors: parameters in a covariance block theta0 + L z (V = L L^T), other
+ * parameters theta0 + sigma z (sigma = prior width, or the free parameter's scale), z standard
+ * normal; the geometry's uniform parameters theta0 + half (2u - 1). Sample b uses Philox4x32-10
+ * counters (b + offset, i, 0x0D8A0001, 0) under key seed. theta_out device [B x P]; masks_out
+ * device [B] or NULL. */
+int fit_warmstart_draw(fit_model *model, const fit_warmstart_geom *geom, int B, uint64_t seed,
+                       uint64_t offset, double *theta_out, uint32_t *masks_out, void *stream);
+
+/* Trains the network for n_steps AdamW steps of `batch` fresh samples each, the geometries in
+ * turn: draw theta and masks, expected spectra with the TF32 tensor-core fold, Poisson counts,
+ * inputs and standardised targets, one step. Learning rate lr (0.05 + 0.95 (1 + cos(pi s /
+ * n_steps)) / 2) at step s. losses_out (host or device [n_steps] double, or NULL) receives each
+ * step's batch loss. Synchronous. */
+int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmstart_geom *geoms,
+                        int n_geoms, int n_steps, int batch, float lr, float weight_decay,
+                        uint64_t seed, double *losses_out, void *stream);
 
 /* Message of the last error on this thread ("" if none). */
 const char *fit_last_error(void);

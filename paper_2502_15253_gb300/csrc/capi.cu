@@ -558,6 +558,10 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
     {
         vector<float> asimov(h.n_data, 0.f);
         A.put(&h.asimov, asimov);
+        vector<int> slot_ds(h.n_data, 0);
+        for (int ds = 0; ds < h.n_ds; ++ds)
+            for (int j = 0; j < h.ds[ds].n_reco; ++j) slot_ds[h.ds[ds].data_off + j] = ds;
+        A.put(&h.slot_ds, slot_ds);
     }
     h.ws_eval_floats = fitcore::eval_ws_floats(Nt, C, max_reco);
     h.ldt = (Nt + 3) / 4 * 4;
@@ -765,38 +769,41 @@ int fit_poisson_sample(int64_t n, const float *mu, uint64_t seed, uint64_t offse
     return rc;
 }
 
-int fit_warmstart_features(const fit_model *model, int B, const float *data, int n_in, int slot0, int onehot_slot,
-                           float *x, void *stream) {
-    if (!model || !data || !x || B < 0 || n_in < 1 || slot0 < 0 || slot0 + model->n_data > n_in)
+int fit_warmstart_features(const fit_model *model, int B, const float *data, const uint32_t *masks, int n_in,
+                           int slot0, int onehot_slot, float *x, void *stream) {
+    if (!model || !data || !x || B < 0 || n_in < 1 || slot0 < 0 || slot0 + model->n_data > n_in ||
+        onehot_slot >= n_in || (onehot_slot >= slot0 && onehot_slot < slot0 + model->n_data))
         return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_features: bad argument");
     if (B == 0) return FIT_OK;
-    if (!on_device(data) || !on_device(x)) return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_features: device buffers");
-    return fitcore::features(B, model->n_data, data, model->host.asimov, n_in, slot0, onehot_slot, x,
-                             (cudaStream_t)stream);
+    if (!on_device(data) || !on_device(x) || (masks && !on_device(masks)))
+        return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_features: device buffers");
+    return fitcore::features(B, model->n_data, data, model->host.asimov, masks, model->host.slot_ds, nullptr, n_in,
+                             slot0, onehot_slot, x, (cudaStream_t)stream);
 }
 
-int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const float *data, int slot0, int onehot_slot,
-                          int n_targets, const int *target_idx, const double *target_scale, double *theta_out,
-                          void *stream) {
+int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const float *data, const uint32_t *masks,
+                          int slot0, int onehot_slot, int n_targets, const int *target_idx,
+                          const double *target_scale, double *theta_out, void *stream) {
     int n_in = 0, n_out = 0;
     if (!mlp || !model || !data || !theta_out || !target_idx || !target_scale || B < 0)
         return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: bad argument");
     fitcore::mlp_dims(mlp, &n_in, &n_out);
     if (n_targets < 1 || n_targets > n_out) return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: n_targets");
     for (int t = 0; t < n_targets; ++t)
-        if (target_idx[t] < 0 || target_idx[t] >= model->n_params)
-            return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: target index");
+        if (target_idx[t] < 0 || target_idx[t] >= model->n_params || !(target_scale[t] > 0.0))
+            return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: target index or scale");
     if (B == 0) return FIT_OK;
-    if (!on_device(data) || !on_device(theta_out)) return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: device buffers");
+    if (!on_device(data) || !on_device(theta_out) || (masks && !on_device(masks)))
+        return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_predict: device buffers");
     cudaStream_t s = (cudaStream_t)stream;
     float *x = fitcore::mlp_input_buffer(mlp, B);
     if (!x) return fail(FIT_ERR_OOM, "fit_warmstart_predict: input buffer");
-    int rc = fit_warmstart_features(model, B, data, n_in, slot0, onehot_slot, x, stream);
+    int rc = fit_warmstart_features(model, B, data, masks, n_in, slot0, onehot_slot, x, stream);
     float *out = nullptr;
     int *idx = nullptr;
     double *scl = nullptr;
-    if (!rc && (cudaMallocAsync(&out, sizeof(float) * (size_t)B * n_out, s) || cudaMallocAsync(&idx, sizeof(int) * n_targets, s) ||
-                cudaMallocAsync(&scl, sizeof(double) * n_targets, s)))
+    if (!rc && (cudaMallocAsync(&out, sizeof(float) * (size_t)B * n_out, s) ||
+                cudaMallocAsync(&idx, sizeof(int) * n_targets, s) || cudaMallocAsync(&scl, sizeof(double) * n_targets, s)))
         rc = fail(FIT_ERR_OOM, "fit_warmstart_predict: workspace");
     if (!rc && (cudaMemcpyAsync(idx, target_idx, sizeof(int) * n_targets, cudaMemcpyHostToDevice, s) ||
                 cudaMemcpyAsync(scl, target_scale, sizeof(double) * n_targets, cudaMemcpyHostToDevice, s)))
@@ -806,6 +813,133 @@ int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const flo
     for (void *p : {(void *)out, (void *)idx, (void *)scl})
         if (p) cudaFreeAsync(p, s);
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_warmstart_predict: sync");
+    return rc;
+}
+
+namespace {
+
+int check_geom(const fit_model *m, const fit_warmstart_geom *g, int n_in, int n_out) {
+    if (!g || g->n_targets < 1 || g->n_targets > FIT_WS_MAX_TARGETS || g->n_targets > n_out || g->n_uniform < 0 ||
+        g->n_uniform > FIT_WS_MAX_TARGETS || g->n_masks < 0 || g->n_masks > FIT_WS_MAX_MASKS || g->slot0 < 0 ||
+        g->slot0 + m->n_data > n_in || g->onehot_slot >= n_in ||
+        (g->onehot_slot >= g->slot0 && g->onehot_slot < g->slot0 + m->n_data))
+        return fail(FIT_ERR_INVALID_ARG, "warm start: bad geometry description");
+    for (int t = 0; t < g->n_targets; ++t)
+        if (g->target_idx[t] < 0 || g->target_idx[t] >= m->n_params || !(g->target_scale[t] > 0.0))
+            return fail(FIT_ERR_INVALID_ARG, "warm start: target index or scale");
+    for (int t = 0; t < g->n_uniform; ++t)
+        if (g->uniform_idx[t] < 0 || g->uniform_idx[t] >= m->n_params || !(g->uniform_half[t] >= 0.0))
+            return fail(FIT_ERR_INVALID_ARG, "warm start: uniform index or half-width");
+    return FIT_OK;
+}
+
+// device copy of one geometry's index and scale tables
+struct GeomDev {
+    int *tidx = nullptr, *uidx = nullptr;
+    double *tscale = nullptr, *uhalf = nullptr;
+    uint32_t *choices = nullptr;
+};
+
+int upload_geom(const fit_warmstart_geom &g, GeomDev &d, cudaStream_t s) {
+    if (cudaMallocAsync(&d.tidx, sizeof(int) * FIT_WS_MAX_TARGETS, s) ||
+        cudaMallocAsync(&d.uidx, sizeof(int) * FIT_WS_MAX_TARGETS, s) ||
+        cudaMallocAsync(&d.tscale, sizeof(double) * FIT_WS_MAX_TARGETS, s) ||
+        cudaMallocAsync(&d.uhalf, sizeof(double) * FIT_WS_MAX_TARGETS, s) ||
+        cudaMallocAsync(&d.choices, sizeof(uint32_t) * FIT_WS_MAX_MASKS, s))
+        return fail(FIT_ERR_OOM, "warm start: geometry tables");
+    if (cudaMemcpyAsync(d.tidx, g.target_idx, sizeof(int) * FIT_WS_MAX_TARGETS, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d.uidx, g.uniform_idx, sizeof(int) * FIT_WS_MAX_TARGETS, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d.tscale, g.target_scale, sizeof(double) * FIT_WS_MAX_TARGETS, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d.uhalf, g.uniform_half, sizeof(double) * FIT_WS_MAX_TARGETS, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d.choices, g.masks, sizeof(uint32_t) * FIT_WS_MAX_MASKS, cudaMemcpyHostToDevice, s))
+        return fail(FIT_ERR_CUDA, "warm start: geometry upload");
+    return FIT_OK;
+}
+
+void free_geom(GeomDev &d, cudaStream_t s) {
+    for (void *p : {(void *)d.tidx, (void *)d.uidx, (void *)d.tscale, (void *)d.uhalf, (void *)d.choices})
+        if (p) cudaFreeAsync(p, s);
+    d = GeomDev();
+}
+
+}  // namespace
+
+int fit_warmstart_draw(fit_model *model, const fit_warmstart_geom *geom, int B, uint64_t seed, uint64_t offset,
+                       double *theta_out, uint32_t *masks_out, void *stream) {
+    if (!model || !geom || B < 0 || !theta_out) return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_draw: bad argument");
+    int rc = check_geom(model, geom, 1 << 30, FIT_WS_MAX_TARGETS);
+    if (rc) return rc;
+    if (B == 0) return FIT_OK;
+    if (!on_device(theta_out) || (masks_out && !on_device(masks_out)))
+        return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_draw: device buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    GeomDev gd;
+    rc = upload_geom(*geom, gd, s);
+    if (!rc) rc = fitcore::draw_theta(model->host, model->dev, B, seed, offset, geom->n_uniform, gd.uidx, gd.uhalf,
+                                      geom->n_masks, gd.choices, theta_out, masks_out, s);
+    free_geom(gd, s);
+    return rc;
+}
+
+int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmstart_geom *geoms, int n_geoms,
+                        int n_steps, int batch, float lr, float weight_decay, uint64_t seed, double *losses_out,
+                        void *stream) {
+    int n_in = 0, n_out = 0;
+    if (!mlp || !models || !geoms || n_geoms < 1 || n_geoms > 16 || n_steps < 0 || batch < 1 || !(lr > 0.f))
+        return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_train: bad argument");
+    fitcore::mlp_dims(mlp, &n_in, &n_out);
+    int max_p = 0, max_d = 0;
+    for (int g = 0; g < n_geoms; ++g) {
+        if (!models[g]) return fail(FIT_ERR_INVALID_ARG, "fit_warmstart_train: null model");
+        int rc = check_geom(models[g], &geoms[g], n_in, n_out);
+        if (rc) return rc;
+        max_p = std::max(max_p, models[g]->n_params);
+        max_d = std::max(max_d, models[g]->n_data);
+    }
+    if (n_steps == 0) return FIT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *theta = nullptr, *loss = nullptr;
+    float *mu = nullptr, *cnt = nullptr, *y = nullptr;
+    uint32_t *masks = nullptr;
+    int *status = nullptr;
+    GeomDev gd[16];
+    int rc = FIT_OK;
+    if (cudaMallocAsync(&theta, sizeof(double) * (size_t)batch * max_p, s) ||
+        cudaMallocAsync(&mu, sizeof(float) * (size_t)batch * max_d, s) ||
+        cudaMallocAsync(&cnt, sizeof(float) * (size_t)batch * max_d, s) ||
+        cudaMallocAsync(&y, sizeof(float) * (size_t)batch * n_out, s) ||
+        cudaMallocAsync(&masks, sizeof(uint32_t) * (size_t)batch, s) ||
+        cudaMallocAsync(&status, sizeof(int) * (size_t)batch, s) ||
+        cudaMallocAsync(&loss, sizeof(double) * (size_t)n_steps, s))
+        rc = fail(FIT_ERR_OOM, "fit_warmstart_train: workspace");
+    for (int g = 0; g < n_geoms && !rc; ++g) rc = upload_geom(geoms[g], gd[g], s);
+    float *x = rc ? nullptr : fitcore::mlp_input_buffer(mlp, batch);
+    if (!rc && !x) rc = fail(FIT_ERR_OOM, "fit_warmstart_train: input buffer");
+    for (int step = 0; step < n_steps && !rc; ++step) {
+        const int g = step % n_geoms;
+        const fit_model *m = models[g];
+        const fit_warmstart_geom &G = geoms[g];
+        // per-step streams of the generator: theta/masks under seed, counts under a derived key
+        const uint64_t off = (uint64_t)step * (uint64_t)batch;
+        const uint64_t pseed = seed ^ 0xA5A5A5A55A5A5A5Aull;
+        const float lr_s = lr * (float)(0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * step / n_steps)));
+        rc = fitcore::draw_theta(m->host, m->dev, batch, seed, off, G.n_uniform, gd[g].uidx, gd[g].uhalf, G.n_masks,
+                                 gd[g].choices, theta, masks, s);
+        if (!rc) rc = fitcore::expected_tc(m->host, m->dev, batch, theta, mu, status, 0, s);
+        if (!rc) rc = fitcore::poisson_sample((int64_t)batch * m->n_data, mu, pseed, off * (uint64_t)m->n_data, cnt, s);
+        if (!rc) rc = fitcore::features(batch, m->n_data, cnt, m->host.asimov, G.n_masks > 0 ? masks : nullptr,
+                                        m->host.slot_ds, status, n_in, G.slot0, G.onehot_slot, x, s);
+        if (!rc) rc = fitcore::targets(batch, m->n_params, theta, m->host.theta0, G.n_targets, gd[g].tidx, gd[g].tscale,
+                                       n_out, status, y, s);
+        if (!rc) rc = fit_mlp_train_step(mlp, batch, x, y, lr_s, weight_decay, loss + step, stream);
+    }
+    if (!rc && losses_out &&
+        cudaMemcpyAsync(losses_out, loss, sizeof(double) * (size_t)n_steps, cudaMemcpyDefault, s) != cudaSuccess)
+        rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: losses");
+    for (int g = 0; g < n_geoms; ++g) free_geom(gd[g], s);
+    for (void *p : {(void *)theta, (void *)mu, (void *)cnt, (void *)y, (void *)masks, (void *)status, (void *)loss})
+        if (p) cudaFreeAsync(p, s);
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: sync");
     return rc;
 }
 

@@ -79,6 +79,7 @@ struct DevModel {
     const float *blk_W;      // L^-1 (row-major, dense lower triangle)
     const double *blk_L64;   // L in double (final theta of a fit)
     const float *asimov;     // [n_data] expectation at theta0
+    const int *slot_ds;      // [n_data] dataset of each data bin
     int ws_eval_floats;      // per-block workspace of one evaluation
     int max_reco;
     int ldt;                 // row stride of the dense response (N_t rounded up to 4)

@@ -36,8 +36,13 @@ size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem);
 int expected_tc(const DevModel &h, const DevModel *dev, int B, const double *theta, float *mu, int *status,
                 int precision, cudaStream_t s);
 int poisson_sample(int64_t n, const float *mu, uint64_t seed, uint64_t offset, float *out, cudaStream_t s);
-int features(int B, int n_data, const float *data, const float *nbar, int n_in, int slot0, int onehot, float *x,
-             cudaStream_t s);
+int features(int B, int n_data, const float *data, const float *nbar, const uint32_t *masks, const int *slot_ds,
+             const int *status, int n_in, int slot0, int onehot, float *x, cudaStream_t s);
+int draw_theta(const DevModel &h, const DevModel *dev, int B, uint64_t seed, uint64_t offset, int n_uni,
+               const int *uidx, const double *uhalf, int n_masks, const uint32_t *choices, double *theta,
+               uint32_t *masks, cudaStream_t s);
+int targets(int B, int P, const double *theta, const double *theta0, int n_t, const int *idx, const double *scale,
+            int n_out, const int *status, float *y, cudaStream_t s);
 int starts(int B, int P, const double *theta0, int n_t, const int *idx, const double *scale, const float *out,
            int n_out, double *theta, cudaStream_t s);
 size_t fit_smem_bytes(int floats);

@@ -121,14 +121,24 @@ __global__ void cast_weights_kernel(int out, int in, const float *__restrict__ w
 
 // Log-normalised spectra: x[b][slot0 + q] = log(1 + n_q) / log(1 + nbar_q) - 1, other slots 0,
 // the geometry's one-hot slot 1.
+// Bins of datasets left out by the sample's mask, and all slots of a sample whose expectation
+// failed (status != 0), are 0.
 __global__ void features_kernel(int B, int n_data, const float *__restrict__ data, const float *__restrict__ nbar,
-                                int n_in, int slot0, int onehot, float *__restrict__ x) {
+                                const uint32_t *__restrict__ masks, const int *__restrict__ slot_ds,
+                                const int *__restrict__ status, int n_in, int slot0, int onehot,
+                                float *__restrict__ x) {
     const int64_t total = (int64_t)B * n_in;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(e / n_in), s = (int)(e % n_in);
         const int q = s - slot0;
         float v = 0.f;
-        if (q >= 0 && q < n_data) {
+        if (status && status[b]) {
+            v = 0.f;
+        } else if (q >= 0 && q < n_data) {
+            if (masks && !((masks[b] >> slot_ds[q]) & 1u)) {
+                x[e] = 0.f;
+                continue;
+            }
             const float nb = nbar[q];
             v = nb > 0.f ? log1pf(data[(int64_t)b * n_data + q]) / log1pf(nb) - 1.f : 0.f;
         } else if (s == onehot) {
@@ -448,9 +458,10 @@ int fit_mlp_set_layer(fit_mlp *m, int layer, const float *w, const float *b) {
 
 namespace fitcore {
 
-int features(int B, int n_data, const float *data, const float *nbar, int n_in, int slot0, int onehot, float *x,
-             cudaStream_t s) {
-    features_kernel<<<grid_for((int64_t)B * n_in), 256, 0, s>>>(B, n_data, data, nbar, n_in, slot0, onehot, x);
+int features(int B, int n_data, const float *data, const float *nbar, const uint32_t *masks, const int *slot_ds,
+             const int *status, int n_in, int slot0, int onehot, float *x, cudaStream_t s) {
+    features_kernel<<<grid_for((int64_t)B * n_in), 256, 0, s>>>(B, n_data, data, nbar, masks, slot_ds, status, n_in,
+                                                                slot0, onehot, x);
     fitcore_count_launch();
     return cudaGetLastError() == cudaSuccess ? FIT_OK : fitcore_fail(FIT_ERR_CUDA, "warm start: features");
 }

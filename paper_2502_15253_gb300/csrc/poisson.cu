@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/fitcore.h"
+#include "philox.cuh"
 
 int fitcore_fail(int code, const std::string &msg);
 void fitcore_count_launch();
@@ -17,31 +18,10 @@ namespace fitcore {
 
 namespace {
 
+using rng::philox4x32_10;
+using rng::u01;
+
 constexpr float kMuMax = 4194304.f;   // 2^22: above, the float steps of PTRS lose integers
-
-__device__ __forceinline__ void philox_round(uint32_t (&c)[4], uint32_t k0, uint32_t k1) {
-    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
-    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
-    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-}
-
-__device__ __forceinline__ void philox4x32_10(uint32_t (&c)[4], uint32_t k0, uint32_t k1) {
-    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        philox_round(c, k0, k1);
-        k0 += W0;
-        k1 += W1;
-    }
-}
-
-// uniform in (0, 1) from the top 23 bits: (m + 1/2) 2^-23, exact in float
-__device__ __forceinline__ float u01(uint32_t x) { return ((float)(x >> 9) + 0.5f) * 1.1920928955078125e-7f; }
 
 struct Stream {
     uint32_t c0, c1, k0, k1, draw;

@@ -1,0 +1,119 @@
+// Training samples of the warm-start network, drawn on the device: parameter vectors theta
+// (nuisances from their priors, the parameters of interest uniform in a window), a dataset
+// mask per sample, and the standardised regression targets. The expected spectra, the Poisson
+// pseudo-data and the log-normalised inputs come from batched.cu, poisson.cu and mlp.cu.
+//
+// Random numbers: Philox4x32-10 under key = seed; parameter i of sample b uses the counter
+// (b + offset, i, 0x0D8A0001, 0) and its four words give a normal deviate (Box-Muller on words
+// 0 and 1), a uniform (word 2) and, for i = 0, the mask choice (word 3).
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "dev_model.cuh"
+#include "kernels.cuh"
+#include "philox.cuh"
+
+int fitcore_fail(int code, const std::string &msg);
+void fitcore_count_launch();
+
+namespace fitcore {
+
+namespace {
+
+constexpr uint32_t kDrawTag = 0x0D8A0001u;
+
+// One block per sample. Individually constrained (or free) parameters: theta0 + zscale z;
+// parameters of a covariance block: theta0 + L z over the block (L the Cholesky factor);
+// listed parameters: theta0 + h (2u - 1), replacing the prior draw.
+__global__ void __launch_bounds__(128) draw_kernel(const DevModel *__restrict__ gm, int B, uint64_t seed,
+                                                   uint64_t offset, int n_uni, const int *__restrict__ uidx,
+                                                   const double *__restrict__ uhalf, int n_masks,
+                                                   const uint32_t *__restrict__ choices, double *__restrict__ theta,
+                                                   uint32_t *__restrict__ masks) {
+    extern __shared__ double z[];
+    const DevModel &m = *gm;
+    const int b = blockIdx.x, P = m.P;
+    const uint64_t ctr = (uint64_t)b + offset;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    double *th = theta + (int64_t)b * P;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        uint32_t c[4] = {(uint32_t)ctr, (uint32_t)(ctr >> 32), (uint32_t)i, kDrawTag};
+        rng::philox4x32_10(c, k0, k1);
+        const double u1 = rng::u01(c[0]), u2 = rng::u01(c[1]);
+        z[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+        const float zs = m.zscale[i];
+        double v = m.theta0[i] + (double)zs * z[i];
+        for (int t = 0; t < n_uni; ++t)
+            if (uidx[t] == i) v = m.theta0[i] + uhalf[t] * (2.0 * (double)rng::u01(c[2]) - 1.0);
+        th[i] = v;   // block rows are overwritten below
+        if (i == 0 && masks) {
+            uint32_t mk = 0xFFFFFFFFu;
+            if (n_masks > 0) {
+                int q = (int)(rng::u01(c[3]) * (float)n_masks);
+                mk = choices[min(q, n_masks - 1)];
+            }
+            masks[b] = mk;
+        }
+    }
+    __syncthreads();
+    // covariance blocks: row r of the block = theta0 + sum_{c <= r} L[r][c] z[idx[c]]
+    for (int k = 0; k < m.n_blocks; ++k) {
+        const int n = m.blk_size[k];
+        const int *idx = m.blk_idx + m.blk_idx_off[k];
+        const double *L = m.blk_L64 + m.blk_mat_off[k];
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            const int p = idx[r];
+            bool listed = false;
+            for (int t = 0; t < n_uni; ++t) listed |= (uidx[t] == p);
+            if (listed) continue;
+            double acc = 0.0;
+            for (int c = 0; c <= r; ++c) acc = fma(L[(int64_t)r * n + c], z[idx[c]], acc);
+            th[p] = m.theta0[p] + acc;
+        }
+    }
+}
+
+// y[b][t] = (theta[b][idx_t] - theta0[idx_t]) / scale_t for t < n_t, 0 for n_t <= t < n_out
+// and for samples whose expectation failed (status != 0)
+__global__ void targets_kernel(int B, int P, const double *__restrict__ theta, const double *__restrict__ theta0,
+                               int n_t, const int *__restrict__ idx, const double *__restrict__ scale, int n_out,
+                               const int *__restrict__ status, float *__restrict__ y) {
+    const int64_t total = (int64_t)B * n_out;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / n_out), t = (int)(e % n_out);
+        float v = 0.f;
+        if (t < n_t && !(status && status[b])) {
+            const int p = idx[t];
+            v = (float)((theta[(int64_t)b * P + p] - theta0[p]) / scale[t]);
+        }
+        y[e] = v;
+    }
+}
+
+}  // namespace
+
+int draw_theta(const DevModel &h, const DevModel *dev, int B, uint64_t seed, uint64_t offset, int n_uni,
+               const int *uidx, const double *uhalf, int n_masks, const uint32_t *choices, double *theta,
+               uint32_t *masks, cudaStream_t s) {
+    const size_t smem = sizeof(double) * (size_t)h.P;
+    if (smem > 48 * 1024) return fitcore_fail(FIT_ERR_INVALID_ARG, "warm-start draw: too many parameters");
+    draw_kernel<<<B, 128, smem, s>>>(dev, B, seed, offset, n_uni, uidx, uhalf, n_masks, choices, theta, masks);
+    fitcore_count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("warm-start draw: ") + cudaGetErrorString(e));
+    return FIT_OK;
+}
+
+int targets(int B, int P, const double *theta, const double *theta0, int n_t, const int *idx, const double *scale,
+            int n_out, const int *status, float *y, cudaStream_t s) {
+    const int64_t n = (int64_t)B * n_out;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+    targets_kernel<<<grid, 256, 0, s>>>(B, P, theta, theta0, n_t, idx, scale, n_out, status, y);
+    fitcore_count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("warm-start targets: ") + cudaGetErrorString(e));
+    return FIT_OK;
+}
+
+}  // namespace fitcore

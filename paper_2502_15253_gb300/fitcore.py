@@ -73,6 +73,19 @@ INSTANCE_DTYPE = np.dtype([("model", "<i4"), ("mask", "<u4"), ("data_off", "<i8"
 assert RESULT_DTYPE.itemsize == C.sizeof(fit_result)
 assert INSTANCE_DTYPE.itemsize == C.sizeof(fit_instance)
 
+WS_MAX_TARGETS = 16
+WS_MAX_MASKS = 8
+
+
+class fit_warmstart_geom(C.Structure):
+    _fields_ = [("slot0", C.c_int), ("onehot_slot", C.c_int), ("n_targets", C.c_int),
+                ("target_idx", C.c_int * WS_MAX_TARGETS),
+                ("target_scale", C.c_double * WS_MAX_TARGETS),
+                ("n_uniform", C.c_int), ("uniform_idx", C.c_int * WS_MAX_TARGETS),
+                ("uniform_half", C.c_double * WS_MAX_TARGETS),
+                ("n_masks", C.c_int), ("masks", C.c_uint32 * WS_MAX_MASKS)]
+
+
 STATUS = {0: "converged", 1: "maxiter", 2: "linesearch_fail", 3: "nonfinite",
           4: "mu_nonpositive", 5: "escale_nonmonotone", 6: "timeout"}
 
@@ -81,7 +94,8 @@ EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model
            "fit_tc_gemm", "fit_tc_gemm_status", "fit_last_error", "fit_kernel_launches",
            "fit_model_expected_tc", "fit_poisson_sample", "fit_mlp_create", "fit_mlp_destroy",
            "fit_mlp_forward", "fit_mlp_train_step", "fit_mlp_get_layer", "fit_mlp_set_layer",
-           "fit_warmstart_features", "fit_warmstart_predict")
+           "fit_warmstart_features", "fit_warmstart_predict", "fit_warmstart_draw",
+           "fit_warmstart_train")
 
 
 def lib_path() -> str:
@@ -121,12 +135,17 @@ def load(build_if_missing: bool = False):
     L.fit_mlp_train_step.argtypes = [vp, C.c_int, vp, vp, C.c_float, C.c_float, vp, vp]
     L.fit_mlp_get_layer.argtypes = [vp, C.c_int, vp, vp, vp, vp]
     L.fit_mlp_set_layer.argtypes = [vp, C.c_int, vp, vp]
-    L.fit_warmstart_features.argtypes = [vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp]
-    L.fit_warmstart_predict.argtypes = [vp, vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp,
-                                        vp, vp]
+    L.fit_warmstart_features.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_int, vp, vp]
+    L.fit_warmstart_predict.argtypes = [vp, vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_int, vp,
+                                        vp, vp, vp]
+    L.fit_warmstart_draw.argtypes = [vp, C.POINTER(fit_warmstart_geom), C.c_int, C.c_uint64,
+                                     C.c_uint64, vp, vp, vp]
+    L.fit_warmstart_train.argtypes = [vp, C.POINTER(vp), C.POINTER(fit_warmstart_geom), C.c_int,
+                                      C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, vp, vp]
     for f in ("fit_model_expected_tc", "fit_poisson_sample", "fit_mlp_create", "fit_mlp_forward",
               "fit_mlp_train_step", "fit_mlp_get_layer", "fit_mlp_set_layer",
-              "fit_warmstart_features", "fit_warmstart_predict"):
+              "fit_warmstart_features", "fit_warmstart_predict", "fit_warmstart_draw",
+              "fit_warmstart_train"):
         getattr(L, f).restype = C.c_int
     L.fit_last_error.restype = C.c_char_p
     L.fit_kernel_launches.restype = C.c_int64
@@ -370,20 +389,59 @@ class Mlp:
         self.close()
 
 
-def fit_warmstart_features(model: Model, B, data, n_in, slot0, onehot_slot, x, stream=None):
-    _check(load().fit_warmstart_features(model.handle, int(B), _ptr(data), int(n_in), int(slot0),
-                                         int(onehot_slot), _ptr(x), _stream_ptr(stream)),
+def fit_warmstart_features(model: Model, B, data, masks, n_in, slot0, onehot_slot, x, stream=None):
+    _check(load().fit_warmstart_features(model.handle, int(B), _ptr(data), _ptr(masks), int(n_in),
+                                         int(slot0), int(onehot_slot), _ptr(x),
+                                         _stream_ptr(stream)),
            "fit_warmstart_features")
 
 
-def fit_warmstart_predict(mlp: Mlp, model: Model, B, data, slot0, onehot_slot, target_idx,
+def fit_warmstart_predict(mlp: Mlp, model: Model, B, data, masks, slot0, onehot_slot, target_idx,
                           target_scale, theta_out, stream=None):
     idx = np.ascontiguousarray(target_idx, dtype=np.int32)
     scl = np.ascontiguousarray(target_scale, dtype=np.float64)
-    _check(load().fit_warmstart_predict(mlp.handle, model.handle, int(B), _ptr(data), int(slot0),
-                                        int(onehot_slot), len(idx), _ptr(idx), _ptr(scl),
-                                        _ptr(theta_out), _stream_ptr(stream)),
+    _check(load().fit_warmstart_predict(mlp.handle, model.handle, int(B), _ptr(data), _ptr(masks),
+                                        int(slot0), int(onehot_slot), len(idx), _ptr(idx),
+                                        _ptr(scl), _ptr(theta_out), _stream_ptr(stream)),
            "fit_warmstart_predict")
+
+
+def make_geom(slot0, onehot_slot, target_idx, target_scale, uniform_idx=(), uniform_half=(),
+              masks=()) -> fit_warmstart_geom:
+    g = fit_warmstart_geom()
+    g.slot0, g.onehot_slot = int(slot0), int(onehot_slot)
+    if not (0 < len(target_idx) <= WS_MAX_TARGETS and len(target_scale) == len(target_idx)
+            and len(uniform_idx) == len(uniform_half) and len(uniform_idx) <= WS_MAX_TARGETS
+            and len(masks) <= WS_MAX_MASKS):
+        raise ValueError("warm-start geometry: table sizes")
+    g.n_targets = len(target_idx)
+    for t, (i, sc) in enumerate(zip(target_idx, target_scale)):
+        g.target_idx[t], g.target_scale[t] = int(i), float(sc)
+    g.n_uniform = len(uniform_idx)
+    for t, (i, h) in enumerate(zip(uniform_idx, uniform_half)):
+        g.uniform_idx[t], g.uniform_half[t] = int(i), float(h)
+    g.n_masks = len(masks)
+    for t, mk in enumerate(masks):
+        g.masks[t] = int(mk)
+    return g
+
+
+def fit_warmstart_draw(model: Model, geom: fit_warmstart_geom, B, seed, offset, theta_out,
+                       masks_out=None, stream=None):
+    _check(load().fit_warmstart_draw(model.handle, C.byref(geom), int(B), C.c_uint64(int(seed)),
+                                     C.c_uint64(int(offset)), _ptr(theta_out), _ptr(masks_out),
+                                     _stream_ptr(stream)),
+           "fit_warmstart_draw")
+
+
+def fit_warmstart_train(mlp: Mlp, models, geoms, n_steps, batch, lr, weight_decay, seed,
+                        losses_out=None, stream=None):
+    hs = (C.c_void_p * len(models))(*[m.handle.value for m in models])
+    gs = (fit_warmstart_geom * len(geoms))(*geoms)
+    _check(load().fit_warmstart_train(mlp.handle, hs, gs, len(geoms), int(n_steps), int(batch),
+                                      float(lr), float(weight_decay), C.c_uint64(int(seed)),
+                                      _ptr(losses_out), _stream_ptr(stream)),
+           "fit_warmstart_train")
 
 
 # ---- convenience wrappers used by tests and the benchmark ---------------------------------
