@@ -164,14 +164,18 @@ typedef struct fit_batch_opts {
     int max_iter;         /* iteration limit (default 2000)                                  */
     int history;          /* L-BFGS pairs kept, 1..16 (default 16)                           */
     double f_noise_rel;   /* relative noise allowance of -2lnL in the line search (1e-6)     */
-    int threads;          /* threads per block, multiple of 32 in [64, 256]; 0 = default 256 */
-    int blocks_per_sm;    /* resident blocks per SM; 0 = autotuned / occupancy maximum      */
-    int use_graph;        /* 1 = launch through a cached CUDA graph                          */
+    int threads;          /* threads per block, multiple of 32 in [64, 128]; 0 = default 128 */
+    int blocks_per_sm;    /* resident blocks per SM: 5 selects the 96-register build of the
+                             kernel, 1-4 the 128-register one (capped); 0 = automatic        */
+    int use_graph;        /* 1 = launch through a cached CUDA graph (work-queue memset and
+                             kernel nodes, parameters updated in place for each call)        */
     double time_budget_s; /* per-launch clock budget (0 = 60 s); exceeded -> FIT_STATUS_TIMEOUT */
     int restarts;         /* history restarts after the first EDM convergence, 0..8 (default 0):
                              each rebuilds the L-BFGS pairs for at least `history` iterations,
                              which firms up the EDM estimate in flat directions             */
-    int pad;
+    int placement;        /* per-fit workspace: 0 = automatic (most resident fits per SM),
+                             1 = all in shared memory, 2 = L-BFGS history in global memory
+                             (L2-resident) and the rest in shared memory, 3 = all global      */
 } fit_batch_opts;
 
 /* Result of one instance. */
@@ -326,6 +330,15 @@ int fit_warmstart_draw(fit_model *model, const fit_warmstart_geom *geom, int B, 
 int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmstart_geom *geoms,
                         int n_geoms, int n_steps, int batch, float lr, float weight_decay,
                         uint64_t seed, double *losses_out, void *stream);
+
+/* Chooses threads per block and resident blocks per SM for fit_batch on the current device by
+ * timing the candidate configurations (96 or 128 threads, 4 or 5 blocks per SM) on the first
+ * n_sample instances (0 = ten per SM, at most n_inst), and writes the fastest into
+ * opts->threads and opts->blocks_per_sm (other fields are used as given). Arguments as for
+ * fit_batch; results of the timing runs are discarded. Synchronous. */
+int fit_batch_autotune(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst,
+                       const float *data, const double *start, int n_sample, fit_batch_opts *opts,
+                       void *stream);
 
 /* Message of the last error on this thread ("" if none). */
 const char *fit_last_error(void);

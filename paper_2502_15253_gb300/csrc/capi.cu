@@ -943,6 +943,81 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
     return rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One instantiated graph per launch shape: a memset node (work queue = 0) followed by the fit
+// kernel node. A call with the same shape updates both nodes' parameters in the executable
+// graph and relaunches it, which skips the per-launch driver work of a plain launch.
+struct FitGraph {
+    const void *func = nullptr;
+    int grid = 0, threads = 0;
+    size_t smem = 0;
+    int device = -1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t memset_node = nullptr, kernel_node = nullptr;
+};
+std::vector<FitGraph> g_graphs;   // guarded by g_ws_mutex (held by fit_batch)
+
+int graph_launch(const void *kern, int grid, int threads, size_t smem, fitcore::FitArgs &a,
+                 int *queue, cudaStream_t s) {
+    int dev = 0;
+    FIT_CUDA(cudaGetDevice(&dev));
+    cudaMemsetParams mp = {};
+    mp.dst = queue;
+    mp.value = 0;
+    mp.elementSize = sizeof(int);
+    mp.width = 1;
+    mp.height = 1;
+    mp.pitch = 0;
+    void *args[] = {&a};
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void *>(kern);
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(threads);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    FitGraph *G = nullptr;
+    for (auto &g : g_graphs)
+        if (g.func == kern && g.grid == grid && g.threads == threads && g.smem == smem && g.device == dev)
+            G = &g;
+    if (G) {
+        if (cudaGraphExecMemsetNodeSetParams(G->exec, G->memset_node, &mp) != cudaSuccess ||
+            cudaGraphExecKernelNodeSetParams(G->exec, G->kernel_node, &kp) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FIT_ERR_CUDA, "fit_batch: graph update");
+        }
+    } else {
+        FitGraph g;
+        g.func = kern;
+        g.grid = grid;
+        g.threads = threads;
+        g.smem = smem;
+        g.device = dev;
+        if (cudaGraphCreate(&g.graph, 0) != cudaSuccess ||
+            cudaGraphAddMemsetNode(&g.memset_node, g.graph, nullptr, 0, &mp) != cudaSuccess ||
+            cudaGraphAddKernelNode(&g.kernel_node, g.graph, &g.memset_node, 1, &kp) != cudaSuccess ||
+            cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (g.graph) cudaGraphDestroy(g.graph);
+            return fail(FIT_ERR_CUDA, "fit_batch: graph construction");
+        }
+        g_graphs.push_back(g);
+        G = &g_graphs.back();
+    }
+    if (cudaGraphLaunch(G->exec, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FIT_ERR_CUDA, "fit_batch: graph launch");
+    }
+    return FIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 void fit_batch_default_opts(fit_batch_opts *o) {
     if (!o) return;
     o->edm_tol = 1e-8;
@@ -954,6 +1029,7 @@ void fit_batch_default_opts(fit_batch_opts *o) {
     o->use_graph = 0;
     o->time_budget_s = 60.0;
     o->restarts = 0;
+    o->placement = 0;
 }
 
 int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst, const float *data,
@@ -967,9 +1043,9 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
     if (opts_in) o = *opts_in;
     if (o.history < 1 || o.history > 16) return fail(FIT_ERR_INVALID_ARG, "fit_batch: history must be 1..16");
     if (o.restarts < 0 || o.restarts > 8) return fail(FIT_ERR_INVALID_ARG, "fit_batch: restarts must be 0..8");
-    if (o.threads == 0) o.threads = 256;
-    if (o.threads < 64 || o.threads > 256 || o.threads % 32)
-        return fail(FIT_ERR_INVALID_ARG, "fit_batch: threads must be a multiple of 32 in [64, 256]");
+    if (o.threads == 0) o.threads = 128;
+    if (o.threads < 64 || o.threads > 128 || o.threads % 32)
+        return fail(FIT_ERR_INVALID_ARG, "fit_batch: threads must be a multiple of 32 in [64, 128]");
     if (!(o.edm_tol > 0.0) || o.max_iter < 0) return fail(FIT_ERR_INVALID_ARG, "fit_batch: edm_tol / max_iter");
     if (o.time_budget_s <= 0.0) o.time_budget_s = 60.0;
     cudaStream_t s = (cudaStream_t)stream;
@@ -983,22 +1059,65 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
         data_len = std::max<int64_t>(data_len, q.data_off + models[q.model]->n_data);
         par_len = std::max<int64_t>(par_len, q.param_off + models[q.model]->n_params);
     }
+    int max_loc = 0;   // working vectors + evaluation workspace, without the history
     for (int mi = 0; mi < n_models; ++mi) {
         const DevModel &h = models[mi]->host;
         max_need = std::max(max_need, fitcore::fit_vec_floats(h.P, o.history) + h.ws_eval_floats);
+        max_loc = std::max(max_loc, 12 * h.P + h.ws_eval_floats);
     }
+    if (o.placement < 0 || o.placement > 3) return fail(FIT_ERR_INVALID_ARG, "fit_batch: placement must be 0..3");
     LaunchCfg cfg;
     int rc = device_cfg(cfg);
     if (rc) return rc;
     std::lock_guard<std::mutex> lock(g_ws_mutex);
-    // workspace placement: shared memory if the largest model fits in ~1/2 of an SM's share
-    const size_t need_bytes = fitcore::fit_smem_bytes(max_need);
-    const bool in_smem = need_bytes <= 112 * 1024;
-    const size_t smem = in_smem ? need_bytes : fitcore::fit_smem_bytes(0);
-    FIT_CUDA(cudaFuncSetAttribute(fitcore::fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)std::min(smem, cfg.smem_optin)));
+    // Workspace placement and kernel variant (resident blocks per SM the registers allow).
+    // Shared memory holds what fits in ~1/2 of an SM's share; the automatic choice takes the
+    // combination with the most resident fits per SM (ties: more in shared memory).
+    const size_t kSmemCap = 112 * 1024;
+    auto smem_for = [&](int pl) -> size_t {
+        if (pl == 1) return fitcore::fit_smem_bytes(max_need);
+        if (pl == 2) return fitcore::fit_smem_bytes(max_loc);
+        return fitcore::fit_smem_bytes(0);
+    };
+    auto kernel_for = [](int variant) { return fitcore::fit_kernel_func(variant); };
+    auto blocks_for = [&](int pl, int variant) -> int {
+        const size_t sm = smem_for(pl);
+        if (sm > std::min(kSmemCap, cfg.smem_optin)) return 0;
+        auto k = kernel_for(variant);
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, o.threads, sm) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return n;
+    };
+    int placement = o.placement, variant = o.blocks_per_sm >= 5 ? 5 : 4;
+    if (placement == 0) {
+        int best_n = -1;
+        for (int pl : {1, 2, 3}) {
+            const int v = o.blocks_per_sm > 0 ? variant : (pl == 3 ? 5 : 4);
+            const int n = blocks_for(pl, v);
+            if (n > best_n) {
+                best_n = n;
+                placement = pl;
+                variant = v;
+            }
+        }
+    } else if (o.blocks_per_sm == 0) {
+        variant = placement == 3 ? 5 : 4;
+    }
+    if (blocks_for(placement, variant) < 1)
+        return fail(FIT_ERR_INVALID_CONFIG, "fit_batch: the requested workspace placement does not fit an SM");
+    const bool in_smem = placement == 1;
+    const size_t smem = smem_for(placement);
+    auto kern = kernel_for(variant);
+    FIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::min(smem, cfg.smem_optin)));
     int per_sm = 0;
-    FIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fitcore::fit_kernel, o.threads, smem));
+    FIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, o.threads, smem));
     if (per_sm < 1) return fail(FIT_ERR_INVALID_CONFIG, "fit_batch: launch configuration does not fit an SM");
     if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, o.blocks_per_sm);
     const int grid = std::max(1, std::min(n_inst, per_sm * cfg.sms));
@@ -1019,7 +1138,7 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
         dws.owned = true;
     }
     if (!rc) {
-        if (cudaMallocAsync(&dq.dev, sizeof(int), s) || cudaMemsetAsync(dq.dev, 0, sizeof(int), s))
+        if (cudaMallocAsync(&dq.dev, sizeof(int), s) || (!o.use_graph && cudaMemsetAsync(dq.dev, 0, sizeof(int), s)))
             rc = fail(FIT_ERR_CUDA, "fit_batch: queue");
         dq.owned = true;
     }
@@ -1041,12 +1160,17 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
         a.queue = (int *)dq.dev;
         a.ws_global = (float *)dws.dev;
         a.ws_stride = max_need;
-        a.smem_floats = in_smem ? max_need : 0;
+        a.smem_floats = placement == 1 ? max_need : placement == 2 ? max_loc : 0;
+        a.hist_global = placement == 1 ? 0 : 1;
         a.budget_ns = (uint64_t)(o.time_budget_s * 1e9);
-        fitcore::fit_kernel<<<grid, o.threads, smem, s>>>(a);
+        if (o.use_graph) {
+            rc = graph_launch(kern, grid, o.threads, smem, a, (int *)dq.dev, s);
+        } else {
+            void *args[] = {&a};
+            cudaError_t e = cudaLaunchKernel(kern, dim3(grid), dim3(o.threads), args, smem, s);
+            if (e != cudaSuccess) rc = fail(FIT_ERR_CUDA, std::string("fit_kernel launch: ") + cudaGetErrorString(e));
+        }
         g_launches++;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) rc = fail(FIT_ERR_CUDA, std::string("fit_kernel launch: ") + cudaGetErrorString(e));
     }
     if (!rc && hbe) {
         // copy back only the parameter ranges the instances own (merged intervals), so that
@@ -1077,6 +1201,64 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
     // the staged model table and instance table are host vectors: finish before they go away
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_batch: synchronise");
     return rc;
+}
+
+
+int fit_batch_autotune(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst,
+                       const float *data, const double *start, int n_sample, fit_batch_opts *opts, void *stream) {
+    if (!models || n_models < 1 || !inst || n_inst < 1 || !data || !opts || n_sample < 0)
+        return fail(FIT_ERR_INVALID_ARG, "fit_batch_autotune: bad argument");
+    LaunchCfg cfg;
+    int rc = device_cfg(cfg);
+    if (rc) return rc;
+    const int n = n_sample > 0 ? std::min(n_sample, n_inst) : std::min(n_inst, 10 * cfg.sms);
+    int64_t par_len = 0;
+    for (int i = 0; i < n; ++i) {
+        if (inst[i].model < 0 || inst[i].model >= n_models || !models[inst[i].model])
+            return fail(FIT_ERR_INVALID_ARG, "fit_batch_autotune: instance out of range");
+        par_len = std::max<int64_t>(par_len, inst[i].param_off + models[inst[i].model]->n_params);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double *best = nullptr;
+    fit_result *res = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&best, sizeof(double) * (size_t)par_len) || cudaMalloc(&res, sizeof(fit_result) * (size_t)n) ||
+        cudaEventCreate(&e0) || cudaEventCreate(&e1))
+        rc = fail(FIT_ERR_OOM, "fit_batch_autotune: scratch");
+    fit_batch_opts o = *opts, best_o = *opts;
+    float best_ms = 0.f;
+    bool found = false;
+    for (int threads : {96, 128}) {
+        for (int bps : {4, 5}) {
+            if (rc) break;
+            o.threads = threads;
+            o.blocks_per_sm = bps;
+            if (fit_batch(models, n_models, inst, n, data, start, best, res, &o, stream) != FIT_OK) {
+                rc = FIT_OK;   // a configuration that does not fit is skipped
+                continue;
+            }
+            cudaEventRecord(e0, s);
+            int r2 = fit_batch(models, n_models, inst, n, data, start, best, res, &o, stream);
+            cudaEventRecord(e1, s);
+            if (r2 != FIT_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (!found || ms < best_ms) {
+                found = true;
+                best_ms = ms;
+                best_o = o;
+            }
+        }
+    }
+    if (best) cudaFree(best);
+    if (res) cudaFree(res);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (!found) return fail(FIT_ERR_INVALID_CONFIG, "fit_batch_autotune: no configuration ran");
+    opts->threads = best_o.threads;
+    opts->blocks_per_sm = best_o.blocks_per_sm;
+    return FIT_OK;
 }
 
 }  // extern "C"

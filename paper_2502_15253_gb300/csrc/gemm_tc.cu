@@ -22,6 +22,7 @@ namespace {
 constexpr int kStages = 4;
 constexpr int kRowBytes = 128;           // one K slice: 128 bytes per row
 constexpr int kTileM = 128;
+constexpr int kNumSMs = 152;
 constexpr uint64_t kMaxTries = 2000000000ull;  // bound of every barrier wait: 2 s
 
 __device__ int g_gemm_err;
@@ -35,7 +36,7 @@ __device__ __forceinline__ float gelu_grad(float x) {
 template <bool TF32>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-                   int K, int n_tile, GemmOut out, int *err) {
+                   int K, int n_tile, int kt_per, GemmOut out, int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int a_bytes = kTileM * kRowBytes;
@@ -48,7 +49,10 @@ __global__ void __launch_bounds__(128, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kTileM, n0 = blockIdx.y * n_tile;
     const int kel = TF32 ? 32 : 64;
-    const int ktiles = (K + kel - 1) / kel;
+    // split K: this CTA reduces K tiles [kt0, kt0 + ktiles) and adds its partial product
+    const int kt0 = blockIdx.z * kt_per;
+    const int ktiles = min(kt_per, (K + kel - 1) / kel - kt0);
+    const bool split = gridDim.z > 1;
     uint32_t ncols = 32;
     while ((int)ncols < n_tile) ncols <<= 1;
 
@@ -78,8 +82,8 @@ __global__ void __launch_bounds__(128, 1)
             }
             uint8_t *sa = smem + s * stage_bytes;
             umma::mbar_arrive_expect_tx(&full[s], stage_bytes);
-            umma::tma_load_2d(sa, &tmA, &full[s], t * kel, m0);
-            umma::tma_load_2d(sa + a_bytes, &tmB, &full[s], t * kel, n0);
+            umma::tma_load_2d(sa, &tmA, &full[s], (kt0 + t) * kel, m0);
+            umma::tma_load_2d(sa + a_bytes, &tmB, &full[s], (kt0 + t) * kel, n0);
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer: 4 MMAs of 32 bytes of K per slice --------------------------------
@@ -121,7 +125,10 @@ __global__ void __launch_bounds__(128, 1)
                 const float d = v[i];
                 switch (out.epi) {
                     case EPI_F32:
-                        out.C[(int64_t)row * out.ldc + n] = d;
+                        if (split)
+                            atomicAdd(&out.C[(int64_t)row * out.ldc + n], d);
+                        else
+                            out.C[(int64_t)row * out.ldc + n] = d;
                         break;
                     case EPI_BIAS_F32:
                         out.C[(int64_t)row * out.ldc + n] = d + out.bias[n];
@@ -137,7 +144,10 @@ __global__ void __launch_bounds__(128, 1)
                             __float2bfloat16(d * gelu_grad(out.aux[(int64_t)row * out.ldaux + n]));
                         break;
                     case EPI_F32_ADD:
-                        out.C[(int64_t)row * out.ldc + n] += d;
+                        if (split)
+                            atomicAdd(&out.C[(int64_t)row * out.ldc + n], d);
+                        else
+                            out.C[(int64_t)row * out.ldc + n] += d;
                         break;
                 }
             }
@@ -196,6 +206,15 @@ int tc_gemm(bool tf32, int M, int N, int K, const void *A, int lda, const void *
     if (rc) return rc;
     const int ntn = (N + 255) / 256;
     const int n_tile = (((N + ntn - 1) / ntn) + 15) / 16 * 16;
+    // Output tiles that cannot fill the SMs (a weight gradient: small M x N, K = the batch)
+    // split K over grid z; the partial products are added with atomics (plain FP32 outputs).
+    const int mt = (M + kTileM - 1) / kTileM;
+    const int ktiles = (K + (tf32 ? 32 : 64) - 1) / (tf32 ? 32 : 64);
+    int splits = 1;
+    if (out.epi == EPI_F32 || out.epi == EPI_F32_ADD)
+        while (mt * ntn * splits * 2 <= 2 * kNumSMs && ktiles / (splits * 2) >= 4) splits *= 2;
+    const int kt_per = (ktiles + splits - 1) / splits;
+    splits = (ktiles + kt_per - 1) / kt_per;   // no empty split
     CUtensorMap ta, tb;
     if ((rc = make_map(&ta, tf32, A, M, K, lda, kTileM))) return rc;
     if ((rc = make_map(&tb, tf32, B, N, K, ldb, n_tile))) return rc;
@@ -211,8 +230,15 @@ int tc_gemm(bool tf32, int M, int N, int K, const void *A, int lda, const void *
         cudaGetLastError();
         return fitcore_fail(FIT_ERR_CUDA, "tensor-core GEMM: shared memory attribute");
     }
-    dim3 grid((M + kTileM - 1) / kTileM, ntn);
-    kern<<<grid, 128, smem, stream>>>(ta, tb, M, N, K, n_tile, out, err_dev);
+    if (splits > 1 && out.epi == EPI_F32) {
+        // C = 0 first: rows of ldc floats (the row tails beyond N are left as they were)
+        cudaError_t e = (out.ldc == N) ? cudaMemsetAsync(out.C, 0, sizeof(float) * (size_t)M * N, stream)
+                                       : cudaMemset2DAsync(out.C, sizeof(float) * (size_t)out.ldc, 0,
+                                                           sizeof(float) * (size_t)N, M, stream);
+        if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, "tensor-core GEMM: clearing C");
+    }
+    dim3 grid(mt, ntn, splits);
+    kern<<<grid, 128, smem, stream>>>(ta, tb, M, N, K, n_tile, kt_per, out, err_dev);
     fitcore_count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

@@ -171,7 +171,8 @@ struct FitVecs {
     float *z, *g, *d, *zt, *gt, *zlo, *glo, *zcr, *gcr, *pv, *pd, *gth, *S, *Y;
 };
 
-__device__ __forceinline__ FitVecs carve_fit_vecs(float *base, int P, int hist) {
+// 12 P-vectors at base; the 2 hist P-vectors of the history at hbase
+__device__ __forceinline__ FitVecs carve_fit_vecs(float *base, float *hbase, int P, int hist) {
     FitVecs v;
     v.z = base;
     v.g = v.z + P;
@@ -185,7 +186,7 @@ __device__ __forceinline__ FitVecs carve_fit_vecs(float *base, int P, int hist) 
     v.pv = v.gcr + P;
     v.pd = v.pv + P;
     v.gth = v.pd + P;
-    v.S = v.gth + P;
+    v.S = hbase;
     v.Y = v.S + (int64_t)hist * P;
     return v;
 }
@@ -420,7 +421,12 @@ __device__ __forceinline__ void vcopy(float *dst, const float *src, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-__global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
+// At most 128 threads; MINB resident blocks per SM (4: <= 128 registers, 5: <= 96). Each block
+// fits one instance at a time, so MINB instances share an SM and cover each other's barrier and
+// load latencies. With the working set in shared memory four blocks of the larger register
+// budget measured faster; with it in global memory (L2) the fifth instance pays for itself.
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FitSmem &S = *reinterpret_cast<FitSmem *>(smem_raw);
     float *dyn = reinterpret_cast<float *>(smem_raw + sizeof(FitSmem));
@@ -440,11 +446,16 @@ __global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
         copy_model(&S.m, A.models + in.model);
         const DevModel &m = S.m;
         const int P = m.P;
-        // workspace: shared memory when the model fits, else this block's global slice
-        const int need = fit_vec_floats(P, hist_max) + m.ws_eval_floats;
-        float *base = (need <= A.smem_floats) ? dyn : gws;
-        FitVecs V = carve_fit_vecs(base, P, hist_max);
-        const EvalWs ws = carve_eval_ws(base + fit_vec_floats(P, hist_max), m.N_t, m.C, m.max_reco);
+        // workspace: the 12 working vectors and the evaluation workspace in shared memory when
+        // they fit, else in this block's global slice; the history in shared memory after them
+        // unless it is placed in the global slice (hist_global)
+        // (global slice: history first, then the rest)
+        const int hfl = fit_hist_floats(P, hist_max), loc = 12 * P + m.ws_eval_floats;
+        const bool loc_smem = loc + (A.hist_global ? 0 : hfl) <= A.smem_floats;
+        float *base = loc_smem ? dyn : gws + (A.hist_global ? hfl : 0);
+        float *hbase = A.hist_global ? gws : base + loc;
+        FitVecs V = carve_fit_vecs(base, hbase, P, hist_max);
+        const EvalWs ws = carve_eval_ws(base + 12 * P, m.N_t, m.C, m.max_reco);
         const float *data = A.data + in.data_off;
         fit_result res;
         res.iters = 0;
@@ -668,6 +679,11 @@ __global__ void __launch_bounds__(256, 2) fit_kernel(FitArgs A) {
         }
         __syncthreads();
     }
+}
+
+const void *fit_kernel_func(int variant) {
+    return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5>)
+                        : reinterpret_cast<const void *>(&fit_kernel<4>);
 }
 
 size_t fit_smem_bytes(int floats) { return sizeof(FitSmem) + sizeof(float) * (size_t)floats; }

@@ -22,13 +22,15 @@ struct FitArgs {
     float *ws_global;            // per-block global workspace slices (or nullptr)
     int64_t ws_stride;           // floats per block slice
     int smem_floats;             // dynamic shared floats available for the workspace
+    int hist_global;             // 1: the L-BFGS history lives in the global slice
     uint64_t budget_ns;
 };
 
 __global__ void eval_kernel(const DevModel *gm, int B, const double *theta, const float *data,
                             const uint32_t *masks, double *nll_out, float *grad_out,
                             float *mu_out, int *status_out, float *ws_global, int ws_in_smem);
-__global__ void fit_kernel(FitArgs A);
+// the persistent fit kernel compiled for 4 or 5 resident blocks per SM (host entry address)
+const void *fit_kernel_func(int variant);
 
 size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem);
 
@@ -47,5 +49,6 @@ int starts(int B, int P, const double *theta0, int n_t, const int *idx, const do
            int n_out, double *theta, cudaStream_t s);
 size_t fit_smem_bytes(int floats);
 __host__ __device__ inline int fit_vec_floats(int P, int hist) { return (12 + 2 * hist) * P; }
+__host__ __device__ inline int fit_hist_floats(int P, int hist) { return 2 * hist * P; }
 
 }  // namespace fitcore

@@ -58,7 +58,7 @@ class fit_batch_opts(C.Structure):
     _fields_ = [("edm_tol", C.c_double), ("max_iter", C.c_int), ("history", C.c_int),
                 ("f_noise_rel", C.c_double), ("threads", C.c_int), ("blocks_per_sm", C.c_int),
                 ("use_graph", C.c_int), ("time_budget_s", C.c_double), ("restarts", C.c_int),
-                ("pad", C.c_int)]
+                ("placement", C.c_int)]
 
 
 class fit_result(C.Structure):
@@ -95,7 +95,7 @@ EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model
            "fit_model_expected_tc", "fit_poisson_sample", "fit_mlp_create", "fit_mlp_destroy",
            "fit_mlp_forward", "fit_mlp_train_step", "fit_mlp_get_layer", "fit_mlp_set_layer",
            "fit_warmstart_features", "fit_warmstart_predict", "fit_warmstart_draw",
-           "fit_warmstart_train")
+           "fit_warmstart_train", "fit_batch_autotune")
 
 
 def lib_path() -> str:
@@ -147,6 +147,9 @@ def load(build_if_missing: bool = False):
               "fit_warmstart_features", "fit_warmstart_predict", "fit_warmstart_draw",
               "fit_warmstart_train"):
         getattr(L, f).restype = C.c_int
+    L.fit_batch_autotune.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_int, vp, vp, C.c_int,
+                                     C.POINTER(fit_batch_opts), vp]
+    L.fit_batch_autotune.restype = C.c_int
     L.fit_last_error.restype = C.c_char_p
     L.fit_kernel_launches.restype = C.c_int64
     for f in ("fit_model_create", "fit_model_info", "fit_model_expected", "fit_model_eval",
@@ -307,6 +310,18 @@ def fit_batch(models, inst, data, start, best, results, opts=None, stream=None):
     _check(L.fit_batch(hs, len(models), inst.ctypes.data, len(inst), _ptr(data), _ptr(start),
                        _ptr(best), _ptr(results), C.byref(o), _stream_ptr(stream)),
            "fit_batch")
+
+
+def fit_batch_autotune(models, inst, data, start=None, n_sample=0, opts=None, stream=None):
+    """Times the fit kernel's launch configurations on a sample; returns the tuned options."""
+    L = load()
+    hs = (C.c_void_p * len(models))(*[m.handle.value for m in models])
+    inst = np.ascontiguousarray(inst, dtype=INSTANCE_DTYPE)
+    o = opts if opts is not None else fit_batch_default_opts()
+    _check(L.fit_batch_autotune(hs, len(models), inst.ctypes.data, len(inst), _ptr(data),
+                                _ptr(start), int(n_sample), C.byref(o), _stream_ptr(stream)),
+           "fit_batch_autotune")
+    return o
 
 
 def fit_tc_gemm(tf32, M, N, K, A, lda, B, ldb, epi, C=None, ldc=0, Y=None, ldy=0, bias=None,

@@ -1,0 +1,74 @@
+"""Launch configurations of the persistent fit kernel: workspace placements, the two
+residency builds, the CUDA-graph path and the autotuner give the same fits."""
+import numpy as np
+import pytest
+
+from paper_2502_15253_gb300 import fitcore, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def work():
+    spec = synth.make_model("c1")
+    gm = fitcore.Model(spec)
+    B = 200
+    rng = np.random.default_rng(9)
+    truths = np.stack([synth.draw_theta_true(spec, rng) for _ in range(B)])
+    mu, st = fitcore.expected_numpy(gm, truths)
+    data = rng.poisson(mu.astype(np.float64)).astype(np.float32)
+    inst = np.zeros(B, fitcore.INSTANCE_DTYPE)
+    inst["mask"] = [synth.C1_MASKS[i % 3] for i in range(B)]
+    inst["data_off"] = np.arange(B) * spec.n_bins
+    inst["param_off"] = np.arange(B) * spec.n_params
+    return spec, gm, data, inst
+
+
+def _fit(gm, inst, data, **kw):
+    o = fitcore.fit_batch_default_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return fitcore.fit_numpy([gm], inst, data, opts=o)
+
+
+def test_placements_and_builds_agree(work):
+    spec, gm, data, inst = work
+    best0, r0 = _fit(gm, inst, data)
+    assert np.all(r0["status"] == 0)
+    for kw in [dict(placement=1), dict(placement=2), dict(placement=3),
+               dict(placement=3, blocks_per_sm=5), dict(placement=2, blocks_per_sm=4),
+               dict(threads=96), dict(threads=64, placement=3)]:
+        best, r = _fit(gm, inst, data, **kw)
+        assert np.all(r["status"] == 0), kw
+        same = np.abs(r["nll_min"] - r0["nll_min"]) <= 1e-3
+        assert same.mean() >= 0.97, (kw, same.mean())
+
+
+def test_graph_launch_matches_plain_launch(work):
+    spec, gm, data, inst = work
+    torch = pytest.importorskip("torch")
+    dd = torch.from_numpy(data.ravel()).cuda()
+    P = spec.n_params
+    outs = []
+    for use_graph in [0, 1, 1]:
+        best = torch.zeros(len(inst) * P, dtype=torch.float64, device="cuda")
+        res = torch.zeros(len(inst) * 32, dtype=torch.uint8, device="cuda")
+        o = fitcore.fit_batch_default_opts()
+        o.use_graph = use_graph
+        fitcore.fit_batch([gm], inst, dd, None, best, res, o)
+        torch.cuda.synchronize()
+        outs.append((best.cpu().numpy(), np.frombuffer(res.cpu().numpy().tobytes(),
+                                                       dtype=fitcore.RESULT_DTYPE)))
+    for best, r in outs[1:]:
+        np.testing.assert_array_equal(best, outs[0][0])
+        np.testing.assert_array_equal(r["nll_min"], outs[0][1]["nll_min"])
+        np.testing.assert_array_equal(r["iters"], outs[0][1]["iters"])
+
+
+def test_autotune_picks_a_candidate(work):
+    spec, gm, data, inst = work
+    o = fitcore.fit_batch_autotune([gm], inst, data, n_sample=150)
+    assert o.threads in (96, 128) and o.blocks_per_sm in (4, 5)
+    best, r = fitcore.fit_numpy([gm], inst, data, opts=o)
+    _, r0 = _fit(gm, inst, data)
+    assert np.mean(np.abs(r["nll_min"] - r0["nll_min"]) <= 1e-3) >= 0.97

@@ -105,19 +105,33 @@ def test_features_and_start_points(name, slot0, onehot):
     data = np.stack([synth.poisson_data(nbar, 100 + b) for b in range(B)]).astype(np.float32)
     dd = torch.from_numpy(data).cuda()
     x = torch.zeros((B, n_in), dtype=torch.float32, device="cuda")
-    fitcore.fit_warmstart_features(gm, B, dd, n_in, slot0, onehot, x)
+    fitcore.fit_warmstart_features(gm, B, dd, None, n_in, slot0, onehot, x)
     torch.cuda.synchronize()
     ref = np.zeros((B, n_in))
     ref[:, slot0:slot0 + gm.n_data] = np.log1p(data) / np.log1p(nbar) - 1.0
     if onehot >= 0:
         ref[:, onehot] = 1.0
     np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=0, atol=2e-6)
+    # dataset masks: the bins of a left-out dataset read 0
+    n_ds = len(spec.datasets)
+    masks = np.array([(1 << n_ds) - 1 if b % 2 else 1 for b in range(B)], np.uint32)
+    fitcore.fit_warmstart_features(gm, B, dd, torch.from_numpy(masks.view(np.int32)).cuda(),
+                                   n_in, slot0, onehot, x)
+    torch.cuda.synchronize()
+    off = 0
+    for d, ds in enumerate(spec.datasets):
+        n = spec.detectors[ds.det].n_reco
+        keep = (masks >> d) & 1
+        ref[:, slot0 + off:slot0 + off + n] *= keep[:, None]
+        off += n
+    np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=0, atol=2e-6)
     # start points: theta = theta0 + y_t * scale_t on the target parameters
     net = fitcore.Mlp(n_in, 64, 1, 12, seed=9)
     idx = np.arange(3)
     scl = np.array([0.01, 0.02, 0.03])
     th = torch.zeros((B, gm.n_params), dtype=torch.float64, device="cuda")
-    fitcore.fit_warmstart_predict(net, gm, B, dd, slot0, onehot, idx, scl, th)
+    fitcore.fit_warmstart_features(gm, B, dd, None, n_in, slot0, onehot, x)
+    fitcore.fit_warmstart_predict(net, gm, B, dd, None, slot0, onehot, idx, scl, th)
     y = torch.zeros((B, 12), dtype=torch.float32, device="cuda")
     net.forward(B, x, y)
     torch.cuda.synchronize()

@@ -61,3 +61,35 @@ def test_tf32_gemm(M, N, K):
 
 def test_bias_epilogue():
     assert run(False, 200, 120, 96, epi=1) <= 1e-5
+
+
+@pytest.mark.parametrize("tf32,M,N,K", [(False, 512, 438, 16384), (False, 96, 70, 3000),
+                                        (True, 40, 38, 2000), (True, 1, 400, 2000)])
+def test_split_k_padded_output(tf32, M, N, K):
+    """Small output grids with a long K run split over K with atomic accumulation; the output
+    rows are padded (ldc > N) and the padding must stay untouched."""
+    rng = np.random.default_rng(11)
+    lda = ((K + 7) // 8) * 8
+    A = rng.standard_normal((M, lda)).astype(np.float32)
+    B = rng.standard_normal((N, lda)).astype(np.float32)
+    dev = torch.device("cuda")
+    if tf32:
+        Ad, Bd = torch.tensor(A, device=dev), torch.tensor(B, device=dev)
+        Aref, Bref = tf32_trunc(A[:, :K]), tf32_trunc(B[:, :K])
+    else:
+        Ad = torch.tensor(A, device=dev).to(torch.bfloat16)
+        Bd = torch.tensor(B, device=dev).to(torch.bfloat16)
+        Aref, Bref = Ad.float().cpu().numpy()[:, :K], Bd.float().cpu().numpy()[:, :K]
+    ref = Aref.astype(np.float64) @ Bref.astype(np.float64).T
+    absref = np.abs(Aref.astype(np.float64)) @ np.abs(Bref.astype(np.float64)).T
+    ldc = N + 5
+    C = torch.full((M, ldc), np.nan, dtype=torch.float32, device=dev)
+    fitcore.fit_tc_gemm(tf32, M, N, K, Ad, lda, Bd, lda, 0, C=C, ldc=ldc)
+    # accumulate the same product once more (EPI_F32_ADD = 4)
+    fitcore.fit_tc_gemm(tf32, M, N, K, Ad, lda, Bd, lda, 4, C=C, ldc=ldc)
+    torch.cuda.synchronize()
+    assert fitcore.fit_tc_gemm_status() == 0
+    got = C.cpu().numpy().astype(np.float64)
+    assert np.all(np.isnan(got[:, N:]))
+    err = np.abs(got[:, :N] - 2 * ref) / (2 * absref + 1e-30)
+    assert err.max() <= 4e-6 * np.sqrt(K / 32)
