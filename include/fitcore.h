@@ -176,6 +176,11 @@ typedef struct fit_batch_opts {
     int placement;        /* per-fit workspace: 0 = automatic (most resident fits per SM),
                              1 = all in shared memory, 2 = L-BFGS history in global memory
                              (L2-resident) and the rest in shared memory, 3 = all global      */
+    int engine;           /* 0 = persistent kernel (one block per fit at a time); 1 = lockstep:
+                             the fits of a model advance one evaluation per round, each round
+                             three launches over all of them (threads, blocks_per_sm and
+                             placement then do not apply)                                    */
+    int pad;
 } fit_batch_opts;
 
 /* Result of one instance. */

@@ -1014,6 +1014,163 @@ int graph_launch(const void *kern, int grid, int threads, size_t smem, fitcore::
     return FIT_OK;
 }
 
+// Lockstep engine driver: per model, the instances of that model advance together; each round
+// is the forward, adjoint and step launches over the active ones. The host reads the number
+// still active after every round (a 4-byte copy) to size the next launches and to stop.
+int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst,
+                       const float *data, const double *start, double *best, fit_result *results,
+                       const fit_batch_opts &o, cudaStream_t s, int64_t data_len, int64_t par_len) {
+    LaunchCfg cfg;
+    int rc = device_cfg(cfg);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    Staged di, dd, dst, dbe, dre;
+    bool hbe = false, hre = false;
+    rc = stage_in(inst, sizeof(fit_instance) * n_inst, s, di);
+    if (!rc) rc = stage_in(data, sizeof(float) * data_len, s, dd);
+    if (!rc && start) rc = stage_in(start, sizeof(double) * par_len, s, dst);
+    if (!rc) rc = stage_out(best, sizeof(double) * par_len, s, dbe, hbe);
+    if (!rc) rc = stage_out(results, sizeof(fit_result) * n_inst, s, dre, hre);
+    int *cnt_host = nullptr;
+    if (!rc && cudaMallocHost(&cnt_host, sizeof(int)) != cudaSuccess) rc = fail(FIT_ERR_OOM, "fit_batch: pinned counter");
+    for (int mi = 0; mi < n_models && !rc; ++mi) {
+        std::vector<int> grp;
+        for (int i = 0; i < n_inst; ++i)
+            if (inst[i].model == mi) grp.push_back(i);
+        if (grp.empty()) continue;
+        const DevModel &h = models[mi]->host;
+        const int n = (int)grp.size(), P = h.P, nd = h.n_ds;
+        fitcore::LsArgs A{};
+        A.model = models[mi]->dev;
+        A.inst = (const fit_instance *)di.dev;
+        A.n = n;
+        A.data = (const float *)dd.dev;
+        A.start = start ? (const double *)dst.dev : nullptr;
+        A.best = (double *)dbe.dev;
+        A.results = (fit_result *)dre.dev;
+        A.vec_stride = ((int64_t)fitcore::fit_vec_floats(P, o.history) + 3) / 4 * 4;
+        A.hist = o.history;
+        A.max_iter = o.max_iter;
+        A.max_ls = 30;
+        A.restarts = o.restarts;
+        A.edm_tol = o.edm_tol;
+        A.f_noise_rel = o.f_noise_rel;
+        A.budget_ns = (uint64_t)(o.time_budget_s * 1e9);
+        // evaluation workspace: the adjoint needs the full per-dataset arrays
+        const int ws_floats = h.ws_eval_floats;
+        const size_t eval_smem = fitcore::ls_eval_smem_bytes(P, ws_floats);
+        A.ws_in_smem = eval_smem <= 48 * 1024 ? 1 : 0;
+        const size_t esm = A.ws_in_smem ? eval_smem : fitcore::ls_eval_smem_bytes(P, 0);
+        const size_t ssm = fitcore::ls_step_smem_bytes();
+        int per_sm_f = 0, per_sm_a = 0, per_sm_s = 0;
+        for (const void *k : {(const void *)fitcore::ls_forward_kernel, (const void *)fitcore::ls_adjoint_kernel})
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm) != cudaSuccess)
+                rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep shared memory");
+        for (const void *k : {(const void *)fitcore::ls_step_kernel, (const void *)fitcore::ls_init_kernel})
+            if (!rc && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm) != cudaSuccess)
+                rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep shared memory");
+        if (!rc && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, fitcore::ls_forward_kernel, 128, esm) ||
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, fitcore::ls_adjoint_kernel, 128, esm) ||
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, fitcore::ls_step_kernel, 128, ssm)))
+            rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep occupancy");
+        if (!rc && (per_sm_f < 1 || per_sm_a < 1 || per_sm_s < 1))
+            rc = fail(FIT_ERR_INVALID_CONFIG, "fit_batch: lockstep kernels do not fit an SM");
+        if (rc) break;
+        const int cap_f = per_sm_f * cfg.sms, cap_a = per_sm_a * cfg.sms, cap_s = per_sm_s * cfg.sms;
+        A.ws_stride = A.ws_in_smem ? 0 : ws_floats;
+        std::vector<void *> bufs;
+        auto al = [&](void **p, size_t bytes) {
+            if (rc) return;
+            if (cudaMallocAsync(p, std::max<size_t>(bytes, 16), s) != cudaSuccess) {
+                cudaGetLastError();
+                rc = fail(FIT_ERR_OOM, "fit_batch: lockstep buffers");
+                return;
+            }
+            bufs.push_back(*p);
+        };
+        int *grp_d = nullptr, *act0 = nullptr, *act1 = nullptr, *cnt = nullptr, *stat = nullptr;
+        uint64_t *deadline = nullptr;
+        al((void **)&grp_d, sizeof(int) * n);
+        al((void **)&A.state, fitcore::ls_state_bytes() * n);
+        al((void **)&A.vec, sizeof(float) * (size_t)n * A.vec_stride);
+        al((void **)&A.gsl, sizeof(float) * (size_t)n * nd * P);
+        al((void **)&A.nll_ds, sizeof(double) * (size_t)n * nd);
+        al((void **)&A.gmu, sizeof(float) * (size_t)n * nd * h.max_reco);
+        al((void **)&stat, sizeof(int) * n);
+        al((void **)&act0, sizeof(int) * n);
+        al((void **)&act1, sizeof(int) * n);
+        al((void **)&cnt, sizeof(int) * 2);
+        al((void **)&deadline, sizeof(uint64_t));
+        if (!A.ws_in_smem) al((void **)&A.ws_global, sizeof(float) * (size_t)std::max(cap_f, cap_a) * ws_floats);
+        if (!rc && cudaMemcpyAsync(grp_d, grp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep upload");
+        A.group = grp_d;
+        A.stat = stat;
+        A.deadline = deadline;
+        int *acts[2] = {act0, act1};
+        if (!rc) {
+            A.act = act1;
+            A.n_act = cnt + 1;
+            A.act_next = act0;
+            A.n_act_next = cnt;
+            fitcore::ls_init_kernel<<<std::min(n, cap_s), 128, ssm, s>>>(A);
+            g_launches++;
+            if (cudaGetLastError() != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep init launch");
+        }
+        int active = n;
+        const int max_rounds = o.max_iter * 34 + 64;
+        for (int r = 0; !rc && active > 0 && r < max_rounds; ++r) {
+            const int cur = r & 1, nxt = cur ^ 1;
+            A.act = acts[cur];
+            A.n_act = cnt + cur;
+            A.act_next = acts[nxt];
+            A.n_act_next = cnt + nxt;
+            if (cudaMemsetAsync(cnt + nxt, 0, sizeof(int), s) != cudaSuccess) {
+                rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep counter");
+                break;
+            }
+            fitcore::ls_forward_kernel<<<std::max(1, std::min(active * nd, cap_f)), 128, esm, s>>>(A);
+            fitcore::ls_adjoint_kernel<<<std::max(1, std::min(active * nd, cap_a)), 128, esm, s>>>(A);
+            fitcore::ls_step_kernel<<<std::max(1, std::min(active, cap_s)), 128, ssm, s>>>(A);
+            g_launches += 3;
+            if (cudaGetLastError() != cudaSuccess ||
+                cudaMemcpyAsync(cnt_host, cnt + nxt, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep round");
+                break;
+            }
+            active = *cnt_host;
+        }
+        if (!rc && active > 0) rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep did not finish");
+        for (void *p : bufs) cudaFreeAsync(p, s);
+    }
+    if (!rc && hbe) {
+        std::vector<std::pair<int64_t, int64_t>> iv;
+        for (int i = 0; i < n_inst; ++i)
+            iv.emplace_back(inst[i].param_off, inst[i].param_off + models[inst[i].model]->n_params);
+        std::sort(iv.begin(), iv.end());
+        int64_t a = iv[0].first, b = iv[0].second;
+        for (size_t q = 1; q <= iv.size() && !rc; ++q) {
+            if (q < iv.size() && iv[q].first <= b) {
+                b = std::max(b, iv[q].second);
+                continue;
+            }
+            if (cudaMemcpyAsync(best + a, (double *)dbe.dev + a, sizeof(double) * (b - a), cudaMemcpyDeviceToHost, s))
+                rc = fail(FIT_ERR_CUDA, "fit_batch: copy back");
+            if (q < iv.size()) {
+                a = iv[q].first;
+                b = iv[q].second;
+            }
+        }
+    }
+    if (!rc && hre && cudaMemcpyAsync(results, dre.dev, sizeof(fit_result) * n_inst, cudaMemcpyDeviceToHost, s))
+        rc = fail(FIT_ERR_CUDA, "fit_batch: copy back");
+    for (Staged *b : {&di, &dd, &dst, &dbe, &dre}) release(*b, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = fail(FIT_ERR_CUDA, "fit_batch: synchronise");
+    if (cnt_host) cudaFreeHost(cnt_host);
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1030,6 +1187,8 @@ void fit_batch_default_opts(fit_batch_opts *o) {
     o->time_budget_s = 60.0;
     o->restarts = 0;
     o->placement = 0;
+    o->engine = 0;
+    o->pad = 0;
 }
 
 int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst, const float *data,
@@ -1059,6 +1218,9 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
         data_len = std::max<int64_t>(data_len, q.data_off + models[q.model]->n_data);
         par_len = std::max<int64_t>(par_len, q.param_off + models[q.model]->n_params);
     }
+    if (o.engine == 1) return fit_batch_lockstep(models, n_models, inst, n_inst, data, start, best, results, o, s,
+                                                 data_len, par_len);
+    if (o.engine != 0) return fail(FIT_ERR_INVALID_ARG, "fit_batch: engine must be 0 or 1");
     int max_loc = 0;   // working vectors + evaluation workspace, without the history
     for (int mi = 0; mi < n_models; ++mi) {
         const DevModel &h = models[mi]->host;

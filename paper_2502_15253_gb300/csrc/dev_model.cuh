@@ -316,24 +316,38 @@ __device__ __forceinline__ EMap make_emap(const DevModel &m, const DevDataset &d
 }
 
 // ------------------------------------------------------------------------------------
-// Block-level evaluation of one dataset: adds its Poisson -2lnL and (if grad != nullptr)
-// its gradient contributions (in theta space, shared-memory array of P floats).
-// Returns the dataset's -2lnL (all threads); *status |= kSt* bits on failure.
+// Block-level evaluation of one dataset, in stages that the fit kernels call either in one
+// sequence (eval_dataset) or split over two launches (forward + likelihood, then adjoint).
 // ------------------------------------------------------------------------------------
-static __device__ double eval_dataset(const DevModel &m, int d, const float *pv, const float *pd,
-                               const float *data, EvalWs ws, float *grad, double *red,
-                               int *status, float *mu_out) {
+// Per-dataset constants of one evaluation: survival parameters and coefficients,
+// normalisation, efficiency, energy map.
+struct DsCtx {
+    OscCoef kc;
+    float eta[4], eta_lo[4];
+    PP nrm, eff;
+    EMap em;
+};
+
+// Fills c; false (and status |= kStEscale) when the energy map is not increasing with slope in
+// (1/4, 4) on the grid. Contains a barrier.
+static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const float *pd, DsCtx &c,
+                                int *status) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
     const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
-
-    // survival parameters; mass splittings as float pairs theta0_f + (theta0_lo + delta)
+    (void)dt;
+    (void)N_t;
+    (void)C;
+    (void)nr;
+    (void)lane;
+    (void)warp;
+    (void)nw;
     // Survival parameters: mass splittings as theta0_f + (theta0_lo + delta) inside the
     // phase; the sin^2 coefficients from the exact values, in double, by one thread.
     __shared__ OscCoef kco;
-    float eta[4], eta_lo[4];
+    float *eta = c.eta, *eta_lo = c.eta_lo;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int p = m.osc_idx[i];
@@ -352,68 +366,108 @@ static __device__ double eval_dataset(const DevModel &m, int d, const float *pv,
             const int p = m.osc_idx[i];
             e[i] = p >= 0 ? m.theta0[p] + (double)pd[p] : m.osc_val_d[i];
         }
-        double c[3];
+        double cf[3];
         if (m.osc_mode == FIT_OSC_EQ1) {
             const double c2 = 0.5 * (1.0 + sqrt(fmax(1.0 - e[0], 0.0)));
-            c[0] = e[0];
-            c[1] = c2 * c2 * e[2];
-            c[2] = 0.0;
+            cf[0] = e[0];
+            cf[1] = c2 * c2 * e[2];
+            cf[2] = 0.0;
         } else {
             const double S12 = 4.0 * e[0] * (1.0 - e[0]), S13 = 4.0 * e[1] * (1.0 - e[1]);
-            c[0] = (1.0 - e[1]) * (1.0 - e[1]) * S12;
-            c[1] = S13 * (1.0 - e[0]);
-            c[2] = S13 * e[0];
+            cf[0] = (1.0 - e[1]) * (1.0 - e[1]) * S12;
+            cf[1] = S13 * (1.0 - e[0]);
+            cf[2] = S13 * e[0];
         }
         for (int i = 0; i < 3; ++i) {
-            kco.hi[i] = (float)c[i];
-            kco.lo[i] = (float)(c[i] - (double)kco.hi[i]);
+            kco.hi[i] = (float)cf[i];
+            kco.lo[i] = (float)(cf[i] - (double)kco.hi[i]);
         }
     }
     __syncthreads();
-    const OscCoef kc = kco;
-    const PP nrm = ppair(m, pv, pd, ds.norm_idx, 1.f);
-    const PP eff = ppair(m, pv, pd, ds.eff_idx, 1.f);
-    const EMap em = make_emap(m, ds, pv, pd);
+    c.kc = kco;
+    c.nrm = ppair(m, pv, pd, ds.norm_idx, 1.f);
+    c.eff = ppair(m, pv, pd, ds.eff_idx, 1.f);
+    c.em = make_emap(m, ds, pv, pd);
+    const EMap &em = c.em;
 
     // the map must be increasing with slope in (1/4, 4) everywhere on the grid
     {
         const float s0 = em.slope(m.e_edge[0]), s1 = em.slope(m.e_edge[N_t]);
         if (!(s0 > 0.25f && s0 < 4.f && s1 > 0.25f && s1 < 4.f)) {
             if (tid == 0) atomicOr(status, kStEscale);
-            return 0.0;
+            return false;
         }
     }
 
+    return true;
+}
+
+// Stage A: u_k (and with DERIV the per-bin partials the adjoint needs). Ends with a barrier.
+template <bool DERIV>
+static __device__ void ds_signal(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
+                                 EvalWs ws) {
+    const DevDataset &ds = m.ds[d];
+    const DevDetector &dt = m.det[ds.det];
+    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+    (void)dt;
+    (void)N_t;
+    (void)C;
+    (void)nr;
+    (void)lane;
+    (void)warp;
+    (void)nw;
     // ---- stage A: signal on the true grid (Eq. 1/2 x shares x reweights) -----------------
     for (int k = tid; k < N_t; k += nth) {
         const float ih = m.inv_e_hi[k], il = m.inv_e_lo[k];
         float pt = 0.f, dpt[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int c = 0; c < C; ++c) {
-            const float w = ds.w[c];
+        for (int cc = 0; cc < C; ++cc) {
+            const float w = ds.w[cc];
             if (w == 0.f) {
-                ws.pcw[c * N_t + k] = 0.f;
+                if (DERIV) ws.pcw[cc * N_t + k] = 0.f;
                 continue;
             }
-            const float ch = ds.kl_hi[c] * ih;
-            const float cl = fmaf(ds.kl_hi[c], ih, -ch) + ds.kl_hi[c] * il + ds.kl_lo[c] * ih;
+            const float ch = ds.kl_hi[cc] * ih;
+            const float cl = fmaf(ds.kl_hi[cc], ih, -ch) + ds.kl_hi[cc] * il + ds.kl_lo[cc] * ih;
             float dP[4];
-            const float P = survival(m, eta, eta_lo, kc, ch, cl, dP);
-            const PP pw = ppair(m, pv, pd, m.core_power_idx[c], 1.f);
+            const float P = survival(m, c.eta, c.eta_lo, c.kc, ch, cl, dP);
+            const PP pw = ppair(m, pv, pd, m.core_power_idx[cc], 1.f);
             const float wP = w * P;
-            ws.pcw[c * N_t + k] = wP;
+            if (DERIV) ws.pcw[cc * N_t + k] = wP;
             pt += pmul(pw, wP);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) dpt[i] = fmaf(pw.h * w, dP[i], dpt[i]);
+            for (int i = 0; i < 4; ++i) if (DERIV) dpt[i] = fmaf(pw.h * w, dP[i], dpt[i]);
         }
         const float ts = pmul(ppair(m, pv, pd, ds.shape_idx[k], 1.f), ds.t[k]);
-        ws.ts[k] = ts;
-        ws.ptot[k] = pt;
+        if (DERIV) {
+            ws.ts[k] = ts;
+            ws.ptot[k] = pt;
+        }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) ws.dp[i * N_t + k] = dpt[i];
-        ws.u[k] = pmul(nrm, ts * pt);
+        for (int i = 0; i < 4; ++i)
+            if (DERIV) ws.dp[i * N_t + k] = dpt[i];
+        ws.u[k] = pmul(c.nrm, ts * pt);
     }
     __syncthreads();
 
+}
+
+// Stage B: v = M(a) u. Ends with a barrier.
+static __device__ void ds_remap(const DevModel &m, int d, const DsCtx &c, EvalWs ws) {
+    const DevDataset &ds = m.ds[d];
+    const DevDetector &dt = m.det[ds.det];
+    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+    (void)dt;
+    (void)N_t;
+    (void)C;
+    (void)nr;
+    (void)lane;
+    (void)warp;
+    (void)nw;
+    const EMap &em = c.em;
     // ---- stage B: energy correction, gather per target bin ------------------------------
     // Source bin k covers [Y_k, Y_k+1] in grid units, Y_k = k + D(e_k). Target m gathers the
     // sources whose mapped interval overlaps [m, m+1]; overlaps are computed relative to the
@@ -441,6 +495,26 @@ static __device__ double eval_dataset(const DevModel &m, int d, const float *pv,
     }
     __syncthreads();
 
+}
+
+// Stages C and C2: fold, backgrounds, deviance, dD/dmu (ws.gmu) and the background-shape
+// gradient; returns the dataset's -2lnL (all threads). The efficiency and rate gradients are
+// added when grad != nullptr, data != nullptr and no status bit is set.
+static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
+                                     const float *data, EvalWs ws, float *grad, double *red, int *status,
+                                     float *mu_out) {
+    const DevDataset &ds = m.ds[d];
+    const DevDetector &dt = m.det[ds.det];
+    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+    (void)dt;
+    (void)N_t;
+    (void)C;
+    (void)nr;
+    (void)lane;
+    (void)warp;
+    (void)nw;
     // ---- stage C: fold into reco bins (banded rows, warp per row) ------------------------
     for (int j = warp; j < nr; j += nw) {
         const int lo = dt.row_lo[j], len = dt.row_len[j];
@@ -460,7 +534,7 @@ static __device__ double eval_dataset(const DevModel &m, int d, const float *pv,
 #pragma unroll
     for (int i = 0; i < 2 + kMaxBkgDs; ++i) part[i] = 0.f;
     for (int j = tid; j < nr; j += nth) {
-        float mu = pmul(eff, ws.f0[j]);
+        float mu = pmul(c.eff, ws.f0[j]);
 #pragma unroll
         for (int b = 0; b < kMaxBkgDs; ++b) {
             if (b >= nb) break;
@@ -506,6 +580,26 @@ static __device__ double eval_dataset(const DevModel &m, int d, const float *pv,
         }
     }
 
+    return nll_d;
+}
+
+// Stages D, E and F: adjoint of the fold, of the energy map and of the signal; adds the
+// gradient contributions to grad. Needs ws.u/ts/ptot/dp/pcw (ds_signal<true>) and ws.gmu.
+static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
+                                  EvalWs ws, float *grad, double *red) {
+    const DevDataset &ds = m.ds[d];
+    const DevDetector &dt = m.det[ds.det];
+    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+    (void)dt;
+    (void)N_t;
+    (void)C;
+    (void)nr;
+    (void)lane;
+    (void)warp;
+    (void)nw;
+    const EMap &em = c.em;
     // ---- stage D: adjoint of the fold, gv = eff R^T gmu (column bands) --------------------
     float *gv = ws.v;   // v is dead after the fold
     for (int k = tid; k < N_t; k += nth) {
@@ -516,7 +610,7 @@ static __device__ double eval_dataset(const DevModel &m, int d, const float *pv,
             if (j >= nr) break;
             s = fmaf(dt.rcol[b * N_t + k], ws.gmu[j], s);
         }
-        gv[k] = pmul(eff, s);
+        gv[k] = pmul(c.eff, s);
     }
     __syncthreads();
 
@@ -546,14 +640,14 @@ static __device__ double eval_dataset(const DevModel &m, int d, const float *pv,
         ep[1] += (A0 * e0 + A1 * e1) * em.inv_de;
         ep[2] += (A0 * e0 * e0 + A1 * e1 * e1) * em.inv_de;
         const float ts = ws.ts[k], pt = ws.ptot[k];
-        const float gb = pmul(nrm, gu * ts);    // d nll / d(ptot)
+        const float gb = pmul(c.nrm, gu * ts);    // d nll / d(ptot)
 #pragma unroll
         for (int i = 0; i < 4; ++i) ep[3 + i] = fmaf(gb, ws.dp[i * N_t + k], ep[3 + i]);
         ep[7] = fmaf(gu * ts, pt, ep[7]);
 #pragma unroll
-        for (int c = 0; c < FIT_MAX_CORES; ++c)
-            if (c < C) ep[8 + c] = fmaf(gb, ws.pcw[c * N_t + k], ep[8 + c]);
-        ws.dp[k] = pmul(nrm, gu * ds.t[k] * pt);    // d nll / d s for this bin (dp0 reused)
+        for (int cc = 0; cc < FIT_MAX_CORES; ++cc)
+            if (cc < C) ep[8 + cc] = fmaf(gb, ws.pcw[cc * N_t + k], ep[8 + cc]);
+        ws.dp[k] = pmul(c.nrm, gu * ds.t[k] * pt);    // d nll / d s for this bin (dp0 reused)
     }
     double etot[8 + FIT_MAX_CORES];
     block_sum<8 + FIT_MAX_CORES>(ep, red, etot);
@@ -564,8 +658,8 @@ static __device__ double eval_dataset(const DevModel &m, int d, const float *pv,
             if (m.osc_idx[i] >= 0) grad[m.osc_idx[i]] += (float)etot[3 + i];
         if (ds.norm_idx >= 0) grad[ds.norm_idx] += (float)etot[7];
 #pragma unroll
-        for (int c = 0; c < FIT_MAX_CORES; ++c)
-            if (c < C && m.core_power_idx[c] >= 0) grad[m.core_power_idx[c]] += (float)etot[8 + c];
+        for (int cc = 0; cc < FIT_MAX_CORES; ++cc)
+            if (cc < C && m.core_power_idx[cc] >= 0) grad[m.core_power_idx[cc]] += (float)etot[8 + cc];
     }
     // ---- stage F: shape reweights (one thread per distinct parameter, CSR over bins) -----
     for (int i = tid; i < ds.n_sp; i += nth) {
@@ -574,6 +668,24 @@ static __device__ double eval_dataset(const DevModel &m, int d, const float *pv,
         grad[ds.sp_param[i]] += s;
     }
     __syncthreads();
+}
+
+// One dataset in one sequence: adds its Poisson -2lnL and (if grad != nullptr) its gradient
+// contributions (theta space, P floats). Returns the dataset's -2lnL (all threads); *status |=
+// kSt* bits on failure.
+static __device__ double eval_dataset(const DevModel &m, int d, const float *pv, const float *pd,
+                                      const float *data, EvalWs ws, float *grad, double *red,
+                                      int *status, float *mu_out) {
+    DsCtx c;
+    if (!ds_setup(m, d, pv, pd, c, status)) return 0.0;
+    if (grad != nullptr && data != nullptr)
+        ds_signal<true>(m, d, pv, pd, c, ws);
+    else
+        ds_signal<false>(m, d, pv, pd, c, ws);
+    ds_remap(m, d, c, ws);
+    const double nll_d = ds_fold_lik(m, d, pv, pd, c, data, ws, grad, red, status, mu_out);
+    if (data == nullptr || grad == nullptr || (*(volatile int *)status) != 0) return nll_d;
+    ds_adjoint(m, d, pv, pd, c, ws, grad, red);
     return nll_d;
 }
 

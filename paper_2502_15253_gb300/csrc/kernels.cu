@@ -151,19 +151,34 @@ size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem) {
 constexpr int kMaxHist = 16;
 constexpr int kNDots = 4 * kMaxHist + 1;
 
-struct FitSmem {
-    DevModel m;
-    double red[kMaxWarps * 24 + 24];
+// Minimiser state of one fit between two evaluations: in shared memory while a block works on
+// the fit, in global memory between the launches of the lockstep engine.
+constexpr int kPhStart = 0, kPhTrial = 1, kPhDone = 2;
+
+struct FitState {
     // L-BFGS history in scalars: SY[i][j] = s_i.y_j (needed for i older than j and i = j),
     // YY[i][j] = y_i.y_j (symmetric), rho_i = 1 / s_i.y_i, by history slot
     double SY[kMaxHist][kMaxHist], YY[kMaxHist][kMaxHist];
-    double rho[kMaxHist], alf[kMaxHist], bet[kMaxHist];
+    double rho[kMaxHist];
+    double gamma;
+    double f, edm;
+    // line search on phi(alpha) = f(z + alpha d): bracket [lo, hi], kink crossing a_cr
+    double alpha, dphi0, eps_f, lo, flo, dlo, hi, fhi, dhi, a_cr, f_cr;
+    int hn, head, occ;
+    int phase, ls_it, have_lo, pending, restarts_left, since_restart;
+    int iters, n_evals, status;
+    int pad;
+};
+
+struct FitSmem {
+    DevModel m;
+    double red[kMaxWarps * 24 + 24];
+    FitState st;
     double dots[kNDots];       // fused pass: S.y_new | Y.y_new | S.g | Y.g | g.g
     float cs[kMaxHist], cy[kMaxHist];   // d = -(cg g + sum cs_j s_j + sum cy_j y_j)
     float cg;
-    double gHg, gamma;
-    int hn, head, occ;
-    int status;
+    double gHg;
+    int status;                // evaluation status bits
     int inst;
 };
 
@@ -237,47 +252,47 @@ __device__ void lbfgs_scalars(FitSmem &S, int hist_max, bool pending) {
     const int lane = threadIdx.x & 31;
     const double *dt = S.dots;
     if (pending && lane == 0) {
-        const int c = S.head;
+        const int c = S.st.head;
         const double sy = dt[c], yy = dt[kMaxHist + c];
         if (sy > 1e-10 * yy && yy > 0.0) {
             for (int j = 0; j < hist_max; ++j)
-                if (((S.occ >> j) & 1) && j != c) {
-                    S.SY[j][c] = dt[j];
-                    S.YY[j][c] = S.YY[c][j] = dt[kMaxHist + j];
+                if (((S.st.occ >> j) & 1) && j != c) {
+                    S.st.SY[j][c] = dt[j];
+                    S.st.YY[j][c] = S.st.YY[c][j] = dt[kMaxHist + j];
                 }
-            S.SY[c][c] = sy;
-            S.YY[c][c] = yy;
-            S.rho[c] = 1.0 / sy;
-            S.occ |= 1u << c;
-            S.head = (c + 1) % hist_max;
-            S.hn = min(S.hn + 1, hist_max);
-            S.gamma = sy / yy;
-        } else if ((S.occ >> c) & 1) {
+            S.st.SY[c][c] = sy;
+            S.st.YY[c][c] = yy;
+            S.st.rho[c] = 1.0 / sy;
+            S.st.occ |= 1u << c;
+            S.st.head = (c + 1) % hist_max;
+            S.st.hn = min(S.st.hn + 1, hist_max);
+            S.st.gamma = sy / yy;
+        } else if ((S.st.occ >> c) & 1) {
             // rejected pair written over the oldest one: that pair is gone as well
-            S.occ &= ~(1u << c);
-            S.hn -= 1;
+            S.st.occ &= ~(1u << c);
+            S.st.hn -= 1;
         }
     }
     __syncwarp();
-    const int hn = S.hn, oldest = (S.head - hn + hist_max) % hist_max;
-    const double gam = S.gamma, gg = dt[kNDots - 1];
+    const int hn = S.st.hn, oldest = (S.st.head - hn + hist_max) % hist_max;
+    const double gam = S.st.gamma, gg = dt[kNDots - 1];
     const bool live = lane < hn;
     const int sl = live ? (oldest + lane) % hist_max : 0;    // this lane's history slot
     const double sg = live ? dt[2 * kMaxHist + sl] : 0.0, yg = live ? dt[3 * kMaxHist + sl] : 0.0;
-    const double rho = live ? S.rho[sl] : 0.0;
+    const double rho = live ? S.st.rho[sl] : 0.0;
     // alpha_k = rho_k (s_k.g - sum_{l > k} alpha_l s_k.y_l), newest first
     double acc = sg, alpha = 0.0;
     for (int l = hn - 1; l >= 0; --l) {
         const double al = __shfl_sync(0xffffffffu, rho * acc, l);
         if (lane == l) alpha = al;
         const int sll = (oldest + l) % hist_max;
-        if (lane < l) acc -= al * S.SY[sl][sll];
+        if (lane < l) acc -= al * S.st.SY[sl][sll];
     }
     // u_k = sum_l alpha_l y_k.y_l
     double u = 0.0;
     for (int l = 0; l < hn; ++l) {
         const double al = __shfl_sync(0xffffffffu, alpha, l);
-        if (live) u += al * S.YY[sl][(oldest + l) % hist_max];
+        if (live) u += al * S.st.YY[sl][(oldest + l) % hist_max];
     }
     // beta_k = rho_k (gam (y_k.g - u_k) + sum_{l < k} (alpha_l - beta_l) s_l.y_k), oldest first
     double acc2 = gam * (yg - u), beta = 0.0;
@@ -285,7 +300,7 @@ __device__ void lbfgs_scalars(FitSmem &S, int hist_max, bool pending) {
         const double bl = __shfl_sync(0xffffffffu, rho * acc2, l);
         const double cl = __shfl_sync(0xffffffffu, alpha, l) - bl;
         if (lane == l) beta = bl;
-        if (live && lane > l) acc2 += cl * S.SY[(oldest + l) % hist_max][sl];
+        if (live && lane > l) acc2 += cl * S.st.SY[(oldest + l) % hist_max][sl];
     }
     const double cs = alpha - beta, cy = -gam * alpha;
     double part = live ? cs * sg + cy * yg : 0.0;
@@ -306,10 +321,10 @@ __device__ void lbfgs_scalars(FitSmem &S, int hist_max, bool pending) {
     if (!(ghg > 0.0)) {   // not a descent direction: drop the history, steepest descent
         if (lane < kMaxHist) S.cs[lane] = S.cy[lane] = 0.f;
         if (lane == 0) {
-            S.hn = 0;
-            S.occ = 0;
-            S.head = 0;
-            S.gamma = 1.0;
+            S.st.hn = 0;
+            S.st.occ = 0;
+            S.st.head = 0;
+            S.st.gamma = 1.0;
             S.cg = 1.f;
         }
         ghg = gg;
@@ -346,6 +361,42 @@ __device__ void theta_of_z(const DevModel &m, const float *z, float *pv, float *
     __syncthreads();
 }
 
+// Prior in z space and the chain rule back to z: gz = J^T gth + 2 z over the constrained
+// coordinates (J = diag(scale) outside the prior blocks, the Cholesky factor L inside);
+// returns the prior |z|^2 (all threads).
+__device__ double eval_z_prior(const DevModel &m, const float *z, const float *gth, float *gz, double *red) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    float acc[1] = {0.f};
+    for (int i = tid; i < m.P; i += nth) {
+        const float s = m.zscale[i];
+        if (s > 0.f) {
+            const bool con = m.prior_inv[i] > 0.f;
+            gz[i] = s * gth[i] + (con ? 2.f * z[i] : 0.f);
+            if (con) acc[0] = fmaf(z[i], z[i], acc[0]);
+        }
+    }
+    for (int b = 0; b < m.n_blocks; ++b) {
+        const int n = m.blk_size[b];
+        const int *idx = m.blk_idx + m.blk_idx_off[b];
+        const float *L = m.blk_L + m.blk_mat_off[b];   // L, row-major: (L^T g)_j = sum_i L_ij g_i
+        for (int j = tid; j < n; j += nth) {
+            float s0 = 0.f, s1 = 0.f;
+            int i = j;
+            for (; i + 1 < n; i += 2) {
+                s0 = fmaf(L[(int64_t)i * n + j], gth[idx[i]], s0);
+                s1 = fmaf(L[(int64_t)(i + 1) * n + j], gth[idx[i + 1]], s1);
+            }
+            if (i < n) s0 = fmaf(L[(int64_t)i * n + j], gth[idx[i]], s0);
+            const float zj = z[idx[j]];
+            gz[idx[j]] = (s0 + s1) + 2.f * zj;
+            acc[0] = fmaf(zj, zj, acc[0]);
+        }
+    }
+    double tot[1];
+    block_sum<1>(acc, red, tot);
+    return tot[0];
+}
+
 // -2lnL(theta(z)) and its z-gradient gz. Returns +inf on an invalid point.
 __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &V, EvalWs ws,
                          const float *data, uint32_t mask, FitSmem &S) {
@@ -360,37 +411,7 @@ __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &
         __syncthreads();
         if (S.status) return INFINITY;
     }
-    // prior = |z|^2 over constrained coordinates; gz = J^T gth + 2 z
-    const int tid = threadIdx.x, nth = blockDim.x;
-    float acc[1] = {0.f};
-    for (int i = tid; i < m.P; i += nth) {
-        const float s = m.zscale[i];
-        if (s > 0.f) {
-            const bool con = m.prior_inv[i] > 0.f;
-            gz[i] = s * V.gth[i] + (con ? 2.f * z[i] : 0.f);
-            if (con) acc[0] = fmaf(z[i], z[i], acc[0]);
-        }
-    }
-    for (int b = 0; b < m.n_blocks; ++b) {
-        const int n = m.blk_size[b];
-        const int *idx = m.blk_idx + m.blk_idx_off[b];
-        const float *L = m.blk_L + m.blk_mat_off[b];   // L, row-major: (L^T g)_j = sum_i L_ij g_i
-        for (int j = tid; j < n; j += nth) {
-            float s0 = 0.f, s1 = 0.f;
-            int i = j;
-            for (; i + 1 < n; i += 2) {
-                s0 = fmaf(L[(int64_t)i * n + j], V.gth[idx[i]], s0);
-                s1 = fmaf(L[(int64_t)(i + 1) * n + j], V.gth[idx[i + 1]], s1);
-            }
-            if (i < n) s0 = fmaf(L[(int64_t)i * n + j], V.gth[idx[i]], s0);
-            const float zj = z[idx[j]];
-            gz[idx[j]] = (s0 + s1) + 2.f * zj;
-            acc[0] = fmaf(zj, zj, acc[0]);
-        }
-    }
-    double tot[1];
-    block_sum<1>(acc, S.red, tot);
-    return nll + tot[0];
+    return nll + eval_z_prior(m, z, V.gth, gz, S.red);
 }
 
 // cubic minimiser through (a, fa, ga), (b, fb, gb), or the secant of the slopes when the
@@ -421,6 +442,307 @@ __device__ __forceinline__ void vcopy(float *dst, const float *src, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+struct FitParams {
+    int hist, max_iter, max_ls, restarts;
+    double edm_tol, f_noise_rel;
+    uint64_t deadline;         // %globaltimer value past which a fit stops with TIMEOUT
+};
+
+__device__ __forceinline__ void reset_history(FitState &st) {
+    st.hn = 0;
+    st.head = 0;
+    st.occ = 0;
+    st.gamma = 1.0;
+}
+
+// One step of the minimiser: consumes the evaluation (fa, V.gt) of the point V.zt and leaves
+// the next point to evaluate in V.zt (returns true), or ends the fit (returns false, S.st.phase
+// = kPhDone, S.st.status set). Block-wide; every thread holds the same copies of the scalars.
+//
+// L-BFGS in whitened coordinates with the two-loop recursion on scalars (fused_dots,
+// lbfgs_scalars). Line search on phi(alpha) = f(z + alpha d): accepts a strong-Wolfe point or
+// the approximate-Wolfe point of Hager & Zhang (value within the noise allowance eps_f, slope
+// condition), brackets with cubic / secant interpolation, and falls back to the smallest trial
+// that crossed a kink (value not increased, slope risen past c2 phi'(0)) or to the best lower
+// point. A failed search with a history retries from steepest descent. Stop: EDM =
+// 1/2 g^T H g < edm_tol (optionally after `restarts` history rebuilds), max_iter, or the clock.
+__device__ bool fit_decide(FitSmem &S, FitVecs &V, int P, double fa, const FitParams &F) {
+    const double c1 = 1e-4, c2 = 0.9;
+    const int tid = threadIdx.x;
+    FitState &st = S.st;
+    __syncthreads();
+    // block-uniform copies of the scalars
+    double f = st.f, edm = st.edm;
+    double alpha = st.alpha, dphi0 = st.dphi0, eps_f = st.eps_f;
+    double lo = st.lo, flo = st.flo, dlo = st.dlo, hi = st.hi, fhi = st.fhi, dhi = st.dhi;
+    double a_cr = st.a_cr, f_cr = st.f_cr;
+    int phase = st.phase, ls_it = st.ls_it, restarts_left = st.restarts_left, since_restart = st.since_restart;
+    int iters = st.iters, n_evals = st.n_evals + 1, status = st.status;
+    bool have_lo = st.have_lo != 0, pending = st.pending != 0;
+    __syncthreads();
+
+    enum { kDirection, kTrial, kDone } next = kDirection;
+    if (phase == kPhStart) {
+        // the start point's evaluation
+        f = fa;
+        vcopy(V.z, V.zt, P);
+        vcopy(V.g, V.gt, P);
+        if (tid == 0) reset_history(st);
+        restarts_left = F.restarts;
+        since_restart = F.hist;
+        pending = false;
+        if (!isfinite(f)) {
+            status = FIT_STATUS_NONFINITE;
+            next = kDone;
+        }
+    } else {
+        // ---- a line-search trial at alpha came back -------------------------------------
+        const double da = isfinite(fa) ? bdot(V.gt, V.d, P, S.red) : INFINITY;
+        const bool armijo = fa <= f + c1 * alpha * dphi0;
+        const bool approx = fa <= f + eps_f;
+        const bool val_ok = isfinite(fa) && (armijo || approx);
+        bool accepted = false, stop = false;
+        double f_acc = fa;
+        if (val_ok && fabs(da) <= -c2 * dphi0) {
+            accepted = true;
+        } else {
+            if (val_ok && da >= c2 * dphi0 && alpha < a_cr) {   // crossed a kink
+                a_cr = alpha;
+                f_cr = fa;
+                vcopy(V.zcr, V.zt, P);
+                vcopy(V.gcr, V.gt, P);
+            }
+            if (!val_ok || fa > flo + eps_f || da >= 0.0) {
+                hi = alpha;
+                fhi = fa;
+                dhi = da;
+            } else {
+                lo = alpha;
+                flo = fa;
+                dlo = da;
+                have_lo = true;
+                vcopy(V.zlo, V.zt, P);
+                vcopy(V.glo, V.gt, P);
+            }
+            __syncthreads();
+            if (!isfinite(hi)) {
+                alpha = 4.0 * alpha;
+            } else {
+                alpha = ls_interp(lo, flo, dlo, hi, fhi, dhi, eps_f);
+                if (hi - lo <= 1e-7 * hi) stop = true;
+            }
+            if (!stop && ++ls_it < F.max_ls) next = kTrial;
+        }
+        if (next != kTrial) {
+            if (!accepted) {
+                if (isfinite(a_cr)) {
+                    vcopy(V.zt, V.zcr, P);
+                    vcopy(V.gt, V.gcr, P);
+                    f_acc = f_cr;
+                    accepted = true;
+                } else if (have_lo) {
+                    vcopy(V.zt, V.zlo, P);
+                    vcopy(V.gt, V.glo, P);
+                    f_acc = flo;
+                    accepted = true;
+                }
+                __syncthreads();
+            }
+            if (accepted) {
+                // curvature pair into the next slot; folded in by the next fused pass
+                const int c = st.head;
+                float *s_new = V.S + (int64_t)c * P, *y_new = V.Y + (int64_t)c * P;
+                for (int i = tid; i < P; i += blockDim.x) {
+                    s_new[i] = V.zt[i] - V.z[i];
+                    y_new[i] = V.gt[i] - V.g[i];
+                    V.z[i] = V.zt[i];
+                    V.g[i] = V.gt[i];
+                }
+                pending = true;
+                f = f_acc;
+                iters++;
+                since_restart++;
+            } else if (st.hn > 0) {   // retry from steepest descent
+                __syncthreads();
+                if (tid == 0) reset_history(st);
+            } else {
+                status = FIT_STATUS_LINESEARCH_FAIL;
+                next = kDone;
+            }
+        }
+    }
+
+    // ---- direction d = -H g: fused dot products, scalar two-loop, one combination ------------
+    while (next == kDirection) {
+        __syncthreads();
+        fused_dots(V.S, V.Y, pending ? V.Y + (int64_t)st.head * P : nullptr, V.g, P,
+                   (unsigned)st.occ | (pending ? 1u << st.head : 0u), S.dots);
+        if (tid < 32) lbfgs_scalars(S, F.hist, pending);
+        pending = false;
+        __syncthreads();
+        {
+            const float cg = S.cg;
+            const unsigned occ = (unsigned)st.occ;
+            for (int i = tid; i < P; i += blockDim.x) {
+                float h = cg * V.g[i];
+                for (int j = 0; j < F.hist; ++j)
+                    if ((occ >> j) & 1u) {
+                        h = fmaf(S.cs[j], V.S[(int64_t)j * P + i], h);
+                        h = fmaf(S.cy[j], V.Y[(int64_t)j * P + i], h);
+                    }
+                V.d[i] = -h;
+            }
+        }
+        __syncthreads();
+        const double gd = -S.gHg;
+        const int hn = st.hn;
+        edm = -0.5 * gd;
+        if (edm < F.edm_tol && since_restart >= F.hist) {
+            if (restarts_left == 0) {
+                status = FIT_STATUS_CONVERGED;
+                next = kDone;
+                break;
+            }
+            // drop the history and rebuild it (at least hist iterations): the fresh pairs come
+            // from the directions still moving, the flat ones a short history may not have seen
+            --restarts_left;
+            since_restart = 0;
+            __syncthreads();
+            if (tid == 0) reset_history(st);
+            continue;
+        }
+        if (iters >= F.max_iter) {
+            status = FIT_STATUS_MAXITER;
+            next = kDone;
+            break;
+        }
+        if (global_ns() > F.deadline) {
+            status = FIT_STATUS_TIMEOUT;
+            next = kDone;
+            break;
+        }
+        // first trial: the unit step, or a step of length 1 along steepest descent
+        dphi0 = gd;
+        eps_f = F.f_noise_rel * (1.0 + fabs(f));
+        if (hn == 0) {
+            const double dn = (double)S.cg * sqrt(S.dots[kNDots - 1]);
+            alpha = fmin(1.0, 1.0 / fmax(dn, 1e-30));
+        } else {
+            alpha = 1.0;
+        }
+        lo = 0.0;
+        flo = f;
+        dlo = dphi0;
+        hi = fhi = dhi = INFINITY;
+        a_cr = INFINITY;
+        f_cr = 0.0;
+        have_lo = false;
+        ls_it = 0;
+        next = kTrial;
+    }
+    if (next == kTrial) {
+        const float af = (float)alpha;
+        for (int i = tid; i < P; i += blockDim.x) V.zt[i] = fmaf(af, V.d[i], V.z[i]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        st.f = f;
+        st.edm = edm;
+        st.alpha = alpha;
+        st.dphi0 = dphi0;
+        st.eps_f = eps_f;
+        st.lo = lo;
+        st.flo = flo;
+        st.dlo = dlo;
+        st.hi = hi;
+        st.fhi = fhi;
+        st.dhi = dhi;
+        st.a_cr = a_cr;
+        st.f_cr = f_cr;
+        st.phase = next == kTrial ? kPhTrial : kPhDone;
+        st.ls_it = ls_it;
+        st.have_lo = have_lo;
+        st.pending = pending;
+        st.restarts_left = restarts_left;
+        st.since_restart = since_restart;
+        st.iters = iters;
+        st.n_evals = n_evals;
+        st.status = status;
+    }
+    __syncthreads();
+    return next == kTrial;
+}
+
+__device__ __forceinline__ void init_state(FitState &st) {
+    st.phase = kPhStart;
+    st.f = INFINITY;
+    st.edm = INFINITY;
+    st.iters = 0;
+    st.n_evals = 0;
+    st.status = FIT_STATUS_MAXITER;
+    st.pending = 0;
+    st.have_lo = 0;
+    st.ls_it = 0;
+    reset_history(st);
+}
+
+// Start point z0 = J^-1 (theta_start - theta0) into z (theta_start = theta0 if st == nullptr);
+// pd is scratch. Ends with a barrier.
+__device__ void start_z(const DevModel &m, const double *st, float *z, float *pd) {
+    const int tid = threadIdx.x, P = m.P;
+    for (int i = tid; i < P; i += blockDim.x) {
+        const float dd = st ? (float)(st[i] - m.theta0[i]) : 0.f;
+        pd[i] = dd;
+        const float s = m.zscale[i];
+        if (s > 0.f) z[i] = dd / s;
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int b = 0; b < m.n_blocks; ++b) {
+        const int n = m.blk_size[b];
+        const int *idx = m.blk_idx + m.blk_idx_off[b];
+        const float *W = m.blk_W + m.blk_mat_off[b];
+        for (int i = warp; i < n; i += nw) {
+            float s = 0.f;
+            for (int j = lane; j <= i; j += 32) s = fmaf(W[(int64_t)i * n + j], pd[idx[j]], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) z[idx[i]] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Result: theta = theta0 + J z in double, and the fit's summary.
+__device__ void write_result(const DevModel &m, const FitState &st, const float *z, double *best,
+                             fit_result *out) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < m.P; i += blockDim.x) {
+        const float s = m.zscale[i];
+        if (s > 0.f) best[i] = m.theta0[i] + (double)s * (double)z[i];
+    }
+    for (int b = 0; b < m.n_blocks; ++b) {
+        const int n = m.blk_size[b];
+        const int *idx = m.blk_idx + m.blk_idx_off[b];
+        const double *L = m.blk_L64 + m.blk_mat_off[b];
+        for (int i = tid; i < n; i += blockDim.x) {
+            double s = 0.0;
+            for (int j = 0; j <= i; ++j) s += L[(int64_t)i * n + j] * (double)z[idx[j]];
+            best[idx[i]] = m.theta0[idx[i]] + s;
+        }
+    }
+    if (tid == 0) {
+        fit_result r;
+        r.nll_min = st.f;
+        r.edm = st.edm;
+        r.iters = st.iters;
+        r.n_evals = st.n_evals;
+        r.status = st.status;
+        r.pad = 0;
+        *out = r;
+    }
+}
+
 // At most 128 threads; MINB resident blocks per SM (4: <= 128 registers, 5: <= 96). Each block
 // fits one instance at a time, so MINB instances share an SM and cover each other's barrier and
 // load latencies. With the working set in shared memory four blocks of the larger register
@@ -431,10 +753,15 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
     FitSmem &S = *reinterpret_cast<FitSmem *>(smem_raw);
     float *dyn = reinterpret_cast<float *>(smem_raw + sizeof(FitSmem));
     float *gws = A.ws_global + (int64_t)blockIdx.x * A.ws_stride;
-    const uint64_t deadline = global_ns() + A.budget_ns;   // per-block clock budget
+    FitParams F;
+    F.hist = A.hist;
+    F.max_iter = A.max_iter;
+    F.max_ls = A.max_ls;
+    F.restarts = A.restarts;
+    F.edm_tol = A.edm_tol;
+    F.f_noise_rel = A.f_noise_rel;
+    F.deadline = global_ns() + A.budget_ns;   // per-block clock budget
     const int tid = threadIdx.x;
-    const int hist_max = A.hist;
-    const double c1 = 1e-4, c2 = 0.9;
 
     while (true) {
         if (tid == 0) S.inst = atomicAdd(A.queue, 1);
@@ -450,233 +777,235 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
         // they fit, else in this block's global slice; the history in shared memory after them
         // unless it is placed in the global slice (hist_global)
         // (global slice: history first, then the rest)
-        const int hfl = fit_hist_floats(P, hist_max), loc = 12 * P + m.ws_eval_floats;
+        const int hfl = fit_hist_floats(P, F.hist), loc = 12 * P + m.ws_eval_floats;
         const bool loc_smem = loc + (A.hist_global ? 0 : hfl) <= A.smem_floats;
         float *base = loc_smem ? dyn : gws + (A.hist_global ? hfl : 0);
         float *hbase = A.hist_global ? gws : base + loc;
-        FitVecs V = carve_fit_vecs(base, hbase, P, hist_max);
+        FitVecs V = carve_fit_vecs(base, hbase, P, F.hist);
         const EvalWs ws = carve_eval_ws(base + 12 * P, m.N_t, m.C, m.max_reco);
         const float *data = A.data + in.data_off;
-        fit_result res;
-        res.iters = 0;
-        res.n_evals = 0;
-        res.edm = INFINITY;
-        res.nll_min = INFINITY;
-        res.pad = 0;
-        int status = FIT_STATUS_MAXITER;
-
-        if (global_ns() > deadline) {
-            status = FIT_STATUS_TIMEOUT;
+        if (tid == 0) init_state(S.st);
+        __syncthreads();
+        if (global_ns() > F.deadline) {
             for (int i = tid; i < P; i += blockDim.x) V.z[i] = 0.f;
+            if (tid == 0) S.st.status = FIT_STATUS_TIMEOUT;
             __syncthreads();
         } else {
-            // start point z0 = J^-1 (theta_start - theta0)
-            const double *st = A.start ? A.start + in.param_off : nullptr;
-            for (int i = tid; i < P; i += blockDim.x) {
-                const float dd = st ? (float)(st[i] - m.theta0[i]) : 0.f;
-                V.pd[i] = dd;
-                const float s = m.zscale[i];
-                if (s > 0.f) V.z[i] = dd / s;
+            start_z(m, A.start ? A.start + in.param_off : nullptr, V.zt, V.pd);
+            while (true) {
+                const double fa = eval_z(m, V.zt, V.gt, V, ws, data, in.mask, S);
+                if (!fit_decide(S, V, P, fa, F)) break;
             }
-            __syncthreads();
-            {
-                const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-                for (int b = 0; b < m.n_blocks; ++b) {
-                    const int n = m.blk_size[b];
-                    const int *idx = m.blk_idx + m.blk_idx_off[b];
-                    const float *W = m.blk_W + m.blk_mat_off[b];
-                    for (int i = warp; i < n; i += nw) {
-                        float s = 0.f;
-                        for (int j = lane; j <= i; j += 32) s = fmaf(W[(int64_t)i * n + j], V.pd[idx[j]], s);
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                        if (lane == 0) V.z[idx[i]] = s;
-                    }
-                }
-            }
-            __syncthreads();
+        }
+        write_result(m, S.st, V.z, A.best + in.param_off, A.results + ii);
+        __syncthreads();
+    }
+}
 
-            double f = eval_z(m, V.z, V.g, V, ws, data, in.mask, S);
-            res.n_evals = 1;
-            if (!isfinite(f)) status = FIT_STATUS_NONFINITE;
-            if (tid == 0) {
-                S.hn = 0;
-                S.head = 0;
-                S.occ = 0;
-                S.gamma = 1.0;
-            }
-            // After the first EDM convergence the history can be dropped and rebuilt (at
-            // least hist_max iterations) up to A.restarts times: the fresh pairs come from the
-            // directions still moving, the flat ones a short history may not have seen.
-            int restarts_left = A.restarts, since_restart = hist_max;
-            bool pending = false;
-            while (status == FIT_STATUS_MAXITER) {
-                // ---- direction d = -H g: fused dot products, scalar two-loop, one combination
-                __syncthreads();
-                fused_dots(V.S, V.Y, pending ? V.Y + (int64_t)S.head * P : nullptr, V.g, P,
-                           (unsigned)S.occ | (pending ? 1u << S.head : 0u), S.dots);
-                if (tid < 32) lbfgs_scalars(S, hist_max, pending);
-                pending = false;
-                __syncthreads();
-                {
-                    const float cg = S.cg;
-                    const unsigned occ = (unsigned)S.occ;
-                    for (int i = tid; i < P; i += blockDim.x) {
-                        float h = cg * V.g[i];
-                        for (int j = 0; j < hist_max; ++j)
-                            if ((occ >> j) & 1u) {
-                                h = fmaf(S.cs[j], V.S[(int64_t)j * P + i], h);
-                                h = fmaf(S.cy[j], V.Y[(int64_t)j * P + i], h);
-                            }
-                        V.d[i] = -h;
-                    }
-                }
-                __syncthreads();
-                const double gd = -S.gHg;
-                const int hn = S.hn;
-                const double edm = -0.5 * gd;
-                res.edm = edm;
-                if (edm < A.edm_tol && since_restart >= hist_max) {
-                    if (restarts_left == 0) {
-                        status = FIT_STATUS_CONVERGED;
-                        break;
-                    }
-                    --restarts_left;
-                    since_restart = 0;
-                    __syncthreads();
-                    if (tid == 0) {
-                        S.hn = 0;
-                        S.head = 0;
-                        S.occ = 0;
-                    }
-                    continue;
-                }
-                if (res.iters >= A.max_iter) break;
-                if (global_ns() > deadline) {
-                    status = FIT_STATUS_TIMEOUT;
-                    break;
-                }
+// ------------------------------------------------------------------------------------
+// lockstep engine
+// ------------------------------------------------------------------------------------
+size_t ls_state_bytes() { return sizeof(FitState); }
+size_t ls_step_smem_bytes() { return sizeof(FitSmem); }
 
-                // ---- line search on phi(alpha) = f(z + alpha d) -----------------------------
-                const double dphi0 = gd;
-                const double eps_f = A.f_noise_rel * (1.0 + fabs(f));
-                double alpha;
-                if (hn == 0) {   // |d| = cg |g| with the history empty
-                    const double dn = (double)S.cg * sqrt(S.dots[kNDots - 1]);
-                    alpha = fmin(1.0, 1.0 / fmax(dn, 1e-30));
-                } else {
-                    alpha = 1.0;
-                }
-                double lo = 0.0, flo = f, dlo = dphi0, hi = INFINITY, fhi = INFINITY, dhi = INFINITY;
-                double a_cr = INFINITY, f_cr = 0.0;
-                bool have_lo = false, accepted = false;
-                double fa = 0.0;
-                for (int it = 0; it < A.max_ls; ++it) {
-                    const float af = (float)alpha;
-                    for (int i = tid; i < P; i += blockDim.x) V.zt[i] = fmaf(af, V.d[i], V.z[i]);
-                    __syncthreads();
-                    fa = eval_z(m, V.zt, V.gt, V, ws, data, in.mask, S);
-                    res.n_evals++;
-                    const double da = isfinite(fa) ? bdot(V.gt, V.d, P, S.red) : INFINITY;
-                    const bool armijo = fa <= f + c1 * alpha * dphi0;
-                    const bool approx = fa <= f + eps_f;
-                    const bool val_ok = isfinite(fa) && (armijo || approx);
-                    if (val_ok && fabs(da) <= -c2 * dphi0) {
-                        accepted = true;
-                        break;
-                    }
-                    if (val_ok && da >= c2 * dphi0 && alpha < a_cr) {   // crossed a kink
-                        a_cr = alpha;
-                        f_cr = fa;
-                        vcopy(V.zcr, V.zt, P);
-                        vcopy(V.gcr, V.gt, P);
-                    }
-                    if (!val_ok || fa > flo + eps_f || da >= 0.0) {
-                        hi = alpha;
-                        fhi = fa;
-                        dhi = da;
-                    } else {
-                        lo = alpha;
-                        flo = fa;
-                        dlo = da;
-                        have_lo = true;
-                        vcopy(V.zlo, V.zt, P);
-                        vcopy(V.glo, V.gt, P);
-                    }
-                    __syncthreads();
-                    if (!isfinite(hi)) {
-                        alpha = 4.0 * alpha;
-                    } else {
-                        alpha = ls_interp(lo, flo, dlo, hi, fhi, dhi, eps_f);
-                        if (hi - lo <= 1e-7 * hi) break;
-                    }
-                }
-                if (!accepted) {
-                    if (isfinite(a_cr)) {
-                        vcopy(V.zt, V.zcr, P);
-                        vcopy(V.gt, V.gcr, P);
-                        fa = f_cr;
-                        accepted = true;
-                    } else if (have_lo) {
-                        vcopy(V.zt, V.zlo, P);
-                        vcopy(V.gt, V.glo, P);
-                        fa = flo;
-                        accepted = true;
-                    }
-                    __syncthreads();
-                }
-                if (!accepted) {
-                    if (hn > 0) {   // retry from steepest descent
-                        __syncthreads();
-                        if (tid == 0) {
-                            S.hn = 0;
-                            S.head = 0;
-                            S.occ = 0;
-                            S.gamma = 1.0;
-                        }
-                        continue;
-                    }
-                    status = FIT_STATUS_LINESEARCH_FAIL;
-                    break;
-                }
-                // ---- curvature pair into the next slot; folded in by the next fused pass ---
-                {
-                    const int c = S.head;
-                    float *s_new = V.S + (int64_t)c * P, *y_new = V.Y + (int64_t)c * P;
-                    for (int i = tid; i < P; i += blockDim.x) {
-                        s_new[i] = V.zt[i] - V.z[i];
-                        y_new[i] = V.gt[i] - V.g[i];
-                        V.z[i] = V.zt[i];
-                        V.g[i] = V.gt[i];
-                    }
-                    pending = true;
-                }
-                f = fa;
-                res.iters++;
-                since_restart++;
+struct LsEvalSmem {
+    DevModel m;
+    double red[kMaxWarps * 24 + 24];
+    int status;
+};
+
+size_t ls_eval_smem_bytes(int P, int ws_floats) {
+    return sizeof(LsEvalSmem) + sizeof(float) * (2 * (size_t)P + (size_t)ws_floats);
+}
+
+__device__ __forceinline__ FitVecs ls_vecs(const LsArgs &A, int g, int P) {
+    float *base = A.vec + (int64_t)g * A.vec_stride;
+    return carve_fit_vecs(base, base + 12 * P, P, A.hist);
+}
+
+__device__ __forceinline__ void copy_state(FitState *dst, const FitState *src) {
+    const int n = (int)(sizeof(FitState) / sizeof(double));
+    const double *s = reinterpret_cast<const double *>(src);
+    double *d = reinterpret_cast<double *>(dst);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
+}
+
+__device__ __forceinline__ FitParams ls_params(const LsArgs &A) {
+    FitParams F;
+    F.hist = A.hist;
+    F.max_iter = A.max_iter;
+    F.max_ls = A.max_ls;
+    F.restarts = A.restarts;
+    F.edm_tol = A.edm_tol;
+    F.f_noise_rel = A.f_noise_rel;
+    F.deadline = *A.deadline;
+    return F;
+}
+
+// Start points, theta of the first evaluation, state, and the first active list (all of them).
+__global__ void __launch_bounds__(128) ls_init_kernel(LsArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FitSmem &S = *reinterpret_cast<FitSmem *>(smem_raw);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *A.deadline = global_ns() + A.budget_ns;
+        *A.n_act_next = A.n;
+    }
+    copy_model(&S.m, A.model);
+    const DevModel &m = S.m;
+    const int P = m.P, nd = m.n_ds;
+    for (int g = blockIdx.x; g < A.n; g += gridDim.x) {
+        const fit_instance in = A.inst[A.group[g]];
+        FitVecs V = ls_vecs(A, g, P);
+        start_z(m, A.start ? A.start + in.param_off : nullptr, V.zt, V.pd);
+        theta_of_z(m, V.zt, V.pv, V.pd);
+        for (int i = threadIdx.x; i < nd * P; i += blockDim.x) A.gsl[(int64_t)g * nd * P + i] = 0.f;
+        if (threadIdx.x == 0) {
+            init_state(S.st);
+            A.stat[g] = 0;
+            A.act_next[g] = g;
+        }
+        __syncthreads();
+        copy_state(A.state + g, &S.st);
+        __syncthreads();
+    }
+}
+
+// Forward pass and likelihood of one (instance, dataset) per block iteration: stages A (no
+// partials), B, C, C2; stores the dataset's -2lnL, dD/dmu and the efficiency / background
+// gradient contributions.
+__global__ void __launch_bounds__(128) ls_forward_kernel(LsArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LsEvalSmem &S = *reinterpret_cast<LsEvalSmem *>(smem_raw);
+    copy_model(&S.m, A.model);
+    const DevModel &m = S.m;
+    const int P = m.P, nd = m.n_ds, na = *A.n_act;
+    float *pv = reinterpret_cast<float *>(smem_raw + sizeof(LsEvalSmem));
+    float *pd = pv + P;
+    float *wsb = A.ws_in_smem ? pd + P : A.ws_global + (int64_t)blockIdx.x * A.ws_stride;
+    EvalWs ws;
+    ws.u = wsb;
+    ws.v = ws.u + m.N_t;
+    ws.f0 = ws.v + m.N_t;
+    ws.gmu = ws.f0 + m.max_reco;
+    ws.ts = ws.ptot = ws.dp = ws.pcw = nullptr;
+    for (int it = blockIdx.x; it < na * nd; it += gridDim.x) {
+        const int g = A.act[it / nd], d = it % nd;
+        const fit_instance in = A.inst[A.group[g]];
+        const int64_t gd = (int64_t)g * nd + d;
+        if (!((in.mask >> d) & 1u)) {
+            if (threadIdx.x == 0) A.nll_ds[gd] = 0.0;
+            continue;
+        }
+        const FitVecs V = ls_vecs(A, g, P);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            pv[i] = V.pv[i];
+            pd[i] = V.pd[i];
+        }
+        if (threadIdx.x == 0) S.status = 0;
+        __syncthreads();
+        DsCtx c;
+        double nll = 0.0;
+        if (ds_setup(m, d, pv, pd, c, &S.status)) {
+            ds_signal<false>(m, d, pv, pd, c, ws);
+            ds_remap(m, d, c, ws);
+            nll = ds_fold_lik(m, d, pv, pd, c, A.data + in.data_off, ws, A.gsl + gd * P, S.red, &S.status,
+                              nullptr);
+            const int nr = m.ds[d].n_reco;
+            float *gm = A.gmu + gd * m.max_reco;
+            for (int j = threadIdx.x; j < nr; j += blockDim.x) gm[j] = ws.gmu[j];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            A.nll_ds[gd] = nll;
+            if (S.status) atomicOr(&A.stat[g], S.status);
+        }
+        __syncthreads();
+    }
+}
+
+// Adjoint of one (instance, dataset) per block iteration: stage A again with the partials,
+// then stages D, E, F into the dataset's gradient slice.
+__global__ void __launch_bounds__(128) ls_adjoint_kernel(LsArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LsEvalSmem &S = *reinterpret_cast<LsEvalSmem *>(smem_raw);
+    copy_model(&S.m, A.model);
+    const DevModel &m = S.m;
+    const int P = m.P, nd = m.n_ds, na = *A.n_act;
+    float *pv = reinterpret_cast<float *>(smem_raw + sizeof(LsEvalSmem));
+    float *pd = pv + P;
+    float *wsb = A.ws_in_smem ? pd + P : A.ws_global + (int64_t)blockIdx.x * A.ws_stride;
+    const EvalWs ws = carve_eval_ws(wsb, m.N_t, m.C, m.max_reco);
+    for (int it = blockIdx.x; it < na * nd; it += gridDim.x) {
+        const int g = A.act[it / nd], d = it % nd;
+        const fit_instance in = A.inst[A.group[g]];
+        if (!((in.mask >> d) & 1u) || A.stat[g] != 0) continue;
+        const int64_t gd = (int64_t)g * nd + d;
+        const FitVecs V = ls_vecs(A, g, P);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            pv[i] = V.pv[i];
+            pd[i] = V.pd[i];
+        }
+        const int nr = m.ds[d].n_reco;
+        const float *gm = A.gmu + gd * m.max_reco;
+        for (int j = threadIdx.x; j < nr; j += blockDim.x) ws.gmu[j] = gm[j];
+        if (threadIdx.x == 0) S.status = 0;
+        __syncthreads();
+        DsCtx c;
+        if (ds_setup(m, d, pv, pd, c, &S.status)) {
+            ds_signal<true>(m, d, pv, pd, c, ws);
+            ds_adjoint(m, d, pv, pd, c, ws, A.gsl + gd * P, S.red);
+        }
+        __syncthreads();
+    }
+}
+
+// Minimiser step per active instance: gathers the round's evaluation (dataset sums, prior,
+// gradient in z), runs fit_decide, and either prepares theta of the next trial point and puts
+// the instance on the next active list, or writes its result.
+__global__ void __launch_bounds__(128) ls_step_kernel(LsArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FitSmem &S = *reinterpret_cast<FitSmem *>(smem_raw);
+    copy_model(&S.m, A.model);
+    const DevModel &m = S.m;
+    const int P = m.P, nd = m.n_ds, na = *A.n_act;
+    const FitParams F = ls_params(A);
+    for (int a = blockIdx.x; a < na; a += gridDim.x) {
+        const int g = A.act[a];
+        const int ii = A.group[g];
+        const fit_instance in = A.inst[ii];
+        FitVecs V = ls_vecs(A, g, P);
+        copy_state(&S.st, A.state + g);
+        // theta gradient = sum of the dataset slices in a fixed order; the slices are cleared
+        float *gs = A.gsl + (int64_t)g * nd * P;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            float t = 0.f;
+            for (int d = 0; d < nd; ++d) {
+                if ((in.mask >> d) & 1u) t += gs[(int64_t)d * P + i];
+                gs[(int64_t)d * P + i] = 0.f;
             }
-            res.nll_min = f;
+            V.gth[i] = t;
         }
-        // ---- result: theta = theta0 + J z in double ---------------------------------------
-        double *best = A.best + in.param_off;
-        for (int i = tid; i < P; i += blockDim.x) {
-            const float s = m.zscale[i];
-            if (s > 0.f) best[i] = m.theta0[i] + (double)s * (double)V.z[i];
-        }
-        for (int b = 0; b < m.n_blocks; ++b) {
-            const int n = m.blk_size[b];
-            const int *idx = m.blk_idx + m.blk_idx_off[b];
-            const double *L = m.blk_L64 + m.blk_mat_off[b];
-            for (int i = tid; i < n; i += blockDim.x) {
-                double s = 0.0;
-                for (int j = 0; j <= i; ++j) s += L[(int64_t)i * n + j] * (double)V.z[idx[j]];
-                best[idx[i]] = m.theta0[idx[i]] + s;
+        const int st = A.stat[g];
+        double fa = 0.0;
+        for (int d = 0; d < nd; ++d)
+            if ((in.mask >> d) & 1u) fa += A.nll_ds[(int64_t)g * nd + d];
+        __syncthreads();
+        if (st != 0)
+            fa = INFINITY;
+        else
+            fa += eval_z_prior(m, V.zt, V.gth, V.gt, S.red);
+        const bool more = fit_decide(S, V, P, fa, F);
+        if (more) {
+            theta_of_z(m, V.zt, V.pv, V.pd);
+            if (threadIdx.x == 0) {
+                A.stat[g] = 0;
+                A.act_next[atomicAdd(A.n_act_next, 1)] = g;
             }
+        } else {
+            write_result(m, S.st, V.z, A.best + in.param_off, A.results + ii);
         }
-        if (tid == 0) {
-            res.status = status;
-            A.results[ii] = res;
-        }
+        __syncthreads();
+        copy_state(A.state + g, &S.st);
         __syncthreads();
     }
 }

@@ -29,6 +29,48 @@ struct FitArgs {
 __global__ void eval_kernel(const DevModel *gm, int B, const double *theta, const float *data,
                             const uint32_t *masks, double *nll_out, float *grad_out,
                             float *mu_out, int *status_out, float *ws_global, int ws_in_smem);
+// Lockstep engine: the instances of one model advance together, one evaluation per round;
+// a round is three launches (forward + likelihood per (instance, dataset), adjoint per
+// (instance, dataset), minimiser step per instance). Group-local index g addresses the state
+// arrays; `group[g]` is the instance's index in the call.
+struct FitState;
+struct LsArgs {
+    const DevModel *model;       // device
+    const fit_instance *inst;    // device [n_inst of the call]
+    const int *group;            // device [n]
+    int n;
+    const float *data;
+    const double *start;         // device or nullptr
+    double *best;
+    fit_result *results;
+    FitState *state;             // [n]
+    float *vec;                  // [n x vec_stride]: 12 working P-vectors, then the history
+    int64_t vec_stride;
+    float *gsl;                  // [n x n_ds x P] gradient contributions per dataset
+    double *nll_ds;              // [n x n_ds]
+    float *gmu;                  // [n x n_ds x max_reco] dD/dmu of the last forward pass
+    int *stat;                   // [n] evaluation status bits
+    const int *act;              // active group indices this round
+    const int *n_act;
+    int *act_next;               // filled by the step kernel
+    int *n_act_next;
+    float *ws_global;            // evaluation workspace per resident block (when not in smem)
+    int64_t ws_stride;
+    int ws_in_smem;
+    int hist, max_iter, max_ls, restarts;
+    double edm_tol, f_noise_rel;
+    uint64_t budget_ns;
+    uint64_t *deadline;          // device: set by the init kernel
+};
+
+__global__ void ls_init_kernel(LsArgs A);
+__global__ void ls_forward_kernel(LsArgs A);
+__global__ void ls_adjoint_kernel(LsArgs A);
+__global__ void ls_step_kernel(LsArgs A);
+size_t ls_state_bytes();
+size_t ls_step_smem_bytes();
+size_t ls_eval_smem_bytes(int P, int ws_floats);
+
 // the persistent fit kernel compiled for 4 or 5 resident blocks per SM (host entry address)
 const void *fit_kernel_func(int variant);
 

@@ -39,7 +39,7 @@ def test_struct_layouts_match_header_sizes():
     # sizes of the ABI structs as laid out by the binding (natural alignment, x86-64 / aarch64)
     assert ctypes.sizeof(fitcore.fit_instance) == 24
     assert ctypes.sizeof(fitcore.fit_result) == 32
-    assert ctypes.sizeof(fitcore.fit_batch_opts) == 56
+    assert ctypes.sizeof(fitcore.fit_batch_opts) == 64
     assert fitcore.RESULT_DTYPE.itemsize == 32
 
 

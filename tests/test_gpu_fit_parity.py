@@ -50,6 +50,15 @@ def make_instances(name, n, seed, masks=None):
     return datas, ms, truths
 
 
+def engine_opts(engine):
+    o = fitcore.fit_batch_default_opts()
+    o.engine = engine
+    return o
+
+
+ENGINES = pytest.mark.parametrize("engine", [0, 1], ids=["persistent", "lockstep"])
+
+
 def run_gpu(names_per_inst, datas, masks, starts=None, opts=None):
     names = sorted(set(names_per_inst))
     models = [spec_of(n)[2] for n in names]
@@ -97,43 +106,49 @@ def check_against_oracle(name, datas, masks, thetas, res, max_other=None, min_st
     return n_other, n_strict
 
 
-def test_fit_c0_matches_oracle():
+@ENGINES
+def test_fit_c0_matches_oracle(engine):
     datas, masks, _ = make_instances("c0", 12, 100)
-    th, res = run_gpu(["c0"] * 12, datas, masks)
+    th, res = run_gpu(["c0"] * 12, datas, masks, opts=engine_opts(engine))
     check_against_oracle("c0", datas, masks, th, res)
 
 
-def test_fit_c1_with_dataset_masks_matches_oracle():
+@ENGINES
+def test_fit_c1_with_dataset_masks_matches_oracle(engine):
     datas, masks, _ = make_instances("c1", 6, 200, masks=list(synth.C1_MASKS))
-    th, res = run_gpu(["c1"] * 6, datas, masks)
+    th, res = run_gpu(["c1"] * 6, datas, masks, opts=engine_opts(engine))
     check_against_oracle("c1", datas, masks, th, res)
 
 
-def test_fit_c2_matches_oracle():
+@ENGINES
+def test_fit_c2_matches_oracle(engine):
     datas, masks, _ = make_instances("c2", 2, 300)
-    th, res = run_gpu(["c2"] * 2, datas, masks)
+    th, res = run_gpu(["c2"] * 2, datas, masks, opts=engine_opts(engine))
     check_against_oracle("c2", datas, masks, th, res)
 
 
-def test_fit_c1_ensemble_statistics():
+@ENGINES
+def test_fit_c1_ensemble_statistics(engine):
     """64 pseudo-experiments of the three-dataset model: at most 1 in 8 may stop in another
     (certified) minimum; all others match the oracle's minimum within 1e-3 in -2lnL and
     1e-2 sigma in every parameter, and at least 60 % within 1e-3 sigma (64-73 % measured
     across kernel versions: the share moves with FP32 rounding in the flat Li-9 direction)."""
     datas, masks, _ = make_instances("c1", 64, 600)
-    th, res = run_gpu(["c1"] * 64, datas, masks)
+    th, res = run_gpu(["c1"] * 64, datas, masks, opts=engine_opts(engine))
     check_against_oracle("c1", datas, masks, th, res, max_other=8, min_strict=0.6)
 
 
-def test_uneven_mixed_batch_equals_separate_runs():
+@ENGINES
+def test_uneven_mixed_batch_equals_separate_runs(engine):
     d1, m1, _ = make_instances("c1", 5, 400, masks=list(synth.C1_MASKS))
     d2, m2, _ = make_instances("c2", 2, 401)
     names = ["c1", "c2", "c1", "c1", "c2", "c1", "c1"]
     datas = [d1[0], d2[0], d1[1], d1[2], d2[1], d1[3], d1[4]]
     masks = [m1[0], m2[0], m1[1], m1[2], m2[1], m1[3], m1[4]]
-    th, res = run_gpu(names, datas, masks)
-    th1, r1 = run_gpu(["c1"] * 5, d1, m1)
-    th2, r2 = run_gpu(["c2"] * 2, d2, m2)
+    o = engine_opts(engine)
+    th, res = run_gpu(names, datas, masks, opts=o)
+    th1, r1 = run_gpu(["c1"] * 5, d1, m1, opts=o)
+    th2, r2 = run_gpu(["c2"] * 2, d2, m2, opts=o)
     sep = {0: (th1[0], r1[0]), 1: (th2[0], r2[0]), 2: (th1[1], r1[1]), 3: (th1[2], r1[2]),
            4: (th2[1], r2[1]), 5: (th1[3], r1[3]), 6: (th1[4], r1[4])}
     for i in range(len(names)):
@@ -156,10 +171,11 @@ def test_asimov_fit_recovers_truth_and_zero_nll():
     assert np.max(np.abs(th[0] - truth) / sig) < 1e-2
 
 
-def test_start_points_iteration_limit_and_empty_batch():
+@ENGINES
+def test_start_points_iteration_limit_and_empty_batch(engine):
     spec, om, gm = spec_of("c0")
     datas, masks, truths = make_instances("c0", 3, 500)
-    o = fitcore.fit_batch_default_opts()
+    o = engine_opts(engine)
     o.max_iter = 0
     th, res = run_gpu(["c0"] * 3, datas, masks, starts=truths, opts=o)
     for i in range(3):
@@ -168,4 +184,4 @@ def test_start_points_iteration_limit_and_empty_batch():
         assert abs(res[i]["nll_min"] - om.nll(truths[i], datas[i])) <= 1e-3
     empty = np.zeros(0, fitcore.INSTANCE_DTYPE)
     fitcore.fit_batch([gm], empty, np.zeros(1, np.float32), None, np.zeros(1),
-                      np.zeros(1, fitcore.RESULT_DTYPE))
+                      np.zeros(1, fitcore.RESULT_DTYPE), o)
