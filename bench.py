@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=48, help="instances of the CPU baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=250215253)
+    p.add_argument("--engine", default="persistent", choices=["persistent", "lockstep"],
+                   help="fit engine: one persistent launch, or one round of launches per evaluation")
     p.add_argument("--no-warm-start", action="store_true",
                    help="skip the warm-start network measurement")
     p.add_argument("--ws-samples", type=int, default=2_000_000,
@@ -386,6 +388,7 @@ def run_ours(args):
     res_d = torch.zeros(B * fitcore.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts = fitcore.fit_batch_default_opts()
+    opts.engine = 1 if args.engine == "lockstep" else 0
 
     def step():
         fitcore.fit_batch([model], inst, data_d, None, best_d, res_d, opts, stream)
@@ -471,6 +474,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "fits_per_step": world * B, "fits_per_rank": B,
+                       "engine": args.engine,
                        "start": "nominal (cold)", "l2": "flushed (512 MiB write) before each step",
                        "parallelism": f"instances sharded over {world} GPU(s), no collective"},
             "evals_per_s": evals_per_s, "iters_per_fit": iters / B, "evals_per_fit": evals / B,

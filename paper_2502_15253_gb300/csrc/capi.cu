@@ -1224,8 +1224,10 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
     int max_loc = 0;   // working vectors + evaluation workspace, without the history
     for (int mi = 0; mi < n_models; ++mi) {
         const DevModel &h = models[mi]->host;
-        max_need = std::max(max_need, fitcore::fit_vec_floats(h.P, o.history) + h.ws_eval_floats);
-        max_loc = std::max(max_loc, 12 * h.P + h.ws_eval_floats);
+        // (multiples of 4 floats: the fit vectors start on 16-byte boundaries)
+        const int ws4 = (h.ws_eval_floats + 3) & ~3;
+        max_need = std::max(max_need, fitcore::fit_vec_floats(h.P, o.history) + ws4);
+        max_loc = std::max(max_loc, fitcore::fit_work_floats(h.P) + ws4);
     }
     if (o.placement < 0 || o.placement > 3) return fail(FIT_ERR_INVALID_ARG, "fit_batch: placement must be 0..3");
     LaunchCfg cfg;

@@ -170,7 +170,7 @@ struct FitState {
     int pad;
 };
 
-struct FitSmem {
+struct alignas(16) FitSmem {
     DevModel m;
     double red[kMaxWarps * 24 + 24];
     FitState st;
@@ -186,23 +186,24 @@ struct FitVecs {
     float *z, *g, *d, *zt, *gt, *zlo, *glo, *zcr, *gcr, *pv, *pd, *gth, *S, *Y;
 };
 
-// 12 P-vectors at base; the 2 hist P-vectors of the history at hbase
+// 12 P-vectors at base; the 2 hist P-vectors of the history at hbase (pitch fit_vec_pitch(P))
 __device__ __forceinline__ FitVecs carve_fit_vecs(float *base, float *hbase, int P, int hist) {
+    const int Pp = fit_vec_pitch(P);
     FitVecs v;
     v.z = base;
-    v.g = v.z + P;
-    v.d = v.g + P;
-    v.zt = v.d + P;
-    v.gt = v.zt + P;
-    v.zlo = v.gt + P;
-    v.glo = v.zlo + P;
-    v.zcr = v.glo + P;
-    v.gcr = v.zcr + P;
-    v.pv = v.gcr + P;
-    v.pd = v.pv + P;
-    v.gth = v.pd + P;
+    v.g = v.z + Pp;
+    v.d = v.g + Pp;
+    v.zt = v.d + Pp;
+    v.gt = v.zt + Pp;
+    v.zlo = v.gt + Pp;
+    v.glo = v.zlo + Pp;
+    v.zcr = v.glo + Pp;
+    v.gcr = v.zcr + Pp;
+    v.pv = v.gcr + Pp;
+    v.pd = v.pv + Pp;
+    v.gth = v.pd + Pp;
     v.S = hbase;
-    v.Y = v.S + (int64_t)hist * P;
+    v.Y = v.S + (int64_t)hist * Pp;
     return v;
 }
 
@@ -230,11 +231,22 @@ __device__ void fused_dots(const float *Sv, const float *Yv, const float *ynew, 
         } else {
             const int type = q / kMaxHist, slot = q % kMaxHist;
             if (!((occ >> slot) & 1u) || (type < 2 && ynew == nullptr)) continue;
-            a = ((type & 1) ? Yv : Sv) + (int64_t)slot * P;
+            a = ((type & 1) ? Yv : Sv) + (int64_t)slot * fit_vec_pitch(P);
             b = (type < 2) ? ynew : g;
         }
-        float acc = 0.f;
-        for (int i = lane; i < P; i += 32) acc = fmaf(a[i], b[i], acc);
+        // 16-byte loads over the whole quads (vectors start 16-byte aligned), then the tail
+        const float4 *a4 = reinterpret_cast<const float4 *>(a), *b4 = reinterpret_cast<const float4 *>(b);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int k = lane; k < (P >> 2); k += 32) {
+            const float4 x = a4[k], y = b4[k];
+            a0 = fmaf(x.x, y.x, a0);
+            a1 = fmaf(x.y, y.y, a1);
+            a2 = fmaf(x.z, y.z, a2);
+            a3 = fmaf(x.w, y.w, a3);
+        }
+        const int tail = (P & ~3) + lane;
+        if (tail < P) a0 = fmaf(a[tail], b[tail], a0);
+        float acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) out[q] = (double)acc;
@@ -332,29 +344,43 @@ __device__ void lbfgs_scalars(FitSmem &S, int hist_max, bool pending) {
     if (lane == 0) S.gHg = ghg;
 }
 
-// theta from z (transformation layer): pd = J z, pv = theta0 + pd. In a prior block the
-// rows of L z are formed a thread per row over the stored L^T, so each step is a coalesced
-// load plus a shared-memory broadcast of z, and the loop keeps many loads in flight.
+// Row r of the concatenated prior blocks: its block b and the row i within it.
+__device__ __forceinline__ int prior_row_block(const DevModel &m, int r) {
+    int b = 0;
+    while (b + 1 < m.n_blocks && m.blk_idx_off[b + 1] <= r) ++b;
+    return b;
+}
+
+__device__ __forceinline__ int prior_rows(const DevModel &m) {
+    return m.n_blocks > 0 ? m.blk_idx_off[m.n_blocks - 1] + m.blk_size[m.n_blocks - 1] : 0;
+}
+
+// theta from z (transformation layer): pd = J z, pv = theta0 + pd. The rows of all prior
+// blocks are spread over the threads together (a thread per row of L z, formed over the stored
+// L^T so that each step is a coalesced load plus a broadcast of z); four partial sums keep
+// four independent loads per thread in flight.
 __device__ void theta_of_z(const DevModel &m, const float *z, float *pv, float *pd) {
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < m.P; i += nth) {
         const float s = m.zscale[i];
         if (s > 0.f) pd[i] = s * z[i];
     }
-    for (int b = 0; b < m.n_blocks; ++b) {
-        const int n = m.blk_size[b];
+    const int rows = prior_rows(m);
+    for (int r = tid; r < rows; r += nth) {
+        const int b = prior_row_block(m, r);
+        const int n = m.blk_size[b], i = r - m.blk_idx_off[b];
         const int *idx = m.blk_idx + m.blk_idx_off[b];
         const float *Lt = m.blk_L + m.blk_mat_off[b] + (int64_t)n * n;   // L^T, row-major
-        for (int i = tid; i < n; i += nth) {
-            float s0 = 0.f, s1 = 0.f;
-            int j = 0;
-            for (; j + 1 <= i; j += 2) {
-                s0 = fmaf(Lt[(int64_t)j * n + i], z[idx[j]], s0);
-                s1 = fmaf(Lt[(int64_t)(j + 1) * n + i], z[idx[j + 1]], s1);
-            }
-            if (j <= i) s0 = fmaf(Lt[(int64_t)j * n + i], z[idx[j]], s0);
-            pd[idx[i]] = s0 + s1;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int j = 0;
+        for (; j + 3 <= i; j += 4) {
+            s0 = fmaf(Lt[(int64_t)j * n + i], z[idx[j]], s0);
+            s1 = fmaf(Lt[(int64_t)(j + 1) * n + i], z[idx[j + 1]], s1);
+            s2 = fmaf(Lt[(int64_t)(j + 2) * n + i], z[idx[j + 2]], s2);
+            s3 = fmaf(Lt[(int64_t)(j + 3) * n + i], z[idx[j + 3]], s3);
         }
+        for (; j <= i; ++j) s0 = fmaf(Lt[(int64_t)j * n + i], z[idx[j]], s0);
+        pd[idx[i]] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
     for (int i = tid; i < m.P; i += nth) pv[i] = m.theta0_f[i] + pd[i];
@@ -375,22 +401,24 @@ __device__ double eval_z_prior(const DevModel &m, const float *z, const float *g
             if (con) acc[0] = fmaf(z[i], z[i], acc[0]);
         }
     }
-    for (int b = 0; b < m.n_blocks; ++b) {
-        const int n = m.blk_size[b];
+    const int rows = prior_rows(m);
+    for (int r = tid; r < rows; r += nth) {
+        const int b = prior_row_block(m, r);
+        const int n = m.blk_size[b], j = r - m.blk_idx_off[b];
         const int *idx = m.blk_idx + m.blk_idx_off[b];
         const float *L = m.blk_L + m.blk_mat_off[b];   // L, row-major: (L^T g)_j = sum_i L_ij g_i
-        for (int j = tid; j < n; j += nth) {
-            float s0 = 0.f, s1 = 0.f;
-            int i = j;
-            for (; i + 1 < n; i += 2) {
-                s0 = fmaf(L[(int64_t)i * n + j], gth[idx[i]], s0);
-                s1 = fmaf(L[(int64_t)(i + 1) * n + j], gth[idx[i + 1]], s1);
-            }
-            if (i < n) s0 = fmaf(L[(int64_t)i * n + j], gth[idx[i]], s0);
-            const float zj = z[idx[j]];
-            gz[idx[j]] = (s0 + s1) + 2.f * zj;
-            acc[0] = fmaf(zj, zj, acc[0]);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int i = j;
+        for (; i + 3 < n; i += 4) {
+            s0 = fmaf(L[(int64_t)i * n + j], gth[idx[i]], s0);
+            s1 = fmaf(L[(int64_t)(i + 1) * n + j], gth[idx[i + 1]], s1);
+            s2 = fmaf(L[(int64_t)(i + 2) * n + j], gth[idx[i + 2]], s2);
+            s3 = fmaf(L[(int64_t)(i + 3) * n + j], gth[idx[i + 3]], s3);
         }
+        for (; i < n; ++i) s0 = fmaf(L[(int64_t)i * n + j], gth[idx[i]], s0);
+        const float zj = z[idx[j]];
+        gz[idx[j]] = ((s0 + s1) + (s2 + s3)) + 2.f * zj;
+        acc[0] = fmaf(zj, zj, acc[0]);
     }
     double tot[1];
     block_sum<1>(acc, red, tot);
@@ -551,7 +579,7 @@ __device__ bool fit_decide(FitSmem &S, FitVecs &V, int P, double fa, const FitPa
             if (accepted) {
                 // curvature pair into the next slot; folded in by the next fused pass
                 const int c = st.head;
-                float *s_new = V.S + (int64_t)c * P, *y_new = V.Y + (int64_t)c * P;
+                float *s_new = V.S + (int64_t)c * fit_vec_pitch(P), *y_new = V.Y + (int64_t)c * fit_vec_pitch(P);
                 for (int i = tid; i < P; i += blockDim.x) {
                     s_new[i] = V.zt[i] - V.z[i];
                     y_new[i] = V.gt[i] - V.g[i];
@@ -575,22 +603,31 @@ __device__ bool fit_decide(FitSmem &S, FitVecs &V, int P, double fa, const FitPa
     // ---- direction d = -H g: fused dot products, scalar two-loop, one combination ------------
     while (next == kDirection) {
         __syncthreads();
-        fused_dots(V.S, V.Y, pending ? V.Y + (int64_t)st.head * P : nullptr, V.g, P,
+        fused_dots(V.S, V.Y, pending ? V.Y + (int64_t)st.head * fit_vec_pitch(P) : nullptr, V.g, P,
                    (unsigned)st.occ | (pending ? 1u << st.head : 0u), S.dots);
         if (tid < 32) lbfgs_scalars(S, F.hist, pending);
         pending = false;
         __syncthreads();
         {
+            // d = -(cg g + sum cs_j s_j + sum cy_j y_j), four consecutive entries per thread
+            // (16-byte loads; the pitch padding of d receives values nothing reads)
             const float cg = S.cg;
             const unsigned occ = (unsigned)st.occ;
-            for (int i = tid; i < P; i += blockDim.x) {
-                float h = cg * V.g[i];
+            const int Pp = fit_vec_pitch(P);
+            for (int k = tid; k < (Pp >> 2); k += blockDim.x) {
+                const float4 gv = reinterpret_cast<const float4 *>(V.g)[k];
+                float4 h = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
                 for (int j = 0; j < F.hist; ++j)
                     if ((occ >> j) & 1u) {
-                        h = fmaf(S.cs[j], V.S[(int64_t)j * P + i], h);
-                        h = fmaf(S.cy[j], V.Y[(int64_t)j * P + i], h);
+                        const float a = S.cs[j], b = S.cy[j];
+                        const float4 sv = reinterpret_cast<const float4 *>(V.S + (int64_t)j * Pp)[k];
+                        const float4 yv = reinterpret_cast<const float4 *>(V.Y + (int64_t)j * Pp)[k];
+                        h.x = fmaf(b, yv.x, fmaf(a, sv.x, h.x));
+                        h.y = fmaf(b, yv.y, fmaf(a, sv.y, h.y));
+                        h.z = fmaf(b, yv.z, fmaf(a, sv.z, h.z));
+                        h.w = fmaf(b, yv.w, fmaf(a, sv.w, h.w));
                     }
-                V.d[i] = -h;
+                reinterpret_cast<float4 *>(V.d)[k] = make_float4(-h.x, -h.y, -h.z, -h.w);
             }
         }
         __syncthreads();
@@ -777,12 +814,12 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
         // they fit, else in this block's global slice; the history in shared memory after them
         // unless it is placed in the global slice (hist_global)
         // (global slice: history first, then the rest)
-        const int hfl = fit_hist_floats(P, F.hist), loc = 12 * P + m.ws_eval_floats;
+        const int hfl = fit_hist_floats(P, F.hist), loc = fit_work_floats(P) + ((m.ws_eval_floats + 3) & ~3);
         const bool loc_smem = loc + (A.hist_global ? 0 : hfl) <= A.smem_floats;
         float *base = loc_smem ? dyn : gws + (A.hist_global ? hfl : 0);
         float *hbase = A.hist_global ? gws : base + loc;
         FitVecs V = carve_fit_vecs(base, hbase, P, F.hist);
-        const EvalWs ws = carve_eval_ws(base + 12 * P, m.N_t, m.C, m.max_reco);
+        const EvalWs ws = carve_eval_ws(base + fit_work_floats(P), m.N_t, m.C, m.max_reco);
         const float *data = A.data + in.data_off;
         if (tid == 0) init_state(S.st);
         __syncthreads();
@@ -820,7 +857,7 @@ size_t ls_eval_smem_bytes(int P, int ws_floats) {
 
 __device__ __forceinline__ FitVecs ls_vecs(const LsArgs &A, int g, int P) {
     float *base = A.vec + (int64_t)g * A.vec_stride;
-    return carve_fit_vecs(base, base + 12 * P, P, A.hist);
+    return carve_fit_vecs(base, base + fit_work_floats(P), P, A.hist);
 }
 
 __device__ __forceinline__ void copy_state(FitState *dst, const FitState *src) {

@@ -90,7 +90,11 @@ int targets(int B, int P, const double *theta, const double *theta0, int n_t, co
 int starts(int B, int P, const double *theta0, int n_t, const int *idx, const double *scale, const float *out,
            int n_out, double *theta, cudaStream_t s);
 size_t fit_smem_bytes(int floats);
-__host__ __device__ inline int fit_vec_floats(int P, int hist) { return (12 + 2 * hist) * P; }
-__host__ __device__ inline int fit_hist_floats(int P, int hist) { return 2 * hist * P; }
+// Fit vectors are spaced by P rounded up to 4 floats, so that every vector starts on a
+// 16-byte boundary and the history can be read as float4.
+__host__ __device__ inline int fit_vec_pitch(int P) { return (P + 3) & ~3; }
+__host__ __device__ inline int fit_vec_floats(int P, int hist) { return (12 + 2 * hist) * fit_vec_pitch(P); }
+__host__ __device__ inline int fit_hist_floats(int P, int hist) { return 2 * hist * fit_vec_pitch(P); }
+__host__ __device__ inline int fit_work_floats(int P) { return 12 * fit_vec_pitch(P); }
 
 }  // namespace fitcore
