@@ -516,14 +516,33 @@ static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, 
     (void)warp;
     (void)nw;
     // ---- stage C: fold into reco bins (banded rows, warp per row) ------------------------
-    for (int j = warp; j < nr; j += nw) {
-        const int lo = dt.row_lo[j], len = dt.row_len[j];
-        const float *rr = dt.rrow + dt.row_off[j];
-        float s = 0.f;
-        for (int b = lane; b < len; b += 32) s = fmaf(rr[b], ws.v[lo + b], s);
+    // Each warp takes two rows at a time and two strides of each, so four independent
+    // load/FMA chains per lane are in flight.
+    for (int j0 = warp; j0 < nr; j0 += 2 * nw) {
+        const int j1 = j0 + nw;
+        const bool two = j1 < nr;
+        const int lo0 = dt.row_lo[j0], len0 = dt.row_len[j0];
+        const int lo1 = two ? dt.row_lo[j1] : 0, len1 = two ? dt.row_len[j1] : 0;
+        const float *r0 = dt.rrow + dt.row_off[j0];
+        const float *r1 = dt.rrow + (two ? dt.row_off[j1] : 0);
+        float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
+        const int len = max(len0, len1);
+        for (int b = lane; b < len; b += 64) {
+            if (b < len0) s0 = fmaf(r0[b], ws.v[lo0 + b], s0);
+            if (b + 32 < len0) s1 = fmaf(r0[b + 32], ws.v[lo0 + b + 32], s1);
+            if (b < len1) t0 = fmaf(r1[b], ws.v[lo1 + b], t0);
+            if (b + 32 < len1) t1 = fmaf(r1[b + 32], ws.v[lo1 + b + 32], t1);
+        }
+        float s = s0 + s1, t = t0 + t1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) ws.f0[j] = s;
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            t += __shfl_xor_sync(0xffffffffu, t, o);
+        }
+        if (lane == 0) {
+            ws.f0[j0] = s;
+            if (two) ws.f0[j1] = t;
+        }
     }
     __syncthreads();
 
@@ -585,7 +604,8 @@ static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, 
 
 // Stages D, E and F: adjoint of the fold, of the energy map and of the signal; adds the
 // gradient contributions to grad. Needs ws.u/ts/ptot/dp/pcw (ds_signal<true>) and ws.gmu.
-static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
+template <int NC>
+static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
                                   EvalWs ws, float *grad, double *red) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
@@ -602,24 +622,30 @@ static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, con
     const EMap &em = c.em;
     // ---- stage D: adjoint of the fold, gv = eff R^T gmu (column bands) --------------------
     float *gv = ws.v;   // v is dead after the fold
+    // rcol is exactly 0 past each column's band, so the loop runs the full band width with
+    // the row index clamped (no early exit) and four partial sums
     for (int k = tid; k < N_t; k += nth) {
-        const int lo = dt.col_lo[k];
-        float s = 0.f;
-        for (int b = 0; b < dt.col_w; ++b) {
-            const int j = lo + b;
-            if (j >= nr) break;
-            s = fmaf(dt.rcol[b * N_t + k], ws.gmu[j], s);
+        const int lo = dt.col_lo[k], cw = dt.col_w, jmax = nr - 1;
+        const float *rc = dt.rcol + k;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int b = 0;
+        for (; b + 3 < cw; b += 4) {
+            s0 = fmaf(rc[(int64_t)b * N_t], ws.gmu[min(lo + b, jmax)], s0);
+            s1 = fmaf(rc[(int64_t)(b + 1) * N_t], ws.gmu[min(lo + b + 1, jmax)], s1);
+            s2 = fmaf(rc[(int64_t)(b + 2) * N_t], ws.gmu[min(lo + b + 2, jmax)], s2);
+            s3 = fmaf(rc[(int64_t)(b + 3) * N_t], ws.gmu[min(lo + b + 3, jmax)], s3);
         }
-        gv[k] = pmul(c.eff, s);
+        for (; b < cw; ++b) s0 = fmaf(rc[(int64_t)b * N_t], ws.gmu[min(lo + b, jmax)], s0);
+        gv[k] = pmul(c.eff, (s0 + s1) + (s2 + s3));
     }
     __syncthreads();
 
     // ---- stage E: adjoint of the energy map and of the signal ---------------------------
     // per source k: gu = sum_t F_kt gv_t; A0 = (gu - gv(floor Y_k)) / w, A1 = (gv(floor Y_k+1) - gu) / w
-    float ep[8 + FIT_MAX_CORES];
-    // ep[0..2] d/da, ep[3..6] d/d eta, ep[7] d/d norm, ep[8+c] d/d power_c
+    float ep[8 + NC];
+    // ep[0..2] d/da, ep[3..6] d/d eta, ep[7] d/d norm, ep[8+c] d/d power_c (NC >= C cores)
 #pragma unroll
-    for (int i = 0; i < 8 + FIT_MAX_CORES; ++i) ep[i] = 0.f;
+    for (int i = 0; i < 8 + NC; ++i) ep[i] = 0.f;
     for (int k = tid; k < N_t; k += nth) {
         const float e0 = m.e_edge[k], e1 = m.e_edge[k + 1];
         const float d0 = em.disp(e0), d1 = em.disp(e1);
@@ -645,12 +671,12 @@ static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, con
         for (int i = 0; i < 4; ++i) ep[3 + i] = fmaf(gb, ws.dp[i * N_t + k], ep[3 + i]);
         ep[7] = fmaf(gu * ts, pt, ep[7]);
 #pragma unroll
-        for (int cc = 0; cc < FIT_MAX_CORES; ++cc)
+        for (int cc = 0; cc < NC; ++cc)
             if (cc < C) ep[8 + cc] = fmaf(gb, ws.pcw[cc * N_t + k], ep[8 + cc]);
         ws.dp[k] = pmul(c.nrm, gu * ds.t[k] * pt);    // d nll / d s for this bin (dp0 reused)
     }
-    double etot[8 + FIT_MAX_CORES];
-    block_sum<8 + FIT_MAX_CORES>(ep, red, etot);
+    double etot[8 + NC];
+    block_sum<8 + NC>(ep, red, etot);
     if (tid == 0) {
         for (int i = 0; i < 3; ++i)
             if (ds.esc_idx[i] >= 0) grad[ds.esc_idx[i]] += (float)etot[i];
@@ -658,7 +684,7 @@ static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, con
             if (m.osc_idx[i] >= 0) grad[m.osc_idx[i]] += (float)etot[3 + i];
         if (ds.norm_idx >= 0) grad[ds.norm_idx] += (float)etot[7];
 #pragma unroll
-        for (int cc = 0; cc < FIT_MAX_CORES; ++cc)
+        for (int cc = 0; cc < NC; ++cc)
             if (cc < C && m.core_power_idx[cc] >= 0) grad[m.core_power_idx[cc]] += (float)etot[8 + cc];
     }
     // ---- stage F: shape reweights (one thread per distinct parameter, CSR over bins) -----
@@ -673,6 +699,15 @@ static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, con
 // One dataset in one sequence: adds its Poisson -2lnL and (if grad != nullptr) its gradient
 // contributions (theta space, P floats). Returns the dataset's -2lnL (all threads); *status |=
 // kSt* bits on failure.
+// Stages D-F with the per-core sums sized for the model's core count.
+static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
+                                  EvalWs ws, float *grad, double *red) {
+    if (m.C <= 2)
+        ds_adjoint_nc<2>(m, d, pv, pd, c, ws, grad, red);
+    else
+        ds_adjoint_nc<FIT_MAX_CORES>(m, d, pv, pd, c, ws, grad, red);
+}
+
 static __device__ double eval_dataset(const DevModel &m, int d, const float *pv, const float *pd,
                                       const float *data, EvalWs ws, float *grad, double *red,
                                       int *status, float *mu_out) {
