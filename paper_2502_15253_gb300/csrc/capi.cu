@@ -550,6 +550,13 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         A.put(&h.blk_size, bsz);
         A.put(&h.blk_idx_off, boff);
         A.put(&h.blk_idx, bidx);
+        vector<int> bfirst(bsz.size(), -1);
+        for (size_t b = 0; b < bsz.size(); ++b) {
+            bool contig = bsz[b] > 0;
+            for (int i = 1; i < bsz[b] && contig; ++i) contig = bidx[boff[b] + i] == bidx[boff[b]] + i;
+            if (contig) bfirst[b] = bidx[boff[b]];
+        }
+        A.put(&h.blk_first, bfirst);
         A.put(&h.blk_mat_off, moff);
         A.put(&h.blk_L, Lf);
         A.put(&h.blk_W, Wf);

@@ -74,6 +74,7 @@ struct DevModel {
     const int *blk_size;     // [n_blocks]
     const int *blk_idx_off;  // [n_blocks]
     const int *blk_idx;      // concatenated parameter indices
+    const int *blk_first;    // [n_blocks] first index when a block's indices are consecutive, else -1
     const int64_t *blk_mat_off;  // [n_blocks] offset of the block's m x m matrices
     const float *blk_L;      // lower Cholesky factor of V (row-major, dense)
     const float *blk_W;      // L^-1 (row-major, dense lower triangle)
@@ -174,6 +175,46 @@ struct OscCoef {
 
 __device__ __forceinline__ float cterm(const OscCoef &k, int i, float q) {
     return fmaf(q, k.lo[i], k.hi[i] * q);
+}
+
+// Float-pair ("double-float") arithmetic: a value h + l with |l| <= ulp(h) / 2, carried in two
+// floats (error-free transformations of Knuth's two-sum and the FMA two-product, Dekker's
+// normalisation). Used where a few coefficients need more than 24 bits but FP64 would sit on
+// the critical path (GB300 runs FP64 at 1/64 of the FP32 rate).
+struct F2 {
+    float h, l;
+};
+
+__device__ __forceinline__ F2 f2_norm(float h, float l) {
+    const float s = h + l;
+    return F2{s, l - (s - h)};
+}
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b.h - bb);
+    return f2_norm(s, e + (a.l + b.l));
+}
+
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p);
+    return f2_norm(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
+}
+
+__device__ __forceinline__ F2 f2_scale(F2 a, float c) {   // c a power of two
+    return F2{a.h * c, a.l * c};
+}
+
+__device__ __forceinline__ F2 f2_one_minus(F2 a) { return f2_add(F2{1.f, 0.f}, F2{-a.h, -a.l}); }
+
+// square root: s = sqrtf(h) refined by one Newton step on the residual a - s^2
+__device__ __forceinline__ F2 f2_sqrt(F2 a) {
+    if (!(a.h > 0.f)) return F2{0.f, 0.f};
+    const float s = sqrtf(a.h);
+    const float r = fmaf(-s, s, a.h) + a.l;
+    return f2_norm(s, r / (2.f * s));
 }
 
 // P(L_dc, E_k) and dP/d(eta_i) for the four survival parameters.
@@ -345,8 +386,7 @@ static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const
     (void)warp;
     (void)nw;
     // Survival parameters: mass splittings as theta0_f + (theta0_lo + delta) inside the
-    // phase; the sin^2 coefficients from the exact values, in double, by one thread.
-    __shared__ OscCoef kco;
+    // phase.
     float *eta = c.eta, *eta_lo = c.eta_lo;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -360,31 +400,39 @@ static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const
             eta_lo[i] = 0.f;
         }
     }
-    if (tid == 0) {
-        double e[4];
-        for (int i = 0; i < 4; ++i) {
-            const int p = m.osc_idx[i];
-            e[i] = p >= 0 ? m.theta0[p] + (double)pd[p] : m.osc_val_d[i];
-        }
-        double cf[3];
-        if (m.osc_mode == FIT_OSC_EQ1) {
-            const double c2 = 0.5 * (1.0 + sqrt(fmax(1.0 - e[0], 0.0)));
-            cf[0] = e[0];
-            cf[1] = c2 * c2 * e[2];
-            cf[2] = 0.0;
+    // the sin^2 coefficients from float pairs of the exact parameter values (every thread
+    // forms the same values; no barrier)
+    F2 e[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int p = m.osc_idx[i];
+        if (p >= 0) {
+            const float h = pv[p];
+            e[i] = f2_norm(h, ((m.theta0_f[p] - h) + pd[p]) + m.theta0_lo[p]);
         } else {
-            const double S12 = 4.0 * e[0] * (1.0 - e[0]), S13 = 4.0 * e[1] * (1.0 - e[1]);
-            cf[0] = (1.0 - e[1]) * (1.0 - e[1]) * S12;
-            cf[1] = S13 * (1.0 - e[0]);
-            cf[2] = S13 * e[0];
-        }
-        for (int i = 0; i < 3; ++i) {
-            kco.hi[i] = (float)cf[i];
-            kco.lo[i] = (float)(cf[i] - (double)kco.hi[i]);
+            e[i] = F2{m.osc_val[i], m.osc_val_lo[i]};
         }
     }
-    __syncthreads();
-    c.kc = kco;
+    F2 cf[3];
+    if (m.osc_mode == FIT_OSC_EQ1) {
+        // cos^4 th13 = ((1 + sqrt(1 - sin^2 2th13)) / 2)^2
+        const F2 c2 = f2_scale(f2_add(F2{1.f, 0.f}, f2_sqrt(f2_one_minus(e[0]))), 0.5f);
+        cf[0] = e[0];
+        cf[1] = f2_mul(f2_mul(c2, c2), e[2]);
+        cf[2] = F2{0.f, 0.f};
+    } else {
+        const F2 S12 = f2_scale(f2_mul(e[0], f2_one_minus(e[0])), 4.f);
+        const F2 S13 = f2_scale(f2_mul(e[1], f2_one_minus(e[1])), 4.f);
+        const F2 c13 = f2_one_minus(e[1]);
+        cf[0] = f2_mul(f2_mul(c13, c13), S12);
+        cf[1] = f2_mul(S13, f2_one_minus(e[0]));
+        cf[2] = f2_mul(S13, e[0]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        c.kc.hi[i] = cf[i].h;
+        c.kc.lo[i] = cf[i].l;
+    }
     c.nrm = ppair(m, pv, pd, ds.norm_idx, 1.f);
     c.eff = ppair(m, pv, pd, ds.eff_idx, 1.f);
     c.em = make_emap(m, ds, pv, pd);

@@ -368,19 +368,26 @@ __device__ void theta_of_z(const DevModel &m, const float *z, float *pv, float *
     const int rows = prior_rows(m);
     for (int r = tid; r < rows; r += nth) {
         const int b = prior_row_block(m, r);
-        const int n = m.blk_size[b], i = r - m.blk_idx_off[b];
+        const int n = m.blk_size[b], i = r - m.blk_idx_off[b], first = m.blk_first[b];
         const int *idx = m.blk_idx + m.blk_idx_off[b];
         const float *Lt = m.blk_L + m.blk_mat_off[b] + (int64_t)n * n;   // L^T, row-major
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        float s[4] = {0.f, 0.f, 0.f, 0.f};
         int j = 0;
-        for (; j + 3 <= i; j += 4) {
-            s0 = fmaf(Lt[(int64_t)j * n + i], z[idx[j]], s0);
-            s1 = fmaf(Lt[(int64_t)(j + 1) * n + i], z[idx[j + 1]], s1);
-            s2 = fmaf(Lt[(int64_t)(j + 2) * n + i], z[idx[j + 2]], s2);
-            s3 = fmaf(Lt[(int64_t)(j + 3) * n + i], z[idx[j + 3]], s3);
+        if (first >= 0) {   // consecutive indices: z read directly, eight loads in flight
+            const float *zb = z + first;
+            for (; j + 7 <= i; j += 8) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s[q & 3] = fmaf(Lt[(int64_t)(j + q) * n + i], zb[j + q], s[q & 3]);
+            }
+            for (; j <= i; ++j) s[0] = fmaf(Lt[(int64_t)j * n + i], zb[j], s[0]);
+        } else {
+            for (; j + 3 <= i; j += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s[q] = fmaf(Lt[(int64_t)(j + q) * n + i], z[idx[j + q]], s[q]);
+            }
+            for (; j <= i; ++j) s[0] = fmaf(Lt[(int64_t)j * n + i], z[idx[j]], s[0]);
         }
-        for (; j <= i; ++j) s0 = fmaf(Lt[(int64_t)j * n + i], z[idx[j]], s0);
-        pd[idx[i]] = (s0 + s1) + (s2 + s3);
+        pd[idx[i]] = (s[0] + s[1]) + (s[2] + s[3]);
     }
     __syncthreads();
     for (int i = tid; i < m.P; i += nth) pv[i] = m.theta0_f[i] + pd[i];
@@ -404,20 +411,27 @@ __device__ double eval_z_prior(const DevModel &m, const float *z, const float *g
     const int rows = prior_rows(m);
     for (int r = tid; r < rows; r += nth) {
         const int b = prior_row_block(m, r);
-        const int n = m.blk_size[b], j = r - m.blk_idx_off[b];
+        const int n = m.blk_size[b], j = r - m.blk_idx_off[b], first = m.blk_first[b];
         const int *idx = m.blk_idx + m.blk_idx_off[b];
         const float *L = m.blk_L + m.blk_mat_off[b];   // L, row-major: (L^T g)_j = sum_i L_ij g_i
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        float s[4] = {0.f, 0.f, 0.f, 0.f};
         int i = j;
-        for (; i + 3 < n; i += 4) {
-            s0 = fmaf(L[(int64_t)i * n + j], gth[idx[i]], s0);
-            s1 = fmaf(L[(int64_t)(i + 1) * n + j], gth[idx[i + 1]], s1);
-            s2 = fmaf(L[(int64_t)(i + 2) * n + j], gth[idx[i + 2]], s2);
-            s3 = fmaf(L[(int64_t)(i + 3) * n + j], gth[idx[i + 3]], s3);
+        if (first >= 0) {   // consecutive indices: gth read directly, eight loads in flight
+            const float *gb = gth + first;
+            for (; i + 7 < n; i += 8) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s[q & 3] = fmaf(L[(int64_t)(i + q) * n + j], gb[i + q], s[q & 3]);
+            }
+            for (; i < n; ++i) s[0] = fmaf(L[(int64_t)i * n + j], gb[i], s[0]);
+        } else {
+            for (; i + 3 < n; i += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s[q] = fmaf(L[(int64_t)(i + q) * n + j], gth[idx[i + q]], s[q]);
+            }
+            for (; i < n; ++i) s[0] = fmaf(L[(int64_t)i * n + j], gth[idx[i]], s[0]);
         }
-        for (; i < n; ++i) s0 = fmaf(L[(int64_t)i * n + j], gth[idx[i]], s0);
         const float zj = z[idx[j]];
-        gz[idx[j]] = ((s0 + s1) + (s2 + s3)) + 2.f * zj;
+        gz[idx[j]] = ((s[0] + s[1]) + (s[2] + s[3])) + 2.f * zj;
         acc[0] = fmaf(zj, zj, acc[0]);
     }
     double tot[1];
