@@ -19,10 +19,11 @@ namespace fitcore {
 
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr int kRowBytes = 128;           // one K slice: 128 bytes per row
 constexpr int kTileM = 128;
 constexpr int kNumSMs = 152;
+constexpr int kThreads = 256;   // 8 warps: warp w reads accumulator lanes 32 (w % 4).. in the epilogue
 constexpr uint64_t kMaxTries = 2000000000ull;  // bound of every barrier wait: 2 s
 
 __device__ int g_gemm_err;
@@ -34,7 +35,7 @@ __device__ __forceinline__ float gelu_grad(float x) {
 }
 
 template <bool TF32>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                    int K, int n_tile, int kt_per, GemmOut out, int *err) {
     extern __shared__ uint8_t smem_raw[];
@@ -106,50 +107,88 @@ __global__ void __launch_bounds__(128, 1)
     }
     __syncwarp();
 
-    // ---- epilogue: row (m0 + 32 warp + lane), 16 accumulator columns per load -------------
+    // ---- epilogue ------------------------------------------------------------------------
+    // Phase 1: warp w reads its 32 accumulator lanes (rows) with tcgen05.ld, 16 columns per
+    // load, and parks them in a shared-memory tile laid over the (now idle) operand ring (row
+    // pitch n_tile + 1 floats: the 32 rows of a store land in 32 different banks). Phase 2:
+    // the warps walk the tile row by row with the lanes along the columns, so every global
+    // load, store or atomic of the fused epilogue is coalesced.
     bool ready = umma::mbar_wait(done, 0, kMaxTries);
-    ready = __all_sync(0xffffffffu, ready);
-    if (!ready && lane == 0) atomicOr(err, 4);
+    ready = __syncthreads_and(ready) != 0;
+    if (!ready && threadIdx.x == 0) atomicOr(err, 4);
     umma::tc_fence_after();
     if (ready) {
-        const int row = m0 + warp * 32 + lane;
-        const bool row_ok = row < M;
-        for (int c = 0; c < n_tile; c += 16) {
+        float *tile = reinterpret_cast<float *>(smem);
+        const int ldt = n_tile + 1;
+        const int quad = warp & 3, half = warp >> 2, nwarps = kThreads / 32;
+        const int r = quad * 32 + lane;
+        // warps w and w + 4 share a lane quadrant and split its columns
+        for (int c = half * 16; c < n_tile; c += 32) {
             float v[16];
-            umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (!row_ok) continue;
+            umma::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int n = n0 + c + i;
-                if (n >= N) continue;
-                const float d = v[i];
-                switch (out.epi) {
-                    case EPI_F32:
-                        if (split)
-                            atomicAdd(&out.C[(int64_t)row * out.ldc + n], d);
-                        else
-                            out.C[(int64_t)row * out.ldc + n] = d;
-                        break;
-                    case EPI_BIAS_F32:
-                        out.C[(int64_t)row * out.ldc + n] = d + out.bias[n];
-                        break;
-                    case EPI_BIAS_GELU: {
-                        const float pre = d + out.bias[n];
-                        out.C[(int64_t)row * out.ldc + n] = pre;
-                        out.Y[(int64_t)row * out.ldy + n] = __float2bfloat16(gelu(pre));
-                        break;
-                    }
-                    case EPI_DGELU:
-                        out.Y[(int64_t)row * out.ldy + n] =
-                            __float2bfloat16(d * gelu_grad(out.aux[(int64_t)row * out.ldaux + n]));
-                        break;
-                    case EPI_F32_ADD:
-                        if (split)
-                            atomicAdd(&out.C[(int64_t)row * out.ldc + n], d);
-                        else
-                            out.C[(int64_t)row * out.ldc + n] += d;
-                        break;
+            for (int i = 0; i < 16; ++i) tile[r * ldt + c + i] = v[i];
+        }
+        __syncthreads();
+        const int n_valid = min(n_tile, N - n0);
+        for (int rr = warp; rr < kTileM; rr += nwarps) {
+            const int row = m0 + rr;
+            if (row >= M) break;
+            const float *trow = tile + rr * ldt;
+            // the aux operand of the GELU' epilogue is loaded four strides ahead of its use
+            float ax[4] = {0.f, 0.f, 0.f, 0.f};
+            if (out.epi == EPI_DGELU) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = lane + 32 * q;
+                    if (c < n_valid) ax[q] = out.aux[(int64_t)row * out.ldaux + n0 + c];
                 }
+            }
+            for (int c0 = 0; c0 < n_valid; c0 += 128) {
+                float axn[4] = {0.f, 0.f, 0.f, 0.f};
+                if (out.epi == EPI_DGELU) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = c0 + 128 + lane + 32 * q;
+                        if (c < n_valid) axn[q] = out.aux[(int64_t)row * out.ldaux + n0 + c];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = c0 + lane + 32 * q;
+                    if (c >= n_valid) continue;
+                    const int n = n0 + c;
+                    const float d = trow[c];
+                    const int64_t oc = (int64_t)row * out.ldc + n;
+                    switch (out.epi) {
+                        case EPI_F32:
+                            if (split)
+                                atomicAdd(&out.C[oc], d);
+                            else
+                                out.C[oc] = d;
+                            break;
+                        case EPI_BIAS_F32:
+                            out.C[oc] = d + out.bias[n];
+                            break;
+                        case EPI_BIAS_GELU: {
+                            const float pre = d + out.bias[n];
+                            out.C[oc] = pre;
+                            out.Y[(int64_t)row * out.ldy + n] = __float2bfloat16(gelu(pre));
+                            break;
+                        }
+                        case EPI_DGELU:
+                            out.Y[(int64_t)row * out.ldy + n] = __float2bfloat16(d * gelu_grad(ax[q]));
+                            break;
+                        case EPI_F32_ADD:
+                            if (split)
+                                atomicAdd(&out.C[oc], d);
+                            else
+                                out.C[oc] += d;
+                            break;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ax[q] = axn[q];
             }
         }
     }
@@ -204,7 +243,9 @@ int tc_gemm(bool tf32, int M, int N, int K, const void *A, int lda, const void *
         return fitcore_fail(FIT_ERR_INVALID_ARG, "tensor-core GEMM: operands must be 16-byte aligned rows");
     int rc = get_encoder();
     if (rc) return rc;
-    const int ntn = (N + 255) / 256;
+    // Tiles of 128 x (<= 128): a 3-stage ring of 96 KB, so two CTAs share an SM and one's
+    // epilogue overlaps the other's main loop.
+    const int ntn = (N + 127) / 128;
     const int n_tile = (((N + ntn - 1) / ntn) + 15) / 16 * 16;
     // Output tiles that cannot fill the SMs (a weight gradient: small M x N, K = the batch)
     // split K over grid z; the partial products are added with atomics (plain FP32 outputs).
@@ -238,7 +279,7 @@ int tc_gemm(bool tf32, int M, int N, int K, const void *A, int lda, const void *
         if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, "tensor-core GEMM: clearing C");
     }
     dim3 grid(mt, ntn, splits);
-    kern<<<grid, 128, smem, stream>>>(ta, tb, M, N, K, n_tile, kt_per, out, err_dev);
+    kern<<<grid, kThreads, smem, stream>>>(ta, tb, M, N, K, n_tile, kt_per, out, err_dev);
     fitcore_count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

@@ -69,14 +69,34 @@ __global__ void transpose_bf16_kernel(int R, int Cn, int lds, const __nv_bfloat1
     }
 }
 
-// db[o] = sum_b d[b][o]
+// db[o] += sum_b d[b][o] (db cleared by the caller): block (32, 8) covers 64 columns (a column
+// pair per thread, read as bf16x2 along the row, so a warp reads 128 contiguous bytes) and
+// kColRows rows; partial sums meet in shared memory and go out with one atomic per column.
+constexpr int kColRows = 256;
 __global__ void colsum_kernel(int B, int n, int ld, const __nv_bfloat16 *__restrict__ d, float *__restrict__ db) {
-    const int o = blockIdx.x * blockDim.y + threadIdx.y;
-    if (o >= n) return;
-    float acc = 0.f;
-    for (int b = threadIdx.x; b < B; b += 32) acc += __bfloat162float(d[(int64_t)b * ld + o]);
-    for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
-    if (threadIdx.x == 0) db[o] = acc;
+    __shared__ float2 part[8][33];
+    const int cp = blockIdx.x * 32 + threadIdx.x;   // column pair
+    const int c = 2 * cp;
+    const int b0 = blockIdx.y * kColRows;
+    float2 acc = make_float2(0.f, 0.f);
+    if (c < n) {
+        for (int b = b0 + threadIdx.y; b < min(B, b0 + kColRows); b += 8) {
+            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(d + (int64_t)b * ld + c);
+            acc.x += __low2float(v);
+            acc.y += __high2float(v);
+        }
+    }
+    part[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < n) {
+        float2 t = part[0][threadIdx.x];
+        for (int y = 1; y < 8; ++y) {
+            t.x += part[y][threadIdx.x].x;
+            t.y += part[y][threadIdx.x].y;
+        }
+        atomicAdd(&db[c], t.x);
+        if (c + 1 < n) atomicAdd(&db[c + 1], t.y);
+    }
 }
 
 struct AdamW {
@@ -378,7 +398,9 @@ int fit_mlp_train_step(fit_mlp *m, int B, const float *x, const float *target, f
     fitcore_count_launch();
     for (int l = L - 1; l >= 0; --l) {
         const int o = m->dims[l + 1], in = m->dims[l];
-        colsum_kernel<<<(o + 7) / 8, dim3(32, 8), 0, s>>>(B, o, m->ld[l + 1], m->dpre[l], m->gb[l]);
+        cudaMemsetAsync(m->gb[l], 0, sizeof(float) * o, s);
+        colsum_kernel<<<dim3((o + 63) / 64, (B + kColRows - 1) / kColRows), dim3(32, 8), 0, s>>>(B, o, m->ld[l + 1],
+                                                                                               m->dpre[l], m->gb[l]);
         // dW = dpre^T act: operands as K-major rows over the batch
         transpose_bf16_kernel<<<dim3((o + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s>>>(B, o, m->ld[l + 1], m->dpre[l],
                                                                                         Bp, m->tA);
