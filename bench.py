@@ -155,7 +155,14 @@ def make_workload(B, seed, rank):
     return spec, model, data, inst
 
 
+_COLL_DEVICE = "cpu"
+
+
 def dist_setup(args):
+    """Rank layout from the torchrun environment; NCCL with one GPU per rank when CUDA is
+    present, gloo on the host otherwise (the path has no collective on its data; only the
+    barrier and the max of the step times cross ranks)."""
+    global _COLL_DEVICE
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -163,8 +170,13 @@ def dist_setup(args):
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            _COLL_DEVICE = "cuda"
+        else:
+            dist.init_process_group("gloo")
+            _COLL_DEVICE = "cpu"
         pg = dist
     return world, rank, local, pg
 
@@ -180,7 +192,7 @@ def max_over_ranks(x, pg):
     if pg is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_COLL_DEVICE)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
 
@@ -339,6 +351,8 @@ def run_reference(args):
     """Reference arm: the FP64 oracle timed on the host cores on the same workload."""
     world, rank, _, pg = dist_setup(args)
     if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
         return
     from paper_2502_15253_gb300 import synth
     import oracle
@@ -370,6 +384,8 @@ def run_reference(args):
                          "sample": f"{n} instances per step on {cores} host threads"},
         "e2e": {"value": val, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+    if pg is not None:
+        pg.destroy_process_group()
 
 
 def run_ours(args):

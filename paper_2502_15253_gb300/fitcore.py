@@ -492,3 +492,42 @@ def fit_numpy(models, inst, data, start=None, opts=None):
         start = np.ascontiguousarray(start, dtype=np.float64)
     fit_batch(models, inst, data, start, best, res, opts)
     return best, res
+
+
+# ---- torch autograd wrapper ------------------------------------------------------------------
+def _autograd_function():
+    import torch
+
+    class FitNLL(torch.autograd.Function):
+        """-2lnL of a batch of parameter vectors as a differentiable torch op.
+
+        forward(theta [B, P] float64 CUDA tensor, data [B, n_data] float32 CUDA tensor or None
+        (the model's Asimov data), model, masks [B] uint32 tensor or None) -> nll [B] float64.
+        The gradient comes from the library's adjoint (fit_model_eval); backward returns
+        grad_output[:, None] * d(-2lnL)/dtheta.
+        """
+
+        @staticmethod
+        def forward(ctx, theta, data, model, masks=None):
+            if not (theta.is_cuda and theta.dtype == torch.float64 and theta.dim() == 2):
+                raise ValueError("theta must be a [B, P] float64 CUDA tensor")
+            th = theta.detach().contiguous()
+            B = th.shape[0]
+            nll = torch.empty(B, dtype=torch.float64, device=th.device)
+            grad = torch.empty((B, model.n_params), dtype=torch.float32, device=th.device)
+            dd = data.detach().contiguous() if data is not None else None
+            fit_model_eval(model, B, th, dd, masks, nll, grad)
+            ctx.save_for_backward(grad)
+            return nll
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (grad,) = ctx.saved_tensors
+            return grad_out[:, None] * grad.to(grad_out.dtype), None, None, None
+
+    return FitNLL
+
+
+def fit_nll(theta, data, model, masks=None):
+    """Differentiable -2lnL (see FitNLL)."""
+    return _autograd_function().apply(theta, data, model, masks)
