@@ -145,20 +145,6 @@ __device__ __forceinline__ void block_sum_d(double (&v)[N], double *red, double 
     __syncthreads();
 }
 
-// Per-warp partial sums of a dataset's scalar gradient terms: each warp sums its lanes and
-// lane 0 stores the first n_used totals at part[warp * stride + i]; ds_flush_* later add the
-// warps in a fixed order, so no block-wide reduction (and no barrier) is needed here.
-template <int N>
-__device__ __forceinline__ void warp_partials(float (&v)[N], float *part, int stride, int n_used) {
-    warp_sum<N>(v);
-    if ((threadIdx.x & 31) == 0) {
-        const int w = threadIdx.x >> 5;
-#pragma unroll
-        for (int i = 0; i < N; ++i)
-            if (i < n_used) part[w * stride + i] = v[i];
-    }
-}
-
 // ------------------------------------------------------------------------------------
 // Survival probability with phase arithmetic in float pairs.
 // ------------------------------------------------------------------------------------
@@ -344,12 +330,6 @@ __device__ __forceinline__ PP ppair(const DevModel &m, const float *pv, const fl
 }
 
 __device__ __forceinline__ float pmul(PP a, float x) { return fmaf(x, a.l, x * a.h); }
-
-// Strides of the per-warp partial sums (shared scratch of kMaxWarps * stride floats each):
-// likelihood stage: deviance, d/d efficiency, d/d rate_b; adjoint stage: d/d (a0, a1, a2),
-// d/d eta (4), d/d norm, d/d power_c.
-constexpr int kPartLik = 2 + kMaxBkgDs;
-constexpr int kPartAdj = 8 + FIT_MAX_CORES;
 
 // Status bits raised during an evaluation
 constexpr int kStMuNonpos = 1;
@@ -568,9 +548,9 @@ static __device__ void ds_remap(const DevModel &m, int d, const DsCtx &c, EvalWs
 // Stages C and C2: fold, backgrounds, deviance, dD/dmu (ws.gmu) and the background-shape
 // gradient; returns the dataset's -2lnL (all threads). The efficiency and rate gradients are
 // added when grad != nullptr, data != nullptr and no status bit is set.
-static __device__ void ds_fold_lik(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
-                                   const float *data, EvalWs ws, float *grad, float *part, int *status,
-                                   float *mu_out) {
+static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
+                                     const float *data, EvalWs ws, float *grad, double *red, int *status,
+                                     float *mu_out) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
     const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
@@ -616,10 +596,10 @@ static __device__ void ds_fold_lik(const DevModel &m, int d, const float *pv, co
 
     // ---- stage C2: backgrounds, deviance, dD/dmu ----------------------------------------
     const int nb = ds.bkg_end - ds.bkg_begin;
-    float lp[kPartLik];
-    // lp[0] = deviance, lp[1] = d/d eff, lp[2+b] = d/d rate_b
+    float part[2 + kMaxBkgDs];
+    // part[0] = deviance, part[1] = d/d eff, part[2+b] = d/d rate_b
 #pragma unroll
-    for (int i = 0; i < kPartLik; ++i) lp[i] = 0.f;
+    for (int i = 0; i < 2 + kMaxBkgDs; ++i) part[i] = 0.f;
     for (int j = tid; j < nr; j += nth) {
         float mu = pmul(c.eff, ws.f0[j]);
 #pragma unroll
@@ -637,49 +617,44 @@ static __device__ void ds_fold_lik(const DevModel &m, int d, const float *pv, co
             atomicOr(status, kStMuNonpos);
             continue;
         }
-        lp[0] += deviance(n, mu);
+        part[0] += deviance(n, mu);
         const float g = 2.f * (mu - n) / mu;
         ws.gmu[j] = g;
         if (grad) {
-            lp[1] = fmaf(g, ws.f0[j], lp[1]);
+            part[1] = fmaf(g, ws.f0[j], part[1]);
 #pragma unroll
             for (int b = 0; b < kMaxBkgDs; ++b) {
                 if (b >= nb) break;
                 const DevBkg &bk = m.bkg[ds.bkg_begin + b];
                 const int si = bk.shape_idx[j];
                 const float sh = 1.f + (si >= 0 ? pv[si] : 0.f);
-                lp[2 + b] = fmaf(g * bk.tmpl[j], sh, lp[2 + b]);
+                part[2 + b] = fmaf(g * bk.tmpl[j], sh, part[2 + b]);
                 if (si >= 0) atomicAdd(&grad[si], g * pval(pv, bk.rate_idx, 1.f) * bk.tmpl[j]);
             }
         }
     }
-    warp_partials<kPartLik>(lp, part, kPartLik, 2 + nb);
-    __syncthreads();
-}
-
-// After ds_fold_lik: adds the dataset's -2lnL to *nll (one thread) and, with `with_grad` and no
-// status bit set, its efficiency and rate gradients to grad (distinct parameters, a thread each).
-static __device__ void ds_flush_lik(const DevModel &m, int d, const float *part, float *grad, const int *status,
-                                    double *nll, bool with_grad) {
-    const DevDataset &ds = m.ds[d];
-    const int nb = ds.bkg_end - ds.bkg_begin, nw = blockDim.x >> 5, i = threadIdx.x;
-    if (i >= 2 + nb) return;
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += (double)part[w * kPartLik + i];
-    if (i == 0) {
-        *nll += t;
-        return;
+    double tot[2 + kMaxBkgDs];
+    block_sum<2 + kMaxBkgDs>(part, red, tot);
+    const double nll_d = tot[0];
+    if (data == nullptr || grad == nullptr || (*(volatile int *)status) != 0) return nll_d;
+    if (tid == 0) {
+        if (ds.eff_idx >= 0) grad[ds.eff_idx] += (float)tot[1];
+#pragma unroll
+        for (int b = 0; b < kMaxBkgDs; ++b) {
+            if (b >= nb) break;
+            const int ri = m.bkg[ds.bkg_begin + b].rate_idx;
+            if (ri >= 0) grad[ri] += (float)tot[2 + b];
+        }
     }
-    if (!with_grad || *(volatile const int *)status != 0) return;
-    const int p = i == 1 ? ds.eff_idx : m.bkg[ds.bkg_begin + i - 2].rate_idx;
-    if (p >= 0) grad[p] += (float)t;
+
+    return nll_d;
 }
 
 // Stages D, E and F: adjoint of the fold, of the energy map and of the signal; adds the
 // gradient contributions to grad. Needs ws.u/ts/ptot/dp/pcw (ds_signal<true>) and ws.gmu.
 template <int NC>
 static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
-                                     EvalWs ws, float *grad, float *part) {
+                                  EvalWs ws, float *grad, double *red) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
     const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
@@ -748,8 +723,18 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
             if (cc < C) ep[8 + cc] = fmaf(gb, ws.pcw[cc * N_t + k], ep[8 + cc]);
         ws.dp[k] = pmul(c.nrm, gu * ds.t[k] * pt);    // d nll / d s for this bin (dp0 reused)
     }
-    warp_partials<8 + NC>(ep, part, kPartAdj, 8 + C);
-    __syncthreads();
+    double etot[8 + NC];
+    block_sum<8 + NC>(ep, red, etot);
+    if (tid == 0) {
+        for (int i = 0; i < 3; ++i)
+            if (ds.esc_idx[i] >= 0) grad[ds.esc_idx[i]] += (float)etot[i];
+        for (int i = 0; i < 4; ++i)
+            if (m.osc_idx[i] >= 0) grad[m.osc_idx[i]] += (float)etot[3 + i];
+        if (ds.norm_idx >= 0) grad[ds.norm_idx] += (float)etot[7];
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc)
+            if (cc < C && m.core_power_idx[cc] >= 0) grad[m.core_power_idx[cc]] += (float)etot[8 + cc];
+    }
     // ---- stage F: shape reweights (one thread per distinct parameter, CSR over bins) -----
     for (int i = tid; i < ds.n_sp; i += nth) {
         float s = 0.f;
@@ -759,57 +744,32 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
     __syncthreads();
 }
 
-// Stages D-F with the per-core sums sized for the model's core count. Ends with a barrier.
+// One dataset in one sequence: adds its Poisson -2lnL and (if grad != nullptr) its gradient
+// contributions (theta space, P floats). Returns the dataset's -2lnL (all threads); *status |=
+// kSt* bits on failure.
+// Stages D-F with the per-core sums sized for the model's core count.
 static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
-                                  EvalWs ws, float *grad, float *part) {
+                                  EvalWs ws, float *grad, double *red) {
     if (m.C <= 2)
-        ds_adjoint_nc<2>(m, d, pv, pd, c, ws, grad, part);
+        ds_adjoint_nc<2>(m, d, pv, pd, c, ws, grad, red);
     else
-        ds_adjoint_nc<FIT_MAX_CORES>(m, d, pv, pd, c, ws, grad, part);
+        ds_adjoint_nc<FIT_MAX_CORES>(m, d, pv, pd, c, ws, grad, red);
 }
 
-// After ds_adjoint: adds the energy-scale, survival, normalisation and core-power gradients
-// (distinct parameters, a thread each, warps summed in a fixed order).
-static __device__ void ds_flush_adj(const DevModel &m, int d, const float *part, float *grad) {
-    const DevDataset &ds = m.ds[d];
-    const int nw = blockDim.x >> 5, i = threadIdx.x;
-    if (i >= 8 + m.C) return;
-    int p;
-    if (i < 3)
-        p = ds.esc_idx[i];
-    else if (i < 7)
-        p = m.osc_idx[i - 3];
-    else if (i == 7)
-        p = ds.norm_idx;
-    else
-        p = m.core_power_idx[i - 8];
-    if (p < 0) return;
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += (double)part[w * kPartAdj + i];
-    grad[p] += (float)t;
-}
-
-// One dataset in one sequence: adds its Poisson -2lnL to *nll (one thread; read it after a
-// barrier) and (if grad != nullptr) its gradient contributions (theta space, P floats).
-// *status |= kSt* bits on failure. part: shared scratch of kMaxWarps * (kPartLik + kPartAdj)
-// floats.
-static __device__ void eval_dataset(const DevModel &m, int d, const float *pv, const float *pd,
-                                    const float *data, EvalWs ws, float *grad, float *part, double *nll,
-                                    int *status, float *mu_out) {
+static __device__ double eval_dataset(const DevModel &m, int d, const float *pv, const float *pd,
+                                      const float *data, EvalWs ws, float *grad, double *red,
+                                      int *status, float *mu_out) {
     DsCtx c;
-    if (!ds_setup(m, d, pv, pd, c, status)) return;
-    const bool with_grad = grad != nullptr && data != nullptr;
-    if (with_grad)
+    if (!ds_setup(m, d, pv, pd, c, status)) return 0.0;
+    if (grad != nullptr && data != nullptr)
         ds_signal<true>(m, d, pv, pd, c, ws);
     else
         ds_signal<false>(m, d, pv, pd, c, ws);
     ds_remap(m, d, c, ws);
-    float *part_lik = part, *part_adj = part + kMaxWarps * kPartLik;
-    ds_fold_lik(m, d, pv, pd, c, data, ws, grad, part_lik, status, mu_out);
-    ds_flush_lik(m, d, part_lik, grad, status, nll, with_grad);
-    if (!with_grad || (*(volatile int *)status) != 0) return;
-    ds_adjoint(m, d, pv, pd, c, ws, grad, part_adj);
-    ds_flush_adj(m, d, part_adj, grad);
+    const double nll_d = ds_fold_lik(m, d, pv, pd, c, data, ws, grad, red, status, mu_out);
+    if (data == nullptr || grad == nullptr || (*(volatile int *)status) != 0) return nll_d;
+    ds_adjoint(m, d, pv, pd, c, ws, grad, red);
+    return nll_d;
 }
 
 }  // namespace fitcore

@@ -77,8 +77,6 @@ __device__ double prior_theta(const DevModel &m, const float *pd, float *grad, f
 struct EvalSmem {
     DevModel m;
     double red[kMaxWarps * 24 + 24];
-    float part[kMaxWarps * (kPartLik + kPartAdj)];
-    double nll;
     int status;
 };
 
@@ -111,23 +109,21 @@ __global__ void __launch_bounds__(256) eval_kernel(const DevModel *__restrict__ 
             pd[i] = (float)(t - m.theta0[i]);
             grad[i] = 0.f;
         }
-        if (threadIdx.x == 0) {
-            S.status = 0;
-            S.nll = 0.0;
-        }
+        if (threadIdx.x == 0) S.status = 0;
         __syncthreads();
         const float *dat = mu_out ? nullptr : (data ? data + (int64_t)b * m.n_data : m.asimov);
         const uint32_t mask = masks ? masks[b] : 0xffffffffu;
+        double nll = 0.0;
         for (int d = 0; d < m.n_ds; ++d) {
             const bool on = mu_out ? true : ((mask >> d) & 1u);
             if (!on) continue;
             float *mo = mu_out ? mu_out + (int64_t)b * m.n_data + m.ds[d].data_off : nullptr;
-            eval_dataset(m, d, pv, pd, dat, ws, want_grad ? grad : nullptr, S.part, &S.nll, &S.status, mo);
+            nll += eval_dataset(m, d, pv, pd, dat, ws, want_grad ? grad : nullptr, S.red,
+                                &S.status, mo);
             __syncthreads();
             if (S.status) break;
         }
         const int st = S.status;
-        double nll = S.nll;
         if (mu_out == nullptr && st == 0) nll += prior_theta(m, pd, want_grad ? grad : nullptr, zs, S.red);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -177,8 +173,6 @@ struct FitState {
 struct alignas(16) FitSmem {
     DevModel m;
     double red[kMaxWarps * 24 + 24];
-    float part[kMaxWarps * (kPartLik + kPartAdj)];   // per-warp partial sums of an evaluation
-    double nll;
     FitState st;
     double dots[kNDots];       // fused pass: S.y_new | Y.y_new | S.g | Y.g | g.g
     float cs[kMaxHist], cy[kMaxHist];   // d = -(cg g + sum cs_j s_j + sum cy_j y_j)
@@ -450,19 +444,16 @@ __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &
                          const float *data, uint32_t mask, FitSmem &S) {
     theta_of_z(m, z, V.pv, V.pd);
     for (int i = threadIdx.x; i < m.P; i += blockDim.x) V.gth[i] = 0.f;
-    if (threadIdx.x == 0) {
-        S.status = 0;
-        S.nll = 0.0;
-    }
+    if (threadIdx.x == 0) S.status = 0;
     __syncthreads();
+    double nll = 0.0;
     for (int d = 0; d < m.n_ds; ++d) {
         if (!((mask >> d) & 1u)) continue;
-        eval_dataset(m, d, V.pv, V.pd, data, ws, V.gth, S.part, &S.nll, &S.status, nullptr);
+        nll += eval_dataset(m, d, V.pv, V.pd, data, ws, V.gth, S.red, &S.status, nullptr);
         __syncthreads();
         if (S.status) return INFINITY;
     }
-    const double prior = eval_z_prior(m, z, V.gth, gz, S.red);   // (contains barriers)
-    return S.nll + prior;
+    return nll + eval_z_prior(m, z, V.gth, gz, S.red);
 }
 
 // cubic minimiser through (a, fa, ga), (b, fb, gb), or the secant of the slopes when the
@@ -870,8 +861,7 @@ size_t ls_step_smem_bytes() { return sizeof(FitSmem); }
 
 struct LsEvalSmem {
     DevModel m;
-    float part[kMaxWarps * (kPartLik + kPartAdj)];
-    double nll;
+    double red[kMaxWarps * 24 + 24];
     int status;
 };
 
@@ -962,24 +952,22 @@ __global__ void __launch_bounds__(128) ls_forward_kernel(LsArgs A) {
             pv[i] = V.pv[i];
             pd[i] = V.pd[i];
         }
-        if (threadIdx.x == 0) {
-            S.status = 0;
-            S.nll = 0.0;
-        }
+        if (threadIdx.x == 0) S.status = 0;
         __syncthreads();
         DsCtx c;
+        double nll = 0.0;
         if (ds_setup(m, d, pv, pd, c, &S.status)) {
             ds_signal<false>(m, d, pv, pd, c, ws);
             ds_remap(m, d, c, ws);
-            ds_fold_lik(m, d, pv, pd, c, A.data + in.data_off, ws, A.gsl + gd * P, S.part, &S.status, nullptr);
-            ds_flush_lik(m, d, S.part, A.gsl + gd * P, &S.status, &S.nll, true);
+            nll = ds_fold_lik(m, d, pv, pd, c, A.data + in.data_off, ws, A.gsl + gd * P, S.red, &S.status,
+                              nullptr);
             const int nr = m.ds[d].n_reco;
             float *gm = A.gmu + gd * m.max_reco;
             for (int j = threadIdx.x; j < nr; j += blockDim.x) gm[j] = ws.gmu[j];
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            A.nll_ds[gd] = S.nll;
+            A.nll_ds[gd] = nll;
             if (S.status) atomicOr(&A.stat[g], S.status);
         }
         __syncthreads();
@@ -1016,8 +1004,7 @@ __global__ void __launch_bounds__(128) ls_adjoint_kernel(LsArgs A) {
         DsCtx c;
         if (ds_setup(m, d, pv, pd, c, &S.status)) {
             ds_signal<true>(m, d, pv, pd, c, ws);
-            ds_adjoint(m, d, pv, pd, c, ws, A.gsl + gd * P, S.part);
-            ds_flush_adj(m, d, S.part, A.gsl + gd * P);
+            ds_adjoint(m, d, pv, pd, c, ws, A.gsl + gd * P, S.red);
         }
         __syncthreads();
     }
