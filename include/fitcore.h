@@ -162,7 +162,8 @@ typedef struct fit_instance {
 typedef struct fit_batch_opts {
     double edm_tol;       /* stop when EDM = 1/2 g^T H g < edm_tol (default 1e-8)             */
     int max_iter;         /* iteration limit (default 2000)                                  */
-    int history;          /* L-BFGS pairs kept, 1..16 (default 16)                           */
+    int history;          /* L-BFGS pairs kept, 1..32 (default 32; the two-loop recursion runs
+                             on one warp, a lane per pair)                                   */
     double f_noise_rel;   /* relative noise allowance of -2lnL in the line search (1e-6)     */
     int threads;          /* threads per block, multiple of 32 in [64, 128]; 0 = default 128 */
     int blocks_per_sm;    /* resident blocks per SM: 5 selects the 96-register build of the

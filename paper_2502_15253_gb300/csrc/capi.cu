@@ -1186,7 +1186,7 @@ void fit_batch_default_opts(fit_batch_opts *o) {
     if (!o) return;
     o->edm_tol = 1e-8;
     o->max_iter = 2000;
-    o->history = 16;
+    o->history = 32;
     o->f_noise_rel = 1e-6;
     o->threads = 0;
     o->blocks_per_sm = 0;
@@ -1207,7 +1207,7 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
     fit_batch_opts o;
     fit_batch_default_opts(&o);
     if (opts_in) o = *opts_in;
-    if (o.history < 1 || o.history > 16) return fail(FIT_ERR_INVALID_ARG, "fit_batch: history must be 1..16");
+    if (o.history < 1 || o.history > 32) return fail(FIT_ERR_INVALID_ARG, "fit_batch: history must be 1..32");
     if (o.restarts < 0 || o.restarts > 8) return fail(FIT_ERR_INVALID_ARG, "fit_batch: restarts must be 0..8");
     if (o.threads == 0) o.threads = 128;
     if (o.threads < 64 || o.threads > 128 || o.threads % 32)

@@ -697,19 +697,19 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
     for (int k = tid; k < N_t; k += nth) {
         const float e0 = m.e_edge[k], e1 = m.e_edge[k + 1];
         const float d0 = em.disp(e0), d1 = em.disp(e1);
-        const float w = 1.f + (d1 - d0);
+        const float w = 1.f + (d1 - d0), iw = 1.f / w;
         const int f0i = (int)floorf(d0), f1i = (int)floorf(d1);
         const int t0 = k + f0i, t1 = k + 1 + f1i;
         float gu = 0.f;
         for (int t = max(t0, 0); t <= min(t1, N_t - 1); ++t) {
             const float ylo = (float)(k - t) + d0, yhi = (float)(k + 1 - t) + d1;
             const float ov = fminf(yhi, 1.f) - fmaxf(ylo, 0.f);
-            if (ov > 0.f) gu = fmaf(ov / w, gv[t], gu);
+            if (ov > 0.f) gu = fmaf(ov * iw, gv[t], gu);
         }
         const float g0 = (t0 >= 0 && t0 < N_t) ? gv[t0] : 0.f;
         const float g1 = (t1 >= 0 && t1 < N_t) ? gv[t1] : 0.f;
-        const float uk = ws.u[k];
-        const float A0 = uk * (gu - g0) / w, A1 = uk * (g1 - gu) / w;
+        const float uk = ws.u[k] * iw;
+        const float A0 = uk * (gu - g0), A1 = uk * (g1 - gu);
         ep[0] += (A0 + A1) * em.inv_de;
         ep[1] += (A0 * e0 + A1 * e1) * em.inv_de;
         ep[2] += (A0 * e0 * e0 + A1 * e1 * e1) * em.inv_de;

@@ -148,7 +148,7 @@ size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem) {
 // ------------------------------------------------------------------------------------
 // persistent batched L-BFGS
 // ------------------------------------------------------------------------------------
-constexpr int kMaxHist = 16;
+constexpr int kMaxHist = 32;
 constexpr int kNDots = 4 * kMaxHist + 1;
 
 // Minimiser state of one fit between two evaluations: in shared memory while a block works on

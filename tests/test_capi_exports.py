@@ -46,7 +46,7 @@ def test_struct_layouts_match_header_sizes():
 def test_default_opts_and_error_message_without_gpu():
     L = fitcore.load(build_if_missing=True)
     o = fitcore.fit_batch_default_opts()
-    assert o.history == 16 and o.max_iter > 0 and o.edm_tol > 0
+    assert o.history == 32 and o.max_iter > 0 and o.edm_tol > 0
     # invalid arguments are rejected on the host before any device work
     rc = L.fit_model_create(None, None)
     assert rc == -1

@@ -35,7 +35,10 @@ def test_placements_and_builds_agree(work):
     spec, gm, data, inst = work
     best0, r0 = _fit(gm, inst, data)
     assert np.all(r0["status"] == 0)
-    for kw in [dict(placement=1), dict(placement=2), dict(placement=3),
+    with pytest.raises(fitcore.FitError):
+        _fit(gm, inst, data, placement=1)   # 32 pairs of 291 floats do not fit beside the rest
+    # (all in shared memory fits the 291-parameter model only with a shorter history)
+    for kw in [dict(placement=1, history=16), dict(placement=2), dict(placement=3),
                dict(placement=3, blocks_per_sm=5), dict(placement=2, blocks_per_sm=4),
                dict(threads=96), dict(threads=64, placement=3)]:
         best, r = _fit(gm, inst, data, **kw)
