@@ -223,33 +223,49 @@ __device__ __forceinline__ double bdot(const float *a, const float *b, int n, do
 __device__ void fused_dots(const float *Sv, const float *Yv, const float *ynew, const float *g, int P,
                            unsigned occ, double *out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int q = warp; q < kNDots; q += nw) {
-        const float *a, *b;
-        if (q == kNDots - 1) {
-            a = g;
-            b = g;
-        } else {
-            const int type = q / kMaxHist, slot = q % kMaxHist;
-            if (!((occ >> slot) & 1u) || (type < 2 && ynew == nullptr)) continue;
-            a = ((type & 1) ? Yv : Sv) + (int64_t)slot * fit_vec_pitch(P);
-            b = (type < 2) ? ynew : g;
+    const int pitch = fit_vec_pitch(P);
+    // Each warp takes four products at a time, so four independent 16-byte loads per lane are
+    // in flight before the first shuffle reduction.
+    for (int q0 = warp * 4; q0 < kNDots; q0 += nw * 4) {
+        const float *a[4], *b[4];
+        bool on[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u;
+            on[u] = q < kNDots;
+            a[u] = g;
+            b[u] = g;
+            if (on[u] && q < kNDots - 1) {
+                const int type = q / kMaxHist, slot = q % kMaxHist;
+                on[u] = ((occ >> slot) & 1u) && !(type < 2 && ynew == nullptr);
+                a[u] = ((type & 1) ? Yv : Sv) + (int64_t)slot * pitch;
+                b[u] = (type < 2) ? ynew : g;
+            }
         }
-        // 16-byte loads over the whole quads (vectors start 16-byte aligned), then the tail
-        const float4 *a4 = reinterpret_cast<const float4 *>(a), *b4 = reinterpret_cast<const float4 *>(b);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
         for (int k = lane; k < (P >> 2); k += 32) {
-            const float4 x = a4[k], y = b4[k];
-            a0 = fmaf(x.x, y.x, a0);
-            a1 = fmaf(x.y, y.y, a1);
-            a2 = fmaf(x.z, y.z, a2);
-            a3 = fmaf(x.w, y.w, a3);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!on[u]) continue;
+                const float4 x = reinterpret_cast<const float4 *>(a[u])[k];
+                const float4 y = reinterpret_cast<const float4 *>(b[u])[k];
+                acc[u] = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, acc[u]))));
+            }
         }
         const int tail = (P & ~3) + lane;
-        if (tail < P) a0 = fmaf(a[tail], b[tail], a0);
-        float acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) out[q] = (double)acc;
+        for (int u = 0; u < 4; ++u)
+            if (on[u] && tail < P) acc[u] = fmaf(a[u][tail], b[u][tail], acc[u]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (on[u]) out[q0 + u] = (double)acc[u];
+        }
     }
     __syncthreads();
 }

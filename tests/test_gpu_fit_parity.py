@@ -131,11 +131,12 @@ def test_fit_c2_matches_oracle(engine):
 def test_fit_c1_ensemble_statistics(engine):
     """64 pseudo-experiments of the three-dataset model: at most 1 in 8 may stop in another
     (certified) minimum; all others match the oracle's minimum within 1e-3 in -2lnL and
-    1e-2 sigma in every parameter, and at least 60 % within 1e-3 sigma (64-73 % measured
-    across kernel versions: the share moves with FP32 rounding in the flat Li-9 direction)."""
+    1e-2 sigma in every parameter, and at least 85 % within 1e-3 sigma (60/64 measured with
+    the 32-pair history; the share moves with FP32 rounding in the flat Li-9 direction and was
+    64-75 % with 16 pairs)."""
     datas, masks, _ = make_instances("c1", 64, 600)
     th, res = run_gpu(["c1"] * 64, datas, masks, opts=engine_opts(engine))
-    check_against_oracle("c1", datas, masks, th, res, max_other=8, min_strict=0.6)
+    check_against_oracle("c1", datas, masks, th, res, max_other=8, min_strict=0.85)
 
 
 @ENGINES
