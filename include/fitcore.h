@@ -337,6 +337,37 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
                         int n_geoms, int n_steps, int batch, float lr, float weight_decay,
                         uint64_t seed, double *losses_out, void *stream);
 
+/* fit_batch with held parameters: fixed (host or device, indexed like start / best, or NULL)
+ * marks parameters kept at their start values, e.g. the scanned parameters of a profile
+ * likelihood (Eq. 7). Only parameters outside the covariance blocks can be held (their whitened
+ * coordinate is the parameter itself); others give FIT_ERR_INVALID_ARG. */
+int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst,
+                 const float *data, const double *start, const uint8_t *fixed, double *best,
+                 fit_result *results, const fit_batch_opts *opts, void *stream);
+
+/* Profile likelihood on a raster (Eq. 7: -2 ln lambda = -2lnL(held point, best nuisances) -
+ * -2lnL(best)): one launch fits the data vector (host or device, n_data floats, dataset mask
+ * `mask`) without constraint and at each of the n_points rows of `points` (host, [n_points x
+ * n_scan], values of the parameters scan_idx[0..n_scan), held fixed), all from `start` (host or
+ * device, P doubles, or NULL = theta0). Outputs (host): *nll_min (the lowest -2lnL met, normally
+ * the unconstrained fit), theta_best [P] or NULL, dchi2 [n_points] (-2 ln lambda), theta_points
+ * [n_points x P] or NULL, status [n_points] or NULL. Synchronous. */
+int fit_profile_scan(fit_model *model, const float *data, uint32_t mask, int n_scan,
+                     const int *scan_idx, int n_points, const double *points, const double *start,
+                     const fit_batch_opts *opts, double *nll_min, double *theta_best, double *dchi2,
+                     double *theta_points, int *status, void *stream);
+
+/* Wilks interval from a 1-D profile: the points x (increasing) where dchi2 crosses `level`
+ * (1 for 68.27 %, 3.84 for 95 % with one parameter, Wilks' theorem), linearly between raster
+ * points, on each side of the raster minimum. Returns 0, or bit 1 / bit 2 when the lower /
+ * upper side stays below `level` up to the raster edge (then that edge is returned). */
+int fit_wilks_interval(int n, const double *x, const double *dchi2, double level, double *lo,
+                       double *hi);
+
+/* Goodness of fit: P(chi^2_dof >= chi2), the p-value of a deviance (Eq. 8) with dof degrees of
+ * freedom. NaN for dof < 1 or chi2 < 0. */
+double fit_chi2_sf(double chi2, int dof);
+
 /* Chooses threads per block and resident blocks per SM for fit_batch on the current device by
  * timing the candidate configurations (96 or 128 threads, 4 or 5 blocks per SM) on the first
  * n_sample instances (0 = ten per SM, at most n_inst), and writes the fastest into

@@ -33,7 +33,8 @@ _SRCS = [_SRC, os.path.join(_HERE, "rng.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
-STATUS = {0: "converged", 1: "maxiter", 2: "linesearch_fail", 3: "nonfinite"}
+STATUS = {0: "converged", 1: "maxiter", 2: "linesearch_fail", 3: "nonfinite",
+          4: "fixed parameter inside a prior block"}
 
 
 def build(force: bool = False) -> str:
@@ -111,6 +112,9 @@ def _declare(L):
     L.orc_fit.restype = C.c_int
     L.orc_fit.argtypes = [C.c_void_p, _DP, C.c_uint32, _DP, C.c_double, C.c_int, _DP, _DP, _IP,
                           _IP, _DP]
+    L.orc_fit_ex.restype = C.c_int
+    L.orc_fit_ex.argtypes = [C.c_void_p, _DP, C.c_uint32, _DP, C.POINTER(C.c_ubyte), C.c_double,
+                             C.c_int, _DP, _DP, _IP, _IP, _DP]
     L.orc_fit_many.argtypes = [C.POINTER(C.c_void_p), C.c_int, _IP, C.POINTER(_DP),
                                C.POINTER(C.c_uint32), C.POINTER(_DP), C.c_double, C.c_int,
                                C.POINTER(_DP), _DP, _IP, _IP, _IP, C.c_int]
@@ -257,8 +261,12 @@ class OracleModel:
         return z
 
     # -- minimiser ----------------------------------------------------------------------
-    def fit(self, data, mask=None, start=None, edm_tol=1e-10, max_iter=5000):
-        """Dense BFGS fit. Returns dict(theta, nll, iters, nevals, edm, status)."""
+    def fit(self, data, mask=None, start=None, edm_tol=1e-10, max_iter=5000, fixed=None):
+        """Dense BFGS fit. Returns dict(theta, nll, iters, nevals, edm, status).
+
+        fixed: optional boolean array over the parameters held at their start values (the
+        constrained fit of a profile likelihood); parameters inside a prior block cannot be
+        fixed (status 4)."""
         mask = self.spec.all_mask() if mask is None else mask
         start = self.spec.theta0 if start is None else start
         da, dp = _d(data)
@@ -266,9 +274,13 @@ class OracleModel:
         th = np.zeros(self.n_params)
         nll, edm = C.c_double(), C.c_double()
         it, ne = C.c_int(), C.c_int()
-        st = lib().orc_fit(self.h, dp, C.c_uint32(mask), sp, edm_tol, max_iter,
-                           th.ctypes.data_as(_DP), C.byref(nll), C.byref(it), C.byref(ne),
-                           C.byref(edm))
+        fx = None
+        if fixed is not None:
+            fa = np.ascontiguousarray(np.asarray(fixed, dtype=bool), dtype=np.uint8)
+            fx = fa.ctypes.data_as(C.POINTER(C.c_ubyte))
+        st = lib().orc_fit_ex(self.h, dp, C.c_uint32(mask), sp, fx, edm_tol, max_iter,
+                              th.ctypes.data_as(_DP), C.byref(nll), C.byref(it), C.byref(ne),
+                              C.byref(edm))
         return dict(theta=th, nll=nll.value, iters=it.value, nevals=ne.value, edm=edm.value,
                     status=st)
 

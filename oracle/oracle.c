@@ -38,7 +38,7 @@
 
 #define ORC_K_OSC 1.266932679815373 /* dm2[eV^2] L[m] / (4 E[MeV]) -> phase, from hbar c */
 
-enum { ORC_OK = 0, ORC_MAXITER = 1, ORC_LINESEARCH_FAIL = 2, ORC_NONFINITE = 3 };
+enum { ORC_OK = 0, ORC_MAXITER = 1, ORC_LINESEARCH_FAIL = 2, ORC_NONFINITE = 3, ORC_BAD_FIXED = 4 };
 
 typedef struct {
     int n_params;
@@ -595,13 +595,20 @@ typedef struct {
     uint32_t mask;
     double *theta, *gt;
     int n_evals;
+    const unsigned char *fixed;   /* parameters held at their start value, or NULL */
 } objective;
 
+/* A fixed parameter (one outside the prior blocks, so that its z coordinate is the parameter
+ * itself up to a scale) gets a zero z-gradient: the BFGS directions then never move it, which
+ * is the constrained minimisation of the profile likelihood (Eq. 7, likelihood ratio). */
 static double obj_eval(objective *o, const double *z, double *gz)
 {
     theta_of_z(o->h, z, o->theta);
     double f = orc_nll(o->h, o->theta, o->data, o->mask, o->gt);
     grad_z_of_theta(o->h, o->gt, gz);
+    if (o->fixed)
+        for (int i = 0; i < o->h->m.n_params; ++i)
+            if (o->fixed[i]) gz[i] = 0.0;
     o->n_evals++;
     return f;
 }
@@ -697,13 +704,17 @@ static int line_search(objective *o, int n, const double *z, double f0, const do
 /* Minimises -2lnL(theta(z)) from theta_start. Writes the best fit to theta_out and returns a
  * status: 0 converged (EDM < edm_tol), 1 iteration limit, 2 line search failed, 3 non-finite
  * start. */
-int orc_fit(const orc_handle *h, const double *data, uint32_t mask, const double *theta_start,
-            double edm_tol, int max_iter, double *theta_out, double *nll_out, int *iters_out,
-            int *nevals_out, double *edm_out)
+int orc_fit_ex(const orc_handle *h, const double *data, uint32_t mask, const double *theta_start,
+               const unsigned char *fixed, double edm_tol, int max_iter, double *theta_out, double *nll_out,
+               int *iters_out, int *nevals_out, double *edm_out)
 {
     const orc_model *m = &h->m;
     int n = m->n_params;
-    objective o = {h, data, mask, (double *)malloc(sizeof(double) * n), (double *)malloc(sizeof(double) * n), 0};
+    if (fixed)
+        for (int i = 0; i < n; ++i)
+            if (fixed[i] && h->in_block[i]) return ORC_BAD_FIXED;
+    objective o = {h, data, mask, (double *)malloc(sizeof(double) * n), (double *)malloc(sizeof(double) * n), 0,
+                   fixed};
     double *z = (double *)malloc(sizeof(double) * n), *g = (double *)malloc(sizeof(double) * n);
     double *zn = (double *)malloc(sizeof(double) * n), *gn = (double *)malloc(sizeof(double) * n);
     double *p = (double *)malloc(sizeof(double) * n), *H = (double *)malloc(sizeof(double) * n * n);
@@ -756,6 +767,14 @@ int orc_fit(const orc_handle *h, const double *data, uint32_t mask, const double
     free(o.theta); free(o.gt); free(z); free(g); free(zn); free(gn); free(p); free(H);
     free(s); free(y); free(Hy);
     return status;
+}
+
+int orc_fit(const orc_handle *h, const double *data, uint32_t mask, const double *theta_start,
+            double edm_tol, int max_iter, double *theta_out, double *nll_out, int *iters_out,
+            int *nevals_out, double *edm_out)
+{
+    return orc_fit_ex(h, data, mask, theta_start, NULL, edm_tol, max_iter, theta_out, nll_out, iters_out,
+                      nevals_out, edm_out);
 }
 
 /* Fits n_inst instances on n_threads host threads (OpenMP when compiled with it).

@@ -165,6 +165,7 @@ struct fit_model {
     void *arena = nullptr;
     size_t bytes = 0;
     int n_params = 0, n_data = 0, n_ds = 0, n_true = 0;
+    std::vector<uint8_t> in_block;   // parameter belongs to a covariance block (host copy)
 };
 
 // error / launch-count hooks for the other translation units of the library
@@ -557,6 +558,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
             if (contig) bfirst[b] = bidx[boff[b]];
         }
         A.put(&h.blk_first, bfirst);
+        M->in_block.assign(in_block.begin(), in_block.end());
         A.put(&h.blk_mat_off, moff);
         A.put(&h.blk_L, Lf);
         A.put(&h.blk_W, Wf);
@@ -1025,17 +1027,19 @@ int graph_launch(const void *kern, int grid, int threads, size_t smem, fitcore::
 // is the forward, adjoint and step launches over the active ones. The host reads the number
 // still active after every round (a 4-byte copy) to size the next launches and to stop.
 int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst,
-                       const float *data, const double *start, double *best, fit_result *results,
-                       const fit_batch_opts &o, cudaStream_t s, int64_t data_len, int64_t par_len) {
+                       const float *data, const double *start, const uint8_t *fixed, double *best,
+                       fit_result *results, const fit_batch_opts &o, cudaStream_t s, int64_t data_len,
+                       int64_t par_len) {
     LaunchCfg cfg;
     int rc = device_cfg(cfg);
     if (rc) return rc;
     std::lock_guard<std::mutex> lock(g_ws_mutex);
-    Staged di, dd, dst, dbe, dre;
+    Staged di, dd, dst, dfx, dbe, dre;
     bool hbe = false, hre = false;
     rc = stage_in(inst, sizeof(fit_instance) * n_inst, s, di);
     if (!rc) rc = stage_in(data, sizeof(float) * data_len, s, dd);
     if (!rc && start) rc = stage_in(start, sizeof(double) * par_len, s, dst);
+    if (!rc && fixed) rc = stage_in(fixed, (size_t)par_len, s, dfx);
     if (!rc) rc = stage_out(best, sizeof(double) * par_len, s, dbe, hbe);
     if (!rc) rc = stage_out(results, sizeof(fit_result) * n_inst, s, dre, hre);
     int *cnt_host = nullptr;
@@ -1053,6 +1057,7 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
         A.n = n;
         A.data = (const float *)dd.dev;
         A.start = start ? (const double *)dst.dev : nullptr;
+        A.fixed = fixed ? (const uint8_t *)dfx.dev : nullptr;
         A.best = (double *)dbe.dev;
         A.results = (fit_result *)dre.dev;
         A.vec_stride = ((int64_t)fitcore::fit_vec_floats(P, o.history) + 3) / 4 * 4;
@@ -1172,7 +1177,7 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
     }
     if (!rc && hre && cudaMemcpyAsync(results, dre.dev, sizeof(fit_result) * n_inst, cudaMemcpyDeviceToHost, s))
         rc = fail(FIT_ERR_CUDA, "fit_batch: copy back");
-    for (Staged *b : {&di, &dd, &dst, &dbe, &dre}) release(*b, s);
+    for (Staged *b : {&di, &dd, &dst, &dfx, &dbe, &dre}) release(*b, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = fail(FIT_ERR_CUDA, "fit_batch: synchronise");
     if (cnt_host) cudaFreeHost(cnt_host);
     return rc;
@@ -1201,6 +1206,12 @@ void fit_batch_default_opts(fit_batch_opts *o) {
 int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst, const float *data,
               const double *start, double *best, fit_result *results, const fit_batch_opts *opts_in,
               void *stream) {
+    return fit_batch_ex(models, n_models, inst, n_inst, data, start, nullptr, best, results, opts_in, stream);
+}
+
+int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst, const float *data,
+                 const double *start, const uint8_t *fixed, double *best, fit_result *results,
+                 const fit_batch_opts *opts_in, void *stream) {
     if (!models || n_models < 1 || !inst || n_inst < 0 || !data || !best || !results)
         return fail(FIT_ERR_INVALID_ARG, "fit_batch: bad argument");
     if (n_inst == 0) return FIT_OK;
@@ -1225,8 +1236,24 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
         data_len = std::max<int64_t>(data_len, q.data_off + models[q.model]->n_data);
         par_len = std::max<int64_t>(par_len, q.param_off + models[q.model]->n_params);
     }
-    if (o.engine == 1) return fit_batch_lockstep(models, n_models, inst, n_inst, data, start, best, results, o, s,
-                                                 data_len, par_len);
+    // held parameters: only outside the prior blocks (checked on a host copy)
+    std::vector<uint8_t> fixed_h;
+    if (fixed) {
+        fixed_h.resize(par_len);
+        if (cudaMemcpy(fixed_h.data(), fixed, par_len, cudaMemcpyDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FIT_ERR_INVALID_ARG, "fit_batch: fixed flags not readable");
+        }
+        for (int i = 0; i < n_inst; ++i) {
+            const fit_model *mm = models[inst[i].model];
+            for (int p = 0; p < mm->n_params; ++p)
+                if (fixed_h[inst[i].param_off + p] && mm->in_block[p])
+                    return fail(FIT_ERR_INVALID_ARG, "fit_batch: parameter " + std::to_string(p) +
+                                                         " of a prior block cannot be held fixed");
+        }
+    }
+    if (o.engine == 1) return fit_batch_lockstep(models, n_models, inst, n_inst, data, start, fixed, best, results,
+                                                 o, s, data_len, par_len);
     if (o.engine != 0) return fail(FIT_ERR_INVALID_ARG, "fit_batch: engine must be 0 or 1");
     int max_loc = 0;   // working vectors + evaluation workspace, without the history
     for (int mi = 0; mi < n_models; ++mi) {
@@ -1293,7 +1320,7 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
     if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, o.blocks_per_sm);
     const int grid = std::max(1, std::min(n_inst, per_sm * cfg.sms));
 
-    Staged dm, di, dd, dst, dbe, dre, dws, dq;
+    Staged dm, di, dd, dst, dfx, dbe, dre, dws, dq;
     bool hbe = false, hre = false;
     std::vector<DevModel> hm(n_models);
     for (int i = 0; i < n_models; ++i) hm[i] = models[i]->host;
@@ -1301,6 +1328,7 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
     if (!rc) rc = stage_in(inst, sizeof(fit_instance) * n_inst, s, di);
     if (!rc) rc = stage_in(data, sizeof(float) * data_len, s, dd);
     if (!rc && start) rc = stage_in(start, sizeof(double) * par_len, s, dst);
+    if (!rc && fixed) rc = stage_in(fixed, (size_t)par_len, s, dfx);
     if (!rc) rc = stage_out(best, sizeof(double) * par_len, s, dbe, hbe);
     if (!rc) rc = stage_out(results, sizeof(fit_result) * n_inst, s, dre, hre);
     if (!rc && !in_smem) {
@@ -1326,6 +1354,7 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
         a.f_noise_rel = o.f_noise_rel;
         a.data = (const float *)dd.dev;
         a.start = start ? (const double *)dst.dev : nullptr;
+        a.fixed = fixed ? (const uint8_t *)dfx.dev : nullptr;
         a.best = (double *)dbe.dev;
         a.results = (fit_result *)dre.dev;
         a.queue = (int *)dq.dev;
@@ -1368,7 +1397,7 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
     }
     if (!rc && hre && cudaMemcpyAsync(results, dre.dev, sizeof(fit_result) * n_inst, cudaMemcpyDeviceToHost, s))
         rc = fail(FIT_ERR_CUDA, "fit_batch: copy back");
-    for (Staged *b : {&dm, &di, &dd, &dst, &dbe, &dre, &dws, &dq}) release(*b, s);
+    for (Staged *b : {&dm, &di, &dd, &dst, &dfx, &dbe, &dre, &dws, &dq}) release(*b, s);
     // the staged model table and instance table are host vectors: finish before they go away
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_batch: synchronise");
     return rc;
@@ -1430,6 +1459,130 @@ int fit_batch_autotune(fit_model *const *models, int n_models, const fit_instanc
     opts->threads = best_o.threads;
     opts->blocks_per_sm = best_o.blocks_per_sm;
     return FIT_OK;
+}
+
+
+int fit_profile_scan(fit_model *model, const float *data, uint32_t mask, int n_scan, const int *scan_idx,
+                     int n_points, const double *points, const double *start, const fit_batch_opts *opts,
+                     double *nll_min, double *theta_best, double *dchi2, double *theta_points, int *status,
+                     void *stream) {
+    if (!model || !data || n_scan < 1 || n_scan > 8 || !scan_idx || n_points < 1 || !points || !nll_min ||
+        !dchi2)
+        return fail(FIT_ERR_INVALID_ARG, "fit_profile_scan: bad argument");
+    const int P = model->n_params;
+    for (int q = 0; q < n_scan; ++q)
+        if (scan_idx[q] < 0 || scan_idx[q] >= P || model->in_block[scan_idx[q]])
+            return fail(FIT_ERR_INVALID_ARG, "fit_profile_scan: scan parameters must lie outside the prior blocks");
+    const int n = n_points + 1;   // instance 0: the unconstrained fit
+    std::vector<double> st((size_t)n * P), best((size_t)n * P);
+    std::vector<uint8_t> fx((size_t)n * P, 0);
+    std::vector<double> st0(P);
+    if (start) {
+        if (cudaMemcpy(st0.data(), start, sizeof(double) * P, cudaMemcpyDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FIT_ERR_INVALID_ARG, "fit_profile_scan: start not readable");
+        }
+    } else {
+        if (cudaMemcpy(st0.data(), model->host.theta0, sizeof(double) * P, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(FIT_ERR_CUDA, "fit_profile_scan: theta0");
+    }
+    std::vector<fit_instance> inst(n);
+    for (int k = 0; k < n; ++k) {
+        inst[k].model = 0;
+        inst[k].mask = mask;
+        inst[k].data_off = 0;   // every point fits the same data vector
+        inst[k].param_off = (int64_t)k * P;
+        std::copy(st0.begin(), st0.end(), st.begin() + (size_t)k * P);
+        if (k > 0)
+            for (int q = 0; q < n_scan; ++q) {
+                st[(size_t)k * P + scan_idx[q]] = points[(size_t)(k - 1) * n_scan + q];
+                fx[(size_t)k * P + scan_idx[q]] = 1;
+            }
+    }
+    std::vector<fit_result> res(n);
+    fit_model *ms[1] = {model};
+    int rc = fit_batch_ex(ms, 1, inst.data(), n, data, st.data(), fx.data(), best.data(), res.data(), opts,
+                          stream);
+    if (rc) return rc;
+    // the profile's minimum: the unconstrained fit, unless a raster point went lower
+    int kmin = 0;
+    for (int k = 1; k < n; ++k)
+        if (res[k].nll_min < res[kmin].nll_min) kmin = k;
+    *nll_min = res[kmin].nll_min;
+    if (theta_best) std::copy(best.begin() + (size_t)kmin * P, best.begin() + (size_t)(kmin + 1) * P, theta_best);
+    for (int k = 1; k < n; ++k) {
+        dchi2[k - 1] = res[k].nll_min - res[kmin].nll_min;
+        if (status) status[k - 1] = res[k].status;
+        if (theta_points)
+            std::copy(best.begin() + (size_t)k * P, best.begin() + (size_t)(k + 1) * P,
+                      theta_points + (size_t)(k - 1) * P);
+    }
+    return FIT_OK;
+}
+
+int fit_wilks_interval(int n, const double *x, const double *dchi2, double level, double *lo, double *hi) {
+    if (n < 2 || !x || !dchi2 || !lo || !hi || !(level > 0.0))
+        return fail(FIT_ERR_INVALID_ARG, "fit_wilks_interval: bad argument");
+    for (int i = 1; i < n; ++i)
+        if (!(x[i] > x[i - 1])) return fail(FIT_ERR_INVALID_ARG, "fit_wilks_interval: x must increase");
+    int im = 0;
+    for (int i = 1; i < n; ++i)
+        if (dchi2[i] < dchi2[im]) im = i;
+    int open = 0;
+    // crossing of `level` on each side of the minimum, linear between the raster points
+    int i = im;
+    while (i > 0 && dchi2[i - 1] < level) --i;
+    if (i == 0) {
+        *lo = x[0];
+        open |= 1;
+    } else {
+        const double t = (level - dchi2[i]) / (dchi2[i - 1] - dchi2[i]);
+        *lo = x[i] + t * (x[i - 1] - x[i]);
+    }
+    i = im;
+    while (i < n - 1 && dchi2[i + 1] < level) ++i;
+    if (i == n - 1) {
+        *hi = x[n - 1];
+        open |= 2;
+    } else {
+        const double t = (level - dchi2[i]) / (dchi2[i + 1] - dchi2[i]);
+        *hi = x[i] + t * (x[i + 1] - x[i]);
+    }
+    return open;
+}
+
+double fit_chi2_sf(double chi2, int dof) {
+    // Q(a, x) = Gamma(a, x) / Gamma(a) with a = dof / 2, x = chi2 / 2: the series of the lower
+    // function P(a, x) = x^a e^-x / Gamma(a) sum_n x^n / (a (a+1) ... (a+n)) below x = a + 1, the
+    // continued fraction of the upper one (evaluated by the modified Lentz method) above.
+    if (dof < 1 || !(chi2 >= 0.0)) return NAN;
+    const double a = 0.5 * dof, x = 0.5 * chi2;
+    if (x == 0.0) return 1.0;
+    const double lpre = a * std::log(x) - x - std::lgamma(a);
+    if (x < a + 1.0) {
+        double term = 1.0 / a, sum = term;
+        for (int k = 1; k < 100000; ++k) {
+            term *= x / (a + k);
+            sum += term;
+            if (std::fabs(term) < 1e-17 * std::fabs(sum)) break;
+        }
+        return 1.0 - std::exp(lpre) * sum;
+    }
+    const double tiny = 1e-300;
+    double b = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / b, f = d;
+    for (int k = 1; k < 100000; ++k) {
+        const double an = -k * (k - a);
+        b += 2.0;
+        d = an * d + b;
+        if (std::fabs(d) < tiny) d = tiny;
+        c = b + an / c;
+        if (std::fabs(c) < tiny) c = tiny;
+        d = 1.0 / d;
+        const double del = d * c;
+        f *= del;
+        if (std::fabs(del - 1.0) < 1e-16) break;
+    }
+    return std::exp(lpre) * f;
 }
 
 }  // extern "C"

@@ -564,32 +564,41 @@ static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, 
     (void)warp;
     (void)nw;
     // ---- stage C: fold into reco bins (banded rows, warp per row) ------------------------
-    // Each warp takes two rows at a time and two strides of each, so four independent
+    // Each warp takes four rows at a time and two strides of each, so eight independent
     // load/FMA chains per lane are in flight.
-    for (int j0 = warp; j0 < nr; j0 += 2 * nw) {
-        const int j1 = j0 + nw;
-        const bool two = j1 < nr;
-        const int lo0 = dt.row_lo[j0], len0 = dt.row_len[j0];
-        const int lo1 = two ? dt.row_lo[j1] : 0, len1 = two ? dt.row_len[j1] : 0;
-        const float *r0 = dt.rrow + dt.row_off[j0];
-        const float *r1 = dt.rrow + (two ? dt.row_off[j1] : 0);
-        float s0 = 0.f, s1 = 0.f, t0 = 0.f, t1 = 0.f;
-        const int len = max(len0, len1);
-        for (int b = lane; b < len; b += 64) {
-            if (b < len0) s0 = fmaf(r0[b], ws.v[lo0 + b], s0);
-            if (b + 32 < len0) s1 = fmaf(r0[b + 32], ws.v[lo0 + b + 32], s1);
-            if (b < len1) t0 = fmaf(r1[b], ws.v[lo1 + b], t0);
-            if (b + 32 < len1) t1 = fmaf(r1[b + 32], ws.v[lo1 + b + 32], t1);
+    for (int j0 = warp; j0 < nr; j0 += 4 * nw) {
+        int lo[4], len[4];
+        const float *rr[4];
+        int lmax = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * nw;
+            const bool on = j < nr;
+            lo[u] = on ? dt.row_lo[j] : 0;
+            len[u] = on ? dt.row_len[j] : 0;
+            rr[u] = dt.rrow + (on ? dt.row_off[j] : 0);
+            lmax = max(lmax, len[u]);
         }
-        float s = s0 + s1, t = t0 + t1;
+        float s[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        for (int b = lane; b < lmax; b += 64) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (b < len[u]) s[u][0] = fmaf(rr[u][b], ws.v[lo[u] + b], s[u][0]);
+                if (b + 32 < len[u]) s[u][1] = fmaf(rr[u][b + 32], ws.v[lo[u] + b + 32], s[u][1]);
+            }
+        }
+        float t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = s[u][0] + s[u][1];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            t += __shfl_xor_sync(0xffffffffu, t, o);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t[u] += __shfl_xor_sync(0xffffffffu, t[u], o);
         }
         if (lane == 0) {
-            ws.f0[j0] = s;
-            if (two) ws.f0[j1] = t;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j0 + u * nw < nr) ws.f0[j0 + u * nw] = t[u];
         }
     }
     __syncthreads();
@@ -675,16 +684,15 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
     for (int k = tid; k < N_t; k += nth) {
         const int lo = dt.col_lo[k], cw = dt.col_w, jmax = nr - 1;
         const float *rc = dt.rcol + k;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        float s[4] = {0.f, 0.f, 0.f, 0.f};
         int b = 0;
-        for (; b + 3 < cw; b += 4) {
-            s0 = fmaf(rc[(int64_t)b * N_t], ws.gmu[min(lo + b, jmax)], s0);
-            s1 = fmaf(rc[(int64_t)(b + 1) * N_t], ws.gmu[min(lo + b + 1, jmax)], s1);
-            s2 = fmaf(rc[(int64_t)(b + 2) * N_t], ws.gmu[min(lo + b + 2, jmax)], s2);
-            s3 = fmaf(rc[(int64_t)(b + 3) * N_t], ws.gmu[min(lo + b + 3, jmax)], s3);
+        for (; b + 7 < cw; b += 8) {   // eight loads in flight
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                s[q & 3] = fmaf(rc[(int64_t)(b + q) * N_t], ws.gmu[min(lo + b + q, jmax)], s[q & 3]);
         }
-        for (; b < cw; ++b) s0 = fmaf(rc[(int64_t)b * N_t], ws.gmu[min(lo + b, jmax)], s0);
-        gv[k] = pmul(c.eff, (s0 + s1) + (s2 + s3));
+        for (; b < cw; ++b) s[0] = fmaf(rc[(int64_t)b * N_t], ws.gmu[min(lo + b, jmax)], s[0]);
+        gv[k] = pmul(c.eff, (s[0] + s[1]) + (s[2] + s[3]));
     }
     __syncthreads();
 

@@ -455,9 +455,18 @@ __device__ double eval_z_prior(const DevModel &m, const float *z, const float *g
     return tot[0];
 }
 
+// Parameters held at their start values (a profile-likelihood point): a zero z-gradient keeps
+// every L-BFGS direction, and so the parameter, where it is. Only parameters outside the prior
+// blocks can be held (their z coordinate is the parameter itself, scaled).
+__device__ __forceinline__ void hold_fixed(const uint8_t *fixed, float *gz, int P) {
+    if (fixed == nullptr) return;
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        if (fixed[i]) gz[i] = 0.f;
+}
+
 // -2lnL(theta(z)) and its z-gradient gz. Returns +inf on an invalid point.
 __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &V, EvalWs ws,
-                         const float *data, uint32_t mask, FitSmem &S) {
+                         const float *data, uint32_t mask, FitSmem &S, const uint8_t *fixed) {
     theta_of_z(m, z, V.pv, V.pd);
     for (int i = threadIdx.x; i < m.P; i += blockDim.x) V.gth[i] = 0.f;
     if (threadIdx.x == 0) S.status = 0;
@@ -469,7 +478,9 @@ __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &
         __syncthreads();
         if (S.status) return INFINITY;
     }
-    return nll + eval_z_prior(m, z, V.gth, gz, S.red);
+    const double prior = eval_z_prior(m, z, V.gth, gz, S.red);
+    hold_fixed(fixed, gz, m.P);
+    return nll + prior;
 }
 
 // cubic minimiser through (a, fa, ga), (b, fb, gb), or the secant of the slopes when the
@@ -860,7 +871,8 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
         } else {
             start_z(m, A.start ? A.start + in.param_off : nullptr, V.zt, V.pd);
             while (true) {
-                const double fa = eval_z(m, V.zt, V.gt, V, ws, data, in.mask, S);
+                const double fa = eval_z(m, V.zt, V.gt, V, ws, data, in.mask, S,
+                                         A.fixed ? A.fixed + in.param_off : nullptr);
                 if (!fit_decide(S, V, P, fa, F)) break;
             }
         }
@@ -1057,10 +1069,12 @@ __global__ void __launch_bounds__(128) ls_step_kernel(LsArgs A) {
         for (int d = 0; d < nd; ++d)
             if ((in.mask >> d) & 1u) fa += A.nll_ds[(int64_t)g * nd + d];
         __syncthreads();
-        if (st != 0)
+        if (st != 0) {
             fa = INFINITY;
-        else
+        } else {
             fa += eval_z_prior(m, V.zt, V.gth, V.gt, S.red);
+            hold_fixed(A.fixed ? A.fixed + in.param_off : nullptr, V.gt, P);
+        }
         const bool more = fit_decide(S, V, P, fa, F);
         if (more) {
             theta_of_z(m, V.zt, V.pv, V.pd);

@@ -23,6 +23,7 @@ struct FitArgs {
     int64_t ws_stride;           // floats per block slice
     int smem_floats;             // dynamic shared floats available for the workspace
     int hist_global;             // 1: the L-BFGS history lives in the global slice
+    const uint8_t *fixed;        // device, indexed like start/best, or nullptr: held parameters
     uint64_t budget_ns;
 };
 
@@ -41,6 +42,7 @@ struct LsArgs {
     int n;
     const float *data;
     const double *start;         // device or nullptr
+    const uint8_t *fixed;        // device, indexed like start, or nullptr
     double *best;
     fit_result *results;
     FitState *state;             // [n]

@@ -95,7 +95,8 @@ EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model
            "fit_model_expected_tc", "fit_poisson_sample", "fit_mlp_create", "fit_mlp_destroy",
            "fit_mlp_forward", "fit_mlp_train_step", "fit_mlp_get_layer", "fit_mlp_set_layer",
            "fit_warmstart_features", "fit_warmstart_predict", "fit_warmstart_draw",
-           "fit_warmstart_train", "fit_batch_autotune")
+           "fit_warmstart_train", "fit_batch_autotune", "fit_batch_ex", "fit_profile_scan",
+           "fit_wilks_interval", "fit_chi2_sf")
 
 
 def lib_path() -> str:
@@ -150,6 +151,17 @@ def load(build_if_missing: bool = False):
     L.fit_batch_autotune.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_int, vp, vp, C.c_int,
                                      C.POINTER(fit_batch_opts), vp]
     L.fit_batch_autotune.restype = C.c_int
+    L.fit_batch_ex.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_int, vp, vp, vp, vp, vp,
+                               C.POINTER(fit_batch_opts), vp]
+    L.fit_batch_ex.restype = C.c_int
+    L.fit_profile_scan.argtypes = [vp, vp, C.c_uint32, C.c_int, vp, C.c_int, vp, vp,
+                                   C.POINTER(fit_batch_opts), vp, vp, vp, vp, vp, vp]
+    L.fit_profile_scan.restype = C.c_int
+    L.fit_wilks_interval.argtypes = [C.c_int, vp, vp, C.c_double, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]
+    L.fit_wilks_interval.restype = C.c_int
+    L.fit_chi2_sf.argtypes = [C.c_double, C.c_int]
+    L.fit_chi2_sf.restype = C.c_double
     L.fit_last_error.restype = C.c_char_p
     L.fit_kernel_launches.restype = C.c_int64
     for f in ("fit_model_create", "fit_model_info", "fit_model_expected", "fit_model_eval",
@@ -300,16 +312,66 @@ def fit_batch_default_opts() -> fit_batch_opts:
     return o
 
 
-def fit_batch(models, inst, data, start, best, results, opts=None, stream=None):
+def fit_batch(models, inst, data, start, best, results, opts=None, stream=None, fixed=None):
     """inst: numpy structured array of INSTANCE_DTYPE; results: RESULT_DTYPE array or a
-    uint8 device tensor of n_inst * 32 bytes."""
+    uint8 device tensor of n_inst * 32 bytes; fixed: optional uint8 flags indexed like start
+    (held parameters, fit_batch_ex)."""
     L = load()
     hs = (C.c_void_p * len(models))(*[m.handle.value for m in models])
     inst = np.ascontiguousarray(inst, dtype=INSTANCE_DTYPE)
     o = opts if opts is not None else fit_batch_default_opts()
-    _check(L.fit_batch(hs, len(models), inst.ctypes.data, len(inst), _ptr(data), _ptr(start),
-                       _ptr(best), _ptr(results), C.byref(o), _stream_ptr(stream)),
-           "fit_batch")
+    if fixed is None:
+        _check(L.fit_batch(hs, len(models), inst.ctypes.data, len(inst), _ptr(data), _ptr(start),
+                           _ptr(best), _ptr(results), C.byref(o), _stream_ptr(stream)),
+               "fit_batch")
+    else:
+        if not hasattr(fixed, "data_ptr"):
+            fixed = np.ascontiguousarray(fixed, dtype=np.uint8)
+        _check(L.fit_batch_ex(hs, len(models), inst.ctypes.data, len(inst), _ptr(data),
+                              _ptr(start), _ptr(fixed), _ptr(best), _ptr(results), C.byref(o),
+                              _stream_ptr(stream)),
+               "fit_batch_ex")
+
+
+def fit_profile_scan(model: Model, data, mask, scan_idx, points, start=None, opts=None,
+                     stream=None):
+    """Profile likelihood on a raster; returns dict(nll_min, theta_best, dchi2, theta, status)."""
+    idx = np.ascontiguousarray(scan_idx, dtype=np.int32)
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, len(idx)))
+    n = len(pts)
+    P = model.n_params
+    nll = C.c_double()
+    tb = np.zeros(P)
+    dchi2 = np.zeros(n)
+    th = np.zeros((n, P))
+    st = np.zeros(n, np.int32)
+    if data is not None and not hasattr(data, "data_ptr"):
+        data = np.ascontiguousarray(data, dtype=np.float32)
+    if start is not None and not hasattr(start, "data_ptr"):
+        start = np.ascontiguousarray(start, dtype=np.float64)
+    o = opts if opts is not None else fit_batch_default_opts()
+    _check(load().fit_profile_scan(model.handle, _ptr(data), C.c_uint32(int(mask)), len(idx),
+                                   _ptr(idx), n, _ptr(pts), _ptr(start), C.byref(o),
+                                   C.byref(nll), _ptr(tb), _ptr(dchi2), _ptr(th), _ptr(st),
+                                   _stream_ptr(stream)),
+           "fit_profile_scan")
+    return dict(nll_min=nll.value, theta_best=tb, dchi2=dchi2, theta=th, status=st)
+
+
+def fit_wilks_interval(x, dchi2, level=1.0):
+    """(lo, hi, open_flags) where the 1-D profile dchi2(x) crosses `level`."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    d = np.ascontiguousarray(dchi2, dtype=np.float64)
+    lo, hi = C.c_double(), C.c_double()
+    rc = load().fit_wilks_interval(len(x), _ptr(x), _ptr(d), float(level), C.byref(lo),
+                                   C.byref(hi))
+    if rc < 0:
+        _check(rc, "fit_wilks_interval")
+    return lo.value, hi.value, rc
+
+
+def fit_chi2_sf(chi2, dof):
+    return float(load().fit_chi2_sf(float(chi2), int(dof)))
 
 
 def fit_batch_autotune(models, inst, data, start=None, n_sample=0, opts=None, stream=None):
@@ -481,7 +543,7 @@ def expected_numpy(model: Model, theta):
     return mu, st
 
 
-def fit_numpy(models, inst, data, start=None, opts=None):
+def fit_numpy(models, inst, data, start=None, opts=None, fixed=None):
     """Runs fit_batch on host arrays; returns (best [flat float64], results RESULT_DTYPE)."""
     inst = np.ascontiguousarray(inst, dtype=INSTANCE_DTYPE)
     npar = max(int(r["param_off"]) + models[int(r["model"])].n_params for r in inst)
@@ -490,7 +552,7 @@ def fit_numpy(models, inst, data, start=None, opts=None):
     data = np.ascontiguousarray(data, dtype=np.float32)
     if start is not None:
         start = np.ascontiguousarray(start, dtype=np.float64)
-    fit_batch(models, inst, data, start, best, res, opts)
+    fit_batch(models, inst, data, start, best, res, opts, fixed=fixed)
     return best, res
 
 

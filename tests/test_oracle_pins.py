@@ -416,3 +416,39 @@ def test_grid_scan_matches_fit_minimum():
         wa, wb = wa / 3, wb / 3
     assert r["nll"] == pytest.approx(best, abs=1e-6)
     assert r["nll"] <= best + 1e-9
+
+
+def test_fixed_parameter_fit_is_the_profile_minimum():
+    """Profile likelihood (Eq. 7): with sin^2 2th13 held at a, the fit over dm2_ee returns the
+    minimum of -2lnL(a, .) found by a brute-force 1-D scan with zoomed refinement; the profile
+    is >= the global minimum and touches it at the unconstrained best fit."""
+    spec = synth.make_model("c0_tiny")
+    om = oracle.OracleModel(spec)
+    data = synth.poisson_data(om.expected(np.array([0.085, 2.45e-3])), 15)
+    glob = om.fit(data)
+    assert glob["status"] == 0
+    fixed = np.array([True, False])
+    for a in (0.04, 0.085, 0.13, glob["theta"][0]):
+        r = om.fit(data, start=[a, 2.5e-3], fixed=fixed)
+        assert r["status"] == 0 and r["theta"][0] == pytest.approx(a, rel=1e-14)
+        dm = np.linspace(1.5e-3, 3.5e-3, 2001)
+        v = np.array([om.nll([a, b], data) for b in dm])
+        c, w, best = dm[np.argmin(v)], 3 * (dm[1] - dm[0]), v.min()
+        for _ in range(14):
+            bb = np.linspace(c - w, c + w, 21)
+            v2 = np.array([om.nll([a, b], data) for b in bb])
+            c, best, w = bb[np.argmin(v2)], min(best, v2.min()), w / 3
+        assert r["nll"] == pytest.approx(best, abs=1e-6)
+        assert r["nll"] >= glob["nll"] - 1e-9
+    r = om.fit(data, start=glob["theta"], fixed=fixed)
+    assert r["nll"] == pytest.approx(glob["nll"], abs=1e-8)
+
+
+def test_fixing_a_parameter_inside_a_prior_block_is_rejected():
+    spec = synth.make_model("c0")
+    om = oracle.OracleModel(spec)
+    idx = spec.cov_blocks[0][0][0]
+    fixed = np.zeros(spec.n_params, bool)
+    fixed[idx] = True
+    r = om.fit(om.expected(spec.theta0), fixed=fixed)
+    assert r["status"] == 4
