@@ -74,8 +74,10 @@ def flops_per_eval(spec, mask) -> float:
     return f
 
 
-def flops_lbfgs_iter(P, m=10) -> float:
-    return 4.0 * m * P + 12.0 * P
+def flops_lbfgs_iter(P, m) -> float:
+    """One L-BFGS iteration with m pairs: 4m + 1 dot products (2P each), the direction
+    combination over 2m + 1 vectors (2P each) and ~10P of vector updates."""
+    return (4.0 * m + 1) * 2.0 * P + (2.0 * m + 1) * 2.0 * P + 10.0 * P
 
 
 # ---------------------------------------------------------------------------------------
@@ -444,7 +446,7 @@ def run_ours(args):
 
     # roofline of the fit kernel: FP32 ALU peak from unit counts and the maximum SM clock
     f_eval = flops_per_eval(spec, spec.all_mask())
-    alg_flops = evals * f_eval + iters * flops_lbfgs_iter(P)
+    alg_flops = evals * f_eval + iters * flops_lbfgs_iter(P, opts.history)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     sm_max = 2070.0
