@@ -368,6 +368,26 @@ int fit_wilks_interval(int n, const double *x, const double *dchi2, double level
  * freedom. NaN for dof < 1 or chi2 < 0. */
 double fit_chi2_sf(double chi2, int dof);
 
+/* Event-level reweighting ([S], "GPU accelerated computation": the oscillation weights of the
+ * simulated events are the step the paper moves to the GPU). A set of simulated signal events
+ * of one detector stays on the device: true energy (MeV, > 0), emitting core (< n_cores, with
+ * baseline core_L[c] in m), weight (expected events it represents), reco bin (0..n_bins-1,
+ * non-decreasing: the events sorted by bin). Arrays host or device, copied. */
+typedef struct fit_mc fit_mc;
+int fit_mc_create(int osc_mode, int n_cores, const double *core_L, int64_t n_events,
+                  const float *energy, const uint8_t *core, const float *weight, const int *bin,
+                  int n_bins, fit_mc **out);
+void fit_mc_destroy(fit_mc *mc);
+/* out[b][j] = sum over the events e of bin j of weight_e P(L_core(e), E_e; params[b]) for
+ * b < B <= 64 parameter sets (params [B x 4] in the osc_mode's order, host or device; out
+ * [B x n_bins] double, host or device). One pass over the events serves all B sets. With
+ * device buffers the call is asynchronous on stream; with host buffers it returns when out is
+ * written. */
+int fit_mc_spectrum(fit_mc *mc, int B, const double *params, double *out, void *stream);
+/* Synchronises the device and returns FIT_ERR_CUDA if any fit_mc_spectrum call on mc gave up
+ * waiting for its staged event copies (bounded waits of 2 s; its spectra are then incomplete). */
+int fit_mc_status(fit_mc *mc);
+
 /* Chooses threads per block and resident blocks per SM for fit_batch on the current device by
  * timing the candidate configurations (96 or 128 threads, 4 or 5 blocks per SM) on the first
  * n_sample instances (0 = ten per SM, at most n_inst), and writes the fastest into

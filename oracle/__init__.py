@@ -15,6 +15,8 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
   fit (BFGS)                          - pinned (Asimov recovery, pure-scale closed form,
       prior-only closed form, brute-force grid scan on a 2-parameter model)
   sigma (FD Hessian)                  - pinned (prior-only model: 2 H^-1 = V exactly)
+  event_spectrum (event reweighting)  - pinned (zero mixing = weighted bin counts; per-event
+      sum of the pinned survival function on a small sample)
   philox4x32_10 (rng.c)               - pinned (published known-answer vectors)
   poisson_sample (rng.c)              - pinned (chi-square against the exact Poisson PMF,
       mean and variance, counter/offset invariance)
@@ -127,6 +129,9 @@ def _declare(L):
     L.orc_ptrs_step_many.argtypes = [C.c_float, C.c_int64, C.POINTER(C.c_float),
                                      C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.orc_ptrs_step_many.restype = None
+    L.orc_event_spectrum.argtypes = [C.c_int, _DP, _DP, C.c_longlong, C.POINTER(C.c_float),
+                                     C.POINTER(C.c_ubyte), C.POINTER(C.c_float), _IP, C.c_int, _DP]
+    L.orc_event_spectrum.restype = None
 
 
 def _d(a):
@@ -382,3 +387,21 @@ def ptrs_step(mu: float, U, V):
     lib().orc_ptrs_step_many(float(mu), len(U), U.ctypes.data_as(F), V.ctypes.data_as(F),
                              k.ctypes.data_as(F))
     return k
+
+
+def event_spectrum(events, params):
+    """Oscillated spectrum of Monte Carlo events (synth.McEvents) at the survival parameters
+    params[4], summed per reco bin in FP64."""
+    e = np.ascontiguousarray(events.energy, dtype=np.float32)
+    c = np.ascontiguousarray(events.core, dtype=np.uint8)
+    w = np.ascontiguousarray(events.weight, dtype=np.float32)
+    b = np.ascontiguousarray(events.bin, dtype=np.int32)
+    pa, pp = _d(params)
+    la, lp = _d(events.core_L)
+    out = np.zeros(events.n_bins)
+    lib().orc_event_spectrum(int(events.osc_mode), pp, lp, len(e),
+                             e.ctypes.data_as(C.POINTER(C.c_float)),
+                             c.ctypes.data_as(C.POINTER(C.c_ubyte)),
+                             w.ctypes.data_as(C.POINTER(C.c_float)), b.ctypes.data_as(_IP),
+                             int(events.n_bins), out.ctypes.data_as(_DP))
+    return out

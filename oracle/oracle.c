@@ -795,6 +795,21 @@ void orc_fit_many(orc_handle *const *hs, int n_inst, const int *model_of, const 
     (void)n_threads;
 }
 
+/* Event-level reweighting ([S], "GPU accelerated computation"): the oscillated spectrum of
+ * simulated events, out[b] = sum over the events in reco bin b of weight_e P(L_core(e), E_e)
+ * with the survival formula `mode` at the parameters p[4]. Events in any order; bins outside
+ * [0, n_bins) are skipped. */
+void orc_event_spectrum(int mode, const double *p, const double *core_L, long long n_events, const float *energy,
+                        const unsigned char *core, const float *weight, const int *bin, int n_bins, double *out)
+{
+    for (int b = 0; b < n_bins; ++b) out[b] = 0.0;
+    for (long long e = 0; e < n_events; ++e) {
+        int b = bin[e];
+        if (b < 0 || b >= n_bins) continue;
+        out[b] += (double)weight[e] * orc_survival(mode, p, core_L[core[e]], (double)energy[e], NULL);
+    }
+}
+
 int orc_openmp_enabled(void)
 {
 #ifdef _OPENMP

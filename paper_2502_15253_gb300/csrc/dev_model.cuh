@@ -221,11 +221,11 @@ __device__ __forceinline__ F2 f2_sqrt(F2 a) {
 //  mode FIT_OSC_EQ1:     eta = (sin^2 2th13, dm2_ee, sin^2 2th12, dm2_21), Eq. 1
 //  mode FIT_OSC_VACUUM3: eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31), exact vacuum P
 // eta_lo carries the low parts of the two mass splittings; dx = pi c (dx/d dm2).
-__device__ __forceinline__ float survival(const DevModel &m, const float (&eta)[4],
-                                          const float (&eta_lo)[4], const OscCoef &k,
-                                          float c_hi, float c_lo, float (&dP)[4]) {
+__device__ __forceinline__ float survival_mode(int mode, const float (&eta)[4],
+                                               const float (&eta_lo)[4], const OscCoef &k,
+                                               float c_hi, float c_lo, float (&dP)[4]) {
     const float dx = 3.14159265358979f * c_hi;
-    if (m.osc_mode == FIT_OSC_EQ1) {
+    if (mode == FIT_OSC_EQ1) {
         const float S13 = eta[0], S12 = eta[2];
         const float root = sqrtf(fmaxf(1.f - S13, 1e-12f));
         const float c2 = 0.5f * (1.f + root);
@@ -260,6 +260,38 @@ __device__ __forceinline__ float survival(const DevModel &m, const float (&eta)[
         dP[3] = -S13 * (c12 * d31 + s12 * d32);
         return P;
     }
+}
+
+// The sin^2 coefficients of survival_mode from float pairs e of the exact parameter values.
+__device__ __forceinline__ OscCoef osc_coef(int mode, const F2 (&e)[4]) {
+    F2 cf[3];
+    if (mode == FIT_OSC_EQ1) {
+        // cos^4 th13 = ((1 + sqrt(1 - sin^2 2th13)) / 2)^2
+        const F2 c2 = f2_scale(f2_add(F2{1.f, 0.f}, f2_sqrt(f2_one_minus(e[0]))), 0.5f);
+        cf[0] = e[0];
+        cf[1] = f2_mul(f2_mul(c2, c2), e[2]);
+        cf[2] = F2{0.f, 0.f};
+    } else {
+        const F2 S12 = f2_scale(f2_mul(e[0], f2_one_minus(e[0])), 4.f);
+        const F2 S13 = f2_scale(f2_mul(e[1], f2_one_minus(e[1])), 4.f);
+        const F2 c13 = f2_one_minus(e[1]);
+        cf[0] = f2_mul(f2_mul(c13, c13), S12);
+        cf[1] = f2_mul(S13, f2_one_minus(e[0]));
+        cf[2] = f2_mul(S13, e[0]);
+    }
+    OscCoef k;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        k.hi[i] = cf[i].h;
+        k.lo[i] = cf[i].l;
+    }
+    return k;
+}
+
+__device__ __forceinline__ float survival(const DevModel &m, const float (&eta)[4],
+                                          const float (&eta_lo)[4], const OscCoef &k,
+                                          float c_hi, float c_lo, float (&dP)[4]) {
+    return survival_mode(m.osc_mode, eta, eta_lo, k, c_hi, c_lo, dP);
 }
 
 // Poisson deviance 2[mu - n + n ln(n/mu)] = 2 mu h(r), r = (n - mu)/mu,
@@ -413,26 +445,7 @@ static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const
             e[i] = F2{m.osc_val[i], m.osc_val_lo[i]};
         }
     }
-    F2 cf[3];
-    if (m.osc_mode == FIT_OSC_EQ1) {
-        // cos^4 th13 = ((1 + sqrt(1 - sin^2 2th13)) / 2)^2
-        const F2 c2 = f2_scale(f2_add(F2{1.f, 0.f}, f2_sqrt(f2_one_minus(e[0]))), 0.5f);
-        cf[0] = e[0];
-        cf[1] = f2_mul(f2_mul(c2, c2), e[2]);
-        cf[2] = F2{0.f, 0.f};
-    } else {
-        const F2 S12 = f2_scale(f2_mul(e[0], f2_one_minus(e[0])), 4.f);
-        const F2 S13 = f2_scale(f2_mul(e[1], f2_one_minus(e[1])), 4.f);
-        const F2 c13 = f2_one_minus(e[1]);
-        cf[0] = f2_mul(f2_mul(c13, c13), S12);
-        cf[1] = f2_mul(S13, f2_one_minus(e[0]));
-        cf[2] = f2_mul(S13, e[0]);
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        c.kc.hi[i] = cf[i].h;
-        c.kc.lo[i] = cf[i].l;
-    }
+    c.kc = osc_coef(m.osc_mode, e);
     c.nrm = ppair(m, pv, pd, ds.norm_idx, 1.f);
     c.eff = ppair(m, pv, pd, ds.eff_idx, 1.f);
     c.em = make_emap(m, ds, pv, pd);

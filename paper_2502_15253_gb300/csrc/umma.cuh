@@ -60,6 +60,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
 }
 
 // ---- TMA ------------------------------------------------------------------------------
+// 1-D bulk copy of `bytes` from global to shared memory (no tensor map); both addresses
+// 16-byte aligned and bytes a multiple of 16; completes the transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // 2-D tiled load of box (x = inner coordinate, y = outer) into shared memory; completes the
 // transaction bytes on `bar`. x must be a multiple of 16 bytes' worth of elements.
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {

@@ -96,7 +96,8 @@ EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model
            "fit_mlp_forward", "fit_mlp_train_step", "fit_mlp_get_layer", "fit_mlp_set_layer",
            "fit_warmstart_features", "fit_warmstart_predict", "fit_warmstart_draw",
            "fit_warmstart_train", "fit_batch_autotune", "fit_batch_ex", "fit_profile_scan",
-           "fit_wilks_interval", "fit_chi2_sf")
+           "fit_wilks_interval", "fit_chi2_sf", "fit_mc_create", "fit_mc_destroy",
+           "fit_mc_spectrum", "fit_mc_status")
 
 
 def lib_path() -> str:
@@ -162,6 +163,15 @@ def load(build_if_missing: bool = False):
     L.fit_wilks_interval.restype = C.c_int
     L.fit_chi2_sf.argtypes = [C.c_double, C.c_int]
     L.fit_chi2_sf.restype = C.c_double
+    L.fit_mc_create.argtypes = [C.c_int, C.c_int, vp, C.c_int64, vp, vp, vp, vp, C.c_int,
+                                C.POINTER(vp)]
+    L.fit_mc_create.restype = C.c_int
+    L.fit_mc_destroy.argtypes = [vp]
+    L.fit_mc_destroy.restype = None
+    L.fit_mc_spectrum.argtypes = [vp, C.c_int, vp, vp, vp]
+    L.fit_mc_spectrum.restype = C.c_int
+    L.fit_mc_status.argtypes = [vp]
+    L.fit_mc_status.restype = C.c_int
     L.fit_last_error.restype = C.c_char_p
     L.fit_kernel_launches.restype = C.c_int64
     for f in ("fit_model_create", "fit_model_info", "fit_model_expected", "fit_model_eval",
@@ -415,6 +425,45 @@ def fit_poisson_sample(n, mu, seed, offset, out, stream=None):
     _check(load().fit_poisson_sample(int(n), _ptr(mu), C.c_uint64(int(seed) & (2**64 - 1)),
                                      C.c_uint64(int(offset)), _ptr(out), _stream_ptr(stream)),
            "fit_poisson_sample")
+
+
+class McEventSet:
+    """Simulated signal events of one detector resident on the current CUDA device (wraps
+    fit_mc*). events: an object with energy, core, weight, bin (sorted), n_bins, core_L and
+    osc_mode, e.g. synth.McEvents."""
+
+    def __init__(self, events):
+        e = np.ascontiguousarray(events.energy, dtype=np.float32)
+        c = np.ascontiguousarray(events.core, dtype=np.uint8)
+        w = np.ascontiguousarray(events.weight, dtype=np.float32)
+        b = np.ascontiguousarray(events.bin, dtype=np.int32)
+        L = np.ascontiguousarray(events.core_L, dtype=np.float64)
+        if not (len(e) == len(c) == len(w) == len(b)):
+            raise ValueError("event arrays differ in length")
+        h = C.c_void_p()
+        _check(load().fit_mc_create(int(events.osc_mode), len(L), _ptr(L), len(e), _ptr(e), _ptr(c),
+                                    _ptr(w), _ptr(b), int(events.n_bins), C.byref(h)),
+               "fit_mc_create")
+        self.handle = h
+        self.n_events, self.n_bins = len(e), int(events.n_bins)
+
+    def spectrum(self, B, params, out, stream=None):
+        """out[b, j] = sum of w_e P(L_e, E_e; params[b]) over the events of bin j (float64 [B x
+        n_bins]; params float64 [B x 4]; host or device buffers)."""
+        _check(load().fit_mc_spectrum(self.handle, int(B), _ptr(params), _ptr(out),
+                                      _stream_ptr(stream)), "fit_mc_spectrum")
+
+    def status(self):
+        """Raises FitError if a staging wait of an earlier spectrum call ran out of time."""
+        _check(load().fit_mc_status(self.handle), "fit_mc_status")
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.fit_mc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
 
 
 class Mlp:

@@ -52,3 +52,23 @@ def test_default_opts_and_error_message_without_gpu():
     assert rc == -1
     assert b"null" in L.fit_last_error()
     assert np.isfinite(o.f_noise_rel)
+
+
+def test_event_set_rejects_unsorted_bins_on_the_host():
+    """fit_mc_create validates the events before it touches the device."""
+    import ctypes as C
+    L = fitcore.load()
+    e = np.array([2.0, 3.0, 4.0], np.float32)
+    c = np.zeros(3, np.uint8)
+    w = np.ones(3, np.float32)
+    b = np.array([0, 2, 1], np.int32)
+    Lc = np.array([1000.0])
+    h = C.c_void_p()
+    rc = L.fit_mc_create(0, 1, Lc.ctypes.data, 3, e.ctypes.data, c.ctypes.data, w.ctypes.data,
+                         b.ctypes.data, 3, C.byref(h))
+    assert rc != 0 and b"not sorted" in L.fit_last_error()
+    b = np.array([0, 1, 1], np.int32)
+    c[1] = 1   # core out of range
+    rc = L.fit_mc_create(0, 1, Lc.ctypes.data, 3, e.ctypes.data, c.ctypes.data, w.ctypes.data,
+                         b.ctypes.data, 3, C.byref(h))
+    assert rc != 0
