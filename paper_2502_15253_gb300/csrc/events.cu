@@ -69,11 +69,11 @@ struct McArgs {
     double *out;            // [B x n_bins], cleared by the caller
 };
 
-// One parameter set: the phases' mass splittings as float pairs and the sin^2 coefficients as
-// float pairs (Eq. 1: x_ee, x_21 with C0, C1; exact 3-flavour: x_21, x_31, x_32 with C0..C2).
-struct McSet {
-    float dm[3], dm_lo[3];
-    OscCoef kc;
+// One parameter set: the phases' mass splittings as float pairs (Eq. 1: x_ee, x_21; exact
+// 3-flavour: x_21, x_31, x_32) and the sin^2 coefficients C rounded once to FP32 (a relative
+// 6e-8, below the error of the sin^2 polynomial). Padded to three 16-byte vectors.
+struct __align__(16) McSet {
+    float dm[4], dm_lo[4], C[4];
 };
 
 __device__ McSet make_set(int mode, const double *p) {
@@ -94,12 +94,14 @@ __device__ McSet make_set(int mode, const double *p) {
         d[1] = e[3];
         d[2] = f2_add(e[3], F2{-e[2].h, -e[2].l});   // dm2_32 = dm2_31 - dm2_21
     }
+    const OscCoef k = osc_coef(mode, e);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         s.dm[i] = d[i].h;
         s.dm_lo[i] = d[i].l;
+        s.C[i] = k.hi[i] + k.lo[i];
     }
-    s.kc = osc_coef(mode, e);
+    s.dm[3] = s.dm_lo[3] = s.C[3] = 0.f;
     return s;
 }
 
@@ -125,6 +127,15 @@ __device__ __forceinline__ float sin2_phase(float dm, float dm_lo, float c_hi, f
     const float yh = dm * c_hi;
     const float yl = fmaf(dm, c_hi, -yh) + fmaf(dm, c_lo, dm_lo * c_hi);
     return sin2pi((yh - rintf(yh)) + yl);
+}
+
+// P(L, E) of one event for one set: 1 - sum_i C_i sin^2(x_i)
+template <int NPH>
+__device__ __forceinline__ float survival_ev(const McSet &S, float c_hi, float c_lo) {
+    float P = 1.f;
+#pragma unroll
+    for (int i = 0; i < NPH; ++i) P = fmaf(-S.C[i], sin2_phase(S.dm[i], S.dm_lo[i], c_hi, c_lo), P);
+    return P;
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -232,8 +243,37 @@ __global__ void __launch_bounds__(kThreads, 3) mc_spectrum_kernel(McArgs a) {
             ch_[v] = kh * ih;
             cl_[v] = fmaf(kh, ih, -ch_[v]) + fmaf(kh, il, kl * ih);
         }
+        // the whole chunk in one bin (the common case with sorted events): plain warp sums
+        const int k0 = __shfl_sync(0xffffffffu, bn[0], 0);
+        if (__all_sync(0xffffffffu, bn[0] == k0 && bn[kV - 1] == k0)) {
+            for (int b = 0; b < a.B; ++b) {
+                const McSet S = sets[b];
+                float run = 0.f;
+#pragma unroll
+                for (int v = 0; v < kV; ++v) run = fmaf(w[v], survival_ev<NPH>(S, ch_[v], cl_[v]), run);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) run += __shfl_xor_sync(0xffffffffu, run, off);
+                if (lane == 0) {
+                    const int ck = carry_k[warp][b];
+                    const float c_h = carry_h[warp][b], c_l = carry_l[warp][b];
+                    float nh = run, nl = 0.f;
+                    if (ck == k0) {   // two-sum of the carry's high part and the chunk
+                        nh = c_h + run;
+                        const float bb = nh - c_h;
+                        nl = c_l + ((c_h - (nh - bb)) + (run - bb));
+                    } else if (ck >= 0) {
+                        atomicAdd(&a.out[(int64_t)b * a.n_bins + ck], (double)c_h + (double)c_l);
+                    }
+                    carry_h[warp][b] = nh;
+                    carry_l[warp][b] = nl;
+                    carry_k[warp][b] = k0;
+                }
+            }
+            __syncwarp();
+            continue;
+        }
         for (int b = 0; b < a.B; ++b) {
-            const McSet &S = sets[b];
+            const McSet S = sets[b];
             double *out = a.out + (int64_t)b * a.n_bins;
             float run = 0.f;
             int key = bn[0];
@@ -244,11 +284,7 @@ __global__ void __launch_bounds__(kThreads, 3) mc_spectrum_kernel(McArgs a) {
                     run = 0.f;
                     key = bn[v];
                 }
-                float P = 1.f;
-#pragma unroll
-                for (int i = 0; i < NPH; ++i)
-                    P -= cterm(S.kc, i, sin2_phase(S.dm[i], S.dm_lo[i], ch_[v], cl_[v]));
-                run = fmaf(w[v], P, run);
+                run = fmaf(w[v], survival_ev<NPH>(S, ch_[v], cl_[v]), run);
             }
             // segmented sum over lanes with equal keys: valid keys do not decrease along the
             // lanes and the padding key -1 only follows them, so equal keys are contiguous
