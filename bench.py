@@ -45,6 +45,8 @@ def parse():
                    help="fit engine: one persistent launch, or one round of launches per evaluation")
     p.add_argument("--mc-events", type=int, default=20_000_000,
                    help="simulated events of the event-reweighting measurement (0: skip)")
+    p.add_argument("--no-profile", action="store_true",
+                   help="skip the profile-likelihood and mass-ordering scans")
     p.add_argument("--no-warm-start", action="store_true",
                    help="skip the warm-start network measurement")
     p.add_argument("--ws-samples", type=int, default=2_000_000,
@@ -351,6 +353,11 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
     }
 
 
+# DRAM bytes (read + write) per event of mc_spectrum_kernel for one parameter set, from an ncu
+# capture of 11,904,680 events (154.81 MB read, 3.62 MB written); traffic grows with the events
+MC_DRAM_BYTES_PER_EVENT = (154.809088e6 + 3.621632e6) / 11_904_680
+
+
 def event_reweighting_measurement(args, stream, pg, world):
     """Event-level reweighting (the loop the paper moves to the GPU): oscillated spectra of
     args.mc_events simulated events of the two-core far detector (13 bytes an event, resident,
@@ -393,7 +400,9 @@ def event_reweighting_measurement(args, stream, pg, world):
         if B == 1:
             gbs = 13.0 * n / (ms / 1e3) / 1e9
             r["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": gbs / hbm_peak, "traffic": None,
+                             "frac": gbs / hbm_peak, "traffic": MC_DRAM_BYTES_PER_EVENT * n,
+                             "traffic_note": "DRAM read+write bytes per event of an ncu capture "
+                                             "of this kernel (11.9M events, one set), scaled",
                              "kernel": "mc_spectrum_kernel",
                              "peak_note": "measured copy bandwidth (hbm_gbs)"}
         out[f"sets_{B}"] = r
@@ -409,6 +418,68 @@ def event_reweighting_measurement(args, stream, pg, world):
         out["cpu_baseline"] = {"value": m / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
                                "sample": f"first {m} events, one parameter set, FP64"}
     mc.close()
+    return out
+
+
+def profile_measurement(args, spec, model, data_h, pg, world):
+    """Profile likelihood (Eq. 7): a 32 x 32 raster of constrained fits of the three-dataset
+    model in (sin^2 2th13, dm2_ee) on the first pseudo-experiment, one launch, with its 1-D
+    Wilks interval and goodness of fit; and the mass-ordering profiles of the 53 km model
+    (dm2_31 > 0 and < 0: Eq. 10 with +phi and -phi) on its normal-ordering Asimov data."""
+    import torch
+    from paper_2502_15253_gb300 import fitcore, synth
+
+    D = spec.n_bins
+    data = np.ascontiguousarray(data_h[:D])
+    mask = spec.all_mask()
+    i13, idm = spec.index("sin2_2th13"), spec.index("dm2_ee")
+    a = np.linspace(0.05, 0.13, 32)
+    b = np.linspace(2.3e-3, 2.7e-3, 32)
+    pts = np.array([[x, y] for x in a for y in b])
+    fitcore.fit_profile_scan(model, data, mask, [i13, idm], pts[:16])   # warm-up
+    barrier(pg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fitcore.fit_profile_scan(model, data, mask, [i13, idm], pts)
+    dt = max_over_ranks(time.perf_counter() - t0, pg)
+    g1 = np.linspace(0.0, 0.2, 81)
+    r1 = fitcore.fit_profile_scan(model, data, mask, [i13], g1)
+    lo, hi, op = fitcore.fit_wilks_interval(g1, r1["dchi2"], 1.0)
+    out = {"raster": "32 x 32 in sin^2 2th13 [0.05, 0.13] x dm2_ee [2.3e-3, 2.7e-3], plus the "
+                     "unconstrained fit, one launch",
+           "fits": len(pts) + 1, "s": dt, "raster_points_per_s": world * len(pts) / dt,
+           "converged_frac": float(np.mean(r["status"] == 0)),
+           "wilks_1sigma_sin2_2th13": [lo, hi], "wilks_open": int(op),
+           "gof_p": fitcore.fit_chi2_sf(r1["nll_min"], D - 2), "gof_dof": D - 2}
+    spec2 = synth.make_model("c2")
+    m2 = fitcore.Model(spec2)
+    asimov, _ = fitcore.expected_numpy(m2, spec2.theta0[None, :])
+    i31 = spec2.index("dm2_31")
+    no = np.linspace(2.44e-3, 2.56e-3, 25)
+    io = -np.linspace(2.40e-3, 2.52e-3, 25)
+    st_io = spec2.theta0.copy()
+    st_io[i31] = io[12]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r_no = fitcore.fit_profile_scan(m2, asimov[0], spec2.all_mask(), [i31], no)
+    r_io = fitcore.fit_profile_scan(m2, asimov[0], spec2.all_mask(), [i31], io, start=st_io)
+    dt2 = max_over_ranks(time.perf_counter() - t0, pg)
+    nll0 = min(r_no["nll_min"], r_io["nll_min"])
+    d_no = r_no["dchi2"] + r_no["nll_min"] - nll0
+    d_io = r_io["dchi2"] + r_io["nll_min"] - nll0
+
+    def ee(th):   # Eq. 2, magnitudes
+        s12 = th[spec2.index("sin2_th12")]
+        d21, d31 = th[spec2.index("dm2_21")], th[i31]
+        return (1 - s12) * abs(d31) + s12 * abs(d31 - d21)
+
+    k_no, k_io = int(np.argmin(d_no)), int(np.argmin(d_io))
+    out["mass_ordering"] = {
+        "model": "53 km ten-core far + near detector, Asimov data of the normal ordering",
+        "points": len(no) + len(io), "s": dt2,
+        "dchi2_inverted_min": float(d_io[k_io]),
+        "best_dm2_ee_normal": ee(r_no["theta"][k_no]), "best_dm2_ee_inverted": ee(r_io["theta"][k_io]),
+        "converged_frac": float(np.mean(np.concatenate([r_no["status"], r_io["status"]]) == 0))}
     return out
 
 
@@ -543,6 +614,10 @@ def run_ours(args):
         ws = warm_start_measurement(args, spec, model, inst, data_d, res, best_d, opts, stream,
                                     flush, pg, world)
 
+    prof = None
+    if not args.no_profile:
+        prof = profile_measurement(args, spec, model, data_h, pg, world)
+
     mc = None
     if args.mc_events > 0:
         mc = event_reweighting_measurement(args, stream, pg, world)
@@ -574,6 +649,7 @@ def run_ours(args):
             "clocks": clk, "wall_s": wall,
             "cpu_baseline": cpu,
             "warm_start": ws,
+            "profile_likelihood": prof,
             "event_reweighting": mc,
         }
         print(json.dumps(out))

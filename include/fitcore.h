@@ -64,7 +64,7 @@ extern "C" {
 
 /* Survival-probability forms */
 #define FIT_OSC_EQ1 0     /* eta = (sin^2 2th13, dm2_ee, sin^2 2th12, dm2_21)       Eq. 1, 2 */
-#define FIT_OSC_VACUUM3 1 /* eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31), normal ordering */
+#define FIT_OSC_VACUUM3 1 /* eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31); dm2_31 > 0 normal, < 0 inverted ordering (Eq. 10 with +phi / -phi) */
 
 /* Size limits of one model */
 #define FIT_MAX_DATASETS 8

@@ -188,7 +188,8 @@ int orc_n_data(const orc_handle *h) { return h->n_data; }
  *   p = (sin^2 2th13, dm2_ee, sin^2 2th12, dm2_21)
  *   P = 1 - sin^2 2th13 sin^2(x_ee) - cos^4 th13 sin^2 2th12 sin^2(x_21),
  *   x_ab = K dm2_ab L / E, cos^2 th13 = (1 + sqrt(1 - sin^2 2th13)) / 2.
- * mode 1 - exact vacuum three-flavour survival for normal ordering (the quantity the
+ * mode 1 - exact vacuum three-flavour survival, normal ordering for dm2_31 > 0 and inverted for
+ *   dm2_31 < 0 (the quantity the
  *   medium-baseline expansion of Eq. 10 approximates):
  *   p = (sin^2 th12, sin^2 th13, dm2_21, dm2_31), dm2_32 = dm2_31 - dm2_21,
  *   P = 1 - cos^4 th13 sin^2 2th12 sin^2 x_21

@@ -33,7 +33,7 @@ BASE_SEED = 250215253
 
 # Survival-probability parameterisations understood by both implementations.
 OSC_EQ1 = 0        # Eq. 1: (sin^2 2th13, dm2_ee, sin^2 2th12, dm2_21)
-OSC_VACUUM3 = 1    # exact 3-flavour vacuum, normal ordering: (sin^2 th12, sin^2 th13, dm2_21, dm2_31)
+OSC_VACUUM3 = 1    # exact 3-flavour vacuum: (sin^2 th12, sin^2 th13, dm2_21, dm2_31); the sign of dm2_31 is the ordering
 
 PROMPT_SHIFT_MEV = 0.782   # E_vis = E_nu - 0.782 MeV (IBD kinematics, neutron recoil neglected)
 RESPONSE_EPS0 = 0.9        # nominal detection efficiency folded into the response

@@ -36,14 +36,15 @@ def p_two_flavour_amplitude(theta, dm2, L, E):
     return abs(amp) ** 2
 
 
-def p_eq10_corrected(s12, s13, dm21, dm31, L, E):
-    """Eq. 10 in its corrected reading (normal ordering, +phi)."""
+def p_eq10_corrected(s12, s13, dm21, dm31, L, E, sign=1.0):
+    """Eq. 10 in its corrected reading: +phi for normal ordering, -phi (sign = -1) for
+    inverted ordering; Delta m^2_ee of Eq. 2 taken in magnitude."""
     t12, t13 = np.arcsin(np.sqrt(s12)), np.arcsin(np.sqrt(s13))
     S12, S13 = np.sin(2 * t12) ** 2, np.sin(2 * t13) ** 2
     dmee = np.cos(t12) ** 2 * abs(dm31) + np.sin(t12) ** 2 * abs(dm31 - dm21)   # Eq. 2
     d21, dee = K * dm21 * L / E, K * dmee * L / E
     phi = np.arctan2(np.cos(2 * t12) * np.sin(d21), np.cos(d21)) - d21 * np.cos(2 * t12)
-    return (1 - 0.5 * S13 * (1 - np.sqrt(1 - S12 * np.sin(d21) ** 2) * np.cos(2 * dee + phi))
+    return (1 - 0.5 * S13 * (1 - np.sqrt(1 - S12 * np.sin(d21) ** 2) * np.cos(2 * dee + sign * phi))
             - S12 * np.cos(t13) ** 4 * np.sin(d21) ** 2)
 
 
@@ -71,6 +72,23 @@ def test_vacuum3_matches_corrected_eq10():
     for L, E in GRID:
         p = [0.307, 0.022, 7.5e-5, 2.5e-3]
         assert oracle.survival(1, p, L, E) == pytest.approx(p_eq10_corrected(*p, L, E), abs=1e-13)
+
+
+def test_inverted_ordering_is_eq10_with_minus_phi():
+    """The exact vacuum formula at negative dm2_31 (inverted ordering) is the PMNS amplitude
+    sum with m_3^2 < 0 and the corrected Eq. 10 with the sign of phi flipped; with +phi it is
+    not (the two orderings differ at 53 km)."""
+    s12, s13, dm21 = 0.307, 0.022, 7.5e-5
+    worst_plus = 0.0
+    for L, E in GRID:
+        for dm31 in (-2.4e-3, -2.5e-3):
+            p = [s12, s13, dm21, dm31]
+            got = oracle.survival(1, p, L, E)
+            assert got == pytest.approx(p_amplitude(*p, L, E), abs=1e-13)
+            assert got == pytest.approx(p_eq10_corrected(*p, L, E, sign=-1.0), abs=1e-13)
+            if L > 5e4:
+                worst_plus = max(worst_plus, abs(got - p_eq10_corrected(*p, L, E, sign=1.0)))
+    assert worst_plus > 1e-2
 
 
 def test_eq1_two_flavour_limit_matches_rotation_amplitude():
