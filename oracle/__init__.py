@@ -74,7 +74,7 @@ class _OrcModel(C.Structure):
         ("scale", C.POINTER(C.c_double)),
         ("n_cov", C.c_int), ("cov_size", C.POINTER(C.c_int)), ("cov_idx", C.POINTER(C.c_int)),
         ("cov", C.POINTER(C.c_double)),
-        ("osc_mode", C.c_int), ("osc_idx", C.c_int * 4), ("osc_val", C.c_double * 4),
+        ("osc_mode", C.c_int), ("osc_idx", C.c_int * 6), ("osc_val", C.c_double * 6),
         ("n_cores", C.c_int), ("core_power_idx", C.POINTER(C.c_int)),
         ("n_true", C.c_int), ("e_lo", C.c_double), ("e_hi", C.c_double),
         ("n_det", C.c_int), ("det_n_reco", C.POINTER(C.c_int)),
@@ -145,9 +145,14 @@ def _i(a):
 
 
 def survival(mode: int, p, L: float, E: float, with_grad: bool = False):
-    """Survival probability P(L, E) (Eq. 1 for mode 0, exact 3-flavour vacuum for mode 1)."""
+    """Survival probability P(L, E) (Eq. 1 for mode 0, exact 3-flavour vacuum for mode 1, exact
+    3+1 vacuum for mode 2 with p = (sin^2 th12, sin^2 th13, dm2_21, dm2_31, sin^2 2th14, dm2_41))."""
+    n = 6 if int(mode) == 2 else 4
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    if p.size != n:
+        raise ValueError(f"mode {mode} takes {n} parameters")
     pa, pp = _d(p)
-    dp = np.zeros(4)
+    dp = np.zeros(n)
     val = lib().orc_survival(int(mode), pp, float(L), float(E), _d(dp)[1] if with_grad else None)
     if with_grad:
         # _d returned a view of dp (already float64 contiguous), so dp was written in place
@@ -185,9 +190,9 @@ class OracleModel:
         m.cov_idx = i(np.concatenate([ix for ix, _ in s.cov_blocks]) if s.cov_blocks else [0])
         m.cov = d(np.concatenate([c.ravel() for _, c in s.cov_blocks]) if s.cov_blocks else [0.0])
         m.osc_mode = s.osc_mode
-        for k in range(4):
-            m.osc_idx[k] = int(s.osc_idx[k])
-            m.osc_val[k] = float(s.osc_val[k])
+        for k in range(6):   # the 3+1 formula has six survival parameters, the others four
+            m.osc_idx[k] = int(s.osc_idx[k]) if k < len(s.osc_idx) else -1
+            m.osc_val[k] = float(s.osc_val[k]) if k < len(s.osc_val) else 0.0
         m.n_cores = s.n_cores
         m.core_power_idx = i(s.core_power_idx)
         m.n_true, m.e_lo, m.e_hi = s.n_true, s.e_lo, s.e_hi

@@ -47,9 +47,9 @@ typedef struct {
     const int *cov_size;   /* [n_cov] */
     const int *cov_idx;    /* concatenated parameter indices */
     const double *cov;     /* concatenated row-major m x m covariances */
-    int osc_mode;          /* 0: Eq. 1 ; 1: exact 3-flavour vacuum */
-    int osc_idx[4];
-    double osc_val[4];
+    int osc_mode;          /* 0: Eq. 1 ; 1: exact 3-flavour vacuum ; 2: exact 3+1 vacuum */
+    int osc_idx[6];        /* entries 4, 5 used by mode 2 only */
+    double osc_val[6];
     int n_cores;
     const int *core_power_idx;
     int n_true;
@@ -194,6 +194,16 @@ int orc_n_data(const orc_handle *h) { return h->n_data; }
  *   p = (sin^2 th12, sin^2 th13, dm2_21, dm2_31), dm2_32 = dm2_31 - dm2_21,
  *   P = 1 - cos^4 th13 sin^2 2th12 sin^2 x_21
  *         - sin^2 2th13 (cos^2 th12 sin^2 x_31 + sin^2 th12 sin^2 x_32).
+ * mode 2 - exact vacuum 3+1 survival (one sterile state; the 3+1 model of the sterile
+ *   search, with the two new parameters sin^2 2th14 and dm2_41):
+ *   p = (sin^2 th12, sin^2 th13, dm2_21, dm2_31, sin^2 2th14, dm2_41),
+ *   P = 1 - 4 sum_{i<j} |U_ei|^2 |U_ej|^2 sin^2 x_ji with the first row of the mixing matrix
+ *   |U_e| = (c12 c13 c14, s12 c13 c14, s13 c14, s14), i.e.
+ *   P = 1 - cos^4 th14 [cos^4 th13 sin^2 2th12 sin^2 x_21
+ *                       + sin^2 2th13 (cos^2 th12 sin^2 x_31 + sin^2 th12 sin^2 x_32)]
+ *         - sin^2 2th14 [cos^2 th13 (cos^2 th12 sin^2 x_41 + sin^2 th12 sin^2 x_42)
+ *                        + sin^2 th13 sin^2 x_43],
+ *   dm2_42 = dm2_41 - dm2_21, dm2_43 = dm2_41 - dm2_31, cos^2 th14 = (1 + sqrt(1 - sin^2 2th14))/2.
  * Returns P; dP (if not NULL) receives dP/dp_i. */
 double orc_survival(int mode, const double *p, double L, double E, double *dP)
 {
@@ -212,6 +222,35 @@ double orc_survival(int mode, const double *p, double L, double E, double *dP)
             dP[1] = -s2t13 * 2.0 * see * cos(xee) * kl;
             dP[2] = -c4 * s21 * s21;
             dP[3] = -c4 * s2t12 * 2.0 * s21 * cos(x21) * kl;
+        }
+        return P;
+    } else if (mode == 2) {
+        double s12 = p[0], s13 = p[1], dm21 = p[2], dm31 = p[3], S14 = p[4], dm41 = p[5];
+        double c12 = 1.0 - s12, c13 = 1.0 - s13;
+        double S12 = 4.0 * s12 * c12, S13 = 4.0 * s13 * c13;
+        double root = sqrt(1.0 - S14);
+        double c14 = 0.5 * (1.0 + root);          /* cos^2 th14 */
+        double C4 = c14 * c14;
+        double x21 = dm21 * kl, x31 = dm31 * kl, x32 = (dm31 - dm21) * kl;
+        double x41 = dm41 * kl, x42 = (dm41 - dm21) * kl, x43 = (dm41 - dm31) * kl;
+        double q21 = sin(x21) * sin(x21), q31 = sin(x31) * sin(x31), q32 = sin(x32) * sin(x32);
+        double q41 = sin(x41) * sin(x41), q42 = sin(x42) * sin(x42), q43 = sin(x43) * sin(x43);
+        double A = c13 * c13 * S12 * q21 + S13 * (c12 * q31 + s12 * q32);   /* three-flavour bracket */
+        double Bs = c13 * (c12 * q41 + s12 * q42) + s13 * q43;              /* sterile bracket */
+        double P = 1.0 - C4 * A - S14 * Bs;
+        if (dP) {
+            /* d sin^2 x / d dm2 = 2 sin x cos x kl */
+            double d21 = sin(2.0 * x21) * kl, d31 = sin(2.0 * x31) * kl, d32 = sin(2.0 * x32) * kl;
+            double d41 = sin(2.0 * x41) * kl, d42 = sin(2.0 * x42) * kl, d43 = sin(2.0 * x43) * kl;
+            double dC4 = -c14 / (2.0 * root);      /* d cos^4 th14 / d sin^2 2th14 */
+            dP[0] = -C4 * (c13 * c13 * 4.0 * (1.0 - 2.0 * s12) * q21 + S13 * (q32 - q31))
+                    - S14 * c13 * (q42 - q41);
+            dP[1] = -C4 * (-2.0 * c13 * S12 * q21 + 4.0 * (1.0 - 2.0 * s13) * (c12 * q31 + s12 * q32))
+                    - S14 * (q43 - (c12 * q41 + s12 * q42));
+            dP[2] = -C4 * (c13 * c13 * S12 * d21 - S13 * s12 * d32) + S14 * c13 * s12 * d42;
+            dP[3] = -C4 * S13 * (c12 * d31 + s12 * d32) + S14 * s13 * d43;
+            dP[4] = -dC4 * A - Bs;
+            dP[5] = -S14 * (c13 * (c12 * d41 + s12 * d42) + s13 * d43);
         }
         return P;
     } else {
@@ -331,16 +370,21 @@ static void escale_of(const orc_model *m, const double *theta, int d, double *a)
     a[2] = pval(theta, ai[2], 0.0);
 }
 
+/* number of survival parameters of a formula */
+static int n_osc(int mode) { return mode == 2 ? 6 : 4; }
+
 static void osc_params(const orc_model *m, const double *theta, double *p)
 {
-    for (int i = 0; i < 4; ++i) p[i] = m->osc_idx[i] >= 0 ? theta[m->osc_idx[i]] : m->osc_val[i];
+    for (int i = 0; i < 6; ++i) p[i] = 0.0;
+    for (int i = 0; i < n_osc(m->osc_mode); ++i)
+        p[i] = m->osc_idx[i] >= 0 ? theta[m->osc_idx[i]] : m->osc_val[i];
 }
 
 /* u_d (signal per true bin before energy correction) for dataset d */
 static void signal_true(const orc_handle *h, const double *theta, int d, double *u)
 {
     const orc_model *m = &h->m;
-    double de = (m->e_hi - m->e_lo) / m->n_true, p[4];
+    double de = (m->e_hi - m->e_lo) / m->n_true, p[6];
     osc_params(m, theta, p);
     double n = pval(theta, m->ds_norm_idx[d], 1.0);
     for (int k = 0; k < m->n_true; ++k) {
@@ -443,7 +487,7 @@ double orc_nll(const orc_handle *h, const double *theta, const double *data, uin
     double *gu = (double *)malloc(sizeof(double) * nt);
     double *mu = (double *)malloc(sizeof(double) * (h->n_data > 0 ? h->n_data : 1));
     double *gmu = (double *)malloc(sizeof(double) * (h->n_data > 0 ? h->n_data : 1));
-    double nll = 0.0, p[4];
+    double nll = 0.0, p[6];
     osc_params(m, theta, p);
     if (grad) memset(grad, 0, sizeof(double) * m->n_params);
 
@@ -502,18 +546,18 @@ double orc_nll(const orc_handle *h, const double *theta, const double *data, uin
             double t = m->ds_t[d * nt + k];
             int si = m->ds_shape_idx[d * nt + k];
             double s = pval(theta, si, 1.0);
-            double ptot = 0.0, dptot[4] = {0.0, 0.0, 0.0, 0.0};
+            double ptot = 0.0, dptot[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
             for (int c = 0; c < C; ++c) {
                 double w = m->ds_weight[d * C + c];
                 if (w == 0.0) continue;
-                double dP[4];
+                double dP[6];
                 double P = orc_survival(m->osc_mode, p, m->ds_baseline[d * C + c], E, dP);
                 double pw = pval(theta, m->core_power_idx[c], 1.0);
                 ptot += pw * w * P;
-                for (int i = 0; i < 4; ++i) dptot[i] += pw * w * dP[i];
+                for (int i = 0; i < n_osc(m->osc_mode); ++i) dptot[i] += pw * w * dP[i];
                 if (m->core_power_idx[c] >= 0) grad[m->core_power_idx[c]] += gu[k] * t * n * s * w * P;
             }
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < n_osc(m->osc_mode); ++i)
                 if (m->osc_idx[i] >= 0) grad[m->osc_idx[i]] += gu[k] * t * n * s * dptot[i];
             if (m->ds_norm_idx[d] >= 0) grad[m->ds_norm_idx[d]] += gu[k] * t * s * ptot;
             if (si >= 0) grad[si] += gu[k] * t * n * ptot;
@@ -798,7 +842,7 @@ void orc_fit_many(orc_handle *const *hs, int n_inst, const int *model_of, const 
 
 /* Event-level reweighting ([S], "GPU accelerated computation"): the oscillated spectrum of
  * simulated events, out[b] = sum over the events in reco bin b of weight_e P(L_core(e), E_e)
- * with the survival formula `mode` at the parameters p[4]. Events in any order; bins outside
+ * with the survival formula `mode` at the parameters p (4, or 6 for mode 2). Events in any order; bins outside
  * [0, n_bins) are skipped. */
 void orc_event_spectrum(int mode, const double *p, const double *core_L, long long n_events, const float *energy,
                         const unsigned char *core, const float *weight, const int *bin, int n_bins, double *out)

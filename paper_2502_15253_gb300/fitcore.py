@@ -29,7 +29,7 @@ class fit_model_desc(C.Structure):
         ("scale", C.POINTER(C.c_double)),
         ("n_cov", C.c_int), ("cov_size", C.POINTER(C.c_int)), ("cov_idx", C.POINTER(C.c_int)),
         ("cov", C.POINTER(C.c_double)),
-        ("osc_mode", C.c_int), ("osc_idx", C.c_int * 4), ("osc_val", C.c_double * 4),
+        ("osc_mode", C.c_int), ("osc_idx", C.c_int * 6), ("osc_val", C.c_double * 6),
         ("n_cores", C.c_int), ("core_power_idx", C.POINTER(C.c_int)),
         ("n_true", C.c_int), ("e_lo", C.c_double), ("e_hi", C.c_double),
         ("n_det", C.c_int), ("det_n_reco", C.POINTER(C.c_int)),
@@ -241,9 +241,9 @@ class Model:
         m.cov_idx = i(np.concatenate([ix for ix, _ in s.cov_blocks]) if s.cov_blocks else [0])
         m.cov = d(np.concatenate([c.ravel() for _, c in s.cov_blocks]) if s.cov_blocks else [0.0])
         m.osc_mode = s.osc_mode
-        for k in range(4):
-            m.osc_idx[k] = int(s.osc_idx[k])
-            m.osc_val[k] = float(s.osc_val[k])
+        for k in range(6):   # the 3+1 formula has six survival parameters, the others four
+            m.osc_idx[k] = int(s.osc_idx[k]) if k < len(s.osc_idx) else -1
+            m.osc_val[k] = float(s.osc_val[k]) if k < len(s.osc_val) else 0.0
         m.n_cores = s.n_cores
         m.core_power_idx = i(s.core_power_idx)
         m.n_true, m.e_lo, m.e_hi = s.n_true, s.e_lo, s.e_hi

@@ -34,6 +34,7 @@ BASE_SEED = 250215253
 # Survival-probability parameterisations understood by both implementations.
 OSC_EQ1 = 0        # Eq. 1: (sin^2 2th13, dm2_ee, sin^2 2th12, dm2_21)
 OSC_VACUUM3 = 1    # exact 3-flavour vacuum: (sin^2 th12, sin^2 th13, dm2_21, dm2_31); the sign of dm2_31 is the ordering
+OSC_STERILE4 = 2   # exact 3+1 vacuum: the four above, then (sin^2 2th14, dm2_41)
 
 PROMPT_SHIFT_MEV = 0.782   # E_vis = E_nu - 0.782 MeV (IBD kinematics, neutron recoil neglected)
 RESPONSE_EPS0 = 0.9        # nominal detection efficiency folded into the response
@@ -98,8 +99,8 @@ class ModelSpec:
     scale: np.ndarray             # [P] minimiser step scale (the "transformation layer" unit)
     cov_blocks: list              # [(idx int32[m], cov float64[m, m])], prior mean theta0[idx]
     osc_mode: int
-    osc_idx: np.ndarray           # [4] int32 parameter index or -1
-    osc_val: np.ndarray           # [4] value used when osc_idx == -1
+    osc_idx: np.ndarray           # [4] ([6] for OSC_STERILE4) int32 parameter index or -1
+    osc_val: np.ndarray           # [4] ([6]) value used when osc_idx == -1
     core_power_idx: np.ndarray    # [C] int32 parameter index of each core's power, -1 = fixed 1
     n_true: int
     e_lo: float
@@ -307,10 +308,13 @@ def make_c0(seed=BASE_SEED, tiny=False):
                      np.array([-1], np.int32), n_true, e_lo, e_hi, [det], [ds])
 
 
-def make_c1(seed=BASE_SEED):
+def make_c1(seed=BASE_SEED, sterile=False):
     """Double Chooz-like FD-I / FD-II / ND with two cores, 38 reco bins each, ~291 parameters.
 
-    Oscillation: full Eq. 1 with sin^2 2th12 and dm2_21 as constrained nuisances. Per dataset:
+    Oscillation: full Eq. 1 with sin^2 2th12 and dm2_21 as constrained nuisances. With
+    sterile=True ("c1s", the 3+1 search): the exact 3+1 vacuum survival with sin^2 th12,
+    dm2_21 and dm2_31 constrained, sin^2 th13 free, and the two new parameters sin^2 2th14
+    (nominal 0) and dm2_41 (nominal 0.1 eV^2) free; everything else as c1. Per dataset:
     efficiency (correlated prior), energy scale (a0, a1, a2), 38 signal shape reweights
     (joint 114 x 114 prior, FD-I/FD-II correlation 0.9). Backgrounds: Li-9 (shape shared by
     all datasets, rate shared by FD-I/FD-II, rates free), accidentals (per-dataset shape and
@@ -323,10 +327,17 @@ def make_c1(seed=BASE_SEED):
     redges = np.linspace(1.0, 8.6, 39)
     nr = 38
     p = _Params()
-    i_s13 = p.add("sin2_2th13", 0.09, 0.0, 0.016)
-    i_dmee = p.add("dm2_ee", 2.5e-3, 1e-4)
-    i_s12 = p.add("sin2_2th12", 0.851, 0.02)
-    i_dm21 = p.add("dm2_21", 7.53e-5, 0.18e-5)
+    if sterile:
+        osc = np.array([p.add("sin2_th12", 0.307, 0.013), p.add("sin2_th13", 0.0231, 0.0, 0.004),
+                        p.add("dm2_21", 7.53e-5, 0.18e-5), p.add("dm2_31", 2.5e-3, 1e-4),
+                        p.add("sin2_2th14", 0.0, 0.0, 0.01), p.add("dm2_41", 0.1, 0.0, 0.002)],
+                       np.int32)
+        osc_val = np.array([0.307, 0.0231, 7.53e-5, 2.5e-3, 0.0, 0.1])
+    else:
+        osc = np.array([p.add("sin2_2th13", 0.09, 0.0, 0.016), p.add("dm2_ee", 2.5e-3, 1e-4),
+                        p.add("sin2_2th12", 0.851, 0.02), p.add("dm2_21", 7.53e-5, 0.18e-5)],
+                       np.int32)
+        osc_val = np.array([0.09, 2.5e-3, 0.851, 7.53e-5])
     eff = p.add_block("eff", 3, 1.0, 0.01)
     esc = [np.array([p.add(f"a0[{d}]", 0.0, 0.01), p.add(f"a1[{d}]", 1.0, 0.005),
                      p.add(f"a2[{d}]", 0.0, 0.001)], np.int32) for d in range(3)]
@@ -364,10 +375,9 @@ def make_c1(seed=BASE_SEED):
         base = np.array(base)
         datasets.append(Dataset(nm, det, signal_spectrum(tedges, nev), base, _core_weights(base),
                                 -1, int(eff[d]), esc[d], shp[d * nr + gidx].astype(np.int32), bk))
-    return ModelSpec("c1", names, th0, sig, scl, cov_blocks, OSC_EQ1,
-                     np.array([i_s13, i_dmee, i_s12, i_dm21], np.int32),
-                     np.array([0.09, 2.5e-3, 0.851, 7.53e-5]), pw, n_true, e_lo, e_hi, dets,
-                     datasets)
+    return ModelSpec("c1s" if sterile else "c1", names, th0, sig, scl, cov_blocks,
+                     OSC_STERILE4 if sterile else OSC_EQ1, osc, osc_val, pw, n_true, e_lo, e_hi,
+                     dets, datasets)
 
 
 def make_c2(seed=BASE_SEED):
@@ -422,6 +432,8 @@ def make_model(name: str, seed: int = BASE_SEED) -> ModelSpec:
         return make_c0(seed, tiny=True)
     if name == "c1":
         return make_c1(seed)
+    if name == "c1s":
+        return make_c1(seed, sterile=True)
     if name == "c2":
         return make_c2(seed)
     raise ValueError(f"unknown model {name!r}")

@@ -30,6 +30,17 @@ def p_amplitude(s12, s13, dm21, dm31, L, E, delta=0.0):
     return abs(amp) ** 2
 
 
+def p_amplitude4(s12, s13, dm21, dm31, S14, dm41, L, E):
+    """3+1: |sum_i |U_ei|^2 exp(-i m_i^2 L / 2E)|^2 with the first row (c12 c13 c14,
+    s12 c13 c14, s13 c14, s14) of the 4x4 mixing matrix (m_1 = 0)."""
+    s14 = 0.5 * (1.0 - np.sqrt(1.0 - S14))          # sin^2 th14 for th14 <= pi/4
+    c14 = 1.0 - s14
+    ue2 = np.array([(1 - s12) * (1 - s13) * c14, s12 * (1 - s13) * c14, s13 * c14, s14])
+    m2 = np.array([0.0, dm21, dm31, dm41])
+    amp = (ue2 * np.exp(-1j * 2.0 * K * m2 * L / E)).sum()
+    return abs(amp) ** 2
+
+
 def p_two_flavour_amplitude(theta, dm2, L, E):
     """2x2 rotation amplitude: |cos^2 th + sin^2 th exp(-i dm2 L / 2E)|^2."""
     amp = np.cos(theta) ** 2 + np.sin(theta) ** 2 * np.exp(-1j * 2.0 * K * dm2 * L / E)
@@ -55,6 +66,38 @@ def test_survival_zero_mixing_is_one():
     for L, E in GRID:
         assert oracle.survival(0, [0.0, 2.5e-3, 0.0, 7.5e-5], L, E) == 1.0
         assert oracle.survival(1, [0.0, 0.0, 7.5e-5, 2.5e-3], L, E) == 1.0
+        assert oracle.survival(2, [0.0, 0.0, 7.5e-5, 2.5e-3, 0.0, 0.5], L, E) == 1.0
+
+
+def test_sterile_matches_four_flavour_amplitude():
+    rng = np.random.default_rng(4)
+    for _ in range(300):
+        s12, s13 = rng.uniform(0.05, 0.6), rng.uniform(0.0, 0.2)
+        dm21, dm31 = rng.uniform(1e-5, 2e-4), rng.choice([-1, 1]) * rng.uniform(1e-3, 4e-3)
+        S14, dm41 = rng.uniform(0.0, 0.99), 10 ** rng.uniform(-3.5, 0.5)
+        L, E = rng.uniform(10, 6e4), rng.uniform(1.8, 10)
+        p = [s12, s13, dm21, dm31, S14, dm41]
+        # both sides take sines of phases up to ~1e5 rad: a few ulps of the phase each
+        tol = 1e-13 + 1e-15 * 2.0 * K * dm41 * L / E
+        assert oracle.survival(2, p, L, E) == pytest.approx(p_amplitude4(*p, L, E), abs=tol)
+
+
+def test_sterile_without_sterile_mixing_is_three_flavour():
+    for L, E in GRID:
+        for dm41 in (1e-3, 0.05, 2.0):
+            p3 = [0.307, 0.022, 7.5e-5, 2.5e-3]
+            assert oracle.survival(2, p3 + [0.0, dm41], L, E) == pytest.approx(
+                oracle.survival(1, p3, L, E), abs=4e-16)
+
+
+def test_sterile_two_flavour_limit_matches_rotation_amplitude():
+    """th12 = th13 = 0: P = 1 - sin^2 2th14 sin^2 x_41, the 2x2 rotation by th14."""
+    for L, E in GRID:
+        for S14, dm41 in ((0.1, 0.05), (0.3, 1.2)):
+            th = 0.5 * np.arcsin(np.sqrt(S14))
+            got = oracle.survival(2, [0.0, 0.0, 7.5e-5, 2.5e-3, S14, dm41], L, E)
+            tol = 1e-14 + 1e-15 * 2.0 * K * dm41 * L / E   # ulps of phases up to ~5e4 rad
+            assert got == pytest.approx(p_two_flavour_amplitude(th, dm41, L, E), abs=tol)
 
 
 def test_vacuum3_matches_pmns_amplitude():
@@ -118,12 +161,15 @@ def test_eq1_with_eq2_close_to_exact_at_short_baseline_only():
 
 
 @pytest.mark.parametrize("mode,p", [(0, [0.09, 2.5e-3, 0.851, 7.53e-5]),
-                                    (1, [0.307, 0.022, 7.5e-5, 2.5e-3])])
+                                    (1, [0.307, 0.022, 7.5e-5, 2.5e-3]),
+                                    (2, [0.307, 0.022, 7.5e-5, 2.5e-3, 0.05, 0.3])])
 def test_survival_partials_match_central_differences(mode, p):
     for L, E in GRID[::5]:
         _, dp = oracle.survival(mode, p, L, E, with_grad=True)
-        for i in range(4):
+        for i in range(len(p)):
             h = 1e-6 * abs(p[i])
+            if p[i] < 1e-2 or i == 5:   # a mass splitting: keep the phase step below 1e-4 rad
+                h = min(h, 1e-4 / (K * L / E))
             pp, pm = list(p), list(p)
             pp[i] += h
             pm[i] -= h
@@ -291,7 +337,7 @@ def test_expected_backgrounds_and_efficiency_c1():
 # ---------------------------------------------------------------------------------------
 # -2lnL and gradient
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["c0", "c1", "c2"])
+@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s"])
 def test_asimov_nll_is_zero(name):
     spec = synth.make_model(name)
     om = oracle.OracleModel(spec)
@@ -317,7 +363,7 @@ def test_poisson_part_equals_library_pmf_sum():
     assert om.nll(theta, data, mask=m) == pytest.approx(ref_m, rel=1e-10)
 
 
-@pytest.mark.parametrize("name", ["c0", "c1", "c2"])
+@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s"])
 def test_gradient_matches_central_differences(name):
     spec = synth.make_model(name)
     om = oracle.OracleModel(spec)
