@@ -65,6 +65,10 @@ extern "C" {
 /* Survival-probability forms */
 #define FIT_OSC_EQ1 0     /* eta = (sin^2 2th13, dm2_ee, sin^2 2th12, dm2_21)       Eq. 1, 2 */
 #define FIT_OSC_VACUUM3 1 /* eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31); dm2_31 > 0 normal, < 0 inverted ordering (Eq. 10 with +phi / -phi) */
+/* exact 3+1 vacuum survival of the sterile-neutrino search ("Sterile neutrino searches": the
+ * two new parameters sin^2 2th14 and dm2_41, 0 <= sin^2 2th14 < 1):
+ * eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31, sin^2 2th14, dm2_41) */
+#define FIT_OSC_STERILE4 2
 
 /* Size limits of one model */
 #define FIT_MAX_DATASETS 8
@@ -90,9 +94,9 @@ typedef struct fit_model_desc {
     const int *cov_size;       /* [n_cov] block sizes m_b                                      */
     const int *cov_idx;        /* concatenated parameter indices, sum m_b                      */
     const double *cov;         /* concatenated row-major m_b x m_b covariance matrices         */
-    int osc_mode;              /* FIT_OSC_EQ1 or FIT_OSC_VACUUM3                               */
-    int osc_idx[4];            /* parameter index of each survival parameter, or -1            */
-    double osc_val[4];         /* value used where osc_idx is -1                               */
+    int osc_mode;              /* FIT_OSC_EQ1, FIT_OSC_VACUUM3 or FIT_OSC_STERILE4              */
+    int osc_idx[6];            /* parameter index of each survival parameter, or -1 (entries    */
+    double osc_val[6];         /* 4, 5 only for FIT_OSC_STERILE4); value where osc_idx is -1    */
     int n_cores;               /* reactor cores, <= FIT_MAX_CORES                              */
     const int *core_power_idx; /* [C] parameter index of each core's power factor              */
     int n_true;                /* true-energy grid: n_true uniform bins over [e_lo, e_hi] MeV  */
@@ -379,7 +383,8 @@ int fit_mc_create(int osc_mode, int n_cores, const double *core_L, int64_t n_eve
                   int n_bins, fit_mc **out);
 void fit_mc_destroy(fit_mc *mc);
 /* out[b][j] = sum over the events e of bin j of weight_e P(L_core(e), E_e; params[b]) for
- * b < B <= 64 parameter sets (params [B x 4] in the osc_mode's order, host or device; out
+ * b < B <= 64 parameter sets (params [B x 4], [B x 6] for FIT_OSC_STERILE4, in the
+ * osc_mode's order, host or device; out
  * [B x n_bins] double, host or device). One pass over the events serves all B sets. With
  * device buffers the call is asynchronous on stream; with host buffers it returns when out is
  * written. */

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) signal_v_kernel(const DevModel *__restric
     float *pv = reinterpret_cast<float *>(smem_raw + sizeof(DevModel));
     float *pd = pv + m.P;
     float *u = pd + m.P;
-    __shared__ OscCoef kco;
+    __shared__ OscCoefN<6> kco;
     const int b = blockIdx.x, d = blockIdx.y, tid = threadIdx.x, nth = blockDim.x;
     const DevDataset &ds = m.ds[d];
     const int N_t = m.N_t;
@@ -60,12 +60,11 @@ __global__ void __launch_bounds__(256) signal_v_kernel(const DevModel *__restric
             pd_out[(int64_t)b * m.P + i] = pd[i];
         }
     }
-    float eta[4], eta_lo[4];
+    float eta[kMaxOsc], eta_lo[kMaxOsc];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int p = m.osc_idx[i];
-        const bool is_dm = (m.osc_mode == FIT_OSC_EQ1) ? (i == 1 || i == 3) : (i >= 2);
-        if (is_dm) {
+    for (int i = 0; i < kMaxOsc; ++i) {
+        const int p = i < m.n_osc ? m.osc_idx[i] : -1;
+        if (osc_is_dm(m.osc_mode, i)) {
             eta[i] = p >= 0 ? m.theta0_f[p] : m.osc_val[i];
             eta_lo[i] = p >= 0 ? m.theta0_lo[p] + (float)(th[p] - m.theta0[p]) : m.osc_val_lo[i];
         } else {
@@ -74,27 +73,48 @@ __global__ void __launch_bounds__(256) signal_v_kernel(const DevModel *__restric
         }
     }
     if (tid == 0) {
-        double e[4];
-        for (int i = 0; i < 4; ++i) e[i] = m.osc_idx[i] >= 0 ? th[m.osc_idx[i]] : m.osc_val_d[i];
-        double c[3];
+        double e[kMaxOsc];
+        for (int i = 0; i < kMaxOsc; ++i)
+            e[i] = i >= m.n_osc ? 0.0 : (m.osc_idx[i] >= 0 ? th[m.osc_idx[i]] : m.osc_val_d[i]);
+        double c[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (m.osc_mode == FIT_OSC_EQ1) {
             const double c2 = 0.5 * (1.0 + sqrt(fmax(1.0 - e[0], 0.0)));
             c[0] = e[0];
             c[1] = c2 * c2 * e[2];
-            c[2] = 0.0;
         } else {
             const double S12 = 4.0 * e[0] * (1.0 - e[0]), S13 = 4.0 * e[1] * (1.0 - e[1]);
-            c[0] = (1.0 - e[1]) * (1.0 - e[1]) * S12;
-            c[1] = S13 * (1.0 - e[0]);
-            c[2] = S13 * e[0];
+            double C4 = 1.0;   // cos^4 th14 (3+1 formula; 1 without a sterile state)
+            if (m.osc_mode == FIT_OSC_STERILE4) {
+                const double c14 = 0.5 * (1.0 + sqrt(fmax(1.0 - e[4], 0.0)));
+                C4 = c14 * c14;
+                c[3] = e[4] * (1.0 - e[1]) * (1.0 - e[0]);
+                c[4] = e[4] * (1.0 - e[1]) * e[0];
+                c[5] = e[4] * e[1];
+            }
+            c[0] = C4 * (1.0 - e[1]) * (1.0 - e[1]) * S12;
+            c[1] = C4 * S13 * (1.0 - e[0]);
+            c[2] = C4 * S13 * e[0];
         }
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < 6; ++i) {
             kco.hi[i] = (float)c[i];
             kco.lo[i] = (float)(c[i] - (double)kco.hi[i]);
         }
     }
     __syncthreads();
-    const OscCoef kc = kco;
+    const OscCoefN<6> kc6 = kco;
+    OscCoef kc;
+    float eta4[4], eta_lo4[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        kc.hi[i] = kc6.hi[i];
+        kc.lo[i] = kc6.lo[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        eta4[i] = eta[i];
+        eta_lo4[i] = eta_lo[i];
+    }
+    const bool sterile = m.osc_mode == FIT_OSC_STERILE4;
     const PP nrm = ppair(m, pv, pd, ds.norm_idx, 1.f);
     const EMap em = make_emap(m, ds, pv, pd);
     {
@@ -116,8 +136,14 @@ __global__ void __launch_bounds__(256) signal_v_kernel(const DevModel *__restric
             if (w == 0.f) continue;
             const float ch = ds.kl_hi[c] * ih;
             const float cl = fmaf(ds.kl_hi[c], ih, -ch) + ds.kl_hi[c] * il + ds.kl_lo[c] * ih;
-            float dP[4];
-            const float P = survival(m, eta, eta_lo, kc, ch, cl, dP);
+            float P;
+            if (sterile) {
+                float dP[6];
+                P = survival_sterile(eta, eta_lo, kc6, ch, cl, dP);
+            } else {
+                float dP[4];
+                P = survival(m, eta4, eta_lo4, kc, ch, cl, dP);
+            }
             pt += pmul(ppair(m, pv, pd, m.core_power_idx[c], 1.f), w * P);
         }
         const float ts = pmul(ppair(m, pv, pd, ds.shape_idx[k], 1.f), ds.t[k]);

@@ -222,7 +222,9 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
     if (d->n_det < 1 || d->n_det > FIT_MAX_DETECTORS) return bad("n_det out of range");
     if (d->n_ds < 1 || d->n_ds > FIT_MAX_DATASETS) return bad("n_ds out of range");
     if (d->n_bkg < 0 || d->n_bkg > FIT_MAX_BACKGROUNDS) return bad("n_bkg out of range");
-    if (d->osc_mode != FIT_OSC_EQ1 && d->osc_mode != FIT_OSC_VACUUM3) return bad("osc_mode");
+    if (d->osc_mode != FIT_OSC_EQ1 && d->osc_mode != FIT_OSC_VACUUM3 && d->osc_mode != FIT_OSC_STERILE4)
+        return bad("osc_mode");
+    const int n_osc = d->osc_mode == FIT_OSC_STERILE4 ? 6 : 4;
     if (!(d->e_lo > 0.0 && d->e_hi > d->e_lo)) return bad("energy grid");
     if (!d->theta0 || !d->prior_sigma || !d->scale || !d->core_power_idx || !d->det_n_reco ||
         !d->det_response || !d->ds_det || !d->ds_t || !d->ds_baseline || !d->ds_weight ||
@@ -232,8 +234,10 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
     if (d->n_bkg > 0 && (!d->bkg_ds || !d->bkg_template || !d->bkg_rate_idx || !d->bkg_shape_idx))
         return bad("missing background arrays");
     auto pidx_ok = [P](int i) { return i >= -1 && i < P; };
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < n_osc; ++i)
         if (!pidx_ok(d->osc_idx[i])) return bad("osc_idx");
+    if (n_osc == 6 && d->osc_idx[4] < 0 && !(d->osc_val[4] >= 0.0 && d->osc_val[4] < 1.0))
+        return bad("sin^2 2th14 outside [0, 1)");
     for (int c = 0; c < C; ++c)
         if (!pidx_ok(d->core_power_idx[c])) return bad("core_power_idx");
     for (int i = 0; i < d->n_det; ++i)
@@ -252,11 +256,13 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
     h.e_lo = (float)d->e_lo;
     h.de = (float)de;
     h.inv_de = (float)(1.0 / de);
-    for (int i = 0; i < 4; ++i) {
-        h.osc_idx[i] = d->osc_idx[i];
-        h.osc_val[i] = (float)d->osc_val[i];
-        h.osc_val_lo[i] = (float)(d->osc_val[i] - (double)h.osc_val[i]);
-        h.osc_val_d[i] = d->osc_val[i];
+    h.n_osc = n_osc;
+    for (int i = 0; i < fitcore::kMaxOsc; ++i) {
+        const double v = i < n_osc ? d->osc_val[i] : 0.0;
+        h.osc_idx[i] = i < n_osc ? d->osc_idx[i] : -1;
+        h.osc_val[i] = (float)v;
+        h.osc_val_lo[i] = (float)(v - (double)h.osc_val[i]);
+        h.osc_val_d[i] = v;
     }
     for (int c = 0; c < C; ++c) h.core_power_idx[c] = d->core_power_idx[c];
     {
@@ -572,7 +578,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
             for (int j = 0; j < h.ds[ds].n_reco; ++j) slot_ds[h.ds[ds].data_off + j] = ds;
         A.put(&h.slot_ds, slot_ds);
     }
-    h.ws_eval_floats = fitcore::eval_ws_floats(Nt, C, max_reco);
+    h.ws_eval_floats = fitcore::eval_ws_floats(Nt, C, max_reco, n_osc);
     h.ldt = (Nt + 3) / 4 * 4;
 
     // ---- upload ---------------------------------------------------------------------------
@@ -1074,15 +1080,18 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
         A.ws_in_smem = eval_smem <= 48 * 1024 ? 1 : 0;
         const size_t esm = A.ws_in_smem ? eval_smem : fitcore::ls_eval_smem_bytes(P, 0);
         const size_t ssm = fitcore::ls_step_smem_bytes();
+        const bool six = h.n_osc == 6;   // the 3+1 builds of the evaluation kernels
+        const void *kf = six ? (const void *)fitcore::ls_forward_kernel6 : (const void *)fitcore::ls_forward_kernel;
+        const void *ka = six ? (const void *)fitcore::ls_adjoint_kernel6 : (const void *)fitcore::ls_adjoint_kernel;
         int per_sm_f = 0, per_sm_a = 0, per_sm_s = 0;
-        for (const void *k : {(const void *)fitcore::ls_forward_kernel, (const void *)fitcore::ls_adjoint_kernel})
+        for (const void *k : {kf, ka})
             if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm) != cudaSuccess)
                 rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep shared memory");
         for (const void *k : {(const void *)fitcore::ls_step_kernel, (const void *)fitcore::ls_init_kernel})
             if (!rc && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm) != cudaSuccess)
                 rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep shared memory");
-        if (!rc && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, fitcore::ls_forward_kernel, 128, esm) ||
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, fitcore::ls_adjoint_kernel, 128, esm) ||
+        if (!rc && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, kf, 128, esm) ||
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, ka, 128, esm) ||
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, fitcore::ls_step_kernel, 128, ssm)))
             rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep occupancy");
         if (!rc && (per_sm_f < 1 || per_sm_a < 1 || per_sm_s < 1))
@@ -1141,8 +1150,9 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
                 rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep counter");
                 break;
             }
-            fitcore::ls_forward_kernel<<<std::max(1, std::min(active * nd, cap_f)), 128, esm, s>>>(A);
-            fitcore::ls_adjoint_kernel<<<std::max(1, std::min(active * nd, cap_a)), 128, esm, s>>>(A);
+            void *largs[] = {&A};
+            cudaLaunchKernel(kf, dim3(std::max(1, std::min(active * nd, cap_f))), dim3(128), largs, esm, s);
+            cudaLaunchKernel(ka, dim3(std::max(1, std::min(active * nd, cap_a))), dim3(128), largs, esm, s);
             fitcore::ls_step_kernel<<<std::max(1, std::min(active, cap_s)), 128, ssm, s>>>(A);
             g_launches += 3;
             if (cudaGetLastError() != cudaSuccess ||
@@ -1256,8 +1266,10 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
                                                  o, s, data_len, par_len);
     if (o.engine != 0) return fail(FIT_ERR_INVALID_ARG, "fit_batch: engine must be 0 or 1");
     int max_loc = 0;   // working vectors + evaluation workspace, without the history
+    int n_osc = 4;     // the 3+1 build of the kernel when any model uses that formula
     for (int mi = 0; mi < n_models; ++mi) {
         const DevModel &h = models[mi]->host;
+        n_osc = std::max(n_osc, h.n_osc);
         // (multiples of 4 floats: the fit vectors start on 16-byte boundaries)
         const int ws4 = (h.ws_eval_floats + 3) & ~3;
         max_need = std::max(max_need, fitcore::fit_vec_floats(h.P, o.history) + ws4);
@@ -1277,7 +1289,7 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
         if (pl == 2) return fitcore::fit_smem_bytes(max_loc);
         return fitcore::fit_smem_bytes(0);
     };
-    auto kernel_for = [](int variant) { return fitcore::fit_kernel_func(variant); };
+    auto kernel_for = [n_osc](int variant) { return fitcore::fit_kernel_func(variant, n_osc); };
     auto blocks_for = [&](int pl, int variant) -> int {
         const size_t sm = smem_for(pl);
         if (sm > std::min(kSmemCap, cfg.smem_optin)) return 0;

@@ -14,6 +14,7 @@ namespace fitcore {
 
 constexpr int kMaxWarps = 16;      // blocks of at most 512 threads
 constexpr int kMaxBkgDs = 6;       // backgrounds per dataset
+constexpr int kMaxOsc = 6;         // survival parameters (6 for the 3+1 formula, else 4)
 
 struct DevDetector {
     int n_reco;
@@ -54,10 +55,11 @@ struct DevDataset {
 struct DevModel {
     int P, N_t, C, n_ds, n_data, osc_mode, n_blocks, n_bkg;
     float e_lo, de, inv_de;
-    int osc_idx[4];
-    float osc_val[4];
-    float osc_val_lo[4];     // low parts of the constant survival parameters
-    double osc_val_d[4];     // the constant survival parameters in double
+    int n_osc;               // survival parameters of osc_mode: 4, or 6 (FIT_OSC_STERILE4)
+    int osc_idx[kMaxOsc];
+    float osc_val[kMaxOsc];
+    float osc_val_lo[kMaxOsc];   // low parts of the constant survival parameters
+    double osc_val_d[kMaxOsc];   // the constant survival parameters in double
     int core_power_idx[FIT_MAX_CORES];
     const float *e_edge;     // [N_t + 1]
     const float *inv_e_hi;   // [N_t] 1 / E_k (true-bin centre) as a float pair
@@ -169,11 +171,14 @@ __device__ __forceinline__ void phase_sc(float dm, float dm_lo, float c_hi, floa
 //   FIT_OSC_VACUUM3: P = 1 - C0 sin^2 x_21 - C1 sin^2 x_31 - C2 sin^2 x_32,
 //                    C0 = cos^4 th13 sin^2 2th12, C1 = sin^2 2th13 cos^2 th12,
 //                    C2 = sin^2 2th13 sin^2 th12
-struct OscCoef {
-    float hi[3], lo[3];
+template <int NT>
+struct OscCoefN {
+    float hi[NT], lo[NT];
 };
+using OscCoef = OscCoefN<3>;
 
-__device__ __forceinline__ float cterm(const OscCoef &k, int i, float q) {
+template <int NT>
+__device__ __forceinline__ float cterm(const OscCoefN<NT> &k, int i, float q) {
     return fmaf(q, k.lo[i], k.hi[i] * q);
 }
 
@@ -294,6 +299,100 @@ __device__ __forceinline__ float survival(const DevModel &m, const float (&eta)[
     return survival_mode(m.osc_mode, eta, eta_lo, k, c_hi, c_lo, dP);
 }
 
+// Exact 3+1 vacuum survival (FIT_OSC_STERILE4), one sterile state added to the three-flavour
+// formula: eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31, sin^2 2th14, dm2_41),
+//   P = 1 - cos^4 th14 [C0 sin^2 x21 + C1 sin^2 x31 + C2 sin^2 x32]
+//         - sin^2 2th14 [cos^2 th13 (cos^2 th12 sin^2 x41 + sin^2 th12 sin^2 x42)
+//                        + sin^2 th13 sin^2 x43]
+// (the first row of the 4x4 mixing matrix is (c12 c13 c14, s12 c13 c14, s13 c14, s14)), with
+// the coefficients k.hi/lo[0..5] of the six sin^2 terms; x32, x42 and x43 from the angle
+// differences of x21, x31 and x41.
+__device__ __forceinline__ float survival_sterile(const float (&eta)[6], const float (&eta_lo)[6],
+                                                  const OscCoefN<6> &k, float c_hi, float c_lo,
+                                                  float (&dP)[6]) {
+    const float dx = 3.14159265358979f * c_hi;
+    const float s12 = eta[0], s13 = eta[1], S14 = eta[4];
+    const float c12 = 1.f - s12, c13 = 1.f - s13;
+    const float S12 = 4.f * s12 * c12, S13 = 4.f * s13 * c13;
+    const float root = sqrtf(fmaxf(1.f - S14, 1e-12f));
+    const float c14 = 0.5f * (1.f + root), C4 = c14 * c14;
+    float a21, b21, a31, b31, a41, b41;
+    phase_sc(eta[2], eta_lo[2], c_hi, c_lo, a21, b21);
+    phase_sc(eta[3], eta_lo[3], c_hi, c_lo, a31, b31);
+    phase_sc(eta[5], eta_lo[5], c_hi, c_lo, a41, b41);
+    const float a32 = a31 * b21 - b31 * a21, b32 = b31 * b21 + a31 * a21;   // x31 - x21
+    const float a42 = a41 * b21 - b41 * a21, b42 = b41 * b21 + a41 * a21;   // x41 - x21
+    const float a43 = a41 * b31 - b41 * a31, b43 = b41 * b31 + a41 * a31;   // x41 - x31
+    const float q21 = a21 * a21, q31 = a31 * a31, q32 = a32 * a32;
+    const float q41 = a41 * a41, q42 = a42 * a42, q43 = a43 * a43;
+    const float P = ((((((1.f - cterm(k, 0, q21)) - cterm(k, 1, q31)) - cterm(k, 2, q32)) -
+                      cterm(k, 3, q41)) - cterm(k, 4, q42)) - cterm(k, 5, q43));
+    const float d21 = 2.f * a21 * b21 * dx, d31 = 2.f * a31 * b31 * dx, d32 = 2.f * a32 * b32 * dx;
+    const float d41 = 2.f * a41 * b41 * dx, d42 = 2.f * a42 * b42 * dx, d43 = 2.f * a43 * b43 * dx;
+    const float A = c13 * c13 * S12 * q21 + S13 * (c12 * q31 + s12 * q32);
+    const float Bs = c13 * (c12 * q41 + s12 * q42) + s13 * q43;
+    const float dC4 = -c14 * 0.5f / root;
+    dP[0] = -C4 * (c13 * c13 * 4.f * (1.f - 2.f * s12) * q21 + S13 * (q32 - q31)) - S14 * c13 * (q42 - q41);
+    dP[1] = -C4 * (-2.f * c13 * S12 * q21 + 4.f * (1.f - 2.f * s13) * (c12 * q31 + s12 * q32)) -
+            S14 * (q43 - (c12 * q41 + s12 * q42));
+    dP[2] = -C4 * (c13 * c13 * S12 * d21 - S13 * s12 * d32) + S14 * c13 * s12 * d42;
+    dP[3] = -C4 * S13 * (c12 * d31 + s12 * d32) + S14 * s13 * d43;
+    dP[4] = -dC4 * A - Bs;
+    dP[5] = -S14 * (c13 * (c12 * d41 + s12 * d42) + s13 * d43);
+    return P;
+}
+
+// The six coefficients of survival_sterile from float pairs e of the exact parameter values.
+__device__ __forceinline__ OscCoefN<6> osc_coef_sterile(const F2 (&e)[6]) {
+    const F2 one{1.f, 0.f};
+    const F2 c12 = f2_one_minus(e[0]), c13 = f2_one_minus(e[1]);
+    const F2 S12 = f2_scale(f2_mul(e[0], c12), 4.f), S13 = f2_scale(f2_mul(e[1], c13), 4.f);
+    const F2 c14 = f2_scale(f2_add(one, f2_sqrt(f2_one_minus(e[4]))), 0.5f);   // cos^2 th14
+    const F2 C4 = f2_mul(c14, c14);
+    F2 cf[6];
+    cf[0] = f2_mul(C4, f2_mul(f2_mul(c13, c13), S12));
+    cf[1] = f2_mul(C4, f2_mul(S13, c12));
+    cf[2] = f2_mul(C4, f2_mul(S13, e[0]));
+    cf[3] = f2_mul(e[4], f2_mul(c13, c12));
+    cf[4] = f2_mul(e[4], f2_mul(c13, e[0]));
+    cf[5] = f2_mul(e[4], e[1]);
+    OscCoefN<6> k;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        k.hi[i] = cf[i].h;
+        k.lo[i] = cf[i].l;
+    }
+    return k;
+}
+
+// whether survival parameter i of a formula is a mass splitting (carried as a float pair)
+__host__ __device__ __forceinline__ bool osc_is_dm(int mode, int i) {
+    return mode == FIT_OSC_EQ1 ? (i == 1 || i == 3) : (i == 2 || i == 3 || i == 5);
+}
+
+// Survival of the formula with NOSC parameters: 4 (Eq. 1 or the three-flavour formula) or 6
+// (the 3+1 formula).
+template <int NOSC>
+struct OscTraits;
+template <>
+struct OscTraits<4> {
+    using Coef = OscCoefN<3>;
+    static __device__ __forceinline__ float survival(int mode, const float (&eta)[4], const float (&eta_lo)[4],
+                                                     const Coef &k, float c_hi, float c_lo, float (&dP)[4]) {
+        return survival_mode(mode, eta, eta_lo, k, c_hi, c_lo, dP);
+    }
+    static __device__ __forceinline__ Coef coef(int mode, const F2 (&e)[4]) { return osc_coef(mode, e); }
+};
+template <>
+struct OscTraits<6> {
+    using Coef = OscCoefN<6>;
+    static __device__ __forceinline__ float survival(int, const float (&eta)[6], const float (&eta_lo)[6],
+                                                     const Coef &k, float c_hi, float c_lo, float (&dP)[6]) {
+        return survival_sterile(eta, eta_lo, k, c_hi, c_lo, dP);
+    }
+    static __device__ __forceinline__ Coef coef(int, const F2 (&e)[6]) { return osc_coef_sterile(e); }
+};
+
 // Poisson deviance 2[mu - n + n ln(n/mu)] = 2 mu h(r), r = (n - mu)/mu,
 // h(r) = (1+r) ln(1+r) - r, by its alternating series for |r| < 1/4.
 __device__ __forceinline__ float deviance(float n, float mu) {
@@ -324,18 +423,18 @@ struct EvalWs {
     float *u, *v, *ts, *ptot, *dp, *pcw, *f0, *gmu;
 };
 
-__host__ __device__ inline int eval_ws_floats(int N_t, int C, int max_reco) {
-    return (8 + C) * N_t + 2 * max_reco;
+__host__ __device__ inline int eval_ws_floats(int N_t, int C, int max_reco, int n_osc) {
+    return (4 + n_osc + C) * N_t + 2 * max_reco;
 }
 
-__device__ __forceinline__ EvalWs carve_eval_ws(float *base, int N_t, int C, int max_reco) {
+__device__ __forceinline__ EvalWs carve_eval_ws(float *base, int N_t, int C, int max_reco, int n_osc) {
     EvalWs w;
     w.u = base;
     w.v = w.u + N_t;
     w.ts = w.v + N_t;
     w.ptot = w.ts + N_t;
-    w.dp = w.ptot + N_t;          // 4 * N_t
-    w.pcw = w.dp + 4 * N_t;       // C * N_t
+    w.dp = w.ptot + N_t;          // n_osc * N_t
+    w.pcw = w.dp + n_osc * N_t;   // C * N_t
     w.f0 = w.pcw + C * N_t;       // max_reco
     w.gmu = w.f0 + max_reco;      // max_reco
     return w;
@@ -394,16 +493,19 @@ __device__ __forceinline__ EMap make_emap(const DevModel &m, const DevDataset &d
 // ------------------------------------------------------------------------------------
 // Per-dataset constants of one evaluation: survival parameters and coefficients,
 // normalisation, efficiency, energy map.
-struct DsCtx {
-    OscCoef kc;
-    float eta[4], eta_lo[4];
+template <int NOSC>
+struct DsCtxT {
+    typename OscTraits<NOSC>::Coef kc;
+    float eta[NOSC], eta_lo[NOSC];
     PP nrm, eff;
     EMap em;
 };
+using DsCtx = DsCtxT<4>;
 
 // Fills c; false (and status |= kStEscale) when the energy map is not increasing with slope in
 // (1/4, 4) on the grid. Contains a barrier.
-static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const float *pd, DsCtx &c,
+template <int NOSC>
+static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const float *pd, DsCtxT<NOSC> &c,
                                 int *status) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
@@ -421,10 +523,9 @@ static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const
     // phase.
     float *eta = c.eta, *eta_lo = c.eta_lo;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < NOSC; ++i) {
         const int p = m.osc_idx[i];
-        const bool is_dm = (m.osc_mode == FIT_OSC_EQ1) ? (i == 1 || i == 3) : (i >= 2);
-        if (is_dm) {
+        if (osc_is_dm(m.osc_mode, i)) {
             eta[i] = p >= 0 ? m.theta0_f[p] : m.osc_val[i];
             eta_lo[i] = p >= 0 ? m.theta0_lo[p] + pd[p] : m.osc_val_lo[i];
         } else {
@@ -434,9 +535,9 @@ static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const
     }
     // the sin^2 coefficients from float pairs of the exact parameter values (every thread
     // forms the same values; no barrier)
-    F2 e[4];
+    F2 e[NOSC];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < NOSC; ++i) {
         const int p = m.osc_idx[i];
         if (p >= 0) {
             const float h = pv[p];
@@ -445,7 +546,7 @@ static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const
             e[i] = F2{m.osc_val[i], m.osc_val_lo[i]};
         }
     }
-    c.kc = osc_coef(m.osc_mode, e);
+    c.kc = OscTraits<NOSC>::coef(m.osc_mode, e);
     c.nrm = ppair(m, pv, pd, ds.norm_idx, 1.f);
     c.eff = ppair(m, pv, pd, ds.eff_idx, 1.f);
     c.em = make_emap(m, ds, pv, pd);
@@ -464,9 +565,9 @@ static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const
 }
 
 // Stage A: u_k (and with DERIV the per-bin partials the adjoint needs). Ends with a barrier.
-template <bool DERIV>
-static __device__ void ds_signal(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
-                                 EvalWs ws) {
+template <bool DERIV, int NOSC>
+static __device__ void ds_signal(const DevModel &m, int d, const float *pv, const float *pd,
+                                 const DsCtxT<NOSC> &c, EvalWs ws) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
     const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
@@ -482,7 +583,9 @@ static __device__ void ds_signal(const DevModel &m, int d, const float *pv, cons
     // ---- stage A: signal on the true grid (Eq. 1/2 x shares x reweights) -----------------
     for (int k = tid; k < N_t; k += nth) {
         const float ih = m.inv_e_hi[k], il = m.inv_e_lo[k];
-        float pt = 0.f, dpt[4] = {0.f, 0.f, 0.f, 0.f};
+        float pt = 0.f, dpt[NOSC];
+#pragma unroll
+        for (int i = 0; i < NOSC; ++i) dpt[i] = 0.f;
         for (int cc = 0; cc < C; ++cc) {
             const float w = ds.w[cc];
             if (w == 0.f) {
@@ -491,14 +594,14 @@ static __device__ void ds_signal(const DevModel &m, int d, const float *pv, cons
             }
             const float ch = ds.kl_hi[cc] * ih;
             const float cl = fmaf(ds.kl_hi[cc], ih, -ch) + ds.kl_hi[cc] * il + ds.kl_lo[cc] * ih;
-            float dP[4];
-            const float P = survival(m, c.eta, c.eta_lo, c.kc, ch, cl, dP);
+            float dP[NOSC];
+            const float P = OscTraits<NOSC>::survival(m.osc_mode, c.eta, c.eta_lo, c.kc, ch, cl, dP);
             const PP pw = ppair(m, pv, pd, m.core_power_idx[cc], 1.f);
             const float wP = w * P;
             if (DERIV) ws.pcw[cc * N_t + k] = wP;
             pt += pmul(pw, wP);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) if (DERIV) dpt[i] = fmaf(pw.h * w, dP[i], dpt[i]);
+            for (int i = 0; i < NOSC; ++i) if (DERIV) dpt[i] = fmaf(pw.h * w, dP[i], dpt[i]);
         }
         const float ts = pmul(ppair(m, pv, pd, ds.shape_idx[k], 1.f), ds.t[k]);
         if (DERIV) {
@@ -506,7 +609,7 @@ static __device__ void ds_signal(const DevModel &m, int d, const float *pv, cons
             ws.ptot[k] = pt;
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < NOSC; ++i)
             if (DERIV) ws.dp[i * N_t + k] = dpt[i];
         ws.u[k] = pmul(c.nrm, ts * pt);
     }
@@ -515,7 +618,8 @@ static __device__ void ds_signal(const DevModel &m, int d, const float *pv, cons
 }
 
 // Stage B: v = M(a) u. Ends with a barrier.
-static __device__ void ds_remap(const DevModel &m, int d, const DsCtx &c, EvalWs ws) {
+template <class Ctx>
+static __device__ void ds_remap(const DevModel &m, int d, const Ctx &c, EvalWs ws) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
     const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
@@ -561,7 +665,8 @@ static __device__ void ds_remap(const DevModel &m, int d, const DsCtx &c, EvalWs
 // Stages C and C2: fold, backgrounds, deviance, dD/dmu (ws.gmu) and the background-shape
 // gradient; returns the dataset's -2lnL (all threads). The efficiency and rate gradients are
 // added when grad != nullptr, data != nullptr and no status bit is set.
-static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
+template <class Ctx>
+static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, const float *pd, const Ctx &c,
                                      const float *data, EvalWs ws, float *grad, double *red, int *status,
                                      float *mu_out) {
     const DevDataset &ds = m.ds[d];
@@ -674,9 +779,9 @@ static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, 
 
 // Stages D, E and F: adjoint of the fold, of the energy map and of the signal; adds the
 // gradient contributions to grad. Needs ws.u/ts/ptot/dp/pcw (ds_signal<true>) and ws.gmu.
-template <int NC>
-static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
-                                  EvalWs ws, float *grad, double *red) {
+template <int NC, int NOSC>
+static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, const float *pd,
+                                     const DsCtxT<NOSC> &c, EvalWs ws, float *grad, double *red) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
     const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
@@ -711,10 +816,11 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
 
     // ---- stage E: adjoint of the energy map and of the signal ---------------------------
     // per source k: gu = sum_t F_kt gv_t; A0 = (gu - gv(floor Y_k)) / w, A1 = (gv(floor Y_k+1) - gu) / w
-    float ep[8 + NC];
-    // ep[0..2] d/da, ep[3..6] d/d eta, ep[7] d/d norm, ep[8+c] d/d power_c (NC >= C cores)
+    constexpr int kN = 3 + NOSC, kP = 4 + NOSC;   // index of d/d norm, first d/d power
+    float ep[kP + NC];
+    // ep[0..2] d/da, ep[3..3+NOSC) d/d eta, ep[kN] d/d norm, ep[kP+c] d/d power_c (NC >= C)
 #pragma unroll
-    for (int i = 0; i < 8 + NC; ++i) ep[i] = 0.f;
+    for (int i = 0; i < kP + NC; ++i) ep[i] = 0.f;
     for (int k = tid; k < N_t; k += nth) {
         const float e0 = m.e_edge[k], e1 = m.e_edge[k + 1];
         const float d0 = em.disp(e0), d1 = em.disp(e1);
@@ -737,24 +843,24 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
         const float ts = ws.ts[k], pt = ws.ptot[k];
         const float gb = pmul(c.nrm, gu * ts);    // d nll / d(ptot)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) ep[3 + i] = fmaf(gb, ws.dp[i * N_t + k], ep[3 + i]);
-        ep[7] = fmaf(gu * ts, pt, ep[7]);
+        for (int i = 0; i < NOSC; ++i) ep[3 + i] = fmaf(gb, ws.dp[i * N_t + k], ep[3 + i]);
+        ep[kN] = fmaf(gu * ts, pt, ep[kN]);
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc)
-            if (cc < C) ep[8 + cc] = fmaf(gb, ws.pcw[cc * N_t + k], ep[8 + cc]);
+            if (cc < C) ep[kP + cc] = fmaf(gb, ws.pcw[cc * N_t + k], ep[kP + cc]);
         ws.dp[k] = pmul(c.nrm, gu * ds.t[k] * pt);    // d nll / d s for this bin (dp0 reused)
     }
-    double etot[8 + NC];
-    block_sum<8 + NC>(ep, red, etot);
+    double etot[kP + NC];
+    block_sum<kP + NC>(ep, red, etot);
     if (tid == 0) {
         for (int i = 0; i < 3; ++i)
             if (ds.esc_idx[i] >= 0) grad[ds.esc_idx[i]] += (float)etot[i];
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < NOSC; ++i)
             if (m.osc_idx[i] >= 0) grad[m.osc_idx[i]] += (float)etot[3 + i];
-        if (ds.norm_idx >= 0) grad[ds.norm_idx] += (float)etot[7];
+        if (ds.norm_idx >= 0) grad[ds.norm_idx] += (float)etot[kN];
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc)
-            if (cc < C && m.core_power_idx[cc] >= 0) grad[m.core_power_idx[cc]] += (float)etot[8 + cc];
+            if (cc < C && m.core_power_idx[cc] >= 0) grad[m.core_power_idx[cc]] += (float)etot[kP + cc];
     }
     // ---- stage F: shape reweights (one thread per distinct parameter, CSR over bins) -----
     for (int i = tid; i < ds.n_sp; i += nth) {
@@ -769,18 +875,20 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
 // contributions (theta space, P floats). Returns the dataset's -2lnL (all threads); *status |=
 // kSt* bits on failure.
 // Stages D-F with the per-core sums sized for the model's core count.
-static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, const float *pd, const DsCtx &c,
-                                  EvalWs ws, float *grad, double *red) {
+template <int NOSC>
+static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, const float *pd,
+                                  const DsCtxT<NOSC> &c, EvalWs ws, float *grad, double *red) {
     if (m.C <= 2)
         ds_adjoint_nc<2>(m, d, pv, pd, c, ws, grad, red);
     else
         ds_adjoint_nc<FIT_MAX_CORES>(m, d, pv, pd, c, ws, grad, red);
 }
 
-static __device__ double eval_dataset(const DevModel &m, int d, const float *pv, const float *pd,
-                                      const float *data, EvalWs ws, float *grad, double *red,
-                                      int *status, float *mu_out) {
-    DsCtx c;
+template <int NOSC>
+static __device__ double eval_dataset_n(const DevModel &m, int d, const float *pv, const float *pd,
+                                        const float *data, EvalWs ws, float *grad, double *red,
+                                        int *status, float *mu_out) {
+    DsCtxT<NOSC> c;
     if (!ds_setup(m, d, pv, pd, c, status)) return 0.0;
     if (grad != nullptr && data != nullptr)
         ds_signal<true>(m, d, pv, pd, c, ws);
@@ -791,6 +899,19 @@ static __device__ double eval_dataset(const DevModel &m, int d, const float *pv,
     if (data == nullptr || grad == nullptr || (*(volatile int *)status) != 0) return nll_d;
     ds_adjoint(m, d, pv, pd, c, ws, grad, red);
     return nll_d;
+}
+
+// One dataset's -2lnL (and gradient). NOSC = 4: models of Eq. 1 or the three-flavour formula
+// only; NOSC = 6: any model (the 3+1 formula, the others through the four-parameter path).
+template <int NOSC = 4>
+static __device__ double eval_dataset(const DevModel &m, int d, const float *pv, const float *pd,
+                                      const float *data, EvalWs ws, float *grad, double *red,
+                                      int *status, float *mu_out) {
+    if constexpr (NOSC == 6) {
+        if (m.osc_mode == FIT_OSC_STERILE4)
+            return eval_dataset_n<6>(m, d, pv, pd, data, ws, grad, red, status, mu_out);
+    }
+    return eval_dataset_n<4>(m, d, pv, pd, data, ws, grad, red, status, mu_out);
 }
 
 }  // namespace fitcore

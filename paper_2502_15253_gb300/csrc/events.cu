@@ -70,38 +70,51 @@ struct McArgs {
 };
 
 // One parameter set: the phases' mass splittings as float pairs (Eq. 1: x_ee, x_21; exact
-// 3-flavour: x_21, x_31, x_32) and the sin^2 coefficients C rounded once to FP32 (a relative
-// 6e-8, below the error of the sin^2 polynomial). Padded to three 16-byte vectors.
+// 3-flavour: x_21, x_31, x_32; 3+1: those and x_41, x_42, x_43) and the sin^2 coefficients C
+// rounded once to FP32 (a relative 6e-8, below the error of the sin^2 polynomial).
 struct __align__(16) McSet {
-    float dm[4], dm_lo[4], C[4];
+    float dm[6], dm_lo[6], C[6];
 };
 
 __device__ McSet make_set(int mode, const double *p) {
     McSet s;
-    F2 e[4];
+    const int n = mode == FIT_OSC_STERILE4 ? 6 : 4;
+    F2 e[6];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float h = (float)p[i];
-        e[i] = f2_norm(h, (float)(p[i] - (double)h));
+    for (int i = 0; i < 6; ++i) {
+        const float h = i < n ? (float)p[i] : 0.f;
+        e[i] = f2_norm(h, i < n ? (float)(p[i] - (double)h) : 0.f);
     }
-    F2 d[3];
+    auto sub = [](F2 a, F2 b) { return f2_add(a, F2{-b.h, -b.l}); };
+    F2 d[6] = {};
+    float C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (mode == FIT_OSC_EQ1) {
         d[0] = e[1];
         d[1] = e[3];
-        d[2] = F2{0.f, 0.f};
     } else {
         d[0] = e[2];
         d[1] = e[3];
-        d[2] = f2_add(e[3], F2{-e[2].h, -e[2].l});   // dm2_32 = dm2_31 - dm2_21
+        d[2] = sub(e[3], e[2]);   // dm2_32 = dm2_31 - dm2_21
     }
-    const OscCoef k = osc_coef(mode, e);
+    if (mode == FIT_OSC_STERILE4) {
+        d[3] = e[5];
+        d[4] = sub(e[5], e[2]);   // dm2_42
+        d[5] = sub(e[5], e[3]);   // dm2_43
+        const OscCoefN<6> k = osc_coef_sterile(e);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < 6; ++i) C[i] = k.hi[i] + k.lo[i];
+    } else {
+        const F2 (&e4)[4] = reinterpret_cast<const F2 (&)[4]>(e);
+        const OscCoef k = osc_coef(mode, e4);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) C[i] = k.hi[i] + k.lo[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
         s.dm[i] = d[i].h;
         s.dm_lo[i] = d[i].l;
-        s.C[i] = k.hi[i] + k.lo[i];
+        s.C[i] = C[i];
     }
-    s.dm[3] = s.dm_lo[3] = s.C[3] = 0.f;
     return s;
 }
 
@@ -184,7 +197,8 @@ __global__ void __launch_bounds__(kThreads, 3) mc_spectrum_kernel(McArgs a) {
         (&carry_l[0][0])[i] = 0.f;
         (&carry_k[0][0])[i] = -1;
     }
-    for (int b = tid; b < a.B; b += kThreads) sets[b] = make_set(a.mode, a.params + 4 * b);
+    const int np = a.mode == FIT_OSC_STERILE4 ? 6 : 4;
+    for (int b = tid; b < a.B; b += kThreads) sets[b] = make_set(a.mode, a.params + np * b);
     if (tid < FIT_MAX_CORES) {
         klh[tid] = a.kl_hi[tid];
         kll[tid] = a.kl_lo[tid];
@@ -336,7 +350,8 @@ extern "C" {
 
 int fit_mc_create(int osc_mode, int n_cores, const double *core_L, int64_t n_events, const float *energy,
                   const uint8_t *core, const float *weight, const int *bin, int n_bins, fit_mc **out) {
-    if (!out || (osc_mode != FIT_OSC_EQ1 && osc_mode != FIT_OSC_VACUUM3) || n_cores < 1 ||
+    if (!out || (osc_mode != FIT_OSC_EQ1 && osc_mode != FIT_OSC_VACUUM3 && osc_mode != FIT_OSC_STERILE4) ||
+        n_cores < 1 ||
         n_cores > FIT_MAX_CORES || !core_L || n_events < 0 || n_bins < 1 ||
         (n_events > 0 && (!energy || !core || !weight || !bin)))
         return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_mc_create: bad argument");
@@ -416,8 +431,9 @@ int fit_mc_spectrum(fit_mc *m, int B, const double *params, double *out, void *s
     cudaGetLastError();
     double *pd = nullptr, *od = nullptr;
     int rc = FIT_OK;
-    if (!p_dev && (cudaMallocAsync(&pd, sizeof(double) * 4 * B, s) ||
-                   cudaMemcpyAsync(pd, params, sizeof(double) * 4 * B, cudaMemcpyHostToDevice, s)))
+    const size_t np = m->mode == FIT_OSC_STERILE4 ? 6 : 4;   // survival parameters per set
+    if (!p_dev && (cudaMallocAsync(&pd, sizeof(double) * np * B, s) ||
+                   cudaMemcpyAsync(pd, params, sizeof(double) * np * B, cudaMemcpyHostToDevice, s)))
         rc = fitcore_fail(FIT_ERR_CUDA, "fit_mc_spectrum: parameters");
     if (!rc && !o_dev && cudaMallocAsync(&od, sizeof(double) * (size_t)B * m->n_bins, s))
         rc = fitcore_fail(FIT_ERR_OOM, "fit_mc_spectrum: output");
@@ -443,8 +459,9 @@ int fit_mc_spectrum(fit_mc *m, int B, const double *params, double *out, void *s
         a.params = p_dev ? params : pd;
         a.out = outd;
         // one wave of resident blocks, each with a contiguous range of staging blocks
-        const void *fn = m->mode == FIT_OSC_EQ1 ? (const void *)fitcore::mc_spectrum_kernel<2>
-                                                : (const void *)fitcore::mc_spectrum_kernel<3>;
+        const void *fn = m->mode == FIT_OSC_EQ1       ? (const void *)fitcore::mc_spectrum_kernel<2>
+                         : m->mode == FIT_OSC_VACUUM3 ? (const void *)fitcore::mc_spectrum_kernel<3>
+                                                      : (const void *)fitcore::mc_spectrum_kernel<6>;
         const int dyn = 2 * (int)sizeof(fitcore::Stage);
         int dev = 0, n_sm = 0, per_sm = 0;
         cudaGetDevice(&dev);

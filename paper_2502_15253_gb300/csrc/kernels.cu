@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) eval_kernel(const DevModel *__restrict__ 
     float *grad = pd + m.P;
     float *zs = grad + m.P;
     float *wsb = ws_in_smem ? (zs + m.P) : (ws_global + (int64_t)blockIdx.x * m.ws_eval_floats);
-    const EvalWs ws = carve_eval_ws(wsb, m.N_t, m.C, m.max_reco);
+    const EvalWs ws = carve_eval_ws(wsb, m.N_t, m.C, m.max_reco, m.n_osc);
     const bool want_grad = grad_out != nullptr;
 
     for (int b = blockIdx.x; b < B; b += gridDim.x) {
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256) eval_kernel(const DevModel *__restrict__ 
             const bool on = mu_out ? true : ((mask >> d) & 1u);
             if (!on) continue;
             float *mo = mu_out ? mu_out + (int64_t)b * m.n_data + m.ds[d].data_off : nullptr;
-            nll += eval_dataset(m, d, pv, pd, dat, ws, want_grad ? grad : nullptr, S.red,
-                                &S.status, mo);
+            nll += eval_dataset<6>(m, d, pv, pd, dat, ws, want_grad ? grad : nullptr, S.red,
+                                   &S.status, mo);
             __syncthreads();
             if (S.status) break;
         }
@@ -465,6 +465,7 @@ __device__ __forceinline__ void hold_fixed(const uint8_t *fixed, float *gz, int 
 }
 
 // -2lnL(theta(z)) and its z-gradient gz. Returns +inf on an invalid point.
+template <int NOSC>
 __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &V, EvalWs ws,
                          const float *data, uint32_t mask, FitSmem &S, const uint8_t *fixed) {
     theta_of_z(m, z, V.pv, V.pd);
@@ -474,7 +475,7 @@ __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &
     double nll = 0.0;
     for (int d = 0; d < m.n_ds; ++d) {
         if (!((mask >> d) & 1u)) continue;
-        nll += eval_dataset(m, d, V.pv, V.pd, data, ws, V.gth, S.red, &S.status, nullptr);
+        nll += eval_dataset<NOSC>(m, d, V.pv, V.pd, data, ws, V.gth, S.red, &S.status, nullptr);
         __syncthreads();
         if (S.status) return INFINITY;
     }
@@ -792,12 +793,15 @@ __device__ void start_z(const DevModel &m, const double *st, float *z, float *pd
 }
 
 // Result: theta = theta0 + J z in double, and the fit's summary.
+// Held parameters (fixed) are reported at their start values exactly (their z carries the
+// start's FP32 rounding, ~1e-8 relative).
 __device__ void write_result(const DevModel &m, const FitState &st, const float *z, double *best,
-                             fit_result *out) {
+                             fit_result *out, const double *start, const uint8_t *fixed) {
     const int tid = threadIdx.x;
     for (int i = tid; i < m.P; i += blockDim.x) {
         const float s = m.zscale[i];
-        if (s > 0.f) best[i] = m.theta0[i] + (double)s * (double)z[i];
+        if (fixed && fixed[i]) best[i] = start ? start[i] : m.theta0[i];
+        else if (s > 0.f) best[i] = m.theta0[i] + (double)s * (double)z[i];
     }
     for (int b = 0; b < m.n_blocks; ++b) {
         const int n = m.blk_size[b];
@@ -825,7 +829,9 @@ __device__ void write_result(const DevModel &m, const FitState &st, const float 
 // fits one instance at a time, so MINB instances share an SM and cover each other's barrier and
 // load latencies. With the working set in shared memory four blocks of the larger register
 // budget measured faster; with it in global memory (L2) the fifth instance pays for itself.
-template <int MINB>
+// NOSC = 4: models of Eq. 1 or the three-flavour formula; NOSC = 6: any model, the 3+1 formula
+// included (a separate build, so that the common case carries none of its registers).
+template <int MINB, int NOSC>
 __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FitSmem &S = *reinterpret_cast<FitSmem *>(smem_raw);
@@ -860,7 +866,7 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
         float *base = loc_smem ? dyn : gws + (A.hist_global ? hfl : 0);
         float *hbase = A.hist_global ? gws : base + loc;
         FitVecs V = carve_fit_vecs(base, hbase, P, F.hist);
-        const EvalWs ws = carve_eval_ws(base + fit_work_floats(P), m.N_t, m.C, m.max_reco);
+        const EvalWs ws = carve_eval_ws(base + fit_work_floats(P), m.N_t, m.C, m.max_reco, m.n_osc);
         const float *data = A.data + in.data_off;
         if (tid == 0) init_state(S.st);
         __syncthreads();
@@ -871,12 +877,13 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
         } else {
             start_z(m, A.start ? A.start + in.param_off : nullptr, V.zt, V.pd);
             while (true) {
-                const double fa = eval_z(m, V.zt, V.gt, V, ws, data, in.mask, S,
+                const double fa = eval_z<NOSC>(m, V.zt, V.gt, V, ws, data, in.mask, S,
                                          A.fixed ? A.fixed + in.param_off : nullptr);
                 if (!fit_decide(S, V, P, fa, F)) break;
             }
         }
-        write_result(m, S.st, V.z, A.best + in.param_off, A.results + ii);
+        write_result(m, S.st, V.z, A.best + in.param_off, A.results + ii,
+                     A.start ? A.start + in.param_off : nullptr, A.fixed ? A.fixed + in.param_off : nullptr);
         __syncthreads();
     }
 }
@@ -952,7 +959,8 @@ __global__ void __launch_bounds__(128) ls_init_kernel(LsArgs A) {
 // Forward pass and likelihood of one (instance, dataset) per block iteration: stages A (no
 // partials), B, C, C2; stores the dataset's -2lnL, dD/dmu and the efficiency / background
 // gradient contributions.
-__global__ void __launch_bounds__(128) ls_forward_kernel(LsArgs A) {
+template <int NOSC>
+__device__ __forceinline__ void ls_forward_body(LsArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LsEvalSmem &S = *reinterpret_cast<LsEvalSmem *>(smem_raw);
     copy_model(&S.m, A.model);
@@ -982,7 +990,7 @@ __global__ void __launch_bounds__(128) ls_forward_kernel(LsArgs A) {
         }
         if (threadIdx.x == 0) S.status = 0;
         __syncthreads();
-        DsCtx c;
+        DsCtxT<NOSC> c;
         double nll = 0.0;
         if (ds_setup(m, d, pv, pd, c, &S.status)) {
             ds_signal<false>(m, d, pv, pd, c, ws);
@@ -1002,9 +1010,13 @@ __global__ void __launch_bounds__(128) ls_forward_kernel(LsArgs A) {
     }
 }
 
+__global__ void __launch_bounds__(128) ls_forward_kernel(LsArgs A) { ls_forward_body<4>(A); }
+__global__ void __launch_bounds__(128) ls_forward_kernel6(LsArgs A) { ls_forward_body<6>(A); }
+
 // Adjoint of one (instance, dataset) per block iteration: stage A again with the partials,
 // then stages D, E, F into the dataset's gradient slice.
-__global__ void __launch_bounds__(128) ls_adjoint_kernel(LsArgs A) {
+template <int NOSC>
+__device__ __forceinline__ void ls_adjoint_body(LsArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LsEvalSmem &S = *reinterpret_cast<LsEvalSmem *>(smem_raw);
     copy_model(&S.m, A.model);
@@ -1013,7 +1025,7 @@ __global__ void __launch_bounds__(128) ls_adjoint_kernel(LsArgs A) {
     float *pv = reinterpret_cast<float *>(smem_raw + sizeof(LsEvalSmem));
     float *pd = pv + P;
     float *wsb = A.ws_in_smem ? pd + P : A.ws_global + (int64_t)blockIdx.x * A.ws_stride;
-    const EvalWs ws = carve_eval_ws(wsb, m.N_t, m.C, m.max_reco);
+    const EvalWs ws = carve_eval_ws(wsb, m.N_t, m.C, m.max_reco, m.n_osc);
     for (int it = blockIdx.x; it < na * nd; it += gridDim.x) {
         const int g = A.act[it / nd], d = it % nd;
         const fit_instance in = A.inst[A.group[g]];
@@ -1029,7 +1041,7 @@ __global__ void __launch_bounds__(128) ls_adjoint_kernel(LsArgs A) {
         for (int j = threadIdx.x; j < nr; j += blockDim.x) ws.gmu[j] = gm[j];
         if (threadIdx.x == 0) S.status = 0;
         __syncthreads();
-        DsCtx c;
+        DsCtxT<NOSC> c;
         if (ds_setup(m, d, pv, pd, c, &S.status)) {
             ds_signal<true>(m, d, pv, pd, c, ws);
             ds_adjoint(m, d, pv, pd, c, ws, A.gsl + gd * P, S.red);
@@ -1037,6 +1049,9 @@ __global__ void __launch_bounds__(128) ls_adjoint_kernel(LsArgs A) {
         __syncthreads();
     }
 }
+
+__global__ void __launch_bounds__(128) ls_adjoint_kernel(LsArgs A) { ls_adjoint_body<4>(A); }
+__global__ void __launch_bounds__(128) ls_adjoint_kernel6(LsArgs A) { ls_adjoint_body<6>(A); }
 
 // Minimiser step per active instance: gathers the round's evaluation (dataset sums, prior,
 // gradient in z), runs fit_decide, and either prepares theta of the next trial point and puts
@@ -1083,7 +1098,9 @@ __global__ void __launch_bounds__(128) ls_step_kernel(LsArgs A) {
                 A.act_next[atomicAdd(A.n_act_next, 1)] = g;
             }
         } else {
-            write_result(m, S.st, V.z, A.best + in.param_off, A.results + ii);
+            write_result(m, S.st, V.z, A.best + in.param_off, A.results + ii,
+                         A.start ? A.start + in.param_off : nullptr,
+                         A.fixed ? A.fixed + in.param_off : nullptr);
         }
         __syncthreads();
         copy_state(A.state + g, &S.st);
@@ -1091,9 +1108,12 @@ __global__ void __launch_bounds__(128) ls_step_kernel(LsArgs A) {
     }
 }
 
-const void *fit_kernel_func(int variant) {
-    return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5>)
-                        : reinterpret_cast<const void *>(&fit_kernel<4>);
+const void *fit_kernel_func(int variant, int n_osc) {
+    if (n_osc == 6)
+        return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5, 6>)
+                            : reinterpret_cast<const void *>(&fit_kernel<4, 6>);
+    return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5, 4>)
+                        : reinterpret_cast<const void *>(&fit_kernel<4, 4>);
 }
 
 size_t fit_smem_bytes(int floats) { return sizeof(FitSmem) + sizeof(float) * (size_t)floats; }

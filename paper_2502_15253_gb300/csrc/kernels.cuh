@@ -68,13 +68,15 @@ struct LsArgs {
 __global__ void ls_init_kernel(LsArgs A);
 __global__ void ls_forward_kernel(LsArgs A);
 __global__ void ls_adjoint_kernel(LsArgs A);
+__global__ void ls_forward_kernel6(LsArgs A);   // models with the 3+1 formula
+__global__ void ls_adjoint_kernel6(LsArgs A);
 __global__ void ls_step_kernel(LsArgs A);
 size_t ls_state_bytes();
 size_t ls_step_smem_bytes();
 size_t ls_eval_smem_bytes(int P, int ws_floats);
 
 // the persistent fit kernel compiled for 4 or 5 resident blocks per SM (host entry address)
-const void *fit_kernel_func(int variant);
+const void *fit_kernel_func(int variant, int n_osc);
 
 size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem);
 

@@ -22,7 +22,7 @@ from paper_2502_15253_gb300 import fitcore, synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=["c0", "c1", "c2"])
+@pytest.fixture(scope="module", params=["c0", "c1", "c2", "c1s"])
 def pair(request):
     spec = synth.make_model(request.param)
     return spec, oracle.OracleModel(spec), fitcore.Model(spec)
