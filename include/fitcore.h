@@ -61,6 +61,11 @@ extern "C" {
 #define FIT_STATUS_MU_NONPOSITIVE 4     /* an expected count <= 0 on a used bin (nll = +inf)  */
 #define FIT_STATUS_ESCALE_NONMONOTONE 5 /* dE'/dE outside (0.25, 4) on the grid (nll = +inf)  */
 #define FIT_STATUS_TIMEOUT 6            /* the fit exceeded its clock budget                  */
+#define FIT_STATUS_STALLED 7            /* 100 iterations lowered -2lnL by less than twice the
+                                         * FP32 noise allowance (f_noise_rel (1 + |f|)): the
+                                         * point is that close in value to a minimum, but EDM
+                                         * stayed above edm_tol (e.g. on a crease of the
+                                         * overlap-length energy correction)                  */
 
 /* Survival-probability forms */
 #define FIT_OSC_EQ1 0     /* eta = (sin^2 2th13, dm2_ee, sin^2 2th12, dm2_21)       Eq. 1, 2 */

@@ -149,6 +149,7 @@ size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem) {
 // persistent batched L-BFGS
 // ------------------------------------------------------------------------------------
 constexpr int kMaxHist = 32;
+constexpr int kStallWindow = 100;   // iterations per stall check
 constexpr int kNDots = 4 * kMaxHist + 1;
 
 // Minimiser state of one fit between two evaluations: in shared memory while a block works on
@@ -167,7 +168,8 @@ struct FitState {
     int hn, head, occ;
     int phase, ls_it, have_lo, pending, restarts_left, since_restart;
     int iters, n_evals, status;
-    int pad;
+    int win_it;     // stall window: iteration and value at its start
+    double f_win;
 };
 
 struct alignas(16) FitSmem {
@@ -552,6 +554,7 @@ __device__ bool fit_decide(FitSmem &S, FitVecs &V, int P, double fa, const FitPa
     __syncthreads();
 
     enum { kDirection, kTrial, kDone } next = kDirection;
+    bool stall_mark = false;   // a stall window ended in this pass
     if (phase == kPhStart) {
         // the start point's evaluation
         f = fa;
@@ -561,6 +564,10 @@ __device__ bool fit_decide(FitSmem &S, FitVecs &V, int P, double fa, const FitPa
         restarts_left = F.restarts;
         since_restart = F.hist;
         pending = false;
+        if (tid == 0) {
+            st.f_win = f;
+            st.win_it = 0;
+        }
         if (!isfinite(f)) {
             status = FIT_STATUS_NONFINITE;
             next = kDone;
@@ -632,6 +639,18 @@ __device__ bool fit_decide(FitSmem &S, FitVecs &V, int P, double fa, const FitPa
                 f = f_acc;
                 iters++;
                 since_restart++;
+                // stall: a whole window of iterations that lowered the value by no more than
+                // the FP32 noise allowance (the line search then only trades noise, e.g. on a
+                // crease of the energy correction)
+                // (the window's start lives in shared memory only: read here, written by thread 0
+                // after the barrier at the end of this pass)
+                if (iters - st.win_it >= kStallWindow) {
+                    if (st.f_win - f <= 2.0 * F.f_noise_rel * (1.0 + fabs(f))) {
+                        status = FIT_STATUS_STALLED;
+                        next = kDone;
+                    }
+                    stall_mark = true;
+                }
             } else if (st.hn > 0) {   // retry from steepest descent
                 __syncthreads();
                 if (tid == 0) reset_history(st);
@@ -747,6 +766,10 @@ __device__ bool fit_decide(FitSmem &S, FitVecs &V, int P, double fa, const FitPa
         st.iters = iters;
         st.n_evals = n_evals;
         st.status = status;
+        if (stall_mark) {
+            st.f_win = f;
+            st.win_it = iters;
+        }
     }
     __syncthreads();
     return next == kTrial;
@@ -758,6 +781,8 @@ __device__ __forceinline__ void init_state(FitState &st) {
     st.edm = INFINITY;
     st.iters = 0;
     st.n_evals = 0;
+    st.win_it = 0;
+    st.f_win = INFINITY;
     st.status = FIT_STATUS_MAXITER;
     st.pending = 0;
     st.have_lo = 0;

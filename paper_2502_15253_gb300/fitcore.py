@@ -87,7 +87,7 @@ class fit_warmstart_geom(C.Structure):
 
 
 STATUS = {0: "converged", 1: "maxiter", 2: "linesearch_fail", 3: "nonfinite",
-          4: "mu_nonpositive", 5: "escale_nonmonotone", 6: "timeout"}
+          4: "mu_nonpositive", 5: "escale_nonmonotone", 6: "timeout", 7: "stalled"}
 
 EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model_expected",
            "fit_model_eval", "fit_model_eval_noalloc", "fit_batch_default_opts", "fit_batch",
