@@ -70,6 +70,7 @@ typedef struct {
     const double *bkg_template;   /* concatenated, N_r of its dataset each */
     const int *bkg_rate_idx;
     const int *bkg_shape_idx;     /* concatenated, N_r each */
+    int remap_mode;               /* 0: overlap length ; 1: area-conserving spline */
 } orc_model;
 
 typedef struct {
@@ -301,10 +302,13 @@ static void target_window(const orc_model *m, double y0, double y1, int *mlo, in
     *mhi = hi > m->n_true - 1 ? m->n_true - 1 : hi;
 }
 
+static int remap_spline(const orc_model *m, const double *a, const double *u, double *v);
+
 /* v = M(a) u. Returns 0, or 1 if E' is not increasing on the grid (v untouched). */
 int orc_remap(const orc_model *m, const double *a, const double *u, double *v)
 {
     if (!remap_monotone(m, a)) return 1;
+    if (m->remap_mode == 1) return remap_spline(m, a, u, v);
     double de = (m->e_hi - m->e_lo) / m->n_true;
     for (int i = 0; i < m->n_true; ++i) v[i] = 0.0;
     for (int k = 0; k < m->n_true; ++k) {
@@ -319,6 +323,118 @@ int orc_remap(const orc_model *m, const double *a, const double *u, double *v)
         }
     }
     return 0;
+}
+
+/* ---- area-conserving spline remap ----------------------------------------------------
+ * The energy correction of the paper's signal chain taken literally: the bin contents u on
+ * the uniform true grid define the cumulative C(e_k) = sum_{i<k} u_i at the edges; an area-
+ * conserving spline F interpolates C with continuous first derivative (the density f = F'),
+ * F is energy-corrected (E' = a0 + a1 E + a2 E^2) and integrated over the original binning:
+ *   v_j = F(x_{j+1}) - F(x_j),  x_j = E'^{-1}(e_j)  (content mapped off the grid is dropped).
+ * Spline (reading; the paper names only "area conserving spline"): on bin k the cubic Hermite
+ * interpolant of C with end slopes f(e_k) = (rho_{k-1} + rho_k) / 2, rho = u / de (one-sided
+ * at the grid ends): F(e_k + t de) = C(e_k) + u_k h01(t) + de f(e_k) h10(t) + de f(e_{k+1}) h11(t)
+ * with the Hermite basis h01 = 3t^2 - 2t^3, h10 = t^3 - 2t^2 + t, h11 = t^3 - t^2. F matches C
+ * at every edge (each bin keeps its content) and f is continuous, so v is continuously
+ * differentiable in (a0, a1, a2) (the overlap rule is not). */
+static double edge_slope(const orc_model *m, const double *u, int k, double de)
+{
+    int n = m->n_true;
+    if (k <= 0) return u[0] / de;
+    if (k >= n) return u[n - 1] / de;
+    return 0.5 * (u[k - 1] + u[k]) / de;
+}
+
+/* F(x) and f(x) = F'(x); cum[k] = sum_{i<k} u_i */
+static double spline_F(const orc_model *m, const double *u, const double *cum, double x, double *f)
+{
+    double de = (m->e_hi - m->e_lo) / m->n_true;
+    double y = (x - m->e_lo) / de;
+    if (y <= 0.0) { if (f) *f = 0.0; return 0.0; }
+    if (y >= m->n_true) { if (f) *f = 0.0; return cum[m->n_true]; }
+    int k = (int)floor(y);
+    if (k > m->n_true - 1) k = m->n_true - 1;
+    double t = y - k, t2 = t * t, t3 = t2 * t;
+    double s0 = edge_slope(m, u, k, de) * de, s1 = edge_slope(m, u, k + 1, de) * de;
+    double F = cum[k] + u[k] * (3.0 * t2 - 2.0 * t3) + s0 * (t3 - 2.0 * t2 + t) + s1 * (t3 - t2);
+    if (f) *f = (u[k] * (6.0 * t - 6.0 * t2) + s0 * (3.0 * t2 - 4.0 * t + 1.0) + s1 * (3.0 * t2 - 2.0 * t)) / de;
+    return F;
+}
+
+/* x with a0 + a1 x + a2 x^2 = e on the increasing branch */
+static double qmap_inv(const double *a, double e)
+{
+    double r = e - a[0];
+    return 2.0 * r / (a[1] + sqrt(a[1] * a[1] + 4.0 * a[2] * r));
+}
+
+static int remap_spline(const orc_model *m, const double *a, const double *u, double *v)
+{
+    int n = m->n_true;
+    double de = (m->e_hi - m->e_lo) / n;
+    double *cum = (double *)malloc(sizeof(double) * (n + 1));
+    cum[0] = 0.0;
+    for (int k = 0; k < n; ++k) cum[k + 1] = cum[k] + u[k];
+    double Fprev = spline_F(m, u, cum, qmap_inv(a, m->e_lo), NULL);
+    for (int j = 0; j < n; ++j) {
+        double F1 = spline_F(m, u, cum, qmap_inv(a, m->e_lo + (j + 1) * de), NULL);
+        v[j] = F1 - Fprev;
+        Fprev = F1;
+    }
+    free(cum);
+    return 0;
+}
+
+/* Adjoint of the spline remap: gu = M^T gv and ga += dv/da^T gv.
+ * dF(x)/du_i: 1 for i < k (the cumulative), the Hermite weights of u_k and of the two edge
+ * slopes for i = k - 1, k, k + 1; 1 for every i when x is past the grid, 0 below it.
+ * dx/da_i = -x^i / (a1 + 2 a2 x). */
+static void remap_spline_adjoint(const orc_model *m, const double *a, const double *u, const double *gv,
+                                 double *gu, double *ga)
+{
+    int n = m->n_true;
+    double de = (m->e_hi - m->e_lo) / n;
+    double *cum = (double *)malloc(sizeof(double) * (n + 1));
+    double *w = (double *)malloc(sizeof(double) * (n + 1));   /* d(-2lnL)/dF at each edge */
+    double *below = (double *)calloc(n + 1, sizeof(double));  /* below[k]: added to gu[i], i < k */
+    cum[0] = 0.0;
+    for (int k = 0; k < n; ++k) cum[k + 1] = cum[k] + u[k];
+    for (int k = 0; k < n; ++k) gu[k] = 0.0;
+    for (int e = 0; e <= n; ++e) w[e] = (e > 0 ? gv[e - 1] : 0.0) - (e < n ? gv[e] : 0.0);
+    for (int e = 0; e <= n; ++e) {
+        double x = qmap_inv(a, m->e_lo + e * de), f;
+        spline_F(m, u, cum, x, &f);
+        double dxd = -1.0 / (a[1] + 2.0 * a[2] * x);
+        ga[0] += w[e] * f * dxd;
+        ga[1] += w[e] * f * dxd * x;
+        ga[2] += w[e] * f * dxd * x * x;
+        double y = (x - m->e_lo) / de;
+        if (y <= 0.0) continue;
+        if (y >= n) {
+            below[n] += w[e];
+            continue;
+        }
+        int k = (int)floor(y);
+        if (k > n - 1) k = n - 1;
+        double t = y - k, t2 = t * t, t3 = t2 * t;
+        double h01 = 3.0 * t2 - 2.0 * t3, h10 = t3 - 2.0 * t2 + t, h11 = t3 - t2;
+        below[k] += w[e];
+        gu[k] += w[e] * h01;
+        /* de * f(e_k) = (u_{k-1} + u_k) / 2, or u_0 at the lower end */
+        if (k == 0) gu[0] += w[e] * h10;
+        else { gu[k - 1] += w[e] * 0.5 * h10; gu[k] += w[e] * 0.5 * h10; }
+        /* de * f(e_{k+1}) = (u_k + u_{k+1}) / 2, or u_{n-1} at the upper end */
+        if (k + 1 >= n) gu[n - 1] += w[e] * h11;
+        else { gu[k] += w[e] * 0.5 * h11; gu[k + 1] += w[e] * 0.5 * h11; }
+    }
+    double acc = 0.0;
+    for (int i = n - 1; i >= 0; --i) {
+        acc += below[i + 1];
+        gu[i] += acc;
+    }
+    free(cum);
+    free(w);
+    free(below);
 }
 
 /* Adjoint of the remap: given gv = d(-2lnL)/dv, accumulate gu = M^T gv and
@@ -536,7 +652,10 @@ double orc_nll(const orc_handle *h, const double *theta, const double *data, uin
         /* energy correction */
         double a[3], ga[3] = {0.0, 0.0, 0.0};
         escale_of(m, theta, d, a);
-        remap_adjoint(m, a, u, gv, gu, ga);
+        if (m->remap_mode == 1)
+            remap_spline_adjoint(m, a, u, gv, gu, ga);
+        else
+            remap_adjoint(m, a, u, gv, gu, ga);
         for (int i = 0; i < 3; ++i)
             if (m->ds_escale_idx[3 * d + i] >= 0) grad[m->ds_escale_idx[3 * d + i]] += ga[i];
         /* signal: u_k = t_k n s_k sum_c p_c w_c P(L_c, E_k) */

@@ -107,6 +107,7 @@ class ModelSpec:
     e_hi: float
     detectors: list
     datasets: list
+    remap: int = 0                # energy correction: 0 overlap length, 1 area-conserving spline
 
     @property
     def n_params(self) -> int:
@@ -425,7 +426,12 @@ def make_c2(seed=BASE_SEED):
                      datasets)
 
 
-def make_model(name: str, seed: int = BASE_SEED) -> ModelSpec:
+def make_model(name: str, seed: int = BASE_SEED, remap: int = 0) -> ModelSpec:
+    """The named model; remap=1 selects the area-conserving spline energy correction."""
+    if remap:
+        spec = make_model(name, seed)
+        spec.remap = int(remap)
+        return spec
     if name == "c0":
         return make_c0(seed)
     if name == "c0_tiny":

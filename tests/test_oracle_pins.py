@@ -206,6 +206,74 @@ def test_remap_whole_bin_shift(c0):
         np.testing.assert_allclose(v, ref, rtol=1e-9, atol=1e-9)
 
 
+# area-conserving spline remap ---------------------------------------------------------
+@pytest.fixture(scope="module")
+def c0s():
+    spec = synth.make_model("c0", remap=1)
+    return spec, oracle.OracleModel(spec)
+
+
+def _spline_reference(spec, a, u):
+    """The same definition through a library interpolant: scipy's cubic Hermite spline of the
+    cumulative content at the edges with the averaged-density edge slopes, differenced at the
+    inverse-mapped edges (roots of the quadratic by numpy)."""
+    from scipy.interpolate import CubicHermiteSpline
+    n = spec.n_true
+    edges = np.linspace(spec.e_lo, spec.e_hi, n + 1)
+    de = edges[1] - edges[0]
+    rho = u / de
+    slope = np.concatenate([[rho[0]], 0.5 * (rho[:-1] + rho[1:]), [rho[-1]]])
+    F = CubicHermiteSpline(edges, np.concatenate([[0.0], np.cumsum(u)]), slope)
+    x = np.array([max(np.roots([a[2], a[1], a[0] - e]).real, key=lambda r: -abs(r - e))
+                  if a[2] != 0 else (e - a[0]) / a[1] for e in edges])
+    Fx = np.where(x <= edges[0], 0.0, np.where(x >= edges[-1], u.sum(), F(np.clip(x, edges[0], edges[-1]))))
+    return np.diff(Fx)
+
+
+def test_spline_remap_identity_and_whole_bin_shift(c0s):
+    spec, om = c0s
+    de = (spec.e_hi - spec.e_lo) / spec.n_true
+    u = np.random.default_rng(5).uniform(0, 10, spec.n_true)
+    np.testing.assert_allclose(om.remap([0.0, 1.0, 0.0], u), u, rtol=1e-12, atol=1e-12)
+    for m in (1, 3, -2):
+        ref = np.zeros_like(u)
+        if m > 0:
+            ref[m:] = u[:-m]
+        else:
+            ref[:m] = u[-m:]
+        np.testing.assert_allclose(om.remap([m * de, 1.0, 0.0], u), ref, rtol=1e-10, atol=1e-10)
+
+
+def test_spline_remap_matches_library_hermite_spline(c0s):
+    spec, om = c0s
+    u = np.random.default_rng(6).uniform(1, 5, spec.n_true)
+    for a in ([0.02, 1.003, -0.0005], [-0.03, 0.99, 0.001], [0.013, 1.0, 0.0], [0.0, 1.02, 0.0]):
+        np.testing.assert_allclose(om.remap(a, u), _spline_reference(spec, a, u), rtol=1e-10,
+                                   atol=1e-10 * u.sum())
+
+
+def test_spline_remap_is_smooth_where_the_overlap_rule_kinks(c0, c0s):
+    """At a0 = one or two bins every mapped edge sits on a grid edge: there the overlap rule's
+    derivative jumps, the spline's left and right derivatives agree. (Content that starts
+    abruptly at a grid end would still kink the spline where a mapped edge crosses that end;
+    the spectra, like the model's, go to zero there.)"""
+    (spec, om), (_, oms) = c0, c0s
+    de = (spec.e_hi - spec.e_lo) / spec.n_true
+    u = np.zeros(spec.n_true)
+    u[10:-10] = np.random.default_rng(7).uniform(1, 5, spec.n_true - 20)
+    gv = np.random.default_rng(8).standard_normal(spec.n_true)
+    h = 1e-6 * de
+    for a0 in (de, 2 * de):
+        def phi(m, x):
+            return m.remap([x, 1.0, 0.0], u) @ gv
+        right_s = (phi(oms, a0 + h) - phi(oms, a0)) / h
+        left_s = (phi(oms, a0) - phi(oms, a0 - h)) / h
+        right_o = (phi(om, a0 + h) - phi(om, a0)) / h
+        left_o = (phi(om, a0) - phi(om, a0 - h)) / h
+        assert abs(right_s - left_s) <= 1e-4 * max(abs(right_s), 1.0)
+        assert abs(right_o - left_o) > 1e-2 * max(abs(right_o), 1.0)
+
+
 def test_remap_conserves_content_inside_grid(c0):
     spec, om = c0
     u = np.zeros(spec.n_true)
@@ -337,9 +405,9 @@ def test_expected_backgrounds_and_efficiency_c1():
 # ---------------------------------------------------------------------------------------
 # -2lnL and gradient
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s"])
+@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s", "c0/spline", "c1/spline"])
 def test_asimov_nll_is_zero(name):
-    spec = synth.make_model(name)
+    spec = synth.make_model(name.split("/")[0], remap=int(name.endswith("spline")))
     om = oracle.OracleModel(spec)
     v, g = om.nll(spec.theta0, om.expected(spec.theta0), grad=True)
     assert abs(v) < 1e-9
@@ -363,9 +431,9 @@ def test_poisson_part_equals_library_pmf_sum():
     assert om.nll(theta, data, mask=m) == pytest.approx(ref_m, rel=1e-10)
 
 
-@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s"])
+@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s", "c0/spline", "c1/spline", "c2/spline"])
 def test_gradient_matches_central_differences(name):
-    spec = synth.make_model(name)
+    spec = synth.make_model(name.split("/")[0], remap=int(name.endswith("spline")))
     om = oracle.OracleModel(spec)
     rng = np.random.default_rng(9)
     data = synth.poisson_data(om.expected(spec.theta0), 12)
