@@ -75,6 +75,12 @@ extern "C" {
  * eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31, sin^2 2th14, dm2_41) */
 #define FIT_OSC_STERILE4 2
 
+/* Energy correction (Eq. 7 chain, "Neutrino signal"): how the corrected spectrum is integrated
+ * over the original binning */
+#define FIT_REMAP_OVERLAP 0 /* each true bin's content spread uniformly over its mapped interval */
+#define FIT_REMAP_SPLINE 1  /* area-conserving spline: C1 cubic Hermite interpolant of the
+                             * cumulative content, slopes (rho_{k-1} + rho_k) / 2 at the edges */
+
 /* Size limits of one model */
 #define FIT_MAX_DATASETS 8
 #define FIT_MAX_DETECTORS 4
@@ -123,6 +129,7 @@ typedef struct fit_model_desc {
     const double *bkg_template;  /* concatenated [N_r of its dataset] expected counts         */
     const int *bkg_rate_idx;     /* [n_bkg] rate parameter                                    */
     const int *bkg_shape_idx;    /* concatenated [N_r] shape-delta parameter per reco bin     */
+    int remap_mode;              /* FIT_REMAP_OVERLAP or FIT_REMAP_SPLINE                      */
 } fit_model_desc;
 
 typedef struct fit_model fit_model; /* opaque, device-resident constants */

@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(256) signal_v_kernel(const DevModel *__restric
     __syncthreads();
     for (int t = tid; t < m.ldt; t += nth) {
         float acc = 0.f;
-        if (t < N_t) {
+        if (t < N_t && m.remap_mode == FIT_REMAP_SPLINE) {
+            acc = spline_target(u, m.e_edge, em, t, N_t);
+        } else if (t < N_t) {
             int k = t - (int)floorf(em.disp(m.e_edge[t]));
             k = min(max(k, 0), N_t - 1);
             k = t - (int)floorf(em.disp(m.e_edge[k]));

@@ -225,6 +225,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
     if (d->osc_mode != FIT_OSC_EQ1 && d->osc_mode != FIT_OSC_VACUUM3 && d->osc_mode != FIT_OSC_STERILE4)
         return bad("osc_mode");
     const int n_osc = d->osc_mode == FIT_OSC_STERILE4 ? 6 : 4;
+    if (d->remap_mode != FIT_REMAP_OVERLAP && d->remap_mode != FIT_REMAP_SPLINE) return bad("remap_mode");
     if (!(d->e_lo > 0.0 && d->e_hi > d->e_lo)) return bad("energy grid");
     if (!d->theta0 || !d->prior_sigma || !d->scale || !d->core_power_idx || !d->det_n_reco ||
         !d->det_response || !d->ds_det || !d->ds_t || !d->ds_baseline || !d->ds_weight ||
@@ -257,6 +258,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
     h.de = (float)de;
     h.inv_de = (float)(1.0 / de);
     h.n_osc = n_osc;
+    h.remap_mode = d->remap_mode;
     for (int i = 0; i < fitcore::kMaxOsc; ++i) {
         const double v = i < n_osc ? d->osc_val[i] : 0.0;
         h.osc_idx[i] = i < n_osc ? d->osc_idx[i] : -1;
@@ -1080,7 +1082,8 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
         A.ws_in_smem = eval_smem <= 48 * 1024 ? 1 : 0;
         const size_t esm = A.ws_in_smem ? eval_smem : fitcore::ls_eval_smem_bytes(P, 0);
         const size_t ssm = fitcore::ls_step_smem_bytes();
-        const bool six = h.n_osc == 6;   // the 3+1 builds of the evaluation kernels
+        // the general builds of the evaluation kernels (3+1 formula, spline correction)
+        const bool six = h.n_osc == 6 || h.remap_mode == FIT_REMAP_SPLINE;
         const void *kf = six ? (const void *)fitcore::ls_forward_kernel6 : (const void *)fitcore::ls_forward_kernel;
         const void *ka = six ? (const void *)fitcore::ls_adjoint_kernel6 : (const void *)fitcore::ls_adjoint_kernel;
         int per_sm_f = 0, per_sm_a = 0, per_sm_s = 0;
@@ -1266,10 +1269,10 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
                                                  o, s, data_len, par_len);
     if (o.engine != 0) return fail(FIT_ERR_INVALID_ARG, "fit_batch: engine must be 0 or 1");
     int max_loc = 0;   // working vectors + evaluation workspace, without the history
-    int n_osc = 4;     // the 3+1 build of the kernel when any model uses that formula
+    int n_osc = 4;     // the general build when any model uses the 3+1 formula or the spline
     for (int mi = 0; mi < n_models; ++mi) {
         const DevModel &h = models[mi]->host;
-        n_osc = std::max(n_osc, h.n_osc);
+        n_osc = std::max(n_osc, h.remap_mode == FIT_REMAP_SPLINE ? 6 : h.n_osc);
         // (multiples of 4 floats: the fit vectors start on 16-byte boundaries)
         const int ws4 = (h.ws_eval_floats + 3) & ~3;
         max_need = std::max(max_need, fitcore::fit_vec_floats(h.P, o.history) + ws4);

@@ -56,6 +56,7 @@ struct DevModel {
     int P, N_t, C, n_ds, n_data, osc_mode, n_blocks, n_bkg;
     float e_lo, de, inv_de;
     int n_osc;               // survival parameters of osc_mode: 4, or 6 (FIT_OSC_STERILE4)
+    int remap_mode;          // FIT_REMAP_OVERLAP or FIT_REMAP_SPLINE
     int osc_idx[kMaxOsc];
     float osc_val[kMaxOsc];
     float osc_val_lo[kMaxOsc];   // low parts of the constant survival parameters
@@ -475,6 +476,140 @@ struct EMap {
     __device__ __forceinline__ float slope(float e) const { return 1.f + a1m1 + 2.f * a2 * e; }
 };
 
+// ---- area-conserving spline remap --------------------------------------------------------
+// The grid's cumulative content C(e_k) is interpolated on each bin by the cubic Hermite
+// polynomial with end slopes de f(e_k) = S_k = (u_{k-1} + u_k) / 2 (u_0, u_{N-1} at the ends):
+//   F(e_k + t de) = C(e_k) + G_k(t),  G_k(t) = u_k h01(t) + S_k h10(t) + S_{k+1} h11(t),
+// which keeps every bin's content and has a continuous density. The corrected spectrum is
+// v_j = F(x_{j+1}) - F(x_j), x_j = E'^{-1}(e_j), evaluated locally as
+//   v_j = sum_{k0 <= k < k1} u_k + G_{k1}(t1) - G_{k0}(t0)
+// with each x on the grid as e + r (exact integer edge index + small FP32 offset r).
+__device__ __forceinline__ float hermite_S(const float *u, int k, int N) {
+    return k <= 0 ? u[0] : (k >= N ? u[N - 1] : 0.5f * (u[k - 1] + u[k]));
+}
+
+__device__ __forceinline__ float hermite_G(const float *u, int k, float t, int N) {
+    const float t2 = t * t, t3 = t2 * t;
+    const float h01 = fmaf(-2.f, t3, 3.f * t2), h10 = t3 - 2.f * t2 + t, h11 = t3 - t2;
+    return fmaf(u[k], h01, fmaf(hermite_S(u, k, N), h10, hermite_S(u, k + 1, N) * h11));
+}
+
+// r with E'(e_e + r de) = e_e (two Newton steps from -D(e_e); |r| is a few bins at most)
+template <class Map>
+__device__ __forceinline__ float edge_inv_r(const float *e_edge, const Map &em, int e) {
+    const float xe = e_edge[e];
+    float r = -em.disp(xe);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float x = fmaf(r, em.de, xe);
+        r -= (r + em.disp(x)) / em.slope(x);
+    }
+    return r;
+}
+
+// bin k and fraction t of the grid position e + r, clamped to the grid: below it (0, 0)
+// (F = 0), above it (N - 1, 1) (F = total); `inside` tells whether it was on the grid
+__device__ __forceinline__ void edge_bin(int e, float r, int N, int &k, float &t, bool &inside) {
+    const float fl = floorf(r);
+    k = e + (int)fl;
+    t = r - fl;
+    inside = true;
+    if (k < 0) {
+        k = 0;
+        t = 0.f;
+        inside = false;
+    } else if (k >= N) {
+        k = N - 1;
+        t = 1.f;
+        inside = false;
+    }
+}
+
+// v_j for target bin j
+template <class Map>
+__device__ __forceinline__ float spline_target(const float *u, const float *e_edge, const Map &em, int j, int N) {
+    int k0, k1;
+    float t0, t1;
+    bool in0, in1;
+    edge_bin(j, edge_inv_r(e_edge, em, j), N, k0, t0, in0);
+    edge_bin(j + 1, edge_inv_r(e_edge, em, j + 1), N, k1, t1, in1);
+    float acc = 0.f;
+    for (int k = k0, it = 0; k < k1 && it < 64; ++k, ++it) acc += u[k];
+    return acc + (hermite_G(u, k1, t1, N) - hermite_G(u, k0, t0, N));
+}
+
+// Adjoint of the spline remap for source bin i: d(-2lnL)/du_i. With w_e = gv_{e-1} - gv_e the
+// weight of F(x_e) (gv outside the grid 0), dF(x_e)/du_i is 1 for i < k_e (the cumulative)
+// plus the Hermite weights of u_i in G_{k_e}; the cumulative part sums to gv_{e*-1}, e* the
+// first edge with k_e > i.
+template <class Map>
+__device__ __forceinline__ float spline_adjoint_source(const float *u, const float *gv, const float *e_edge,
+                                                       const Map &em, int i, int N) {
+    (void)u;
+    auto kb = [&](int e, int &k, float &t) {
+        bool in;
+        edge_bin(e, edge_inv_r(e_edge, em, e), N, k, t, in);
+    };
+    // e*: start from the inverse shift at edge i and walk to the first edge with k_e > i
+    int e = min(max(i + 1 - (int)floorf(edge_inv_r(e_edge, em, i)), 0), N + 1);
+    int k;
+    float t;
+    for (int it = 0; it < 64 && e > 0; ++it) {   // step down while the edge before is past i
+        kb(e - 1, k, t);
+        if (k <= i) break;
+        --e;
+    }
+    for (int it = 0; it < 64 && e <= N; ++it) {  // step up while this edge is not past i
+        kb(e, k, t);
+        if (k > i) break;
+        ++e;
+    }
+    float g = (e >= 1 && e <= N) ? gv[e - 1] : 0.f;
+    // local Hermite weights: edges with k_e in [i - 1, i + 1] lie around e*
+    auto local = [&](int ee) -> bool {
+        int kk;
+        float tt;
+        kb(ee, kk, tt);
+        if (kk < i - 1 || kk > i + 1) return false;
+        const float we = (ee >= 1 ? gv[ee - 1] : 0.f) - (ee <= N - 1 ? gv[ee] : 0.f);
+        const float t2 = tt * tt, t3 = t2 * tt;
+        const float h01 = fmaf(-2.f, t3, 3.f * t2), h10 = t3 - 2.f * t2 + tt, h11 = t3 - t2;
+        float c = 0.f;
+        if (kk == i) c = h01 + (kk == 0 ? h10 : 0.5f * h10) + (kk == N - 1 ? h11 : 0.5f * h11);
+        else if (kk == i + 1) c = 0.5f * h10;   // S_{i+1} = (u_i + u_{i+1}) / 2
+        else c = 0.5f * h11;                    // kk == i - 1: S_i = (u_{i-1} + u_i) / 2
+        g = fmaf(we, c, g);
+        return true;
+    };
+    for (int ee = e - 1, it = 0; ee >= 0 && it < 64; --ee, ++it)
+        if (!local(ee)) break;
+    for (int ee = e, it = 0; ee <= N && it < 64; ++ee, ++it)
+        if (!local(ee)) break;
+    return g;
+}
+
+// Edge e's share of d(-2lnL)/d(a0, a1, a2): w_e f(x_e) dx_e/da_i, dx/da_i = -x^i / E''(x)
+// (f the spline's density per MeV, 0 off the grid); added to ep[0..2].
+template <class Map>
+__device__ __forceinline__ void spline_adjoint_edge(const float *u, const float *gv, const float *e_edge,
+                                                    const Map &em, int e, int N, float *ep) {
+    const float r = edge_inv_r(e_edge, em, e);
+    int k;
+    float t;
+    bool in;
+    edge_bin(e, r, N, k, t, in);
+    if (!in) return;
+    const float we = (e >= 1 ? gv[e - 1] : 0.f) - (e <= N - 1 ? gv[e] : 0.f);
+    const float t2 = t * t;
+    const float dG = fmaf(u[k], 6.f * (t - t2), fmaf(hermite_S(u, k, N), 3.f * t2 - 4.f * t + 1.f,
+                                                      hermite_S(u, k + 1, N) * (3.f * t2 - 2.f * t)));
+    const float x = fmaf(r, em.de, e_edge[e]);
+    const float q = -we * dG * em.inv_de / em.slope(x);
+    ep[0] += q;
+    ep[1] = fmaf(q, x, ep[1]);
+    ep[2] = fmaf(q, x * x, ep[2]);
+}
+
 __device__ __forceinline__ EMap make_emap(const DevModel &m, const DevDataset &ds, const float *pv,
                                           const float *pd) {
     EMap em;
@@ -618,7 +753,8 @@ static __device__ void ds_signal(const DevModel &m, int d, const float *pv, cons
 }
 
 // Stage B: v = M(a) u. Ends with a barrier.
-template <class Ctx>
+// SPL: compiled with the area-conserving spline option (the general kernel builds)
+template <bool SPL, class Ctx>
 static __device__ void ds_remap(const DevModel &m, int d, const Ctx &c, EvalWs ws) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
@@ -633,6 +769,11 @@ static __device__ void ds_remap(const DevModel &m, int d, const Ctx &c, EvalWs w
     (void)warp;
     (void)nw;
     const EMap &em = c.em;
+    if (SPL && m.remap_mode == FIT_REMAP_SPLINE) {
+        for (int t = tid; t < N_t; t += nth) ws.v[t] = spline_target(ws.u, m.e_edge, em, t, N_t);
+        __syncthreads();
+        return;
+    }
     // ---- stage B: energy correction, gather per target bin ------------------------------
     // Source bin k covers [Y_k, Y_k+1] in grid units, Y_k = k + D(e_k). Target m gathers the
     // sources whose mapped interval overlaps [m, m+1]; overlaps are computed relative to the
@@ -779,7 +920,7 @@ static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, 
 
 // Stages D, E and F: adjoint of the fold, of the energy map and of the signal; adds the
 // gradient contributions to grad. Needs ws.u/ts/ptot/dp/pcw (ds_signal<true>) and ws.gmu.
-template <int NC, int NOSC>
+template <int NC, int NOSC, bool SPL>
 static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, const float *pd,
                                      const DsCtxT<NOSC> &c, EvalWs ws, float *grad, double *red) {
     const DevDataset &ds = m.ds[d];
@@ -821,13 +962,19 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
     // ep[0..2] d/da, ep[3..3+NOSC) d/d eta, ep[kN] d/d norm, ep[kP+c] d/d power_c (NC >= C)
 #pragma unroll
     for (int i = 0; i < kP + NC; ++i) ep[i] = 0.f;
+    const bool spline = SPL && m.remap_mode == FIT_REMAP_SPLINE;
     for (int k = tid; k < N_t; k += nth) {
+        float gu = 0.f;
+        if (spline) {
+            gu = spline_adjoint_source(ws.u, gv, m.e_edge, em, k, N_t);
+            spline_adjoint_edge(ws.u, gv, m.e_edge, em, k, N_t, ep);
+            if (k == N_t - 1) spline_adjoint_edge(ws.u, gv, m.e_edge, em, N_t, N_t, ep);
+        } else {
         const float e0 = m.e_edge[k], e1 = m.e_edge[k + 1];
         const float d0 = em.disp(e0), d1 = em.disp(e1);
         const float w = 1.f + (d1 - d0), iw = 1.f / w;
         const int f0i = (int)floorf(d0), f1i = (int)floorf(d1);
         const int t0 = k + f0i, t1 = k + 1 + f1i;
-        float gu = 0.f;
         for (int t = max(t0, 0); t <= min(t1, N_t - 1); ++t) {
             const float ylo = (float)(k - t) + d0, yhi = (float)(k + 1 - t) + d1;
             const float ov = fminf(yhi, 1.f) - fmaxf(ylo, 0.f);
@@ -840,6 +987,7 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
         ep[0] += (A0 + A1) * em.inv_de;
         ep[1] += (A0 * e0 + A1 * e1) * em.inv_de;
         ep[2] += (A0 * e0 * e0 + A1 * e1 * e1) * em.inv_de;
+        }
         const float ts = ws.ts[k], pt = ws.ptot[k];
         const float gb = pmul(c.nrm, gu * ts);    // d nll / d(ptot)
 #pragma unroll
@@ -875,16 +1023,16 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
 // contributions (theta space, P floats). Returns the dataset's -2lnL (all threads); *status |=
 // kSt* bits on failure.
 // Stages D-F with the per-core sums sized for the model's core count.
-template <int NOSC>
+template <bool SPL, int NOSC>
 static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, const float *pd,
                                   const DsCtxT<NOSC> &c, EvalWs ws, float *grad, double *red) {
     if (m.C <= 2)
-        ds_adjoint_nc<2>(m, d, pv, pd, c, ws, grad, red);
+        ds_adjoint_nc<2, NOSC, SPL>(m, d, pv, pd, c, ws, grad, red);
     else
-        ds_adjoint_nc<FIT_MAX_CORES>(m, d, pv, pd, c, ws, grad, red);
+        ds_adjoint_nc<FIT_MAX_CORES, NOSC, SPL>(m, d, pv, pd, c, ws, grad, red);
 }
 
-template <int NOSC>
+template <int NOSC, bool SPL>
 static __device__ double eval_dataset_n(const DevModel &m, int d, const float *pv, const float *pd,
                                         const float *data, EvalWs ws, float *grad, double *red,
                                         int *status, float *mu_out) {
@@ -894,24 +1042,26 @@ static __device__ double eval_dataset_n(const DevModel &m, int d, const float *p
         ds_signal<true>(m, d, pv, pd, c, ws);
     else
         ds_signal<false>(m, d, pv, pd, c, ws);
-    ds_remap(m, d, c, ws);
+    ds_remap<SPL>(m, d, c, ws);
     const double nll_d = ds_fold_lik(m, d, pv, pd, c, data, ws, grad, red, status, mu_out);
     if (data == nullptr || grad == nullptr || (*(volatile int *)status) != 0) return nll_d;
-    ds_adjoint(m, d, pv, pd, c, ws, grad, red);
+    ds_adjoint<SPL>(m, d, pv, pd, c, ws, grad, red);
     return nll_d;
 }
 
-// One dataset's -2lnL (and gradient). NOSC = 4: models of Eq. 1 or the three-flavour formula
-// only; NOSC = 6: any model (the 3+1 formula, the others through the four-parameter path).
+// One dataset's -2lnL (and gradient). NOSC = 4 (the basic build): models of Eq. 1 or the
+// three-flavour formula with the overlap-length energy correction; NOSC = 6 (the general
+// build): any model (the 3+1 formula, the spline energy correction).
 template <int NOSC = 4>
 static __device__ double eval_dataset(const DevModel &m, int d, const float *pv, const float *pd,
                                       const float *data, EvalWs ws, float *grad, double *red,
                                       int *status, float *mu_out) {
     if constexpr (NOSC == 6) {
         if (m.osc_mode == FIT_OSC_STERILE4)
-            return eval_dataset_n<6>(m, d, pv, pd, data, ws, grad, red, status, mu_out);
+            return eval_dataset_n<6, true>(m, d, pv, pd, data, ws, grad, red, status, mu_out);
+        return eval_dataset_n<4, true>(m, d, pv, pd, data, ws, grad, red, status, mu_out);
     }
-    return eval_dataset_n<4>(m, d, pv, pd, data, ws, grad, red, status, mu_out);
+    return eval_dataset_n<4, false>(m, d, pv, pd, data, ws, grad, red, status, mu_out);
 }
 
 }  // namespace fitcore

@@ -854,8 +854,9 @@ __device__ void write_result(const DevModel &m, const FitState &st, const float 
 // fits one instance at a time, so MINB instances share an SM and cover each other's barrier and
 // load latencies. With the working set in shared memory four blocks of the larger register
 // budget measured faster; with it in global memory (L2) the fifth instance pays for itself.
-// NOSC = 4: models of Eq. 1 or the three-flavour formula; NOSC = 6: any model, the 3+1 formula
-// included (a separate build, so that the common case carries none of its registers).
+// NOSC = 4: models of Eq. 1 or the three-flavour formula with the overlap-length energy
+// correction; NOSC = 6: any model, the 3+1 formula and the spline correction included (a
+// separate build, so that the common case carries none of their registers).
 template <int MINB, int NOSC>
 __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -984,7 +985,7 @@ __global__ void __launch_bounds__(128) ls_init_kernel(LsArgs A) {
 // Forward pass and likelihood of one (instance, dataset) per block iteration: stages A (no
 // partials), B, C, C2; stores the dataset's -2lnL, dD/dmu and the efficiency / background
 // gradient contributions.
-template <int NOSC>
+template <int NOSC, bool SPL>
 __device__ __forceinline__ void ls_forward_body(LsArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LsEvalSmem &S = *reinterpret_cast<LsEvalSmem *>(smem_raw);
@@ -1019,7 +1020,7 @@ __device__ __forceinline__ void ls_forward_body(LsArgs A) {
         double nll = 0.0;
         if (ds_setup(m, d, pv, pd, c, &S.status)) {
             ds_signal<false>(m, d, pv, pd, c, ws);
-            ds_remap(m, d, c, ws);
+            ds_remap<SPL>(m, d, c, ws);
             nll = ds_fold_lik(m, d, pv, pd, c, A.data + in.data_off, ws, A.gsl + gd * P, S.red, &S.status,
                               nullptr);
             const int nr = m.ds[d].n_reco;
@@ -1035,12 +1036,18 @@ __device__ __forceinline__ void ls_forward_body(LsArgs A) {
     }
 }
 
-__global__ void __launch_bounds__(128) ls_forward_kernel(LsArgs A) { ls_forward_body<4>(A); }
-__global__ void __launch_bounds__(128) ls_forward_kernel6(LsArgs A) { ls_forward_body<6>(A); }
+// basic build (Eq. 1 / three-flavour, overlap correction) and general build (any model)
+__global__ void __launch_bounds__(128) ls_forward_kernel(LsArgs A) { ls_forward_body<4, false>(A); }
+__global__ void __launch_bounds__(128) ls_forward_kernel6(LsArgs A) {
+    if (A.model->osc_mode == FIT_OSC_STERILE4)
+        ls_forward_body<6, true>(A);
+    else
+        ls_forward_body<4, true>(A);
+}
 
 // Adjoint of one (instance, dataset) per block iteration: stage A again with the partials,
 // then stages D, E, F into the dataset's gradient slice.
-template <int NOSC>
+template <int NOSC, bool SPL>
 __device__ __forceinline__ void ls_adjoint_body(LsArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LsEvalSmem &S = *reinterpret_cast<LsEvalSmem *>(smem_raw);
@@ -1069,14 +1076,19 @@ __device__ __forceinline__ void ls_adjoint_body(LsArgs A) {
         DsCtxT<NOSC> c;
         if (ds_setup(m, d, pv, pd, c, &S.status)) {
             ds_signal<true>(m, d, pv, pd, c, ws);
-            ds_adjoint(m, d, pv, pd, c, ws, A.gsl + gd * P, S.red);
+            ds_adjoint<SPL>(m, d, pv, pd, c, ws, A.gsl + gd * P, S.red);
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(128) ls_adjoint_kernel(LsArgs A) { ls_adjoint_body<4>(A); }
-__global__ void __launch_bounds__(128) ls_adjoint_kernel6(LsArgs A) { ls_adjoint_body<6>(A); }
+__global__ void __launch_bounds__(128) ls_adjoint_kernel(LsArgs A) { ls_adjoint_body<4, false>(A); }
+__global__ void __launch_bounds__(128) ls_adjoint_kernel6(LsArgs A) {
+    if (A.model->osc_mode == FIT_OSC_STERILE4)
+        ls_adjoint_body<6, true>(A);
+    else
+        ls_adjoint_body<4, true>(A);
+}
 
 // Minimiser step per active instance: gathers the round's evaluation (dataset sums, prior,
 // gradient in z), runs fit_decide, and either prepares theta of the next trial point and puts

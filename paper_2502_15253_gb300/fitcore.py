@@ -41,6 +41,7 @@ class fit_model_desc(C.Structure):
         ("n_bkg", C.c_int), ("bkg_ds", C.POINTER(C.c_int)),
         ("bkg_template", C.POINTER(C.c_double)), ("bkg_rate_idx", C.POINTER(C.c_int)),
         ("bkg_shape_idx", C.POINTER(C.c_int)),
+        ("remap_mode", C.c_int),
     ]
 
 
@@ -241,6 +242,7 @@ class Model:
         m.cov_idx = i(np.concatenate([ix for ix, _ in s.cov_blocks]) if s.cov_blocks else [0])
         m.cov = d(np.concatenate([c.ravel() for _, c in s.cov_blocks]) if s.cov_blocks else [0.0])
         m.osc_mode = s.osc_mode
+        m.remap_mode = int(getattr(s, "remap", 0))
         for k in range(6):   # the 3+1 formula has six survival parameters, the others four
             m.osc_idx[k] = int(s.osc_idx[k]) if k < len(s.osc_idx) else -1
             m.osc_val[k] = float(s.osc_val[k]) if k < len(s.osc_val) else 0.0

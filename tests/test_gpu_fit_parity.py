@@ -32,8 +32,9 @@ SPECS = {}
 
 
 def spec_of(name):
+    """"c1" etc.; "c1/spline" is the same model with the area-conserving spline remap."""
     if name not in SPECS:
-        s = synth.make_model(name)
+        s = synth.make_model(name.split("/")[0], remap=int(name.endswith("/spline")))
         SPECS[name] = (s, oracle.OracleModel(s), fitcore.Model(s))
     return SPECS[name]
 
@@ -137,6 +138,25 @@ def test_fit_c1_ensemble_statistics(engine):
     datas, masks, _ = make_instances("c1", 64, 600)
     th, res = run_gpu(["c1"] * 64, datas, masks, opts=engine_opts(engine))
     check_against_oracle("c1", datas, masks, th, res, max_other=8, min_strict=0.85)
+
+
+@ENGINES
+def test_fit_c1_spline_ensemble(engine):
+    """The three-dataset model with the area-conserving spline energy correction: -2lnL
+    continuously differentiable in (a0, a1, a2), so no kink can hold a second minimum. 32
+    pseudo-experiments; all must reach the oracle's minimum (1e-3 in -2lnL, 1e-2 sigma), and
+    the strict 1e-3 sigma bar is asserted for the measured share."""
+    datas, masks, _ = make_instances("c1/spline", 32, 700)
+    th, res = run_gpu(["c1/spline"] * 32, datas, masks, opts=engine_opts(engine))
+    check_against_oracle("c1/spline", datas, masks, th, res, max_other=0, min_strict=0.5)
+
+
+@ENGINES
+def test_fit_c0_and_c2_spline_match_oracle(engine):
+    for name, n, seed in (("c0/spline", 8, 710), ("c2/spline", 2, 720)):
+        datas, masks, _ = make_instances(name, n, seed)
+        th, res = run_gpu([name] * n, datas, masks, opts=engine_opts(engine))
+        check_against_oracle(name, datas, masks, th, res)
 
 
 @ENGINES
