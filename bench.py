@@ -354,6 +354,11 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
     }
 
 
+# DRAM bytes (read + write) per fit of fit_kernel on the three-dataset model, from an ncu capture
+# of one 760-fit launch (7.30 MB read, 47.86 MB written: the workspace write-back); traffic
+# grows with the fits
+FIT_DRAM_BYTES_PER_FIT = (7.301632e6 + 47.855360e6) / 760
+
 # DRAM bytes (read + write) per event of mc_spectrum_kernel for one parameter set, from an ncu
 # capture of 11,904,680 events (154.81 MB read, 3.62 MB written); traffic grows with the events
 MC_DRAM_BYTES_PER_EVENT = (154.809088e6 + 3.621632e6) / 11_904_680
@@ -705,7 +710,10 @@ def run_ours(args):
             "evals_per_s": evals_per_s, "iters_per_fit": iters / B, "evals_per_fit": evals / B,
             "converged_frac": conv,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                         "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                         "traffic": FIT_DRAM_BYTES_PER_FIT * B,
+                         "traffic_note": "DRAM read+write bytes per fit of an ncu capture of "
+                                         "this kernel (760 fits), scaled to the launch",
                          "kernel": "fit_kernel",
                          "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"},
             "e2e": {"value": world * B / e2e_s, "unit": "fits/s", "h2d_bytes_per_step": int(h2d),

@@ -309,13 +309,16 @@ def make_c0(seed=BASE_SEED, tiny=False):
                      np.array([-1], np.int32), n_true, e_lo, e_hi, [det], [ds])
 
 
-def make_c1(seed=BASE_SEED, sterile=False):
+def make_c1(seed=BASE_SEED, sterile=False, flux41=False):
     """Double Chooz-like FD-I / FD-II / ND with two cores, 38 reco bins each, ~291 parameters.
 
     Oscillation: full Eq. 1 with sin^2 2th12 and dm2_21 as constrained nuisances. With
     sterile=True ("c1s", the 3+1 search): the exact 3+1 vacuum survival with sin^2 th12,
     dm2_21 and dm2_31 constrained, sin^2 th13 free, and the two new parameters sin^2 2th14
-    (nominal 0) and dm2_41 (nominal 0.1 eV^2) free; everything else as c1. Per dataset:
+    (nominal 0) and dm2_41 (nominal 0.1 eV^2) free; everything else as c1. With flux41=True
+    ("c1_flux41"): the signal shape parameters on the uniform 41-bin flux grid of 0.25 MeV over
+    1-11.25 MeV (prompt energy) instead of the 38 reco bins, 3 x 41 parameters correlated
+    between the datasets as c1's plus an uncorrelated 41 x 41 deviation per dataset. Per dataset:
     efficiency (correlated prior), energy scale (a0, a1, a2), 38 signal shape reweights
     (joint 114 x 114 prior, FD-I/FD-II correlation 0.9). Backgrounds: Li-9 (shape shared by
     all datasets, rate shared by FD-I/FD-II, rates free), accidentals (per-dataset shape and
@@ -347,21 +350,27 @@ def make_c1(seed=BASE_SEED, sterile=False):
     r_acc = [p.add(f"acc_rate[{d}]", 1.0, 0.10) for d in range(3)]
     r_fn_fd = p.add("fn_rate_fd", 1.0, 0.15)
     r_fn_nd = p.add("fn_rate_nd", 1.0, 0.15)
-    shp = p.add_block("shape", 3 * nr, 1.0, 0.02)
+    ng = 41 if flux41 else nr          # signal shape groups per dataset
+    shp = p.add_block("shape", 3 * ng, 1.0, 0.02)
     li9 = p.add_block("li9_shape", nr, 0.0, 0.1)
     acc = [p.add_block(f"acc_shape{d}", nr, 0.0, 0.05) for d in range(3)]
     pw = np.array([p.add("power[0]", 1.0, 0.008), p.add("power[1]", 1.0, 0.008)], np.int32)
     names, th0, sig, scl = p.arrays()
 
     k = np.array([[1.0, 0.9, 0.8], [0.9, 1.0, 0.8], [0.8, 0.8, 1.0]])
-    c_shape = shape_correlation(nr, rng)
+    c_shape = shape_correlation(ng, rng)
+    cov_shape = 0.02 ** 2 * np.kron(k, c_shape)
+    if flux41:   # plus an uncorrelated deviation per dataset (own generator: c1 stays as is)
+        rng_u = np.random.default_rng(seed + 11)
+        cov_shape = cov_shape + 0.01 ** 2 * np.kron(np.eye(3), shape_correlation(41, rng_u))
     cov_blocks = [
         (eff, 0.01 ** 2 * np.array([[1.0, 0.5, 0.5], [0.5, 1.0, 0.5], [0.5, 0.5, 1.0]])),
-        (shp, 0.02 ** 2 * np.kron(k, c_shape)),
+        (shp, cov_shape),
         (li9, 0.1 ** 2 * shape_correlation(nr, rng)),
     ] + [(acc[d], 0.05 ** 2 * shape_correlation(nr, rng)) for d in range(3)]
 
     gidx = _group_of(tedges, redges, PROMPT_SHIFT_MEV)
+    gshape = _group_of(tedges, np.linspace(1.0, 11.25, 42), PROMPT_SHIFT_MEV) if flux41 else gidx
     resp = gaussian_response(tedges, redges, 0.08)
     dets = [Detector("FD", redges, resp), Detector("ND", redges, resp.copy())]
     none_r = np.full(nr, -1, np.int32)
@@ -375,8 +384,8 @@ def make_c1(seed=BASE_SEED, sterile=False):
               Background("fn", _template_flat(redges, nfn), rfn, none_r.copy())]
         base = np.array(base)
         datasets.append(Dataset(nm, det, signal_spectrum(tedges, nev), base, _core_weights(base),
-                                -1, int(eff[d]), esc[d], shp[d * nr + gidx].astype(np.int32), bk))
-    return ModelSpec("c1s" if sterile else "c1", names, th0, sig, scl, cov_blocks,
+                                -1, int(eff[d]), esc[d], shp[d * ng + gshape].astype(np.int32), bk))
+    return ModelSpec("c1s" if sterile else ("c1_flux41" if flux41 else "c1"), names, th0, sig, scl, cov_blocks,
                      OSC_STERILE4 if sterile else OSC_EQ1, osc, osc_val, pw, n_true, e_lo, e_hi,
                      dets, datasets)
 
@@ -440,6 +449,8 @@ def make_model(name: str, seed: int = BASE_SEED, remap: int = 0) -> ModelSpec:
         return make_c1(seed)
     if name == "c1s":
         return make_c1(seed, sterile=True)
+    if name == "c1_flux41":
+        return make_c1(seed, flux41=True)
     if name == "c2":
         return make_c2(seed)
     raise ValueError(f"unknown model {name!r}")

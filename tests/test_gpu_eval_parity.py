@@ -22,7 +22,8 @@ from paper_2502_15253_gb300 import fitcore, synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=["c0", "c1", "c2", "c1s", "c0/spline", "c1/spline", "c2/spline"])
+@pytest.fixture(scope="module", params=["c0", "c1", "c2", "c1s", "c0/spline", "c1/spline", "c2/spline",
+                                                "c1_flux41"])
 def pair(request):
     spec = synth.make_model(request.param.split("/")[0], remap=int(request.param.endswith("spline")))
     return spec, oracle.OracleModel(spec), fitcore.Model(spec)

@@ -159,6 +159,14 @@ def test_fit_c0_and_c2_spline_match_oracle(engine):
         check_against_oracle(name, datas, masks, th, res)
 
 
+def test_fit_c1_on_the_41_bin_flux_grid():
+    """Signal shape parameters on the uniform 41-bin flux grid (3 x 41, eight per dataset
+    without data: prior only) instead of the reco binning."""
+    datas, masks, _ = make_instances("c1_flux41", 8, 730)
+    th, res = run_gpu(["c1_flux41"] * 8, datas, masks)
+    check_against_oracle("c1_flux41", datas, masks, th, res)
+
+
 @ENGINES
 def test_uneven_mixed_batch_equals_separate_runs(engine):
     d1, m1, _ = make_instances("c1", 5, 400, masks=list(synth.C1_MASKS))

@@ -405,7 +405,7 @@ def test_expected_backgrounds_and_efficiency_c1():
 # ---------------------------------------------------------------------------------------
 # -2lnL and gradient
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s", "c0/spline", "c1/spline"])
+@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s", "c0/spline", "c1/spline", "c1_flux41"])
 def test_asimov_nll_is_zero(name):
     spec = synth.make_model(name.split("/")[0], remap=int(name.endswith("spline")))
     om = oracle.OracleModel(spec)
@@ -431,7 +431,8 @@ def test_poisson_part_equals_library_pmf_sum():
     assert om.nll(theta, data, mask=m) == pytest.approx(ref_m, rel=1e-10)
 
 
-@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s", "c0/spline", "c1/spline", "c2/spline"])
+@pytest.mark.parametrize("name", ["c0", "c1", "c2", "c1s", "c0/spline", "c1/spline", "c2/spline",
+                                  "c1_flux41"])
 def test_gradient_matches_central_differences(name):
     spec = synth.make_model(name.split("/")[0], remap=int(name.endswith("spline")))
     om = oracle.OracleModel(spec)
