@@ -45,6 +45,8 @@ def parse():
                    help="fit engine: one persistent launch, or one round of launches per evaluation")
     p.add_argument("--mc-events", type=int, default=20_000_000,
                    help="simulated events of the event-reweighting measurement (0: skip)")
+    p.add_argument("--no-precondition", action="store_true",
+                   help="fit in plain whitened coordinates (no Fisher preconditioner)")
     p.add_argument("--no-profile", action="store_true",
                    help="skip the profile-likelihood and mass-ordering scans")
     p.add_argument("--no-warm-start", action="store_true",
@@ -607,6 +609,7 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts = fitcore.fit_batch_default_opts()
     opts.engine = 1 if args.engine == "lockstep" else 0
+    opts.precondition = 0 if (args.no_precondition or args.engine == "lockstep") else 1
 
     def step():
         fitcore.fit_batch([model], inst, data_d, None, best_d, res_d, opts, stream)
@@ -644,8 +647,12 @@ def run_ours(args):
     value = world * B / (ms / 1e3)
     evals_per_s = world * evals / (ms / 1e3)
 
-    # roofline of the fit kernel: FP32 ALU peak from unit counts and the maximum SM clock
+    # roofline of the fit kernel: FP32 ALU peak from unit counts and the maximum SM clock;
+    # with the Fisher preconditioner each evaluation also applies T twice (Q^T x and Q u:
+    # 2 P r multiply-adds each, r = min(32, bins, P))
     f_eval = flops_per_eval(spec, spec.all_mask())
+    if opts.precondition:
+        f_eval += 8.0 * P * min(32, D, P)
     alg_flops = evals * f_eval + iters * flops_lbfgs_iter(P, opts.history)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -705,6 +712,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "fits_per_step": world * B, "fits_per_rank": B,
                        "engine": args.engine,
+                       "minimiser": "L-BFGS (32 pairs)" + (", Fisher-preconditioned coordinates"
+                                                          if opts.precondition else ""),
                        "start": "nominal (cold)", "l2": "flushed (512 MiB write) before each step",
                        "parallelism": f"instances sharded over {world} GPU(s), no collective"},
             "evals_per_s": evals_per_s, "iters_per_fit": iters / B, "evals_per_fit": evals / B,

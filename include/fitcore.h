@@ -197,7 +197,12 @@ typedef struct fit_batch_opts {
                              the fits of a model advance one evaluation per round, each round
                              three launches over all of them (threads, blocks_per_sm and
                              placement then do not apply)                                    */
-    int pad;
+    int precondition;     /* 1 (default) = persistent engine fits in Fisher-preconditioned
+                             coordinates: the expected Hessian of -2lnL at the model's nominal
+                             point, built once per model on first use, makes the quasi-Newton
+                             problem nearly isotropic (fewer iterations); 0 = plain whitened
+                             coordinates. Not applied to fits with held parameters nor to
+                             the lockstep engine.                                             */
 } fit_batch_opts;
 
 /* Result of one instance. */

@@ -156,6 +156,7 @@ void release(Staged &b, cudaStream_t s) {
 }
 
 std::mutex g_ws_mutex;
+std::mutex g_pre_mutex;   // guards building a model's preconditioner
 
 }  // namespace
 
@@ -166,6 +167,12 @@ struct fit_model {
     size_t bytes = 0;
     int n_params = 0, n_data = 0, n_ds = 0, n_true = 0;
     std::vector<uint8_t> in_block;   // parameter belongs to a covariance block (host copy)
+    // host copy of the transformation layer theta = theta0 + J z (for the preconditioner)
+    std::vector<double> theta0, zscale, blk_L;   // blk_L: the blocks' lower factors, packed
+    std::vector<int> bsz, bidx;
+    // Fisher preconditioner (built on first use): device matrices T, T^T, T^-1, state
+    float *pre = nullptr;
+    int pre_state = 0;     // 0 not built, 1 built, -1 failed (fits run unpreconditioned)
 };
 
 // error / launch-count hooks for the other translation units of the library
@@ -193,6 +200,7 @@ int64_t fit_kernel_launches(void) {
 void fit_model_destroy(fit_model *model) {
     if (!model) return;
     if (model->arena) cudaFree(model->arena);
+    if (model->pre) cudaFree(model->pre);
     delete model;
 }
 
@@ -567,6 +575,16 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         }
         A.put(&h.blk_first, bfirst);
         M->in_block.assign(in_block.begin(), in_block.end());
+        M->theta0 = th0;
+        M->zscale.assign(P, 0.0);
+        for (int i = 0; i < P; ++i)
+            if (!in_block[i]) M->zscale[i] = d->prior_sigma[i] > 0.0 ? d->prior_sigma[i] : d->scale[i];
+        for (int b = 0; b < d->n_cov; ++b) {
+            const int n = bsz[b];
+            M->bsz.push_back(n);
+            for (int i = 0; i < n; ++i) M->bidx.push_back(bidx[boff[b] + i]);
+            for (int64_t q = 0; q < (int64_t)n * n; ++q) M->blk_L.push_back(L64[moff[b] + q]);
+        }
         A.put(&h.blk_mat_off, moff);
         A.put(&h.blk_L, Lf);
         A.put(&h.blk_W, Wf);
@@ -1196,6 +1214,180 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
     return rc;
 }
 
+// theta = theta0 + J z on the host (single parameters: z times their scale; blocks: L z)
+void theta_of_z_host(const fit_model *M, const double *z, double *th) {
+    const int P = M->n_params;
+    for (int i = 0; i < P; ++i) th[i] = M->theta0[i] + M->zscale[i] * z[i];
+    size_t io = 0, lo = 0;
+    for (size_t b = 0; b < M->bsz.size(); ++b) {
+        const int n = M->bsz[b];
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j <= i; ++j) acc += M->blk_L[lo + (size_t)i * n + j] * z[M->bidx[io + j]];
+            th[M->bidx[io + i]] = M->theta0[M->bidx[io + i]] + acc;
+        }
+        io += n;
+        lo += (size_t)n * n;
+    }
+}
+
+// Eigen-decomposition of a small symmetric matrix A (n x n, row-major, destroyed) by cyclic
+// Jacobi rotations; eigenvalues into lam, eigenvectors into the columns of V.
+void jacobi_eigen(int n, std::vector<double> &A, std::vector<double> &lam, std::vector<double> &V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (off < 1e-30) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                const double th = 0.5 * (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / apq;
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {   // V <- V J
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    lam.resize(n);
+    for (int i = 0; i < n; ++i) lam[i] = A[(size_t)i * n + i];
+}
+
+// Fisher preconditioner of the whitened coordinates z (not in the paper). The expected Hessian
+// of -2lnL at theta0 over all datasets is H0 = 2 (I + U U^T), U = J^T diag(mu0)^(-1/2) with
+// J = d mu / d z (central differences, step 0.01 in z, of the device expectation). Its few
+// large eigen-directions (the data constrain ~10-40 combinations; the whitened prior gives 2 I
+// elsewhere) are found by subspace iteration on U U^T with a Rayleigh-Ritz step: U U^T ~
+// Q diag(lam) Q^T, Q orthonormal P x r, r = min(32, n_data, P). The fit then runs in w,
+//   z = T w,  T = I + Q diag(c) Q^T,  c_k = (1 + lam_k)^(-1/2) - 1,
+// where the expected Hessian is 2 I along Q and unchanged elsewhere; T is symmetric (the
+// gradient maps with the same product) and T^-1 = I + Q diag(c') Q^T, c'_k = (1 + lam_k)^(1/2) - 1.
+// Device storage: Q^T as r rows of P floats on the vector pitch, then c and c'. A model whose
+// expectation fails keeps pre_state = -1 and fits unpreconditioned.
+int build_preconditioner(fit_model *M, cudaStream_t s) {
+    if (M->pre_state != 0) return FIT_OK;
+    M->pre_state = -1;
+    const int P = M->n_params, D = M->n_data, Pp = fitcore::fit_vec_pitch(P);
+    const int r = std::min(fitcore::kMaxPreRank, std::min(D, P));
+    const double hz = 1e-2;
+    const int R = 2 * P + 1;
+    std::vector<double> th((size_t)R * P), z(P, 0.0);
+    for (int q = 0; q < R; ++q) {
+        std::fill(z.begin(), z.end(), 0.0);
+        if (q > 0) z[(q - 1) / 2] = (q % 2) ? hz : -hz;
+        theta_of_z_host(M, z.data(), th.data() + (size_t)q * P);
+    }
+    std::vector<float> mu((size_t)R * D);
+    std::vector<int> st(R, 0);
+    if (fit_model_expected(M, R, th.data(), mu.data(), st.data(), s) != FIT_OK) return FIT_OK;
+    for (int q = 0; q < R; ++q)
+        if (st[q] != 0) return FIT_OK;
+    // U [P x D]
+    std::vector<double> U((size_t)P * D, 0.0);
+    for (int j = 0; j < D; ++j) {
+        const double m0 = mu[j];
+        if (!(m0 > 0.0)) continue;
+        const double w = 1.0 / (2.0 * hz * std::sqrt(m0));
+        for (int i = 0; i < P; ++i)
+            U[(size_t)i * D + j] = ((double)mu[(size_t)(2 * i + 1) * D + j] - (double)mu[(size_t)(2 * i + 2) * D + j]) * w;
+    }
+    // subspace iteration X <- orth(U U^T X), X [P x r] (column k at X[k * P ...])
+    std::vector<double> X((size_t)r * P), Y((size_t)r * P), t((size_t)D);
+    uint64_t seed = 0x9e3779b97f4a7c15ull;
+    for (auto &x : X) {
+        seed ^= seed << 13; seed ^= seed >> 7; seed ^= seed << 17;
+        x = (double)(seed >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    auto apply = [&](const double *x, double *y) {   // y = U (U^T x)
+        for (int j = 0; j < D; ++j) t[j] = 0.0;
+        for (int i = 0; i < P; ++i) {
+            const double xi = x[i];
+            if (xi == 0.0) continue;
+            const double *Ui = U.data() + (size_t)i * D;
+            for (int j = 0; j < D; ++j) t[j] += Ui[j] * xi;
+        }
+        for (int i = 0; i < P; ++i) {
+            const double *Ui = U.data() + (size_t)i * D;
+            double acc = 0.0;
+            for (int j = 0; j < D; ++j) acc += Ui[j] * t[j];
+            y[i] = acc;
+        }
+    };
+    auto orth = [&](std::vector<double> &B) {   // modified Gram-Schmidt on the r columns
+        for (int k = 0; k < r; ++k) {
+            double *bk = B.data() + (size_t)k * P;
+            for (int l = 0; l < k; ++l) {
+                const double *bl = B.data() + (size_t)l * P;
+                double d = 0.0;
+                for (int i = 0; i < P; ++i) d += bk[i] * bl[i];
+                for (int i = 0; i < P; ++i) bk[i] -= d * bl[i];
+            }
+            double nn = 0.0;
+            for (int i = 0; i < P; ++i) nn += bk[i] * bk[i];
+            nn = std::sqrt(nn);
+            for (int i = 0; i < P; ++i) bk[i] = nn > 0.0 ? bk[i] / nn : 0.0;
+        }
+    };
+    orth(X);
+    for (int it = 0; it < 40; ++it) {
+        for (int k = 0; k < r; ++k) apply(X.data() + (size_t)k * P, Y.data() + (size_t)k * P);
+        X.swap(Y);
+        orth(X);
+    }
+    // Rayleigh-Ritz: B = X^T U U^T X, B = E diag(lam) E^T, Q = X E
+    for (int k = 0; k < r; ++k) apply(X.data() + (size_t)k * P, Y.data() + (size_t)k * P);
+    std::vector<double> B((size_t)r * r), lam, E;
+    for (int a = 0; a < r; ++a)
+        for (int b = 0; b < r; ++b) {
+            double d = 0.0;
+            for (int i = 0; i < P; ++i) d += X[(size_t)a * P + i] * Y[(size_t)b * P + i];
+            B[(size_t)a * r + b] = d;
+        }
+    for (int a = 0; a < r; ++a)   // symmetrise the rounding
+        for (int b = 0; b < a; ++b) B[(size_t)a * r + b] = B[(size_t)b * r + a] = 0.5 * (B[(size_t)a * r + b] + B[(size_t)b * r + a]);
+    jacobi_eigen(r, B, lam, E);
+    std::vector<float> buf((size_t)r * Pp + 2 * (size_t)r, 0.f);
+    for (int k = 0; k < r; ++k) {
+        for (int i = 0; i < P; ++i) {
+            double q = 0.0;
+            for (int a = 0; a < r; ++a) q += X[(size_t)a * P + i] * E[(size_t)a * r + k];
+            buf[(size_t)k * Pp + i] = (float)q;
+        }
+        const double l = std::max(lam[k], 0.0);
+        buf[(size_t)r * Pp + k] = (float)(1.0 / std::sqrt(1.0 + l) - 1.0);
+        buf[(size_t)r * Pp + r + k] = (float)(std::sqrt(1.0 + l) - 1.0);
+    }
+    float *dev = nullptr;
+    if (cudaMalloc(&dev, sizeof(float) * buf.size()) != cudaSuccess ||
+        cudaMemcpy(dev, buf.data(), sizeof(float) * buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        if (dev) cudaFree(dev);
+        return FIT_OK;
+    }
+    M->pre = dev;
+    M->host.pre_Q = dev;
+    M->host.pre_c = dev + (size_t)r * Pp;
+    M->host.pre_r = r;
+    M->pre_state = 1;
+    return FIT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1213,7 +1405,7 @@ void fit_batch_default_opts(fit_batch_opts *o) {
     o->restarts = 0;
     o->placement = 0;
     o->engine = 0;
-    o->pad = 0;
+    o->precondition = 1;
 }
 
 int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst, const float *data,
@@ -1292,7 +1484,16 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
         if (pl == 2) return fitcore::fit_smem_bytes(max_loc);
         return fitcore::fit_smem_bytes(0);
     };
-    auto kernel_for = [n_osc](int variant) { return fitcore::fit_kernel_func(variant, n_osc); };
+    // the preconditioned build when asked for and every model has its preconditioner
+    bool precond = o.precondition != 0 && fixed == nullptr;
+    if (precond) {
+        std::lock_guard<std::mutex> plock(g_pre_mutex);
+        for (int i = 0; i < n_models; ++i) {
+            build_preconditioner(models[i], s);
+            precond = precond && models[i]->pre_state == 1;
+        }
+    }
+    auto kernel_for = [n_osc, precond](int variant) { return fitcore::fit_kernel_func(variant, n_osc, precond); };
     auto blocks_for = [&](int pl, int variant) -> int {
         const size_t sm = smem_for(pl);
         if (sm > std::min(kSmemCap, cfg.smem_optin)) return 0;
@@ -1378,6 +1579,7 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
         a.smem_floats = placement == 1 ? max_need : placement == 2 ? max_loc : 0;
         a.hist_global = placement == 1 ? 0 : 1;
         a.budget_ns = (uint64_t)(o.time_budget_s * 1e9);
+        a.precond = precond ? 1 : 0;
         if (o.use_graph) {
             rc = graph_launch(kern, grid, o.threads, smem, a, (int *)dq.dev, s);
         } else {

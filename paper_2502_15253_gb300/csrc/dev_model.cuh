@@ -87,6 +87,10 @@ struct DevModel {
     int ws_eval_floats;      // per-block workspace of one evaluation
     int max_reco;
     int ldt;                 // row stride of the dense response (N_t rounded up to 4)
+    // Fisher preconditioner (nullptr until built): z = T w, T = I + Q diag(c) Q^T; pre_Q holds
+    // Q^T as pre_r rows on the vector pitch, pre_c the r coefficients c then the r of T^-1
+    const float *pre_Q, *pre_c;
+    int pre_r;
 };
 
 // ------------------------------------------------------------------------------------

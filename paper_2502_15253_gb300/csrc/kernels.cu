@@ -182,10 +182,11 @@ struct alignas(16) FitSmem {
     double gHg;
     int status;                // evaluation status bits
     int inst;
+    float pre_u[kMaxPreRank];  // preconditioner scratch
 };
 
 struct FitVecs {
-    float *z, *g, *d, *zt, *gt, *zlo, *glo, *zcr, *gcr, *pv, *pd, *gth, *S, *Y;
+    float *z, *g, *d, *zt, *gt, *zlo, *glo, *zcr, *gcr, *pv, *pd, *gth, *zw, *gzw, *S, *Y;
 };
 
 // 12 P-vectors at base; the 2 hist P-vectors of the history at hbase (pitch fit_vec_pitch(P))
@@ -204,6 +205,8 @@ __device__ __forceinline__ FitVecs carve_fit_vecs(float *base, float *hbase, int
     v.pv = v.gcr + Pp;
     v.pd = v.pv + Pp;
     v.gth = v.pd + Pp;
+    v.zw = v.gth + Pp;    // preconditioned fits: z of the trial point and its z-gradient
+    v.gzw = v.zw + Pp;
     v.S = hbase;
     v.Y = v.S + (int64_t)hist * Pp;
     return v;
@@ -466,6 +469,38 @@ __device__ __forceinline__ void hold_fixed(const uint8_t *fixed, float *gz, int 
         if (fixed[i]) gz[i] = 0.f;
 }
 
+// y = x + Q (coef o (Q^T x)) for the model's preconditioner (coef = pre_c: y = T x; coef =
+// pre_c + r: y = T^-1 x). Q^T rows: a warp per row, 16-byte loads, the last P mod 4 entries
+// scalar (the padding of x is never read); then a thread per entry over the r rows. x and y
+// may be the same vector. u: r floats of shared scratch. Ends with a barrier.
+__device__ void pre_apply(const DevModel &m, const float *coef, const float *x, float *y, float *u) {
+    const int P = m.P, Pp = fit_vec_pitch(P), r = m.pre_r;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nfull = P >> 2;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    for (int k = warp; k < r; k += nw) {
+        const float *q = m.pre_Q + (int64_t)k * Pp;
+        const float4 *q4 = reinterpret_cast<const float4 *>(q);
+        float acc = 0.f;
+        for (int c = lane; c < nfull; c += 32) {
+            const float4 a = __ldg(q4 + c), b = x4[c];
+            acc = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+        }
+        if (lane < (P & 3)) acc = fmaf(__ldg(q + 4 * nfull + lane), x[4 * nfull + lane], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) u[k] = __ldg(coef + k) * acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        float acc = x[i];
+#pragma unroll 8
+        for (int k = 0; k < r; ++k) acc = fmaf(__ldg(m.pre_Q + (int64_t)k * Pp + i), u[k], acc);
+        y[i] = acc;
+    }
+    __syncthreads();
+}
+
 // -2lnL(theta(z)) and its z-gradient gz. Returns +inf on an invalid point.
 template <int NOSC>
 __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &V, EvalWs ws,
@@ -484,6 +519,17 @@ __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &
     const double prior = eval_z_prior(m, z, V.gth, gz, S.red);
     hold_fixed(fixed, gz, m.P);
     return nll + prior;
+}
+
+// The same in the preconditioned coordinates w (z = T w): -2lnL and g_w = T^T g_z.
+template <int NOSC>
+__device__ double eval_w(const DevModel &m, const float *w, float *gw, FitVecs &V, EvalWs ws,
+                         const float *data, uint32_t mask, FitSmem &S) {
+    pre_apply(m, m.pre_c, w, V.zw, S.pre_u);
+    const double f = eval_z<NOSC>(m, V.zw, V.gzw, V, ws, data, mask, S, nullptr);
+    __syncthreads();
+    pre_apply(m, m.pre_c, V.gzw, gw, S.pre_u);   // T is symmetric
+    return f;
 }
 
 // cubic minimiser through (a, fa, ga), (b, fb, gb), or the secant of the slopes when the
@@ -857,7 +903,9 @@ __device__ void write_result(const DevModel &m, const FitState &st, const float 
 // NOSC = 4: models of Eq. 1 or the three-flavour formula with the overlap-length energy
 // correction; NOSC = 6: any model, the 3+1 formula and the spline correction included (a
 // separate build, so that the common case carries none of their registers).
-template <int MINB, int NOSC>
+// PRE: the preconditioned build (fits in w, z = T w), used when the launch asks for it and every
+// model of the batch has its preconditioner.
+template <int MINB, int NOSC, bool PRE>
 __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FitSmem &S = *reinterpret_cast<FitSmem *>(smem_raw);
@@ -894,6 +942,7 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
         FitVecs V = carve_fit_vecs(base, hbase, P, F.hist);
         const EvalWs ws = carve_eval_ws(base + fit_work_floats(P), m.N_t, m.C, m.max_reco, m.n_osc);
         const float *data = A.data + in.data_off;
+        constexpr bool pre = PRE;
         if (tid == 0) init_state(S.st);
         __syncthreads();
         if (global_ns() > F.deadline) {
@@ -902,13 +951,20 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
             __syncthreads();
         } else {
             start_z(m, A.start ? A.start + in.param_off : nullptr, V.zt, V.pd);
+            if (pre) pre_apply(m, m.pre_c + m.pre_r, V.zt, V.zt, S.pre_u);   // w0 = T^-1 z0
             while (true) {
-                const double fa = eval_z<NOSC>(m, V.zt, V.gt, V, ws, data, in.mask, S,
-                                         A.fixed ? A.fixed + in.param_off : nullptr);
+                const double fa = pre ? eval_w<NOSC>(m, V.zt, V.gt, V, ws, data, in.mask, S)
+                                      : eval_z<NOSC>(m, V.zt, V.gt, V, ws, data, in.mask, S,
+                                                     A.fixed ? A.fixed + in.param_off : nullptr);
                 if (!fit_decide(S, V, P, fa, F)) break;
             }
         }
-        write_result(m, S.st, V.z, A.best + in.param_off, A.results + ii,
+        const float *zres = V.z;
+        if (pre) {   // back to z = T w
+            pre_apply(m, m.pre_c, V.z, V.zw, S.pre_u);
+            zres = V.zw;
+        }
+        write_result(m, S.st, zres, A.best + in.param_off, A.results + ii,
                      A.start ? A.start + in.param_off : nullptr, A.fixed ? A.fixed + in.param_off : nullptr);
         __syncthreads();
     }
@@ -1145,12 +1201,19 @@ __global__ void __launch_bounds__(128) ls_step_kernel(LsArgs A) {
     }
 }
 
-const void *fit_kernel_func(int variant, int n_osc) {
+const void *fit_kernel_func(int variant, int n_osc, bool pre) {
+    if (pre) {
+        if (n_osc == 6)
+            return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5, 6, true>)
+                                : reinterpret_cast<const void *>(&fit_kernel<4, 6, true>);
+        return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5, 4, true>)
+                            : reinterpret_cast<const void *>(&fit_kernel<4, 4, true>);
+    }
     if (n_osc == 6)
-        return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5, 6>)
-                            : reinterpret_cast<const void *>(&fit_kernel<4, 6>);
-    return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5, 4>)
-                        : reinterpret_cast<const void *>(&fit_kernel<4, 4>);
+        return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5, 6, false>)
+                            : reinterpret_cast<const void *>(&fit_kernel<4, 6, false>);
+    return variant == 5 ? reinterpret_cast<const void *>(&fit_kernel<5, 4, false>)
+                        : reinterpret_cast<const void *>(&fit_kernel<4, 4, false>);
 }
 
 size_t fit_smem_bytes(int floats) { return sizeof(FitSmem) + sizeof(float) * (size_t)floats; }

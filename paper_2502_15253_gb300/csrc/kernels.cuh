@@ -25,6 +25,7 @@ struct FitArgs {
     int hist_global;             // 1: the L-BFGS history lives in the global slice
     const uint8_t *fixed;        // device, indexed like start/best, or nullptr: held parameters
     uint64_t budget_ns;
+    int precond;                 // 1: fit in the models' preconditioned coordinates (if built)
 };
 
 __global__ void eval_kernel(const DevModel *gm, int B, const double *theta, const float *data,
@@ -76,7 +77,7 @@ size_t ls_step_smem_bytes();
 size_t ls_eval_smem_bytes(int P, int ws_floats);
 
 // the persistent fit kernel compiled for 4 or 5 resident blocks per SM (host entry address)
-const void *fit_kernel_func(int variant, int n_osc);
+const void *fit_kernel_func(int variant, int n_osc, bool pre);
 
 size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem);
 
@@ -97,8 +98,9 @@ size_t fit_smem_bytes(int floats);
 // Fit vectors are spaced by P rounded up to 4 floats, so that every vector starts on a
 // 16-byte boundary and the history can be read as float4.
 __host__ __device__ inline int fit_vec_pitch(int P) { return (P + 3) & ~3; }
-__host__ __device__ inline int fit_vec_floats(int P, int hist) { return (12 + 2 * hist) * fit_vec_pitch(P); }
+constexpr int kMaxPreRank = 32;   // eigen-directions of the Fisher preconditioner
+__host__ __device__ inline int fit_vec_floats(int P, int hist) { return (14 + 2 * hist) * fit_vec_pitch(P); }
 __host__ __device__ inline int fit_hist_floats(int P, int hist) { return 2 * hist * fit_vec_pitch(P); }
-__host__ __device__ inline int fit_work_floats(int P) { return 12 * fit_vec_pitch(P); }
+__host__ __device__ inline int fit_work_floats(int P) { return 14 * fit_vec_pitch(P); }
 
 }  // namespace fitcore

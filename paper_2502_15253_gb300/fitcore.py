@@ -59,7 +59,7 @@ class fit_batch_opts(C.Structure):
     _fields_ = [("edm_tol", C.c_double), ("max_iter", C.c_int), ("history", C.c_int),
                 ("f_noise_rel", C.c_double), ("threads", C.c_int), ("blocks_per_sm", C.c_int),
                 ("use_graph", C.c_int), ("time_budget_s", C.c_double), ("restarts", C.c_int),
-                ("placement", C.c_int), ("engine", C.c_int), ("pad", C.c_int)]
+                ("placement", C.c_int), ("engine", C.c_int), ("precondition", C.c_int)]
 
 
 class fit_result(C.Structure):
