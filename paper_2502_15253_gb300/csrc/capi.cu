@@ -1485,7 +1485,7 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
         return fitcore::fit_smem_bytes(0);
     };
     // the preconditioned build when asked for and every model has its preconditioner
-    bool precond = o.precondition != 0 && fixed == nullptr;
+    bool precond = o.precondition != 0;
     if (precond) {
         std::lock_guard<std::mutex> plock(g_pre_mutex);
         for (int i = 0; i < n_models; ++i) {

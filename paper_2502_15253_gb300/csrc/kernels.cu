@@ -472,8 +472,12 @@ __device__ __forceinline__ void hold_fixed(const uint8_t *fixed, float *gz, int 
 // y = x + Q (coef o (Q^T x)) for the model's preconditioner (coef = pre_c: y = T x; coef =
 // pre_c + r: y = T^-1 x). Q^T rows: a warp per row, 16-byte loads, the last P mod 4 entries
 // scalar (the padding of x is never read); then a thread per entry over the r rows. x and y
-// may be the same vector. u: r floats of shared scratch. Ends with a barrier.
-__device__ void pre_apply(const DevModel &m, const float *coef, const float *x, float *y, float *u) {
+// may be the same vector. u: r floats of shared scratch. Held parameters (fixed) are left out
+// of Q: T then maps them to themselves and mixes them into nothing, so they stay held in w
+// (T^-1 is then only approximate for the free part, which only moves the start). Ends with a
+// barrier.
+__device__ void pre_apply(const DevModel &m, const float *coef, const float *x, float *y, float *u,
+                          const uint8_t *fixed) {
     const int P = m.P, Pp = fit_vec_pitch(P), r = m.pre_r;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nfull = P >> 2;
@@ -483,10 +487,19 @@ __device__ void pre_apply(const DevModel &m, const float *coef, const float *x, 
         const float4 *q4 = reinterpret_cast<const float4 *>(q);
         float acc = 0.f;
         for (int c = lane; c < nfull; c += 32) {
-            const float4 a = __ldg(q4 + c), b = x4[c];
+            float4 a = __ldg(q4 + c);
+            const float4 b = x4[c];
+            if (fixed) {
+                const uint8_t *f = fixed + 4 * c;
+                if (f[0]) a.x = 0.f;
+                if (f[1]) a.y = 0.f;
+                if (f[2]) a.z = 0.f;
+                if (f[3]) a.w = 0.f;
+            }
             acc = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
         }
-        if (lane < (P & 3)) acc = fmaf(__ldg(q + 4 * nfull + lane), x[4 * nfull + lane], acc);
+        if (lane < (P & 3) && !(fixed && fixed[4 * nfull + lane]))
+            acc = fmaf(__ldg(q + 4 * nfull + lane), x[4 * nfull + lane], acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) u[k] = __ldg(coef + k) * acc;
@@ -494,8 +507,10 @@ __device__ void pre_apply(const DevModel &m, const float *coef, const float *x, 
     __syncthreads();
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         float acc = x[i];
+        if (!(fixed && fixed[i])) {
 #pragma unroll 8
-        for (int k = 0; k < r; ++k) acc = fmaf(__ldg(m.pre_Q + (int64_t)k * Pp + i), u[k], acc);
+            for (int k = 0; k < r; ++k) acc = fmaf(__ldg(m.pre_Q + (int64_t)k * Pp + i), u[k], acc);
+        }
         y[i] = acc;
     }
     __syncthreads();
@@ -524,11 +539,11 @@ __device__ double eval_z(const DevModel &m, const float *z, float *gz, FitVecs &
 // The same in the preconditioned coordinates w (z = T w): -2lnL and g_w = T^T g_z.
 template <int NOSC>
 __device__ double eval_w(const DevModel &m, const float *w, float *gw, FitVecs &V, EvalWs ws,
-                         const float *data, uint32_t mask, FitSmem &S) {
-    pre_apply(m, m.pre_c, w, V.zw, S.pre_u);
-    const double f = eval_z<NOSC>(m, V.zw, V.gzw, V, ws, data, mask, S, nullptr);
+                         const float *data, uint32_t mask, FitSmem &S, const uint8_t *fixed) {
+    pre_apply(m, m.pre_c, w, V.zw, S.pre_u, fixed);
+    const double f = eval_z<NOSC>(m, V.zw, V.gzw, V, ws, data, mask, S, fixed);
     __syncthreads();
-    pre_apply(m, m.pre_c, V.gzw, gw, S.pre_u);   // T is symmetric
+    pre_apply(m, m.pre_c, V.gzw, gw, S.pre_u, fixed);   // T is symmetric; held entries stay 0
     return f;
 }
 
@@ -951,17 +966,17 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
             __syncthreads();
         } else {
             start_z(m, A.start ? A.start + in.param_off : nullptr, V.zt, V.pd);
-            if (pre) pre_apply(m, m.pre_c + m.pre_r, V.zt, V.zt, S.pre_u);   // w0 = T^-1 z0
+            const uint8_t *fx = A.fixed ? A.fixed + in.param_off : nullptr;
+            if (pre) pre_apply(m, m.pre_c + m.pre_r, V.zt, V.zt, S.pre_u, fx);   // w0 = T^-1 z0
             while (true) {
-                const double fa = pre ? eval_w<NOSC>(m, V.zt, V.gt, V, ws, data, in.mask, S)
-                                      : eval_z<NOSC>(m, V.zt, V.gt, V, ws, data, in.mask, S,
-                                                     A.fixed ? A.fixed + in.param_off : nullptr);
+                const double fa = pre ? eval_w<NOSC>(m, V.zt, V.gt, V, ws, data, in.mask, S, fx)
+                                      : eval_z<NOSC>(m, V.zt, V.gt, V, ws, data, in.mask, S, fx);
                 if (!fit_decide(S, V, P, fa, F)) break;
             }
         }
         const float *zres = V.z;
         if (pre) {   // back to z = T w
-            pre_apply(m, m.pre_c, V.z, V.zw, S.pre_u);
+            pre_apply(m, m.pre_c, V.z, V.zw, S.pre_u, A.fixed ? A.fixed + in.param_off : nullptr);
             zres = V.zw;
         }
         write_result(m, S.st, zres, A.best + in.param_off, A.results + ii,
