@@ -356,10 +356,11 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
     }
 
 
-# DRAM bytes (read + write) per fit of fit_kernel on the three-dataset model, from an ncu capture
-# of one 760-fit launch (7.30 MB read, 47.86 MB written: the workspace write-back); traffic
-# grows with the fits
-FIT_DRAM_BYTES_PER_FIT = (7.301632e6 + 47.855360e6) / 760
+# DRAM bytes (read + write) per fit of fit_kernel on the three-dataset model, from ncu captures
+# of one 760-fit launch each: the preconditioned build (default; 4.28 MB read, 14.82 MB written,
+# mostly the workspace write-back) and the plain one (7.30 MB, 47.86 MB); traffic grows with
+# the fits
+FIT_DRAM_BYTES_PER_FIT = {1: (4.278272e6 + 14.816768e6) / 760, 0: (7.301632e6 + 47.855360e6) / 760}
 
 # DRAM bytes (read + write) per event of mc_spectrum_kernel for one parameter set, from an ncu
 # capture of 11,904,680 events (154.81 MB read, 3.62 MB written); traffic grows with the events
@@ -723,7 +724,7 @@ def run_ours(args):
             "converged_frac": conv,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                         "traffic": FIT_DRAM_BYTES_PER_FIT * B,
+                         "traffic": FIT_DRAM_BYTES_PER_FIT[1 if opts.precondition else 0] * B,
                          "traffic_note": "DRAM read+write bytes per fit of an ncu capture of "
                                          "this kernel (760 fits), scaled to the launch",
                          "kernel": "fit_kernel",

@@ -159,6 +159,32 @@ def test_fit_c0_and_c2_spline_match_oracle(engine):
         check_against_oracle(name, datas, masks, th, res)
 
 
+def test_plain_coordinates_match_oracle():
+    """Fits without the Fisher preconditioner (plain whitened coordinates, the lockstep
+    engine's and the option precondition = 0) on the three-dataset and the 53 km model."""
+    o = fitcore.fit_batch_default_opts()
+    o.precondition = 0
+    datas, masks, _ = make_instances("c1", 16, 740, masks=list(synth.C1_MASKS))
+    th, res = run_gpu(["c1"] * 16, datas, masks, opts=o)
+    check_against_oracle("c1", datas, masks, th, res)
+    datas, masks, _ = make_instances("c2", 2, 750)
+    th, res = run_gpu(["c2"] * 2, datas, masks, opts=o)
+    check_against_oracle("c2", datas, masks, th, res)
+
+
+def test_preconditioned_and_plain_fits_agree_on_smooth_models():
+    """On a model without kinks (spline correction) both coordinate systems reach the same
+    minimum of every pseudo-experiment; the preconditioned one in fewer iterations."""
+    datas, masks, _ = make_instances("c1/spline", 64, 760)
+    o0 = fitcore.fit_batch_default_opts()
+    o0.precondition = 0
+    th0, r0 = run_gpu(["c1/spline"] * 64, datas, masks, opts=o0)
+    th1, r1 = run_gpu(["c1/spline"] * 64, datas, masks)
+    assert np.all(r0["status"] == 0) and np.all(r1["status"] == 0)
+    assert np.max(np.abs(r0["nll_min"] - r1["nll_min"])) <= 1e-3
+    assert r1["iters"].mean() < 0.6 * r0["iters"].mean()
+
+
 def test_fit_c1_on_the_41_bin_flux_grid():
     """Signal shape parameters on the uniform 41-bin flux grid (3 x 41, eight per dataset
     without data: prior only) instead of the reco binning."""
