@@ -319,6 +319,23 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
     fold_flops = 2.0 * fb * n_t * sum(spec2.detectors[d.det].n_reco for d in spec2.datasets)
     tf32_peak = bf16_peak * 1.1 / 2.25
 
+    # the fold's tensor-core GEMM alone at the same shape: V [fb x N_t'] (FP32 read as TF32)
+    # times the far detector's response [400 x N_t']^T
+    ldk = (n_t + 3) // 4 * 4
+    Va = torch.rand((fb, ldk), dtype=torch.float32, device=dev)
+    Rb = torch.rand((400, ldk), dtype=torch.float32, device=dev)
+    Cc = torch.empty((fb, 400), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        fitcore.fit_tc_gemm(1, fb, 400, n_t, Va, ldk, Rb, ldk, 0, Cc, 400, stream=stream)
+    ev0.record(stream)
+    for _ in range(10):
+        fitcore.fit_tc_gemm(1, fb, 400, n_t, Va, ldk, Rb, ldk, 0, Cc, 400, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    gemm_ms = ev0.elapsed_time(ev1) / 10
+    gemm_tflops = 2.0 * fb * 400 * n_t / (gemm_ms / 1e3) / 1e12
+    del Va, Rb, Cc
+
     # warm fits of the benchmark's pseudo-experiments
     starts = torch.zeros((B, P), dtype=torch.float64, device=dev)
     flush.fill_(0.5)
@@ -346,7 +363,12 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
                            "unit": "TFLOP/s", "peak": tf32_peak,
                            "frac": fold_flops / fold_ms / 1e9 / tf32_peak,
                            "peak_note": "measured bf16 burst x 1.1/2.25 (nominal tf32/bf16)",
-                           "timed": "whole fit_model_expected_tc call (spectra, GEMMs, epilogue)"},
+                           "timed": "whole fit_model_expected_tc call (spectra, GEMMs, epilogue); "
+                                    "the spectra kernel (survival at 2000 bins x 10 cores per "
+                                    "instance and detector) dominates"},
+        "fold_gemm_tf32_alone": {"M": fb, "N": 400, "K": n_t, "ms": gemm_ms, "achieved": gemm_tflops,
+                                 "unit": "TFLOP/s", "peak": tf32_peak, "frac": gemm_tflops / tf32_peak,
+                                 "bound": "tensor", "kernel": "tc_gemm_kernel<TF32>"},
         "fits_per_s_warm": world * B / (warm_ms / 1e3),
         "warm_ms_incl_inference": warm_ms,
         "iters_per_fit_warm": float(rw["iters"].mean()),

@@ -27,7 +27,8 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(b);
 }
 
-// One block per (instance b, dataset d): survival x reweights on the true grid, energy
+// One block per (instance b, dataset d): survival (FP32 float-pair phases and the fitted
+// sin^2(pi r) polynomial, as the event kernel) x reweights on the true grid, energy
 // correction gathered per target bin, written as V_hi / V_lo rows of length ldt. Blocks of
 // dataset 0 also store the instance's parameter pairs for the epilogue.
 __global__ void __launch_bounds__(256) signal_v_kernel(const DevModel *__restrict__ gm, int B,
@@ -102,19 +103,37 @@ __global__ void __launch_bounds__(256) signal_v_kernel(const DevModel *__restric
     }
     __syncthreads();
     const OscCoefN<6> kc6 = kco;
-    OscCoef kc;
-    float eta4[4], eta_lo4[4];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        kc.hi[i] = kc6.hi[i];
-        kc.lo[i] = kc6.lo[i];
+    // the phases of the sin^2 terms in the order of the coefficients: Eq. 1: x_ee, x_21;
+    // three-flavour: x_21, x_31, x_32; 3+1: and x_41, x_42, x_43 (mass splittings as float pairs)
+    float pdm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, pdl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int nph;
+    {
+        // normalised pairs: sin2_phase needs the low part to stay below an ulp of the high one
+        // (the parameter offset sits in eta_lo here), so that the reduced phase is within 1/2
+        auto pr = [&](int i) { return f2_norm(eta[i], eta_lo[i]); };
+        auto sub = [](F2 a, F2 b) { return f2_add(a, F2{-b.h, -b.l}); };
+        F2 d[6];
+        if (m.osc_mode == FIT_OSC_EQ1) {
+            nph = 2;
+            d[0] = pr(1);
+            d[1] = pr(3);
+        } else {
+            nph = 3;
+            d[0] = pr(2);
+            d[1] = pr(3);
+            d[2] = sub(pr(3), pr(2));
+            if (m.osc_mode == FIT_OSC_STERILE4) {
+                nph = 6;
+                d[3] = pr(5);
+                d[4] = sub(pr(5), pr(2));
+                d[5] = sub(pr(5), pr(3));
+            }
+        }
+        for (int i = 0; i < nph; ++i) {
+            pdm[i] = d[i].h;
+            pdl[i] = d[i].l;
+        }
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        eta4[i] = eta[i];
-        eta_lo4[i] = eta_lo[i];
-    }
-    const bool sterile = m.osc_mode == FIT_OSC_STERILE4;
     const PP nrm = ppair(m, pv, pd, ds.norm_idx, 1.f);
     const EMap em = make_emap(m, ds, pv, pd);
     {
@@ -136,14 +155,12 @@ __global__ void __launch_bounds__(256) signal_v_kernel(const DevModel *__restric
             if (w == 0.f) continue;
             const float ch = ds.kl_hi[c] * ih;
             const float cl = fmaf(ds.kl_hi[c], ih, -ch) + ds.kl_hi[c] * il + ds.kl_lo[c] * ih;
-            float P;
-            if (sterile) {
-                float dP[6];
-                P = survival_sterile(eta, eta_lo, kc6, ch, cl, dP);
-            } else {
-                float dP[4];
-                P = survival(m, eta4, eta_lo4, kc, ch, cl, dP);
-            }
+            // P = 1 - sum_i C_i sin^2(x_i) with the fitted sin^2(pi r) polynomial (no
+            // derivatives are needed here)
+            float P = 1.f;
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                if (i < nph) P -= cterm(kc6, i, sin2_phase(pdm[i], pdl[i], ch, cl));
             pt += pmul(ppair(m, pv, pd, m.core_power_idx[c], 1.f), w * P);
         }
         const float ts = pmul(ppair(m, pv, pd, ds.shape_idx[k], 1.f), ds.t[k]);

@@ -168,6 +168,31 @@ __device__ __forceinline__ void phase_sc(float dm, float dm_lo, float c_hi, floa
     sincospif(r, &s, &c);
 }
 
+// sin^2(pi r) for |r| <= 1/2: u q(u), u = r^2, q a degree-7 polynomial fitted for the
+// smallest largest absolute error (Lawson iteration; sin2pi_fit.py in this directory). Its
+// FP32 evaluation is within 1.8e-7 of sin^2.
+__device__ __forceinline__ float sin2pi(float r) {
+    const float u = r * r;
+    float q = -0.122019291f;
+    q = fmaf(q, u, 0.848584056f);
+    q = fmaf(q, u, -3.94964409f);
+    q = fmaf(q, u, 13.2128229f);
+    q = fmaf(q, u, -30.1222954f);
+    q = fmaf(q, u, 42.7284088f);
+    q = fmaf(q, u, -32.469696f);
+    q = fmaf(q, u, 9.86960411f);
+    return u * q;
+}
+
+// sin^2 of the phase pi (dm + dm_lo)(c_hi + c_lo): the half-turn count reduced by its nearest
+// integer as in the binned evaluation. Both pairs normalised (|low| <= ulp(high) / 2), so the
+// reduced phase stays within 1/2 (the polynomial's range) up to rounding.
+__device__ __forceinline__ float sin2_phase(float dm, float dm_lo, float c_hi, float c_lo) {
+    const float yh = dm * c_hi;
+    const float yl = fmaf(dm, c_hi, -yh) + fmaf(dm, c_lo, dm_lo * c_hi);
+    return sin2pi((yh - rintf(yh)) + yl);
+}
+
 // Coefficients of the sin^2 terms of P, formed once per evaluation in double from the exact
 // parameter values and applied as float pairs (a single FP32 rounding of a coefficient would
 // bias every bin coherently).

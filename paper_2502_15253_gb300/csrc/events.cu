@@ -118,30 +118,6 @@ __device__ McSet make_set(int mode, const double *p) {
     return s;
 }
 
-// sin^2(pi r) for |r| <= 1/2: u q(u), u = r^2, q a degree-7 polynomial fitted for the
-// smallest largest absolute error (Lawson iteration; sin2pi_fit.py in this directory). Its
-// FP32 evaluation is within 1.8e-7 of sin^2.
-__device__ __forceinline__ float sin2pi(float r) {
-    const float u = r * r;
-    float q = -0.122019291f;
-    q = fmaf(q, u, 0.848584056f);
-    q = fmaf(q, u, -3.94964409f);
-    q = fmaf(q, u, 13.2128229f);
-    q = fmaf(q, u, -30.1222954f);
-    q = fmaf(q, u, 42.7284088f);
-    q = fmaf(q, u, -32.469696f);
-    q = fmaf(q, u, 9.86960411f);
-    return u * q;
-}
-
-// sin^2 of the phase pi (dm + dm_lo)(c_hi + c_lo): the half-turn count reduced by its nearest
-// integer as in the binned evaluation.
-__device__ __forceinline__ float sin2_phase(float dm, float dm_lo, float c_hi, float c_lo) {
-    const float yh = dm * c_hi;
-    const float yl = fmaf(dm, c_hi, -yh) + fmaf(dm, c_lo, dm_lo * c_hi);
-    return sin2pi((yh - rintf(yh)) + yl);
-}
-
 // P(L, E) of one event for one set: 1 - sum_i C_i sin^2(x_i)
 template <int NPH>
 __device__ __forceinline__ float survival_ev(const McSet &S, float c_hi, float c_lo) {

@@ -8,10 +8,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_sin2pi_polynomial_of_the_event_kernel():
-    """The degree-7 polynomial in r^2 that the event kernel evaluates for sin^2(pi r) is within
-    2e-7 of the exact value over |r| <= 1/2 when evaluated as the kernel does (FP32 Horner with
-    fused multiply-adds), and its leading coefficient is pi^2 rounded to FP32."""
-    src = open(os.path.join(ROOT, "paper_2502_15253_gb300", "csrc", "events.cu")).read()
+    """The degree-7 polynomial in r^2 that the event and batched-expectation kernels evaluate
+    for sin^2(pi r) is within 2e-7 of the exact value over |r| <= 1/2 when evaluated as the
+    kernels do (FP32 Horner with fused multiply-adds), and its leading coefficient is pi^2
+    rounded to FP32."""
+    src = open(os.path.join(ROOT, "paper_2502_15253_gb300", "csrc", "dev_model.cuh")).read()
     body = src[src.index("float sin2pi(float r)"):]
     body = body[:body.index("return u * q;")]
     first = float(re.search(r"float q = (-?[\d.e+-]+)f;", body).group(1))
