@@ -572,9 +572,8 @@ __device__ __forceinline__ float spline_target(const float *u, const float *e_ed
 // plus the Hermite weights of u_i in G_{k_e}; the cumulative part sums to gv_{e*-1}, e* the
 // first edge with k_e > i.
 template <class Map>
-__device__ __forceinline__ float spline_adjoint_source(const float *u, const float *gv, const float *e_edge,
-                                                       const Map &em, int i, int N) {
-    (void)u;
+__device__ __forceinline__ float spline_adjoint_source(const float *gv, const float *e_edge, const Map &em,
+                                                       int i, int N) {
     auto kb = [&](int e, int &k, float &t) {
         bool in;
         edge_bin(e, edge_inv_r(e_edge, em, e), N, k, t, in);
@@ -672,17 +671,8 @@ template <int NOSC>
 static __device__ bool ds_setup(const DevModel &m, int d, const float *pv, const float *pd, DsCtxT<NOSC> &c,
                                 int *status) {
     const DevDataset &ds = m.ds[d];
-    const DevDetector &dt = m.det[ds.det];
-    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
-    (void)dt;
-    (void)N_t;
-    (void)C;
-    (void)nr;
-    (void)lane;
-    (void)warp;
-    (void)nw;
+    const int N_t = m.N_t;
+    const int tid = threadIdx.x;
     // Survival parameters: mass splittings as theta0_f + (theta0_lo + delta) inside the
     // phase.
     float *eta = c.eta, *eta_lo = c.eta_lo;
@@ -733,17 +723,8 @@ template <bool DERIV, int NOSC>
 static __device__ void ds_signal(const DevModel &m, int d, const float *pv, const float *pd,
                                  const DsCtxT<NOSC> &c, EvalWs ws) {
     const DevDataset &ds = m.ds[d];
-    const DevDetector &dt = m.det[ds.det];
-    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
+    const int N_t = m.N_t, C = m.C;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
-    (void)dt;
-    (void)N_t;
-    (void)C;
-    (void)nr;
-    (void)lane;
-    (void)warp;
-    (void)nw;
     // ---- stage A: signal on the true grid (Eq. 1/2 x shares x reweights) -----------------
     for (int k = tid; k < N_t; k += nth) {
         const float ih = m.inv_e_hi[k], il = m.inv_e_lo[k];
@@ -785,18 +766,9 @@ static __device__ void ds_signal(const DevModel &m, int d, const float *pv, cons
 // SPL: compiled with the area-conserving spline option (the general kernel builds)
 template <bool SPL, class Ctx>
 static __device__ void ds_remap(const DevModel &m, int d, const Ctx &c, EvalWs ws) {
-    const DevDataset &ds = m.ds[d];
-    const DevDetector &dt = m.det[ds.det];
-    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
+    (void)d;   // the energy map is in c
+    const int N_t = m.N_t;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
-    (void)dt;
-    (void)N_t;
-    (void)C;
-    (void)nr;
-    (void)lane;
-    (void)warp;
-    (void)nw;
     const EMap &em = c.em;
     if (SPL && m.remap_mode == FIT_REMAP_SPLINE) {
         for (int t = tid; t < N_t; t += nth) ws.v[t] = spline_target(ws.u, m.e_edge, em, t, N_t);
@@ -841,16 +813,9 @@ static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, 
                                      float *mu_out) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
-    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
+    const int nr = ds.n_reco;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
-    (void)dt;
-    (void)N_t;
-    (void)C;
-    (void)nr;
-    (void)lane;
-    (void)warp;
-    (void)nw;
     // ---- stage C: fold into reco bins (banded rows, warp per row) ------------------------
     // Each warp takes four rows at a time and two strides of each, so eight independent
     // load/FMA chains per lane are in flight.
@@ -956,14 +921,6 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
     const DevDetector &dt = m.det[ds.det];
     const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
-    (void)dt;
-    (void)N_t;
-    (void)C;
-    (void)nr;
-    (void)lane;
-    (void)warp;
-    (void)nw;
     const EMap &em = c.em;
     // ---- stage D: adjoint of the fold, gv = eff R^T gmu (column bands) --------------------
     float *gv = ws.v;   // v is dead after the fold
@@ -995,7 +952,7 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
     for (int k = tid; k < N_t; k += nth) {
         float gu = 0.f;
         if (spline) {
-            gu = spline_adjoint_source(ws.u, gv, m.e_edge, em, k, N_t);
+            gu = spline_adjoint_source(gv, m.e_edge, em, k, N_t);
             spline_adjoint_edge(ws.u, gv, m.e_edge, em, k, N_t, ep);
             if (k == N_t - 1) spline_adjoint_edge(ws.u, gv, m.e_edge, em, N_t, N_t, ep);
         } else {
