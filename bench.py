@@ -635,7 +635,7 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts = fitcore.fit_batch_default_opts()
     opts.engine = 1 if args.engine == "lockstep" else 0
-    opts.precondition = 0 if (args.no_precondition or args.engine == "lockstep") else 1
+    opts.precondition = 0 if args.no_precondition else 1
 
     def step():
         fitcore.fit_batch([model], inst, data_d, None, best_d, res_d, opts, stream)

@@ -201,8 +201,7 @@ typedef struct fit_batch_opts {
                              coordinates: the expected Hessian of -2lnL at the model's nominal
                              point, built once per model on first use, makes the quasi-Newton
                              problem nearly isotropic (fewer iterations); 0 = plain whitened
-                             coordinates. Held parameters are left out of the transform.
-                             Not applied on the lockstep engine.                              */
+                             coordinates. Held parameters are left out of the transform.    */
 } fit_batch_opts;
 
 /* Result of one instance. */

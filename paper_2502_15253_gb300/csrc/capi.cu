@@ -1055,7 +1055,7 @@ int graph_launch(const void *kern, int grid, int threads, size_t smem, fitcore::
 int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst,
                        const float *data, const double *start, const uint8_t *fixed, double *best,
                        fit_result *results, const fit_batch_opts &o, cudaStream_t s, int64_t data_len,
-                       int64_t par_len) {
+                       int64_t par_len, bool precond) {
     LaunchCfg cfg;
     int rc = device_cfg(cfg);
     if (rc) return rc;
@@ -1094,6 +1094,7 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
         A.edm_tol = o.edm_tol;
         A.f_noise_rel = o.f_noise_rel;
         A.budget_ns = (uint64_t)(o.time_budget_s * 1e9);
+        A.precond = precond && models[mi]->pre_state == 1 ? 1 : 0;
         // evaluation workspace: the adjoint needs the full per-dataset arrays
         const int ws_floats = h.ws_eval_floats;
         const size_t eval_smem = fitcore::ls_eval_smem_bytes(P, ws_floats);
@@ -1384,6 +1385,13 @@ int build_preconditioner(fit_model *M, cudaStream_t s) {
     M->host.pre_Q = dev;
     M->host.pre_c = dev + (size_t)r * Pp;
     M->host.pre_r = r;
+    // the device copy of the model too (the lockstep kernels read it)
+    if (cudaMemcpy(M->dev, &M->host, sizeof(DevModel), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        M->host.pre_Q = M->host.pre_c = nullptr;
+        M->host.pre_r = 0;
+        return FIT_OK;
+    }
     M->pre_state = 1;
     return FIT_OK;
 }
@@ -1457,8 +1465,15 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
                                                          " of a prior block cannot be held fixed");
         }
     }
-    if (o.engine == 1) return fit_batch_lockstep(models, n_models, inst, n_inst, data, start, fixed, best, results,
-                                                 o, s, data_len, par_len);
+    if (o.engine == 1) {
+        bool pre = o.precondition != 0;
+        if (pre) {
+            std::lock_guard<std::mutex> plock(g_pre_mutex);
+            for (int i = 0; i < n_models; ++i) build_preconditioner(models[i], s);
+        }
+        return fit_batch_lockstep(models, n_models, inst, n_inst, data, start, fixed, best, results, o, s,
+                                  data_len, par_len, pre);
+    }
     if (o.engine != 0) return fail(FIT_ERR_INVALID_ARG, "fit_batch: engine must be 0 or 1");
     int max_loc = 0;   // working vectors + evaluation workspace, without the history
     int n_osc = 4;     // the general build when any model uses the 3+1 formula or the spline

@@ -1040,7 +1040,14 @@ __global__ void __launch_bounds__(128) ls_init_kernel(LsArgs A) {
         const fit_instance in = A.inst[A.group[g]];
         FitVecs V = ls_vecs(A, g, P);
         start_z(m, A.start ? A.start + in.param_off : nullptr, V.zt, V.pd);
-        theta_of_z(m, V.zt, V.pv, V.pd);
+        if (A.precond) {   // w0 = T^-1 z0; the trial's z = T w0 is kept in zw
+            const uint8_t *fx = A.fixed ? A.fixed + in.param_off : nullptr;
+            pre_apply(m, m.pre_c + m.pre_r, V.zt, V.zt, S.pre_u, fx);
+            pre_apply(m, m.pre_c, V.zt, V.zw, S.pre_u, fx);
+            theta_of_z(m, V.zw, V.pv, V.pd);
+        } else {
+            theta_of_z(m, V.zt, V.pv, V.pd);
+        }
         for (int i = threadIdx.x; i < nd * P; i += blockDim.x) A.gsl[(int64_t)g * nd * P + i] = 0.f;
         if (threadIdx.x == 0) {
             init_state(S.st);
@@ -1192,23 +1199,38 @@ __global__ void __launch_bounds__(128) ls_step_kernel(LsArgs A) {
         for (int d = 0; d < nd; ++d)
             if ((in.mask >> d) & 1u) fa += A.nll_ds[(int64_t)g * nd + d];
         __syncthreads();
+        const uint8_t *fx = A.fixed ? A.fixed + in.param_off : nullptr;
         if (st != 0) {
             fa = INFINITY;
+        } else if (A.precond) {   // z of the trial in zw; g_w = T g_z
+            fa += eval_z_prior(m, V.zw, V.gth, V.gzw, S.red);
+            hold_fixed(fx, V.gzw, P);
+            __syncthreads();
+            pre_apply(m, m.pre_c, V.gzw, V.gt, S.pre_u, fx);
         } else {
             fa += eval_z_prior(m, V.zt, V.gth, V.gt, S.red);
-            hold_fixed(A.fixed ? A.fixed + in.param_off : nullptr, V.gt, P);
+            hold_fixed(fx, V.gt, P);
         }
         const bool more = fit_decide(S, V, P, fa, F);
         if (more) {
-            theta_of_z(m, V.zt, V.pv, V.pd);
+            if (A.precond) {
+                pre_apply(m, m.pre_c, V.zt, V.zw, S.pre_u, fx);
+                theta_of_z(m, V.zw, V.pv, V.pd);
+            } else {
+                theta_of_z(m, V.zt, V.pv, V.pd);
+            }
             if (threadIdx.x == 0) {
                 A.stat[g] = 0;
                 A.act_next[atomicAdd(A.n_act_next, 1)] = g;
             }
         } else {
-            write_result(m, S.st, V.z, A.best + in.param_off, A.results + ii,
-                         A.start ? A.start + in.param_off : nullptr,
-                         A.fixed ? A.fixed + in.param_off : nullptr);
+            const float *zres = V.z;
+            if (A.precond) {   // back to z = T w
+                pre_apply(m, m.pre_c, V.z, V.zw, S.pre_u, fx);
+                zres = V.zw;
+            }
+            write_result(m, S.st, zres, A.best + in.param_off, A.results + ii,
+                         A.start ? A.start + in.param_off : nullptr, fx);
         }
         __syncthreads();
         copy_state(A.state + g, &S.st);

@@ -64,6 +64,7 @@ struct LsArgs {
     double edm_tol, f_noise_rel;
     uint64_t budget_ns;
     uint64_t *deadline;          // device: set by the init kernel
+    int precond;                 // 1: fit in the model's preconditioned coordinates
 };
 
 __global__ void ls_init_kernel(LsArgs A);
