@@ -1089,7 +1089,7 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
         A.vec_stride = ((int64_t)fitcore::fit_vec_floats(P, o.history) + 3) / 4 * 4;
         A.hist = o.history;
         A.max_iter = o.max_iter;
-        A.max_ls = 30;
+        A.max_ls = 8;
         A.restarts = o.restarts;
         A.edm_tol = o.edm_tol;
         A.f_noise_rel = o.f_noise_rel;
@@ -1579,7 +1579,7 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
         a.n_inst = n_inst;
         a.hist = o.history;
         a.max_iter = o.max_iter;
-        a.max_ls = 30;
+        a.max_ls = 8;
         a.restarts = o.restarts;
         a.edm_tol = o.edm_tol;
         a.f_noise_rel = o.f_noise_rel;

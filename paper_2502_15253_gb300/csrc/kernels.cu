@@ -150,6 +150,7 @@ size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem) {
 // ------------------------------------------------------------------------------------
 constexpr int kMaxHist = 32;
 constexpr int kStallWindow = 100;   // iterations per stall check
+constexpr int kMaxLsFresh = 30;     // line-search trials along steepest descent
 constexpr int kNDots = 4 * kMaxHist + 1;
 
 // Minimiser state of one fit between two evaluations: in shared memory while a block works on
@@ -669,7 +670,10 @@ __device__ bool fit_decide(FitSmem &S, FitVecs &V, int P, double fa, const FitPa
                 alpha = ls_interp(lo, flo, dlo, hi, fhi, dhi, eps_f);
                 if (hi - lo <= 1e-7 * hi) stop = true;
             }
-            if (!stop && ++ls_it < F.max_ls) next = kTrial;
+            // a quasi-Newton direction is well scaled (the unit step is usually right), so its
+            // search stops after max_ls trials; a steepest-descent search (fresh history) has
+            // to find the scale and gets kMaxLsFresh
+            if (!stop && ++ls_it < (st.hn == 0 ? kMaxLsFresh : F.max_ls)) next = kTrial;
         }
         if (next != kTrial) {
             if (!accepted) {
