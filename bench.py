@@ -379,14 +379,14 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
 
 
 # DRAM bytes (read + write) per fit of fit_kernel on the three-dataset model, from ncu captures
-# of one 760-fit launch each: the preconditioned build (default; 4.28 MB read, 14.82 MB written,
+# of one 760-fit launch each: the preconditioned build (default; 4.39 MB read, 14.58 MB written,
 # mostly the workspace write-back) and the plain one (7.30 MB, 47.86 MB); traffic grows with
 # the fits
-FIT_DRAM_BYTES_PER_FIT = {1: (4.278272e6 + 14.816768e6) / 760, 0: (7.301632e6 + 47.855360e6) / 760}
+FIT_DRAM_BYTES_PER_FIT = {1: (4.394240e6 + 14.576896e6) / 760, 0: (7.301632e6 + 47.855360e6) / 760}
 
 # DRAM bytes (read + write) per event of mc_spectrum_kernel for one parameter set, from an ncu
 # capture of 11,904,680 events (154.81 MB read, 3.62 MB written); traffic grows with the events
-MC_DRAM_BYTES_PER_EVENT = (154.809088e6 + 3.621632e6) / 11_904_680
+MC_DRAM_BYTES_PER_EVENT = (154.811136e6 + 3.620096e6) / 11_904_680
 
 
 def event_reweighting_measurement(args, stream, pg, world):
