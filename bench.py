@@ -57,7 +57,7 @@ def parse():
 
 
 # ---------------------------------------------------------------------------------------
-# algorithmic work model (FP32 operations of one evaluation + gradient, see DESIGN.md)
+# algorithmic work model (FP32 operations of one evaluation + gradient)
 # ---------------------------------------------------------------------------------------
 def flops_per_eval(spec, mask) -> float:
     """Algorithmic FP32 FLOPs of one -2lnL + gradient evaluation of one instance."""
