@@ -38,7 +38,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--batch", type=int, default=8192, help="fits per rank per step")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--cpu-sample", type=int, default=48, help="instances of the CPU baseline")
+    p.add_argument("--cpu-sample", type=int, default=2560,
+                   help="instances of the CPU baseline (about 10 s of the FP64 oracle on 16 cores)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=250215253)
     p.add_argument("--engine", default="persistent", choices=["persistent", "lockstep"],

@@ -72,3 +72,30 @@ def test_event_set_rejects_unsorted_bins_on_the_host():
     rc = L.fit_mc_create(0, 1, Lc.ctypes.data, 3, e.ctypes.data, c.ctypes.data, w.ctypes.data,
                          b.ctypes.data, 3, C.byref(h))
     assert rc != 0
+
+
+def _create_error(spec):
+    """fit_model_create on a description the library must reject before touching the device."""
+    import pytest
+    with pytest.raises(fitcore.FitError) as e:
+        fitcore.Model(spec)
+    return str(e.value)
+
+
+def test_model_options_are_validated_on_the_host():
+    import copy
+    from paper_2502_15253_gb300 import synth
+    base = synth.make_model("c0")
+    s = copy.deepcopy(base)
+    s.remap = 7
+    assert "remap_mode" in _create_error(s)
+    s = copy.deepcopy(base)
+    s.osc_mode = 5
+    assert "osc_mode" in _create_error(s)
+    # the 3+1 formula with a held sin^2 2th14 outside [0, 1)
+    s = copy.deepcopy(synth.make_model("c1s"))
+    s.osc_idx = s.osc_idx.copy()
+    s.osc_val = s.osc_val.copy()
+    s.osc_idx[4] = -1
+    s.osc_val[4] = 1.5
+    assert "2th14" in _create_error(s)
