@@ -150,6 +150,32 @@ int fit_model_create(const fit_model_desc *desc, fit_model **out);
 void fit_model_destroy(fit_model *model);
 int fit_model_info(const fit_model *model, fit_model_info_t *info);
 
+/* Builds a model from a JSON configuration ([S]: the framework's first component reads a
+ * configuration file naming the parameters, their priors and the datasets). `json` is a
+ * NUL-terminated UTF-8 string (host memory, read during the call only). Schema (fields in
+ * brackets are optional; a parameter reference is a name string, an index, or null = held
+ * at its nominal value as in fit_model_desc):
+ *   parameters:  [{name, value, [sigma], [scale]}, ...]        -> theta0, prior_sigma, scale
+ *   [covariances]: [{params: [ref, ...], cov: [[...], ...]}]   -> Eq. 6 blocks
+ *   oscillation: {formula: "eq1" | "vacuum3" | "sterile4",
+ *                 params: [4 or 6 entries: a parameter name, or a number = held constant]}
+ *   true_grid:   {bins, e_lo, e_hi}          [energy_correction]: "overlap" (default) | "spline"
+ *   core_powers: [ref per reactor core]
+ *   detectors:   [{[name], response: [[n_true numbers] per reco bin]}]
+ *   datasets:    [{detector: name | index, t: [n_true], baseline: [C], weight: [C],
+ *                  [norm], [efficiency], [escale: [a0, a1, a2]], [shape: [n_true refs]],
+ *                  [backgrounds: [{template: [N_r], [rate], [shape: [N_r refs]]}]]}]
+ * Backgrounds take the order datasets, then their lists. Unknown keys are ignored. The model
+ * keeps the parameter names (fit_model_param_name).
+ * Errors: INVALID_ARG (null), INVALID_CONFIG (malformed JSON with its byte offset, a missing
+ * or mistyped field, an unknown name, a size mismatch; the message names the field), then
+ * those of fit_model_create. All configuration errors are found before any device call. */
+int fit_model_create_json(const char *json, fit_model **out);
+
+/* Name of parameter i of a model created by fit_model_create_json; NULL for a model created
+ * from a fit_model_desc or for i out of range. The string lives as long as the model. */
+const char *fit_model_param_name(const fit_model *model, int i);
+
 /* Expected counts mu ([L], [S]) for B parameter vectors.
  * theta: host or device, [B x P] double. mu_out: host or device, [B x n_data] float.
  * status_out: host or device [B] int (FIT_STATUS_*) or NULL. */

@@ -173,6 +173,7 @@ struct fit_model {
     // Fisher preconditioner (built on first use): device matrices T, T^T, T^-1, state
     float *pre = nullptr;
     int pre_state = 0;     // 0 not built, 1 built, -1 failed (fits run unpreconditioned)
+    std::vector<std::string> names;   // parameter names (models created from a configuration)
 };
 
 // error / launch-count hooks for the other translation units of the library
@@ -186,6 +187,7 @@ int fitcore_model_device(fit_model *model, const DevModel **dev, const DevModel 
     return FIT_OK;
 }
 void fitcore_count_launch() { g_launches++; }
+void fitcore_model_set_names(fit_model *model, const std::vector<std::string> &names) { model->names = names; }
 
 extern "C" {
 
@@ -212,6 +214,11 @@ int fit_model_info(const fit_model *model, fit_model_info_t *info) {
     info->n_true = model->n_true;
     info->device_bytes = model->bytes;
     return FIT_OK;
+}
+
+const char *fit_model_param_name(const fit_model *model, int i) {
+    if (!model || i < 0 || i >= (int)model->names.size()) return nullptr;
+    return model->names[i].c_str();
 }
 
 static int launch_eval(fit_model *model, int B, const double *theta_d, const float *data_d,

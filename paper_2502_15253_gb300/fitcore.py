@@ -98,7 +98,7 @@ EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model
            "fit_warmstart_features", "fit_warmstart_predict", "fit_warmstart_draw",
            "fit_warmstart_train", "fit_batch_autotune", "fit_batch_ex", "fit_profile_scan",
            "fit_wilks_interval", "fit_chi2_sf", "fit_mc_create", "fit_mc_destroy",
-           "fit_mc_spectrum", "fit_mc_status")
+           "fit_mc_spectrum", "fit_mc_status", "fit_model_create_json", "fit_model_param_name")
 
 
 def lib_path() -> str:
@@ -173,6 +173,10 @@ def load(build_if_missing: bool = False):
     L.fit_mc_spectrum.restype = C.c_int
     L.fit_mc_status.argtypes = [vp]
     L.fit_mc_status.restype = C.c_int
+    L.fit_model_create_json.argtypes = [C.c_char_p, C.POINTER(vp)]
+    L.fit_model_create_json.restype = C.c_int
+    L.fit_model_param_name.argtypes = [vp, C.c_int]
+    L.fit_model_param_name.restype = C.c_char_p
     L.fit_last_error.restype = C.c_char_p
     L.fit_kernel_launches.restype = C.c_int64
     for f in ("fit_model_create", "fit_model_info", "fit_model_expected", "fit_model_eval",
@@ -216,11 +220,17 @@ def _stream_ptr(stream):
 
 
 class Model:
-    """A model resident on the current CUDA device (wraps fit_model*)."""
+    """A model resident on the current CUDA device (wraps fit_model*).
 
-    def __init__(self, spec):
+    Model(spec) builds it from a synth.ModelSpec through fit_model_create;
+    Model.from_json(text) from a JSON configuration through fit_model_create_json."""
+
+    def __init__(self, spec, _handle=None):
         L = load()
         self.spec = spec
+        if _handle is not None:
+            self._attach(_handle)
+            return
         keep = []
 
         def d(a):
@@ -270,11 +280,32 @@ class Model:
         m.bkg_shape_idx = i(np.concatenate([b.shape_idx for _, b in bk]) if bk else [0])
         h = C.c_void_p()
         _check(L.fit_model_create(C.byref(m), C.byref(h)), "fit_model_create")
+        self._attach(h)
+
+    def _attach(self, h):
         self.handle = h
         info = fit_model_info_t()
-        _check(L.fit_model_info(h, C.byref(info)), "fit_model_info")
+        _check(load().fit_model_info(h, C.byref(info)), "fit_model_info")
         self.n_params, self.n_data = info.n_params, info.n_data
         self.n_datasets, self.device_bytes = info.n_datasets, info.device_bytes
+
+    @classmethod
+    def from_json(cls, text, spec=None):
+        """Model from a JSON configuration (str, bytes or a dict); `spec` is kept as metadata."""
+        if isinstance(text, dict):
+            import json
+            text = json.dumps(text)
+        if isinstance(text, str):
+            text = text.encode()
+        h = C.c_void_p()
+        _check(load().fit_model_create_json(text, C.byref(h)), "fit_model_create_json")
+        return cls(spec, _handle=h)
+
+    def param_names(self):
+        """Parameter names kept by the library (None for a model built from a description)."""
+        L = load()
+        out = [L.fit_model_param_name(self.handle, i) for i in range(self.n_params)]
+        return None if out[0] is None else [x.decode() for x in out]
 
     def close(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -287,6 +318,10 @@ class Model:
 
 def fit_model_create(spec) -> Model:
     return Model(spec)
+
+
+def fit_model_create_json(text, spec=None) -> Model:
+    return Model.from_json(text, spec)
 
 
 def fit_model_destroy(model: Model):

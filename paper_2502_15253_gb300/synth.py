@@ -138,6 +138,48 @@ class ModelSpec:
     def index(self, name: str) -> int:
         return self.param_names.index(name)
 
+    def to_config(self) -> dict:
+        """The JSON configuration of this model (the schema fit_model_create_json reads):
+        parameters by name, held entries as null, survival constants as numbers."""
+        names = list(self.param_names)
+
+        def ref(i):
+            return None if int(i) < 0 else names[int(i)]
+
+        def refs(a):
+            return [ref(i) for i in np.asarray(a).ravel()]
+
+        def nums(a):
+            return [float(x) for x in np.asarray(a, dtype=np.float64).ravel()]
+
+        formula = {OSC_EQ1: "eq1", OSC_VACUUM3: "vacuum3", OSC_STERILE4: "sterile4"}[self.osc_mode]
+        return {
+            "parameters": [{"name": n, "value": float(v), "sigma": float(s), "scale": float(c)}
+                           for n, v, s, c in zip(names, self.theta0, self.prior_sigma, self.scale)],
+            "covariances": [{"params": refs(ix), "cov": [nums(r) for r in np.asarray(cv)]}
+                            for ix, cv in self.cov_blocks],
+            "oscillation": {"formula": formula,
+                            "params": [names[int(i)] if int(i) >= 0 else float(v)
+                                       for i, v in zip(self.osc_idx, self.osc_val)]},
+            "true_grid": {"bins": int(self.n_true), "e_lo": float(self.e_lo), "e_hi": float(self.e_hi)},
+            "energy_correction": "spline" if int(self.remap) == 1 else "overlap",
+            "core_powers": refs(self.core_power_idx),
+            "detectors": [{"name": dt.name, "response": [nums(r) for r in dt.response]}
+                          for dt in self.detectors],
+            "datasets": [{"name": x.name, "detector": self.detectors[x.det].name,
+                          "t": nums(x.t), "baseline": nums(x.baseline), "weight": nums(x.weight),
+                          "norm": ref(x.norm_idx), "efficiency": ref(x.eff_idx),
+                          "escale": refs(x.escale_idx), "shape": refs(x.shape_idx),
+                          "backgrounds": [{"name": b.name, "template": nums(b.template),
+                                           "rate": ref(b.rate_idx), "shape": refs(b.shape_idx)}
+                                          for b in x.backgrounds]}
+                         for x in self.datasets],
+        }
+
+    def to_json(self) -> str:
+        import json
+        return json.dumps(self.to_config())
+
 
 # ----------------------------------------------------------------------------------------
 # Building blocks

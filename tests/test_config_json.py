@@ -1,0 +1,129 @@
+"""Model creation from a JSON configuration (fit_model_create_json): the reader and the
+mapping onto the model description are host code, so every rejection below happens before a
+device call and runs on the CPU. ([S]: the framework reads a configuration file naming the
+parameters, their priors and the datasets.)"""
+import copy
+import ctypes
+import json
+
+import numpy as np
+import pytest
+
+from paper_2502_15253_gb300 import fitcore, synth
+
+INVALID_CONFIG = -2
+
+
+def _create(text):
+    """(rc, message, handle) of fit_model_create_json on a str / bytes configuration."""
+    L = fitcore.load()
+    h = ctypes.c_void_p()
+    raw = text.encode() if isinstance(text, str) else text
+    rc = L.fit_model_create_json(raw, ctypes.byref(h))
+    msg = L.fit_last_error().decode() if rc else ""
+    if rc == 0:   # only where a device is present
+        L.fit_model_destroy(h)
+    return rc, msg
+
+
+def _reject(cfg):
+    rc, msg = _create(json.dumps(cfg) if isinstance(cfg, dict) else cfg)
+    assert rc == INVALID_CONFIG, (rc, msg)
+    return msg
+
+
+@pytest.fixture(scope="module")
+def cfg():
+    return synth.make_model("c0").to_config()
+
+
+@pytest.mark.parametrize("text,where", [
+    ("", "offset 0"), ("{", "offset 1"), ('{"a": }', "offset 6"), ('{"a" 1}', "expected ':'"),
+    ('{"a": [1, 2}', "expected ',' or ']'"), ('{"a": "x}', "unterminated string"),
+    ('{"a": 1} 2', "trailing characters"), ('{"a": tru}', "offset"), ('{"a": "\\q"}', "bad escape"),
+    ("[" * 100 + "]" * 100, "nesting too deep"), ("[1, 2]", "must be an object"),
+])
+def test_malformed_json_is_rejected_with_its_offset(text, where):
+    assert where in _reject(text)
+
+
+def test_null_arguments():
+    L = fitcore.load()
+    h = ctypes.c_void_p()
+    assert L.fit_model_create_json(None, ctypes.byref(h)) == -1
+    assert L.fit_model_create_json(b"{}", None) == -1
+    assert L.fit_model_param_name(None, 0) is None
+
+
+def _edit(cfg, fn):
+    c = copy.deepcopy(cfg)
+    fn(c)
+    return c
+
+
+@pytest.mark.parametrize("edit,where", [
+    (lambda c: c.pop("parameters"), 'missing "parameters"'),
+    (lambda c: c.pop("datasets"), 'missing "datasets"'),
+    (lambda c: c["parameters"][3].pop("value"), "parameters[3]: missing \"value\""),
+    (lambda c: c["parameters"][1].update(name=c["parameters"][0]["name"]), "duplicate name"),
+    (lambda c: c["parameters"][2].update(sigma="wide"), "parameters[2].sigma: expected a number"),
+    (lambda c: c["datasets"][0].update(norm="no_such"), 'unknown parameter "no_such"'),
+    (lambda c: c["datasets"][0].update(efficiency=10**6), "datasets[0].efficiency: parameter index out of range"),
+    (lambda c: c["datasets"][0].update(efficiency=1.5), "expected an integer"),
+    (lambda c: c["datasets"][0].update(detector="nd"), 'unknown detector "nd"'),
+    (lambda c: c["datasets"][0].update(detector=3), "datasets[0].detector: out of range"),
+    (lambda c: c["datasets"][0]["t"].pop(), "datasets[0].t: expected true_grid.bins entries"),
+    (lambda c: c["datasets"][0]["shape"].pop(), "datasets[0].shape"),
+    (lambda c: c["datasets"][0]["escale"].pop(), "three entries"),
+    (lambda c: c["datasets"][0]["baseline"].append(400.0), "one entry per core"),
+    (lambda c: c["datasets"][0]["backgrounds"][0]["template"].pop(), "backgrounds[0].template"),
+    (lambda c: c["datasets"][0]["backgrounds"][0].update(rate="x"), "backgrounds[0].rate"),
+    (lambda c: c["detectors"][0]["response"][0].pop(), "detectors[0].response"),
+    (lambda c: c["oscillation"].update(formula="eq2"), "oscillation.formula"),
+    (lambda c: c["oscillation"]["params"].pop(), "expected 4 entries"),
+    (lambda c: c["oscillation"]["params"].__setitem__(0, "nope"), 'unknown parameter "nope"'),
+    (lambda c: c["oscillation"]["params"].__setitem__(0, [1]), "oscillation.params[0]: expected a number"),
+    (lambda c: c.update(energy_correction="cubic"), "energy_correction"),
+    (lambda c: c["true_grid"].update(bins=0.5), "true_grid.bins: expected an integer"),
+    (lambda c: c["covariances"][0]["cov"].pop(), "covariances[0].cov"),
+    (lambda c: c["covariances"][0]["params"].__setitem__(0, None), "null is not a parameter"),
+    # caught by the description's own validation, still before any device call
+    (lambda c: c["true_grid"].update(e_lo=20.0), "energy grid"),
+    (lambda c: c["parameters"][0].update(sigma=-1.0), "prior_sigma"),
+])
+def test_configuration_errors_name_the_field(cfg, edit, where):
+    assert where in _reject(_edit(cfg, edit))
+
+
+def test_config_round_trips_the_description():
+    """The configuration written by ModelSpec.to_config carries every array of the
+    description exactly (JSON numbers are printed to round-trip FP64)."""
+    for name in ["c0", "c1", "c1s"]:
+        s = synth.make_model(name, remap=1 if name == "c1" else 0)
+        c = json.loads(s.to_json())
+        ix = {p["name"]: i for i, p in enumerate(c["parameters"])}
+        assert [p["name"] for p in c["parameters"]] == list(s.param_names)
+        assert np.array_equal([p["value"] for p in c["parameters"]], s.theta0)
+        assert np.array_equal([p["sigma"] for p in c["parameters"]], s.prior_sigma)
+        assert c["energy_correction"] == ("spline" if name == "c1" else "overlap")
+        for k, e in enumerate(c["oscillation"]["params"]):
+            if isinstance(e, str):
+                assert ix[e] == s.osc_idx[k]
+            else:
+                assert s.osc_idx[k] == -1 and e == s.osc_val[k]
+        for d, x in zip(c["datasets"], s.datasets):
+            assert np.array_equal(d["t"], x.t)
+            assert [ix[n] if n else -1 for n in d["shape"]] == list(x.shape_idx)
+            for b, y in zip(d["backgrounds"], x.backgrounds):
+                assert np.array_equal(b["template"], y.template)
+        for dt, y in zip(c["detectors"], s.detectors):
+            assert np.array_equal(np.asarray(dt["response"]), y.response)
+
+
+def test_valid_configuration_reaches_the_device_step(cfg):
+    """A valid configuration passes every host check: without a device the first error is the
+    allocation's (OOM or CUDA); with one the model is created."""
+    rc, msg = _create(json.dumps(cfg))
+    assert rc in (0, -4, -6), (rc, msg)
+    if rc:
+        assert msg.startswith("fit_model_create:") and "cuda" in msg.lower()
