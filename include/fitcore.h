@@ -172,6 +172,11 @@ int fit_model_info(const fit_model *model, fit_model_info_t *info);
  * those of fit_model_create. All configuration errors are found before any device call. */
 int fit_model_create_json(const char *json, fit_model **out);
 
+/* Nominal values and prior widths ([S] parameter handling; Eq. 5, 6), host buffers [n_params]
+ * (either may be NULL). prior_sigma is the individual Gaussian width, sqrt(V_ii) for a member
+ * of a covariance block, 0 for a parameter without prior. */
+int fit_model_params(const fit_model *model, double *theta0, double *prior_sigma);
+
 /* Name of parameter i of a model created by fit_model_create_json; NULL for a model created
  * from a fit_model_desc or for i out of range. The string lives as long as the model. */
 const char *fit_model_param_name(const fit_model *model, int i);
@@ -242,6 +247,18 @@ typedef struct fit_result {
 
 /* Sets *opts to the defaults. */
 void fit_batch_default_opts(fit_batch_opts *opts);
+
+/* The best fit of one instance as a JSON object ([S]: the output component writes the
+ * converged fit as JSON, the interface to the rest of an analysis chain):
+ *   {"nll_min": x, "edm": x, "iters": n, "n_evals": n, "status": "converged" | ...,
+ *    "params": {"<name>": value, ...}}
+ * with the model's parameter names (p0, p1, ... for a model built from a description);
+ * numbers print with 17 significant digits (exact FP64 round trip), non-finite ones as null.
+ * best: host [n_params] doubles; res: host. buf: host, or NULL to query the size only.
+ * *needed receives the size in bytes including the terminating NUL.
+ * Errors: INVALID_ARG (null argument, buf_len < *needed: nothing is written). */
+int fit_result_json(const fit_model *model, const double *best, const fit_result *res, char *buf,
+                    size_t buf_len, size_t *needed);
 
 /* Fits n_inst pseudo-experiments of possibly different models in one persistent launch:
  * one block per instance at a time, per-instance L-BFGS state on the device, the whole

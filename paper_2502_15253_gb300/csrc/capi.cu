@@ -174,6 +174,7 @@ struct fit_model {
     float *pre = nullptr;
     int pre_state = 0;     // 0 not built, 1 built, -1 failed (fits run unpreconditioned)
     std::vector<std::string> names;   // parameter names (models created from a configuration)
+    std::vector<double> sigma;        // prior width per parameter (block members: sqrt(V_ii))
 };
 
 // error / launch-count hooks for the other translation units of the library
@@ -213,6 +214,13 @@ int fit_model_info(const fit_model *model, fit_model_info_t *info) {
     info->n_datasets = model->n_ds;
     info->n_true = model->n_true;
     info->device_bytes = model->bytes;
+    return FIT_OK;
+}
+
+int fit_model_params(const fit_model *model, double *theta0, double *prior_sigma) {
+    if (!model) return fail(FIT_ERR_INVALID_ARG, "fit_model_params: null model");
+    if (theta0) std::copy(model->theta0.begin(), model->theta0.end(), theta0);
+    if (prior_sigma) std::copy(model->sigma.begin(), model->sigma.end(), prior_sigma);
     return FIT_OK;
 }
 
@@ -583,6 +591,10 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         A.put(&h.blk_first, bfirst);
         M->in_block.assign(in_block.begin(), in_block.end());
         M->theta0 = th0;
+        M->sigma.assign(d->prior_sigma, d->prior_sigma + P);
+        for (int b = 0, q = 0, mo = 0; b < d->n_cov; mo += d->cov_size[b] * d->cov_size[b], q += d->cov_size[b], ++b)
+            for (int i = 0; i < d->cov_size[b]; ++i)
+                M->sigma[d->cov_idx[q + i]] = std::sqrt(d->cov[mo + i * d->cov_size[b] + i]);
         M->zscale.assign(P, 0.0);
         for (int i = 0; i < P; ++i)
             if (!in_block[i]) M->zscale[i] = d->prior_sigma[i] > 0.0 ? d->prior_sigma[i] : d->scale[i];

@@ -6,6 +6,7 @@
 // a survival-probability entry is either a parameter name or a number (a held constant).
 #include <cctype>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -481,4 +482,73 @@ extern "C" int fit_model_create_json(const char *text, fit_model **out) {
     } catch (const ConfigError &e) {
         return fitcore_fail(FIT_ERR_INVALID_CONFIG, "fit_model_create_json: " + e.msg);
     }
+}
+
+// ---- best-fit output as JSON ([S]: the third component writes the converged fit to a JSON
+// file, the interface to the rest of an analysis chain) --------------------------------------
+namespace {
+
+const char *status_name(int s) {
+    static const char *k[] = {"converged", "maxiter", "linesearch_fail", "nonfinite",
+                              "mu_nonpositive", "escale_nonmonotone", "timeout", "stalled"};
+    return s >= 0 && s < 8 ? k[s] : "unknown";
+}
+
+void put_number(std::string &o, double x) {
+    if (!std::isfinite(x)) {   // JSON has no inf / nan
+        o += "null";
+        return;
+    }
+    char b[32];
+    std::snprintf(b, sizeof(b), "%.17g", x);
+    o += b;
+}
+
+void put_string(std::string &o, const char *s) {
+    o += '"';
+    for (; *s; ++s) {
+        const unsigned char c = (unsigned char)*s;
+        if (c == '"' || c == '\\') {
+            o += '\\';
+            o += (char)c;
+        } else if (c < 0x20) {
+            char b[8];
+            std::snprintf(b, sizeof(b), "\\u%04x", c);
+            o += b;
+        } else {
+            o += (char)c;
+        }
+    }
+    o += '"';
+}
+
+}  // namespace
+
+extern "C" int fit_result_json(const fit_model *model, const double *best, const fit_result *res,
+                               char *buf, size_t buf_len, size_t *needed) {
+    if (!model || !best || !res || !needed) return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_result_json: null argument");
+    fit_model_info_t info;
+    const int rc = fit_model_info(model, &info);
+    if (rc != FIT_OK) return rc;
+    std::string o = "{\"nll_min\": ";
+    put_number(o, res->nll_min);
+    o += ", \"edm\": ";
+    put_number(o, res->edm);
+    o += ", \"iters\": " + std::to_string(res->iters) + ", \"n_evals\": " + std::to_string(res->n_evals);
+    o += ", \"status\": ";
+    put_string(o, status_name(res->status));
+    o += ", \"params\": {";
+    for (int i = 0; i < info.n_params; ++i) {
+        if (i) o += ", ";
+        const char *nm = fit_model_param_name(model, i);
+        put_string(o, nm ? nm : ("p" + std::to_string(i)).c_str());
+        o += ": ";
+        put_number(o, best[i]);
+    }
+    o += "}}";
+    *needed = o.size() + 1;
+    if (!buf) return FIT_OK;
+    if (buf_len < o.size() + 1) return fitcore_fail(FIT_ERR_INVALID_ARG, "fit_result_json: buffer too small");
+    std::memcpy(buf, o.c_str(), o.size() + 1);
+    return FIT_OK;
 }

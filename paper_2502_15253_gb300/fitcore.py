@@ -98,7 +98,8 @@ EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model
            "fit_warmstart_features", "fit_warmstart_predict", "fit_warmstart_draw",
            "fit_warmstart_train", "fit_batch_autotune", "fit_batch_ex", "fit_profile_scan",
            "fit_wilks_interval", "fit_chi2_sf", "fit_mc_create", "fit_mc_destroy",
-           "fit_mc_spectrum", "fit_mc_status", "fit_model_create_json", "fit_model_param_name")
+           "fit_mc_spectrum", "fit_mc_status", "fit_model_create_json", "fit_model_param_name",
+           "fit_model_params", "fit_result_json")
 
 
 def lib_path() -> str:
@@ -177,6 +178,10 @@ def load(build_if_missing: bool = False):
     L.fit_model_create_json.restype = C.c_int
     L.fit_model_param_name.argtypes = [vp, C.c_int]
     L.fit_model_param_name.restype = C.c_char_p
+    L.fit_model_params.argtypes = [vp, vp, vp]
+    L.fit_model_params.restype = C.c_int
+    L.fit_result_json.argtypes = [vp, vp, vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.fit_result_json.restype = C.c_int
     L.fit_last_error.restype = C.c_char_p
     L.fit_kernel_launches.restype = C.c_int64
     for f in ("fit_model_create", "fit_model_info", "fit_model_expected", "fit_model_eval",
@@ -301,6 +306,12 @@ class Model:
         _check(load().fit_model_create_json(text, C.byref(h)), "fit_model_create_json")
         return cls(spec, _handle=h)
 
+    def params(self):
+        """(theta0, prior_sigma) host arrays kept by the library."""
+        th, sg = np.zeros(self.n_params), np.zeros(self.n_params)
+        _check(load().fit_model_params(self.handle, th.ctypes.data, sg.ctypes.data), "fit_model_params")
+        return th, sg
+
     def param_names(self):
         """Parameter names kept by the library (None for a model built from a description)."""
         L = load()
@@ -322,6 +333,22 @@ def fit_model_create(spec) -> Model:
 
 def fit_model_create_json(text, spec=None) -> Model:
     return Model.from_json(text, spec)
+
+
+def fit_result_json(model: Model, best, result) -> str:
+    """The library's JSON record of one fit: best = [n_params] float64 host array, result = one
+    RESULT_DTYPE record (or a fit_result)."""
+    best = np.ascontiguousarray(best, dtype=np.float64)
+    if best.shape != (model.n_params,):
+        raise ValueError("best must hold n_params values")
+    r = np.ascontiguousarray(np.asarray(result).reshape(1), dtype=RESULT_DTYPE)
+    L, n = load(), C.c_size_t()
+    _check(L.fit_result_json(model.handle, best.ctypes.data, r.ctypes.data, None, 0, C.byref(n)),
+           "fit_result_json")
+    buf = C.create_string_buffer(n.value)
+    _check(L.fit_result_json(model.handle, best.ctypes.data, r.ctypes.data, buf, n.value, C.byref(n)),
+           "fit_result_json")
+    return buf.value.decode()
 
 
 def fit_model_destroy(model: Model):

@@ -127,3 +127,11 @@ def test_valid_configuration_reaches_the_device_step(cfg):
     assert rc in (0, -4, -6), (rc, msg)
     if rc:
         assert msg.startswith("fit_model_create:") and "cuda" in msg.lower()
+
+
+def test_result_json_and_params_reject_null_arguments():
+    L = fitcore.load()
+    n = ctypes.c_size_t()
+    assert L.fit_result_json(None, None, None, None, 0, ctypes.byref(n)) == -1
+    assert "null argument" in L.fit_last_error().decode()
+    assert L.fit_model_params(None, None, None) == -1

@@ -57,3 +57,35 @@ def test_fits_are_identical(models):
     np.testing.assert_array_equal(best_j, best_s)
     np.testing.assert_array_equal(r_j["nll_min"], r_s["nll_min"])
     np.testing.assert_array_equal(r_j["iters"], r_s["iters"])
+
+
+def test_params_report_nominal_values_and_prior_widths(models):
+    spec, gs, gj = models
+    sig = spec.prior_sigma.copy()
+    for ix, cov in spec.cov_blocks:
+        sig[np.asarray(ix)] = np.sqrt(np.diag(cov))
+    for g in (gs, gj):
+        th, sg = g.params()
+        np.testing.assert_array_equal(th, spec.theta0)
+        np.testing.assert_array_equal(sg, sig)
+
+
+def test_result_json_round_trips_the_fit(models):
+    """fit_result_json writes the best fit with the configuration's names; every number reads
+    back exactly ([S]: the output component's JSON record)."""
+    import json
+    spec, gs, gj = models
+    mu, _ = fitcore.expected_numpy(gj, spec.theta0[None])
+    data = np.random.default_rng(8).poisson(mu.astype(np.float64)).astype(np.float32)
+    inst = np.zeros(1, fitcore.INSTANCE_DTYPE)
+    inst["mask"] = spec.all_mask()
+    best, r = fitcore.fit_numpy([gj], inst, data)
+    rec = json.loads(fitcore.fit_result_json(gj, best, r[0]))
+    assert rec["status"] == fitcore.STATUS[int(r[0]["status"])]
+    assert rec["nll_min"] == r[0]["nll_min"] and rec["edm"] == r[0]["edm"]
+    assert (rec["iters"], rec["n_evals"]) == (r[0]["iters"], r[0]["n_evals"])
+    assert list(rec["params"]) == list(spec.param_names)
+    np.testing.assert_array_equal(np.array(list(rec["params"].values())), best)
+    # a model built from a description names its parameters p0, p1, ...
+    rec = json.loads(fitcore.fit_result_json(gs, best, r[0]))
+    assert list(rec["params"])[:3] == ["p0", "p1", "p2"]
