@@ -98,6 +98,35 @@ class Parser {
         v.kind = Value::Number;
         return true;
     }
+    bool hex4(const char *q, unsigned &cp) {
+        cp = 0;
+        for (int i = 0; i < 4; ++i) {
+            const char c = q[i];
+            if (!std::isxdigit((unsigned char)c)) {
+                msg_ = "bad \\u escape";
+                return false;
+            }
+            cp = cp * 16 + (unsigned)(std::isdigit((unsigned char)c) ? c - '0' : std::tolower((unsigned char)c) - 'a' + 10);
+        }
+        return true;
+    }
+    static void utf8(std::string &out, unsigned cp) {
+        if (cp < 0x80) {
+            out += (char)cp;
+        } else if (cp < 0x800) {
+            out += (char)(0xC0 | (cp >> 6));
+            out += (char)(0x80 | (cp & 0x3F));
+        } else if (cp < 0x10000) {
+            out += (char)(0xE0 | (cp >> 12));
+            out += (char)(0x80 | ((cp >> 6) & 0x3F));
+            out += (char)(0x80 | (cp & 0x3F));
+        } else {
+            out += (char)(0xF0 | (cp >> 18));
+            out += (char)(0x80 | ((cp >> 12) & 0x3F));
+            out += (char)(0x80 | ((cp >> 6) & 0x3F));
+            out += (char)(0x80 | (cp & 0x3F));
+        }
+    }
     bool string(std::string &out) {
         if (*p_ != '"') return false;
         ++p_;
@@ -114,18 +143,23 @@ class Parser {
                     case 'n': out += '\n'; break;
                     case 'r': out += '\r'; break;
                     case 't': out += '\t'; break;
-                    case 'u': {   // \uXXXX: code points below 0x80 kept, others as '?'
+                    case 'u': {   // \uXXXX (a surrogate pair for code points above U+FFFF), as UTF-8
                         unsigned cp = 0;
-                        for (int i = 1; i <= 4; ++i) {
-                            const char c = p_[i];
-                            if (!std::isxdigit((unsigned char)c)) {
-                                msg_ = "bad \\u escape";
+                        if (!hex4(p_ + 1, cp)) return false;
+                        p_ += 4;
+                        if (cp >= 0xD800 && cp < 0xDC00) {
+                            unsigned lo = 0;
+                            if (p_[1] != '\\' || p_[2] != 'u' || !hex4(p_ + 3, lo) || lo < 0xDC00 || lo >= 0xE000) {
+                                msg_ = "unpaired surrogate";
                                 return false;
                             }
-                            cp = cp * 16 + (unsigned)(std::isdigit((unsigned char)c) ? c - '0' : (std::tolower(c) - 'a' + 10));
+                            cp = 0x10000 + ((cp - 0xD800) << 10) + (lo - 0xDC00);
+                            p_ += 6;
+                        } else if (cp >= 0xDC00 && cp < 0xE000) {
+                            msg_ = "unpaired surrogate";
+                            return false;
                         }
-                        out += cp < 0x80 ? (char)cp : '?';
-                        p_ += 4;
+                        utf8(out, cp);
                         break;
                     }
                     default: msg_ = "bad escape"; return false;

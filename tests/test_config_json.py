@@ -42,6 +42,8 @@ def cfg():
     ('{"a": [1, 2}', "expected ',' or ']'"), ('{"a": "x}', "unterminated string"),
     ('{"a": 1} 2', "trailing characters"), ('{"a": tru}', "offset"), ('{"a": "\\q"}', "bad escape"),
     ("[" * 100 + "]" * 100, "nesting too deep"), ("[1, 2]", "must be an object"),
+    ('{"a": "\\ud800"}', "unpaired surrogate"), ('{"a": "\\udc00x"}', "unpaired surrogate"),
+    ('{"a": "\\u12G4"}', "bad \\u escape"),
 ])
 def test_malformed_json_is_rejected_with_its_offset(text, where):
     assert where in _reject(text)
