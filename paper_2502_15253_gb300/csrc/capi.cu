@@ -202,6 +202,7 @@ int64_t fit_kernel_launches(void) {
 
 void fit_model_destroy(fit_model *model) {
     if (!model) return;
+    if (model->dev) cudaFree(model->dev);
     if (model->arena) cudaFree(model->arena);
     if (model->pre) cudaFree(model->pre);
     delete model;
@@ -633,7 +634,6 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
     if (e == cudaSuccess) e = cudaMemcpy(M->dev, &h, sizeof(DevModel), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (M->dev) cudaFree(M->dev);
         fit_model_destroy(M);
         return fail(FIT_ERR_CUDA, std::string("fit_model_create: upload: ") + cudaGetErrorString(e));
     }
@@ -657,8 +657,6 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         if (th) cudaFree(th);
         if (rc != FIT_OK) {
             cudaGetLastError();
-            cudaFree(M->dev);
-            M->dev = nullptr;
             fit_model_destroy(M);
             return rc;
         }
