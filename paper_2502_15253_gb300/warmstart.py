@@ -75,3 +75,59 @@ def predict_starts(net, model, spec, B, data, masks, theta_out, stream=None):
     fitcore.fit_warmstart_predict(net, model, B, data, masks, g.slot0, g.onehot_slot,
                                   list(g.target_idx)[:n], list(g.target_scale)[:n], theta_out,
                                   stream)
+
+
+# ---- weights on disk ------------------------------------------------------------------------
+def save_layers(path, dims, layers):
+    """Writes a network's FP32 master weights: dims = (n_in, n_hidden, n_hidden_layers, n_out),
+    layers = [(w [out x in], b [out]), ...]. One .npz (w0, b0, w1, ...) with the dimensions as a
+    JSON string, replaced atomically. The optimiser moments are not kept (a resumed training
+    starts them at zero)."""
+    import json
+    import os
+    n_in, n_hidden, n_hl, n_out = (int(x) for x in dims)
+    shapes = [(n_hidden if l < n_hl else n_out, n_in if l == 0 else n_hidden) for l in range(n_hl + 1)]
+    if len(layers) != len(shapes):
+        raise ValueError(f"expected {len(shapes)} layers")
+    arrays = {}
+    for l, ((w, b), (o, i)) in enumerate(zip(layers, shapes)):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        if w.shape != (o, i) or b.shape != (o,):
+            raise ValueError(f"layer {l}: expected w {(o, i)} and b {(o,)}")
+        arrays[f"w{l}"], arrays[f"b{l}"] = w, b
+    meta = json.dumps({"n_in": n_in, "n_hidden": n_hidden, "n_hidden_layers": n_hl, "n_out": n_out})
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        np.savez(f, meta=np.array(meta), **arrays)
+    os.replace(tmp, path)
+
+
+def load_layers(path):
+    """(dims, layers) as written by save_layers, shapes checked against the dimensions."""
+    import json
+    with np.load(path, allow_pickle=False) as z:
+        m = json.loads(str(z["meta"]))
+        dims = (m["n_in"], m["n_hidden"], m["n_hidden_layers"], m["n_out"])
+        layers = [(z[f"w{l}"].copy(), z[f"b{l}"].copy()) for l in range(dims[2] + 1)]
+    n_in, n_hidden, n_hl, n_out = dims
+    for l, (w, b) in enumerate(layers):
+        o, i = (n_hidden if l < n_hl else n_out), (n_in if l == 0 else n_hidden)
+        if w.shape != (o, i) or b.shape != (o,) or w.dtype != np.float32:
+            raise ValueError(f"{path}: layer {l} does not match the dimensions")
+    return dims, layers
+
+
+def save_network(net: fitcore.Mlp, path):
+    """Copies the device weights of `net` to `path` (fit_mlp_get_layer per layer)."""
+    dims = (net.n_in, net.n_hidden, net.n_layers - 1, net.n_out)
+    save_layers(path, dims, [net.get_layer(l)[:2] for l in range(net.n_layers)])
+
+
+def load_network(path, seed: int = 0) -> fitcore.Mlp:
+    """A device network with the weights stored at `path` (fit_mlp_create, fit_mlp_set_layer)."""
+    dims, layers = load_layers(path)
+    net = fitcore.Mlp(*dims, seed=seed)
+    for l, (w, b) in enumerate(layers):
+        net.set_layer(l, w, b)
+    return net

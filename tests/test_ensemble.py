@@ -88,3 +88,23 @@ def test_chunk_size_does_not_change_results():
     np.testing.assert_array_equal(a[1], b[1])
     with pytest.raises(ValueError):
         fit_ensemble(models, inst, data, chunk=0, fit_fn=_fake([]))
+
+
+def test_network_weights_round_trip_on_disk(tmp_path):
+    from paper_2502_15253_gb300 import warmstart
+    rng = np.random.default_rng(3)
+    dims = (10, 8, 2, 3)
+    shapes = [(8, 10), (8, 8), (3, 8)]
+    layers = [(rng.standard_normal(s).astype(np.float32), rng.standard_normal(s[0]).astype(np.float32))
+              for s in shapes]
+    p = str(tmp_path / "net.npz")
+    warmstart.save_layers(p, dims, layers)
+    d2, l2 = warmstart.load_layers(p)
+    assert tuple(d2) == dims
+    for (w, b), (w2, b2) in zip(layers, l2):
+        np.testing.assert_array_equal(w, w2)
+        np.testing.assert_array_equal(b, b2)
+    with pytest.raises(ValueError):
+        warmstart.save_layers(p, dims, layers[:2])
+    with pytest.raises(ValueError):
+        warmstart.save_layers(p, (10, 8, 2, 4), layers)
