@@ -137,3 +137,37 @@ def test_result_json_and_params_reject_null_arguments():
     assert L.fit_result_json(None, None, None, None, 0, ctypes.byref(n)) == -1
     assert "null argument" in L.fit_last_error().decode()
     assert L.fit_model_params(None, None, None) == -1
+
+
+def test_covariance_blocks_must_be_symmetric_positive_definite(cfg):
+    """Eq. 6: a covariance prior needs V_B symmetric positive definite (its Cholesky factor is
+    the transformation layer); either failure is NON_SPD_COV, found on the host."""
+    NON_SPD = -3
+    c = copy.deepcopy(cfg)
+    cov = np.asarray(c["covariances"][0]["cov"])
+    m = len(cov)
+    assert m >= 2
+    asym = cov.copy()
+    asym[0, 1] += 0.1 * np.sqrt(cov[0, 0] * cov[1, 1])
+    c["covariances"][0]["cov"] = asym.tolist()
+    rc, msg = _create(json.dumps(c))
+    assert rc == NON_SPD and "symmetric" in msg
+    # symmetric but indefinite: a negative eigenvalue
+    w, v = np.linalg.eigh(cov)
+    w[0] = -abs(w[-1])
+    c["covariances"][0]["cov"] = ((v * w) @ v.T).tolist()
+    rc, msg = _create(json.dumps(c))
+    assert rc == NON_SPD and "positive definite" in msg
+
+
+def test_non_finite_inputs_are_rejected(cfg):
+    """JSON has no NaN or infinity: such a number (as Python writes it) is malformed JSON; in a
+    description a non-finite response entry is a configuration error."""
+    c = _edit(cfg, lambda c: c["detectors"][0]["response"][3].__setitem__(5, float("nan")))
+    assert "expected a value" in _reject(json.dumps(c))
+    c = _edit(cfg, lambda c: c["datasets"][0]["t"].__setitem__(2, float("inf")))
+    assert "expected a value" in _reject(json.dumps(c))
+    s2 = copy.deepcopy(synth.make_model("c0"))
+    s2.detectors[0].response[3, 5] = np.nan
+    with pytest.raises(fitcore.FitError, match="finite"):
+        fitcore.Model(s2)
