@@ -95,6 +95,7 @@ extern "C" {
  * A parameter index of -1 means "fixed at its nominal value": 1 for multiplicative factors
  * (norm, efficiency, shape reweight, rate, core power), (0, 1, 0) for (a0, a1, a2), 0 for a
  * background shape delta. Arrays marked "concatenated" list the items back to back.
+ * Every number must be finite; ds_t, det_response and bkg_template entries must be >= 0.
  */
 typedef struct fit_model_desc {
     int n_params;

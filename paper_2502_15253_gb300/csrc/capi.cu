@@ -250,7 +250,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         return bad("osc_mode");
     const int n_osc = d->osc_mode == FIT_OSC_STERILE4 ? 6 : 4;
     if (d->remap_mode != FIT_REMAP_OVERLAP && d->remap_mode != FIT_REMAP_SPLINE) return bad("remap_mode");
-    if (!(d->e_lo > 0.0 && d->e_hi > d->e_lo)) return bad("energy grid");
+    if (!(d->e_lo > 0.0 && d->e_hi > d->e_lo) || !std::isfinite(d->e_hi)) return bad("energy grid");
     if (!d->theta0 || !d->prior_sigma || !d->scale || !d->core_power_idx || !d->det_n_reco ||
         !d->det_response || !d->ds_det || !d->ds_t || !d->ds_baseline || !d->ds_weight ||
         !d->ds_norm_idx || !d->ds_eff_idx || !d->ds_escale_idx || !d->ds_shape_idx)
@@ -259,8 +259,12 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
     if (d->n_bkg > 0 && (!d->bkg_ds || !d->bkg_template || !d->bkg_rate_idx || !d->bkg_shape_idx))
         return bad("missing background arrays");
     auto pidx_ok = [P](int i) { return i >= -1 && i < P; };
-    for (int i = 0; i < n_osc; ++i)
+    for (int i = 0; i < P; ++i)
+        if (!std::isfinite(d->theta0[i])) return bad("theta0 entries must be finite");
+    for (int i = 0; i < n_osc; ++i) {
         if (!pidx_ok(d->osc_idx[i])) return bad("osc_idx");
+        if (d->osc_idx[i] < 0 && !std::isfinite(d->osc_val[i])) return bad("osc_val entries must be finite");
+    }
     if (n_osc == 6 && d->osc_idx[4] < 0 && !(d->osc_val[4] >= 0.0 && d->osc_val[4] < 1.0))
         return bad("sin^2 2th14 outside [0, 1)");
     for (int c = 0; c < C; ++c)
@@ -407,7 +411,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         D.a1_off = D.esc_idx[1] >= 0 ? (float)(d->theta0[D.esc_idx[1]] - 1.0) : 0.f;
         for (int c = 0; c < C; ++c) {
             const double w = d->ds_weight[ds * C + c], L = d->ds_baseline[ds * C + c];
-            if (!(w >= 0.0) || (w > 0.0 && !(L > 0.0))) {
+            if (!(w >= 0.0) || !std::isfinite(w) || (w > 0.0 && !(L > 0.0 && std::isfinite(L)))) {
                 delete M;
                 return bad("ds_weight / ds_baseline");
             }
@@ -421,7 +425,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         for (int k = 0; k < Nt; ++k) {
             t[k] = (float)d->ds_t[(size_t)ds * Nt + k];
             sidx[k] = d->ds_shape_idx[(size_t)ds * Nt + k];
-            if (!pidx_ok(sidx[k]) || !(t[k] >= 0.f)) {
+            if (!pidx_ok(sidx[k]) || !(t[k] >= 0.f) || !std::isfinite(t[k])) {
                 delete M;
                 return bad("ds_t / ds_shape_idx");
             }
@@ -476,6 +480,10 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
                 if (!pidx_ok(si[j])) {
                     delete M;
                     return bad("bkg_shape_idx");
+                }
+                if (!(tm[j] >= 0.f) || !std::isfinite(tm[j])) {
+                    delete M;
+                    return bad("bkg_template entries must be finite and >= 0");
                 }
             }
             if (!pidx_ok(d->bkg_rate_idx[b])) {

@@ -256,6 +256,7 @@ const json::Value &need(const json::Value &o, const std::string &key, const std:
 
 double num(const json::Value &v, const std::string &where) {
     if (v.kind != json::Value::Number) bad(where + ": expected a number");
+    if (!std::isfinite(v.num)) bad(where + ": number out of range");
     return v.num;
 }
 

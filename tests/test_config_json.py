@@ -171,3 +171,33 @@ def test_non_finite_inputs_are_rejected(cfg):
     s2.detectors[0].response[3, 5] = np.nan
     with pytest.raises(fitcore.FitError, match="finite"):
         fitcore.Model(s2)
+
+
+@pytest.mark.parametrize("mutate,where", [
+    (lambda s: s.theta0.__setitem__(0, np.inf), "theta0 entries must be finite"),
+    (lambda s: s.datasets[0].backgrounds[0].template.__setitem__(0, -1.0), "bkg_template"),
+    (lambda s: s.datasets[0].backgrounds[0].template.__setitem__(1, np.nan), "bkg_template"),
+    (lambda s: s.datasets[0].t.__setitem__(0, 1e39), "ds_t"),
+    (lambda s: s.datasets[0].baseline.__setitem__(0, np.inf), "ds_weight / ds_baseline"),
+    (lambda s: s.datasets[0].weight.__setitem__(0, np.inf), "ds_weight / ds_baseline"),
+    (lambda s: setattr(s, "e_hi", np.inf), "energy grid"),
+])
+def test_description_numbers_must_be_finite(mutate, where):
+    s = copy.deepcopy(synth.make_model("c0"))
+    mutate(s)
+    with pytest.raises(fitcore.FitError, match=where):
+        fitcore.Model(s)
+
+
+def test_every_synthetic_model_passes_the_host_checks():
+    """The benchmark's and the tests' models pass every host check through both entry points:
+    without a device the first error is the allocation's (with one, the model is created)."""
+    for name in ["c0", "c0_tiny", "c1", "c2", "c1s", "c1_flux41"]:
+        for remap in (0, 1):
+            s = synth.make_model(name, remap=remap)
+            rc, msg = _create(s.to_json())
+            assert rc in (0, -4, -6), (name, remap, msg)
+            try:
+                fitcore.Model(s).close()
+            except fitcore.FitError as e:
+                assert "cudaMalloc" in str(e), (name, remap, str(e))
