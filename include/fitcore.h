@@ -157,6 +157,8 @@ int fit_model_info(const fit_model *model, fit_model_info_t *info);
  * brackets are optional; a parameter reference is a name string, an index, or null = held
  * at its nominal value as in fit_model_desc):
  *   parameters:  [{name, value, [sigma], [scale]}, ...]        -> theta0, prior_sigma, scale
+ *                an entry {namespace: ns, parameters: [...]} groups parameters whose names
+ *                then read "ns.name" (nested groups "a.b.name"; [S]: parameter namespaces)
  *   [covariances]: [{params: [ref, ...], cov: [[...], ...]}]   -> Eq. 6 blocks
  *   oscillation: {formula: "eq1" | "vacuum3" | "sterile4",
  *                 params: [4 or 6 entries: a parameter name, or a number = held constant]}

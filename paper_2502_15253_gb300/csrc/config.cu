@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -313,25 +314,38 @@ extern "C" int fit_model_create_json(const char *text, fit_model **out) {
     if (!json::Parser(text).parse(root, err)) return fitcore_fail(FIT_ERR_INVALID_CONFIG, "fit_model_create_json: " + err);
     try {
         if (root.kind != json::Value::Object) bad("the configuration must be an object");
-        // parameters
+        // parameters; a group {"namespace": ns, "parameters": [...]} prefixes its members'
+        // names with "ns." ([S]: the parameter handling allows several namespaces)
         Params prm;
         std::vector<double> theta0, sigma, scale;
-        const auto &pl = arr(need(root, "parameters", "config"), "parameters");
-        for (size_t i = 0; i < pl.size(); ++i) {
-            const std::string w = "parameters[" + std::to_string(i) + "]";
-            const json::Value &p = pl[i];
-            if (p.kind != json::Value::Object) bad(w + ": expected an object");
-            const json::Value &nm = need(p, "name", w);
-            if (nm.kind != json::Value::String || nm.str.empty()) bad(w + ".name: expected a string");
-            if (prm.index.count(nm.str)) bad(w + ": duplicate name \"" + nm.str + "\"");
-            prm.index[nm.str] = (int)i;
-            prm.names.push_back(nm.str);
-            theta0.push_back(num(need(p, "value", w), w + ".value"));
-            const json::Value *sg = p.get("sigma");
-            const json::Value *sc = p.get("scale");
-            sigma.push_back(sg ? num(*sg, w + ".sigma") : 0.0);
-            scale.push_back(sc ? num(*sc, w + ".scale") : 0.0);
-        }
+        std::function<void(const json::Value &, const std::string &, const std::string &, int)> add;
+        add = [&](const json::Value &list, const std::string &prefix, const std::string &where, int depth) {
+            if (depth > 8) bad(where + ": namespaces nested too deep");
+            const auto &pl = arr(list, where);
+            for (size_t i = 0; i < pl.size(); ++i) {
+                const std::string w = where + "[" + std::to_string(i) + "]";
+                const json::Value &p = pl[i];
+                if (p.kind != json::Value::Object) bad(w + ": expected an object");
+                if (const json::Value *ns = p.get("namespace")) {
+                    if (ns->kind != json::Value::String || ns->str.empty() || ns->str.find('.') != std::string::npos)
+                        bad(w + ".namespace: expected a name without '.'");
+                    add(need(p, "parameters", w), prefix + ns->str + ".", w + ".parameters", depth + 1);
+                    continue;
+                }
+                const json::Value &nm = need(p, "name", w);
+                if (nm.kind != json::Value::String || nm.str.empty()) bad(w + ".name: expected a string");
+                const std::string full = prefix + nm.str;
+                if (prm.index.count(full)) bad(w + ": duplicate name \"" + full + "\"");
+                prm.index[full] = (int)prm.names.size();
+                prm.names.push_back(full);
+                theta0.push_back(num(need(p, "value", w), w + ".value"));
+                const json::Value *sg = p.get("sigma");
+                const json::Value *sc = p.get("scale");
+                sigma.push_back(sg ? num(*sg, w + ".sigma") : 0.0);
+                scale.push_back(sc ? num(*sc, w + ".scale") : 0.0);
+            }
+        };
+        add(need(root, "parameters", "config"), "", "parameters", 0);
         const int P = (int)prm.names.size();
         // covariance blocks
         std::vector<int> cov_size, cov_idx;

@@ -201,3 +201,30 @@ def test_every_synthetic_model_passes_the_host_checks():
                 fitcore.Model(s).close()
             except fitcore.FitError as e:
                 assert "cudaMalloc" in str(e), (name, remap, str(e))
+
+
+def _namespaced(cfg):
+    """c0's configuration with its survival parameters in namespace "osc" and the rest in
+    "det" (references rewritten to the full names)."""
+    c = copy.deepcopy(cfg)
+    osc = {e for e in c["oscillation"]["params"] if isinstance(e, str)}
+    full = {p["name"]: ("osc." if p["name"] in osc else "det.") + p["name"] for p in c["parameters"]}
+    c["parameters"] = [{"namespace": "osc", "parameters": [p for p in c["parameters"] if p["name"] in osc]},
+                       {"namespace": "det", "parameters": [p for p in c["parameters"] if p["name"] not in osc]}]
+    return json.dumps(c), full
+
+
+def test_parameter_namespaces(cfg):
+    text, full = _namespaced(cfg)
+    assert _reject(text).count("unknown parameter")   # references still use the short names
+    for short, long_ in full.items():
+        text = text.replace(json.dumps(short), json.dumps(long_))
+    text = text.replace('"name": "osc.', '"name": "').replace('"name": "det.', '"name": "')
+    rc, msg = _create(text)
+    assert rc in (0, -4, -6), msg
+    c = json.loads(text)
+    c["parameters"][0]["namespace"] = "a.b"
+    assert "without '.'" in _reject(c)
+    c = json.loads(text)
+    c["parameters"][1]["parameters"].append(dict(c["parameters"][1]["parameters"][0]))
+    assert 'duplicate name "det.' in _reject(c)
