@@ -160,6 +160,11 @@ int fit_model_info(const fit_model *model, fit_model_info_t *info);
  *                an entry {namespace: ns, parameters: [...]} groups parameters whose names
  *                then read "ns.name" (nested groups "a.b.name"; [S]: parameter namespaces)
  *   [covariances]: [{params: [ref, ...], cov: [[...], ...]}]   -> Eq. 6 blocks
+ *                or, for a prior on b = A theta (Eq. 6's generalised parametrisation, linear):
+ *                {params: [k refs], map: [[k numbers] x m], mean: [m], cov: [[m x m]]}, m >= k,
+ *                taken as the equivalent block C = (A^T V^-1 A)^-1 on the parameters with
+ *                nominal values C A^T V^-1 b0 (these replace the parameters' "value"); the
+ *                constant left over does not depend on theta and is dropped
  *   oscillation: {formula: "eq1" | "vacuum3" | "sterile4",
  *                 params: [4 or 6 entries: a parameter name, or a number = held constant]}
  *   true_grid:   {bins, e_lo, e_hi}          [energy_correction]: "overlap" (default) | "spline"
@@ -171,8 +176,9 @@ int fit_model_info(const fit_model *model, fit_model_info_t *info);
  * Backgrounds take the order datasets, then their lists. Unknown keys are ignored. The model
  * keeps the parameter names (fit_model_param_name).
  * Errors: INVALID_ARG (null), INVALID_CONFIG (malformed JSON with its byte offset, a missing
- * or mistyped field, an unknown name, a size mismatch; the message names the field), then
- * those of fit_model_create. All configuration errors are found before any device call. */
+ * or mistyped field, an unknown name, a size mismatch; the message names the field),
+ * NON_SPD_COV (a map's V or A^T V^-1 A not positive definite), then those of
+ * fit_model_create. All configuration errors are found before any device call. */
 int fit_model_create_json(const char *json, fit_model **out);
 
 /* Nominal values and prior widths ([S] parameter handling; Eq. 5, 6), host buffers [n_params]

@@ -20,6 +20,8 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
   philox4x32_10 (rng.c)               - pinned (published known-answer vectors)
   poisson_sample (rng.c)              - pinned (chi-square against the exact Poisson PMF,
       mean and variance, counter/offset invariance)
+  linear_prior_block (Eq. 6, b = A theta) - pinned (the quadratic forms agree at random points
+      up to one constant; A = identity returns (b0, V, 0); a direct search for the minimum)
 """
 from __future__ import annotations
 
@@ -412,3 +414,19 @@ def event_spectrum(events, params):
                              w.ctypes.data_as(C.POINTER(C.c_float)), b.ctypes.data_as(_IP),
                              int(events.n_bins), out.ctypes.data_as(_DP))
     return out
+
+
+def linear_prior_block(A, b0, V):
+    """Eq. 6 with a linear generalised parametrisation b(theta) = A theta: the Gaussian prior
+    (A theta - b0)^T V^-1 (A theta - b0) written as a covariance block on theta,
+    (theta - t)^T Cb^-1 (theta - t) + const. Expanding the quadratic form:
+    Cb = (A^T V^-1 A)^-1, t = Cb A^T V^-1 b0, const = b0^T V^-1 b0 - t^T Cb^-1 t.
+    Returns (t, Cb, const)."""
+    A = np.asarray(A, dtype=np.float64)
+    b0 = np.asarray(b0, dtype=np.float64)
+    Vinv = np.linalg.inv(np.asarray(V, dtype=np.float64))
+    F = A.T @ Vinv @ A
+    Cb = np.linalg.inv(F)
+    t = Cb @ (A.T @ Vinv @ b0)
+    const = float(b0 @ Vinv @ b0 - t @ F @ t)
+    return t, Cb, const

@@ -245,9 +245,80 @@ namespace {
 
 struct ConfigError {
     std::string msg;
+    int code;
 };
 
-[[noreturn]] void bad(const std::string &m) { throw ConfigError{m}; }
+[[noreturn]] void bad(const std::string &m) { throw ConfigError{m, FIT_ERR_INVALID_CONFIG}; }
+[[noreturn]] void not_spd(const std::string &m) { throw ConfigError{m, FIT_ERR_NON_SPD_COV}; }
+
+// Lower Cholesky factor of the symmetric n x n matrix a (row-major); false unless positive definite.
+bool cholesky(int n, const std::vector<double> &a, std::vector<double> &l) {
+    l.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double d = a[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= l[(size_t)j * n + k] * l[(size_t)j * n + k];
+        if (!(d > 0.0) || !std::isfinite(d)) return false;
+        const double r = std::sqrt(d);
+        l[(size_t)j * n + j] = r;
+        for (int i = j + 1; i < n; ++i) {
+            double s = a[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) s -= l[(size_t)i * n + k] * l[(size_t)j * n + k];
+            l[(size_t)i * n + j] = s / r;
+        }
+    }
+    return true;
+}
+
+// x = (L L^T)^-1 b for one right-hand side, in place
+void chol_solve(int n, const std::vector<double> &l, double *x) {
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < i; ++k) x[i] -= l[(size_t)i * n + k] * x[k];
+        x[i] /= l[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        for (int k = i + 1; k < n; ++k) x[i] -= l[(size_t)k * n + i] * x[k];
+        x[i] /= l[(size_t)i * n + i];
+    }
+}
+
+// Gaussian prior on b = A theta (A: m x k, m >= k), mean b0, covariance V (m x m), Eq. 6 with
+// a linear generalised parametrisation. As a function of theta,
+//   (A theta - b0)^T V^-1 (A theta - b0) = (theta - t)^T C^-1 (theta - t) + const
+// with C = (A^T V^-1 A)^-1 and t = C A^T V^-1 b0, so the prior is the covariance block C on
+// theta with mean t (the constant, the part of b0 no theta reaches, does not depend on theta).
+void linear_prior(int m, int k, const std::vector<double> &A, const std::vector<double> &b0,
+                  const std::vector<double> &V, const std::string &w, std::vector<double> &C,
+                  std::vector<double> &t) {
+    std::vector<double> lv, lf;
+    if (!cholesky(m, V, lv)) not_spd(w + ".cov: not positive definite");
+    std::vector<double> X((size_t)m * k), col(m), wb(b0);   // X = V^-1 A, wb = V^-1 b0
+    for (int j = 0; j < k; ++j) {
+        for (int i = 0; i < m; ++i) col[i] = A[(size_t)i * k + j];
+        chol_solve(m, lv, col.data());
+        for (int i = 0; i < m; ++i) X[(size_t)i * k + j] = col[i];
+    }
+    chol_solve(m, lv, wb.data());
+    std::vector<double> F((size_t)k * k, 0.0), g(k, 0.0);   // F = A^T V^-1 A, g = A^T V^-1 b0
+    for (int a = 0; a < k; ++a) {
+        for (int i = 0; i < m; ++i) g[a] += A[(size_t)i * k + a] * wb[i];
+        for (int b = 0; b < k; ++b)
+            for (int i = 0; i < m; ++i) F[(size_t)a * k + b] += A[(size_t)i * k + a] * X[(size_t)i * k + b];
+    }
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < a; ++b) F[(size_t)a * k + b] = F[(size_t)b * k + a] = 0.5 * (F[(size_t)a * k + b] + F[(size_t)b * k + a]);
+    if (!cholesky(k, F, lf)) not_spd(w + ".map: A^T V^-1 A is not positive definite (the map does not fix every parameter)");
+    C.assign((size_t)k * k, 0.0);
+    for (int j = 0; j < k; ++j) {
+        for (int i = 0; i < k; ++i) col[i] = i == j ? 1.0 : 0.0;
+        chol_solve(k, lf, col.data());
+        for (int i = 0; i < k; ++i) C[(size_t)i * k + j] = col[i];
+    }
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < a; ++b) C[(size_t)a * k + b] = C[(size_t)b * k + a] = 0.5 * (C[(size_t)a * k + b] + C[(size_t)b * k + a]);
+    t.assign(k, 0.0);
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) t[a] += C[(size_t)a * k + b] * g[b];
+}
 
 const json::Value &need(const json::Value &o, const std::string &key, const std::string &where) {
     const json::Value *v = o.get(key);
@@ -355,17 +426,36 @@ extern "C" int fit_model_create_json(const char *text, fit_model **out) {
                 const std::string w = "covariances[" + std::to_string(b) + "]";
                 const json::Value &blk = cb->arr[b];
                 const std::vector<int> idx = prm.refs(need(blk, "params", w), w + ".params");
+                const int k = (int)idx.size();
+                const json::Value *mp = blk.get("map");
+                const int m = mp ? (int)arr(*mp, w + ".map").size() : k;
+                std::vector<double> V;
                 const auto &rows = arr(need(blk, "cov", w), w + ".cov");
-                if (rows.size() != idx.size()) bad(w + ".cov: expected " + std::to_string(idx.size()) + " rows");
+                if ((int)rows.size() != m) bad(w + ".cov: expected " + std::to_string(m) + " rows");
                 for (size_t r = 0; r < rows.size(); ++r) {
                     const std::vector<double> row = numbers(rows[r], w + ".cov[" + std::to_string(r) + "]");
-                    if (row.size() != idx.size()) bad(w + ".cov: rows must be square");
-                    cov.insert(cov.end(), row.begin(), row.end());
+                    if ((int)row.size() != m) bad(w + ".cov: rows must be square");
+                    V.insert(V.end(), row.begin(), row.end());
                 }
-                for (int i : idx) {
+                for (int i : idx)
                     if (i < 0) bad(w + ".params: null is not a parameter");
-                    cov_idx.push_back(i);
+                if (mp) {   // prior on b = A theta with mean b0: the equivalent block on theta
+                    if (m < k) bad(w + ".map: fewer rows than parameters");
+                    std::vector<double> A;
+                    for (int r = 0; r < m; ++r) {
+                        const std::vector<double> row = numbers(mp->arr[r], w + ".map[" + std::to_string(r) + "]");
+                        if ((int)row.size() != k) bad(w + ".map: rows need one entry per parameter");
+                        A.insert(A.end(), row.begin(), row.end());
+                    }
+                    const std::vector<double> b0 = numbers(need(blk, "mean", w), w + ".mean");
+                    if ((int)b0.size() != m) bad(w + ".mean: one entry per map row");
+                    std::vector<double> Cb, tb;
+                    linear_prior(m, k, A, b0, V, w, Cb, tb);
+                    for (int i = 0; i < k; ++i) theta0[idx[i]] = tb[i];
+                    V.swap(Cb);
                 }
+                cov.insert(cov.end(), V.begin(), V.end());
+                for (int i : idx) cov_idx.push_back(i);
                 cov_size.push_back((int)idx.size());
             }
         }
@@ -529,7 +619,7 @@ extern "C" int fit_model_create_json(const char *text, fit_model **out) {
         *out = m;
         return FIT_OK;
     } catch (const ConfigError &e) {
-        return fitcore_fail(FIT_ERR_INVALID_CONFIG, "fit_model_create_json: " + e.msg);
+        return fitcore_fail(e.code, "fit_model_create_json: " + e.msg);
     }
 }
 

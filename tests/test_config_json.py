@@ -228,3 +228,47 @@ def test_parameter_namespaces(cfg):
     c = json.loads(text)
     c["parameters"][1]["parameters"].append(dict(c["parameters"][1]["parameters"][0]))
     assert 'duplicate name "det.' in _reject(c)
+
+
+def _mapped_config(seed=3):
+    """c1's configuration with the nine energy-scale coefficients constrained through a
+    12-row linear map (each coefficient measured, plus three random combinations, with
+    correlated errors of the coefficients' own sizes): Eq. 6 with b = A theta. Returns
+    (config, A, b0, V, the coefficient names)."""
+    spec = synth.make_model("c1")
+    cfg = spec.to_config()
+    esc = [f"a{k}[{d}]" for d in range(3) for k in range(3)]
+    rng = np.random.default_rng(seed)
+    A = np.vstack([np.eye(9), rng.standard_normal((3, 9))])
+    w = np.array([0.01, 0.005, 0.001] * 3 + [0.005] * 3)
+    Q = rng.standard_normal((12, 12))
+    R = Q @ Q.T + 12 * np.eye(12)
+    R /= np.sqrt(np.outer(np.diag(R), np.diag(R)))
+    V = R * np.outer(w, w)
+    b0 = A @ np.array([spec.theta0[spec.index(n)] for n in esc]) + 0.5 * w * rng.standard_normal(12)
+    for p in cfg["parameters"]:
+        if p["name"] in esc:
+            p["sigma"] = 0.0
+    cfg["covariances"].append({"params": esc, "map": A.tolist(), "mean": b0.tolist(), "cov": V.tolist()})
+    return cfg, A, b0, V, esc
+
+
+def test_linear_map_priors_are_checked_on_the_host():
+    cfg, A, b0, V, esc = _mapped_config()
+    rc, msg = _create(json.dumps(cfg))
+    assert rc in (0, -4, -6), msg
+    NON_SPD = -3
+    c = copy.deepcopy(cfg)
+    c["covariances"][-1]["map"] = np.zeros_like(A).tolist()
+    rc, msg = _create(json.dumps(c))
+    assert rc == NON_SPD and "does not fix every parameter" in msg
+    c = copy.deepcopy(cfg)
+    c["covariances"][-1]["cov"][0][0] = -1.0
+    rc, msg = _create(json.dumps(c))
+    assert rc == NON_SPD and ".cov: not positive definite" in msg
+    c = copy.deepcopy(cfg)
+    c["covariances"][-1].update(map=A[:5].tolist(), cov=V[:5, :5].tolist(), mean=b0[:5].tolist())
+    assert "fewer rows than parameters" in _reject(c)
+    c = copy.deepcopy(cfg)
+    c["covariances"][-1]["mean"] = b0[:4].tolist()
+    assert "one entry per map row" in _reject(c)

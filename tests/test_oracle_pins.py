@@ -607,3 +607,47 @@ def test_event_spectrum_is_the_per_event_sum(geometry):
     for e, c, w, b in zip(ev.energy, ev.core, ev.weight, ev.bin):
         ref[b] += float(w) * oracle.survival(ev.osc_mode, p, ev.core_L[c], float(e))
     np.testing.assert_allclose(oracle.event_spectrum(ev, p), ref, rtol=1e-13, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------------------
+# Eq. 6 with a linear generalised parametrisation b = A theta
+# ---------------------------------------------------------------------------------------
+def _spd(rng, n):
+    Q = rng.standard_normal((n, n))
+    return Q @ Q.T + n * np.eye(n)
+
+
+def test_linear_prior_block_reproduces_the_quadratic_form():
+    """9 constrained coefficients from 7 parameters (the energy-scale case of the detector
+    response): at random points the two quadratic forms differ by one constant, which is >= 0
+    and equals the form's minimum over theta."""
+    rng = np.random.default_rng(11)
+    m, k = 9, 7
+    A, b0, V = rng.standard_normal((m, k)), rng.standard_normal(m), _spd(rng, m)
+    t, Cb, const = oracle.linear_prior_block(A, b0, V)
+    Vi, Ci = np.linalg.inv(V), np.linalg.inv(Cb)
+    for _ in range(20):
+        th = t + rng.standard_normal(k)
+        full = (A @ th - b0) @ Vi @ (A @ th - b0)
+        assert full == pytest.approx((th - t) @ Ci @ (th - t) + const, rel=1e-10, abs=1e-10)
+    assert const >= -1e-12
+    # the minimum over theta by a generic minimiser sits at t with value const
+    from scipy.optimize import minimize
+    f = lambda th: (A @ th - b0) @ Vi @ (A @ th - b0)
+    r = minimize(f, np.zeros(k), method="BFGS", options={"gtol": 1e-10})
+    np.testing.assert_allclose(r.x, t, atol=1e-6)
+    assert r.fun == pytest.approx(const, abs=1e-8)
+
+
+def test_linear_prior_block_special_cases():
+    rng = np.random.default_rng(12)
+    V, b0 = _spd(rng, 4), rng.standard_normal(4)
+    t, Cb, const = oracle.linear_prior_block(np.eye(4), b0, V)
+    np.testing.assert_allclose(t, b0, rtol=1e-12)
+    np.testing.assert_allclose(Cb, V, rtol=1e-10)
+    assert abs(const) < 1e-10
+    # one parameter measured twice with independent errors: inverse-variance mean
+    t, Cb, const = oracle.linear_prior_block([[1.0], [1.0]], [1.0, 3.0], np.diag([1.0, 4.0]))
+    assert t[0] == pytest.approx((1.0 / 1 + 3.0 / 4) / (1 / 1 + 1 / 4), rel=1e-14)
+    assert Cb[0, 0] == pytest.approx(1 / (1 + 1 / 4), rel=1e-14)
+    assert const == pytest.approx((1.0 - t[0]) ** 2 + (3.0 - t[0]) ** 2 / 4, rel=1e-12)
