@@ -11,7 +11,6 @@
 #include <cstring>
 #include <functional>
 #include <map>
-#include <memory>
 #include <string>
 #include <vector>
 
