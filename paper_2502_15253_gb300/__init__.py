@@ -1,8 +1,10 @@
 """GB300-native forward-folding likelihood fits (PhyLiNO, arXiv 2502.15253).
 
 Submodules:
-  synth    - seeded synthetic model descriptions, ensembles and pseudo-data (inputs only)
-  fitcore  - ctypes binding of the C ABI of libfitcore.so (include/fitcore.h)
-  build    - nvcc build of libfitcore.so for sm_103a
+  synth     - seeded synthetic model descriptions, ensembles and pseudo-data (inputs only)
+  fitcore   - ctypes binding of the C ABI of libfitcore.so (include/fitcore.h)
+  ensemble  - checkpointed ensemble fits and their JSON-lines output (host orchestration)
+  warmstart - the warm-start network's argument tables and weight files
+  build     - nvcc build of libfitcore.so for sm_103a
 """
-__all__ = ["synth", "fitcore", "build"]
+__all__ = ["synth", "fitcore", "ensemble", "warmstart", "build"]
