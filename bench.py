@@ -379,11 +379,12 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
     }
 
 
-# DRAM bytes (read + write) per fit of fit_kernel on the three-dataset model, from ncu captures
-# of one 760-fit launch each: the preconditioned build (default; 4.39 MB read, 14.58 MB written,
-# mostly the workspace write-back) and the plain one (7.30 MB, 47.86 MB); traffic grows with
-# the fits
-FIT_DRAM_BYTES_PER_FIT = {1: (4.394240e6 + 14.576896e6) / 760, 0: (7.301632e6 + 47.855360e6) / 760}
+# DRAM bytes (read + write) per fit of fit_kernel on the three-dataset model, from an ncu
+# capture of one 760-fit launch of the preconditioned build (the default; 4.39 MB read,
+# 14.58 MB written, mostly the workspace write-back); traffic grows with the fits. The plain
+# build's capture (7.30 MB, 47.86 MB) predates later changes of the kernel, so a run with
+# --no-precondition reports no traffic.
+FIT_DRAM_BYTES_PER_FIT = (4.394240e6 + 14.576896e6) / 760
 
 # DRAM bytes (read + write) per event of mc_spectrum_kernel for one parameter set, from an ncu
 # capture of 11,904,680 events (154.81 MB read, 3.62 MB written); traffic grows with the events
@@ -747,9 +748,11 @@ def run_ours(args):
             "converged_frac": conv,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                          "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                         "traffic": FIT_DRAM_BYTES_PER_FIT[1 if opts.precondition else 0] * B,
-                         "traffic_note": "DRAM read+write bytes per fit of an ncu capture of "
-                                         "this kernel (760 fits), scaled to the launch",
+                         "traffic": FIT_DRAM_BYTES_PER_FIT * B if opts.precondition else None,
+                         "traffic_note": ("DRAM read+write bytes per fit of an ncu capture of "
+                                          "this kernel (760 fits), scaled to the launch"
+                                          if opts.precondition else
+                                          "no capture of the current plain build"),
                          "kernel": "fit_kernel",
                          "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"},
             "e2e": {"value": world * B / e2e_s, "unit": "fits/s", "h2d_bytes_per_step": int(h2d),
