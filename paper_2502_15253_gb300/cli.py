@@ -1,0 +1,111 @@
+"""Command-line driver: configuration in, fits on the GPU, JSON records out.
+
+The three steps follow the framework's structure ([S]): a configuration file names the model,
+the library fits every pseudo-experiment, and each best fit is written as a JSON record.
+
+  python -m paper_2502_15253_gb300.cli config --model c1 [--spline] > c1.json
+  python -m paper_2502_15253_gb300.cli pseudo --config c1.json --n 64 --seed 1 --out data.npy
+  python -m paper_2502_15253_gb300.cli fit --config c1.json --data data.npy --out fits.jsonl \\
+      [--mask 7] [--chunk 4096] [--checkpoint fits.npz] [--no-precondition]
+
+`config` writes the JSON configuration of a synthetic model. `pseudo` draws Poisson
+pseudo-data at the nominal point on the device (fit_model_expected, fit_poisson_sample).
+`fit` fits each row of a [n, n_data] float32 .npy file from the nominal point and writes one
+fit_result_json line per row; with --checkpoint an interrupted run resumes. This module only
+orchestrates: every computation runs in the library.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+
+import numpy as np
+
+from . import ensemble, fitcore, synth
+
+
+def _parser():
+    p = argparse.ArgumentParser(prog="python -m paper_2502_15253_gb300.cli")
+    sub = p.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("config", help="write the JSON configuration of a synthetic model")
+    c.add_argument("--model", required=True, choices=["c0", "c0_tiny", "c1", "c2", "c1s", "c1_flux41"])
+    c.add_argument("--spline", action="store_true", help="area-conserving spline energy correction")
+    c.add_argument("--seed", type=int, default=synth.BASE_SEED)
+    c.add_argument("--out", default="-")
+    q = sub.add_parser("pseudo", help="Poisson pseudo-data at the nominal point (GPU)")
+    q.add_argument("--config", required=True)
+    q.add_argument("--n", type=int, default=16)
+    q.add_argument("--seed", type=int, default=1)
+    q.add_argument("--out", required=True)
+    f = sub.add_parser("fit", help="fit every row of a data file (GPU)")
+    f.add_argument("--config", required=True)
+    f.add_argument("--data", required=True)
+    f.add_argument("--out", required=True)
+    f.add_argument("--mask", type=int, default=0, help="datasets in the likelihood (0 = all)")
+    f.add_argument("--chunk", type=int, default=4096)
+    f.add_argument("--checkpoint", default=None)
+    f.add_argument("--no-precondition", action="store_true")
+    return p
+
+
+def _read_config(path):
+    with open(path) as fh:
+        return fh.read()
+
+
+def _load_data(path, model):
+    data = np.load(path)
+    data = np.ascontiguousarray(np.atleast_2d(data), dtype=np.float32)
+    if data.shape[1] != model.n_data:
+        raise SystemExit(f"{path}: rows hold {data.shape[1]} bins, the model has {model.n_data}")
+    return data
+
+
+def main(argv=None, model_factory=None, fit_fn=None, write_fn=None):
+    """Runs one command. model_factory(json_text) -> model, fit_fn (see ensemble.fit_ensemble)
+    and write_fn(path, models, inst, best, results) replace the library calls in tests."""
+    a = _parser().parse_args(argv)
+    if a.cmd == "config":
+        text = synth.make_model(a.model, a.seed, remap=int(a.spline)).to_json()
+        if a.out == "-":
+            sys.stdout.write(text + "\n")
+        else:
+            with open(a.out, "w") as fh:
+                fh.write(text + "\n")
+        return 0
+    make = model_factory or fitcore.Model.from_json
+    model = make(_read_config(a.config))
+    if a.cmd == "pseudo":
+        if a.n < 1:
+            raise SystemExit("--n must be >= 1")
+        th0, _ = model.params()
+        mu = np.zeros((1, model.n_data), np.float32)
+        fitcore.fit_model_expected(model, 1, th0[None], mu)
+        mu = np.repeat(mu, a.n, axis=0)
+        out = np.zeros_like(mu)
+        fitcore.fit_poisson_sample(mu.size, mu, a.seed, 0, out)
+        np.save(a.out, out)
+        return 0
+    data = _load_data(a.data, model)
+    n = len(data)
+    inst = np.zeros(n, fitcore.INSTANCE_DTYPE)
+    inst["mask"] = a.mask if a.mask else (1 << model.n_datasets) - 1
+    inst["data_off"] = np.arange(n) * model.n_data
+    inst["param_off"] = np.arange(n) * model.n_params
+    th0, _ = model.params()
+    start = np.tile(th0, n)
+    opts = None
+    if fit_fn is None:
+        opts = fitcore.fit_batch_default_opts()
+        opts.precondition = 0 if a.no_precondition else 1
+    best, res = ensemble.fit_ensemble([model], inst, data, start=start, opts=opts, chunk=a.chunk,
+                                      checkpoint=a.checkpoint, fit_fn=fit_fn)
+    (write_fn or ensemble.write_results_json)(a.out, [model], inst, best, res)
+    bad = int(np.sum(res["status"] != 0))
+    print(json.dumps({"fits": n, "not_converged": bad, "out": a.out}))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

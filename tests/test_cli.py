@@ -1,0 +1,68 @@
+"""Command-line driver (host orchestration): the configuration it writes, and the fit command's
+instance table, checkpointing and output with the library calls replaced by stand-ins."""
+import json
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from paper_2502_15253_gb300 import cli, fitcore, synth
+
+
+def test_config_command_writes_the_model_configuration(tmp_path):
+    out = tmp_path / "c1.json"
+    assert cli.main(["config", "--model", "c1", "--spline", "--out", str(out)]) == 0
+    cfg = json.loads(out.read_text())
+    assert cfg == json.loads(synth.make_model("c1", remap=1).to_json())
+    assert cfg["energy_correction"] == "spline"
+
+
+def test_fit_command_fits_every_row_and_resumes(tmp_path, capsys):
+    spec = synth.make_model("c0")
+    cfg = tmp_path / "c0.json"
+    cfg.write_text(spec.to_json())
+    n = 11
+    data = np.random.default_rng(0).poisson(50.0, (n, spec.n_bins)).astype(np.float32)
+    np.save(tmp_path / "d.npy", data)
+    model = SimpleNamespace(n_data=spec.n_bins, n_params=spec.n_params,
+                            n_datasets=len(spec.datasets),
+                            params=lambda: (spec.theta0.copy(), spec.prior_sigma.copy()))
+    seen, written = [], {}
+
+    def fit_fn(models, sub, d, start, opts, fixed):
+        seen.append(len(sub))
+        assert np.all(sub["mask"] == 1) and d.shape == (n, spec.n_bins)
+        best = np.array(start, dtype=np.float64)
+        res = np.zeros(len(sub), fitcore.RESULT_DTYPE)
+        res["iters"] = sub["data_off"] // spec.n_bins
+        return best, res
+
+    def write_fn(path, models, inst, best, res):
+        written.update(path=path, best=best.copy(), res=res.copy(), inst=inst.copy())
+
+    argv = ["fit", "--config", str(cfg), "--data", str(tmp_path / "d.npy"), "--out",
+            str(tmp_path / "f.jsonl"), "--chunk", "4", "--checkpoint", str(tmp_path / "ck.npz")]
+    assert cli.main(argv, model_factory=lambda text: model, fit_fn=fit_fn, write_fn=write_fn) == 0
+    assert seen == [4, 4, 3]
+    assert json.loads(capsys.readouterr().out.strip().splitlines()[-1]) == {
+        "fits": n, "not_converged": 0, "out": str(tmp_path / "f.jsonl")}
+    np.testing.assert_array_equal(written["res"]["iters"], np.arange(n))
+    np.testing.assert_array_equal(written["best"], np.tile(spec.theta0, n))
+    np.testing.assert_array_equal(written["inst"]["param_off"], np.arange(n) * spec.n_params)
+    # the same command again finds every instance done in its checkpoint
+    seen.clear()
+    assert cli.main(argv, model_factory=lambda text: model, fit_fn=fit_fn, write_fn=write_fn) == 0
+    assert seen == []
+
+
+def test_fit_command_rejects_data_of_another_model(tmp_path):
+    spec = synth.make_model("c0")
+    cfg = tmp_path / "c0.json"
+    cfg.write_text(spec.to_json())
+    np.save(tmp_path / "d.npy", np.zeros((2, spec.n_bins + 1), np.float32))
+    model = SimpleNamespace(n_data=spec.n_bins, n_params=spec.n_params, n_datasets=1,
+                            params=lambda: (spec.theta0, spec.prior_sigma))
+    with pytest.raises(SystemExit, match="bins"):
+        cli.main(["fit", "--config", str(cfg), "--data", str(tmp_path / "d.npy"), "--out",
+                  str(tmp_path / "f.jsonl")], model_factory=lambda text: model,
+                 fit_fn=lambda *a: None)
