@@ -192,10 +192,10 @@ def dist_setup(args):
 
 
 def shard_range(n_total, rank, world):
-    """Contiguous share of n_total units for a rank (the first n_total % world ranks get +1)."""
-    base, rem = divmod(n_total, world)
-    lo = rank * base + min(rank, rem)
-    return lo, lo + base + (1 if rank < rem else 0)
+    """Contiguous share of n_total units for a rank (the first n_total % world ranks get +1),
+    the same split as the library's sharded ensembles."""
+    from paper_2502_15253_gb300.ensemble import shard
+    return shard(n_total, rank, world)
 
 
 def max_over_ranks(x, pg):

@@ -105,3 +105,43 @@ def write_results_json(path, models, inst, best, results):
             o = int(inst[i]["param_off"])
             f.write(fitcore.fit_result_json(m, best[o:o + m.n_params], r) + "\n")
     os.replace(tmp, path)
+
+
+def shard(n_total, rank, world):
+    """Contiguous share [lo, hi) of n_total instances for a rank; the first n_total % world
+    ranks take one more."""
+    base, rem = divmod(n_total, world)
+    lo = rank * base + min(rank, rem)
+    return lo, lo + base + (1 if rank < rem else 0)
+
+
+def fit_ensemble_sharded(models, inst, data, start=None, opts=None, fixed=None, chunk=4096,
+                         checkpoint=None, fit_fn=None, group=None):
+    """fit_ensemble over the ranks of a torch.distributed process group, one GPU per rank.
+
+    Pseudo-experiments are independent ([S]: parallel fits, with MPI across processes), so
+    each rank fits a contiguous share of `inst` (its own checkpoint file `<checkpoint>.rank<r>`)
+    and the results meet on the host in one all_gather of Python objects at the end: no
+    collective runs during the fits. Every rank returns the whole (best, results)."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
+    rank = dist.get_rank(group) if world > 1 else 0
+    inst = np.ascontiguousarray(inst, dtype=fitcore.INSTANCE_DTYPE)
+    if world == 1:
+        return fit_ensemble(models, inst, data, start, opts, fixed, chunk, checkpoint, fit_fn)
+    lo, hi = shard(len(inst), rank, world)
+    ck = f"{checkpoint}.rank{rank}" if checkpoint else None
+    b, r = fit_ensemble(models, inst[lo:hi], data, start, opts, fixed, chunk, ck, fit_fn)
+    sl = [b[int(q["param_off"]):int(q["param_off"]) + models[int(q["model"])].n_params]
+          for q in inst[lo:hi]]
+    parts = [None] * world
+    dist.all_gather_object(parts, (lo, hi, sl, r.tobytes()), group=group)
+    npar = max((int(q["param_off"]) + models[int(q["model"])].n_params for q in inst), default=0)
+    best = np.zeros(npar)
+    res = np.zeros(len(inst), fitcore.RESULT_DTYPE)
+    for plo, phi, psl, pres in parts:
+        res[plo:phi] = np.frombuffer(pres, dtype=fitcore.RESULT_DTYPE)
+        for i, v in zip(range(plo, phi), psl):
+            o = int(inst[i]["param_off"])
+            best[o:o + len(v)] = v
+    return best, res

@@ -108,3 +108,42 @@ def test_network_weights_round_trip_on_disk(tmp_path):
         warmstart.save_layers(p, dims, layers[:2])
     with pytest.raises(ValueError):
         warmstart.save_layers(p, (10, 8, 2, 4), layers)
+
+
+def _sharded_worker(rank, world, port, out_dir, ck):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world),
+                      RANK=str(rank))
+    import torch.distributed as dist
+    from paper_2502_15253_gb300.ensemble import fit_ensemble_sharded
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    models, inst, data = _job()
+    log = []
+    best, res = fit_ensemble_sharded(models, inst, data, chunk=5, checkpoint=ck, fit_fn=_fake(log))
+    np.save(os.path.join(out_dir, f"best{rank}.npy"), best)
+    np.save(os.path.join(out_dir, f"res{rank}.npy"), res.view(np.uint8))
+    np.save(os.path.join(out_dir, f"log{rank}.npy"), np.array(log))
+    dist.destroy_process_group()
+
+
+def test_sharded_ensemble_over_two_gloo_ranks(tmp_path):
+    """Two ranks split the 37 instances (19 + 18), fit them with no collective, gather on the
+    host, and both return the single-process result; each kept its own checkpoint."""
+    torch = pytest.importorskip("torch")
+    import socket
+    import torch.multiprocessing as mp
+    if torch.cuda.is_available():
+        pytest.skip("the host-only (gloo) path is exercised where no GPU is visible")
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ck = str(tmp_path / "ens.npz")
+    mp.spawn(_sharded_worker, args=(2, port, str(tmp_path), ck), nprocs=2, join=True)
+    models, inst, data = _job()
+    ref_best, ref_res = fit_ensemble(models, inst, data, chunk=5, fit_fn=_fake([]))
+    for r in range(2):
+        np.testing.assert_array_equal(np.load(tmp_path / f"best{r}.npy"), ref_best)
+        got = np.load(tmp_path / f"res{r}.npy").view(fitcore.RESULT_DTYPE)
+        np.testing.assert_array_equal(got, ref_res)
+        assert os.path.exists(ck + f".rank{r}")
+    assert list(np.load(tmp_path / "log0.npy")) == [5, 5, 5, 4]
+    assert list(np.load(tmp_path / "log1.npy")) == [5, 5, 5, 3]
