@@ -11,7 +11,8 @@ the library fits every pseudo-experiment, and each best fit is written as a JSON
 `config` writes the JSON configuration of a synthetic model. `pseudo` draws Poisson
 pseudo-data at the nominal point on the device (fit_model_expected, fit_poisson_sample).
 `fit` fits each row of a [n, n_data] float32 .npy file from the nominal point and writes one
-fit_result_json line per row; with --checkpoint an interrupted run resumes. This module only
+fit_result_json line per row; with --checkpoint an interrupted run resumes. Under torchrun the
+rows are split over the ranks (one GPU each) and rank 0 writes the records. This module only
 orchestrates: every computation runs in the library.
 """
 from __future__ import annotations
@@ -99,13 +100,37 @@ def main(argv=None, model_factory=None, fit_fn=None, write_fn=None):
     if fit_fn is None:
         opts = fitcore.fit_batch_default_opts()
         opts.precondition = 0 if a.no_precondition else 1
-    best, res = ensemble.fit_ensemble([model], inst, data, start=start, opts=opts, chunk=a.chunk,
-                                      checkpoint=a.checkpoint, fit_fn=fit_fn)
-    (write_fn or ensemble.write_results_json)(a.out, [model], inst, best, res)
-    bad = int(np.sum(res["status"] != 0))
-    print(json.dumps({"fits": n, "not_converged": bad, "out": a.out}))
+    best, res = ensemble.fit_ensemble_sharded([model], inst, data, start=start, opts=opts,
+                                              chunk=a.chunk, checkpoint=a.checkpoint,
+                                              fit_fn=fit_fn)
+    if _rank() == 0:
+        (write_fn or ensemble.write_results_json)(a.out, [model], inst, best, res)
+        bad = int(np.sum(res["status"] != 0))
+        print(json.dumps({"fits": n, "not_converged": bad, "out": a.out}))
     return 0
 
 
+def _rank():
+    try:
+        import torch.distributed as dist
+        return dist.get_rank() if dist.is_available() and dist.is_initialized() else 0
+    except ImportError:
+        return 0
+
+
+def _init_distributed():
+    """Under torchrun (WORLD_SIZE > 1): one process per GPU, the instances split over the ranks
+    and the results gathered on the host (ensemble.fit_ensemble_sharded)."""
+    import os
+    if int(os.environ.get("WORLD_SIZE", "1")) <= 1:
+        return
+    import torch
+    import torch.distributed as dist
+    if torch.cuda.is_available():
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist.init_process_group("gloo")   # the only exchange is the host-side gather of results
+
+
 if __name__ == "__main__":
+    _init_distributed()
     sys.exit(main())

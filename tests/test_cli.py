@@ -66,3 +66,51 @@ def test_fit_command_rejects_data_of_another_model(tmp_path):
         cli.main(["fit", "--config", str(cfg), "--data", str(tmp_path / "d.npy"), "--out",
                   str(tmp_path / "f.jsonl")], model_factory=lambda text: model,
                  fit_fn=lambda *a: None)
+
+
+def _cli_worker(rank, world, port, d):
+    import os
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world),
+                      RANK=str(rank), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    from paper_2502_15253_gb300 import cli as c
+    c._init_distributed()
+    spec = synth.make_model("c0")
+    model = SimpleNamespace(n_data=spec.n_bins, n_params=spec.n_params, n_datasets=1,
+                            params=lambda: (spec.theta0.copy(), spec.prior_sigma.copy()))
+
+    def fit_fn(models, sub, data, start, opts, fixed):
+        res = np.zeros(len(sub), fitcore.RESULT_DTYPE)
+        res["iters"] = sub["data_off"] // spec.n_bins
+        res["n_evals"] = rank
+        return np.array(start, dtype=np.float64), res
+
+    def write_fn(path, models, inst, best, res):
+        np.save(path, res.view(np.uint8))
+
+    c.main(["fit", "--config", os.path.join(d, "c0.json"), "--data", os.path.join(d, "d.npy"),
+            "--out", os.path.join(d, f"out{rank}.npy"), "--chunk", "3"],
+           model_factory=lambda text: model, fit_fn=fit_fn, write_fn=write_fn)
+    dist.destroy_process_group()
+
+
+def test_fit_command_under_two_gloo_ranks(tmp_path):
+    """Under torchrun-style environment variables the fit command splits the rows over the
+    ranks; rank 0 alone writes every row's record."""
+    torch = pytest.importorskip("torch")
+    import socket
+    import torch.multiprocessing as mp
+    if torch.cuda.is_available():
+        pytest.skip("the host-only (gloo) path is exercised where no GPU is visible")
+    spec = synth.make_model("c0")
+    (tmp_path / "c0.json").write_text(spec.to_json())
+    n = 9
+    np.save(tmp_path / "d.npy", np.ones((n, spec.n_bins), np.float32))
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.spawn(_cli_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    assert not (tmp_path / "out1.npy").exists()
+    res = np.load(tmp_path / "out0.npy").view(fitcore.RESULT_DTYPE)
+    np.testing.assert_array_equal(res["iters"], np.arange(n))
+    np.testing.assert_array_equal(res["n_evals"], [0] * 5 + [1] * 4)   # rows 0-4 on rank 0
