@@ -478,12 +478,17 @@ def profile_measurement(args, spec, model, data_h, pg, world):
     g1 = np.linspace(0.0, 0.2, 81)
     r1 = fitcore.fit_profile_scan(model, data, mask, [i13], g1)
     lo, hi, op = fitcore.fit_wilks_interval(g1, r1["dchi2"], 1.0)
+    # goodness of fit: chi^2 with (bins - free parameters without any prior) degrees of freedom
+    in_block = np.zeros(spec.n_params, bool)
+    for ix, _ in spec.cov_blocks:
+        in_block[np.asarray(ix)] = True
+    dof = D - int(np.sum((spec.prior_sigma == 0) & ~in_block))
     out = {"raster": "32 x 32 in sin^2 2th13 [0.05, 0.13] x dm2_ee [2.3e-3, 2.7e-3], plus the "
                      "unconstrained fit, one launch",
            "fits": len(pts) + 1, "s": dt, "raster_points_per_s": world * len(pts) / dt,
            "converged_frac": float(np.mean(r["status"] == 0)),
            "wilks_1sigma_sin2_2th13": [lo, hi], "wilks_open": int(op),
-           "gof_p": fitcore.fit_chi2_sf(r1["nll_min"], D - 2), "gof_dof": D - 2}
+           "gof_p": fitcore.fit_chi2_sf(r1["nll_min"], dof), "gof_dof": dof}
     spec2 = synth.make_model("c2")
     m2 = fitcore.Model(spec2)
     asimov, _ = fitcore.expected_numpy(m2, spec2.theta0[None, :])
