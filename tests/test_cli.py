@@ -114,3 +114,43 @@ def test_fit_command_under_two_gloo_ranks(tmp_path):
     res = np.load(tmp_path / "out0.npy").view(fitcore.RESULT_DTYPE)
     np.testing.assert_array_equal(res["iters"], np.arange(n))
     np.testing.assert_array_equal(res["n_evals"], [0] * 5 + [1] * 4)   # rows 0-4 on rank 0
+
+
+def test_scan_command_reports_profile_intervals_and_goodness_of_fit(tmp_path, capsys):
+    """The scan command with the library's profile fit replaced by a parabola of width 0.02
+    around 0.09: Wilks intervals at +-1 and +-1.96 widths; the goodness of fit counts the
+    bins of the selected datasets minus the parameters without a prior (c0: 40 - 2)."""
+    from scipy import stats
+    spec = synth.make_model("c0")
+    (tmp_path / "c0.json").write_text(spec.to_json())
+    np.save(tmp_path / "d.npy", np.ones((3, spec.n_bins), np.float32))
+    sigma = spec.prior_sigma.copy()   # as fit_model_params reports them: sqrt(V_ii) in blocks
+    for ix, cov in spec.cov_blocks:
+        sigma[np.asarray(ix)] = np.sqrt(np.diag(cov))
+    model = SimpleNamespace(n_data=spec.n_bins, n_params=spec.n_params, n_datasets=1,
+                            params=lambda: (spec.theta0.copy(), sigma),
+                            param_names=lambda: list(spec.param_names))
+    calls = []
+
+    def scan_fn(m, data, mask, idx, pts):
+        calls.append((data.shape, mask, list(idx)))
+        x = pts[:, 0]
+        return dict(nll_min=41.0, theta_best=spec.theta0, dchi2=((x - 0.09) / 0.02) ** 2,
+                    status=np.zeros(len(x), np.int32))
+
+    fitcore.load()
+    argv = ["scan", "--config", str(tmp_path / "c0.json"), "--data", str(tmp_path / "d.npy"),
+            "--row", "2", "--param", "sin2_2th13", "--lo", "0.0", "--hi", "0.2", "--points", "201"]
+    assert cli.main(argv, model_factory=lambda t: model, scan_fn=scan_fn) == 0
+    out = json.loads(capsys.readouterr().out)
+    assert calls == [((spec.n_bins,), 1, [spec.index("sin2_2th13")])]
+    w1, w2 = out["wilks"]["1.0"], out["wilks"]["3.84"]
+    assert w1["lo"] == pytest.approx(0.07, abs=1e-5) and w1["hi"] == pytest.approx(0.11, abs=1e-5)
+    assert w2["lo"] == pytest.approx(0.09 - 0.02 * 3.84 ** 0.5, abs=1e-5)
+    assert not (w1["open_low"] or w1["open_high"])
+    assert out["gof"]["dof"] == 38
+    assert out["gof"]["p"] == pytest.approx(stats.chi2.sf(41.0, 38), rel=1e-9)
+    assert out["best"]["sin2_2th13"] == spec.theta0[0] and out["status"][0] == "converged"
+    with pytest.raises(SystemExit, match="not a parameter"):
+        cli.main(argv[:7] + ["--param", "nope"] + argv[9:], model_factory=lambda t: model,
+                 scan_fn=scan_fn)
