@@ -99,3 +99,31 @@ def test_model_options_are_validated_on_the_host():
     s.osc_idx[4] = -1
     s.osc_val[4] = 1.5
     assert "2th14" in _create_error(s)
+
+
+def test_fit_options_are_validated_before_any_model_or_device_access():
+    """fit_batch checks its options first: a bad history, restart count, block size or
+    stopping rule is INVALID_ARG with a message naming it, before the models are read (the
+    model handle here is a placeholder that must never be dereferenced) or the device used."""
+    L = fitcore.load()
+    fake = (ctypes.c_void_p * 1)(ctypes.c_void_p(8))
+    inst = np.zeros(1, fitcore.INSTANCE_DTYPE)
+    buf = np.zeros(64)
+    res = np.zeros(1, fitcore.RESULT_DTYPE)
+    cases = [("history", 0, "history must be 1..32"), ("history", 33, "history must be 1..32"),
+             ("restarts", 9, "restarts must be 0..8"), ("threads", 48, "threads must be"),
+             ("threads", 100, "threads must be"), ("edm_tol", 0.0, "edm_tol / max_iter"),
+             ("max_iter", -1, "edm_tol / max_iter")]
+    for field, value, msg in cases:
+        o = fitcore.fit_batch_default_opts()
+        setattr(o, field, value)
+        rc = L.fit_batch(fake, 1, inst.ctypes.data, 1, buf.ctypes.data, None, buf.ctypes.data,
+                         res.ctypes.data, ctypes.byref(o), None)
+        assert rc == -1, field
+        assert msg in L.fit_last_error().decode(), (field, L.fit_last_error())
+    assert L.fit_batch(None, 1, inst.ctypes.data, 1, buf.ctypes.data, None, buf.ctypes.data,
+                       res.ctypes.data, None, None) == -1
+    # no instances: nothing to do, and nothing is read
+    o = fitcore.fit_batch_default_opts()
+    assert L.fit_batch(fake, 1, inst.ctypes.data, 0, buf.ctypes.data, None, buf.ctypes.data,
+                       res.ctypes.data, ctypes.byref(o), None) == 0
