@@ -154,6 +154,7 @@ class ModelSpec:
 
         formula = {OSC_EQ1: "eq1", OSC_VACUUM3: "vacuum3", OSC_STERILE4: "sterile4"}[self.osc_mode]
         return {
+            "name": self.name,
             "parameters": [{"name": n, "value": float(v), "sigma": float(s), "scale": float(c)}
                            for n, v, s, c in zip(names, self.theta0, self.prior_sigma, self.scale)],
             "covariances": [{"params": refs(ix), "cov": [nums(r) for r in np.asarray(cv)]}
@@ -164,7 +165,8 @@ class ModelSpec:
             "true_grid": {"bins": int(self.n_true), "e_lo": float(self.e_lo), "e_hi": float(self.e_hi)},
             "energy_correction": "spline" if int(self.remap) == 1 else "overlap",
             "core_powers": refs(self.core_power_idx),
-            "detectors": [{"name": dt.name, "response": [nums(r) for r in dt.response]}
+            "detectors": [{"name": dt.name, "reco_edges": nums(dt.reco_edges),
+                           "response": [nums(r) for r in dt.response]}
                           for dt in self.detectors],
             "datasets": [{"name": x.name, "detector": self.detectors[x.det].name,
                           "t": nums(x.t), "baseline": nums(x.baseline), "weight": nums(x.weight),
@@ -179,6 +181,75 @@ class ModelSpec:
     def to_json(self) -> str:
         import json
         return json.dumps(self.to_config())
+
+    @classmethod
+    def from_config(cls, cfg) -> "ModelSpec":
+        """The description held by a JSON configuration (a dict or its text) in the schema of
+        fit_model_create_json: names resolved (namespaces flattened to "ns.name"), held
+        entries as -1. Priors given through a linear map (b = A theta) are not read here:
+        their conversion belongs to the model, not to the input description."""
+        import json
+        if isinstance(cfg, (str, bytes)):
+            cfg = json.loads(cfg)
+        names, th0, sig, scl = [], [], [], []
+
+        def add(entries, prefix):
+            for e in entries:
+                if "namespace" in e:
+                    add(e["parameters"], prefix + e["namespace"] + ".")
+                    continue
+                names.append(prefix + e["name"])
+                th0.append(float(e["value"]))
+                sig.append(float(e.get("sigma", 0.0)))
+                scl.append(float(e.get("scale", 0.0)))
+
+        add(cfg["parameters"], "")
+        index = {n: i for i, n in enumerate(names)}
+        if len(index) != len(names):
+            raise ValueError("duplicate parameter names")
+
+        def ref(v):
+            if v is None:
+                return -1
+            return index[v] if isinstance(v, str) else int(v)
+
+        def refs(vs):
+            return np.array([ref(v) for v in vs], np.int32)
+
+        cov_blocks = []
+        for b in cfg.get("covariances", []):
+            if "map" in b:
+                raise ValueError("a prior on b = A theta is converted by the model, not read here")
+            cov_blocks.append((refs(b["params"]), np.array(b["cov"], np.float64)))
+        osc = cfg["oscillation"]
+        mode = {"eq1": OSC_EQ1, "vacuum3": OSC_VACUUM3, "sterile4": OSC_STERILE4}[osc["formula"]]
+        osc_idx = np.array([ref(e) if isinstance(e, str) else -1 for e in osc["params"]], np.int32)
+        osc_val = np.array([th0[index[e]] if isinstance(e, str) else float(e) for e in osc["params"]])
+        grid = cfg["true_grid"]
+        n_true = int(grid["bins"])
+        dets, det_index = [], {}
+        for k, d in enumerate(cfg["detectors"]):
+            resp = np.array(d["response"], np.float64).reshape(-1, n_true)
+            edges = np.array(d.get("reco_edges", np.arange(len(resp) + 1)), np.float64)
+            dets.append(Detector(d.get("name", f"det{k}"), edges, resp))
+            det_index[dets[-1].name] = k
+        datasets = []
+        for k, d in enumerate(cfg["datasets"]):
+            det = det_index[d["detector"]] if isinstance(d["detector"], str) else int(d["detector"])
+            nr = dets[det].n_reco
+            bkgs = [Background(b.get("name", f"bkg{j}"), np.array(b["template"], np.float64),
+                               ref(b.get("rate")), refs(b.get("shape", [None] * nr)))
+                    for j, b in enumerate(d.get("backgrounds", []))]
+            datasets.append(Dataset(d.get("name", f"ds{k}"), det, np.array(d["t"], np.float64),
+                                    np.array(d["baseline"], np.float64),
+                                    np.array(d["weight"], np.float64), ref(d.get("norm")),
+                                    ref(d.get("efficiency")),
+                                    refs(d.get("escale", [None] * 3)),
+                                    refs(d.get("shape", [None] * n_true)), bkgs))
+        remap = 1 if cfg.get("energy_correction", "overlap") == "spline" else 0
+        return cls(cfg.get("name", "config"), names, np.array(th0), np.array(sig), np.array(scl),
+                   cov_blocks, mode, osc_idx, osc_val, refs(cfg["core_powers"]), n_true,
+                   float(grid["e_lo"]), float(grid["e_hi"]), dets, datasets, remap)
 
 
 # ----------------------------------------------------------------------------------------

@@ -272,3 +272,42 @@ def test_linear_map_priors_are_checked_on_the_host():
     c = copy.deepcopy(cfg)
     c["covariances"][-1]["mean"] = b0[:4].tolist()
     assert "one entry per map row" in _reject(c)
+
+
+def _same(a, b, path=""):
+    import dataclasses
+    if dataclasses.is_dataclass(a):
+        for f in dataclasses.fields(a):
+            _same(getattr(a, f.name), getattr(b, f.name), path + "." + f.name)
+    elif isinstance(a, (list, tuple)):
+        assert len(a) == len(b), path
+        for i, (x, y) in enumerate(zip(a, b)):
+            _same(x, y, f"{path}[{i}]")
+    elif isinstance(a, np.ndarray):
+        assert np.array_equal(a, np.asarray(b)), path
+        assert np.asarray(b).dtype.kind == a.dtype.kind, path
+    else:
+        assert a == b, (path, a, b)
+
+
+@pytest.mark.parametrize("name", ["c0", "c0_tiny", "c1", "c2", "c1s", "c1_flux41"])
+def test_description_round_trips_through_its_configuration(name):
+    """ModelSpec.from_config(to_config()) is the description again, array for array, so the
+    oracle can be built from any configuration the library reads."""
+    for remap in (0, 1):
+        s = synth.make_model(name, remap=remap)
+        _same(s, synth.ModelSpec.from_config(s.to_json()), name)
+
+
+def test_description_from_a_namespaced_configuration(cfg):
+    text, full = _namespaced(cfg)
+    for short, long_ in full.items():
+        text = text.replace(json.dumps(short), json.dumps(long_))
+    text = text.replace('"name": "osc.', '"name": "').replace('"name": "det.', '"name": "')
+    s = synth.ModelSpec.from_config(text)
+    assert s.param_names[:2] == ["osc.sin2_2th13", "osc.dm2_ee"]
+    assert all(n.startswith(("osc.", "det.")) for n in s.param_names)
+    assert s.osc_idx[0] == 0 and s.osc_idx[1] == 1
+    cfg2, *_ = _mapped_config()
+    with pytest.raises(ValueError, match="converted by the model"):
+        synth.ModelSpec.from_config(cfg2)
