@@ -97,7 +97,8 @@ def _scan(a, model, text, scan_fn):
         wilks[str(level)] = {"lo": lo, "hi": hi, "open_low": bool(op & 1), "open_high": bool(op & 2)}
     _, sigma = model.params()
     dof = _bins_in_mask(json.loads(text), mask) - int(np.sum(sigma == 0))
-    return {"param": a.param, "x": x.tolist(), "dchi2": np.asarray(r["dchi2"]).tolist(),
+    d = [float(v) if np.isfinite(v) else None for v in np.asarray(r["dchi2"])]   # JSON: no NaN
+    return {"param": a.param, "x": x.tolist(), "dchi2": d,
             "status": [fitcore.STATUS.get(int(v), str(int(v))) for v in r["status"]],
             "nll_min": float(r["nll_min"]),
             "best": dict(zip(names, np.asarray(r["theta_best"], dtype=float).tolist())),
