@@ -1,14 +1,20 @@
-"""Benchmark: batched cold-start fits of the two-detector, three-dataset model (FD-I, FD-II, ND;
-291 parameters), fits/s on one or more GPUs.
+"""Benchmark: batched cold-start fits of an uneven ensemble of pseudo-experiments, fits/s on one
+or more GPUs.
 
-One step = one fit_batch() call that fits B Poisson pseudo-experiments from the nominal start:
-every evaluation of the expectation, -2lnL, adjoint gradient and every L-BFGS update runs in
-the persistent fit kernel. Inputs are resident in device memory when the timed region starts;
-L2 is flushed (a 512 MiB write) before every timed step. With torchrun, each rank fits its own
-B instances (weak scaling, no collective on the data path); the step time is the maximum over
-ranks and value = total fits / that time.
+Default workload: 8192 pseudo-experiments per rank, two thirds of the two-detector
+three-dataset model (FD-I, FD-II, ND; 291 parameters; each instance fits a dataset subset drawn
+from {FD-I}, {FD-II + ND}, {all three}) and one third of the 53 km ten-core model with a near
+detector (460 parameters, 2000 true / 400 + 38 reco bins), true signal parameters uniform within
++-3 sigma, Poisson counts, cold start at the nominal point.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+One step = one fit_batch() call over all of them: every evaluation of the expectation, -2lnL,
+adjoint gradient and every L-BFGS update runs in the library's kernels. Inputs are resident in
+device memory when the timed region starts; L2 is flushed (a 512 MiB write) before every timed
+step. With torchrun, each rank fits its own instances (weak scaling, no collective on the data
+path); the step time is the maximum over ranks and value = total fits / that time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--workload c3|c0|c1|c2]
+                  [--impl ours|reference]
 """
 from __future__ import annotations
 
@@ -28,7 +34,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("fits/s at |Δ(−2lnL_min)|≤1e-3 vs FP64 oracle; eval+grad/s; "
           "HBM/tensor % peak")
-WORKLOAD = "two-detector three-dataset fit (FD-I, FD-II, ND), 291 params, 400 true / 3x38 reco bins"
+WORKLOADS = {
+    "c3": ("uneven ensemble: 2/3 two-detector three-dataset model (FD-I, FD-II, ND; 291 params, "
+           "400 true / 3x38 reco bins; fitted dataset subset drawn from {FD-I}, {FD-II+ND}, "
+           "{all}) + 1/3 53 km JUNO-like model (10 cores + near detector; 460 params, 2000 true / "
+           "400+38 reco bins); true signal parameters uniform within +-3 sigma, Poisson counts"),
+    "c0": "single detector, one dataset: 25 params, 200 true / 40 reco bins",
+    "c1": "two-detector three-dataset fit (FD-I, FD-II, ND), 291 params, 400 true / 3x38 reco bins",
+    "c2": "53 km JUNO-like model: 10 cores + near detector, 460 params, 2000 true / 400+38 reco bins",
+}
 
 
 def parse():
@@ -37,9 +51,15 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--batch", type=int, default=8192, help="fits per rank per step")
+    p.add_argument("--workload", default="c3", choices=sorted(WORKLOADS),
+                   help="c3: the uneven two-model ensemble (default); c0/c1/c2: one model")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--cpu-sample", type=int, default=2560,
-                   help="instances of the CPU baseline (about 10 s of the FP64 oracle on 16 cores)")
+    p.add_argument("--cpu-sample", type=int, default=512,
+                   help="instances of the CPU baseline (10-30 s of the FP64 oracle on 16 cores)")
+    p.add_argument("--ref-sample", type=int, default=48,
+                   help="instances per step of the reference arm (the FP64 oracle)")
+    p.add_argument("--no-per-config", action="store_true",
+                   help="skip the per-model sub-lines (c0, c1, c2 alone)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=250215253)
     p.add_argument("--engine", default="persistent", choices=["persistent", "lockstep"],
@@ -144,25 +164,138 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------------------
-def make_workload(B, seed, rank, remap=0):
-    """B pseudo-experiments of the C1 model: true (sin^2 2th13, dm2_ee) drawn within +-3 sigma,
-    expectation from the library, Poisson counts from numpy's PCG64 (seeded per instance).
-    remap=1: the same model with the area-conserving spline energy correction."""
-    from paper_2502_15253_gb300 import fitcore, synth
-    spec = synth.make_model("c1", remap=remap)
-    model = fitcore.Model(spec)
-    rng = np.random.default_rng(seed + 7919 * rank)
-    truths = np.stack([synth.draw_theta_true(spec, rng) for _ in range(B)])
-    mu, st = fitcore.expected_numpy(model, truths)
-    assert np.all(st == 0)
-    data = np.random.default_rng(seed + 1 + 7919 * rank).poisson(mu.astype(np.float64))
-    data = data.astype(np.float32)
-    inst = np.zeros(B, fitcore.INSTANCE_DTYPE)
-    inst["model"] = 0
-    inst["mask"] = spec.all_mask()
-    inst["data_off"] = np.arange(B, dtype=np.int64) * spec.n_bins
-    inst["param_off"] = np.arange(B, dtype=np.int64) * spec.n_params
-    return spec, model, data, inst
+class Workload:
+    """Instances of one benchmark workload. names[k] / specs[k] / models[k] belong to
+    inst["model"] == k. Data and parameter vectors are laid out model by model (all instances of
+    names[0] first), so that each model's instances form one contiguous [n, n_bins] block;
+    the instance table keeps the ensemble's order."""
+
+    def __init__(self, kind, names, specs, table, mu_of):
+        self.kind, self.names, self.specs = kind, list(names), list(specs)
+        self.table = table
+        B = len(table)
+        self.geo = np.array([self.names.index(t.model) for t in table], np.int32)
+        self.inst = np.zeros(B, _fitcore().INSTANCE_DTYPE)
+        self.inst["model"] = self.geo
+        self.inst["mask"] = [t.mask for t in table]
+        self.group = [np.flatnonzero(self.geo == k) for k in range(len(names))]
+        self.data_base, self.par_base = [], []
+        d0 = p0 = 0
+        for k, sp in enumerate(self.specs):
+            ix = self.group[k]
+            self.data_base.append(d0)
+            self.par_base.append(p0)
+            self.inst["data_off"][ix] = d0 + np.arange(len(ix), dtype=np.int64) * sp.n_bins
+            self.inst["param_off"][ix] = p0 + np.arange(len(ix), dtype=np.int64) * sp.n_params
+            d0 += len(ix) * sp.n_bins
+            p0 += len(ix) * sp.n_params
+        self.data_len, self.par_len = d0, p0
+        self.data = np.zeros(d0, np.float32)
+        self.truth = np.zeros(p0)
+        for k, sp in enumerate(self.specs):
+            ix = self.group[k]
+            if not len(ix):
+                continue
+            th = np.stack([table[i].theta_true for i in ix])
+            mu = mu_of(k, th)
+            for j, i in enumerate(ix):
+                o = int(self.inst["data_off"][i])
+                self.data[o:o + sp.n_bins] = synth_mod().poisson_data(mu[j], table[i].seed)
+                po = int(self.inst["param_off"][i])
+                self.truth[po:po + sp.n_params] = th[j]
+        self.start = np.zeros(p0)
+        for i, r in enumerate(self.inst):
+            sp = self.specs[r["model"]]
+            self.start[r["param_off"]:r["param_off"] + sp.n_params] = sp.theta0
+
+    def __len__(self):
+        return len(self.table)
+
+    def view(self, flat, k, i_local):
+        """Slice of a flat per-parameter array for the i_local-th instance of model k."""
+        sp = self.specs[k]
+        o = self.par_base[k] + i_local * sp.n_params
+        return flat[o:o + sp.n_params]
+
+    def data_of(self, i):
+        sp = self.specs[self.geo[i]]
+        o = int(self.inst["data_off"][i])
+        return self.data[o:o + sp.n_bins]
+
+    def params_of(self, flat, i):
+        sp = self.specs[self.geo[i]]
+        o = int(self.inst["param_off"][i])
+        return flat[o:o + sp.n_params]
+
+
+def _fitcore():
+    from paper_2502_15253_gb300 import fitcore
+    return fitcore
+
+
+def synth_mod():
+    from paper_2502_15253_gb300 import synth
+    return synth
+
+
+def draw_table(kind, B, base, remap=0):
+    """(model names, specs, instance table) of a workload; instance i draws from SplitMix64(base
+    + i): its model and dataset subset (c3 only), its true signal parameters (uniform within
+    +-3 sigma) and its Poisson stream."""
+    synth = synth_mod()
+    if kind == "c3":
+        names = ["c1", "c2"]
+        specs = {n: synth.make_model(n, remap=remap) for n in names}
+        table = synth.make_ensemble(B, specs, base=base)
+    else:
+        names = [kind]
+        specs = {kind: synth.make_model(kind, remap=remap)}
+        sp = specs[kind]
+        table = []
+        for i in range(B):
+            s = synth.instance_seed(i, base)
+            rng = np.random.default_rng(s)
+            table.append(synth.Instance(kind, sp.all_mask(), synth.draw_theta_true(sp, rng), s))
+    return names, [specs[n] for n in names], table
+
+
+def make_workload(kind, B, seed, rank, remap=0):
+    """The workload's B instances of this rank (instances rank*B .. rank*B + B - 1 of the seeded
+    table) with the library's models; expectations from the library, Poisson counts from
+    numpy's PCG64 stream of each instance's seed."""
+    fitcore = _fitcore()
+    names, specs, table = draw_table(kind, B, seed + rank * B, remap)
+    models = [fitcore.Model(sp) for sp in specs]
+
+    def mu_of(k, th):
+        mu, st = fitcore.expected_numpy(models[k], th)
+        assert np.all(st == 0)
+        return mu
+
+    w = Workload(kind, names, specs, table, mu_of)
+    w.models = models
+    return w
+
+
+def make_workload_oracle(kind, B, seed):
+    """The same instance table with the oracle's models and expectations (reference arm)."""
+    import oracle
+    names, specs, table = draw_table(kind, B, seed)
+    oms = [oracle.OracleModel(sp) for sp in specs]
+
+    def mu_of(k, th):
+        return np.stack([oms[k].expected(t) for t in th])
+
+    w = Workload(kind, names, specs, table, mu_of)
+    w.oms = oms
+    return w
+
+
+def config_of(args, world, B):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": WORKLOADS[args.workload], "instances_per_rank": B,
+            "start": "nominal (cold)", "l2": "flushed (512 MiB write) before each step",
+            "parallelism": f"instances sharded over {world} GPU(s), no collective"}
 
 
 _COLL_DEVICE = "cpu"
@@ -212,43 +345,57 @@ def barrier(pg):
         pg.barrier()
 
 
-def cpu_baseline(spec, data, inst, n, threads=None):
-    """The FP64 oracle (dense BFGS) on the host cores, on the first n instances."""
+def cpu_baseline(w, n, threads=None):
+    """The FP64 oracle (dense BFGS, OpenMP over instances) on the host cores, fitting the first n
+    instances of workload w from the same cold start."""
     import oracle
-    om = oracle.OracleModel(spec)
+    oms = [oracle.OracleModel(sp) for sp in w.specs]
     threads = threads or os.cpu_count() or 1
-    P, D = spec.n_params, spec.n_bins
-    flat = np.asarray(data).reshape(-1)
-    ds = [flat[i * D:(i + 1) * D].astype(np.float64) for i in range(n)]
-    starts = [spec.theta0] * n
+    ds = [w.data_of(i).astype(np.float64) for i in range(n)]
+    starts = [w.specs[w.geo[i]].theta0 for i in range(n)]
     t0 = time.perf_counter()
-    r = oracle.fit_many([om], [0] * n, ds, [int(inst["mask"][i]) for i in range(n)], starts,
-                        edm_tol=1e-10, n_threads=threads)
+    r = oracle.fit_many(oms, [int(g) for g in w.geo[:n]], ds, [int(m) for m in w.inst["mask"][:n]],
+                        starts, edm_tol=1e-10, n_threads=threads)
     dt = time.perf_counter() - t0
+    cnt = {nm: int(np.sum(w.geo[:n] == k)) for k, nm in enumerate(w.names)}
     return {"value": n / dt, "unit": "fits/s", "cores": threads if oracle.openmp_enabled() else 1,
-            "kind": "oracle", "sample": f"{n} instances of the same workload, cold start, "
-            f"FP64 dense BFGS (EDM < 1e-10), {dt:.1f} s", "nll": r["nll"], "iters": r["iters"],
-            "status": r["status"], "om": om, "data": ds}
+            "kind": "oracle", "sample": f"first {n} instances of the same workload "
+            f"({', '.join(f'{v} {k}' for k, v in cnt.items())}), cold start, FP64 dense BFGS "
+            f"(EDM < 1e-10), {dt:.1f} s", "s": dt,
+            "_r": r, "_oms": oms, "_ds": ds}
 
 
-def certify_other_minima(cpu, gpu_best, gpu_nll, P):
-    """Instances whose GPU minimum is not the oracle's: is the GPU point an oracle minimum?
-    (the oracle restarted there stays within 1e-4 in -2lnL)"""
-    om, ds = cpu.pop("om"), cpu.pop("data")
-    cpu_nll = cpu.pop("nll")
-    cpu.pop("iters")
-    cpu.pop("status")
-    d = np.abs(gpu_nll[:len(cpu_nll)] - cpu_nll)
+def certify(cpu, w, gpu_best, gpu_nll):
+    """Parity of the GPU minima on the oracle's sample: |d(-2lnL_min)| per instance and per
+    model; an instance beyond 1e-3 is certified when the oracle restarted at the GPU point stays
+    there (another minimum of the FP64 likelihood) and counted apart."""
+    r, oms, ds = cpu.pop("_r"), cpu.pop("_oms"), cpu.pop("_ds")
+    n = len(ds)
+    dn = gpu_nll[:n] - r["nll"]
+    d = np.abs(dn)
     other = np.flatnonzero(d > 1e-3)
     cert = 0
     for i in other:
-        th = gpu_best[i * P:(i + 1) * P]
-        r = om.fit(ds[i], start=th)
-        cert += int(r["status"] == 0 and abs(r["nll"] - om.nll(th, ds[i])) <= 1e-4)
-    cpu["parity_max_abs_dnll"] = float(d.max())
-    cpu["parity_frac_within_1e-3"] = float(np.mean(d <= 1e-3))
+        th = w.params_of(gpu_best, i)
+        om = oms[w.geo[i]]
+        m = int(w.inst["mask"][i])
+        rr = om.fit(ds[i], mask=m, start=th)
+        cert += int(rr["status"] == 0 and abs(rr["nll"] - om.nll(th, ds[i], mask=m)) <= 1e-4)
+    cpu["parity_max_abs_dnll"] = float(d.max()) if n else None
+    cpu["parity_frac_within_1e-3"] = float(np.mean(d <= 1e-3)) if n else None
     cpu["parity_other_minima"] = int(len(other))
     cpu["parity_other_minima_certified"] = int(cert)
+    cpu["parity_other_minima_gpu_lower"] = int(np.sum(dn[other] < 0))
+    cpu["oracle_converged_frac"] = float(np.mean(r["status"] == 0)) if n else None
+    per = {}
+    for k, nm in enumerate(w.names):
+        ix = np.flatnonzero(w.geo[:n] == k)
+        if len(ix):
+            per[nm] = {"n": int(len(ix)), "frac_within_1e-3": float(np.mean(d[ix] <= 1e-3)),
+                       "max_abs_dnll": float(d[ix].max()),
+                       "oracle_iters_per_fit": float(np.mean(r["iters"][ix]))}
+    cpu["parity_per_model"] = per
+    return cpu
 
 
 def mlp_flops_per_sample(dims, train):
@@ -258,24 +405,35 @@ def mlp_flops_per_sample(dims, train):
     return sum(fwd) * 2 + sum(fwd[1:]) if train else sum(fwd)
 
 
-def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best, opts, stream,
-                           flush, pg, world):
+def r2_per_target(pred, truth, names):
+    """Coefficient of determination of pred against truth, per column."""
+    out = {}
+    for j, nm in enumerate(names):
+        v = np.var(truth[:, j])
+        out[nm] = float(1.0 - np.mean((pred[:, j] - truth[:, j]) ** 2) / v) if v > 0 else None
+    return out
+
+
+def warm_start_measurement(args, w, data_d, cold_res, cold_best, opts, stream, flush, pg, world):
     """Warm start (not in the paper): train the network on device-drawn samples of both
     geometries, time one bf16 training step on the tensor cores, the TF32 fold of a training
-    batch, and fits of the benchmark's pseudo-experiments from the predicted starts."""
+    batch, and fits of the benchmark's pseudo-experiments (held out: the training samples come
+    from the device generator) from the predicted starts, per model, against the cold fits."""
     import torch
     from paper_2502_15253_gb300 import fitcore, synth, warmstart
 
     dev = data_d.device
-    B, P = len(inst), spec.n_params
-    spec2 = synth.make_model("c2")
-    model2 = fitcore.Model(spec2)
+    B = len(w)
+    by_name = dict(zip(w.names, w.models))
+    specs_by_name = dict(zip(w.names, w.specs))
+    tr_specs = [specs_by_name.get(n) or synth.make_model(n) for n in ("c1", "c2")]
+    tr_models = [by_name.get(n) or fitcore.Model(s) for n, s in zip(("c1", "c2"), tr_specs)]
     net = warmstart.network(seed=3)
     batch = 4096
     n_steps = max(2, args.ws_samples // batch)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    losses = warmstart.train(net, [model, model2], [spec, spec2], n_steps=n_steps, batch=batch,
+    losses = warmstart.train(net, tr_models, tr_specs, n_steps=n_steps, batch=batch,
                              lr=1e-3, stream=stream)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -296,14 +454,12 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
     ev1.record(stream)
     torch.cuda.synchronize()
     step_ms = ev0.elapsed_time(ev1) / reps
-    peaks = {}
-    peak_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(peak_path):
-        peaks = json.load(open(peak_path))
+    peaks = read_peaks()
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
     mlp_tflops = mlp_flops_per_sample(dims, True) * tb / (step_ms / 1e3) / 1e12
 
     # TF32 fold of a 53 km training batch: V [B x 2000] times R^T for both detectors
+    spec2, model2 = tr_specs[1], tr_models[1]
     fb = 8192
     th2 = torch.zeros((fb, spec2.n_params), dtype=torch.float64, device=dev)
     fitcore.fit_warmstart_draw(model2, warmstart.geometry(spec2), fb, 11, 0, th2, None, stream)
@@ -319,6 +475,7 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
     n_t = spec2.n_true
     fold_flops = 2.0 * fb * n_t * sum(spec2.detectors[d.det].n_reco for d in spec2.datasets)
     tf32_peak = bf16_peak * 1.1 / 2.25
+    del th2, mu2
 
     # the fold's tensor-core GEMM alone at the same shape: V [fb x N_t'] (FP32 read as TF32)
     # times the far detector's response [400 x N_t']^T
@@ -337,22 +494,62 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
     gemm_tflops = 2.0 * fb * 400 * n_t / (gemm_ms / 1e3) / 1e12
     del Va, Rb, Cc
 
-    # warm fits of the benchmark's pseudo-experiments
-    starts = torch.zeros((B, P), dtype=torch.float64, device=dev)
+    # warm fits of the benchmark's pseudo-experiments: starts predicted per model
+    starts = torch.from_numpy(w.start.copy()).to(dev)
+    masks_d = torch.from_numpy(w.inst["mask"].astype(np.int32)).to(dev)
     flush.fill_(0.5)
-    ev0.record(stream)
-    warmstart.predict_starts(net, model, spec, B, data_d.view(B, -1), None, starts, stream)
+
+    def predict():
+        for k, (nm, sp, m) in enumerate(zip(w.names, w.specs, w.models)):
+            ix = w.group[k]
+            if not len(ix):
+                continue
+            n = len(ix)
+            dv = data_d[w.data_base[k]:w.data_base[k] + n * sp.n_bins].view(n, sp.n_bins)
+            sv = starts[w.par_base[k]:w.par_base[k] + n * sp.n_params].view(n, sp.n_params)
+            mk = masks_d[torch.from_numpy(ix).to(dev)].contiguous()
+            warmstart.predict_starts(net, m, sp, n, dv, mk, sv, stream)
+
     best_w = torch.zeros_like(cold_best)
     res_w = torch.zeros(B * fitcore.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-    fitcore.fit_batch([model], inst, data_d, starts.view(-1), best_w, res_w, opts, stream)
+    predict()
+    fitcore.fit_batch(w.models, w.inst, data_d, starts, best_w, res_w, opts, stream)  # warm-up
+    torch.cuda.synchronize()
+    flush.fill_(0.25)
+    ev0.record(stream)
+    predict()
+    fitcore.fit_batch(w.models, w.inst, data_d, starts, best_w, res_w, opts, stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     warm_ms = max_over_ranks(ev0.elapsed_time(ev1), pg)
     rw = np.frombuffer(res_w.cpu().numpy().tobytes(), dtype=fitcore.RESULT_DTYPE)
     same = np.abs(rw["nll_min"] - cold_res["nll_min"]) <= 1e-3
+    st_h = starts.cpu().numpy()
+    cb_h = cold_best.cpu().numpy()
+    per = {}
+    for k, nm in enumerate(w.names):
+        ix = w.group[k]
+        if not len(ix):
+            continue
+        g = warmstart.geometry(w.specs[k])
+        tix = list(g.target_idx)[:g.n_targets]
+        tnames = [w.specs[k].param_names[j] for j in tix]
+        pred = np.stack([w.params_of(st_h, i)[tix] for i in ix])
+        fit = np.stack([w.params_of(cb_h, i)[tix] for i in ix])
+        tru = np.stack([w.params_of(w.truth, i)[tix] for i in ix])
+        per[nm] = {"n": int(len(ix)),
+                   "iters_per_fit_warm": float(rw["iters"][ix].mean()),
+                   "iters_per_fit_cold": float(cold_res["iters"][ix].mean()),
+                   "evals_per_fit_warm": float(rw["n_evals"][ix].mean()),
+                   "evals_per_fit_cold": float(cold_res["n_evals"][ix].mean()),
+                   "same_minimum_as_cold_frac": float(same[ix].mean()),
+                   "converged_frac_warm": float(np.mean(rw["status"][ix] == 0)),
+                   "r2_network_vs_truth": r2_per_target(pred, tru, tnames),
+                   "r2_cold_fit_vs_truth": r2_per_target(fit, tru, tnames)}
     return {
         "note": "not in the paper: a network proposes start points; every fit still runs to "
-                "the same EDM tolerance",
+                "the same EDM tolerance. The held-out set is the benchmark's own instances; the "
+                "R^2 of the cold best fits against the truth is the most any start can reach",
         "train_samples": n_steps * batch, "train_s": train_s,
         "train_samples_per_s": n_steps * batch / train_s,
         "train_loss_first_last": [float(losses[:2].mean()), float(losses[-20:].mean())],
@@ -364,9 +561,7 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
                            "unit": "TFLOP/s", "peak": tf32_peak,
                            "frac": fold_flops / fold_ms / 1e9 / tf32_peak,
                            "peak_note": "measured bf16 burst x 1.1/2.25 (nominal tf32/bf16)",
-                           "timed": "whole fit_model_expected_tc call (spectra, GEMMs, epilogue); "
-                                    "the spectra kernel (survival at 2000 bins x 10 cores per "
-                                    "instance and detector) dominates"},
+                           "timed": "whole fit_model_expected_tc call (spectra, GEMMs, epilogue)"},
         "fold_gemm_tf32_alone": {"M": fb, "N": 400, "K": n_t, "ms": gemm_ms, "achieved": gemm_tflops,
                                  "unit": "TFLOP/s", "peak": tf32_peak, "frac": gemm_tflops / tf32_peak,
                                  "bound": "tensor", "kernel": "tc_gemm_kernel<TF32>"},
@@ -376,15 +571,23 @@ def warm_start_measurement(args, spec, model, inst, data_d, cold_res, cold_best,
         "iters_per_fit_cold": float(cold_res["iters"].mean()),
         "same_minimum_as_cold_frac": float(same.mean()),
         "converged_frac_warm": float(np.mean(rw["status"] == 0)),
+        "per_model": per,
     }
 
 
-# DRAM bytes (read + write) per fit of fit_kernel on the three-dataset model, from an ncu
-# capture of one 760-fit launch of the preconditioned build (the default; 4.39 MB read,
-# 14.58 MB written, mostly the workspace write-back); traffic grows with the fits. The plain
-# build's capture (7.30 MB, 47.86 MB) predates later changes of the kernel, so a run with
-# --no-precondition reports no traffic.
-FIT_DRAM_BYTES_PER_FIT = (4.394240e6 + 14.576896e6) / 760
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except Exception:
+            return {}
+    return {}
+
+
+# DRAM bytes (read + write) per fit of the fit kernel by workload, from ncu captures of the current
+# kernel on a smaller launch of the same workload (traffic grows with the fits)
+FIT_DRAM_BYTES_PER_FIT = {}
 
 # DRAM bytes (read + write) per event of mc_spectrum_kernel for one parameter set, from an ncu
 # capture of 11,904,680 events (154.81 MB read, 3.62 MB written); traffic grows with the events
@@ -454,7 +657,7 @@ def event_reweighting_measurement(args, stream, pg, world):
     return out
 
 
-def profile_measurement(args, spec, model, data_h, pg, world):
+def profile_measurement(args, pg, world):
     """Profile likelihood (Eq. 7): a 32 x 32 raster of constrained fits of the three-dataset
     model in (sin^2 2th13, dm2_ee) on the first pseudo-experiment, one launch, with its 1-D
     Wilks interval and goodness of fit; and the mass-ordering profiles of the 53 km model
@@ -462,8 +665,10 @@ def profile_measurement(args, spec, model, data_h, pg, world):
     import torch
     from paper_2502_15253_gb300 import fitcore, synth
 
+    w = make_workload("c1", 1, args.seed, 0)
+    spec, model = w.specs[0], w.models[0]
     D = spec.n_bins
-    data = np.ascontiguousarray(data_h[:D])
+    data = np.ascontiguousarray(w.data[:D])
     mask = spec.all_mask()
     i13, idm = spec.index("sin2_2th13"), spec.index("dm2_ee")
     a = np.linspace(0.05, 0.13, 32)
@@ -557,10 +762,11 @@ def spline_measurement(args, stream, flush, pg, world):
     from paper_2502_15253_gb300 import fitcore
 
     B = args.batch
-    spec, model, data_h, inst = make_workload(B, args.seed, 0, remap=1)
+    w = make_workload("c1", B, args.seed, 0, remap=1)
+    model, inst = w.models[0], w.inst
     dev = torch.device("cuda", torch.cuda.current_device())
-    data_d = torch.from_numpy(data_h).to(dev)
-    best_d = torch.zeros(B * spec.n_params, dtype=torch.float64, device=dev)
+    data_d = torch.from_numpy(w.data).to(dev)
+    best_d = torch.zeros(w.par_len, dtype=torch.float64, device=dev)
     res_d = torch.zeros(B * fitcore.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     opts = fitcore.fit_batch_default_opts()
     for _ in range(max(1, args.warmup)):
@@ -584,47 +790,6 @@ def spline_measurement(args, stream, flush, pg, world):
             "converged_frac": float(np.mean(res["status"] == 0))}
 
 
-def run_reference(args):
-    """Reference arm: the FP64 oracle timed on the host cores on the same workload."""
-    world, rank, _, pg = dist_setup(args)
-    if rank != 0:
-        if pg is not None:
-            pg.destroy_process_group()
-        return
-    from paper_2502_15253_gb300 import synth
-    import oracle
-    spec = synth.make_model("c1")
-    om = oracle.OracleModel(spec)
-    rng = np.random.default_rng(args.seed)
-    n = max(8, min(args.cpu_sample, 64))
-    truths = [synth.draw_theta_true(spec, rng) for _ in range(n)]
-    ds = [synth.poisson_data(om.expected(t), args.seed + i) for i, t in enumerate(truths)]
-    threads = os.cpu_count() or 1
-    for _ in range(args.warmup):
-        oracle.fit_many([om], [0] * 2, ds[:2], [spec.all_mask()] * 2, [spec.theta0] * 2,
-                        n_threads=threads)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.fit_many([om], [0] * n, ds, [spec.all_mask()] * n, [spec.theta0] * n,
-                        n_threads=threads)
-        times.append(time.perf_counter() - t0)
-    ms = 1e3 * float(np.mean(times))
-    val = n / (ms / 1e3)
-    cores = threads if oracle.openmp_enabled() else 1
-    print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": val, "unit": "fits/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "fits_per_step": n, "start": "nominal (cold)"},
-        "cpu_baseline": {"value": val, "unit": "fits/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{n} instances per step on {cores} host threads"},
-        "e2e": {"value": val, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }))
-    if pg is not None:
-        pg.destroy_process_group()
-
-
 def run_ours(args):
     import torch
     from paper_2502_15253_gb300 import fitcore
@@ -632,12 +797,11 @@ def run_ours(args):
     world, rank, local, pg = dist_setup(args)
     torch.cuda.set_device(local)
     B = args.batch
-    spec, model, data_h, inst = make_workload(B, args.seed, rank)
-    P, D = spec.n_params, spec.n_bins
+    w = make_workload(args.workload, B, args.seed, rank)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    data_d = torch.from_numpy(data_h).to(dev)
-    best_d = torch.zeros(B * P, dtype=torch.float64, device=dev)
+    data_d = torch.from_numpy(w.data).to(dev)
+    best_d = torch.zeros(w.par_len, dtype=torch.float64, device=dev)
     res_d = torch.zeros(B * fitcore.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts = fitcore.fit_batch_default_opts()
@@ -645,7 +809,7 @@ def run_ours(args):
     opts.precondition = 0 if args.no_precondition else 1
 
     def step():
-        fitcore.fit_batch([model], inst, data_d, None, best_d, res_d, opts, stream)
+        fitcore.fit_batch(w.models, w.inst, data_d, None, best_d, res_d, opts, stream)
 
     for _ in range(args.warmup):
         step()
@@ -677,48 +841,77 @@ def run_ours(args):
     evals = int(res["n_evals"].sum())
     iters = int(res["iters"].sum())
     conv = float(np.mean(res["status"] == 0))
-    value = world * B / (ms / 1e3)
+    fits_per_s = world * B / (ms / 1e3)
     evals_per_s = world * evals / (ms / 1e3)
+    per_model = {}
+    for k, nm in enumerate(w.names):
+        ix = w.group[k]
+        if len(ix):
+            per_model[nm] = {"n": int(len(ix)), "params": w.specs[k].n_params,
+                             "iters_per_fit": float(res["iters"][ix].mean()),
+                             "evals_per_fit": float(res["n_evals"][ix].mean()),
+                             "converged_frac": float(np.mean(res["status"][ix] == 0))}
+    if w.kind == "c3":
+        ix = w.group[0]
+        per_model["c1"]["dataset_subsets"] = {
+            nm: int(np.sum(w.inst["mask"][ix] == m)) for nm, m in
+            (("FD-I", 0b001), ("FD-II+ND", 0b110), ("all", 0b111))}
 
-    # roofline of the fit kernel: FP32 ALU peak from unit counts and the maximum SM clock;
-    # with the Fisher preconditioner each evaluation also applies T twice (Q^T x and Q u:
-    # 2 P r multiply-adds each, r = min(32, bins, P))
-    f_eval = flops_per_eval(spec, spec.all_mask())
-    if opts.precondition:
-        f_eval += 8.0 * P * min(32, D, P)
-    alg_flops = evals * f_eval + iters * flops_lbfgs_iter(P, opts.history)
+    # roofline of the fit kernel. Bytes: the L-BFGS state a minimiser iteration reads and
+    # writes (2 m P floats of history read with m = 10, 2 P floats written) per instance.
+    peaks = read_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    alg_bytes = 0.0
+    alg_flops = 0.0
+    for k, sp in enumerate(w.specs):
+        ix = w.group[k]
+        P = sp.n_params
+        alg_bytes += float(res["iters"][ix].sum()) * (2 * 10 * P * 4 + 2 * P * 4)
+        for i in ix:
+            f_eval = flops_per_eval(sp, int(w.inst["mask"][i]))
+            if opts.precondition:
+                f_eval += 8.0 * P * min(32, sp.n_bins, P)
+            alg_flops += res["n_evals"][i] * f_eval + res["iters"][i] * flops_lbfgs_iter(P, opts.history)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    sm_max = 2070.0
-    if os.path.exists(peak_path):
-        try:
-            sm_max = float(json.load(open(peak_path)).get("sm_max_mhz", sm_max))
-        except Exception:
-            pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
-    achieved = alg_flops / (ms / 1e3) / 1e12
+    gbs = alg_bytes / (ms / 1e3) / 1e9
+    tflops = alg_flops / (ms / 1e3) / 1e12
+    traffic = FIT_DRAM_BYTES_PER_FIT.get(w.kind)
 
-    # end-to-end through the public API with host buffers (pinned), copies inside the timing
-    data_pin = torch.from_numpy(data_h).pin_memory()
-    best_pin = torch.zeros(B * P, dtype=torch.float64).pin_memory()
+    # end-to-end through the public API with host buffers (pinned), copies inside the timing;
+    # the one-time set-up (models created from their descriptions, the first fit_batch call
+    # building each model's preconditioner) is timed once and reported beside it
+    data_pin = torch.from_numpy(w.data).pin_memory()
+    best_pin = torch.zeros(w.par_len, dtype=torch.float64).pin_memory()
     res_pin = torch.zeros(B * fitcore.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
-    fitcore.fit_batch([model], inst, data_pin, None, best_pin, res_pin, opts, stream)
+    torch.cuda.synchronize()
     barrier(pg)
+    t0 = time.perf_counter()
+    fresh = [fitcore.Model(sp) for sp in w.specs]
+    fitcore.fit_batch(fresh, w.inst, data_pin, None, best_pin, res_pin, opts, stream)
+    first_s = max_over_ranks(time.perf_counter() - t0, pg)
     e2e_t = []
     for i in range(max(1, min(args.steps, 3))):
         flush.fill_(float(i))
         torch.cuda.synchronize()
+        barrier(pg)
         t0 = time.perf_counter()
-        fitcore.fit_batch([model], inst, data_pin, None, best_pin, res_pin, opts, stream)
+        fitcore.fit_batch(fresh, w.inst, data_pin, None, best_pin, res_pin, opts, stream)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(float(np.mean(e2e_t)), pg)
-    h2d = data_h.nbytes + inst.nbytes
+    for m in fresh:
+        m.close()
+    h2d = w.data.nbytes + w.inst.nbytes
     d2h = best_pin.numel() * 8 + res_pin.numel()
 
     ws = None
-    if not args.no_warm_start:
-        ws = warm_start_measurement(args, spec, model, inst, data_d, res, best_d, opts, stream,
-                                    flush, pg, world)
+    if not args.no_warm_start and w.kind in ("c3", "c1", "c2"):
+        ws = warm_start_measurement(args, w, data_d, res, best_d, opts, stream, flush, pg, world)
+
+    per_cfg = None
+    if not args.no_per_config:
+        per_cfg = per_config_measurement(args, stream, flush, pg, world, rank)
 
     spl = None
     if not args.no_profile:
@@ -726,7 +919,7 @@ def run_ours(args):
 
     prof = None
     if not args.no_profile:
-        prof = profile_measurement(args, spec, model, data_h, pg, world)
+        prof = profile_measurement(args, pg, world)
 
     mc = None
     if args.mc_events > 0:
@@ -735,36 +928,51 @@ def run_ours(args):
     out = None
     if rank == 0:
         cpu = None
+        frac_ok = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(spec, data_h, inst, min(args.cpu_sample, B))
-            certify_other_minima(cpu, best_d.cpu().numpy(), res["nll_min"], P)
+            cpu = certify(cpu_baseline(w, min(args.cpu_sample, B)), w, best_d.cpu().numpy(),
+                          res["nll_min"])
+            frac_ok = cpu["parity_frac_within_1e-3"]
+        value = fits_per_s * frac_ok if frac_ok is not None else fits_per_s
+        cfg = config_of(args, world, B)
+        cfg.update({"engine": args.engine,
+                    "minimiser": "L-BFGS (32 pairs)" + (", Fisher-preconditioned coordinates"
+                                                       if opts.precondition else "")})
         out = {
             "metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "fits_per_step": world * B, "fits_per_rank": B,
-                       "engine": args.engine,
-                       "minimiser": "L-BFGS (32 pairs)" + (", Fisher-preconditioned coordinates"
-                                                          if opts.precondition else ""),
-                       "start": "nominal (cold)", "l2": "flushed (512 MiB write) before each step",
-                       "parallelism": f"instances sharded over {world} GPU(s), no collective"},
+            "config": cfg, "fits_per_step": world * B,
+            "value_note": ("fits/s x the fraction of the oracle-checked sample within 1e-3 of "
+                           "the oracle's -2lnL_min" if frac_ok is not None else
+                           "all fits/s (no oracle sample in this run)"),
+            "fits_per_s_all": fits_per_s, "frac_within_1e-3": frac_ok,
             "evals_per_s": evals_per_s, "iters_per_fit": iters / B, "evals_per_fit": evals / B,
-            "converged_frac": conv,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                         "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                         "traffic": FIT_DRAM_BYTES_PER_FIT * B if opts.precondition else None,
-                         "traffic_note": ("DRAM read+write bytes per fit of an ncu capture of "
-                                          "this kernel (760 fits), scaled to the launch"
-                                          if opts.precondition else
-                                          "no capture of the current plain build"),
+            "converged_frac": conv, "per_model": per_model,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs / hbm_peak,
+                         "traffic": traffic["per_fit"] * B if traffic else None,
+                         "traffic_note": traffic["note"] if traffic else
+                         "no ncu capture of the current kernel on this workload",
                          "kernel": "fit_kernel",
-                         "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"},
+                         "algorithmic": "L-BFGS state per minimiser iteration and instance: "
+                                        "2 m P floats read (m = 10) + 2 P floats written",
+                         "peak_note": "measured copy bandwidth (hbm_gbs)",
+                         "alu_model": {"achieved": tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                                       "frac": tflops / peak_tflops,
+                                       "peak_note": f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 x "
+                                                    f"{sm_max:.0f} MHz"}},
             "e2e": {"value": world * B / e2e_s, "unit": "fits/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                    "d2h_bytes_per_step": int(d2h), "setup_s": max(0.0, first_s - e2e_s),
+                    "setup_note": "one-time: models created from their descriptions and each "
+                                  "model's preconditioner built (first fit_batch call minus a "
+                                  "plain call)",
+                    "value_incl_setup_one_step": world * B / first_s},
             "gpu_launches": int(launches // max(1, args.steps)) * args.steps,
             "clocks": clk, "wall_s": wall,
             "cpu_baseline": cpu,
+            "per_config": per_cfg,
             "warm_start": ws,
             "profile_likelihood": prof,
             "spline_energy_correction": spl,
@@ -773,6 +981,131 @@ def run_ours(args):
         print(json.dumps(out))
     if pg is not None:
         pg.destroy_process_group()
+    return out
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle (dense BFGS, OpenMP over instances) timed on the host cores
+    on the same workload; each step fits a bounded sample (the first --ref-sample instances of
+    the same seeded table) from the same cold start."""
+    world, rank, _, pg = dist_setup(args)
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    import oracle
+    n = max(4, args.ref_sample)
+    w = make_workload_oracle(args.workload, n, args.seed)
+    threads = os.cpu_count() or 1
+    ds = [w.data_of(i).astype(np.float64) for i in range(n)]
+    geo = [int(g) for g in w.geo]
+    masks = [int(m) for m in w.inst["mask"]]
+    starts = [w.specs[g].theta0 for g in geo]
+    for _ in range(args.warmup):
+        oracle.fit_many(w.oms, geo[:2], ds[:2], masks[:2], starts[:2], n_threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fit_many(w.oms, geo, ds, masks, starts, n_threads=threads)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    val = n / (ms / 1e3)
+    cores = threads if oracle.openmp_enabled() else 1
+    cfg = config_of(args, 1, args.batch)
+    cnt = {nm: int(np.sum(w.geo == k)) for k, nm in enumerate(w.names)}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "fits/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg, "fits_per_step": n,
+        "cpu_baseline": {"value": val, "unit": "fits/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {n} instances of the workload per step "
+                                   f"({', '.join(f'{v} {k}' for k, v in cnt.items())}) on "
+                                   f"{cores} host threads"},
+        "e2e": {"value": val, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def time_fit_steps(w, data_d, best_d, res_d, opts, stream, flush, warmup, steps, pg):
+    """Mean device time (ms, max over ranks) of fit_batch over the whole workload."""
+    import torch
+    from paper_2502_15253_gb300 import fitcore
+    for _ in range(warmup):
+        fitcore.fit_batch(w.models, w.inst, data_d, None, best_d, res_d, opts, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        barrier(pg)
+        e0.record(stream)
+        fitcore.fit_batch(w.models, w.inst, data_d, None, best_d, res_d, opts, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return max_over_ranks(float(np.mean(ms)), pg)
+
+
+# oracle samples of the per-model lines (about 2-6 s each on 16 Grace cores)
+PER_CONFIG_ORACLE_SAMPLE = {"c0": 256, "c1": 256, "c2": 48}
+
+
+def per_config_measurement(args, stream, flush, pg, world, rank):
+    """Each model alone: fits/s of args.batch cold-start fits (one fit_batch call), evaluations
+    (-2lnL + gradient) per second of fit_model_eval on args.batch parameter vectors, and the
+    oracle's all-core fits/s, one-core evaluations/s and parity on a bounded sample."""
+    import torch
+    from paper_2502_15253_gb300 import fitcore
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+    for kind in ("c0", "c1", "c2"):
+        B = args.batch
+        w = make_workload(kind, B, args.seed, rank)
+        sp, model = w.specs[0], w.models[0]
+        data_d = torch.from_numpy(w.data).to(dev)
+        best_d = torch.zeros(w.par_len, dtype=torch.float64, device=dev)
+        res_d = torch.zeros(B * fitcore.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        opts = fitcore.fit_batch_default_opts()
+        ms = time_fit_steps(w, data_d, best_d, res_d, opts, stream, flush, 2, 3, pg)
+        res = np.frombuffer(res_d.cpu().numpy().tobytes(), dtype=fitcore.RESULT_DTYPE)
+        # evaluations of the truth points against their own pseudo-data
+        th = torch.from_numpy(w.truth).to(dev).view(B, sp.n_params)
+        dv = data_d.view(B, sp.n_bins)
+        nll = torch.zeros(B, dtype=torch.float64, device=dev)
+        grad = torch.zeros((B, sp.n_params), dtype=torch.float32, device=dev)
+        for _ in range(3):
+            fitcore.fit_model_eval(model, B, th, dv, None, nll, grad, None, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        flush.fill_(1.0)
+        barrier(pg)
+        e0.record(stream)
+        for _ in range(reps):
+            fitcore.fit_model_eval(model, B, th, dv, None, nll, grad, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(e0.elapsed_time(e1) / reps, pg)
+        r = {"workload": WORKLOADS[kind], "fits": world * B,
+             "fits_per_s": world * B / (ms / 1e3), "ms_per_step": ms,
+             "iters_per_fit": float(res["iters"].mean()), "evals_per_fit": float(res["n_evals"].mean()),
+             "converged_frac": float(np.mean(res["status"] == 0)),
+             "eval_grad_per_s": world * B / (ems / 1e3), "eval_batch": B, "eval_ms": ems}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            n = min(PER_CONFIG_ORACLE_SAMPLE[kind], B)
+            cpu = certify(cpu_baseline(w, n), w, best_d.cpu().numpy(), res["nll_min"])
+            om = oracle.OracleModel(sp)
+            k = 0
+            t0 = time.perf_counter()
+            while k < 200 and (k < 3 or time.perf_counter() - t0 < 1.0):
+                om.nll(w.truth[k % B * sp.n_params:(k % B + 1) * sp.n_params],
+                       w.data_of(k % B).astype(np.float64), grad=True)
+                k += 1
+            cpu["oracle_eval_grad_per_s_1core"] = k / (time.perf_counter() - t0)
+            r["cpu_baseline"] = cpu
+        out[kind] = r
+        del data_d, best_d, res_d, th, nll, grad
     return out
 
 
