@@ -89,6 +89,11 @@ class _OrcModel(C.Structure):
         ("bkg_template", C.POINTER(C.c_double)), ("bkg_rate_idx", C.POINTER(C.c_int)),
         ("bkg_shape_idx", C.POINTER(C.c_int)),
         ("remap_mode", C.c_int),
+        ("n_map", C.c_int),
+        ("map_k", C.POINTER(C.c_int)), ("map_m", C.POINTER(C.c_int)),
+        ("map_idx", C.POINTER(C.c_int)),
+        ("map_A", C.POINTER(C.c_double)), ("map_b0", C.POINTER(C.c_double)),
+        ("map_V", C.POINTER(C.c_double)),
     ]
 
 
@@ -219,11 +224,24 @@ class OracleModel:
         m.bkg_template = d(np.concatenate([b.template for _, b in bk]) if bk else [0.0])
         m.bkg_rate_idx = i([b.rate_idx for _, b in bk] or [0])
         m.bkg_shape_idx = i(np.concatenate([b.shape_idx for _, b in bk]) if bk else [0])
+        # Eq. 6 priors on b = A theta (evaluated as written, not converted)
+        mp = list(getattr(s, "map_priors", []) or [])
+        m.n_map = len(mp)
+        m.map_k = i([len(ix) for ix, _, _, _ in mp] or [0])
+        m.map_m = i([len(b0) for _, _, b0, _ in mp] or [0])
+        m.map_idx = i(np.concatenate([np.asarray(ix) for ix, _, _, _ in mp]) if mp else [0])
+        m.map_A = d(np.concatenate([np.asarray(A, np.float64).ravel() for _, A, _, _ in mp]) if mp else [0.0])
+        m.map_b0 = d(np.concatenate([np.asarray(b0, np.float64) for _, _, b0, _ in mp]) if mp else [0.0])
+        m.map_V = d(np.concatenate([np.asarray(V, np.float64).ravel() for _, _, _, V in mp]) if mp else [0.0])
+        for ix, A, b0, V in mp:
+            if np.shape(A) != (len(b0), len(ix)) or np.shape(V) != (len(b0), len(b0)):
+                raise ValueError("oracle: a map prior needs A [m x k], b0 [m] and V [m x m]")
         self._keep = keep
         self._m = m
         self.h = lib().orc_create(C.byref(m))
         if not self.h:
-            raise ValueError("oracle: a prior covariance block is not symmetric positive definite")
+            raise ValueError("oracle: a prior covariance (block or map) is not symmetric positive "
+                             "definite")
         self.n_params = s.n_params
         self.n_data = lib().orc_n_data(self.h)
 

@@ -23,6 +23,8 @@
  *                                                                 to the saturated model, Eq. 8
  *             + sum_i ((theta_i - theta0_i)/sigma_i)^2            Gaussian priors, Eq. 6
  *             + sum_B (theta_B - theta0_B)^T V_B^-1 (theta_B - theta0_B)   Eq. 6 / Eq. 9
+ *             + sum_maps (A theta - b0)^T V^-1 (A theta - b0)       Eq. 6, generalised
+ *                                                                 parametrisation b = A theta
  *
  * plus the analytic gradient of -2lnL with respect to every parameter, and a dense BFGS
  * minimiser with a strong-Wolfe line search that stops when the estimated distance to the
@@ -71,6 +73,14 @@ typedef struct {
     const int *bkg_rate_idx;
     const int *bkg_shape_idx;     /* concatenated, N_r each */
     int remap_mode;               /* 0: overlap length ; 1: area-conserving spline */
+    /* Eq. 6 with a generalised parametrisation b(theta) = A theta_idx: per map, k parameters,
+     * m >= 1 constrained quantities with measured values b0 and covariance V (m x m) */
+    int n_map;
+    const int *map_k, *map_m;     /* [n_map] */
+    const int *map_idx;           /* concatenated, k per map */
+    const double *map_A;          /* concatenated row-major m x k */
+    const double *map_b0;         /* concatenated, m per map */
+    const double *map_V;          /* concatenated row-major m x m */
 } orc_model;
 
 typedef struct {
@@ -83,6 +93,8 @@ typedef struct {
     double *vinv;          /* concatenated V_B^-1 */
     double *chol;          /* concatenated lower Cholesky factors of V_B */
     int *in_block;         /* per parameter: 1 if it belongs to a covariance block */
+    int *map_ioff, *map_aoff, *map_boff, *map_voff;   /* offsets into the map arrays */
+    double *map_vinv;      /* concatenated V^-1 of the maps */
 } orc_handle;
 
 /* ------------------------------------------------------------------------------------ */
@@ -130,6 +142,7 @@ void orc_destroy(orc_handle *h)
     if (!h) return;
     free(h->ds_off); free(h->det_off); free(h->bkg_off); free(h->cov_off); free(h->cov_moff);
     free(h->vinv); free(h->chol); free(h->in_block);
+    free(h->map_ioff); free(h->map_aoff); free(h->map_boff); free(h->map_voff); free(h->map_vinv);
     free(h);
 }
 
@@ -176,6 +189,37 @@ orc_handle *orc_create(const orc_model *m)
         }
         chol_inverse(n, h->chol + h->cov_moff[b], h->vinv + h->cov_moff[b]);
         for (int i = 0; i < n; ++i) h->in_block[m->cov_idx[h->cov_off[b] + i]] = 1;
+    }
+    /* covariances of the Eq. 6 maps: symmetric positive definite, inverted once */
+    int nmap = m->n_map > 0 ? m->n_map : 0;
+    h->map_ioff = (int *)malloc(sizeof(int) * (nmap + 1));
+    h->map_aoff = (int *)malloc(sizeof(int) * (nmap + 1));
+    h->map_boff = (int *)malloc(sizeof(int) * (nmap + 1));
+    h->map_voff = (int *)malloc(sizeof(int) * (nmap + 1));
+    h->map_ioff[0] = h->map_aoff[0] = h->map_boff[0] = h->map_voff[0] = 0;
+    for (int q = 0; q < nmap; ++q) {
+        int k = m->map_k[q], r = m->map_m[q];
+        h->map_ioff[q + 1] = h->map_ioff[q] + k;
+        h->map_aoff[q + 1] = h->map_aoff[q] + r * k;
+        h->map_boff[q + 1] = h->map_boff[q] + r;
+        h->map_voff[q + 1] = h->map_voff[q] + r * r;
+    }
+    h->map_vinv = (double *)malloc(sizeof(double) * (h->map_voff[nmap] > 0 ? h->map_voff[nmap] : 1));
+    for (int q = 0; q < nmap; ++q) {
+        int r = m->map_m[q];
+        const double *v = m->map_V + h->map_voff[q];
+        double *l = (double *)malloc(sizeof(double) * r * r);
+        int bad = 0;
+        for (int i = 0; i < r && !bad; ++i)
+            for (int j = 0; j < r; ++j)
+                if (fabs(v[i * r + j] - v[j * r + i]) > 1e-12 * (fabs(v[i * r + i]) + fabs(v[j * r + j]))) bad = 1;
+        if (!bad) bad = cholesky(r, v, l) != 0;
+        if (!bad) chol_inverse(r, l, h->map_vinv + h->map_voff[q]);
+        free(l);
+        if (bad) {
+            orc_destroy(h);
+            return NULL;
+        }
     }
     return h;
 }
@@ -585,6 +629,29 @@ static double prior_term(const orc_handle *h, const double *theta, double *grad)
             q += (theta[idx[i]] - m->theta0[idx[i]]) * row;
             if (grad) grad[idx[i]] += 2.0 * row;
         }
+    }
+    /* Eq. 6 with b(theta) = A theta_idx: q += (b - b0)^T V^-1 (b - b0); its gradient is
+     * A^T 2 V^-1 (b - b0) */
+    for (int p = 0; p < m->n_map; ++p) {
+        int k = m->map_k[p], r = m->map_m[p];
+        const int *idx = m->map_idx + h->map_ioff[p];
+        const double *A = m->map_A + h->map_aoff[p];
+        const double *b0 = m->map_b0 + h->map_boff[p];
+        const double *vi = h->map_vinv + h->map_voff[p];
+        double *res = (double *)malloc(sizeof(double) * r);
+        for (int i = 0; i < r; ++i) {
+            double b = 0.0;
+            for (int j = 0; j < k; ++j) b += A[i * k + j] * theta[idx[j]];
+            res[i] = b - b0[i];
+        }
+        for (int i = 0; i < r; ++i) {
+            double row = 0.0;
+            for (int j = 0; j < r; ++j) row += vi[i * r + j] * res[j];
+            q += res[i] * row;
+            if (grad)
+                for (int j = 0; j < k; ++j) grad[idx[j]] += 2.0 * A[i * k + j] * row;
+        }
+        free(res);
     }
     return q;
 }

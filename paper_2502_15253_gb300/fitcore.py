@@ -236,6 +236,13 @@ class Model:
         if _handle is not None:
             self._attach(_handle)
             return
+        if getattr(spec, "map_priors", None):
+            # priors on b = A theta exist only in the JSON schema (fit_model_create_json)
+            h = C.c_void_p()
+            _check(L.fit_model_create_json(spec.to_json().encode(), C.byref(h)),
+                   "fit_model_create_json")
+            self._attach(h)
+            return
         keep = []
 
         def d(a):

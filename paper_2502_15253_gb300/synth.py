@@ -108,6 +108,9 @@ class ModelSpec:
     detectors: list
     datasets: list
     remap: int = 0                # energy correction: 0 overlap length, 1 area-conserving spline
+    # Eq. 6 priors on b = A theta[idx]: [(idx int32[k], A float64[m, k], b0 float64[m],
+    # V float64[m, m])]; the measured values b0 with covariance V
+    map_priors: list = field(default_factory=list)
 
     @property
     def n_params(self) -> int:
@@ -158,7 +161,10 @@ class ModelSpec:
             "parameters": [{"name": n, "value": float(v), "sigma": float(s), "scale": float(c)}
                            for n, v, s, c in zip(names, self.theta0, self.prior_sigma, self.scale)],
             "covariances": [{"params": refs(ix), "cov": [nums(r) for r in np.asarray(cv)]}
-                            for ix, cv in self.cov_blocks],
+                            for ix, cv in self.cov_blocks]
+                           + [{"params": refs(ix), "map": [nums(r) for r in np.asarray(A)],
+                               "mean": nums(b0), "cov": [nums(r) for r in np.asarray(V)]}
+                              for ix, A, b0, V in self.map_priors],
             "oscillation": {"formula": formula,
                             "params": [names[int(i)] if int(i) >= 0 else float(v)
                                        for i, v in zip(self.osc_idx, self.osc_val)]},
@@ -186,8 +192,8 @@ class ModelSpec:
     def from_config(cls, cfg) -> "ModelSpec":
         """The description held by a JSON configuration (a dict or its text) in the schema of
         fit_model_create_json: names resolved (namespaces flattened to "ns.name"), held
-        entries as -1. Priors given through a linear map (b = A theta) are not read here:
-        their conversion belongs to the model, not to the input description."""
+        entries as -1. Priors given through a linear map (b = A theta) are kept as they are
+        written (map_priors): the map, the measured values and their covariance."""
         import json
         if isinstance(cfg, (str, bytes)):
             cfg = json.loads(cfg)
@@ -216,10 +222,12 @@ class ModelSpec:
         def refs(vs):
             return np.array([ref(v) for v in vs], np.int32)
 
-        cov_blocks = []
+        cov_blocks, map_priors = [], []
         for b in cfg.get("covariances", []):
             if "map" in b:
-                raise ValueError("a prior on b = A theta is converted by the model, not read here")
+                map_priors.append((refs(b["params"]), np.array(b["map"], np.float64),
+                                   np.array(b["mean"], np.float64), np.array(b["cov"], np.float64)))
+                continue
             cov_blocks.append((refs(b["params"]), np.array(b["cov"], np.float64)))
         osc = cfg["oscillation"]
         mode = {"eq1": OSC_EQ1, "vacuum3": OSC_VACUUM3, "sterile4": OSC_STERILE4}[osc["formula"]]
@@ -249,7 +257,7 @@ class ModelSpec:
         remap = 1 if cfg.get("energy_correction", "overlap") == "spline" else 0
         return cls(cfg.get("name", "config"), names, np.array(th0), np.array(sig), np.array(scl),
                    cov_blocks, mode, osc_idx, osc_val, refs(cfg["core_powers"]), n_true,
-                   float(grid["e_lo"]), float(grid["e_hi"]), dets, datasets, remap)
+                   float(grid["e_lo"]), float(grid["e_hi"]), dets, datasets, remap, map_priors)
 
 
 # ----------------------------------------------------------------------------------------

@@ -308,6 +308,10 @@ def test_description_from_a_namespaced_configuration(cfg):
     assert s.param_names[:2] == ["osc.sin2_2th13", "osc.dm2_ee"]
     assert all(n.startswith(("osc.", "det.")) for n in s.param_names)
     assert s.osc_idx[0] == 0 and s.osc_idx[1] == 1
-    cfg2, *_ = _mapped_config()
-    with pytest.raises(ValueError, match="converted by the model"):
-        synth.ModelSpec.from_config(cfg2)
+    cfg2, A, b0, V, esc = _mapped_config()
+    s2 = synth.ModelSpec.from_config(cfg2)
+    assert len(s2.map_priors) == 1
+    ix, A2, b2, V2 = s2.map_priors[0]
+    assert [s2.param_names[i] for i in ix] == esc
+    assert np.array_equal(A2, A) and np.array_equal(b2, b0) and np.array_equal(V2, V)
+    _same(s2, synth.ModelSpec.from_config(s2.to_json()), "mapped")

@@ -651,3 +651,109 @@ def test_linear_prior_block_special_cases():
     assert t[0] == pytest.approx((1.0 / 1 + 3.0 / 4) / (1 / 1 + 1 / 4), rel=1e-14)
     assert Cb[0, 0] == pytest.approx(1 / (1 + 1 / 4), rel=1e-14)
     assert const == pytest.approx((1.0 - t[0]) ** 2 + (3.0 - t[0]) ** 2 / 4, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------------------
+# Eq. 6 with a generalised parametrisation, evaluated as written: (A theta - b0)^T V^-1 (A theta - b0)
+# ---------------------------------------------------------------------------------------
+def _with_maps(spec, maps, free=()):
+    """A copy of spec with map priors added; the parameters in `free` lose their individual
+    Gaussian priors (a map then constrains them)."""
+    s = copy.deepcopy(spec)
+    s.prior_sigma = s.prior_sigma.copy()
+    for i in free:
+        s.prior_sigma[i] = 0.0
+    s.map_priors = list(maps)
+    return s
+
+
+def test_map_prior_term_is_the_hand_computed_quadratic_form():
+    """Two parameters (a0, a1 of the single-detector model) and three measured combinations
+    b = (a0, a1, a0 + a1) with the covariance V = [[4, 2, 0], [2, 4, 0], [0, 0, 1]] (10^-4).
+    By hand: V^-1 = 10^4 [[1/3, -1/6, 0], [-1/6, 1/3, 0], [0, 0, 1]], so with residuals
+    r = (b - b0) the term is 10^4 (r1^2/3 - r1 r2/3 + r2^2/3 + r3^2); its gradient is
+    A^T 2 V^-1 r. The term is isolated as the difference to the model without the map."""
+    base = synth.make_model("c0")
+    i0, i1 = base.index("a0"), base.index("a1")
+    A = np.array([[1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    b0 = np.array([0.003, 1.001, 1.0])
+    V = 1e-4 * np.array([[4.0, 2.0, 0.0], [2.0, 4.0, 0.0], [0.0, 0.0, 1.0]])
+    ix = np.array([i0, i1], np.int32)
+    with_map = oracle.OracleModel(_with_maps(base, [(ix, A, b0, V)], free=ix))
+    without = oracle.OracleModel(_with_maps(base, [], free=ix))
+    data = synth.poisson_data(without.expected(base.theta0), 21)
+    theta = base.theta0.copy()
+    theta[i0], theta[i1] = 0.012, 0.995
+    r1, r2, r3 = theta[i0] - 0.003, theta[i1] - 1.001, theta[i0] + theta[i1] - 1.0
+    hand = 1e4 * (r1 * r1 / 3 - r1 * r2 / 3 + r2 * r2 / 3 + r3 * r3)
+    v1, g1 = with_map.nll(theta, data, grad=True)
+    v0, g0 = without.nll(theta, data, grad=True)
+    assert v1 - v0 == pytest.approx(hand, rel=1e-12)
+    # gradient by hand: d/da0 = 1e4 (2 r1/3 - r2/3 + 2 r3), d/da1 = 1e4 (2 r2/3 - r1/3 + 2 r3)
+    dg = g1 - g0
+    assert dg[i0] == pytest.approx(1e4 * (2 * r1 / 3 - r2 / 3 + 2 * r3), rel=1e-10)
+    assert dg[i1] == pytest.approx(1e4 * (2 * r2 / 3 - r1 / 3 + 2 * r3), rel=1e-10)
+    others = np.ones(base.n_params, bool)
+    others[ix] = False
+    assert np.all(dg[others] == 0.0)
+
+
+def test_map_prior_with_identity_map_is_a_covariance_block():
+    """A = I makes Eq. 6's generalised term the plain correlated prior of Eq. 6 on the
+    parameters themselves with mean b0: both oracle paths give the same -2lnL and gradient."""
+    base = synth.make_model("c0")
+    rng = np.random.default_rng(22)
+    names = ["a0", "a1", "a2"]
+    ix = np.array([base.index(n) for n in names], np.int32)
+    sig = np.array([0.01, 0.005, 0.001])
+    R = np.array([[1.0, 0.3, -0.2], [0.3, 1.0, 0.1], [-0.2, 0.1, 1.0]])
+    V = R * np.outer(sig, sig)
+    b0 = base.theta0[ix] + sig * rng.standard_normal(3)
+    m = oracle.OracleModel(_with_maps(base, [(ix, np.eye(3), b0, V)], free=ix))
+    blk = _with_maps(base, [], free=ix)
+    blk.theta0 = blk.theta0.copy()
+    blk.theta0[ix] = b0
+    blk.cov_blocks = list(blk.cov_blocks) + [(ix, V)]
+    b = oracle.OracleModel(blk)
+    data = synth.poisson_data(b.expected(base.theta0), 23)
+    for _ in range(5):
+        th = base.theta0.copy()
+        th[ix] += 2 * sig * rng.standard_normal(3)
+        v1, g1 = m.nll(th, data, grad=True)
+        v2, g2 = b.nll(th, data, grad=True)
+        assert v1 == pytest.approx(v2, rel=1e-12)
+        np.testing.assert_allclose(g1, g2, rtol=1e-9, atol=1e-9 * np.abs(g2).max())
+
+
+def test_map_prior_gradient_matches_central_differences():
+    """c1 with its nine energy-scale coefficients constrained through a 12-row map: the
+    analytic gradient of the whole -2lnL against central differences."""
+    base = synth.make_model("c1")
+    rng = np.random.default_rng(24)
+    esc = [f"a{k}[{d}]" for d in range(3) for k in range(3)]
+    ix = np.array([base.index(n) for n in esc], np.int32)
+    A = np.vstack([np.eye(9), rng.standard_normal((3, 9))])
+    w = np.array([0.01, 0.005, 0.001] * 3 + [0.005] * 3)
+    V = _spd(rng, 12)
+    V = V / np.sqrt(np.outer(np.diag(V), np.diag(V))) * np.outer(w, w)
+    b0 = A @ base.theta0[ix] + 0.5 * w * rng.standard_normal(12)
+    spec = _with_maps(base, [(ix, A, b0, V)], free=ix)
+    om = oracle.OracleModel(spec)
+    data = synth.poisson_data(om.expected(base.theta0), 25)
+    theta = om.theta_of_z(0.4 * rng.standard_normal(spec.n_params))
+    _, g = om.nll(theta, data, grad=True)
+    for i in ix:
+        h = 1e-6 * spec.scale[i]
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (om.nll(tp, data) - om.nll(tm, data)) / (2 * h)
+        assert abs(fd - g[i]) * spec.scale[i] < 1e-5 * (1 + abs(g[i]) * spec.scale[i])
+
+
+def test_map_prior_is_rejected_when_not_positive_definite():
+    base = synth.make_model("c0")
+    ix = np.array([base.index("a0")], np.int32)
+    with pytest.raises(ValueError, match="positive"):
+        oracle.OracleModel(_with_maps(base, [(ix, np.ones((2, 1)), np.zeros(2),
+                                              np.array([[1.0, 2.0], [2.0, 1.0]]))]))
