@@ -2,23 +2,25 @@
 
 Bar per instance:
   * |nll_min - nll_min_oracle| <= 1e-3 (the tolerance on -2lnL at the minimum), and
-  * every best-fit parameter within 1e-2 of its oracle sigma, and within 1e-3 sigma (the
-    strict bar) for a stated share of the instances.
+  * every best-fit parameter within 1e-3 of its oracle sigma (the strict bar).
 sigma = sqrt(2 (H^-1)_ii) at the oracle minimum, H from central differences of the analytic
 gradient. Parameters without curvature (no data, no prior under the dataset mask) have
 sigma = inf and only need a finite value.
 
-Why two parameter bars. The energy correction by overlap length is only continuous in
-(a0, a1, a2). In directions that are nearly flat and cross its kinks - here the Li-9 rates
-against the common mode of their shape parameters - the minimum is not pinned to 1e-3 sigma
-by an FP32 gradient (whose noise is ~1e-4 in whitened units), and in some instances not even
-by the FP64 fit started from two different points. The strict bar is asserted for the share
-of instances measured to meet it; the 1e-2 sigma bar for all.
+The strict bar holds for every instance of every test (min_strict = 1, no other minimum)
+except on the three-dataset model with the overlap-length energy correction. There the
+correction is only continuous in (a0, a1, a2): the gradient jumps where a mapped bin edge
+crosses a grid edge, and the FP32 evaluation places each such crease within ~1e-7 of a bin
+of where the FP64 oracle places it. Along the nearly flat directions that cross the creases
+(the Li-9 rates against the common mode of their 38 shape parameters) this moves the minimum
+of the FP32 likelihood by more than 1e-3 sigma in some instances, while the same fits on the
+C1-continuous spline correction meet the strict bar in all instances. For those tests the
+strict bar is asserted for the measured share and 1e-2 sigma for all.
 
-Several minima: the kinks can also hold separate local minima. Where the GPU result is not
+Several minima: the creases can also hold separate local minima. Where the GPU result is not
 the oracle's minimum (|dnll| > 1e-3 or a parameter beyond 1e-2 sigma), the test requires it
 to be a minimum of the FP64 likelihood: the oracle restarted there stays within 1e-2 sigma and
-1e-4 in -2lnL. Such instances must stay rare (at most 1 in 8).
+1e-4 in -2lnL; tests that allow this say how many instances may.
 """
 import numpy as np
 import pytest
@@ -76,7 +78,7 @@ def run_gpu(names_per_inst, datas, masks, starts=None, opts=None):
     return thetas, res
 
 
-def check_against_oracle(name, datas, masks, thetas, res, max_other=None, min_strict=0.5):
+def check_against_oracle(name, datas, masks, thetas, res, max_other=0, min_strict=1.0):
     spec, om, _ = spec_of(name)
     n_other = n_strict = 0
     for i, (d, m) in enumerate(zip(datas, masks)):
@@ -99,8 +101,7 @@ def check_against_oracle(name, datas, masks, thetas, res, max_other=None, min_st
         dev2 = np.abs(thetas[i][fin] - cert["theta"][fin]) / sig[fin]
         assert dev2.max() <= 1e-2, (i, spec.param_names[np.flatnonzero(fin)[dev2.argmax()]], dev2.max())
         n_other += 1
-    limit = max(1, len(datas) // 8) if max_other is None else max_other
-    assert n_other <= limit, (n_other, len(datas))
+    assert n_other <= max_other, (n_other, len(datas))
     assert n_strict >= min_strict * len(datas), (n_strict, len(datas))
     print(f"{name}: {n_strict}/{len(datas)} instances meet the strict 1e-3 sigma bar, "
           f"{n_other} stopped in another certified minimum")
@@ -118,7 +119,8 @@ def test_fit_c0_matches_oracle(engine):
 def test_fit_c1_with_dataset_masks_matches_oracle(engine):
     datas, masks, _ = make_instances("c1", 6, 200, masks=list(synth.C1_MASKS))
     th, res = run_gpu(["c1"] * 6, datas, masks, opts=engine_opts(engine))
-    check_against_oracle("c1", datas, masks, th, res)
+    # overlap-rule creases on the three-dataset model (module docstring)
+    check_against_oracle("c1", datas, masks, th, res, max_other=1, min_strict=0.5)
 
 
 @ENGINES
@@ -143,12 +145,12 @@ def test_fit_c1_ensemble_statistics(engine):
 @ENGINES
 def test_fit_c1_spline_ensemble(engine):
     """The three-dataset model with the area-conserving spline energy correction: -2lnL
-    continuously differentiable in (a0, a1, a2), so no kink can hold a second minimum. 32
-    pseudo-experiments; all must reach the oracle's minimum (1e-3 in -2lnL, 1e-2 sigma), and
-    the strict 1e-3 sigma bar is asserted for the measured share."""
+    continuously differentiable in (a0, a1, a2), so no crease can hold a second minimum. 32
+    pseudo-experiments; all must reach the oracle's minimum within 1e-3 in -2lnL and 1e-3
+    sigma in every parameter."""
     datas, masks, _ = make_instances("c1/spline", 32, 700)
     th, res = run_gpu(["c1/spline"] * 32, datas, masks, opts=engine_opts(engine))
-    check_against_oracle("c1/spline", datas, masks, th, res, max_other=0, min_strict=0.5)
+    check_against_oracle("c1/spline", datas, masks, th, res)
 
 
 @ENGINES
@@ -166,7 +168,7 @@ def test_plain_coordinates_match_oracle():
     o.precondition = 0
     datas, masks, _ = make_instances("c1", 16, 740, masks=list(synth.C1_MASKS))
     th, res = run_gpu(["c1"] * 16, datas, masks, opts=o)
-    check_against_oracle("c1", datas, masks, th, res)
+    check_against_oracle("c1", datas, masks, th, res, max_other=2, min_strict=0.5)
     datas, masks, _ = make_instances("c2", 2, 750)
     th, res = run_gpu(["c2"] * 2, datas, masks, opts=o)
     check_against_oracle("c2", datas, masks, th, res)
@@ -190,7 +192,7 @@ def test_fit_c1_on_the_41_bin_flux_grid():
     without data: prior only) instead of the reco binning."""
     datas, masks, _ = make_instances("c1_flux41", 8, 730)
     th, res = run_gpu(["c1_flux41"] * 8, datas, masks)
-    check_against_oracle("c1_flux41", datas, masks, th, res)
+    check_against_oracle("c1_flux41", datas, masks, th, res, max_other=1, min_strict=0.5)
 
 
 @ENGINES
@@ -243,3 +245,23 @@ def test_start_points_iteration_limit_and_empty_batch(engine):
     empty = np.zeros(0, fitcore.INSTANCE_DTYPE)
     fitcore.fit_batch([gm], empty, np.zeros(1, np.float32), None, np.zeros(1),
                       np.zeros(1, fitcore.RESULT_DTYPE), o)
+
+
+@ENGINES
+def test_clock_budget_ends_every_fit_with_timeout(engine):
+    """A clock budget far below one evaluation (1 ns) ends every fit with FIT_STATUS_TIMEOUT:
+    the device limit gives up and returns (no wait is left open), each fit reports its start
+    point, and the next call on the same models runs normally."""
+    spec, om, _ = spec_of("c1")
+    datas, masks, _ = make_instances("c1", 40, 810, masks=list(synth.C1_MASKS))
+    o = engine_opts(engine)
+    o.time_budget_s = 1e-9
+    th, res = run_gpu(["c1"] * 40, datas, masks, opts=o)
+    assert np.all(res["status"] == 6), np.unique(res["status"])   # FIT_STATUS_TIMEOUT
+    assert res["iters"].max() <= 1
+    scale = np.where(spec.prior_sigma > 0, spec.prior_sigma, spec.scale)
+    for t in th:
+        assert np.all(np.isfinite(t))
+        assert np.all(np.abs(t - spec.theta0) <= 1e-5 * (scale + np.abs(spec.theta0)))
+    th2, res2 = run_gpu(["c1"] * 4, datas[:4], masks[:4], opts=engine_opts(engine))
+    assert np.all(res2["status"] == 0)
