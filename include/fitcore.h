@@ -75,8 +75,10 @@ extern "C" {
  * eta = (sin^2 th12, sin^2 th13, dm2_21, dm2_31, sin^2 2th14, dm2_41) */
 #define FIT_OSC_STERILE4 2
 
-/* Energy correction (Eq. 7 chain, "Neutrino signal"): how the corrected spectrum is integrated
- * over the original binning */
+/* Energy correction (the third step of the signal chain in "Structure of the framework": the
+ * spectrum smoothed with a second-degree polynomial energy map and integrated again over the
+ * original binning; "Neutrino signal" for the area-conserving spline): how the corrected
+ * spectrum is integrated over the original binning */
 #define FIT_REMAP_OVERLAP 0 /* each true bin's content spread uniformly over its mapped interval */
 #define FIT_REMAP_SPLINE 1  /* area-conserving spline: C1 cubic Hermite interpolant of the
                              * cumulative content, slopes (rho_{k-1} + rho_k) / 2 at the edges */
@@ -149,6 +151,12 @@ typedef struct fit_model_info_t {
  * Errors: INVALID_ARG / INVALID_CONFIG (message names the field), NON_SPD_COV, OOM, CUDA. */
 int fit_model_create(const fit_model_desc *desc, fit_model **out);
 void fit_model_destroy(fit_model *model);
+/* Sizes of a model: parameter count (the likelihood's parameter vector, signal and nuisance
+ * parameters of the general concept, "General concept and statistical methods"), the data
+ * vector's length (reco bins of all datasets, Eq. 9's product over datasets and bins), the
+ * dataset and true-bin counts, and the device memory the model holds. model: from
+ * fit_model_create*; info: host, written. Errors: INVALID_ARG on NULL. Synchronous, no
+ * device call. */
 int fit_model_info(const fit_model *model, fit_model_info_t *info);
 
 /* Builds a model from a JSON configuration ([S]: the framework's first component reads a
@@ -292,8 +300,10 @@ int fit_batch(fit_model *const *models, int n_models, const fit_instance *inst, 
  *  - Allocates nothing: it calls no cudaMalloc / cudaFree / allocating library routine. Its
  *    per-block workspace is a 16 MiB array in this library's device memory, which every GPU
  *    that loads the library holds until the process exits.
- *  - theta, data, masks, nll_out, grad_out, status_out must all be device memory (host
- *    buffers are rejected with FIT_ERR_INVALID_ARG, since staging them would allocate).
+ *  - theta, data, masks, nll_out, grad_out, status_out must all be device memory of the
+ *    current device, or managed memory (host buffers are rejected with FIT_ERR_INVALID_ARG,
+ *    since staging them would allocate; so is another GPU's memory). The model must have
+ *    been created on the current device (else FIT_ERR_INVALID_ARG).
  *    data and masks may be NULL with the meaning they have in fit_model_eval, whose outputs
  *    and semantics this call shares.
  *  - A model whose per-block workspace exceeds the 16 MiB is rejected (FIT_ERR_INVALID_ARG);

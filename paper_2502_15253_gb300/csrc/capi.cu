@@ -175,6 +175,7 @@ struct fit_model {
     int pre_state = 0;     // 0 not built, 1 built, -1 failed (fits run unpreconditioned)
     std::vector<std::string> names;   // parameter names (models created from a configuration)
     std::vector<double> sigma;        // prior width per parameter (block members: sqrt(V_ii))
+    int device = -1;                  // the CUDA device holding the model's memory
 };
 
 // error / launch-count hooks for the other translation units of the library
@@ -182,9 +183,29 @@ int fitcore_fail(int code, const std::string &msg) { return fail(code, msg); }
 
 // hooks for noalloc.cu (same library)
 int fitcore_noalloc_fail(int code, const std::string &msg) { return fail(code, msg); }
-int fitcore_model_device(fit_model *model, const DevModel **dev, const DevModel **host) {
+int fitcore_model_device(fit_model *model, const DevModel **dev, const DevModel **host, int *device) {
     *dev = model->dev;
     *host = &model->host;
+    *device = model->device;
+    return FIT_OK;
+}
+
+// The largest dynamic shared memory eval_kernel has been allowed on each device. The attribute
+// is shared by every thread of the process, so the evaluation paths only ever raise it (under
+// this lock): a smaller request never lowers a limit another thread's launch relies on.
+namespace {
+std::mutex g_eval_smem_mutex;
+std::vector<size_t> g_eval_smem_limit;
+}  // namespace
+
+int fitcore_raise_eval_smem(size_t bytes) {
+    int dev = 0;
+    FIT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_eval_smem_mutex);
+    if ((int)g_eval_smem_limit.size() <= dev) g_eval_smem_limit.resize(dev + 1, 0);
+    if (bytes <= g_eval_smem_limit[dev]) return FIT_OK;
+    FIT_CUDA(cudaFuncSetAttribute(fitcore::eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    g_eval_smem_limit[dev] = bytes;
     return FIT_OK;
 }
 void fitcore_count_launch() { g_launches++; }
@@ -646,6 +667,11 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         return fail(FIT_ERR_CUDA, std::string("fit_model_create: upload: ") + cudaGetErrorString(e));
     }
     M->bytes = A.buf.size() + sizeof(DevModel);
+    if (cudaGetDevice(&M->device) != cudaSuccess) {
+        cudaGetLastError();
+        fit_model_destroy(M);
+        return fail(FIT_ERR_CUDA, "fit_model_create: cudaGetDevice");
+    }
     M->n_params = P;
     M->n_data = h.n_data;
     M->n_ds = h.n_ds;
@@ -684,8 +710,8 @@ static int launch_eval(fit_model *model, int B, const double *theta_d, const flo
     const int threads = 256;
     bool in_smem = fitcore::eval_smem_bytes(h, true) <= 96 * 1024;
     size_t smem = fitcore::eval_smem_bytes(h, in_smem);
-    FIT_CUDA(cudaFuncSetAttribute(fitcore::eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)std::min(smem, cfg.smem_optin)));
+    rc = fitcore_raise_eval_smem(std::min(smem, cfg.smem_optin));
+    if (rc) return rc;
     int per_sm = 0;
     FIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fitcore::eval_kernel, threads, smem));
     if (per_sm < 1) return fail(FIT_ERR_INVALID_CONFIG, "fit_model_eval: model too large for one block");
@@ -1576,11 +1602,30 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
     if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, o.blocks_per_sm);
     const int grid = std::max(1, std::min(n_inst, per_sm * cfg.sms));
 
-    Staged dm, di, dd, dst, dfx, dbe, dre, dws, dq;
+    Staged dm, di, dd, dst, dfx, dbe, dre, dws, dq, dord;
     bool hbe = false, hre = false;
     std::vector<DevModel> hm(n_models);
     for (int i = 0; i < n_models; ++i) hm[i] = models[i]->host;
+    // Queue order: the costliest fits first, so that no long fit is picked up last and holds
+    // the launch while the other blocks are idle (instances of uneven size). Cost of one
+    // evaluation ~ the survival and energy-correction work, true bins x (cores + 4) per fitted
+    // dataset, plus the parameter vector.
+    std::vector<int> order(n_inst);
+    bool reordered = false;
+    {
+        std::vector<double> cost(n_inst);
+        for (int i = 0; i < n_inst; ++i) {
+            const DevModel &h = hm[inst[i].model];
+            int nd = 0;
+            for (int d = 0; d < h.n_ds; ++d) nd += (inst[i].mask >> d) & 1u;
+            cost[i] = (double)nd * h.N_t * (h.C + 4) + h.P;
+            order[i] = i;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        for (int i = 0; i < n_inst && !reordered; ++i) reordered = order[i] != i;
+    }
     rc = stage_in(hm.data(), sizeof(DevModel) * n_models, s, dm);
+    if (!rc && reordered) rc = stage_in(order.data(), sizeof(int) * n_inst, s, dord);
     if (!rc) rc = stage_in(inst, sizeof(fit_instance) * n_inst, s, di);
     if (!rc) rc = stage_in(data, sizeof(float) * data_len, s, dd);
     if (!rc && start) rc = stage_in(start, sizeof(double) * par_len, s, dst);
@@ -1620,6 +1665,7 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
         a.hist_global = placement == 1 ? 0 : 1;
         a.budget_ns = (uint64_t)(o.time_budget_s * 1e9);
         a.precond = precond ? 1 : 0;
+        a.order = reordered ? (const int *)dord.dev : nullptr;
         if (o.use_graph) {
             rc = graph_launch(kern, grid, o.threads, smem, a, (int *)dq.dev, s);
         } else {
@@ -1654,7 +1700,7 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
     }
     if (!rc && hre && cudaMemcpyAsync(results, dre.dev, sizeof(fit_result) * n_inst, cudaMemcpyDeviceToHost, s))
         rc = fail(FIT_ERR_CUDA, "fit_batch: copy back");
-    for (Staged *b : {&dm, &di, &dd, &dst, &dfx, &dbe, &dre, &dws, &dq}) release(*b, s);
+    for (Staged *b : {&dm, &di, &dd, &dst, &dfx, &dbe, &dre, &dws, &dq, &dord}) release(*b, s);
     // the staged model table and instance table are host vectors: finish before they go away
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_batch: synchronise");
     return rc;

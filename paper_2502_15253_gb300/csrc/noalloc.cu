@@ -30,8 +30,24 @@ extern "C" int fit_model_eval_noalloc(fit_model *model, int B, const double *the
                                       int *status_out, void *stream);
 
 // The model's device layout lives in capi.cu; it hands the pieces needed here through this hook.
-int fitcore_model_device(fit_model *model, const fitcore::DevModel **dev, const fitcore::DevModel **host);
+int fitcore_model_device(fit_model *model, const fitcore::DevModel **dev, const fitcore::DevModel **host,
+                         int *device);
+int fitcore_raise_eval_smem(size_t bytes);
 void fitcore_count_launch();
+
+// Host-side decision on where the call's memory lives (no CUDA call): the model must be on the
+// current device, and every buffer either managed memory or device memory of that device
+// (another GPU's memory is not readable there without peer access). types[i] / devices[i]:
+// the cudaMemoryType and device of buffer i. Returns FIT_OK or FIT_ERR_INVALID_ARG.
+extern "C" int fitcore_noalloc_check_devices(int model_device, int current_device, int n, const int *types,
+                                             const int *devices) {
+    if (model_device != current_device) return FIT_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (types[i] == cudaMemoryTypeManaged) continue;
+        if (types[i] != cudaMemoryTypeDevice || devices[i] != current_device) return FIT_ERR_INVALID_ARG;
+    }
+    return FIT_OK;
+}
 
 extern "C" int fit_model_eval_noalloc(fit_model *model, int B, const double *theta, const float *data,
                                       const uint32_t *masks, double *nll_out, float *grad_out,
@@ -40,7 +56,8 @@ extern "C" int fit_model_eval_noalloc(fit_model *model, int B, const double *the
         return fitcore_noalloc_fail(FIT_ERR_INVALID_ARG, "fit_model_eval_noalloc: bad argument");
     if (B == 0) return FIT_OK;
     const fitcore::DevModel *dev = nullptr, *h = nullptr;
-    fitcore_model_device(model, &dev, &h);
+    int model_device = -1;
+    fitcore_model_device(model, &dev, &h, &model_device);
     const size_t per_block = (size_t)h->ws_eval_floats;
     if (per_block > kScratchFloats)
         return fitcore_noalloc_fail(FIT_ERR_INVALID_ARG,
@@ -66,17 +83,30 @@ extern "C" int fit_model_eval_noalloc(fit_model *model, int B, const double *the
         }
         scratch = g_scratch_addr[device];
     }
-    // every buffer must already be device memory: staging a host buffer would allocate
+    // every buffer must already be memory of the current device (or managed): staging a host
+    // buffer would allocate, and another GPU's memory is not readable here
     const void *ptrs[] = {theta, data, masks, nll_out, grad_out, status_out};
+    int types[6], devices[6], n = 0;
     for (const void *p : ptrs) {
         if (!p) continue;
         cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
-            !(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
             cudaGetLastError();
             return fitcore_noalloc_fail(FIT_ERR_INVALID_ARG, "fit_model_eval_noalloc: every buffer must be device memory");
         }
+        types[n] = (int)a.type;
+        devices[n] = a.device;
+        ++n;
     }
+    if (model_device != device)
+        return fitcore_noalloc_fail(FIT_ERR_INVALID_ARG,
+                                    "fit_model_eval_noalloc: the model was created on device " +
+                                        std::to_string(model_device) + ", the current device is " +
+                                        std::to_string(device));
+    if (fitcore_noalloc_check_devices(model_device, device, n, types, devices) != FIT_OK)
+        return fitcore_noalloc_fail(FIT_ERR_INVALID_ARG,
+                                    "fit_model_eval_noalloc: every buffer must be device memory of the current "
+                                    "device (or managed memory)");
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();
@@ -84,8 +114,8 @@ extern "C" int fit_model_eval_noalloc(fit_model *model, int B, const double *the
     }
     const int threads = 256;
     const size_t smem = fitcore::eval_smem_bytes(*h, false);
-    if (cudaFuncSetAttribute(fitcore::eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
+    // (raised only: the attribute is shared with fit_model_eval's launches in other threads)
+    if (fitcore_raise_eval_smem(smem) != FIT_OK) {
         cudaGetLastError();
         return fitcore_noalloc_fail(FIT_ERR_CUDA, "fit_model_eval_noalloc: cudaFuncSetAttribute");
     }
