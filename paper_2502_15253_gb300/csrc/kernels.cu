@@ -943,9 +943,10 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
     while (true) {
         if (tid == 0) S.inst = atomicAdd(A.queue, 1);
         __syncthreads();
-        const int ii = S.inst;
+        const int q = S.inst;
         __syncthreads();
-        if (ii >= A.n_inst) break;
+        if (q >= A.n_inst) break;
+        const int ii = A.order ? A.order[q] : q;   // queue position -> instance
         const fit_instance in = A.inst[ii];
         copy_model(&S.m, A.models + in.model);
         const DevModel &m = S.m;

@@ -26,6 +26,8 @@ struct FitArgs {
     const uint8_t *fixed;        // device, indexed like start/best, or nullptr: held parameters
     uint64_t budget_ns;
     int precond;                 // 1: fit in the models' preconditioned coordinates (if built)
+    const int *order;            // device [n_inst] or nullptr: the instance taken at each queue
+                                 // position (costliest first, so no long fit starts last)
 };
 
 __global__ void eval_kernel(const DevModel *gm, int B, const double *theta, const float *data,
