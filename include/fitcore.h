@@ -244,7 +244,11 @@ typedef struct fit_batch_opts {
     int engine;           /* 0 = persistent kernel (one block per fit at a time); 1 = lockstep:
                              the fits of a model advance one evaluation per round, each round
                              three launches over all of them (threads, blocks_per_sm and
-                             placement then do not apply)                                    */
+                             placement then do not apply); 2 = lockstep with the response
+                             fold and its adjoint as tensor-core GEMMs over all active fits
+                             of a model (F = V R^T, G R; split TF32, the fold of [S] "one
+                             response matrix times many spectra"), one workspace per
+                             (fit, dataset) kept through the round                          */
     int precondition;     /* 1 (default) = persistent engine fits in Fisher-preconditioned
                              coordinates: the expected Hessian of -2lnL at the model's nominal
                              point, built once per model on first use, makes the quasi-Newton

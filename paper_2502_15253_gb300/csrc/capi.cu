@@ -400,6 +400,17 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
             }
         A.put(&dt.rdense_hi, rhi);
         A.put(&dt.rdense_lo, rlow);
+        // and its transpose [N_t x ldr] for the adjoint fold G R on the tensor cores
+        const int ldr = (nr + 3) / 4 * 4;
+        vector<float> thi((size_t)Nt * ldr, 0.f), tlo((size_t)Nt * ldr, 0.f);
+        for (int j = 0; j < nr; ++j)
+            for (int k = 0; k < Nt; ++k) {
+                thi[(size_t)k * ldr + j] = rhi[(size_t)j * ldt + k];
+                tlo[(size_t)k * ldr + j] = rlow[(size_t)j * ldt + k];
+            }
+        dt.ldr = ldr;
+        A.put(&dt.rdt_hi, thi);
+        A.put(&dt.rdt_lo, tlo);
     }
     h.max_reco = max_reco;
     // ---- datasets -------------------------------------------------------------------------
@@ -1106,7 +1117,7 @@ int graph_launch(const void *kern, int grid, int threads, size_t smem, fitcore::
 int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instance *inst, int n_inst,
                        const float *data, const double *start, const uint8_t *fixed, double *best,
                        fit_result *results, const fit_batch_opts &o, cudaStream_t s, int64_t data_len,
-                       int64_t par_len, bool precond) {
+                       int64_t par_len, bool precond, bool tc) {
     LaunchCfg cfg;
     int rc = device_cfg(cfg);
     if (rc) return rc;
@@ -1146,20 +1157,29 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
         A.f_noise_rel = o.f_noise_rel;
         A.budget_ns = (uint64_t)(o.time_budget_s * 1e9);
         A.precond = precond && models[mi]->pre_state == 1 ? 1 : 0;
-        // evaluation workspace: the adjoint needs the full per-dataset arrays
+        // evaluation workspace: the adjoint needs the full per-dataset arrays (engine 2: one
+        // per (active instance, dataset) pair in global memory, kept for the round)
         const int ws_floats = h.ws_eval_floats;
         const size_t eval_smem = fitcore::ls_eval_smem_bytes(P, ws_floats);
-        A.ws_in_smem = eval_smem <= 48 * 1024 ? 1 : 0;
+        A.ws_in_smem = !tc && eval_smem <= 48 * 1024 ? 1 : 0;
         const size_t esm = A.ws_in_smem ? eval_smem : fitcore::ls_eval_smem_bytes(P, 0);
         const size_t ssm = fitcore::ls_step_smem_bytes();
         // the general builds of the evaluation kernels (3+1 formula, spline correction)
         const bool six = h.n_osc == 6 || h.remap_mode == FIT_REMAP_SPLINE;
         const void *kf = six ? (const void *)fitcore::ls_forward_kernel6 : (const void *)fitcore::ls_forward_kernel;
         const void *ka = six ? (const void *)fitcore::ls_adjoint_kernel6 : (const void *)fitcore::ls_adjoint_kernel;
-        int per_sm_f = 0, per_sm_a = 0, per_sm_s = 0;
-        for (const void *k : {kf, ka})
-            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm) != cudaSuccess)
+        const void *kl = nullptr;
+        if (tc) {
+            kf = six ? (const void *)fitcore::ls_tc_fwd_kernel6 : (const void *)fitcore::ls_tc_fwd_kernel;
+            kl = six ? (const void *)fitcore::ls_tc_lik_kernel6 : (const void *)fitcore::ls_tc_lik_kernel;
+            ka = six ? (const void *)fitcore::ls_tc_adj_kernel6 : (const void *)fitcore::ls_tc_adj_kernel;
+        }
+        int per_sm_f = 0, per_sm_a = 0, per_sm_s = 0, per_sm_l = 0;
+        for (const void *k : {kf, ka, kl})
+            if (k && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm) != cudaSuccess)
                 rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep shared memory");
+        if (!rc && kl && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_l, kl, 128, esm) || per_sm_l < 1))
+            rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep occupancy");
         for (const void *k : {(const void *)fitcore::ls_step_kernel, (const void *)fitcore::ls_init_kernel})
             if (!rc && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm) != cudaSuccess)
                 rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep shared memory");
@@ -1170,7 +1190,8 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
         if (!rc && (per_sm_f < 1 || per_sm_a < 1 || per_sm_s < 1))
             rc = fail(FIT_ERR_INVALID_CONFIG, "fit_batch: lockstep kernels do not fit an SM");
         if (rc) break;
-        const int cap_f = per_sm_f * cfg.sms, cap_a = per_sm_a * cfg.sms, cap_s = per_sm_s * cfg.sms;
+        const int cap_f = per_sm_f * cfg.sms, cap_a = per_sm_a * cfg.sms, cap_s = per_sm_s * cfg.sms,
+                  cap_l = per_sm_l * cfg.sms;
         A.ws_stride = A.ws_in_smem ? 0 : ws_floats;
         std::vector<void *> bufs;
         auto al = [&](void **p, size_t bytes) {
@@ -1195,7 +1216,28 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
         al((void **)&act1, sizeof(int) * n);
         al((void **)&cnt, sizeof(int) * 2);
         al((void **)&deadline, sizeof(uint64_t));
-        if (!A.ws_in_smem) al((void **)&A.ws_global, sizeof(float) * (size_t)std::max(cap_f, cap_a) * ws_floats);
+        if (tc) {
+            // per (active instance, dataset) workspace and the GEMM operands per dataset
+            A.ldf = (h.max_reco + 3) / 4 * 4;
+            A.ldr = A.ldf;
+            const size_t rows = (size_t)nd * n;
+            al((void **)&A.ws_global, sizeof(float) * rows * ws_floats);
+            al((void **)&A.vhi, sizeof(float) * rows * h.ldt);
+            al((void **)&A.vlo, sizeof(float) * rows * h.ldt);
+            al((void **)&A.fbuf, sizeof(float) * rows * A.ldf);
+            al((void **)&A.ghi, sizeof(float) * rows * A.ldr);
+            al((void **)&A.glo, sizeof(float) * rows * A.ldr);
+            al((void **)&A.gvbuf, sizeof(float) * rows * h.ldt);
+            // rows of datasets an instance does not fit are still multiplied: keep them finite
+            for (float *p : {A.vhi, A.vlo})
+                if (!rc && cudaMemsetAsync(p, 0, sizeof(float) * rows * h.ldt, s) != cudaSuccess)
+                    rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep clear");
+            for (float *p : {A.ghi, A.glo})
+                if (!rc && cudaMemsetAsync(p, 0, sizeof(float) * rows * A.ldr, s) != cudaSuccess)
+                    rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep clear");
+        } else if (!A.ws_in_smem) {
+            al((void **)&A.ws_global, sizeof(float) * (size_t)std::max(cap_f, cap_a) * ws_floats);
+        }
         if (!rc && cudaMemcpyAsync(grp_d, grp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
             rc = fail(FIT_ERR_CUDA, "fit_batch: lockstep upload");
         A.group = grp_d;
@@ -1225,6 +1267,48 @@ int fit_batch_lockstep(fit_model *const *models, int n_models, const fit_instanc
             }
             void *largs[] = {&A};
             cudaLaunchKernel(kf, dim3(std::max(1, std::min(active * nd, cap_f))), dim3(128), largs, esm, s);
+            if (tc) {
+                // F_d = V_d R^T and, after the likelihood, GV_d = G_d R, each as the split
+                // product hi hi + hi lo + lo hi (TF32 operands, FP32 accumulation)
+                for (int d = 0; d < nd && !rc; ++d) {
+                    const fitcore::DevDetector &dt = h.det[h.ds[d].det];
+                    const size_t vo = (size_t)d * n * h.ldt;
+                    fitcore::GemmOut go;
+                    go.C = A.fbuf + (size_t)d * n * A.ldf;
+                    go.ldc = A.ldf;
+                    go.epi = fitcore::EPI_F32;
+                    rc = fitcore::tc_gemm(true, active, dt.n_reco, h.N_t, A.vhi + vo, h.ldt, dt.rdense_hi, h.ldt, go, s,
+                                          nullptr);
+                    go.epi = fitcore::EPI_F32_ADD;
+                    if (!rc)
+                        rc = fitcore::tc_gemm(true, active, dt.n_reco, h.N_t, A.vhi + vo, h.ldt, dt.rdense_lo, h.ldt,
+                                              go, s, nullptr);
+                    if (!rc)
+                        rc = fitcore::tc_gemm(true, active, dt.n_reco, h.N_t, A.vlo + vo, h.ldt, dt.rdense_hi, h.ldt,
+                                              go, s, nullptr);
+                }
+                if (rc) break;
+                cudaLaunchKernel(kl, dim3(std::max(1, std::min(active * nd, cap_l))), dim3(128), largs, esm, s);
+                g_launches++;
+                for (int d = 0; d < nd && !rc; ++d) {
+                    const fitcore::DevDetector &dt = h.det[h.ds[d].det];
+                    const size_t go_ = (size_t)d * n * A.ldr;
+                    fitcore::GemmOut go;
+                    go.C = A.gvbuf + (size_t)d * n * h.ldt;
+                    go.ldc = h.ldt;
+                    go.epi = fitcore::EPI_F32;
+                    rc = fitcore::tc_gemm(true, active, h.N_t, dt.n_reco, A.ghi + go_, A.ldr, dt.rdt_hi, dt.ldr, go, s,
+                                          nullptr);
+                    go.epi = fitcore::EPI_F32_ADD;
+                    if (!rc)
+                        rc = fitcore::tc_gemm(true, active, h.N_t, dt.n_reco, A.ghi + go_, A.ldr, dt.rdt_lo, dt.ldr, go,
+                                              s, nullptr);
+                    if (!rc)
+                        rc = fitcore::tc_gemm(true, active, h.N_t, dt.n_reco, A.glo + go_, A.ldr, dt.rdt_hi, dt.ldr, go,
+                                              s, nullptr);
+                }
+                if (rc) break;
+            }
             cudaLaunchKernel(ka, dim3(std::max(1, std::min(active * nd, cap_a))), dim3(128), largs, esm, s);
             fitcore::ls_step_kernel<<<std::max(1, std::min(active, cap_s)), 128, ssm, s>>>(A);
             g_launches += 3;
@@ -1516,16 +1600,16 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
                                                          " of a prior block cannot be held fixed");
         }
     }
-    if (o.engine == 1) {
+    if (o.engine == 1 || o.engine == 2) {
         bool pre = o.precondition != 0;
         if (pre) {
             std::lock_guard<std::mutex> plock(g_pre_mutex);
             for (int i = 0; i < n_models; ++i) build_preconditioner(models[i], s);
         }
         return fit_batch_lockstep(models, n_models, inst, n_inst, data, start, fixed, best, results, o, s,
-                                  data_len, par_len, pre);
+                                  data_len, par_len, pre, o.engine == 2);
     }
-    if (o.engine != 0) return fail(FIT_ERR_INVALID_ARG, "fit_batch: engine must be 0 or 1");
+    if (o.engine != 0) return fail(FIT_ERR_INVALID_ARG, "fit_batch: engine must be 0, 1 or 2");
     int max_loc = 0;   // working vectors + evaluation workspace, without the history
     int n_osc = 4;     // the general build when any model uses the 3+1 formula or the spline
     for (int mi = 0; mi < n_models; ++mi) {

@@ -27,6 +27,9 @@ struct DevDetector {
     const float *rcol;       // [col_w x N_t]: rcol[b * N_t + k] = R[col_lo[k] + b][k] (0 past the band)
     const float *rdense_hi;  // [N_r x ldt] dense response, TF32-exact high part (tensor-core fold)
     const float *rdense_lo;  // [N_r x ldt] R - rdense_hi
+    const float *rdt_hi;     // [N_t x ldr] R^T, TF32-exact high part (tensor-core adjoint fold)
+    const float *rdt_lo;     // [N_t x ldr] R^T - rdt_hi
+    int ldr;                 // row stride of R^T (N_r rounded up to 4)
 };
 
 struct DevBkg {
@@ -804,13 +807,8 @@ static __device__ void ds_remap(const DevModel &m, int d, const Ctx &c, EvalWs w
 
 }
 
-// Stages C and C2: fold, backgrounds, deviance, dD/dmu (ws.gmu) and the background-shape
-// gradient; returns the dataset's -2lnL (all threads). The efficiency and rate gradients are
-// added when grad != nullptr, data != nullptr and no status bit is set.
-template <class Ctx>
-static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, const float *pd, const Ctx &c,
-                                     const float *data, EvalWs ws, float *grad, double *red, int *status,
-                                     float *mu_out) {
+// Stage C: fold into reco bins, ws.f0 = R v (before the efficiency). Ends with a barrier.
+static __device__ void ds_fold(const DevModel &m, int d, EvalWs ws) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
     const int nr = ds.n_reco;
@@ -855,7 +853,18 @@ static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, 
         }
     }
     __syncthreads();
+}
 
+// Stage C2: backgrounds, deviance, dD/dmu (ws.gmu) and the background-shape gradient from the
+// folded spectrum ws.f0; returns the dataset's -2lnL (all threads). The efficiency and rate
+// gradients are added when grad != nullptr, data != nullptr and no status bit is set.
+template <class Ctx>
+static __device__ double ds_lik(const DevModel &m, int d, const float *pv, const float *pd, const Ctx &c,
+                                const float *data, EvalWs ws, float *grad, double *red, int *status,
+                                float *mu_out) {
+    const DevDataset &ds = m.ds[d];
+    const int nr = ds.n_reco;
+    const int tid = threadIdx.x, nth = blockDim.x;
     // ---- stage C2: backgrounds, deviance, dD/dmu ----------------------------------------
     const int nb = ds.bkg_end - ds.bkg_begin;
     float part[2 + kMaxBkgDs];
@@ -912,16 +921,22 @@ static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, 
     return nll_d;
 }
 
-// Stages D, E and F: adjoint of the fold, of the energy map and of the signal; adds the
-// gradient contributions to grad. Needs ws.u/ts/ptot/dp/pcw (ds_signal<true>) and ws.gmu.
-template <int NC, int NOSC, bool SPL>
-static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, const float *pd,
-                                     const DsCtxT<NOSC> &c, EvalWs ws, float *grad, double *red) {
+// Stages C and C2 in one sequence.
+template <class Ctx>
+static __device__ double ds_fold_lik(const DevModel &m, int d, const float *pv, const float *pd, const Ctx &c,
+                                     const float *data, EvalWs ws, float *grad, double *red, int *status,
+                                     float *mu_out) {
+    ds_fold(m, d, ws);
+    return ds_lik(m, d, pv, pd, c, data, ws, grad, red, status, mu_out);
+}
+
+// Stage D: adjoint of the fold, ws.v <- gv = eff R^T gmu (column bands). Ends with a barrier.
+template <int NOSC>
+static __device__ void ds_adjoint_fold(const DevModel &m, int d, const DsCtxT<NOSC> &c, EvalWs ws) {
     const DevDataset &ds = m.ds[d];
     const DevDetector &dt = m.det[ds.det];
-    const int N_t = m.N_t, C = m.C, nr = ds.n_reco;
+    const int N_t = m.N_t, nr = ds.n_reco;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const EMap &em = c.em;
     // ---- stage D: adjoint of the fold, gv = eff R^T gmu (column bands) --------------------
     float *gv = ws.v;   // v is dead after the fold
     // rcol is exactly 0 past each column's band, so the loop runs the full band width with
@@ -940,7 +955,20 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
         gv[k] = pmul(c.eff, (s[0] + s[1]) + (s[2] + s[3]));
     }
     __syncthreads();
+}
 
+// Stages E and F: adjoint of the energy map and of the signal from gv (in ws.v); adds the
+// gradient contributions to grad. Needs ws.u/ts/ptot/dp/pcw (ds_signal<true>).
+template <int NC, int NOSC, bool SPL>
+static __device__ void ds_adjoint_ef(const DevModel &m, int d, const float *pv, const float *pd,
+                                     const DsCtxT<NOSC> &c, EvalWs ws, float *grad, double *red) {
+    const DevDataset &ds = m.ds[d];
+    const int N_t = m.N_t, C = m.C;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const EMap &em = c.em;
+    const float *gv = ws.v;
+    (void)pv;
+    (void)pd;
     // ---- stage E: adjoint of the energy map and of the signal ---------------------------
     // per source k: gu = sum_t F_kt gv_t; A0 = (gu - gv(floor Y_k)) / w, A1 = (gv(floor Y_k+1) - gu) / w
     constexpr int kN = 3 + NOSC, kP = 4 + NOSC;   // index of d/d norm, first d/d power
@@ -1005,18 +1033,28 @@ static __device__ void ds_adjoint_nc(const DevModel &m, int d, const float *pv, 
     __syncthreads();
 }
 
-// One dataset in one sequence: adds its Poisson -2lnL and (if grad != nullptr) its gradient
-// contributions (theta space, P floats). Returns the dataset's -2lnL (all threads); *status |=
-// kSt* bits on failure.
-// Stages D-F with the per-core sums sized for the model's core count.
+// Stages E-F with the per-core sums sized for the model's core count.
+template <bool SPL, int NOSC>
+static __device__ void ds_adjoint_rest(const DevModel &m, int d, const float *pv, const float *pd,
+                                       const DsCtxT<NOSC> &c, EvalWs ws, float *grad, double *red) {
+    if (m.C <= 2)
+        ds_adjoint_ef<2, NOSC, SPL>(m, d, pv, pd, c, ws, grad, red);
+    else
+        ds_adjoint_ef<FIT_MAX_CORES, NOSC, SPL>(m, d, pv, pd, c, ws, grad, red);
+}
+
+// Stages D-F: adjoint of the fold, of the energy map and of the signal; adds the gradient
+// contributions to grad. Needs ws.u/ts/ptot/dp/pcw (ds_signal<true>) and ws.gmu.
 template <bool SPL, int NOSC>
 static __device__ void ds_adjoint(const DevModel &m, int d, const float *pv, const float *pd,
                                   const DsCtxT<NOSC> &c, EvalWs ws, float *grad, double *red) {
-    if (m.C <= 2)
-        ds_adjoint_nc<2, NOSC, SPL>(m, d, pv, pd, c, ws, grad, red);
-    else
-        ds_adjoint_nc<FIT_MAX_CORES, NOSC, SPL>(m, d, pv, pd, c, ws, grad, red);
+    ds_adjoint_fold(m, d, c, ws);
+    ds_adjoint_rest<SPL>(m, d, pv, pd, c, ws, grad, red);
 }
+
+// One dataset in one sequence: adds its Poisson -2lnL and (if grad != nullptr) its gradient
+// contributions (theta space, P floats). Returns the dataset's -2lnL (all threads); *status |=
+// kSt* bits on failure.
 
 template <int NOSC, bool SPL>
 static __device__ double eval_dataset_n(const DevModel &m, int d, const float *pv, const float *pd,

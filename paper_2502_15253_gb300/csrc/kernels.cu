@@ -1173,6 +1173,172 @@ __global__ void __launch_bounds__(128) ls_adjoint_kernel6(LsArgs A) {
         ls_adjoint_body<4, true>(A);
 }
 
+// ---- lockstep rounds with the folds on the tensor cores (engine 2) ---------------------------
+// Between these kernels the library runs, per dataset d, F_d = V_d R^T and GV_d = G_d R as
+// split-TF32 GEMMs over the active instances (row a of each matrix = active position a). Each
+// (instance, dataset) pair keeps its own evaluation workspace for the whole round, so the
+// survival partials of the forward pass serve the adjoint without being recomputed.
+
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t b = __float_as_uint(x);
+    b = (b + 0x1000u) & 0xFFFFE000u;   // nearest value with 10 mantissa bits
+    return __uint_as_float(b);
+}
+
+__device__ __forceinline__ EvalWs ls_pair_ws(const LsArgs &A, const DevModel &m, int it) {
+    return carve_eval_ws(A.ws_global + (int64_t)it * A.ws_stride, m.N_t, m.C, m.max_reco, m.n_osc);
+}
+
+// Stage A (with the partials) and B per (instance, dataset); v as TF32 high part and rest.
+template <int NOSC, bool SPL>
+__device__ __forceinline__ void ls_tc_fwd_body(LsArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LsEvalSmem &S = *reinterpret_cast<LsEvalSmem *>(smem_raw);
+    copy_model(&S.m, A.model);
+    const DevModel &m = S.m;
+    const int P = m.P, nd = m.n_ds, na = *A.n_act;
+    float *pv = reinterpret_cast<float *>(smem_raw + sizeof(LsEvalSmem));
+    float *pd = pv + P;
+    for (int it = blockIdx.x; it < na * nd; it += gridDim.x) {
+        const int a = it / nd, d = it % nd, g = A.act[a];
+        const fit_instance in = A.inst[A.group[g]];
+        const int64_t gd = (int64_t)g * nd + d;
+        if (!((in.mask >> d) & 1u)) {
+            if (threadIdx.x == 0) A.nll_ds[gd] = 0.0;
+            continue;
+        }
+        const EvalWs ws = ls_pair_ws(A, m, it);
+        const FitVecs V = ls_vecs(A, g, P);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            pv[i] = V.pv[i];
+            pd[i] = V.pd[i];
+        }
+        if (threadIdx.x == 0) S.status = 0;
+        __syncthreads();
+        DsCtxT<NOSC> c;
+        if (ds_setup(m, d, pv, pd, c, &S.status)) {
+            ds_signal<true>(m, d, pv, pd, c, ws);
+            ds_remap<SPL>(m, d, c, ws);
+            float *vh = A.vhi + ((int64_t)d * A.n + a) * m.ldt, *vl = A.vlo + ((int64_t)d * A.n + a) * m.ldt;
+            for (int t = threadIdx.x; t < m.ldt; t += blockDim.x) {
+                const float x = t < m.N_t ? ws.v[t] : 0.f;
+                const float hi = tf32_hi(x);
+                vh[t] = hi;
+                vl[t] = x - hi;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && S.status) atomicOr(&A.stat[g], S.status);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(128) ls_tc_fwd_kernel(LsArgs A) { ls_tc_fwd_body<4, false>(A); }
+__global__ void __launch_bounds__(128) ls_tc_fwd_kernel6(LsArgs A) {
+    if (A.model->osc_mode == FIT_OSC_STERILE4)
+        ls_tc_fwd_body<6, true>(A);
+    else
+        ls_tc_fwd_body<4, true>(A);
+}
+
+// Stage C2 per (instance, dataset) from the fold F = R v of the GEMM: -2lnL, dD/dmu (TF32
+// high part and rest for the adjoint GEMM), efficiency and background gradients.
+template <int NOSC>
+__device__ __forceinline__ void ls_tc_lik_body(LsArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LsEvalSmem &S = *reinterpret_cast<LsEvalSmem *>(smem_raw);
+    copy_model(&S.m, A.model);
+    const DevModel &m = S.m;
+    const int P = m.P, nd = m.n_ds, na = *A.n_act;
+    float *pv = reinterpret_cast<float *>(smem_raw + sizeof(LsEvalSmem));
+    float *pd = pv + P;
+    for (int it = blockIdx.x; it < na * nd; it += gridDim.x) {
+        const int a = it / nd, d = it % nd, g = A.act[a];
+        const fit_instance in = A.inst[A.group[g]];
+        const int64_t gd = (int64_t)g * nd + d;
+        if (!((in.mask >> d) & 1u) || A.stat[g] != 0) continue;
+        const EvalWs ws = ls_pair_ws(A, m, it);
+        const FitVecs V = ls_vecs(A, g, P);
+        const int nr = m.ds[d].n_reco;
+        const float *fr = A.fbuf + ((int64_t)d * A.n + a) * A.ldf;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            pv[i] = V.pv[i];
+            pd[i] = V.pd[i];
+        }
+        for (int j = threadIdx.x; j < nr; j += blockDim.x) ws.f0[j] = fr[j];
+        if (threadIdx.x == 0) S.status = 0;
+        __syncthreads();
+        DsCtxT<NOSC> c;
+        double nll = 0.0;
+        if (ds_setup(m, d, pv, pd, c, &S.status)) {
+            nll = ds_lik(m, d, pv, pd, c, A.data + in.data_off, ws, A.gsl + gd * P, S.red, &S.status, nullptr);
+            float *gh = A.ghi + ((int64_t)d * A.n + a) * A.ldr, *gl = A.glo + ((int64_t)d * A.n + a) * A.ldr;
+            for (int j = threadIdx.x; j < A.ldr; j += blockDim.x) {
+                const float x = j < nr ? ws.gmu[j] : 0.f;
+                const float hi = tf32_hi(x);
+                gh[j] = hi;
+                gl[j] = x - hi;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            A.nll_ds[gd] = nll;
+            if (S.status) atomicOr(&A.stat[g], S.status);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(128) ls_tc_lik_kernel(LsArgs A) { ls_tc_lik_body<4>(A); }
+__global__ void __launch_bounds__(128) ls_tc_lik_kernel6(LsArgs A) {
+    if (A.model->osc_mode == FIT_OSC_STERILE4)
+        ls_tc_lik_body<6>(A);
+    else
+        ls_tc_lik_body<4>(A);
+}
+
+// Stages E and F per (instance, dataset) from GV = R^T dD/dmu of the GEMM (gv = eff GV).
+template <int NOSC, bool SPL>
+__device__ __forceinline__ void ls_tc_adj_body(LsArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LsEvalSmem &S = *reinterpret_cast<LsEvalSmem *>(smem_raw);
+    copy_model(&S.m, A.model);
+    const DevModel &m = S.m;
+    const int P = m.P, nd = m.n_ds, na = *A.n_act;
+    float *pv = reinterpret_cast<float *>(smem_raw + sizeof(LsEvalSmem));
+    float *pd = pv + P;
+    for (int it = blockIdx.x; it < na * nd; it += gridDim.x) {
+        const int a = it / nd, d = it % nd, g = A.act[a];
+        const fit_instance in = A.inst[A.group[g]];
+        if (!((in.mask >> d) & 1u) || A.stat[g] != 0) continue;
+        const int64_t gd = (int64_t)g * nd + d;
+        const EvalWs ws = ls_pair_ws(A, m, it);
+        const FitVecs V = ls_vecs(A, g, P);
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            pv[i] = V.pv[i];
+            pd[i] = V.pd[i];
+        }
+        if (threadIdx.x == 0) S.status = 0;
+        __syncthreads();
+        DsCtxT<NOSC> c;
+        if (ds_setup(m, d, pv, pd, c, &S.status)) {
+            const float *gr = A.gvbuf + ((int64_t)d * A.n + a) * m.ldt;
+            for (int k = threadIdx.x; k < m.N_t; k += blockDim.x) ws.v[k] = pmul(c.eff, gr[k]);
+            __syncthreads();
+            ds_adjoint_rest<SPL>(m, d, pv, pd, c, ws, A.gsl + gd * P, S.red);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(128) ls_tc_adj_kernel(LsArgs A) { ls_tc_adj_body<4, false>(A); }
+__global__ void __launch_bounds__(128) ls_tc_adj_kernel6(LsArgs A) {
+    if (A.model->osc_mode == FIT_OSC_STERILE4)
+        ls_tc_adj_body<6, true>(A);
+    else
+        ls_tc_adj_body<4, true>(A);
+}
+
 // Minimiser step per active instance: gathers the round's evaluation (dataset sums, prior,
 // gradient in z), runs fit_decide, and either prepares theta of the next trial point and puts
 // the instance on the next active list, or writes its result.

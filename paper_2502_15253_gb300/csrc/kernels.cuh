@@ -67,9 +67,22 @@ struct LsArgs {
     uint64_t budget_ns;
     uint64_t *deadline;          // device: set by the init kernel
     int precond;                 // 1: fit in the model's preconditioned coordinates
+    // engine 2 (folds on the tensor cores): ws_global holds one workspace per (active position,
+    // dataset) pair; matrices per dataset d of n rows (row = active position)
+    float *vhi, *vlo;            // [n_ds][n x ldt] corrected spectra, TF32 high part and rest
+    float *fbuf;                 // [n_ds][n x ldf] fold R v (before the efficiency)
+    float *ghi, *glo;            // [n_ds][n x ldr] dD/dmu, TF32 high part and rest
+    float *gvbuf;                // [n_ds][n x ldt] R^T dD/dmu
+    int ldf, ldr;
 };
 
 __global__ void ls_init_kernel(LsArgs A);
+__global__ void ls_tc_fwd_kernel(LsArgs A);
+__global__ void ls_tc_fwd_kernel6(LsArgs A);
+__global__ void ls_tc_lik_kernel(LsArgs A);
+__global__ void ls_tc_lik_kernel6(LsArgs A);
+__global__ void ls_tc_adj_kernel(LsArgs A);
+__global__ void ls_tc_adj_kernel6(LsArgs A);
 __global__ void ls_forward_kernel(LsArgs A);
 __global__ void ls_adjoint_kernel(LsArgs A);
 __global__ void ls_forward_kernel6(LsArgs A);   // models with the 3+1 formula

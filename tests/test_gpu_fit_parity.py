@@ -59,7 +59,7 @@ def engine_opts(engine):
     return o
 
 
-ENGINES = pytest.mark.parametrize("engine", [0, 1], ids=["persistent", "lockstep"])
+ENGINES = pytest.mark.parametrize("engine", [0, 1, 2], ids=["persistent", "lockstep", "lockstep_tc"])
 
 
 def run_gpu(names_per_inst, datas, masks, starts=None, opts=None):
