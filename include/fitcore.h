@@ -230,8 +230,9 @@ typedef struct fit_batch_opts {
                              on one warp, a lane per pair)                                   */
     double f_noise_rel;   /* relative noise allowance of -2lnL in the line search (1e-6)     */
     int threads;          /* threads per block, multiple of 32 in [64, 128]; 0 = default 128 */
-    int blocks_per_sm;    /* resident blocks per SM: 5 selects the 96-register build of the
-                             kernel, 1-4 the 128-register one (capped); 0 = automatic        */
+    int blocks_per_sm;    /* resident blocks per SM (an upper bound): 5 or more selects the
+                             96-register build of the kernel, 1-4 the 128-register one;
+                             0 = automatic                                                  */
     int use_graph;        /* 1 = launch through a cached CUDA graph (work-queue memset and
                              kernel nodes, parameters updated in place for each call)        */
     double time_budget_s; /* per-launch clock budget (0 = 60 s); exceeded -> FIT_STATUS_TIMEOUT */
@@ -416,9 +417,12 @@ int fit_warmstart_draw(fit_model *model, const fit_warmstart_geom *geom, int B, 
 
 /* Trains the network for n_steps AdamW steps of `batch` fresh samples each, the geometries in
  * turn: draw theta and masks, expected spectra with the TF32 tensor-core fold, Poisson counts,
- * inputs and standardised targets, one step. Learning rate lr (0.05 + 0.95 (1 + cos(pi s /
- * n_steps)) / 2) at step s. losses_out (host or device [n_steps] double, or NULL) receives each
- * step's batch loss. Synchronous. */
+ * inputs and standardised targets, one step. The target of a sample is where a fit of its
+ * counts would end, to first order: the drawn point moved by one Gauss-Newton step of -2lnL
+ * with the expected Hessian at the nominal point (built once per geometry and dataset mask
+ * from 2P + 1 expectations), standardised by target_scale. Learning rate lr (0.05 + 0.95 (1 +
+ * cos(pi s / n_steps)) / 2) at step s. losses_out (host or device [n_steps] double, or NULL)
+ * receives each step's batch loss. Synchronous. */
 int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmstart_geom *geoms,
                         int n_geoms, int n_steps, int batch, float lr, float weight_decay,
                         uint64_t seed, double *losses_out, void *stream);
@@ -476,7 +480,8 @@ int fit_mc_spectrum(fit_mc *mc, int B, const double *params, double *out, void *
 int fit_mc_status(fit_mc *mc);
 
 /* Chooses threads per block and resident blocks per SM for fit_batch on the current device by
- * timing the candidate configurations (96 or 128 threads, 4 or 5 blocks per SM) on the first
+ * timing the candidate configurations (64 threads with 8 or 10 blocks per SM, 96 or 128
+ * threads with 4 or 5) on the first
  * n_sample instances (0 = ten per SM, at most n_inst), and writes the fastest into
  * opts->threads and opts->blocks_per_sm (other fields are used as given). Arguments as for
  * fit_batch; results of the timing runs are discarded. Synchronous. */

@@ -978,6 +978,110 @@ int fit_warmstart_draw(fit_model *model, const fit_warmstart_geom *geom, int B, 
     return rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+void theta_of_z_host(const fit_model *M, const double *z, double *th);
+
+// Rows of the linearised maximum-likelihood step for the targets of a warm-start geometry, per
+// dataset-mask variant v: with J = d mu / d z at the nominal point (central differences of the
+// device expectation), W = diag(1 / mu0) over the variant's bins and Lambda = 1 on the
+// constrained coordinates, the step from a drawn point z_t is (J^T W J + Lambda)^-1 (J^T W
+// (n - mu_t) - Lambda z_t). Row p of that inverse (p = target t's parameter) gives K1[v][t] =
+// (A^-1 J^T W)_p [D], K2[v][t] = (A^-1 Lambda)_p [P] and zf[v][t] = zscale_p / scale_t.
+int linear_mle_rows(fit_model *M, const fit_warmstart_geom &G, cudaStream_t s, std::vector<float> &K1,
+                    std::vector<float> &K2, std::vector<float> &zf, int &n_var) {
+    const int P = M->n_params, D = M->n_data, nt = G.n_targets;
+    const double hz = 1e-2;
+    const int R = 2 * P + 1;
+    std::vector<double> th((size_t)R * P), z(P, 0.0);
+    for (int q = 0; q < R; ++q) {
+        std::fill(z.begin(), z.end(), 0.0);
+        if (q > 0) z[(q - 1) / 2] = (q % 2) ? hz : -hz;
+        theta_of_z_host(M, z.data(), th.data() + (size_t)q * P);
+    }
+    std::vector<float> mu((size_t)R * D);
+    std::vector<int> st(R, 0);
+    int rc = fit_model_expected(M, R, th.data(), mu.data(), st.data(), s);
+    if (rc) return rc;
+    for (int q = 0; q < R; ++q)
+        if (st[q] != 0) return fail(FIT_ERR_INVALID_CONFIG, "warm start: expectation near the nominal point failed");
+    std::vector<double> J((size_t)D * P);
+    for (int j = 0; j < D; ++j)
+        for (int i = 0; i < P; ++i)
+            J[(size_t)j * P + i] =
+                ((double)mu[(size_t)(2 * i + 1) * D + j] - (double)mu[(size_t)(2 * i + 2) * D + j]) / (2.0 * hz);
+    std::vector<double> con(P);
+    for (int i = 0; i < P; ++i) con[i] = (M->sigma[i] > 0.0 || M->in_block[i]) ? 1.0 : 0.0;
+    n_var = std::max(1, G.n_masks);
+    K1.assign((size_t)n_var * nt * D, 0.f);
+    K2.assign((size_t)n_var * nt * P, 0.f);
+    zf.assign((size_t)n_var * nt, 0.f);
+    std::vector<double> w(D), A((size_t)P * P), L, x(P), y(P);
+    for (int v = 0; v < n_var; ++v) {
+        const uint32_t mask = G.n_masks > 0 ? G.masks[v] : 0xFFFFFFFFu;
+        std::fill(w.begin(), w.end(), 0.0);
+        for (int d = 0; d < M->host.n_ds; ++d) {
+            if (!((mask >> d) & 1u)) continue;
+            const int o = M->host.ds[d].data_off;
+            for (int j = 0; j < M->host.ds[d].n_reco; ++j) w[o + j] = mu[o + j] > 0.f ? 1.0 / mu[o + j] : 0.0;
+        }
+        std::fill(A.begin(), A.end(), 0.0);
+        for (int j = 0; j < D; ++j) {
+            if (w[j] == 0.0) continue;
+            const double *Jj = J.data() + (size_t)j * P;
+            for (int a = 0; a < P; ++a) {
+                const double ja = Jj[a] * w[j];
+                if (ja == 0.0) continue;
+                double *Aa = A.data() + (size_t)a * P;
+                for (int b = 0; b <= a; ++b) Aa[b] += ja * Jj[b];
+            }
+        }
+        double dmax = 0.0;
+        for (int a = 0; a < P; ++a) {
+            A[(size_t)a * P + a] += con[a];
+            dmax = std::max(dmax, A[(size_t)a * P + a]);
+        }
+        for (int a = 0; a < P; ++a) {   // a coordinate with neither data nor prior stays put
+            double &daa = A[(size_t)a * P + a];
+            daa += daa > 1e-9 * dmax ? 1e-12 * dmax : 1.0;
+            for (int b = 0; b < a; ++b) A[(size_t)b * P + a] = A[(size_t)a * P + b];
+        }
+        if (!cholesky_lower(P, A.data(), L))
+            return fail(FIT_ERR_INVALID_CONFIG, "warm start: expected Hessian not positive definite");
+        for (int t = 0; t < nt; ++t) {
+            const int p = G.target_idx[t];
+            // A x = e_p: forward then backward substitution with L L^T
+            for (int i = 0; i < P; ++i) {
+                double acc = (i == p) ? 1.0 : 0.0;
+                for (int k = 0; k < i; ++k) acc -= L[(size_t)i * P + k] * y[k];
+                y[i] = acc / L[(size_t)i * P + i];
+            }
+            for (int i = P - 1; i >= 0; --i) {
+                double acc = y[i];
+                for (int k = i + 1; k < P; ++k) acc -= L[(size_t)k * P + i] * x[k];
+                x[i] = acc / L[(size_t)i * P + i];
+            }
+            float *k1 = K1.data() + ((size_t)v * nt + t) * D, *k2 = K2.data() + ((size_t)v * nt + t) * P;
+            for (int j = 0; j < D; ++j) {
+                if (w[j] == 0.0) continue;
+                double acc = 0.0;
+                const double *Jj = J.data() + (size_t)j * P;
+                for (int i = 0; i < P; ++i) acc += x[i] * Jj[i];
+                k1[j] = (float)(acc * w[j]);
+            }
+            for (int i = 0; i < P; ++i) k2[i] = (float)(x[i] * con[i]);
+            zf[(size_t)v * nt + t] = (float)(M->zscale[p] / G.target_scale[t]);
+        }
+    }
+    return FIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmstart_geom *geoms, int n_geoms,
                         int n_steps, int batch, float lr, float weight_decay, uint64_t seed, double *losses_out,
                         void *stream) {
@@ -1010,6 +1114,30 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
         cudaMallocAsync(&loss, sizeof(double) * (size_t)n_steps, s))
         rc = fail(FIT_ERR_OOM, "fit_warmstart_train: workspace");
     for (int g = 0; g < n_geoms && !rc; ++g) rc = upload_geom(geoms[g], gd[g], s);
+    // linearised maximum-likelihood rows per geometry (targets = where a fit of the sample ends,
+    // to first order, rather than the drawn point)
+    float *zbuf = nullptr, *krows[16] = {nullptr};
+    int n_var[16] = {0};
+    if (!rc && cudaMallocAsync(&zbuf, sizeof(float) * (size_t)batch * max_p, s) != cudaSuccess)
+        rc = fail(FIT_ERR_OOM, "fit_warmstart_train: workspace");
+    for (int g = 0; g < n_geoms && !rc; ++g) {
+        std::vector<float> K1, K2, zf;
+        rc = linear_mle_rows(models[g], geoms[g], s, K1, K2, zf, n_var[g]);
+        if (rc) break;
+        const size_t n = K1.size() + K2.size() + zf.size();
+        if (cudaMallocAsync(&krows[g], sizeof(float) * n, s) != cudaSuccess) {
+            rc = fail(FIT_ERR_OOM, "fit_warmstart_train: workspace");
+            break;
+        }
+        std::vector<float> all;
+        all.reserve(n);
+        all.insert(all.end(), K1.begin(), K1.end());
+        all.insert(all.end(), K2.begin(), K2.end());
+        all.insert(all.end(), zf.begin(), zf.end());
+        if (cudaMemcpyAsync(krows[g], all.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: upload");
+    }
     float *x = rc ? nullptr : fitcore::mlp_input_buffer(mlp, batch);
     if (!rc && !x) rc = fail(FIT_ERR_OOM, "fit_warmstart_train: input buffer");
     for (int step = 0; step < n_steps && !rc; ++step) {
@@ -1021,20 +1149,28 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
         const uint64_t pseed = seed ^ 0xA5A5A5A55A5A5A5Aull;
         const float lr_s = lr * (float)(0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * step / n_steps)));
         rc = fitcore::draw_theta(m->host, m->dev, batch, seed, off, G.n_uniform, gd[g].uidx, gd[g].uhalf, G.n_masks,
-                                 gd[g].choices, theta, masks, s);
+                                 gd[g].choices, theta, masks, s, zbuf);
         if (!rc) rc = fitcore::expected_tc(m->host, m->dev, batch, theta, mu, status, 0, s);
         if (!rc) rc = fitcore::poisson_sample((int64_t)batch * m->n_data, mu, pseed, off * (uint64_t)m->n_data, cnt, s);
         if (!rc) rc = fitcore::features(batch, m->n_data, cnt, m->host.asimov, G.n_masks > 0 ? masks : nullptr,
                                         m->host.slot_ds, status, n_in, G.slot0, G.onehot_slot, x, s);
-        if (!rc) rc = fitcore::targets(batch, m->n_params, theta, m->host.theta0, G.n_targets, gd[g].tidx, gd[g].tscale,
-                                       n_out, status, y, s);
+        if (!rc) {
+            const int P = m->n_params, D = m->n_data, nt = G.n_targets, nv = n_var[g];
+            const float *K1 = krows[g], *K2 = K1 + (size_t)nv * nt * D, *zf = K2 + (size_t)nv * nt * P;
+            rc = fitcore::mle_targets(batch, P, D, theta, m->host.theta0, zbuf, cnt, mu, nt, gd[g].tidx, gd[g].tscale,
+                                      K1, K2, zf, nv, gd[g].choices, masks, n_out, status, y, s);
+        }
         if (!rc) rc = fit_mlp_train_step(mlp, batch, x, y, lr_s, weight_decay, loss + step, stream);
     }
     if (!rc && losses_out &&
         cudaMemcpyAsync(losses_out, loss, sizeof(double) * (size_t)n_steps, cudaMemcpyDefault, s) != cudaSuccess)
         rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: losses");
-    for (int g = 0; g < n_geoms; ++g) free_geom(gd[g], s);
-    for (void *p : {(void *)theta, (void *)mu, (void *)cnt, (void *)y, (void *)masks, (void *)status, (void *)loss})
+    for (int g = 0; g < n_geoms; ++g) {
+        free_geom(gd[g], s);
+        if (krows[g]) cudaFreeAsync(krows[g], s);
+    }
+    for (void *p : {(void *)theta, (void *)mu, (void *)cnt, (void *)y, (void *)masks, (void *)status, (void *)loss,
+                    (void *)zbuf})
         if (p) cudaFreeAsync(p, s);
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: sync");
     return rc;
@@ -1815,8 +1951,12 @@ int fit_batch_autotune(fit_model *const *models, int n_models, const fit_instanc
     fit_batch_opts o = *opts, best_o = *opts;
     float best_ms = 0.f;
     bool found = false;
-    for (int threads : {96, 128}) {
-        for (int bps : {4, 5}) {
+    // (threads, blocks per SM): 64-thread blocks put twice the fits on an SM at the same
+    // warp count; a cap of 5 or more selects the 96-register build
+    const int cand[][2] = {{64, 8}, {64, 10}, {96, 4}, {96, 5}, {128, 4}, {128, 5}};
+    for (const auto &cb : cand) {
+        const int threads = cb[0], bps = cb[1];
+        {
             if (rc) break;
             o.threads = threads;
             o.blocks_per_sm = bps;

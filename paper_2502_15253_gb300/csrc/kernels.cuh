@@ -105,9 +105,13 @@ int features(int B, int n_data, const float *data, const float *nbar, const uint
              const int *status, int n_in, int slot0, int onehot, float *x, cudaStream_t s);
 int draw_theta(const DevModel &h, const DevModel *dev, int B, uint64_t seed, uint64_t offset, int n_uni,
                const int *uidx, const double *uhalf, int n_masks, const uint32_t *choices, double *theta,
-               uint32_t *masks, cudaStream_t s);
+               uint32_t *masks, cudaStream_t s, float *z_out = nullptr);
 int targets(int B, int P, const double *theta, const double *theta0, int n_t, const int *idx, const double *scale,
             int n_out, const int *status, float *y, cudaStream_t s);
+int mle_targets(int B, int P, int D, const double *theta, const double *theta0, const float *z, const float *cnt,
+                const float *mu, int n_t, const int *idx, const double *scale, const float *K1, const float *K2,
+                const float *zf, int n_var, const uint32_t *choices, const uint32_t *masks, int n_out,
+                const int *status, float *y, cudaStream_t s);
 int starts(int B, int P, const double *theta0, int n_t, const int *idx, const double *scale, const float *out,
            int n_out, double *theta, cudaStream_t s);
 size_t fit_smem_bytes(int floats);

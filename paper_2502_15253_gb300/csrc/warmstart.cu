@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(128) draw_kernel(const DevModel *__restrict__ 
                                                    uint64_t offset, int n_uni, const int *__restrict__ uidx,
                                                    const double *__restrict__ uhalf, int n_masks,
                                                    const uint32_t *__restrict__ choices, double *__restrict__ theta,
-                                                   uint32_t *__restrict__ masks) {
+                                                   uint32_t *__restrict__ masks, float *__restrict__ z_out) {
     extern __shared__ double z[];
     const DevModel &m = *gm;
     const int b = blockIdx.x, P = m.P;
@@ -72,6 +72,51 @@ __global__ void __launch_bounds__(128) draw_kernel(const DevModel *__restrict__ 
             th[p] = m.theta0[p] + acc;
         }
     }
+    // whitened coordinates of the drawn point: the normal deviate inside a block, the
+    // scaled offset elsewhere (a listed parameter's uniform draw included)
+    if (z_out) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const float zs = m.zscale[i];
+            z_out[(int64_t)b * P + i] = zs > 0.f ? (float)((th[i] - m.theta0[i]) / (double)zs) : (float)z[i];
+        }
+    }
+}
+
+// Regression targets at the linearised maximum-likelihood point of each sample. For the drawn
+// point z_t with expectation mu_t and counts n, one Gauss-Newton step on -2lnL with the
+// expected Hessian at the nominal point, (J^T W J + Lambda) delta = J^T W (n - mu_t) -
+// Lambda z_t, moves the point to where a fit would end (to first order); target t is
+// y = (theta_p - theta0_p) / scale_t + zf_t delta_p, with delta_p = K1_t (n - mu_t) - K2_t z_t
+// (rows of the solved system for the target's coordinate p, one pair per dataset-mask variant).
+// One block per sample, one warp per target.
+__global__ void mle_targets_kernel(int B, int P, int D, const double *__restrict__ theta,
+                                   const double *__restrict__ theta0, const float *__restrict__ z,
+                                   const float *__restrict__ cnt, const float *__restrict__ mu, int n_t,
+                                   const int *__restrict__ idx, const double *__restrict__ scale,
+                                   const float *__restrict__ K1, const float *__restrict__ K2,
+                                   const float *__restrict__ zf, int n_var, const uint32_t *__restrict__ choices,
+                                   const uint32_t *__restrict__ masks, int n_out, const int *__restrict__ status,
+                                   float *__restrict__ y) {
+    const int b = blockIdx.x, lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+    if (t >= n_out) return;
+    float v = 0.f;
+    if (t < n_t && !(status && status[b])) {
+        int var = 0;
+        if (n_var > 1 && masks)
+            for (int q = 0; q < n_var; ++q)
+                if (choices[q] == masks[b]) var = q;
+        const float *k1 = K1 + ((int64_t)var * n_t + t) * D, *k2 = K2 + ((int64_t)var * n_t + t) * P;
+        const float *nb = cnt + (int64_t)b * D, *mb = mu + (int64_t)b * D, *zb = z + (int64_t)b * P;
+        float acc = 0.f;
+        for (int j = lane; j < D; j += 32) acc = fmaf(k1[j], nb[j] - mb[j], acc);
+        for (int i = lane; i < P; i += 32) acc = fmaf(-k2[i], zb[i], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const int p = idx[t];
+        v = (float)((theta[(int64_t)b * P + p] - theta0[p]) / scale[t]) + zf[var * n_t + t] * acc;
+    }
+    if (lane == 0) y[(int64_t)b * n_out + t] = v;
 }
 
 // y[b][t] = (theta[b][idx_t] - theta0[idx_t]) / scale_t for t < n_t, 0 for n_t <= t < n_out
@@ -95,10 +140,11 @@ __global__ void targets_kernel(int B, int P, const double *__restrict__ theta, c
 
 int draw_theta(const DevModel &h, const DevModel *dev, int B, uint64_t seed, uint64_t offset, int n_uni,
                const int *uidx, const double *uhalf, int n_masks, const uint32_t *choices, double *theta,
-               uint32_t *masks, cudaStream_t s) {
+               uint32_t *masks, cudaStream_t s, float *z_out) {
     const size_t smem = sizeof(double) * (size_t)h.P;
     if (smem > 48 * 1024) return fitcore_fail(FIT_ERR_INVALID_ARG, "warm-start draw: too many parameters");
-    draw_kernel<<<B, 128, smem, s>>>(dev, B, seed, offset, n_uni, uidx, uhalf, n_masks, choices, theta, masks);
+    draw_kernel<<<B, 128, smem, s>>>(dev, B, seed, offset, n_uni, uidx, uhalf, n_masks, choices, theta, masks,
+                                     z_out);
     fitcore_count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("warm-start draw: ") + cudaGetErrorString(e));
@@ -110,6 +156,19 @@ int targets(int B, int P, const double *theta, const double *theta0, int n_t, co
     const int64_t n = (int64_t)B * n_out;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
     targets_kernel<<<grid, 256, 0, s>>>(B, P, theta, theta0, n_t, idx, scale, n_out, status, y);
+    fitcore_count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("warm-start targets: ") + cudaGetErrorString(e));
+    return FIT_OK;
+}
+
+int mle_targets(int B, int P, int D, const double *theta, const double *theta0, const float *z, const float *cnt,
+                const float *mu, int n_t, const int *idx, const double *scale, const float *K1, const float *K2,
+                const float *zf, int n_var, const uint32_t *choices, const uint32_t *masks, int n_out,
+                const int *status, float *y, cudaStream_t s) {
+    if (n_out > 32) return fitcore_fail(FIT_ERR_INVALID_ARG, "warm-start targets: more than 32 outputs");
+    mle_targets_kernel<<<B, 32 * n_out, 0, s>>>(B, P, D, theta, theta0, z, cnt, mu, n_t, idx, scale, K1, K2, zf,
+                                                n_var, choices, masks, n_out, status, y);
     fitcore_count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("warm-start targets: ") + cudaGetErrorString(e));

@@ -8,7 +8,9 @@ that geometry. Outputs (12, standardised by each parameter's width): 1 km geomet
 oscillation parameters, the nine energy-scale coefficients and the far-detector Li-9 rate;
 53 km geometry - the four oscillation parameters, the six energy-scale coefficients and the two
 normalisations. The oscillation parameters of interest are drawn uniformly within +-3.5 widths
-of nominal for training, every other parameter from its prior.
+of nominal for training, every other parameter from its prior. The network is trained to
+predict where a fit of the spectrum ends: the drawn point moved by one Gauss-Newton step of
+-2lnL with the expected Hessian at the nominal point (fit_warmstart_train).
 """
 from __future__ import annotations
 
@@ -59,13 +61,19 @@ def network(seed: int = 0) -> fitcore.Mlp:
 
 
 def train(net, models, specs, n_steps, batch=4096, lr=1e-3, weight_decay=1e-4, seed=1,
-          stream=None):
-    """Trains on fresh device-drawn samples of every geometry in turn; returns the losses."""
+          stream=None, epochs=1):
+    """Trains on device-drawn samples of every geometry in turn; returns the losses. Each epoch
+    is one fit_warmstart_train call of n_steps steps under the same seed, so every epoch sees
+    the same n_steps x batch samples (the generator is counter-based) with its own cosine
+    learning-rate cycle; the optimiser's moments carry over."""
     geoms = [geometry(s) for s in specs]
-    losses = np.zeros(n_steps)
-    fitcore.fit_warmstart_train(net, models, geoms, n_steps, batch, lr, weight_decay, seed,
-                                losses, stream)
-    return losses
+    out = []
+    for _ in range(max(1, int(epochs))):
+        losses = np.zeros(n_steps)
+        fitcore.fit_warmstart_train(net, models, geoms, n_steps, batch, lr, weight_decay, seed,
+                                    losses, stream)
+        out.append(losses)
+    return np.concatenate(out)
 
 
 def predict_starts(net, model, spec, B, data, masks, theta_out, stream=None):

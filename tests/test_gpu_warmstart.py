@@ -80,8 +80,8 @@ def test_training_learns_and_warm_fits_agree_with_cold(c1, c2):
     net = warmstart.network(seed=3)
     losses = warmstart.train(net, [m1, m2], [spec1, spec2], n_steps=1000, batch=4096, lr=1e-3)
     assert np.all(np.isfinite(losses))
-    # standardised targets: the untrained loss is their mean variance (~1.5 and ~1.0); the
-    # floor is set by how well the data constrain each parameter
+    # standardised targets (the linearised best fit of each sample): the untrained loss is
+    # their mean variance; the floor is how far the linearisation misses the data's best fit
     assert losses[-40::2].mean() < 0.85 * losses[0:4:2].mean()
     assert losses[-39::2].mean() < 0.85 * losses[1:4:2].mean()
 
@@ -117,5 +117,44 @@ def test_training_learns_and_warm_fits_agree_with_cold(c1, c2):
           f"{warm['n_evals'].mean():.1f} cold {cold['n_evals'].mean():.1f}")
     assert same.mean() >= 0.8 and not_worse.mean() >= 0.95
     # the 12 predicted parameters are a small part of the 291 the fit moves, so the iteration
-    # count hardly changes (about 1 % fewer on 8192 fits); it must not grow
+    # count hardly changes on this model (a start at the cold fit's own values of the 12 saves
+    # about 4 % of the evaluations); it must not grow
     assert warm["iters"].mean() <= 1.05 * cold["iters"].mean()
+
+
+def test_warm_start_saves_evaluations_on_the_53km_model(c1, c2):
+    """Held-out pseudo-experiments of the 53 km model drawn by the ensemble recipe (true
+    sin^2 th13 and dm2_31 within +-3 sigma, Poisson counts): fits from the network's starts reach
+    the cold fits' minima (within 1e-3 in -2lnL, so at the cold fits' parity with the oracle) with
+    measurably fewer evaluations. The most any network of these 12 outputs can save: starts at
+    the cold fits' own values of the 12 need 30 % fewer evaluations on this model; the
+    network's targets (one Gauss-Newton step with the nominal point's Jacobian) miss the best
+    fit most in dm2_31, whose Jacobian turns with the oscillation phase."""
+    spec1, m1 = c1
+    spec2, m2 = c2
+    net = warmstart.network(seed=3)
+    # 12 epochs over the same 2M samples (about 16 s): one epoch leaves the network short of
+    # the linearised best fit it is trained on (no gain), twelve bring the 53 km model's
+    # evaluations down by about 8 %
+    warmstart.train(net, [m1, m2], [spec1, spec2], n_steps=488, batch=4096, lr=1e-3, epochs=12)
+    B = 512
+    table = synth.make_ensemble(B, {"c1": spec1, "c2": spec2}, frac_c2=1.0, base=9_000_000)
+    truths = np.stack([t.theta_true for t in table])
+    mu, st = fitcore.expected_numpy(m2, truths)
+    assert np.all(st == 0)
+    data = np.stack([synth.poisson_data(mu[i], t.seed) for i, t in enumerate(table)]).astype(np.float32)
+    starts = torch.zeros((B, spec2.n_params), dtype=torch.float64, device="cuda")
+    warmstart.predict_starts(net, m2, spec2, B, torch.from_numpy(data).cuda(), None, starts)
+    inst = np.zeros(B, fitcore.INSTANCE_DTYPE)
+    inst["mask"] = spec2.all_mask()
+    inst["data_off"] = np.arange(B) * spec2.n_bins
+    inst["param_off"] = np.arange(B) * spec2.n_params
+    _, cold = fitcore.fit_numpy([m2], inst, data)
+    _, warm = fitcore.fit_numpy([m2], inst, data, start=starts.cpu().numpy().ravel())
+    assert np.all(cold["status"] == 0) and np.all(warm["status"] == 0)
+    same = np.abs(warm["nll_min"] - cold["nll_min"]) <= 1e-3
+    gain = 1.0 - warm["n_evals"].mean() / cold["n_evals"].mean()
+    print(f"53 km model: evaluations warm {warm['n_evals'].mean():.2f} cold "
+          f"{cold['n_evals'].mean():.2f} ({100 * gain:.1f} % fewer), same minimum {same.mean():.4f}")
+    assert same.mean() >= 0.99
+    assert gain >= 0.04
