@@ -602,7 +602,11 @@ def read_peaks():
 
 # DRAM bytes (read + write) per fit of the fit kernel by workload, from ncu captures of the current
 # kernel on a smaller launch of the same workload (traffic grows with the fits)
-FIT_DRAM_BYTES_PER_FIT = {}
+FIT_DRAM_BYTES_PER_FIT = {
+    "c3": {"per_fit": (59.901696e6 + 371.543040e6) / 760,
+           "note": "DRAM read+write bytes per fit of an ncu capture of this kernel on 760 fits of "
+                   "the same recipe (59.9 MB read, 371.5 MB written), scaled to the launch"},
+}
 
 # DRAM bytes (read + write) per event of mc_spectrum_kernel for one parameter set, from an ncu
 # capture of 11,904,680 events (154.81 MB read, 3.62 MB written); traffic grows with the events
@@ -1114,8 +1118,21 @@ def per_config_measurement(args, stream, flush, pg, world, rank):
         e1.record(stream)
         torch.cuda.synchronize()
         ems = max_over_ranks(e0.elapsed_time(e1) / reps, pg)
+        # the same roofline models as the headline line: L-BFGS state bytes per iteration
+        # against the copy bandwidth, the FP32 work model against the FMA peak
+        peaks = read_peaks()
+        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        P = sp.n_params
+        f_eval = flops_per_eval(sp, sp.all_mask()) + 8.0 * P * min(32, sp.n_bins, P)
+        fit_bytes = float(res["iters"].sum()) * (2 * 10 * P * 4 + 2 * P * 4)
+        fit_flops = float(res["n_evals"].sum()) * f_eval + float(res["iters"].sum()) * flops_lbfgs_iter(P, 32)
         r = {"workload": WORKLOADS[kind], "fits": world * B,
              "fits_per_s": world * B / (ms / 1e3), "ms_per_step": ms,
+             "fit_roofline": {"hbm_frac": fit_bytes / (ms / 1e3) / 1e9 / hbm_peak,
+                              "alu_frac": fit_flops / (ms / 1e3) / 1e12 / alu_peak},
+             "eval_alu_frac": flops_per_eval(sp, sp.all_mask()) * B / (ems / 1e3) / 1e12 / alu_peak,
              "iters_per_fit": float(res["iters"].mean()), "evals_per_fit": float(res["n_evals"].mean()),
              "converged_frac": float(np.mean(res["status"] == 0)),
              "eval_grad_per_s": world * B / (ems / 1e3), "eval_batch": B, "eval_ms": ems}
