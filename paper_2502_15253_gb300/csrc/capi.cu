@@ -358,7 +358,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
             for (int k = a; k <= b; ++k) rrow.push_back((float)R[(size_t)j * Nt + k]);
             while (rrow.size() % 4) rrow.push_back(0.f);
         }
-        vector<int> clo(Nt);
+        vector<int> clo(Nt), clen(Nt);
         int cw = 1;
         for (int k = 0; k < Nt; ++k) {
             int a = nr, b = -1;
@@ -369,6 +369,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
                 }
             if (b < a) a = b = 0;
             clo[k] = a;
+            clen[k] = b - a + 1;
             cw = std::max(cw, b - a + 1);
         }
         vector<float> rcol((size_t)cw * Nt, 0.f);
@@ -383,6 +384,7 @@ int fit_model_create(const fit_model_desc *d, fit_model **out) {
         A.put(&dt.row_off, roff);
         A.put(&dt.rrow, rrow);
         A.put(&dt.col_lo, clo);
+        A.put(&dt.col_len, clen);
         A.put(&dt.rcol, rcol);
         // dense copy for the tensor-core fold, split into a TF32-exact high part and the rest
         const int ldt = (Nt + 3) / 4 * 4;

@@ -27,6 +27,7 @@ struct DevDetector {
     const float *rcol;       // [col_w x N_t]: rcol[b * N_t + k] = R[col_lo[k] + b][k] (0 past the band)
     const float *rdense_hi;  // [N_r x ldt] dense response, TF32-exact high part (tensor-core fold)
     const float *rdense_lo;  // [N_r x ldt] R - rdense_hi
+    const int *col_len;      // [N_t] band length of column k
     const float *rdt_hi;     // [N_t x ldr] R^T, TF32-exact high part (tensor-core adjoint fold)
     const float *rdt_lo;     // [N_t x ldr] R^T - rdt_hi
     int ldr;                 // row stride of R^T (N_r rounded up to 4)
@@ -939,10 +940,12 @@ static __device__ void ds_adjoint_fold(const DevModel &m, int d, const DsCtxT<NO
     const int tid = threadIdx.x, nth = blockDim.x;
     // ---- stage D: adjoint of the fold, gv = eff R^T gmu (column bands) --------------------
     float *gv = ws.v;   // v is dead after the fold
-    // rcol is exactly 0 past each column's band, so the loop runs the full band width with
-    // the row index clamped (no early exit) and four partial sums
+    // rcol is exactly 0 past each column's band, so the loop runs the widest band of the
+    // warp's 32 adjacent columns (nearly their own widths: the resolution changes slowly with
+    // energy) with the row index clamped (no early exit) and four partial sums
     for (int k = tid; k < N_t; k += nth) {
-        const int lo = dt.col_lo[k], cw = dt.col_w, jmax = nr - 1;
+        const int lo = dt.col_lo[k], jmax = nr - 1;
+        const int cw = __reduce_max_sync(__activemask(), dt.col_len[k]);
         const float *rc = dt.rcol + k;
         float s[4] = {0.f, 0.f, 0.f, 0.f};
         int b = 0;

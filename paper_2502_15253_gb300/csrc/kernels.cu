@@ -395,11 +395,11 @@ __device__ void theta_of_z(const DevModel &m, const float *z, float *pv, float *
         const float *Lt = m.blk_L + m.blk_mat_off[b] + (int64_t)n * n;   // L^T, row-major
         float s[4] = {0.f, 0.f, 0.f, 0.f};
         int j = 0;
-        if (first >= 0) {   // consecutive indices: z read directly, eight loads in flight
+        if (first >= 0) {   // consecutive indices: z read directly, sixteen loads in flight
             const float *zb = z + first;
-            for (; j + 7 <= i; j += 8) {
+            for (; j + 15 <= i; j += 16) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) s[q & 3] = fmaf(Lt[(int64_t)(j + q) * n + i], zb[j + q], s[q & 3]);
+                for (int q = 0; q < 16; ++q) s[q & 3] = fmaf(Lt[(int64_t)(j + q) * n + i], zb[j + q], s[q & 3]);
             }
             for (; j <= i; ++j) s[0] = fmaf(Lt[(int64_t)j * n + i], zb[j], s[0]);
         } else {
@@ -438,11 +438,11 @@ __device__ double eval_z_prior(const DevModel &m, const float *z, const float *g
         const float *L = m.blk_L + m.blk_mat_off[b];   // L, row-major: (L^T g)_j = sum_i L_ij g_i
         float s[4] = {0.f, 0.f, 0.f, 0.f};
         int i = j;
-        if (first >= 0) {   // consecutive indices: gth read directly, eight loads in flight
+        if (first >= 0) {   // consecutive indices: gth read directly, sixteen loads in flight
             const float *gb = gth + first;
-            for (; i + 7 < n; i += 8) {
+            for (; i + 15 < n; i += 16) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) s[q & 3] = fmaf(L[(int64_t)(i + q) * n + j], gb[i + q], s[q & 3]);
+                for (int q = 0; q < 16; ++q) s[q & 3] = fmaf(L[(int64_t)(i + q) * n + j], gb[i + q], s[q & 3]);
             }
             for (; i < n; ++i) s[0] = fmaf(L[(int64_t)i * n + j], gb[i], s[0]);
         } else {
