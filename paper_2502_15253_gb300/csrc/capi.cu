@@ -173,6 +173,8 @@ struct fit_model {
     // Fisher preconditioner (built on first use): device matrices T, T^T, T^-1, state
     float *pre = nullptr;
     int pre_state = 0;     // 0 not built, 1 built, -1 failed (fits run unpreconditioned)
+    std::vector<double> pre_U;                   // J^T diag(mu0)^(-1/2), P x D (host)
+    std::vector<fitcore::PreEntry> pre_masks;    // preconditioners of dataset subsets
     std::vector<std::string> names;   // parameter names (models created from a configuration)
     std::vector<double> sigma;        // prior width per parameter (block members: sqrt(V_ii))
     int device = -1;                  // the CUDA device holding the model's memory
@@ -226,6 +228,8 @@ void fit_model_destroy(fit_model *model) {
     if (model->dev) cudaFree(model->dev);
     if (model->arena) cudaFree(model->arena);
     if (model->pre) cudaFree(model->pre);
+    for (auto &pm : model->pre_masks)
+        if (pm.Q) cudaFree(const_cast<float *>(pm.Q));
     delete model;
 }
 
@@ -1544,7 +1548,7 @@ void jacobi_eigen(int n, std::vector<double> &A, std::vector<double> &lam, std::
 }
 
 // Fisher preconditioner of the whitened coordinates z (not in the paper). The expected Hessian
-// of -2lnL at theta0 over all datasets is H0 = 2 (I + U U^T), U = J^T diag(mu0)^(-1/2) with
+// of -2lnL at theta0 over the fitted datasets is H0 = 2 (I + U U^T), U = J^T diag(mu0)^(-1/2) with
 // J = d mu / d z (central differences, step 0.01 in z, of the device expectation). Its few
 // large eigen-directions (the data constrain ~10-40 combinations; the whitened prior gives 2 I
 // elsewhere) are found by subspace iteration on U U^T with a Rayleigh-Ritz step: U U^T ~
@@ -1553,12 +1557,15 @@ void jacobi_eigen(int n, std::vector<double> &A, std::vector<double> &lam, std::
 // where the expected Hessian is 2 I along Q and unchanged elsewhere; T is symmetric (the
 // gradient maps with the same product) and T^-1 = I + Q diag(c') Q^T, c'_k = (1 + lam_k)^(1/2) - 1.
 // Device storage: Q^T as r rows of P floats on the vector pitch, then c and c'. A model whose
-// expectation fails keeps pre_state = -1 and fits unpreconditioned.
-int build_preconditioner(fit_model *M, cudaStream_t s) {
-    if (M->pre_state != 0) return FIT_OK;
-    M->pre_state = -1;
-    const int P = M->n_params, D = M->n_data, Pp = fitcore::fit_vec_pitch(P);
-    const int r = std::min(fitcore::kMaxPreRank, std::min(D, P));
+// expectation fails keeps pre_state = -1 and fits unpreconditioned. The model's own
+// preconditioner covers all its datasets; an instance fitting a subset of them (a dataset
+// mask) gets the one of that subset, built from the same J on first use: the expected
+// Hessian of data it does not fit would stretch its coordinates in the wrong directions.
+// U = J^T diag(mu0)^(-1/2) [P x D] of the model (cached on the host); false if an expectation
+// near the nominal point failed.
+bool fisher_U(fit_model *M, cudaStream_t s) {
+    if (!M->pre_U.empty()) return true;
+    const int P = M->n_params, D = M->n_data;
     const double hz = 1e-2;
     const int R = 2 * P + 1;
     std::vector<double> th((size_t)R * P), z(P, 0.0);
@@ -1569,10 +1576,9 @@ int build_preconditioner(fit_model *M, cudaStream_t s) {
     }
     std::vector<float> mu((size_t)R * D);
     std::vector<int> st(R, 0);
-    if (fit_model_expected(M, R, th.data(), mu.data(), st.data(), s) != FIT_OK) return FIT_OK;
+    if (fit_model_expected(M, R, th.data(), mu.data(), st.data(), s) != FIT_OK) return false;
     for (int q = 0; q < R; ++q)
-        if (st[q] != 0) return FIT_OK;
-    // U [P x D]
+        if (st[q] != 0) return false;
     std::vector<double> U((size_t)P * D, 0.0);
     for (int j = 0; j < D; ++j) {
         const double m0 = mu[j];
@@ -1581,6 +1587,21 @@ int build_preconditioner(fit_model *M, cudaStream_t s) {
         for (int i = 0; i < P; ++i)
             U[(size_t)i * D + j] = ((double)mu[(size_t)(2 * i + 1) * D + j] - (double)mu[(size_t)(2 * i + 2) * D + j]) * w;
     }
+    M->pre_U.swap(U);
+    return true;
+}
+
+// Preconditioner of the datasets selected by `mask` (the expected Hessian of the data an
+// instance actually fits): U restricted to those datasets' bins, its leading eigen-directions,
+// device buffer [Q^T rows | c | c']. Returns nullptr on failure.
+float *build_pre_buffer(fit_model *M, uint32_t mask, int &r_out) {
+    const int P = M->n_params, D = M->n_data, Pp = fitcore::fit_vec_pitch(P);
+    const int r = std::min(fitcore::kMaxPreRank, std::min(D, P));
+    std::vector<char> keep(D, 0);
+    for (int d = 0; d < M->host.n_ds; ++d)
+        if ((mask >> d) & 1u)
+            for (int j = 0; j < M->host.ds[d].n_reco; ++j) keep[M->host.ds[d].data_off + j] = 1;
+    const std::vector<double> &U = M->pre_U;
     // subspace iteration X <- orth(U U^T X), X [P x r] (column k at X[k * P ...])
     std::vector<double> X((size_t)r * P), Y((size_t)r * P), t((size_t)D);
     uint64_t seed = 0x9e3779b97f4a7c15ull;
@@ -1588,7 +1609,7 @@ int build_preconditioner(fit_model *M, cudaStream_t s) {
         seed ^= seed << 13; seed ^= seed >> 7; seed ^= seed << 17;
         x = (double)(seed >> 11) * (1.0 / 9007199254740992.0) - 0.5;
     }
-    auto apply = [&](const double *x, double *y) {   // y = U (U^T x)
+    auto apply = [&](const double *x, double *y) {   // y = U_mask (U_mask^T x)
         for (int j = 0; j < D; ++j) t[j] = 0.0;
         for (int i = 0; i < P; ++i) {
             const double xi = x[i];
@@ -1596,6 +1617,8 @@ int build_preconditioner(fit_model *M, cudaStream_t s) {
             const double *Ui = U.data() + (size_t)i * D;
             for (int j = 0; j < D; ++j) t[j] += Ui[j] * xi;
         }
+        for (int j = 0; j < D; ++j)
+            if (!keep[j]) t[j] = 0.0;
         for (int i = 0; i < P; ++i) {
             const double *Ui = U.data() + (size_t)i * D;
             double acc = 0.0;
@@ -1652,8 +1675,20 @@ int build_preconditioner(fit_model *M, cudaStream_t s) {
         cudaMemcpy(dev, buf.data(), sizeof(float) * buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         if (dev) cudaFree(dev);
-        return FIT_OK;
+        return nullptr;
     }
+    r_out = r;
+    return dev;
+}
+
+int build_preconditioner(fit_model *M, cudaStream_t s) {
+    if (M->pre_state != 0) return FIT_OK;
+    M->pre_state = -1;
+    if (!fisher_U(M, s)) return FIT_OK;
+    const int P = M->n_params, Pp = fitcore::fit_vec_pitch(P);
+    int r = 0;
+    float *dev = build_pre_buffer(M, 0xFFFFFFFFu, r);
+    if (!dev) return FIT_OK;
     M->pre = dev;
     M->host.pre_Q = dev;
     M->host.pre_c = dev + (size_t)r * Pp;
@@ -1667,6 +1702,38 @@ int build_preconditioner(fit_model *M, cudaStream_t s) {
     }
     M->pre_state = 1;
     return FIT_OK;
+}
+
+// The preconditioner of a dataset subset (built on first use and kept with the model); the
+// all-datasets one is the model's own. Returns false if it could not be built.
+bool pre_for_mask(fit_model *M, uint32_t mask, fitcore::PreEntry &e) {
+    const uint32_t all = (1u << M->host.n_ds) - 1u;
+    mask &= all;
+    const int Pp = fitcore::fit_vec_pitch(M->n_params);
+    e.mask = mask;
+    if (mask == all) {
+        e.Q = M->host.pre_Q;
+        e.c = M->host.pre_c;
+        e.r = M->host.pre_r;
+        return M->pre_state == 1;
+    }
+    for (auto &pm : M->pre_masks)
+        if (pm.mask == mask) {
+            e = pm;
+            return e.Q != nullptr;
+        }
+    fitcore::PreEntry n{};
+    n.mask = mask;
+    int r = 0;
+    float *dev = M->pre_U.empty() ? nullptr : build_pre_buffer(M, mask, r);
+    if (dev) {
+        n.Q = dev;
+        n.c = dev + (size_t)r * Pp;
+        n.r = r;
+    }
+    M->pre_masks.push_back(n);
+    e = n;
+    return dev != nullptr;
 }
 
 }  // namespace
@@ -1774,11 +1841,35 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
     };
     // the preconditioned build when asked for and every model has its preconditioner
     bool precond = o.precondition != 0;
+    std::vector<fitcore::PreEntry> pre_tab;   // [n_models x pre_k]: dataset-subset preconditioners
+    int pre_k = 0;
     if (precond) {
         std::lock_guard<std::mutex> plock(g_pre_mutex);
         for (int i = 0; i < n_models; ++i) {
             build_preconditioner(models[i], s);
             precond = precond && models[i]->pre_state == 1;
+        }
+        if (precond) {
+            // the distinct dataset subsets each model's instances fit (up to 8 per model; an
+            // instance whose subset has no entry uses the all-datasets preconditioner)
+            constexpr int kMaxSubsets = 8;
+            std::vector<std::vector<uint32_t>> subsets(n_models);
+            for (int i = 0; i < n_inst; ++i) {
+                const fit_model *mm = models[inst[i].model];
+                const uint32_t all = (1u << mm->host.n_ds) - 1u, mk = inst[i].mask & all;
+                auto &v = subsets[inst[i].model];
+                if (mk != all && (int)v.size() < kMaxSubsets && std::find(v.begin(), v.end(), mk) == v.end())
+                    v.push_back(mk);
+            }
+            for (auto &v : subsets) pre_k = std::max(pre_k, (int)v.size());
+            if (pre_k > 0) {
+                pre_tab.assign((size_t)n_models * pre_k, fitcore::PreEntry{});
+                for (int mi = 0; mi < n_models; ++mi)
+                    for (size_t q = 0; q < subsets[mi].size(); ++q) {
+                        fitcore::PreEntry e{};
+                        if (pre_for_mask(models[mi], subsets[mi][q], e)) pre_tab[(size_t)mi * pre_k + q] = e;
+                    }
+            }
         }
     }
     auto kernel_for = [n_osc, precond](int variant) { return fitcore::fit_kernel_func(variant, n_osc, precond); };
@@ -1846,8 +1937,11 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
         for (int i = 0; i < n_inst && !reordered; ++i) reordered = order[i] != i;
     }
+    Staged dpre;
     rc = stage_in(hm.data(), sizeof(DevModel) * n_models, s, dm);
     if (!rc && reordered) rc = stage_in(order.data(), sizeof(int) * n_inst, s, dord);
+    if (!rc && precond && pre_k > 0)
+        rc = stage_in(pre_tab.data(), sizeof(fitcore::PreEntry) * pre_tab.size(), s, dpre);
     if (!rc) rc = stage_in(inst, sizeof(fit_instance) * n_inst, s, di);
     if (!rc) rc = stage_in(data, sizeof(float) * data_len, s, dd);
     if (!rc && start) rc = stage_in(start, sizeof(double) * par_len, s, dst);
@@ -1888,6 +1982,8 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
         a.budget_ns = (uint64_t)(o.time_budget_s * 1e9);
         a.precond = precond ? 1 : 0;
         a.order = reordered ? (const int *)dord.dev : nullptr;
+        a.pre_tab = (precond && pre_k > 0) ? (const fitcore::PreEntry *)dpre.dev : nullptr;
+        a.pre_per_model = pre_k;
         if (o.use_graph) {
             rc = graph_launch(kern, grid, o.threads, smem, a, (int *)dq.dev, s);
         } else {
@@ -1922,7 +2018,7 @@ int fit_batch_ex(fit_model *const *models, int n_models, const fit_instance *ins
     }
     if (!rc && hre && cudaMemcpyAsync(results, dre.dev, sizeof(fit_result) * n_inst, cudaMemcpyDeviceToHost, s))
         rc = fail(FIT_ERR_CUDA, "fit_batch: copy back");
-    for (Staged *b : {&dm, &di, &dd, &dst, &dfx, &dbe, &dre, &dws, &dq, &dord}) release(*b, s);
+    for (Staged *b : {&dm, &di, &dd, &dst, &dfx, &dbe, &dre, &dws, &dq, &dord, &dpre}) release(*b, s);
     // the staged model table and instance table are host vectors: finish before they go away
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_batch: synchronise");
     return rc;

@@ -949,6 +949,20 @@ __global__ void __launch_bounds__(128, MINB) fit_kernel(FitArgs A) {
         const int ii = A.order ? A.order[q] : q;   // queue position -> instance
         const fit_instance in = A.inst[ii];
         copy_model(&S.m, A.models + in.model);
+        if (PRE && A.pre_tab) {   // the preconditioner of the datasets this instance fits
+            if (tid == 0) {
+                const uint32_t mk = in.mask & ((1u << S.m.n_ds) - 1u);
+                const PreEntry *e = A.pre_tab + (int64_t)in.model * A.pre_per_model;
+                for (int k = 0; k < A.pre_per_model; ++k)
+                    if (e[k].Q && e[k].mask == mk) {
+                        S.m.pre_Q = e[k].Q;
+                        S.m.pre_c = e[k].c;
+                        S.m.pre_r = e[k].r;
+                        break;
+                    }
+            }
+            __syncthreads();
+        }
         const DevModel &m = S.m;
         const int P = m.P;
         // workspace: the 12 working vectors and the evaluation workspace in shared memory when

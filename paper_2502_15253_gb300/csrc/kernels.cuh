@@ -4,6 +4,13 @@
 
 namespace fitcore {
 
+// Fisher preconditioner of one dataset subset of a model (see the model's pre_Q / pre_c)
+struct PreEntry {
+    uint32_t mask;               // the datasets it covers
+    int r;
+    const float *Q, *c;          // Q^T rows on the vector pitch; c then the coefficients of T^-1
+};
+
 struct FitArgs {
     const DevModel *models;      // device array, one per model
     const fit_instance *inst;    // device [n_inst]
@@ -28,6 +35,8 @@ struct FitArgs {
     int precond;                 // 1: fit in the models' preconditioned coordinates (if built)
     const int *order;            // device [n_inst] or nullptr: the instance taken at each queue
                                  // position (costliest first, so no long fit starts last)
+    const PreEntry *pre_tab;     // device [n_models x pre_per_model] or nullptr: preconditioners
+    int pre_per_model;           // of the dataset subsets the instances fit
 };
 
 __global__ void eval_kernel(const DevModel *gm, int B, const double *theta, const float *data,
