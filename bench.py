@@ -520,13 +520,20 @@ def warm_start_measurement(args, w, data_d, cold_res, cold_best, opts, stream, f
     predict()
     fitcore.fit_batch(w.models, w.inst, data_d, starts, best_w, res_w, opts, stream)  # warm-up
     torch.cuda.synchronize()
-    flush.fill_(0.25)
-    ev0.record(stream)
-    predict()
-    fitcore.fit_batch(w.models, w.inst, data_d, starts, best_w, res_w, opts, stream)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    warm_ms = max_over_ranks(ev0.elapsed_time(ev1), pg)
+    ev2 = torch.cuda.Event(enable_timing=True)
+    tot, fit_only = [], []
+    for r in range(3):   # inference + fits, and the fits alone, over three steps
+        flush.fill_(0.25 + r)
+        ev0.record(stream)
+        predict()
+        ev2.record(stream)
+        fitcore.fit_batch(w.models, w.inst, data_d, starts, best_w, res_w, opts, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        tot.append(ev0.elapsed_time(ev1))
+        fit_only.append(ev2.elapsed_time(ev1))
+    warm_ms = max_over_ranks(float(np.mean(tot)), pg)
+    warm_fit_ms = max_over_ranks(float(np.mean(fit_only)), pg)
     rw = np.frombuffer(res_w.cpu().numpy().tobytes(), dtype=fitcore.RESULT_DTYPE)
     same = np.abs(rw["nll_min"] - cold_res["nll_min"]) <= 1e-3
     st_h = starts.cpu().numpy()
@@ -582,6 +589,8 @@ def warm_start_measurement(args, w, data_d, cold_res, cold_best, opts, stream, f
                                  "bound": "tensor", "kernel": "tc_gemm_kernel<TF32>"},
         "fits_per_s_warm": world * B / (warm_ms / 1e3),
         "warm_ms_incl_inference": warm_ms,
+        "fits_per_s_warm_fits_alone": world * B / (warm_fit_ms / 1e3),
+        "inference_ms": warm_ms - warm_fit_ms,
         "iters_per_fit_warm": float(rw["iters"].mean()),
         "iters_per_fit_cold": float(cold_res["iters"].mean()),
         "same_minimum_as_cold_frac": float(same.mean()),
