@@ -996,8 +996,27 @@ void theta_of_z_host(const fit_model *M, const double *z, double *th);
 // constrained coordinates, the step from a drawn point z_t is (J^T W J + Lambda)^-1 (J^T W
 // (n - mu_t) - Lambda z_t). Row p of that inverse (p = target t's parameter) gives K1[v][t] =
 // (A^-1 J^T W)_p [D], K2[v][t] = (A^-1 Lambda)_p [P] and zf[v][t] = zscale_p / scale_t.
+// Refresh of the mass-splitting columns (free survival parameters whose Jacobian turns with the
+// oscillation phase): with J_o taken at each drawn point instead of the nominal one, the step
+// splits by the Schur complement of the fixed block n = (all other parameters) of
+// A = J^T W J + Lambda: with N = A_nn,
+//   S = J_o^T Gp J_o + Lambda_o,  Gp = W - W J_n N^-1 J_n^T W   (symmetric, D x D)
+//   delta_o = S^-1 (J_o^T (Gp r + H z_n) - Lambda_o z_o),  H = W J_n N^-1 Lambda_n (D x P_n)
+//   delta_n = N^-1 J_n^T W (r - J_o delta_o) - N^-1 Lambda_n z_n   (rows of the targets only)
+// Per variant: Gp [D x D], H^T [P_n x D], R1 = (N^-1 J_n^T W)_T [T_n x D], R2 = (N^-1 Lambda_n)_T
+// [T_n x P_n]; per target t: tkind[t] = q >= 0 (the q-th refreshed column) or -1 - row.
+struct WsRefresh {
+    int k = 0;                         // refreshed columns (0: none)
+    std::vector<int> o_param, n_param; // parameter indices of the two blocks
+    std::vector<int> tkind;            // per target
+    std::vector<float> lam_o;          // Lambda of the refreshed coordinates
+    std::vector<float> buf;            // per variant: Gp | H^T | R1 | R2
+    size_t var_floats = 0;
+    int n_rows = 0;                    // T_n
+};
+
 int linear_mle_rows(fit_model *M, const fit_warmstart_geom &G, cudaStream_t s, std::vector<float> &K1,
-                    std::vector<float> &K2, std::vector<float> &zf, int &n_var) {
+                    std::vector<float> &K2, std::vector<float> &zf, int &n_var, WsRefresh *ref = nullptr) {
     const int P = M->n_params, D = M->n_data, nt = G.n_targets;
     const double hz = 1e-2;
     const int R = 2 * P + 1;
@@ -1025,6 +1044,32 @@ int linear_mle_rows(fit_model *M, const fit_warmstart_geom &G, cudaStream_t s, s
     K2.assign((size_t)n_var * nt * P, 0.f);
     zf.assign((size_t)n_var * nt, 0.f);
     std::vector<double> w(D), A((size_t)P * P), L, x(P), y(P);
+    if (ref) {
+        *ref = WsRefresh();
+        std::vector<char> is_o(P, 0);
+        for (int i = 0; i < M->host.n_osc; ++i) {
+            const int p = M->host.osc_idx[i];
+            if (p >= 0 && fitcore::osc_is_dm(M->host.osc_mode, i) && !M->in_block[p] && !is_o[p]) {
+                is_o[p] = 1;
+                ref->o_param.push_back(p);
+            }
+        }
+        for (int i = 0; i < P; ++i)
+            if (!is_o[i]) ref->n_param.push_back(i);
+        ref->k = (int)ref->o_param.size();
+        for (int t = 0; t < nt; ++t) {
+            const int p = G.target_idx[t];
+            int q = -1;
+            for (int a = 0; a < ref->k; ++a)
+                if (ref->o_param[a] == p) q = a;
+            ref->tkind.push_back(q >= 0 ? q : -1 - ref->n_rows);
+            if (q < 0) ref->n_rows++;
+        }
+        for (int a = 0; a < ref->k; ++a) ref->lam_o.push_back((float)con[ref->o_param[a]]);
+        const size_t Pn = ref->n_param.size();
+        ref->var_floats = (size_t)D * D + Pn * D + (size_t)ref->n_rows * D + (size_t)ref->n_rows * Pn;
+        if (ref->k > 0) ref->buf.assign(ref->var_floats * n_var, 0.f);
+    }
     for (int v = 0; v < n_var; ++v) {
         const uint32_t mask = G.n_masks > 0 ? G.masks[v] : 0xFFFFFFFFu;
         std::fill(w.begin(), w.end(), 0.0);
@@ -1080,6 +1125,69 @@ int linear_mle_rows(fit_model *M, const fit_warmstart_geom &G, cudaStream_t s, s
             for (int i = 0; i < P; ++i) k2[i] = (float)(x[i] * con[i]);
             zf[(size_t)v * nt + t] = (float)(M->zscale[p] / G.target_scale[t]);
         }
+        if (ref && ref->k > 0) {
+            // N = A_nn (A holds both triangles), its Cholesky factor and inverse
+            const std::vector<int> &nx = ref->n_param;
+            const int Pn = (int)nx.size();
+            std::vector<double> Nm((size_t)Pn * Pn), Ln, Ni((size_t)Pn * Pn, 0.0), col(Pn), tmp(Pn);
+            for (int a = 0; a < Pn; ++a)
+                for (int b = 0; b < Pn; ++b) Nm[(size_t)a * Pn + b] = A[(size_t)nx[a] * P + nx[b]];
+            if (!cholesky_lower(Pn, Nm.data(), Ln))
+                return fail(FIT_ERR_INVALID_CONFIG, "warm start: nuisance block not positive definite");
+            for (int c = 0; c < Pn; ++c) {   // column c of N^-1
+                for (int i = 0; i < Pn; ++i) {
+                    double acc = (i == c) ? 1.0 : 0.0;
+                    for (int k2i = 0; k2i < i; ++k2i) acc -= Ln[(size_t)i * Pn + k2i] * tmp[k2i];
+                    tmp[i] = acc / Ln[(size_t)i * Pn + i];
+                }
+                for (int i = Pn - 1; i >= 0; --i) {
+                    double acc = tmp[i];
+                    for (int k2i = i + 1; k2i < Pn; ++k2i) acc -= Ln[(size_t)k2i * Pn + i] * col[k2i];
+                    col[i] = acc / Ln[(size_t)i * Pn + i];
+                }
+                for (int i = 0; i < Pn; ++i) Ni[(size_t)i * Pn + c] = col[i];
+            }
+            // X = N^-1 J_n^T W [Pn x D]
+            std::vector<double> X((size_t)Pn * D, 0.0);
+            for (int a = 0; a < Pn; ++a)
+                for (int j = 0; j < D; ++j) {
+                    if (w[j] == 0.0) continue;
+                    double acc = 0.0;
+                    for (int b = 0; b < Pn; ++b) acc += Ni[(size_t)a * Pn + b] * J[(size_t)j * P + nx[b]];
+                    X[(size_t)a * D + j] = acc * w[j];
+                }
+            float *base = ref->buf.data() + (size_t)v * ref->var_floats;
+            float *Gp = base, *Ht = Gp + (size_t)D * D, *R1 = Ht + (size_t)Pn * D, *R2 = R1 + (size_t)ref->n_rows * D;
+            // Gp = W - W J_n X (symmetric)
+            for (int i = 0; i < D; ++i)
+                for (int j = 0; j < D; ++j) {
+                    double acc = 0.0;
+                    if (w[i] != 0.0)
+                        for (int a = 0; a < Pn; ++a) acc += J[(size_t)i * P + nx[a]] * X[(size_t)a * D + j];
+                    Gp[(size_t)i * D + j] = (float)((i == j ? w[i] : 0.0) - w[i] * acc);
+                }
+            // H^T [Pn x D]: H = W J_n N^-1 Lambda_n
+            for (int c = 0; c < Pn; ++c) {
+                const double lc = con[nx[c]];
+                for (int j = 0; j < D; ++j) {
+                    double acc = 0.0;
+                    if (lc != 0.0 && w[j] != 0.0)
+                        for (int a = 0; a < Pn; ++a) acc += J[(size_t)j * P + nx[a]] * Ni[(size_t)a * Pn + c];
+                    Ht[(size_t)c * D + j] = (float)(w[j] * acc * lc);
+                }
+            }
+            // target rows of the n block
+            int row = 0;
+            for (int t = 0; t < nt; ++t) {
+                if (ref->tkind[t] >= 0) continue;
+                int a = -1;
+                for (int q = 0; q < Pn; ++q)
+                    if (nx[q] == G.target_idx[t]) a = q;
+                for (int j = 0; j < D; ++j) R1[(size_t)row * D + j] = (float)X[(size_t)a * D + j];
+                for (int c = 0; c < Pn; ++c) R2[(size_t)row * Pn + c] = (float)(Ni[(size_t)a * Pn + c] * con[nx[c]]);
+                ++row;
+            }
+        }
     }
     return FIT_OK;
 }
@@ -1124,12 +1232,42 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
     // to first order, rather than the drawn point)
     float *zbuf = nullptr, *krows[16] = {nullptr};
     int n_var[16] = {0};
+    // the refreshed mass-splitting columns: device tables per geometry
+    WsRefresh refs[16];
+    float *rbuf[16] = {nullptr}, *rlam[16] = {nullptr};
+    int *rint[16] = {nullptr};   // o_param | n_param | tkind
+    double *thp = nullptr;
+    float *mup = nullptr;
+    int *stp = nullptr;
+    int max_k = 0;
     if (!rc && cudaMallocAsync(&zbuf, sizeof(float) * (size_t)batch * max_p, s) != cudaSuccess)
         rc = fail(FIT_ERR_OOM, "fit_warmstart_train: workspace");
     for (int g = 0; g < n_geoms && !rc; ++g) {
         std::vector<float> K1, K2, zf;
-        rc = linear_mle_rows(models[g], geoms[g], s, K1, K2, zf, n_var[g]);
+        rc = linear_mle_rows(models[g], geoms[g], s, K1, K2, zf, n_var[g], &refs[g]);
         if (rc) break;
+        WsRefresh &R = refs[g];
+        if (R.k > 3) R.k = 0;   // more than three mass splittings: the nominal-point rows only
+        if (R.k > 0) {
+            max_k = std::max(max_k, R.k);
+            std::vector<int> ints;
+            ints.insert(ints.end(), R.o_param.begin(), R.o_param.end());
+            ints.insert(ints.end(), R.n_param.begin(), R.n_param.end());
+            ints.insert(ints.end(), R.tkind.begin(), R.tkind.end());
+            if (cudaMallocAsync(&rbuf[g], sizeof(float) * R.buf.size(), s) != cudaSuccess ||
+                cudaMallocAsync(&rlam[g], sizeof(float) * R.lam_o.size(), s) != cudaSuccess ||
+                cudaMallocAsync(&rint[g], sizeof(int) * ints.size(), s) != cudaSuccess) {
+                rc = fail(FIT_ERR_OOM, "fit_warmstart_train: workspace");
+                break;
+            }
+            if (cudaMemcpyAsync(rbuf[g], R.buf.data(), sizeof(float) * R.buf.size(), cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(rlam[g], R.lam_o.data(), sizeof(float) * R.lam_o.size(), cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(rint[g], ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice, s) ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: upload");
+                break;
+            }
+        }
         const size_t n = K1.size() + K2.size() + zf.size();
         if (cudaMallocAsync(&krows[g], sizeof(float) * n, s) != cudaSuccess) {
             rc = fail(FIT_ERR_OOM, "fit_warmstart_train: workspace");
@@ -1144,6 +1282,11 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
             cudaStreamSynchronize(s) != cudaSuccess)
             rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: upload");
     }
+    if (!rc && max_k > 0 &&
+        (cudaMallocAsync(&thp, sizeof(double) * (size_t)batch * 2 * max_k * max_p, s) != cudaSuccess ||
+         cudaMallocAsync(&mup, sizeof(float) * (size_t)batch * 2 * max_k * max_d, s) != cudaSuccess ||
+         cudaMallocAsync(&stp, sizeof(int) * (size_t)batch * 2 * max_k, s) != cudaSuccess))
+        rc = fail(FIT_ERR_OOM, "fit_warmstart_train: workspace");
     float *x = rc ? nullptr : fitcore::mlp_input_buffer(mlp, batch);
     if (!rc && !x) rc = fail(FIT_ERR_OOM, "fit_warmstart_train: input buffer");
     for (int step = 0; step < n_steps && !rc; ++step) {
@@ -1163,8 +1306,22 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
         if (!rc) {
             const int P = m->n_params, D = m->n_data, nt = G.n_targets, nv = n_var[g];
             const float *K1 = krows[g], *K2 = K1 + (size_t)nv * nt * D, *zf = K2 + (size_t)nv * nt * P;
-            rc = fitcore::mle_targets(batch, P, D, theta, m->host.theta0, zbuf, cnt, mu, nt, gd[g].tidx, gd[g].tscale,
-                                      K1, K2, zf, nv, gd[g].choices, masks, n_out, status, y, s);
+            const WsRefresh &R = refs[g];
+            if (R.k > 0) {
+                // the mass-splitting columns of J at each drawn point (split-TF32 expectations)
+                const double hz = 1e-2;
+                const int Pn = (int)R.n_param.size();
+                rc = fitcore::perturb_theta(batch, P, R.k, theta, rint[g], m->host.zscale, hz, thp, s);
+                if (!rc) rc = fitcore::expected_tc(m->host, m->dev, batch * 2 * R.k, thp, mup, stp, 1, s);
+                if (!rc)
+                    rc = fitcore::refresh_targets(batch, P, D, R.k, Pn, R.n_rows, theta, m->host.theta0, zbuf, cnt, mu,
+                                                  mup, stp, rint[g], rint[g] + R.k, rint[g] + R.k + Pn, rlam[g],
+                                                  rbuf[g], (int64_t)R.var_floats, hz, nt, gd[g].tidx, gd[g].tscale, zf,
+                                                  nv, gd[g].choices, masks, n_out, status, y, s);
+            } else {
+                rc = fitcore::mle_targets(batch, P, D, theta, m->host.theta0, zbuf, cnt, mu, nt, gd[g].tidx,
+                                          gd[g].tscale, K1, K2, zf, nv, gd[g].choices, masks, n_out, status, y, s);
+            }
         }
         if (!rc) rc = fit_mlp_train_step(mlp, batch, x, y, lr_s, weight_decay, loss + step, stream);
     }
@@ -1173,8 +1330,11 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
         rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: losses");
     for (int g = 0; g < n_geoms; ++g) {
         free_geom(gd[g], s);
-        if (krows[g]) cudaFreeAsync(krows[g], s);
+        for (void *p : {(void *)krows[g], (void *)rbuf[g], (void *)rlam[g], (void *)rint[g]})
+            if (p) cudaFreeAsync(p, s);
     }
+    for (void *p : {(void *)thp, (void *)mup, (void *)stp})
+        if (p) cudaFreeAsync(p, s);
     for (void *p : {(void *)theta, (void *)mu, (void *)cnt, (void *)y, (void *)masks, (void *)status, (void *)loss,
                     (void *)zbuf})
         if (p) cudaFreeAsync(p, s);

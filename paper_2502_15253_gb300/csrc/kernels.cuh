@@ -117,6 +117,14 @@ int draw_theta(const DevModel &h, const DevModel *dev, int B, uint64_t seed, uin
                uint32_t *masks, cudaStream_t s, float *z_out = nullptr);
 int targets(int B, int P, const double *theta, const double *theta0, int n_t, const int *idx, const double *scale,
             int n_out, const int *status, float *y, cudaStream_t s);
+int perturb_theta(int B, int P, int k, const double *theta, const int *o_param, const float *zscale, double hz,
+                  double *out, cudaStream_t s);
+int refresh_targets(int B, int P, int D, int k, int Pn, int n_rows, const double *theta, const double *theta0,
+                    const float *z, const float *cnt, const float *mu, const float *mup, const int *st_p,
+                    const int *o_param, const int *n_param, const int *tkind, const float *lam_o, const float *bufs,
+                    int64_t var_floats, double hz, int n_t, const int *idx, const double *scale, const float *zf,
+                    int n_var, const uint32_t *choices, const uint32_t *masks, int n_out, const int *status, float *y,
+                    cudaStream_t s);
 int mle_targets(int B, int P, int D, const double *theta, const double *theta0, const float *z, const float *cnt,
                 const float *mu, int n_t, const int *idx, const double *scale, const float *K1, const float *K2,
                 const float *zf, int n_var, const uint32_t *choices, const uint32_t *masks, int n_out,

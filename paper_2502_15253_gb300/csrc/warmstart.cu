@@ -175,4 +175,195 @@ int mle_targets(int B, int P, int D, const double *theta, const double *theta0, 
     return FIT_OK;
 }
 
+namespace {
+
+// theta of the 2k perturbed points of each sample: row b 2k + 2q + s is theta_b with parameter
+// o_param[q] moved by +h_q (s = 0) or -h_q (s = 1), h_q = hz zscale (a step of hz in z)
+__global__ void perturb_kernel(int B, int P, int k, const double *__restrict__ theta, const int *__restrict__ o_param,
+                               const float *__restrict__ zscale, double hz, double *__restrict__ out) {
+    const int64_t total = (int64_t)B * 2 * k * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / P;
+        const int i = (int)(e % P), b = (int)(row / (2 * k)), qs = (int)(row % (2 * k)), q = qs / 2;
+        double v = theta[(int64_t)b * P + i];
+        if (i == o_param[q]) v += (qs & 1 ? -hz : hz) * (double)zscale[i];
+        out[e] = v;
+    }
+}
+
+constexpr int kRefMaxK = 3;      // refreshed columns (mass splittings) at most
+
+// Targets at the refreshed linearised best fit (see linear_mle_rows): one block per sample.
+// Shared memory: r, J_o (k rows), y, Gp J_o (k rows) over the D bins, z_n over P_n.
+__global__ void __launch_bounds__(256) refresh_targets_kernel(
+    int B, int P, int D, int k, int Pn, int n_rows, const double *__restrict__ theta,
+    const double *__restrict__ theta0, const float *__restrict__ z, const float *__restrict__ cnt,
+    const float *__restrict__ mu, const float *__restrict__ mup, const int *__restrict__ st_p,
+    const int *__restrict__ o_param, const int *__restrict__ n_param, const int *__restrict__ tkind,
+    const float *__restrict__ lam_o, const float *__restrict__ bufs, int64_t var_floats, float inv2hz, int n_t,
+    const int *__restrict__ idx, const double *__restrict__ scale, const float *__restrict__ zf, int n_var,
+    const uint32_t *__restrict__ choices, const uint32_t *__restrict__ masks, int n_out,
+    const int *__restrict__ status, float *__restrict__ y) {
+    extern __shared__ float sh[];
+    float *r = sh, *Jo = r + D, *yv = Jo + k * D, *GJ = yv + D, *zn = GJ + k * D;
+    __shared__ float red[8][kRefMaxK * kRefMaxK + kRefMaxK];
+    __shared__ float dlt[kRefMaxK];
+    __shared__ int bad;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        int st = status ? status[b] : 0;
+        for (int q = 0; q < 2 * k; ++q) st |= st_p[(int64_t)b * 2 * k + q];
+        bad = st;
+    }
+    __syncthreads();
+    if (bad) {
+        for (int t = tid; t < n_out; t += blockDim.x) y[(int64_t)b * n_out + t] = 0.f;
+        return;
+    }
+    int var = 0;
+    if (n_var > 1 && masks)
+        for (int q = 0; q < n_var; ++q)
+            if (choices[q] == masks[b]) var = q;
+    const float *Gp = bufs + (int64_t)var * var_floats, *Ht = Gp + (int64_t)D * D, *R1 = Ht + (int64_t)Pn * D,
+                *R2 = R1 + (int64_t)n_rows * D;
+    const float *zb = z + (int64_t)b * P;
+    for (int j = tid; j < D; j += blockDim.x) {
+        r[j] = cnt[(int64_t)b * D + j] - mu[(int64_t)b * D + j];
+        for (int q = 0; q < k; ++q)
+            Jo[q * D + j] = (mup[((int64_t)b * 2 * k + 2 * q) * D + j] - mup[((int64_t)b * 2 * k + 2 * q + 1) * D + j]) *
+                            inv2hz;
+    }
+    for (int c = tid; c < Pn; c += blockDim.x) zn[c] = zb[n_param[c]];
+    __syncthreads();
+    // y = Gp r + H z_n and Gp J_o (Gp symmetric: column j read across the threads)
+    for (int j = tid; j < D; j += blockDim.x) {
+        float u = 0.f, g[kRefMaxK] = {0.f, 0.f, 0.f};
+        for (int i = 0; i < D; ++i) {
+            const float gij = Gp[(int64_t)i * D + j];
+            u = fmaf(gij, r[i], u);
+#pragma unroll
+            for (int q = 0; q < kRefMaxK; ++q)
+                if (q < k) g[q] = fmaf(gij, Jo[q * D + i], g[q]);
+        }
+        for (int c = 0; c < Pn; ++c) u = fmaf(Ht[(int64_t)c * D + j], zn[c], u);
+        yv[j] = u;
+        for (int q = 0; q < k; ++q) GJ[q * D + j] = g[q];
+    }
+    __syncthreads();
+    // S = J_o^T Gp J_o, bv = J_o^T y (block sums)
+    float part[kRefMaxK * kRefMaxK + kRefMaxK];
+    const int ns = k * k + k;
+    for (int e = 0; e < ns; ++e) part[e] = 0.f;
+    for (int j = tid; j < D; j += blockDim.x)
+        for (int q1 = 0; q1 < k; ++q1) {
+            const float jq = Jo[q1 * D + j];
+            for (int q2 = 0; q2 < k; ++q2) part[q1 * k + q2] = fmaf(jq, GJ[q2 * D + j], part[q1 * k + q2]);
+            part[k * k + q1] = fmaf(jq, yv[j], part[k * k + q1]);
+        }
+    for (int e = 0; e < ns; ++e) {
+        float v = part[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][e] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double S[kRefMaxK][kRefMaxK], bv[kRefMaxK];
+        for (int q1 = 0; q1 < k; ++q1) {
+            for (int q2 = 0; q2 < k; ++q2) {
+                double acc = 0.0;
+                for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) acc += red[wi][q1 * k + q2];
+                S[q1][q2] = acc;
+            }
+            double acc = 0.0;
+            for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) acc += red[wi][k * k + q1];
+            S[q1][q1] += lam_o[q1];
+            bv[q1] = acc - (double)lam_o[q1] * zb[o_param[q1]];
+        }
+        // Gaussian elimination with partial pivoting (k <= 3)
+        for (int c = 0; c < k; ++c) {
+            int pv = c;
+            for (int rr = c + 1; rr < k; ++rr)
+                if (fabs(S[rr][c]) > fabs(S[pv][c])) pv = rr;
+            for (int cc = 0; cc < k; ++cc) {
+                const double t = S[c][cc];
+                S[c][cc] = S[pv][cc];
+                S[pv][cc] = t;
+            }
+            const double tb = bv[c];
+            bv[c] = bv[pv];
+            bv[pv] = tb;
+            const double piv = S[c][c];
+            for (int rr = c + 1; rr < k; ++rr) {
+                const double f = piv != 0.0 ? S[rr][c] / piv : 0.0;
+                for (int cc = c; cc < k; ++cc) S[rr][cc] -= f * S[c][cc];
+                bv[rr] -= f * bv[c];
+            }
+        }
+        for (int c = k - 1; c >= 0; --c) {
+            double acc = bv[c];
+            for (int cc = c + 1; cc < k; ++cc) acc -= S[c][cc] * (double)dlt[cc];
+            dlt[c] = S[c][c] != 0.0 ? (float)(acc / S[c][c]) : 0.f;
+        }
+    }
+    __syncthreads();
+    // targets: a warp per target
+    for (int t = warp; t < n_out; t += blockDim.x >> 5) {
+        float v = 0.f;
+        if (t < n_t) {
+            const int kind = tkind[t];
+            float d = 0.f;
+            if (kind >= 0) {
+                d = dlt[kind];
+            } else {
+                const int row = -1 - kind;
+                float acc = 0.f;
+                for (int j = lane; j < D; j += 32) {
+                    float rj = r[j];
+                    for (int q = 0; q < k; ++q) rj = fmaf(-Jo[q * D + j], dlt[q], rj);
+                    acc = fmaf(R1[(int64_t)row * D + j], rj, acc);
+                }
+                for (int c = lane; c < Pn; c += 32) acc = fmaf(-R2[(int64_t)row * Pn + c], zn[c], acc);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                d = acc;
+            }
+            const int p = idx[t];
+            v = (float)((theta[(int64_t)b * P + p] - theta0[p]) / scale[t]) + zf[var * n_t + t] * d;
+        }
+        if (lane == 0) y[(int64_t)b * n_out + t] = v;
+    }
+}
+
+}  // namespace
+
+int perturb_theta(int B, int P, int k, const double *theta, const int *o_param, const float *zscale, double hz,
+                  double *out, cudaStream_t s) {
+    const int64_t n = (int64_t)B * 2 * k * P;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+    perturb_kernel<<<grid, 256, 0, s>>>(B, P, k, theta, o_param, zscale, hz, out);
+    fitcore_count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("warm-start refresh: ") + cudaGetErrorString(e));
+    return FIT_OK;
+}
+
+int refresh_targets(int B, int P, int D, int k, int Pn, int n_rows, const double *theta, const double *theta0,
+                    const float *z, const float *cnt, const float *mu, const float *mup, const int *st_p,
+                    const int *o_param, const int *n_param, const int *tkind, const float *lam_o, const float *bufs,
+                    int64_t var_floats, double hz, int n_t, const int *idx, const double *scale, const float *zf,
+                    int n_var, const uint32_t *choices, const uint32_t *masks, int n_out, const int *status, float *y,
+                    cudaStream_t s) {
+    if (k < 1 || k > kRefMaxK) return fitcore_fail(FIT_ERR_INVALID_ARG, "warm-start refresh: 1..3 columns");
+    const size_t smem = sizeof(float) * ((size_t)(2 + 2 * k) * D + Pn);
+    if (smem > 48 * 1024) return fitcore_fail(FIT_ERR_INVALID_ARG, "warm-start refresh: model too large");
+    refresh_targets_kernel<<<B, 256, smem, s>>>(B, P, D, k, Pn, n_rows, theta, theta0, z, cnt, mu, mup, st_p, o_param,
+                                                n_param, tkind, lam_o, bufs, var_floats, (float)(0.5 / hz), n_t, idx,
+                                                scale, zf, n_var, choices, masks, n_out, status, y);
+    fitcore_count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("warm-start refresh: ") + cudaGetErrorString(e));
+    return FIT_OK;
+}
+
 }  // namespace fitcore

@@ -127,15 +127,14 @@ def test_warm_start_saves_evaluations_on_the_53km_model(c1, c2):
     sin^2 th13 and dm2_31 within +-3 sigma, Poisson counts): fits from the network's starts reach
     the cold fits' minima (within 1e-3 in -2lnL, so at the cold fits' parity with the oracle) with
     measurably fewer evaluations. The most any network of these 12 outputs can save: starts at
-    the cold fits' own values of the 12 need 30 % fewer evaluations on this model; the
-    network's targets (one Gauss-Newton step with the nominal point's Jacobian) miss the best
-    fit most in dm2_31, whose Jacobian turns with the oscillation phase."""
+    the cold fits' own values of the 12 need 30 % fewer evaluations on this model; the rest of
+    the gap is the network's own regression error (0.05-0.26 prior widths RMS per target)."""
     spec1, m1 = c1
     spec2, m2 = c2
     net = warmstart.network(seed=3)
-    # 12 epochs over the same 2M samples (about 16 s): one epoch leaves the network short of
+    # 12 epochs over the same 2M samples (about 35 s): one epoch leaves the network short of
     # the linearised best fit it is trained on (no gain), twelve bring the 53 km model's
-    # evaluations down by about 8 %
+    # evaluations down by 8-9 %
     warmstart.train(net, [m1, m2], [spec1, spec2], n_steps=488, batch=4096, lr=1e-3, epochs=12)
     B = 512
     table = synth.make_ensemble(B, {"c1": spec1, "c2": spec2}, frac_c2=1.0, base=9_000_000)
