@@ -419,8 +419,12 @@ int fit_warmstart_draw(fit_model *model, const fit_warmstart_geom *geom, int B, 
  * turn: draw theta and masks, expected spectra with the TF32 tensor-core fold, Poisson counts,
  * inputs and standardised targets, one step. The target of a sample is where a fit of its
  * counts would end, to first order: the drawn point moved by one Gauss-Newton step of -2lnL
- * with the expected Hessian at the nominal point (built once per geometry and dataset mask
- * from 2P + 1 expectations), standardised by target_scale. Learning rate lr (0.05 + 0.95 (1 +
+ * with the expected Hessian, standardised by target_scale. The Jacobian of the expectation is
+ * taken at the nominal point (built once per geometry and dataset mask from 2P + 1
+ * expectations), except the columns of the free mass splittings among the uniform parameters,
+ * which turn with the oscillation phase: those are re-evaluated at each drawn point (two
+ * expectations per column and sample) and the step is solved by the Schur complement against
+ * the block of all other parameters. Learning rate lr (0.05 + 0.95 (1 +
  * cos(pi s / n_steps)) / 2) at step s. losses_out (host or device [n_steps] double, or NULL)
  * receives each step's batch loss. Synchronous. */
 int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmstart_geom *geoms,

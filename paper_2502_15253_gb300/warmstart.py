@@ -10,7 +10,8 @@ oscillation parameters, the nine energy-scale coefficients and the far-detector 
 normalisations. The oscillation parameters of interest are drawn uniformly within +-3.5 widths
 of nominal for training, every other parameter from its prior. The network is trained to
 predict where a fit of the spectrum ends: the drawn point moved by one Gauss-Newton step of
--2lnL with the expected Hessian at the nominal point (fit_warmstart_train).
+-2lnL with the expected Hessian at the nominal point, the mass splittings' columns of the
+Jacobian taken at the drawn point (fit_warmstart_train).
 """
 from __future__ import annotations
 
