@@ -26,6 +26,12 @@ struct GemmOut {
     const float *bias = nullptr;
     const float *aux = nullptr;
     int ldaux = 0;
+    // optional transposed copy of Y (EPI_BIAS_GELU, EPI_DGELU): Yt[n * ldyt + m] = Y[m][n], so
+    // that a later product over the batch (a weight gradient) reads it K-major without a
+    // separate transpose
+    __nv_bfloat16 *Yt = nullptr;
+    int ldyt = 0;
+    int vec = 0;   // set by tc_gemm: bit 0 C, 1 Y, 2 aux, 3 Yt rows 16-byte aligned; bit 4 bias aligned
 };
 
 // Returns 0, or a negative FIT_ERR_* code (message through the library's error string).

@@ -33,39 +33,54 @@ __global__ void prep_input_kernel(int B, int n_in, int ld, const float *__restri
     }
 }
 
-// d loss / d out for the mean squared error over B x n_out; loss (double) accumulated
-__global__ void mse_kernel(int B, int n_out, int ld, const float *__restrict__ out, const float *__restrict__ tgt,
-                           __nv_bfloat16 *__restrict__ dout, double *__restrict__ loss) {
-    const int64_t total = (int64_t)B * ld;
+// d loss / d out for the mean squared error over B x n_out: a thread per sample writes its row
+// of dout (ld per row, zero padding) and its column of the transpose doutT (ldt per feature
+// row, coalesced over the samples); loss (double) accumulated, one atomic per block
+__global__ void __launch_bounds__(256) mse_kernel(int B, int n_out, int ld, const float *__restrict__ out,
+                                                  const float *__restrict__ tgt, __nv_bfloat16 *__restrict__ dout,
+                                                  int ldt, __nv_bfloat16 *__restrict__ doutT, double *__restrict__ loss) {
+    __shared__ double part[8];
     const float scale = 2.f / (float)((int64_t)B * n_out);
     double acc = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(e / ld), o = (int)(e % ld);
-        float g = 0.f;
-        if (o < n_out) {
-            const float r = out[(int64_t)b * n_out + o] - tgt[(int64_t)b * n_out + o];
-            acc += (double)r * r;
-            g = scale * r;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        for (int o = 0; o < ld; ++o) {
+            float g = 0.f;
+            if (o < n_out) {
+                const float r = out[(int64_t)b * n_out + o] - tgt[(int64_t)b * n_out + o];
+                acc += (double)r * r;
+                g = scale * r;
+                doutT[(int64_t)o * ldt + b] = __float2bfloat16(g);
+            }
+            dout[(int64_t)b * ld + o] = __float2bfloat16(g);
         }
-        dout[e] = __float2bfloat16(g);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc / (double)((int64_t)B * n_out));
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(loss, t / (double)((int64_t)B * n_out));
+    }
 }
 
-// dst[c][r] = src[r][c] for r < R, c < Cn; dst rows have ldd elements (padding rows/cols zero)
-__global__ void transpose_bf16_kernel(int R, int Cn, int lds, const __nv_bfloat16 *__restrict__ src, int ldd,
-                                      __nv_bfloat16 *__restrict__ dst) {
-    __shared__ __nv_bfloat16 tile[32][33];
-    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int r = r0 + i, c = c0 + threadIdx.x;
-        tile[i][threadIdx.x] = (r < R && c < Cn) ? src[(int64_t)r * lds + c] : __float2bfloat16(0.f);
+// Input of a training step: a0[b][i] = bf16(x[b][i]) (0 in the padding columns i >= n_in) and
+// the transpose a0t[i][b] for i < n_in; 32 x 32 tiles through shared memory so that both the
+// row-major and the transposed writes are coalesced. Block (32, 8).
+__global__ void prep_input_t_kernel(int B, int n_in, int ld, const float *__restrict__ x,
+                                    __nv_bfloat16 *__restrict__ a0, int ldt, __nv_bfloat16 *__restrict__ a0t) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int i0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int b = b0 + r, i = i0 + threadIdx.x;
+        const __nv_bfloat16 q = __float2bfloat16((b < B && i < n_in) ? x[(int64_t)b * n_in + i] : 0.f);
+        tile[r][threadIdx.x] = q;
+        if (b < B && i < ld) a0[(int64_t)b * ld + i] = q;
     }
     __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int c = c0 + i, r = r0 + threadIdx.x;
-        if (c < Cn && r < ldd) dst[(int64_t)c * ldd + r] = tile[threadIdx.x][i];
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r, b = b0 + threadIdx.x;
+        if (i < n_in && b < B) a0t[(int64_t)i * ldt + b] = tile[threadIdx.x][r];
     }
 }
 
@@ -203,7 +218,10 @@ struct fit_mlp {
     float *pre[kMaxLayers] = {nullptr};              // pre-activation of layer l (hidden layers)
     __nv_bfloat16 *dpre[kMaxLayers] = {nullptr};     // d loss / d pre of layer l (bf16)
     float *out = nullptr, *x32 = nullptr;
-    __nv_bfloat16 *tA = nullptr, *tB = nullptr;      // transposes for the weight gradients
+    // transposed copies [features x pad8(B)] for the weight gradients, written by the kernels
+    // that produce act / dpre (input preparation, forward and backward epilogues, MSE)
+    __nv_bfloat16 *actT[kMaxLayers] = {nullptr};
+    __nv_bfloat16 *dpreT[kMaxLayers] = {nullptr};
     double *loss = nullptr;
     std::vector<void *> owned;
 };
@@ -235,11 +253,15 @@ int ensure_batch(fit_mlp *m, int B) {
         if (m->act[l]) cudaFree(m->act[l]);
         if (m->pre[l]) cudaFree(m->pre[l]);
         if (m->dpre[l]) cudaFree(m->dpre[l]);
+        if (m->actT[l]) cudaFree(m->actT[l]);
+        if (m->dpreT[l]) cudaFree(m->dpreT[l]);
         m->act[l] = nullptr;
         m->pre[l] = nullptr;
         m->dpre[l] = nullptr;
+        m->actT[l] = nullptr;
+        m->dpreT[l] = nullptr;
     }
-    for (void *p : {(void *)m->out, (void *)m->x32, (void *)m->tA, (void *)m->tB})
+    for (void *p : {(void *)m->out, (void *)m->x32})
         if (p) cudaFree(p);
     int rc = FIT_OK;
     const int L = m->n_layers, Bp = pad8(B);
@@ -252,21 +274,20 @@ int ensure_batch(fit_mlp *m, int B) {
         }
         cudaMemset(*p, 0, bytes);
     };
-    int maxld = 0;
-    for (int l = 0; l <= L; ++l) maxld = std::max(maxld, m->ld[l]);
     for (int l = 0; l < L; ++l) al((void **)&m->act[l], sizeof(__nv_bfloat16) * (size_t)B * m->ld[l]);
     for (int l = 0; l < L; ++l) al((void **)&m->pre[l], sizeof(float) * (size_t)B * m->dims[l + 1]);
     for (int l = 0; l < L; ++l) al((void **)&m->dpre[l], sizeof(__nv_bfloat16) * (size_t)B * m->ld[l + 1]);
     al((void **)&m->out, sizeof(float) * (size_t)B * m->dims[L]);
     al((void **)&m->x32, sizeof(float) * (size_t)B * m->dims[0]);
-    al((void **)&m->tA, sizeof(__nv_bfloat16) * (size_t)maxld * Bp);
-    al((void **)&m->tB, sizeof(__nv_bfloat16) * (size_t)maxld * Bp);
+    for (int l = 0; l < L; ++l) al((void **)&m->actT[l], sizeof(__nv_bfloat16) * (size_t)m->dims[l] * Bp);
+    for (int l = 0; l < L; ++l) al((void **)&m->dpreT[l], sizeof(__nv_bfloat16) * (size_t)m->dims[l + 1] * Bp);
     if (rc == FIT_OK) m->cap = B;
     return rc;
 }
 
-// forward through all layers from m->act[0]; result (fp32) in m->out
-int forward(fit_mlp *m, int B, cudaStream_t s) {
+// forward through all layers from m->act[0]; result (fp32) in m->out; with `train` the hidden
+// activations are also written transposed (actT) for the weight gradients
+int forward(fit_mlp *m, int B, cudaStream_t s, bool train) {
     const int L = m->n_layers;
     for (int l = 0; l < L; ++l) {
         fitcore::GemmOut o;
@@ -276,6 +297,10 @@ int forward(fit_mlp *m, int B, cudaStream_t s) {
             o.ldc = m->dims[l + 1];
             o.Y = m->act[l + 1];
             o.ldy = m->ld[l + 1];
+            if (train) {
+                o.Yt = m->actT[l + 1];
+                o.ldyt = pad8(B);
+            }
         } else {
             o.epi = fitcore::EPI_BIAS_F32;
             o.C = m->out;
@@ -358,8 +383,10 @@ void fit_mlp_destroy(fit_mlp *m) {
         if (m->act[l]) cudaFree(m->act[l]);
         if (m->pre[l]) cudaFree(m->pre[l]);
         if (m->dpre[l]) cudaFree(m->dpre[l]);
+        if (m->actT[l]) cudaFree(m->actT[l]);
+        if (m->dpreT[l]) cudaFree(m->dpreT[l]);
     }
-    for (void *p : {(void *)m->out, (void *)m->x32, (void *)m->tA, (void *)m->tB})
+    for (void *p : {(void *)m->out, (void *)m->x32})
         if (p) cudaFree(p);
     delete m;
 }
@@ -372,7 +399,7 @@ int fit_mlp_forward(fit_mlp *m, int B, const float *x, float *y, void *stream) {
     if (rc) return rc;
     prep_input_kernel<<<grid_for((int64_t)B * m->ld[0]), 256, 0, s>>>(B, m->dims[0], m->ld[0], x, m->act[0]);
     fitcore_count_launch();
-    rc = forward(m, B, s);
+    rc = forward(m, B, s, false);
     if (rc) return rc;
     if (cudaMemcpyAsync(y, m->out, sizeof(float) * (size_t)B * m->dims[m->n_layers], cudaMemcpyDefault, s) != cudaSuccess)
         return fitcore_fail(FIT_ERR_CUDA, "fit_mlp_forward: copy out");
@@ -389,31 +416,27 @@ int fit_mlp_train_step(fit_mlp *m, int B, const float *x, const float *target, f
     int rc = ensure_batch(m, B);
     if (rc) return rc;
     const int L = m->n_layers, Bp = pad8(B);
-    prep_input_kernel<<<grid_for((int64_t)B * m->ld[0]), 256, 0, s>>>(B, m->dims[0], m->ld[0], x, m->act[0]);
+    prep_input_t_kernel<<<dim3((m->ld[0] + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s>>>(
+        B, m->dims[0], m->ld[0], x, m->act[0], Bp, m->actT[0]);
     cudaMemsetAsync(m->loss, 0, sizeof(double), s);
     fitcore_count_launch();
-    if ((rc = forward(m, B, s))) return rc;
-    mse_kernel<<<grid_for((int64_t)B * m->ld[L]), 256, 0, s>>>(B, m->dims[L], m->ld[L], m->out, target, m->dpre[L - 1],
-                                                                m->loss);
+    if ((rc = forward(m, B, s, true))) return rc;
+    mse_kernel<<<(B + 255) / 256, 256, 0, s>>>(
+        B, m->dims[L], m->ld[L], m->out, target, m->dpre[L - 1], Bp, m->dpreT[L - 1], m->loss);
     fitcore_count_launch();
     for (int l = L - 1; l >= 0; --l) {
         const int o = m->dims[l + 1], in = m->dims[l];
         cudaMemsetAsync(m->gb[l], 0, sizeof(float) * o, s);
         colsum_kernel<<<dim3((o + 63) / 64, (B + kColRows - 1) / kColRows), dim3(32, 8), 0, s>>>(B, o, m->ld[l + 1],
                                                                                                m->dpre[l], m->gb[l]);
-        // dW = dpre^T act: operands as K-major rows over the batch
-        transpose_bf16_kernel<<<dim3((o + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s>>>(B, o, m->ld[l + 1], m->dpre[l],
-                                                                                        Bp, m->tA);
-        transpose_bf16_kernel<<<dim3((in + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s>>>(B, in, m->ld[l], m->act[l], Bp,
-                                                                                         m->tB);
         fitcore_count_launch();
-        fitcore_count_launch();
-        fitcore_count_launch();
+        // dW = dpre^T act: both operands K-major over the batch, as the producing kernels
+        // wrote them (dpreT, actT)
         fitcore::GemmOut gw;
         gw.epi = fitcore::EPI_F32;
         gw.C = m->gw[l];
         gw.ldc = in;
-        if ((rc = fitcore::tc_gemm(false, o, in, B, m->tA, Bp, m->tB, Bp, gw, s, nullptr))) return rc;
+        if ((rc = fitcore::tc_gemm(false, o, in, B, m->dpreT[l], Bp, m->actT[l], Bp, gw, s, nullptr))) return rc;
         if (l > 0) {
             // d pre_{l-1} = (d pre_l W_l) * gelu'(pre_{l-1})
             fitcore::GemmOut gx;
@@ -422,6 +445,8 @@ int fit_mlp_train_step(fit_mlp *m, int B, const float *x, const float *target, f
             gx.ldy = m->ld[l];
             gx.aux = m->pre[l - 1];
             gx.ldaux = in;
+            gx.Yt = m->dpreT[l - 1];
+            gx.ldyt = Bp;
             if ((rc = fitcore::tc_gemm(false, B, in, o, m->dpre[l], m->ld[l + 1], m->wt[l], m->ld[l + 1], gx, s, nullptr)))
                 return rc;
         }

@@ -93,3 +93,57 @@ def test_split_k_padded_output(tf32, M, N, K):
     assert np.all(np.isnan(got[:, N:]))
     err = np.abs(got[:, :N] - 2 * ref) / (2 * absref + 1e-30)
     assert err.max() <= 4e-6 * np.sqrt(K / 32)
+
+
+@pytest.mark.parametrize("M,N,K", [(16384, 512, 512), (5000, 300, 712)])
+def test_bf16_gemm_many_tiles_per_cta(M, N, K):
+    """More output tiles than SMs: each persistent CTA takes several tiles in turn, alternating
+    its two tensor-memory accumulators (one drained by the epilogue while the other fills)."""
+    assert run(False, M, N, K) <= 4e-6 * np.sqrt(K / 64)
+
+
+def _gelu64(x):
+    from scipy.special import erf
+    return 0.5 * x * (1.0 + erf(x / np.sqrt(2.0)))
+
+
+def _gelu_grad64(x):
+    from scipy.special import erf
+    return 0.5 * (1.0 + erf(x / np.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / np.sqrt(2.0 * np.pi)
+
+
+@pytest.mark.parametrize("M,N,K", [(300, 208, 438), (4100, 512, 512), (77, 12, 64)])
+def test_gelu_epilogues(M, N, K):
+    """Epilogue 2 (C = D + bias, Y = bf16(gelu(C))) and epilogue 3 (Y = bf16(D gelu'(aux)))
+    against float64: C within the accumulation bound, Y within one bf16 rounding (2^-8
+    relative) of the float64 value at the kernel's own C (epilogue 2) or of the float64
+    product (epilogue 3), plus the accumulation error carried through."""
+    rng = np.random.default_rng(5)
+    lda = ((K + 7) // 8) * 8
+    dev = torch.device("cuda")
+    Ad = torch.tensor(rng.standard_normal((M, lda)).astype(np.float32), device=dev).to(torch.bfloat16)
+    Bd = torch.tensor((rng.standard_normal((N, lda)) / np.sqrt(K)).astype(np.float32), device=dev).to(torch.bfloat16)
+    Aref = Ad.float().cpu().numpy()[:, :K].astype(np.float64)
+    Bref = Bd.float().cpu().numpy()[:, :K].astype(np.float64)
+    ref = Aref @ Bref.T
+    absref = np.abs(Aref) @ np.abs(Bref).T
+    bias = torch.tensor(rng.standard_normal(N).astype(np.float32), device=dev)
+    ldy = ((N + 7) // 8) * 8
+    C = torch.full((M, N), np.nan, dtype=torch.float32, device=dev)
+    Y = torch.zeros((M, ldy), dtype=torch.bfloat16, device=dev)
+    fitcore.fit_tc_gemm(False, M, N, K, Ad, lda, Bd, lda, 2, C=C, ldc=N, Y=Y, ldy=ldy, bias=bias)
+    aux = torch.tensor(rng.standard_normal((M, N)).astype(np.float32), device=dev)
+    Y3 = torch.zeros((M, ldy), dtype=torch.bfloat16, device=dev)
+    fitcore.fit_tc_gemm(False, M, N, K, Ad, lda, Bd, lda, 3, Y=Y3, ldy=ldy, aux=aux, ldaux=N)
+    torch.cuda.synchronize()
+    assert fitcore.fit_tc_gemm_status() == 0
+    acc = 4e-6 * np.sqrt(K / 64) * absref
+    c = C.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(c - (ref + bias.cpu().numpy()[None, :])) <= acc + 1e-6)
+    y = Y.float().cpu().numpy()[:, :N].astype(np.float64)
+    g = _gelu64(c)
+    assert np.all(np.abs(y - g) <= 2.0 ** -8 * np.abs(g) + 1e-6)
+    y3 = Y3.float().cpu().numpy()[:, :N].astype(np.float64)
+    gg = _gelu_grad64(aux.cpu().numpy().astype(np.float64))
+    want = ref * gg
+    assert np.all(np.abs(y3 - want) <= 2.0 ** -8 * np.abs(want) + acc * np.abs(gg) + 1e-6)
