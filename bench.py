@@ -612,9 +612,9 @@ def read_peaks():
 # DRAM bytes (read + write) per fit of the fit kernel by workload, from ncu captures of the current
 # kernel on a smaller launch of the same workload (traffic grows with the fits)
 FIT_DRAM_BYTES_PER_FIT = {
-    "c3": {"per_fit": (59.901696e6 + 371.543040e6) / 760,
+    "c3": {"per_fit": (42.005760e6 + 331.655168e6) / 760,
            "note": "DRAM read+write bytes per fit of an ncu capture of this kernel on 760 fits of "
-                   "the same recipe (59.9 MB read, 371.5 MB written), scaled to the launch"},
+                   "the same recipe (42.0 MB read, 331.7 MB written), scaled to the launch"},
 }
 
 # DRAM bytes (read + write) per event of mc_spectrum_kernel for one parameter set, from an ncu
