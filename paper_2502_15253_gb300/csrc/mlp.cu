@@ -33,30 +33,49 @@ __global__ void prep_input_kernel(int B, int n_in, int ld, const float *__restri
     }
 }
 
-// d loss / d out for the mean squared error over B x n_out: a thread per sample writes its row
-// of dout (ld per row, zero padding) and its column of the transpose doutT (ldt per feature
-// row, coalesced over the samples); loss (double) accumulated, one atomic per block
+// d loss / d out for the mean squared error over B x n_out (n_out <= 256): a thread per sample
+// writes its row of dout (ld per row, zero padding) and its column of the transpose doutT (ldt
+// per feature row, coalesced over the samples); the output layer's bias gradient db (cleared
+// by the caller) gets the column sums of the bf16 values, and the loss (double) is
+// accumulated; one atomic per block and column / per block.
 __global__ void __launch_bounds__(256) mse_kernel(int B, int n_out, int ld, const float *__restrict__ out,
                                                   const float *__restrict__ tgt, __nv_bfloat16 *__restrict__ dout,
-                                                  int ldt, __nv_bfloat16 *__restrict__ doutT, double *__restrict__ loss) {
+                                                  int ldt, __nv_bfloat16 *__restrict__ doutT, float *__restrict__ db,
+                                                  double *__restrict__ loss) {
     __shared__ double part[8];
+    __shared__ float col[256];
+    for (int o = threadIdx.x; o < n_out; o += blockDim.x) col[o] = 0.f;
+    __syncthreads();
     const float scale = 2.f / (float)((int64_t)B * n_out);
     double acc = 0.0;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    // the loop bound is uniform over the block, so every lane takes part in the shuffles
+    for (int b0 = blockIdx.x * blockDim.x; b0 < B; b0 += gridDim.x * blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const bool valid = b < B;
         for (int o = 0; o < ld; ++o) {
-            float g = 0.f;
-            if (o < n_out) {
-                const float r = out[(int64_t)b * n_out + o] - tgt[(int64_t)b * n_out + o];
-                acc += (double)r * r;
-                g = scale * r;
-                doutT[(int64_t)o * ldt + b] = __float2bfloat16(g);
+            float q = 0.f;   // the bf16-rounded gradient (0 past B and in the padding)
+            if (valid) {
+                float g = 0.f;
+                if (o < n_out) {
+                    const float r = out[(int64_t)b * n_out + o] - tgt[(int64_t)b * n_out + o];
+                    acc += (double)r * r;
+                    g = scale * r;
+                    doutT[(int64_t)o * ldt + b] = __float2bfloat16(g);
+                }
+                const __nv_bfloat16 h = __float2bfloat16(g);
+                dout[(int64_t)b * ld + o] = h;
+                q = __bfloat162float(h);
             }
-            dout[(int64_t)b * ld + o] = __float2bfloat16(g);
+            if (o < n_out) {   // column sum: a shuffle tree, one shared atomic per warp
+                for (int k = 16; k > 0; k >>= 1) q += __shfl_xor_sync(0xffffffffu, q, k);
+                if ((threadIdx.x & 31) == 0) atomicAdd(&col[o], q);
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
     __syncthreads();
+    for (int o = threadIdx.x; o < n_out; o += blockDim.x) atomicAdd(db + o, col[o]);
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
@@ -118,28 +137,57 @@ struct AdamW {
     float lr, b1, b2, eps, wd, c1, c2;   // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
 };
 
-// AdamW on the [out x in] weights (+ bias); rewrites W (bf16, [out x ldw]) and W^T ([in x ldwt])
-__global__ void adamw_kernel(int out, int in, AdamW h, float *__restrict__ w, const float *__restrict__ g,
-                             float *__restrict__ mw, float *__restrict__ vw, float *__restrict__ bias,
-                             const float *__restrict__ gb, float *__restrict__ mb, float *__restrict__ vb,
-                             __nv_bfloat16 *__restrict__ wbf, int ldw, __nv_bfloat16 *__restrict__ wt, int ldwt) {
-    const int64_t total = (int64_t)out * in + out;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const bool is_b = e >= (int64_t)out * in;
-        float *p = is_b ? bias + (e - (int64_t)out * in) : w + e;
-        const float gr = is_b ? gb[e - (int64_t)out * in] : g[e];
-        float *m = is_b ? mb + (e - (int64_t)out * in) : mw + e;
-        float *v = is_b ? vb + (e - (int64_t)out * in) : vw + e;
-        *m = h.b1 * *m + (1.f - h.b1) * gr;
-        *v = h.b2 * *v + (1.f - h.b2) * gr * gr;
-        const float upd = (*m * h.c1) / (sqrtf(*v * h.c2) + h.eps) + (is_b ? 0.f : h.wd * *p);
-        *p -= h.lr * upd;
-        if (!is_b) {
-            const int o = (int)(e / in), i = (int)(e % in);
-            const __nv_bfloat16 q = __float2bfloat16(*p);
-            wbf[(int64_t)o * ldw + i] = q;
-            wt[(int64_t)i * ldwt + o] = q;
+// One AdamW update of parameter p with gradient gr and moments m, v (decay: weights only).
+__device__ __forceinline__ void adamw_one(const AdamW &h, float *p, float gr, float *m, float *v, bool decay) {
+    *m = h.b1 * *m + (1.f - h.b1) * gr;
+    *v = h.b2 * *v + (1.f - h.b2) * gr * gr;
+    const float upd = (*m * h.c1) / (sqrtf(*v * h.c2) + h.eps) + (decay ? h.wd * *p : 0.f);
+    *p -= h.lr * upd;
+}
+
+// Per-layer arguments of the fused AdamW launch: the [out x in] weights (W bf16 copy with rows
+// of ldw, W^T with rows of ldwt) and the bias.
+struct AdamLayer {
+    int out, in, ldw, ldwt, tiles_i, wtiles;   // wtiles = ceil(out/32) ceil(in/32) weight tiles
+    float *w, *g, *mw, *vw, *b, *gb, *mb, *vb;
+    __nv_bfloat16 *wbf, *wt;
+};
+struct AdamAll {
+    int n;
+    int first[kMaxLayers + 1];   // first block of each layer: its weight tiles, then its bias blocks
+    AdamLayer L[kMaxLayers];
+};
+
+// AdamW on every layer in one launch. A block (32 x 8 threads) updates a 32 x 32 weight tile
+// (rows of W along the lanes) and rewrites both bf16 copies, the transposed one through a
+// shared-memory tile so that its writes are coalesced too; the bias blocks update 256 biases.
+__global__ void __launch_bounds__(256) adamw_all_kernel(AdamW h, AdamAll A) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    int t = blockIdx.x, l = 0;
+    while (l + 1 < A.n && t >= A.first[l + 1]) ++l;
+    const AdamLayer &L = A.L[l];
+    t -= A.first[l];
+    if (t < L.wtiles) {
+        const int o0 = (t / L.tiles_i) * 32, i0 = (t % L.tiles_i) * 32;
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int o = o0 + r, i = i0 + threadIdx.x;
+            __nv_bfloat16 q = __float2bfloat16(0.f);
+            if (o < L.out && i < L.in) {
+                const int64_t e = (int64_t)o * L.in + i;
+                adamw_one(h, L.w + e, L.g[e], L.mw + e, L.vw + e, true);
+                q = __float2bfloat16(L.w[e]);
+                L.wbf[(int64_t)o * L.ldw + i] = q;
+            }
+            tile[r][threadIdx.x] = q;
         }
+        __syncthreads();
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int i = i0 + r, o = o0 + threadIdx.x;
+            if (i < L.in && o < L.out) L.wt[(int64_t)i * L.ldwt + o] = tile[threadIdx.x][r];
+        }
+    } else {
+        const int k = (t - L.wtiles) * 256 + threadIdx.y * 32 + threadIdx.x;
+        if (k < L.out) adamw_one(h, L.b + k, L.gb[k], L.mb + k, L.vb + k, false);
     }
 }
 
@@ -421,15 +469,19 @@ int fit_mlp_train_step(fit_mlp *m, int B, const float *x, const float *target, f
     cudaMemsetAsync(m->loss, 0, sizeof(double), s);
     fitcore_count_launch();
     if ((rc = forward(m, B, s, true))) return rc;
+    // bias gradients (column sums of the bf16 backward signals): the output layer's from the
+    // MSE kernel, the hidden layers' from colsum_kernel
+    for (int l = 0; l < L; ++l) cudaMemsetAsync(m->gb[l], 0, sizeof(float) * m->dims[l + 1], s);
     mse_kernel<<<(B + 255) / 256, 256, 0, s>>>(
-        B, m->dims[L], m->ld[L], m->out, target, m->dpre[L - 1], Bp, m->dpreT[L - 1], m->loss);
+        B, m->dims[L], m->ld[L], m->out, target, m->dpre[L - 1], Bp, m->dpreT[L - 1], m->gb[L - 1], m->loss);
     fitcore_count_launch();
     for (int l = L - 1; l >= 0; --l) {
         const int o = m->dims[l + 1], in = m->dims[l];
-        cudaMemsetAsync(m->gb[l], 0, sizeof(float) * o, s);
-        colsum_kernel<<<dim3((o + 63) / 64, (B + kColRows - 1) / kColRows), dim3(32, 8), 0, s>>>(B, o, m->ld[l + 1],
-                                                                                               m->dpre[l], m->gb[l]);
-        fitcore_count_launch();
+        if (l < L - 1) {   // bias gradient of a hidden layer (the output layer's: mse_kernel)
+            colsum_kernel<<<dim3((o + 63) / 64, (B + kColRows - 1) / kColRows), dim3(32, 8), 0, s>>>(
+                B, o, m->ld[l + 1], m->dpre[l], m->gb[l]);
+            fitcore_count_launch();
+        }
         // dW = dpre^T act: both operands K-major over the batch, as the producing kernels
         // wrote them (dpreT, actT)
         fitcore::GemmOut gw;
@@ -460,13 +512,33 @@ int fit_mlp_train_step(fit_mlp *m, int B, const float *x, const float *target, f
     h.wd = weight_decay;
     h.c1 = (float)(1.0 / (1.0 - std::pow(0.9, m->step)));
     h.c2 = (float)(1.0 / (1.0 - std::pow(0.999, m->step)));
+    AdamAll A;
+    A.n = L;
+    int nblk = 0;
     for (int l = 0; l < L; ++l) {
-        const int o = m->dims[l + 1], in = m->dims[l];
-        adamw_kernel<<<grid_for((int64_t)o * in + o), 256, 0, s>>>(o, in, h, m->w[l], m->gw[l], m->mw[l], m->vw[l], m->b[l],
-                                                                  m->gb[l], m->mb[l], m->vb[l], m->wbf[l], m->ld[l],
-                                                                  m->wt[l], m->ld[l + 1]);
-        fitcore_count_launch();
+        AdamLayer &q = A.L[l];
+        q.out = m->dims[l + 1];
+        q.in = m->dims[l];
+        q.ldw = m->ld[l];
+        q.ldwt = m->ld[l + 1];
+        q.tiles_i = (q.in + 31) / 32;
+        q.wtiles = ((q.out + 31) / 32) * q.tiles_i;
+        q.w = m->w[l];
+        q.g = m->gw[l];
+        q.mw = m->mw[l];
+        q.vw = m->vw[l];
+        q.b = m->b[l];
+        q.gb = m->gb[l];
+        q.mb = m->mb[l];
+        q.vb = m->vb[l];
+        q.wbf = m->wbf[l];
+        q.wt = m->wt[l];
+        A.first[l] = nblk;
+        nblk += q.wtiles + (q.out + 255) / 256;
     }
+    A.first[L] = nblk;
+    adamw_all_kernel<<<nblk, dim3(32, 8), 0, s>>>(h, A);
+    fitcore_count_launch();
     if (loss_out && cudaMemcpyAsync(loss_out, m->loss, sizeof(double), cudaMemcpyDefault, s) != cudaSuccess)
         return fitcore_fail(FIT_ERR_CUDA, "fit_mlp_train_step: loss");
     cudaError_t e = cudaGetLastError();
