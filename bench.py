@@ -1145,6 +1145,24 @@ def per_config_measurement(args, stream, flush, pg, world, rank):
              "iters_per_fit": float(res["iters"].mean()), "evals_per_fit": float(res["n_evals"].mean()),
              "converged_frac": float(np.mean(res["status"] == 0)),
              "eval_grad_per_s": world * B / (ems / 1e3), "eval_batch": B, "eval_ms": ems}
+        if kind == "c2":
+            # the same fits on engine 2, whose rounds fold the spectra of all active fits on the
+            # tensor cores (split-TF32 GEMMs F = V R^T, G R); minima compared with the default's
+            o2 = fitcore.fit_batch_default_opts()
+            o2.engine = 2
+            best2 = torch.zeros_like(best_d)
+            res2_d = torch.zeros_like(res_d)
+            ms2 = time_fit_steps(w, data_d, best2, res2_d, o2, stream, flush, 1, 2, pg)
+            res2 = np.frombuffer(res2_d.cpu().numpy().tobytes(), dtype=fitcore.RESULT_DTYPE)
+            r["engine2_tensor_core_fold"] = {
+                "note": "lockstep rounds over all active fits with the response fold and its adjoint as "
+                        "split-TF32 tcgen05 GEMMs (tensor pipe share of its device time in "
+                        "profiles/lockstep_tc_c2_fits.md)",
+                "fits_per_s": world * B / (ms2 / 1e3), "ms_per_step": ms2,
+                "evals_per_fit": float(res2["n_evals"].mean()),
+                "same_minimum_as_default_frac": float(np.mean(np.abs(res2["nll_min"] - res["nll_min"]) <= 1e-3)),
+                "converged_frac": float(np.mean(res2["status"] == 0))}
+            del best2, res2_d
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             n = min(PER_CONFIG_ORACLE_SAMPLE[kind], B)
             cpu = certify(cpu_baseline(w, n), w, best_d.cpu().numpy(), res["nll_min"])
