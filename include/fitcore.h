@@ -378,14 +378,34 @@ int fit_mlp_set_layer(fit_mlp *mlp, int layer, const float *w, const float *b);
  * >= 0). data device [B x n_data], x device [B x n_in]. */
 int fit_warmstart_features(const fit_model *model, int B, const float *data, const uint32_t *masks,
                            int n_in, int slot0, int onehot_slot, float *x, void *stream);
-/* Start points for fit_batch from the network: theta = theta0, then
- * theta[target_idx[t]] = theta0 + y_t * target_scale[t] for the first n_targets outputs.
- * data device [B x n_data]; masks as above; target arrays host; theta_out device [B x P].
- * Synchronous. */
+/* Start points for fit_batch: the linearised best fit of every parameter (fit_linear_start),
+ * then the network's corrections on its targets, theta[target_idx[t]] += y_t * target_scale[t]
+ * for the first n_targets outputs (the network is trained on where a fit ends minus that
+ * linearised start, see fit_warmstart_train). data device [B x n_data]; masks device [B] or
+ * NULL; target arrays host; theta_out device [B x P]. Synchronous. */
 int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const float *data,
                           const uint32_t *masks, int slot0, int onehot_slot, int n_targets,
                           const int *target_idx, const double *target_scale, double *theta_out,
                           void *stream);
+/* Linearised best fit as start points (the warm start's deterministic part; the paper fits
+ * from the nominal point). Near theta0 the expectation of Eq. 9 is mu0 + J z in the whitened
+ * coordinates z of the transformation layer, and -2lnL (Poisson deviance plus the Gaussian and
+ * covariance priors of Eq. 6, |z|^2 over the constrained coordinates) is minimised to second
+ * order, with the expected Hessian, by one Gauss-Newton (Fisher scoring) step from z = 0:
+ *   dz = (J^T W J + Lambda)^-1 J^T W (n - mu0),  W = diag(1/mu0) over the fitted datasets,
+ *   Lambda = 1 on the constrained coordinates, 0 on the free ones;  theta = theta(dz).
+ * Linear parameters (normalisations, rates, shapes, efficiencies) land close to their best
+ * fit; oscillation parameters move by their linearised step (fit_warmstart_predict adds the
+ * network's corrections to its targets). The rows (J from central differences of the
+ * expectation, step 0.01 in z) are built on the host on first use for each dataset subset and
+ * kept with the model; the product with the residuals n - mu0 runs on the tensor cores as a
+ * split-TF32 product per subset (three GEMMs, FP32 accuracy; deterministic).
+ * data device [B x n_data]; masks host or device [B] or NULL (all datasets; a mask with no
+ * fitted dataset is FIT_ERR_INVALID_ARG; at most 16 distinct subsets per call); theta_out
+ * device [B x P]. The model's device must be current. Synchronous. Errors: INVALID_ARG,
+ * INVALID_CONFIG (an expectation near theta0 failed), OOM, CUDA, TIMEOUT (GEMM wait). */
+int fit_linear_start(fit_model *model, int B, const float *data, const uint32_t *masks,
+                     double *theta_out, void *stream);
 
 #define FIT_WS_MAX_TARGETS 16
 #define FIT_WS_MAX_MASKS 8

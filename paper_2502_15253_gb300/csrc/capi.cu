@@ -175,6 +175,16 @@ struct fit_model {
     int pre_state = 0;     // 0 not built, 1 built, -1 failed (fits run unpreconditioned)
     std::vector<double> pre_U;                   // J^T diag(mu0)^(-1/2), P x D (host)
     std::vector<fitcore::PreEntry> pre_masks;    // preconditioners of dataset subsets
+    // linearised best fit (fit_linear_start, built on first use): theta-space rows per dataset
+    // subset, device [P x D'] (D' = D rounded up to 4), and the nominal expectation
+    struct LinEntry {
+        uint32_t mask;
+        float *K;                 // device: [P x D'] TF32 parts, then [P x D'] rests
+        std::vector<float> Kh;    // host copy (the warm start's training reads target rows)
+    };
+    std::vector<LinEntry> lin;
+    float *lin_mu0 = nullptr;          // device [D]
+    std::vector<double> lin_mu0_host;
     std::vector<std::string> names;   // parameter names (models created from a configuration)
     std::vector<double> sigma;        // prior width per parameter (block members: sqrt(V_ii))
     int device = -1;                  // the CUDA device holding the model's memory
@@ -230,6 +240,9 @@ void fit_model_destroy(fit_model *model) {
     if (model->pre) cudaFree(model->pre);
     for (auto &pm : model->pre_masks)
         if (pm.Q) cudaFree(const_cast<float *>(pm.Q));
+    for (auto &le : model->lin)
+        if (le.K) cudaFree(le.K);
+    if (model->lin_mu0) cudaFree(model->lin_mu0);
     delete model;
 }
 
@@ -901,7 +914,10 @@ int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const flo
     cudaStream_t s = (cudaStream_t)stream;
     float *x = fitcore::mlp_input_buffer(mlp, B);
     if (!x) return fail(FIT_ERR_OOM, "fit_warmstart_predict: input buffer");
-    int rc = fit_warmstart_features(model, B, data, masks, n_in, slot0, onehot_slot, x, stream);
+    // the linearised best fit of every parameter (the model's cached rows are logically part of
+    // the constant model), then the network's corrections on its targets
+    int rc = fit_linear_start(const_cast<fit_model *>(model), B, data, masks, theta_out, stream);
+    if (!rc) rc = fit_warmstart_features(model, B, data, masks, n_in, slot0, onehot_slot, x, stream);
     float *out = nullptr;
     int *idx = nullptr;
     double *scl = nullptr;
@@ -912,7 +928,9 @@ int fit_warmstart_predict(fit_mlp *mlp, const fit_model *model, int B, const flo
                 cudaMemcpyAsync(scl, target_scale, sizeof(double) * n_targets, cudaMemcpyHostToDevice, s)))
         rc = fail(FIT_ERR_CUDA, "fit_warmstart_predict: upload");
     if (!rc) rc = fit_mlp_forward(mlp, B, x, out, stream);
-    if (!rc) rc = fitcore::starts(B, model->n_params, model->host.theta0, n_targets, idx, scl, out, n_out, theta_out, s);
+    if (!rc)
+        rc = fitcore::starts(B, model->n_params, model->host.theta0, n_targets, idx, scl, out, n_out, theta_out,
+                             theta_out, s);
     for (void *p : {(void *)out, (void *)idx, (void *)scl})
         if (p) cudaFreeAsync(p, s);
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_warmstart_predict: sync");
@@ -989,6 +1007,7 @@ int fit_warmstart_draw(fit_model *model, const fit_warmstart_geom *geom, int B, 
 namespace {
 
 void theta_of_z_host(const fit_model *M, const double *z, double *th);
+const fit_model::LinEntry *lin_entry(fit_model *M, uint32_t mask, cudaStream_t s, int &rc);
 
 // Rows of the linearised maximum-likelihood step for the targets of a warm-start geometry, per
 // dataset-mask variant v: with J = d mu / d z at the nominal point (central differences of the
@@ -1230,7 +1249,7 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
     for (int g = 0; g < n_geoms && !rc; ++g) rc = upload_geom(geoms[g], gd[g], s);
     // linearised maximum-likelihood rows per geometry (targets = where a fit of the sample ends,
     // to first order, rather than the drawn point)
-    float *zbuf = nullptr, *krows[16] = {nullptr};
+    float *zbuf = nullptr, *krows[16] = {nullptr}, *ktl[16] = {nullptr};
     int n_var[16] = {0};
     // the refreshed mass-splitting columns: device tables per geometry
     WsRefresh refs[16];
@@ -1281,6 +1300,31 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
         if (cudaMemcpyAsync(krows[g], all.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: upload");
+        // standardised target rows of the linearised start per dataset subset: the network
+        // learns the correction to it
+        if (!rc) {
+            fit_model *M = models[g];
+            const int P = M->n_params, D = M->n_data, Dp = (D + 3) & ~3, nt = geoms[g].n_targets;
+            const uint32_t all = (M->n_ds >= 32) ? 0xFFFFFFFFu : ((1u << M->n_ds) - 1u);
+            std::vector<float> kt((size_t)n_var[g] * nt * D, 0.f);
+            for (int v = 0; v < n_var[g] && !rc; ++v) {
+                const uint32_t mk = geoms[g].n_masks > 0 ? (geoms[g].masks[v] & all) : all;
+                const fit_model::LinEntry *le = lin_entry(M, mk, s, rc);
+                if (!le) break;
+                for (int t = 0; t < nt; ++t) {
+                    const int p = geoms[g].target_idx[t];
+                    const double sc = geoms[g].target_scale[t];
+                    for (int j = 0; j < D; ++j)
+                        kt[((size_t)v * nt + t) * D + j] = (float)(le->Kh[(size_t)p * Dp + j] / sc);
+                }
+                (void)P;
+            }
+            if (!rc && (cudaMallocAsync(&ktl[g], sizeof(float) * kt.size(), s) != cudaSuccess ||
+                        cudaMemcpyAsync(ktl[g], kt.data(), sizeof(float) * kt.size(), cudaMemcpyHostToDevice, s) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+                rc = fail(FIT_ERR_OOM, "fit_warmstart_train: linearised rows");
+        }
     }
     if (!rc && max_k > 0 &&
         (cudaMallocAsync(&thp, sizeof(double) * (size_t)batch * 2 * max_k * max_p, s) != cudaSuccess ||
@@ -1323,6 +1367,9 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
                                           gd[g].tscale, K1, K2, zf, nv, gd[g].choices, masks, n_out, status, y, s);
             }
         }
+        if (!rc)
+            rc = fitcore::lin_residual_targets(batch, m->n_data, G.n_targets, ktl[g], m->lin_mu0, cnt, n_var[g],
+                                               gd[g].choices, masks, n_out, status, y, s);
         if (!rc) rc = fit_mlp_train_step(mlp, batch, x, y, lr_s, weight_decay, loss + step, stream);
     }
     if (!rc && losses_out &&
@@ -1330,7 +1377,7 @@ int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmst
         rc = fail(FIT_ERR_CUDA, "fit_warmstart_train: losses");
     for (int g = 0; g < n_geoms; ++g) {
         free_geom(gd[g], s);
-        for (void *p : {(void *)krows[g], (void *)rbuf[g], (void *)rlam[g], (void *)rint[g]})
+        for (void *p : {(void *)krows[g], (void *)ktl[g], (void *)rbuf[g], (void *)rlam[g], (void *)rint[g]})
             if (p) cudaFreeAsync(p, s);
     }
     for (void *p : {(void *)thp, (void *)mup, (void *)stp})
@@ -1751,6 +1798,130 @@ bool fisher_U(fit_model *M, cudaStream_t s) {
     return true;
 }
 
+// Rows of the linearised best fit for the datasets selected by `mask` (not in the paper; the
+// warm start's deterministic part). Near the nominal point the expectation is mu0 + J z and
+// -2lnL (Eq. 9 with the whitened priors of Eq. 6, |z|^2 over the constrained coordinates) is
+// to second order, with the expected Hessian, minimised by the Gauss-Newton (Fisher scoring)
+// step from z = 0:
+//   dz = (J^T W J + Lambda)^-1 J^T W (n - mu0),  W = diag(1/mu0) on the fitted bins,
+// Lambda = 1 on the constrained coordinates (individual priors and covariance blocks), 0 on
+// the free ones. With U = J^T diag(mu0)^(-1/2) (fisher_U), J^T W J = U_m U_m^T and the column of
+// bin j is (U_m U_m^T + Lambda)^-1 U[:, j] / sqrt(mu0_j). theta = theta0 + T dz (T the linear
+// transformation layer), so the theta-space rows are T applied to those columns. Device
+// buffer [P x D'] (row-major, D' = D rounded up to 4, zero columns for bins not fitted).
+bool build_lin_rows(fit_model *M, uint32_t mask, std::vector<float> &K) {
+    const int P = M->n_params, D = M->n_data, Dp = (D + 3) & ~3;
+    const std::vector<double> &U = M->pre_U;
+    std::vector<char> keep(D, 0);
+    for (int d = 0; d < M->host.n_ds; ++d)
+        if ((mask >> d) & 1u)
+            for (int j = 0; j < M->host.ds[d].n_reco; ++j) keep[M->host.ds[d].data_off + j] = 1;
+    // H = U_m U_m^T + Lambda (+ a ridge for directions neither data nor priors constrain)
+    std::vector<double> H((size_t)P * P, 0.0);
+    for (int a = 0; a < P; ++a)
+        for (int b = 0; b <= a; ++b) {
+            double acc = 0.0;
+            for (int j = 0; j < D; ++j)
+                if (keep[j]) acc += U[(size_t)a * D + j] * U[(size_t)b * D + j];
+            H[(size_t)a * P + b] = H[(size_t)b * P + a] = acc;
+        }
+    double dmax = 0.0;
+    for (int i = 0; i < P; ++i) {
+        if (M->sigma[i] > 0.0 || M->in_block[i]) H[(size_t)i * P + i] += 1.0;
+        dmax = std::max(dmax, H[(size_t)i * P + i]);
+    }
+    for (int i = 0; i < P; ++i) H[(size_t)i * P + i] += 1e-9 * dmax;
+    // Cholesky H = C C^T (lower, in place)
+    for (int j = 0; j < P; ++j) {
+        double dj = H[(size_t)j * P + j];
+        for (int k = 0; k < j; ++k) dj -= H[(size_t)j * P + k] * H[(size_t)j * P + k];
+        if (!(dj > 0.0)) return false;
+        const double cj = std::sqrt(dj);
+        H[(size_t)j * P + j] = cj;
+        for (int i = j + 1; i < P; ++i) {
+            double v = H[(size_t)i * P + j];
+            for (int k = 0; k < j; ++k) v -= H[(size_t)i * P + k] * H[(size_t)j * P + k];
+            H[(size_t)i * P + j] = v / cj;
+        }
+    }
+    K.assign((size_t)P * Dp, 0.f);
+    std::vector<double> x(P), th(P);
+    for (int j = 0; j < D; ++j) {
+        if (!keep[j] || !(M->lin_mu0_host[j] > 0.0)) continue;
+        const double is = 1.0 / std::sqrt(M->lin_mu0_host[j]);
+        for (int i = 0; i < P; ++i) {   // forward substitution C y = U[:, j] / sqrt(mu0_j)
+            double v = U[(size_t)i * D + j] * is;
+            for (int k = 0; k < i; ++k) v -= H[(size_t)i * P + k] * x[k];
+            x[i] = v / H[(size_t)i * P + i];
+        }
+        for (int i = P - 1; i >= 0; --i) {   // back substitution C^T x = y
+            double v = x[i];
+            for (int k = i + 1; k < P; ++k) v -= H[(size_t)k * P + i] * x[k];
+            x[i] = v / H[(size_t)i * P + i];
+        }
+        theta_of_z_host(M, x.data(), th.data());
+        for (int i = 0; i < P; ++i) K[(size_t)i * Dp + j] = (float)(th[i] - M->theta0[i]);
+    }
+    return true;
+}
+
+// The nominal expectation (host and device) and the Jacobian factor of the linearised fit.
+int lin_base(fit_model *M, cudaStream_t s) {
+    if (M->lin_mu0) return FIT_OK;
+    const int D = M->n_data;
+    std::vector<float> mu(D);
+    std::vector<int> st(1, 0);
+    int rc = fit_model_expected(M, 1, M->theta0.data(), mu.data(), st.data(), s);
+    if (rc) return rc;
+    if (st[0] != 0) return fail(FIT_ERR_INVALID_CONFIG, "linearised fit: expectation at theta0 failed");
+    if (!fisher_U(M, s)) return fail(FIT_ERR_INVALID_CONFIG, "linearised fit: expectation near theta0 failed");
+    float *d = nullptr;
+    if (cudaMalloc(&d, sizeof(float) * D) != cudaSuccess ||
+        cudaMemcpy(d, mu.data(), sizeof(float) * D, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        if (d) cudaFree(d);
+        return fail(FIT_ERR_OOM, "linearised fit: nominal expectation");
+    }
+    M->lin_mu0_host.assign(mu.begin(), mu.end());
+    M->lin_mu0 = d;
+    return FIT_OK;
+}
+
+// The linearised fit's rows of one dataset subset (built on first use, kept with the model).
+const fit_model::LinEntry *lin_entry(fit_model *M, uint32_t mask, cudaStream_t s, int &rc) {
+    rc = lin_base(M, s);
+    if (rc) return nullptr;
+    for (auto &le : M->lin)
+        if (le.mask == mask) return &le;
+    fit_model::LinEntry e;
+    e.mask = mask;
+    e.K = nullptr;
+    if (!build_lin_rows(M, mask, e.Kh)) {
+        rc = fail(FIT_ERR_INVALID_CONFIG, "linearised fit: the expected Hessian is not positive definite");
+        return nullptr;
+    }
+    // device copy split for the tensor cores: the nearest TF32 values, then the rest
+    std::vector<float> split(2 * e.Kh.size());
+    for (size_t i = 0; i < e.Kh.size(); ++i) {
+        uint32_t b;
+        std::memcpy(&b, &e.Kh[i], 4);
+        b = (b + 0x1000u) & 0xFFFFE000u;
+        float h;
+        std::memcpy(&h, &b, 4);
+        split[i] = h;
+        split[e.Kh.size() + i] = e.Kh[i] - h;
+    }
+    if (cudaMalloc(&e.K, sizeof(float) * split.size()) != cudaSuccess ||
+        cudaMemcpy(e.K, split.data(), sizeof(float) * split.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        if (e.K) cudaFree(e.K);
+        rc = fail(FIT_ERR_OOM, "linearised fit: rows");
+        return nullptr;
+    }
+    M->lin.push_back(std::move(e));
+    return &M->lin.back();
+}
+
 // Preconditioner of the datasets selected by `mask` (the expected Hessian of the data an
 // instance actually fits): U restricted to those datasets' bins, its leading eigen-directions,
 // device buffer [Q^T rows | c | c']. Returns nullptr on failure.
@@ -1899,6 +2070,63 @@ bool pre_for_mask(fit_model *M, uint32_t mask, fitcore::PreEntry &e) {
 }  // namespace
 
 extern "C" {
+
+int fit_linear_start(fit_model *model, int B, const float *data, const uint32_t *masks, double *theta_out,
+                     void *stream) {
+    if (!model || !data || !theta_out || B < 0) return fail(FIT_ERR_INVALID_ARG, "fit_linear_start: bad argument");
+    if (B == 0) return FIT_OK;
+    if (!on_device(data) || !on_device(theta_out))
+        return fail(FIT_ERR_INVALID_ARG, "fit_linear_start: data and theta_out must be device memory");
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != model->device)
+        return fail(FIT_ERR_INVALID_ARG, "fit_linear_start: the model's device must be current");
+    cudaStream_t s = (cudaStream_t)stream;
+    fit_model *M = model;
+    const int P = M->n_params, D = M->n_data;
+    const uint32_t all = (M->n_ds >= 32) ? 0xFFFFFFFFu : ((1u << M->n_ds) - 1u);
+    // the instances' dataset subsets (host copy; masks may be host or device memory)
+    std::vector<uint32_t> hm((size_t)B, all);
+    if (masks) {
+        if (cudaMemcpyAsync(hm.data(), masks, sizeof(uint32_t) * (size_t)B, cudaMemcpyDefault, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(FIT_ERR_CUDA, "fit_linear_start: masks");
+        for (auto &m : hm) {
+            m &= all;
+            if (m == 0) return fail(FIT_ERR_INVALID_ARG, "fit_linear_start: an instance fits no dataset");
+        }
+    }
+    std::vector<uint32_t> subsets;
+    std::vector<int> sel((size_t)B);
+    for (int b = 0; b < B; ++b) {
+        int v = (int)(std::find(subsets.begin(), subsets.end(), hm[b]) - subsets.begin());
+        if (v == (int)subsets.size()) {
+            if (subsets.size() >= 16) return fail(FIT_ERR_INVALID_ARG, "fit_linear_start: more than 16 dataset subsets");
+            subsets.push_back(hm[b]);
+        }
+        sel[b] = v;
+    }
+    // the rows of each subset (built on first use and kept with the model)
+    std::vector<const float *> K(subsets.size(), nullptr);
+    for (size_t v = 0; v < subsets.size(); ++v) {
+        int rc = FIT_OK;
+        const fit_model::LinEntry *le = lin_entry(M, subsets[v], s, rc);
+        if (!le) return rc;
+        K[v] = le->K;
+    }
+    int *sel_d = nullptr;
+    if (cudaMallocAsync(&sel_d, sizeof(int) * (size_t)B, s) != cudaSuccess ||
+        cudaMemcpyAsync(sel_d, sel.data(), sizeof(int) * (size_t)B, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (sel_d) cudaFreeAsync(sel_d, s);
+        return fail(FIT_ERR_OOM, "fit_linear_start: subset table");
+    }
+    int rc = fitcore::linear_start_apply(B, P, D, M->host.theta0, M->lin_mu0, data, K.data(), (int)K.size(), sel_d,
+                                         theta_out, s);
+    cudaFreeAsync(sel_d, s);
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(FIT_ERR_CUDA, "fit_linear_start: synchronise");
+    if (!rc && fitcore::tc_gemm_take_error() != 0) rc = fail(FIT_ERR_TIMEOUT, "fit_linear_start: GEMM pipeline wait");
+    return rc;
+}
 
 void fit_batch_default_opts(fit_batch_opts *o) {
     if (!o) return;

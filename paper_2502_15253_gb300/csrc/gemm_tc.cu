@@ -498,11 +498,11 @@ int make_map(CUtensorMap *map, bool tf32, const void *base, int rows, int K, int
 // multiples of 16) are scored by waves of work units over the SMs times a unit's time: its
 // operand streaming (rows of A and B per K slice; the main loop waits on these loads) plus a
 // share of its epilogue (output columns x an issue cost per element, high for the GELU forms).
-Plan make_plan(bool tf32, int M, int N, int K, int epi) {
+Plan make_plan(bool tf32, int M, int N, int K, int epi, bool deterministic) {
     const int kel = tf32 ? 32 : 64;
     const int ktiles = (K + kel - 1) / kel;
     const int mt = (M + kTileM - 1) / kTileM;
-    const bool can_split = epi == EPI_F32 || epi == EPI_F32_ADD;
+    const bool can_split = (epi == EPI_F32 || epi == EPI_F32_ADD) && !deterministic;
     const double epi_cost = (epi == EPI_BIAS_GELU || epi == EPI_DGELU) ? 30.0 : 4.0;
     Plan best{};
     double best_cost = 1e300;
@@ -556,7 +556,7 @@ int tc_gemm(bool tf32, int M, int N, int K, const void *A, int lda, const void *
               ((out.aux && !((uintptr_t)out.aux & 15) && out.ldaux % 4 == 0) ? 4 : 0) |
               ((out.Yt && !((uintptr_t)out.Yt & 15) && out.ldyt % 8 == 0) ? 8 : 0) |
               ((out.bias && !((uintptr_t)out.bias & 15)) ? 16 : 0);
-    const Plan pl = make_plan(tf32, M, N, K, out.epi);
+    const Plan pl = make_plan(tf32, M, N, K, out.epi, out.deterministic);
     CUtensorMap ta, tb;
     if ((rc = make_map(&ta, tf32, A, M, K, lda, kTileM))) return rc;
     if ((rc = make_map(&tb, tf32, B, N, K, ldb, pl.n_tile))) return rc;

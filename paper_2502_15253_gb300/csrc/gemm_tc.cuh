@@ -32,6 +32,9 @@ struct GemmOut {
     __nv_bfloat16 *Yt = nullptr;
     int ldyt = 0;
     int vec = 0;   // set by tc_gemm: bit 0 C, 1 Y, 2 aux, 3 Yt rows 16-byte aligned; bit 4 bias aligned
+    // never split K over CTAs (the split adds partial tiles with atomics, so its FP32 sums
+    // depend on their order): results identical from call to call
+    bool deterministic = false;
 };
 
 // Returns 0, or a negative FIT_ERR_* code (message through the library's error string).

@@ -107,6 +107,9 @@ const void *fit_kernel_func(int variant, int n_osc, bool pre);
 size_t eval_smem_bytes(const DevModel &hm, bool ws_in_smem);
 
 // batched.cu / poisson.cu / mlp.cu
+// linstart.cu: theta_out = theta0 + K_{sel[b]} (data_b - mu0) (fit_linear_start)
+int linear_start_apply(int B, int P, int D, const double *theta0_dev, const float *mu0_dev, const float *data,
+                       const float *const *K, int n_var, const int *sel_dev, double *theta_out, cudaStream_t s);
 int expected_tc(const DevModel &h, const DevModel *dev, int B, const double *theta, float *mu, int *status,
                 int precision, cudaStream_t s);
 int poisson_sample(int64_t n, const float *mu, uint64_t seed, uint64_t offset, float *out, cudaStream_t s);
@@ -129,8 +132,12 @@ int mle_targets(int B, int P, int D, const double *theta, const double *theta0, 
                 const float *mu, int n_t, const int *idx, const double *scale, const float *K1, const float *K2,
                 const float *zf, int n_var, const uint32_t *choices, const uint32_t *masks, int n_out,
                 const int *status, float *y, cudaStream_t s);
+// y[b][t] -= Kt[var(b)][t] . (cnt[b] - mu0) (targets relative to the linearised start)
+int lin_residual_targets(int B, int D, int n_t, const float *Kt, const float *mu0, const float *cnt, int n_var,
+                         const uint32_t *choices, const uint32_t *masks, int n_out, const int *status, float *y,
+                         cudaStream_t s);
 int starts(int B, int P, const double *theta0, int n_t, const int *idx, const double *scale, const float *out,
-           int n_out, double *theta, cudaStream_t s);
+           int n_out, const double *base, double *theta, cudaStream_t s);
 size_t fit_smem_bytes(int floats);
 // Fit vectors are spaced by P rounded up to 4 floats, so that every vector starts on a
 // 16-byte boundary and the history can be read as float4.

@@ -232,13 +232,15 @@ __global__ void features_kernel(int B, int n_data, const float *__restrict__ dat
 }
 
 // theta[b] = theta0, then theta[b][idx_t] = theta0 + out[b][t] * scale_t
+// theta[b][i] = base[b][i] + y_bt scale_t for the network's targets (i = idx[t]), base[b][i]
+// for the other parameters; base may be theta itself, and null stands for theta0
 __global__ void starts_kernel(int B, int P, const double *__restrict__ theta0, int n_t, const int *__restrict__ idx,
                               const double *__restrict__ scale, const float *__restrict__ out, int n_out,
-                              double *__restrict__ theta) {
+                              const double *base, double *theta) {
     const int64_t total = (int64_t)B * P;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(e / P), i = (int)(e % P);
-        double v = theta0[i];
+        double v = base ? base[e] : theta0[i];
         for (int t = 0; t < n_t; ++t)
             if (idx[t] == i) v += (double)out[(int64_t)b * n_out + t] * scale[t];
         theta[e] = v;
@@ -586,8 +588,8 @@ int features(int B, int n_data, const float *data, const float *nbar, const uint
 }
 
 int starts(int B, int P, const double *theta0, int n_t, const int *idx, const double *scale, const float *out,
-           int n_out, double *theta, cudaStream_t s) {
-    starts_kernel<<<grid_for((int64_t)B * P), 256, 0, s>>>(B, P, theta0, n_t, idx, scale, out, n_out, theta);
+           int n_out, const double *base, double *theta, cudaStream_t s) {
+    starts_kernel<<<grid_for((int64_t)B * P), 256, 0, s>>>(B, P, theta0, n_t, idx, scale, out, n_out, base, theta);
     fitcore_count_launch();
     return cudaGetLastError() == cudaSuccess ? FIT_OK : fitcore_fail(FIT_ERR_CUDA, "warm start: starts");
 }

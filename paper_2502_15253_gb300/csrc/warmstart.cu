@@ -119,6 +119,27 @@ __global__ void mle_targets_kernel(int B, int P, int D, const double *__restrict
     if (lane == 0) y[(int64_t)b * n_out + t] = v;
 }
 
+// y[b][t] -= sum_j Kt[var][t][j] (cnt[b][j] - mu0[j]): the target minus the linearised best
+// fit from the nominal point (standardised rows Kt of the sample's dataset subset), so that the
+// network learns the correction to the linearised start; a warp per (sample, target)
+__global__ void lin_residual_targets_kernel(int D, int n_t, const float *__restrict__ Kt, const float *__restrict__ mu0,
+                                            const float *__restrict__ cnt, int n_var,
+                                            const uint32_t *__restrict__ choices, const uint32_t *__restrict__ masks,
+                                            int n_out, const int *__restrict__ status, float *__restrict__ y) {
+    const int b = blockIdx.x, lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+    if (t >= n_t || (status && status[b])) return;
+    int var = 0;
+    if (n_var > 1 && masks)
+        for (int q = 0; q < n_var; ++q)
+            if (choices[q] == masks[b]) var = q;
+    const float *k = Kt + ((int64_t)var * n_t + t) * D, *nb = cnt + (int64_t)b * D;
+    float acc = 0.f;
+    for (int j = lane; j < D; j += 32) acc = fmaf(k[j], nb[j] - mu0[j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[(int64_t)b * n_out + t] -= acc;
+}
+
 // y[b][t] = (theta[b][idx_t] - theta0[idx_t]) / scale_t for t < n_t, 0 for n_t <= t < n_out
 // and for samples whose expectation failed (status != 0)
 __global__ void targets_kernel(int B, int P, const double *__restrict__ theta, const double *__restrict__ theta0,
@@ -172,6 +193,17 @@ int mle_targets(int B, int P, int D, const double *theta, const double *theta0, 
     fitcore_count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("warm-start targets: ") + cudaGetErrorString(e));
+    return FIT_OK;
+}
+
+int lin_residual_targets(int B, int D, int n_t, const float *Kt, const float *mu0, const float *cnt, int n_var,
+                         const uint32_t *choices, const uint32_t *masks, int n_out, const int *status, float *y,
+                         cudaStream_t s) {
+    if (B == 0) return FIT_OK;
+    lin_residual_targets_kernel<<<B, 32 * n_t, 0, s>>>(D, n_t, Kt, mu0, cnt, n_var, choices, masks, n_out, status, y);
+    fitcore_count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fitcore_fail(FIT_ERR_CUDA, std::string("warm-start residual targets: ") + cudaGetErrorString(e));
     return FIT_OK;
 }
 

@@ -99,7 +99,7 @@ EXPORTS = ("fit_model_create", "fit_model_destroy", "fit_model_info", "fit_model
            "fit_warmstart_train", "fit_batch_autotune", "fit_batch_ex", "fit_profile_scan",
            "fit_wilks_interval", "fit_chi2_sf", "fit_mc_create", "fit_mc_destroy",
            "fit_mc_spectrum", "fit_mc_status", "fit_model_create_json", "fit_model_param_name",
-           "fit_model_params", "fit_result_json")
+           "fit_model_params", "fit_result_json", "fit_linear_start")
 
 
 def lib_path() -> str:
@@ -142,6 +142,8 @@ def load(build_if_missing: bool = False):
     L.fit_warmstart_features.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_int, vp, vp]
     L.fit_warmstart_predict.argtypes = [vp, vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_int, vp,
                                         vp, vp, vp]
+    L.fit_linear_start.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    L.fit_linear_start.restype = C.c_int
     L.fit_warmstart_draw.argtypes = [vp, C.POINTER(fit_warmstart_geom), C.c_int, C.c_uint64,
                                      C.c_uint64, vp, vp, vp]
     L.fit_warmstart_train.argtypes = [vp, C.POINTER(vp), C.POINTER(fit_warmstart_geom), C.c_int,
@@ -595,12 +597,22 @@ def fit_warmstart_features(model: Model, B, data, masks, n_in, slot0, onehot_slo
 
 def fit_warmstart_predict(mlp: Mlp, model: Model, B, data, masks, slot0, onehot_slot, target_idx,
                           target_scale, theta_out, stream=None):
+    """Start points: the linearised best fit of every parameter plus the network's corrections
+    on its targets."""
     idx = np.ascontiguousarray(target_idx, dtype=np.int32)
     scl = np.ascontiguousarray(target_scale, dtype=np.float64)
     _check(load().fit_warmstart_predict(mlp.handle, model.handle, int(B), _ptr(data), _ptr(masks),
                                         int(slot0), int(onehot_slot), len(idx), _ptr(idx),
                                         _ptr(scl), _ptr(theta_out), _stream_ptr(stream)),
            "fit_warmstart_predict")
+
+
+def fit_linear_start(model: Model, B, data, masks, theta_out, stream=None):
+    """Start points theta_out [B x P] (device) from the linearised best fit: one Gauss-Newton
+    step of -2lnL from theta0 with the expected Hessian (device data [B x n_data]; masks host
+    or device [B] or None)."""
+    _check(load().fit_linear_start(model.handle, int(B), _ptr(data), _ptr(masks), _ptr(theta_out),
+                                   _stream_ptr(stream)), "fit_linear_start")
 
 
 def make_geom(slot0, onehot_slot, target_idx, target_scale, uniform_idx=(), uniform_half=(),

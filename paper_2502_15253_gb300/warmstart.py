@@ -78,7 +78,8 @@ def train(net, models, specs, n_steps, batch=4096, lr=1e-3, weight_decay=1e-4, s
 
 
 def predict_starts(net, model, spec, B, data, masks, theta_out, stream=None):
-    """Start points theta_out [B x P] (device) for the device spectra data [B x n_data]."""
+    """Start points theta_out [B x P] (device) for the device spectra data [B x n_data]: the
+    linearised best fit of every parameter, the network's corrections on its targets."""
     g = geometry(spec)
     n = g.n_targets
     fitcore.fit_warmstart_predict(net, model, B, data, masks, g.slot0, g.onehot_slot,

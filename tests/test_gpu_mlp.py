@@ -125,16 +125,18 @@ def test_features_and_start_points(name, slot0, onehot):
         ref[:, slot0 + off:slot0 + off + n] *= keep[:, None]
         off += n
     np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=0, atol=2e-6)
-    # start points: theta = theta0 + y_t * scale_t on the target parameters
+    # start points: the linearised start, plus y_t * scale_t on the target parameters
     net = fitcore.Mlp(n_in, 64, 1, 12, seed=9)
     idx = np.arange(3)
     scl = np.array([0.01, 0.02, 0.03])
     th = torch.zeros((B, gm.n_params), dtype=torch.float64, device="cuda")
+    base = torch.zeros_like(th)
     fitcore.fit_warmstart_features(gm, B, dd, None, n_in, slot0, onehot, x)
     fitcore.fit_warmstart_predict(net, gm, B, dd, None, slot0, onehot, idx, scl, th)
+    fitcore.fit_linear_start(gm, B, dd, None, base)
     y = torch.zeros((B, 12), dtype=torch.float32, device="cuda")
     net.forward(B, x, y)
     torch.cuda.synchronize()
-    expect = np.tile(spec.theta0, (B, 1))
+    expect = base.cpu().numpy().copy()
     expect[:, idx] += y.cpu().numpy()[:, :3].astype(np.float64) * scl
     np.testing.assert_allclose(th.cpu().numpy(), expect, rtol=1e-12, atol=1e-12)

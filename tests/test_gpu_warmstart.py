@@ -116,25 +116,21 @@ def test_training_learns_and_warm_fits_agree_with_cold(c1, c2):
           f"warm {warm['iters'].mean():.1f} cold {cold['iters'].mean():.1f}, evals warm "
           f"{warm['n_evals'].mean():.1f} cold {cold['n_evals'].mean():.1f}")
     assert same.mean() >= 0.8 and not_worse.mean() >= 0.95
-    # the 12 predicted parameters are a small part of the 291 the fit moves, so the iteration
-    # count hardly changes on this model (a start at the cold fit's own values of the 12 saves
-    # about 4 % of the evaluations); it must not grow
-    assert warm["iters"].mean() <= 1.05 * cold["iters"].mean()
+    # the warm start (every parameter at the linearised best fit, the network's corrections on
+    # 12 of them) must not cost iterations on this model (measured 19.4 against 21.8)
+    assert warm["iters"].mean() <= 1.0 * cold["iters"].mean()
 
 
 def test_warm_start_saves_evaluations_on_the_53km_model(c1, c2):
     """Held-out pseudo-experiments of the 53 km model drawn by the ensemble recipe (true
-    sin^2 th13 and dm2_31 within +-3 sigma, Poisson counts): fits from the network's starts reach
-    the cold fits' minima (within 1e-3 in -2lnL, so at the cold fits' parity with the oracle) with
-    measurably fewer evaluations. The most any network of these 12 outputs can save: starts at
-    the cold fits' own values of the 12 need 30 % fewer evaluations on this model; the rest of
-    the gap is the network's own regression error (0.05-0.26 prior widths RMS per target)."""
+    sin^2 th13 and dm2_31 within +-3 sigma, Poisson counts): fits from the warm start (the
+    linearised best fit of all 460 parameters with the network's corrections on its 12 targets)
+    reach the cold fits' minima (within 1e-3 in -2lnL, so at the cold fits' parity with the
+    oracle) with measurably fewer evaluations (measured 15 %)."""
     spec1, m1 = c1
     spec2, m2 = c2
     net = warmstart.network(seed=3)
-    # 12 epochs over the same 2M samples (about 35 s): one epoch leaves the network short of
-    # the linearised best fit it is trained on (no gain), twelve bring the 53 km model's
-    # evaluations down by 8-9 %
+    # 12 epochs over the same 2M samples (about 35 s)
     warmstart.train(net, [m1, m2], [spec1, spec2], n_steps=488, batch=4096, lr=1e-3, epochs=12)
     B = 512
     table = synth.make_ensemble(B, {"c1": spec1, "c2": spec2}, frac_c2=1.0, base=9_000_000)
@@ -156,4 +152,4 @@ def test_warm_start_saves_evaluations_on_the_53km_model(c1, c2):
     print(f"53 km model: evaluations warm {warm['n_evals'].mean():.2f} cold "
           f"{cold['n_evals'].mean():.2f} ({100 * gain:.1f} % fewer), same minimum {same.mean():.4f}")
     assert same.mean() >= 0.99
-    assert gain >= 0.04
+    assert gain >= 0.10
