@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -182,7 +183,7 @@ struct fit_model {
         float *K;                 // device: [P x D'] TF32 parts, then [P x D'] rests
         std::vector<float> Kh;    // host copy (the warm start's training reads target rows)
     };
-    std::vector<LinEntry> lin;
+    std::deque<LinEntry> lin;          // (a deque: entries stay where they are as it grows)
     float *lin_mu0 = nullptr;          // device [D]
     std::vector<double> lin_mu0_host;
     std::vector<std::string> names;   // parameter names (models created from a configuration)
@@ -1888,7 +1889,10 @@ int lin_base(fit_model *M, cudaStream_t s) {
 }
 
 // The linearised fit's rows of one dataset subset (built on first use, kept with the model).
+// Guarded by the lock of the preconditioner builds, which share the Jacobian factor (fisher_U),
+// so that calls from several host threads on one model are safe.
 const fit_model::LinEntry *lin_entry(fit_model *M, uint32_t mask, cudaStream_t s, int &rc) {
+    std::lock_guard<std::mutex> lock(g_pre_mutex);
     rc = lin_base(M, s);
     if (rc) return nullptr;
     for (auto &le : M->lin)
