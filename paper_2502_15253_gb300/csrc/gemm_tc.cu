@@ -560,11 +560,21 @@ int tc_gemm(bool tf32, int M, int N, int K, const void *A, int lda, const void *
     CUtensorMap ta, tb;
     if ((rc = make_map(&ta, tf32, A, M, K, lda, kTileM))) return rc;
     if ((rc = make_map(&tb, tf32, B, N, K, ldb, pl.n_tile))) return rc;
-    if (!err_dev) {
-        if (cudaGetSymbolAddress((void **)&err_dev, g_gemm_err) != cudaSuccess) {
+    if (!err_dev) {   // the library's flag: its device address, looked up once per device
+        static std::mutex flag_mutex;
+        static int *flag_addr[64] = {nullptr};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
             cudaGetLastError();
+            return fitcore_fail(FIT_ERR_CUDA, "tensor-core GEMM: current device");
+        }
+        std::lock_guard<std::mutex> lock(flag_mutex);
+        if (!flag_addr[dev] && cudaGetSymbolAddress((void **)&flag_addr[dev], g_gemm_err) != cudaSuccess) {
+            cudaGetLastError();
+            flag_addr[dev] = nullptr;
             return fitcore_fail(FIT_ERR_CUDA, "tensor-core GEMM: error flag");
         }
+        err_dev = flag_addr[dev];
     }
     const size_t smem = 1024 + (size_t)pl.stages * (kTileM + pl.n_tile) * kRowBytes + kEpiWarps * sizeof(EpiStage) +
                         (2 * pl.stages + 5) * 8 + 16;
