@@ -444,9 +444,11 @@ int fit_warmstart_draw(fit_model *model, const fit_warmstart_geom *geom, int B, 
  * expectations), except the columns of the free mass splittings among the uniform parameters,
  * which turn with the oscillation phase: those are re-evaluated at each drawn point (two
  * expectations per column and sample) and the step is solved by the Schur complement against
- * the block of all other parameters. Learning rate lr (0.05 + 0.95 (1 +
- * cos(pi s / n_steps)) / 2) at step s. losses_out (host or device [n_steps] double, or NULL)
- * receives each step's batch loss. Synchronous. */
+ * the block of all other parameters. The network learns that target minus the linearised
+ * start of the same counts (fit_linear_start's step from theta0, standardised the same way),
+ * so that fit_warmstart_predict adds its outputs to that start. Learning rate lr (0.05 + 0.95
+ * (1 + cos(pi s / n_steps)) / 2) at step s. losses_out (host or device [n_steps] double, or
+ * NULL) receives each step's batch loss. Synchronous. */
 int fit_warmstart_train(fit_mlp *mlp, fit_model *const *models, const fit_warmstart_geom *geoms,
                         int n_geoms, int n_steps, int batch, float lr, float weight_decay,
                         uint64_t seed, double *losses_out, void *stream);
